@@ -1,0 +1,183 @@
+"""Seeded synthetic inputs for the hybrid LB + FD nematohydrodynamics step.
+
+This module only draws and lays out initial conditions and parameter sets; it
+holds none of the method's arithmetic (no equilibrium, no molecular field, no
+stress).  Both the CUDA library's callers and the FP64 CPU oracle take their
+inputs from here, so the two start from identical bits.
+
+Fields are numpy float64 arrays in structure-of-arrays layout ``[3][N]`` with
+site index ``x + nx*(y + ny*z)``.
+
+Workloads (the paper measures on no public dataset; everything is generated):
+
+* tiny nematic channel 32x32x16: z_hat plus a 0.05 uniform random tilt;
+* single skyrmion tube 96x96x32, q0 = 2 pi/32, radius 12, centred;
+* multi-tube channel 256x256x64, q0 = 2 pi/64, 8 tubes of radius 20 at seeded
+  non-overlapping centres;
+* batched sweep: 64 channels with lateral L in {32,48,64,96}, Lz in {16,24,32},
+  g_x log-uniform in [1e-7, 1e-5], pitch p uniform in [Lz, 2 Lz], one tube each.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# Leslie viscosities for a flow-alignment parameter gamma2/gamma1 = -0.9 with
+# gamma1 = 1: alpha3 - alpha2 = gamma1, alpha3 + alpha2 = gamma2 (Sec. II.A),
+# Parodi alpha6 - alpha5 = gamma2; alpha1 = alpha4' = 0.
+LESLIE_ALIGN_09 = dict(gamma1=1.0, gamma2=-0.9, alpha1=0.0, alpha2=-0.95, alpha3=0.05,
+                       alpha4p=0.0, alpha5=0.45, alpha6=-0.45)
+
+
+def _grid(nx, ny, nz):
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    return x.astype(np.float64), y.astype(np.float64), z.astype(np.float64)
+
+
+def _pack(nx_, ny_, nz_):
+    return np.stack([nx_.ravel(), ny_.ravel(), nz_.ravel()]).astype(np.float64)
+
+
+def uniform_director(nx, ny, nz, direction=(0.0, 0.0, 1.0)):
+    d = np.asarray(direction, dtype=np.float64)
+    d = d / np.linalg.norm(d)
+    N = nx * ny * nz
+    return np.repeat(d[:, None], N, axis=1)
+
+
+def tilted_director(nx, ny, nz, amplitude=0.05, seed=0):
+    """n = normalise(a xi_x, a xi_y, 1), xi ~ U(-1, 1) from numpy PCG64(seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    N = nx * ny * nz
+    xi = rng.uniform(-1.0, 1.0, size=(2, N))
+    n = np.stack([amplitude * xi[0], amplitude * xi[1], np.ones(N)])
+    return n / np.linalg.norm(n, axis=0, keepdims=True)
+
+
+def skyrmion_tubes(nx, ny, nz, centres, radius, handedness=1.0):
+    """Extruded 2D skyrmion ansatz: radial pi-twist of radius R around each centre.
+
+    n = (-s sin(theta) sin(phi), s sin(theta) cos(phi), cos(theta)),
+    theta(r) = pi (1 - r/R) for r < R, else 0, with r and phi about the nearest
+    centre (periodic minimum image in x and y) and s = handedness = +-1.
+    """
+    x, y, _ = _grid(nx, ny, nz)
+    best_r = np.full(x.shape, np.inf)
+    best_dx = np.zeros_like(x)
+    best_dy = np.zeros_like(x)
+    for cx, cy in centres:
+        dx = (x - cx + 0.5 * nx) % nx - 0.5 * nx
+        dy = (y - cy + 0.5 * ny) % ny - 0.5 * ny
+        r = np.hypot(dx, dy)
+        m = r < best_r
+        best_r = np.where(m, r, best_r)
+        best_dx = np.where(m, dx, best_dx)
+        best_dy = np.where(m, dy, best_dy)
+    theta = np.where(best_r < radius, math.pi * (1.0 - best_r / radius), 0.0)
+    phi = np.arctan2(best_dy, best_dx)
+    s = float(handedness)
+    return _pack(-s * np.sin(theta) * np.sin(phi), s * np.sin(theta) * np.cos(phi), np.cos(theta))
+
+
+def place_tubes(nx, ny, count, radius, seed=0, max_tries=100000):
+    """Seeded rejection sampling of tube centres with periodic distance >= 2R."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    centres = []
+    tries = 0
+    while len(centres) < count:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("could not place non-overlapping tubes")
+        c = (float(rng.uniform(0, nx)), float(rng.uniform(0, ny)))
+        ok = True
+        for (px, py) in centres:
+            dx = (c[0] - px + 0.5 * nx) % nx - 0.5 * nx
+            dy = (c[1] - py + 0.5 * ny) % ny - 0.5 * ny
+            if dx * dx + dy * dy < (2 * radius) ** 2:
+                ok = False
+                break
+        if ok:
+            centres.append(c)
+    return centres
+
+
+def twist_mode(nx, ny, nz, amplitude=1e-3, wavenumber=None):
+    """n = (0, cos theta, sin theta), theta = a sin(k x), k = 2 pi / nx by default."""
+    k = 2 * math.pi / nx if wavenumber is None else wavenumber
+    x, _, _ = _grid(nx, ny, nz)
+    th = amplitude * np.sin(k * x)
+    return _pack(np.zeros_like(th), np.cos(th), np.sin(th))
+
+
+def helix(nx, ny, nz, q):
+    """Cholesteric helix along z: n = (cos q z, sin q z, 0)."""
+    _, _, z = _grid(nx, ny, nz)
+    return _pack(np.cos(q * z), np.sin(q * z), np.zeros_like(z))
+
+
+def shear_wave(nx, ny, nz, amplitude, wavenumber=None):
+    """u = (U sin(k z), 0, 0), k = 2 pi / nz by default (periodic box)."""
+    k = 2 * math.pi / nz if wavenumber is None else wavenumber
+    _, _, z = _grid(nx, ny, nz)
+    ux = amplitude * np.sin(k * z)
+    return _pack(ux, np.zeros_like(ux), np.zeros_like(ux))
+
+
+def random_director(nx, ny, nz, seed=0):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    v = rng.normal(size=(3, nx * ny * nz))
+    return v / np.linalg.norm(v, axis=0, keepdims=True)
+
+
+def random_velocity(nx, ny, nz, amplitude, seed=0):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return amplitude * rng.uniform(-1.0, 1.0, size=(3, nx * ny * nz))
+
+
+# ------------------------------------------------------------------ workload presets
+
+def tiny_channel(shifted=True):
+    """32x32x16 nematic channel, tau=1, g_x=1e-6, K=0.04, gamma2/gamma1=-0.9, q0=0."""
+    params = dict(nx=32, ny=32, nz=16, walls_z=True, anchoring="homeotropic", shifted=shifted,
+                  tau=1.0, g=(1e-6, 0.0, 0.0), K=0.04, q0=0.0, W0=0.0, dt_fd=1, **LESLIE_ALIGN_09)
+    n0 = tilted_director(32, 32, 16, amplitude=0.05, seed=0)
+    return params, n0
+
+
+def skyrmion_channel(gx=1e-5, dt_fd=1, shifted=True, K=0.005, nx=96, ny=96, nz=32, radius=12.0):
+    """Single skyrmion tube in Poiseuille flow, 96x96x32, q0 = 2 pi/32."""
+    params = dict(nx=nx, ny=ny, nz=nz, walls_z=True, anchoring="homeotropic", shifted=shifted,
+                  tau=1.0, g=(gx, 0.0, 0.0), K=K, q0=2 * math.pi / 32, W0=0.0, dt_fd=dt_fd,
+                  **LESLIE_ALIGN_09)
+    n0 = skyrmion_tubes(nx, ny, nz, [(nx / 2, ny / 2)], radius)
+    return params, n0
+
+
+def multi_tube_channel(dt_fd=16, shifted=True, K=0.005, seed=0, nx=256, ny=256, nz=64, tubes=8,
+                       radius=20.0, gx=1e-5):
+    """256x256x64, q0 = 2 pi/64, 8 tubes of radius 20 at seeded centres."""
+    params = dict(nx=nx, ny=ny, nz=nz, walls_z=True, anchoring="homeotropic", shifted=shifted,
+                  tau=1.0, g=(gx, 0.0, 0.0), K=K, q0=2 * math.pi / 64, W0=0.0, dt_fd=dt_fd,
+                  **LESLIE_ALIGN_09)
+    centres = place_tubes(nx, ny, tubes, radius, seed=seed)
+    n0 = skyrmion_tubes(nx, ny, nz, centres, radius)
+    return params, n0, centres
+
+
+def batched_sweep(count=64, seed=0, K=0.005, dt_fd=16):
+    """64 channels of uneven size with one tube each; returns a list of (params, n0, centre)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(count):
+        L = int(rng.choice([32, 48, 64, 96]))
+        Lz = int(rng.choice([16, 24, 32]))
+        gx = float(10 ** rng.uniform(-7, -5))
+        pitch = float(rng.uniform(Lz, 2 * Lz))
+        R = 0.25 * L
+        params = dict(nx=L, ny=L, nz=Lz, walls_z=True, anchoring="homeotropic", shifted=True,
+                      tau=1.0, g=(gx, 0.0, 0.0), K=K, q0=2 * math.pi / pitch, W0=0.0, dt_fd=dt_fd,
+                      **LESLIE_ALIGN_09)
+        n0 = skyrmion_tubes(L, L, Lz, [(L / 2, L / 2)], R)
+        out.append((params, n0, (L / 2, L / 2)))
+    return out
