@@ -1,0 +1,328 @@
+"""Throughput benchmark of the hybrid LB + FD nematohydrodynamics step on GB300.
+
+Workload: the 256x256x64 multi-tube channel (8 skyrmion tubes of radius 20,
+q0 = 2 pi/64, g_x = 1e-5, K = 0.005), FP32 arithmetic with shifted FP32
+populations, dt_FD = 16.  One bench step is one hybrid block: dt_FD fused LB
+collide-and-stream launches, one FD predictor-corrector + stress + force update
+and one FP64 diagnostics reduction (mass, Frank energy, tube centroids).
+Metric: MLUPS = sites x LB steps / s (FD, force and diagnostics time included).
+
+The populations (2 x 319 MB) are larger than L2, so no L2 flush is needed
+between steps.  Per-kernel times come from CUDA events on the launching stream
+inside the timed region.  With --gpus N (torchrun) every rank runs its own
+replica of the workload (independent channels, no data-path collective):
+weak scaling, value = sum over ranks.
+
+--impl reference times the FP64 CPU oracle on the machine's host cores on the same
+workload (one LB step per bench step plus the FD update every dt_FD steps).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_SITE_LB = {"f32": 164, "f64": 328, "f16s": 88, "bf16s": 88}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16s", "bf16s"])
+    ap.add_argument("--dt-fd", type=int, default=16)
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison run")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--small", action="store_true", help="64x64x32 case (profiling only)")
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_2503_06610_gb300 import inputs
+    if args.small:
+        params, n0, centres = inputs.multi_tube_channel(dt_fd=args.dt_fd, nx=64, ny=64, nz=32, tubes=2, radius=10)
+        name = f"multi-tube channel 64x64x32, 2 tubes R=10, dt_FD={args.dt_fd}"
+    else:
+        params, n0, centres = inputs.multi_tube_channel(dt_fd=args.dt_fd)
+        name = f"multi-tube channel 256x256x64, 8 tubes R=20, q0=2pi/64, gx=1e-5, dt_FD={args.dt_fd}"
+    return params, n0, centres, name
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+
+def cpu_oracle_mlups(params, n0, sample_lb_steps):
+    """Time the FP64 oracle (as it stands) for `sample_lb_steps` LB steps with the
+    FD update every dt_FD steps; returns (MLUPS, threads, seconds)."""
+    import oracle
+    oracle.build()
+    p = oracle.OracleParams.from_dict(params)
+    sim = oracle.OracleSim(p, n0)
+    t0 = time.perf_counter()
+    sim.step(sample_lb_steps)
+    dt = time.perf_counter() - t0
+    return p.N * sample_lb_steps / dt / 1e6, oracle.num_threads(), dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    params, n0, centres, name = workload(args)
+    import oracle
+    oracle.build()
+    p = oracle.OracleParams.from_dict(params)
+    sim = oracle.OracleSim(p, n0)
+    for _ in range(args.warmup):
+        sim.step(1)
+    t0 = time.perf_counter()
+    sim.step(args.steps)
+    el = time.perf_counter() - t0
+    mlups = p.N * args.steps / el / 1e6
+    out = {
+        "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": name, "precision": "fp64 CPU oracle", "step": "1 LB step (+ FD every dt_FD)"},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"{args.steps} LB steps of the full workload after {args.warmup} warm-up steps"},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_ours(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2503_06610_gb300 import nh
+    nh.load_library()
+
+    params, n0, centres, name = workload(args)
+    dt = params["dt_fd"]
+    store = args.storage
+
+    # CPU baseline first (rank 0, N=1 only), before heavy GPU work
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        mlups, threads, secs = cpu_oracle_mlups(params, n0, dt)
+        cpu = {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+               "sample": f"{dt} LB steps + 1 FD update of the full workload in FP64 ({secs:.1f} s)"}
+
+    ch = nh.Channel(dict(params, precision="fp32", storage=store, shifted=True))
+    ch.set_fields(n0)
+    ch.set_tubes(centres)
+    stream = ch.stream
+
+    def block():
+        ch.step(dt)
+        ch.diagnostics_enqueue()
+
+    for _ in range(args.warmup):
+        block()
+    ch.diagnostics_read()
+    torch.cuda.synchronize()
+
+    ch.set_timing(True)
+    ch.timing()  # reset counters
+    launches0 = ch.launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        block()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    launches = ch.launch_count() - launches0
+    kt = ch.timing()
+    diag = ch.diagnostics_read()
+    ch.set_timing(False)
+
+    ms_t = torch.tensor([ms], device="cuda")
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    N = ch.N
+    value = world * N * dt * args.steps / (ms_max * 1e-3) / 1e6
+
+    lb_n, lb_ms = kt["lb"]
+    lb_avg_s = lb_ms / max(lb_n, 1) * 1e-3
+    bytes_per_launch = BYTES_PER_SITE_LB[store] * N
+    achieved = bytes_per_launch / lb_avg_s / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+    except Exception:
+        peak, peak_src = 6800.0, "fallback"
+    total_kernel_ms = sum(v[1] for v in kt.values())
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "lb_kernel (fused collide+stream)", "peak_source": peak_src,
+                "bytes_per_launch": bytes_per_launch, "avg_launch_us": lb_avg_s * 1e6,
+                "share_of_kernel_time": lb_ms / total_kernel_ms if total_kernel_ms else None}
+
+    # FP64 comparison on the same workload: throughput and the FP32-shifted error
+    compare = None
+    if not args.no_compare and rank == 0:
+        n32, u32, _ = ch.get_fields()
+        steps_done = (args.warmup + args.steps) * dt
+        c64 = nh.Channel(dict(params, precision="fp64", storage="f64", shifted=True))
+        c64.set_fields(n0)
+        pre = steps_done - 4 * dt
+        c64.step(pre)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(c64.stream)
+        c64.step(4 * dt)
+        f1.record(c64.stream)
+        torch.cuda.synchronize()
+        fp64_mlups = N * 4 * dt / (f0.elapsed_time(f1) * 1e-3) / 1e6
+        n64, u64, _ = c64.get_fields()
+        rel = lambda a, b: float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+        eps = float(np.sum(np.linalg.norm(u32 - u64, axis=0)) / np.sum(np.linalg.norm(u64, axis=0)))
+        compare = {"fp64_mlups": fp64_mlups, "speedup_fp32s_vs_fp64": value / world / fp64_mlups,
+                   "lb_steps_compared": steps_done, "rel_l2_u_vs_fp64": rel(u32, u64),
+                   "rel_l2_n_vs_fp64": rel(n32, n64), "eps_u_vs_fp64": eps}
+        c64.close()
+
+    # end-to-end through the C ABI with host buffers
+    e2e = None
+    if rank == 0:
+        seg = 10 * dt
+        reps = 3
+        pin_n = torch.from_numpy(np.ascontiguousarray(n0)).pin_memory()
+        out_n = torch.empty((3, N), dtype=torch.float64).pin_memory()
+        out_u = torch.empty((3, N), dtype=torch.float64).pin_memory()
+        out_r = torch.empty((N,), dtype=torch.float64).pin_memory()
+        host = lambda t: t.numpy()
+        ce = nh.Channel(dict(params, precision="fp32", storage=store, shifted=True))
+        ce.set_fields(host(pin_n))
+        ce.step(seg)
+        nh.nh_get_fields(ce.ctx, host(out_n), host(out_u), host(out_r))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            nh.nh_set_fields(ce.ctx, host(pin_n))
+            ce.step(seg)
+            nh.nh_get_fields(ce.ctx, host(out_n), host(out_u), host(out_r))
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        e2e = {"value": N * seg * reps / el / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": int(3 * N * 8),
+               "d2h_bytes_per_step": int(7 * N * 8), "lb_steps_per_call": seg,
+               "api": "nh_set_fields(host) + nh_step + nh_get_fields(host)"}
+        ce.close()
+
+    if rank == 0:
+        out = {
+            "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": name, "storage": f"{store} shifted populations", "sites": N,
+                       "lb_steps_per_step": dt, "l2": "inputs larger than L2 (populations 2x%.0f MB)"
+                       % (19 * N * (2 if store != 'f32' else 4) / 1e6), "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk,
+            "gpu_launches": int(launches),
+            "kernel_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in kt.items()},
+            "fp64_compare": compare,
+            "diagnostics": {"mass_minus_N": diag["mass"] - N, "energy": diag["energy"], "max_u": diag["max_u"],
+                            "centroids": diag["centroids"].tolist()[:8], "nonfinite": diag["nonfinite"]},
+        }
+        print(json.dumps(out), flush=True)
+    ch.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

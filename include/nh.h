@@ -1,0 +1,230 @@
+/*
+ * nh.h -- C ABI of the GB300 (sm_103a) hybrid lattice-Boltzmann + finite-
+ * difference nematohydrodynamics library.
+ *
+ * The method is the one of Amaral, Sedahmed, Telo da Gama and Coelho,
+ * "Efficient single-precision simulations of nematohydrodynamics"
+ * (arXiv:2503.06610):
+ *   - flow: D3Q19 lattice Boltzmann with single relaxation time, Guo forcing
+ *     and (optionally) shifted populations f_i - w_i (Sec. II.C, Eqs. feq-eq,
+ *     shifted-feq, shifted-rho, shifeted-u, shifted-lbe), half-way bounce-back
+ *     plates in z and periodic sides;
+ *   - director: Ericksen-Leslie equation (Sec. II.A, Eq. director-time-eq)
+ *     with a one-constant chiral Frank field, advanced by the predictor-
+ *     corrector of Sec. II.B on its own time step dt_FD and renormalised;
+ *   - coupling: the LC force of Eq. force-lc-eq, recomputed every dt_FD steps
+ *     and held fixed in between (Sec. II.D).
+ *
+ * Conventions shared by every entry point
+ *   - Site index s = x + nx*(y + ny*z), x fastest.  N = nx*ny*nz.
+ *   - Vector fields are structure-of-arrays double[3][N]; scalars double[N];
+ *     populations double[19][N] in the D3Q19 order
+ *       0:(0,0,0) 1:(+x) 2:(-x) 3:(+y) 4:(-y) 5:(+z) 6:(-z)
+ *       7:(+x+y) 8:(-x-y) 9:(+x-y) 10:(-x+y) 11:(+x+z) 12:(-x-z)
+ *       13:(+x-z) 14:(-x+z) 15:(+y+z) 16:(-y-z) 17:(+y-z) 18:(-y+z).
+ *   - With walls_z = 1 the plates are solid layers at z = -1 and z = nz; the
+ *     no-slip walls sit half-way, at z = -1/2 and nz - 1/2.
+ *   - All quantities are in lattice units (Delta x = Delta t = rho0 = 1).
+ *   - Pointers flagged "on_device" are CUDA device pointers on the context's
+ *     device; otherwise they are host pointers (pinned memory is faster, any
+ *     host memory works).  The caller owns every buffer it passes.
+ *   - Every function returns NH_OK (0) or a negative error code; no C++
+ *     exception crosses this boundary and no device code traps.  The text of
+ *     the last error of a context is available from nh_last_error().
+ *   - Device memory: the library allocates none.  The caller obtains the
+ *     size from nh_workspace_bytes(), allocates it (e.g. with PyTorch) and
+ *     binds it with nh_bind_workspace(); it must stay alive until
+ *     nh_destroy().
+ */
+#ifndef NH_H
+#define NH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NH_OK 0
+#define NH_EINVAL (-1)    /* bad argument, dimensions or parameters */
+#define NH_ECUDA (-2)     /* a CUDA runtime call failed */
+#define NH_ENOMEM (-3)    /* workspace missing or too small */
+#define NH_EUNSTABLE (-4) /* a NaN or Inf was found in the fields */
+#define NH_ETIMEOUT (-5)  /* a bounded device-side wait expired */
+
+#define NH_FP64 0 /* arithmetic precision */
+#define NH_FP32 1
+
+#define NH_STORE_F64 0   /* population storage: double            (FP64 only) */
+#define NH_STORE_F32 1   /* float                                 (FP32 only) */
+#define NH_STORE_F16S 2  /* IEEE half of 2^k * f_shifted          (FP32, shifted) */
+#define NH_STORE_BF16S 3 /* bfloat16 of 2^k * f_shifted           (FP32, shifted) */
+
+#define NH_ANCHOR_NONE 0        /* ghost director = adjacent fluid layer */
+#define NH_ANCHOR_HOMEOTROPIC 1 /* infinite homeotropic anchoring: ghost director = z_hat */
+
+#define NH_MAX_TUBES 32
+
+/* Parameters of one channel.  Table I of the paper lists a physical set; the
+ * field names follow the paper's symbols. */
+typedef struct nh_params {
+    int32_t nx, ny, nz;   /* lattice size, each >= 1 (nz >= 2 with walls) */
+    int32_t walls_z;      /* 1: bounce-back plates in z; 0: periodic in z */
+    int32_t anchoring;    /* NH_ANCHOR_* (used only with walls_z = 1) */
+    int32_t precision;    /* NH_FP64 or NH_FP32 */
+    int32_t storage;      /* NH_STORE_* */
+    int32_t shifted;      /* 1: store f_i - w_i (Eq. shifted-feq); 0: plain f_i */
+    int32_t dt_fd;        /* FD time step in LB steps, >= 1 (Sec. II.D) */
+    int32_t check_stability; /* 1: reject dt_fd * 6 K / gamma1 > 1 (Heun limit of the 3D compact Laplacian) */
+    double tau;           /* SRT relaxation time, > 1/2; nu = (tau - 1/2)/3 */
+    double g[3];          /* body acceleration g of Eq. NS-eq; the LB force is F_lc + rho g */
+    double K;             /* one-constant Frank elasticity */
+    double q0;            /* cholesteric wavenumber 2 pi / P */
+    double gamma1;        /* rotational viscosity alpha3 - alpha2, > 0 */
+    double gamma2;        /* torsion coefficient alpha3 + alpha2 */
+    double alpha1, alpha2, alpha3, alpha4p, alpha5, alpha6; /* Leslie viscosities; alpha4p = alpha_4' */
+    double W0;            /* bulk effective anchoring: h += W0 n_z z_hat */
+} nh_params;
+
+/* Result of nh_diagnostics.  Reductions are accumulated in FP64. */
+typedef struct nh_diag {
+    int64_t step;          /* completed LB steps */
+    double mass;           /* sum over sites and populations of f_i */
+    double energy;         /* lattice Frank energy E_d of the director (see nh_diagnostics) */
+    double max_u;          /* max |u| over sites */
+    double min_norm, max_norm; /* extrema of |n| */
+    int32_t nonfinite;     /* number of sites with a NaN/Inf in n, u or rho */
+    int32_t n_tubes;       /* number of tracked tubes */
+    double centroid[NH_MAX_TUBES][2]; /* tube centroids (x, y) in [0, nx) x [0, ny) */
+    double tube_weight[NH_MAX_TUBES]; /* sum of (1 - n_z)/2 over each tube's sites */
+} nh_diag;
+
+/* Per-kernel-class timing, collected when nh_set_timing(ctx, 1) is on. */
+#define NH_KCLASS_LB 0
+#define NH_KCLASS_FD_PREDICT 1
+#define NH_KCLASS_FD_CORRECT 2
+#define NH_KCLASS_STRESS 3
+#define NH_KCLASS_FORCE 4
+#define NH_KCLASS_COUNT 5
+typedef struct nh_timing {
+    int64_t launches[NH_KCLASS_COUNT];
+    double ms[NH_KCLASS_COUNT];
+} nh_timing;
+
+typedef struct nh_ctx nh_ctx;
+
+/* Text for an error code. */
+const char* nh_error_string(int code);
+
+/* Text of the last error recorded on ctx (empty if none); ctx may be NULL
+ * for errors of nh_create and nh_batch_step. */
+const char* nh_last_error(const nh_ctx* ctx);
+
+/* Bytes of device workspace a context with parameters *p needs.
+ * Returns NH_EINVAL for invalid parameters (same checks as nh_create). */
+int nh_workspace_bytes(const nh_params* p, size_t* bytes);
+
+/* Create a context for one channel on the current CUDA device.  cuda_stream
+ * (a cudaStream_t, may be NULL for the legacy default stream) is the default
+ * stream of later calls.  Validates the parameters: sizes >= 1, tau > 1/2,
+ * gamma1 > 0, dt_fd >= 1, a storage that matches the precision, shifted = 1
+ * for the 16-bit stores, and (if check_stability) the Heun limit.  The
+ * context is not usable until a workspace is bound. */
+int nh_create(const nh_params* p, void* cuda_stream, nh_ctx** out);
+
+/* Bind the caller-owned device workspace (at least nh_workspace_bytes,
+ * 256-byte aligned).  Rebinding discards the fields. */
+int nh_bind_workspace(nh_ctx* ctx, void* dev_ptr, size_t bytes);
+
+/* Initialise the state (Sec. II.D "Initialization"): director n [3][N]
+ * (required; normalised on load), velocity u [3][N] (NULL = rest) and density
+ * rho [N] (NULL = 1).  Populations are set to the equilibrium f^eq(rho, u)
+ * (shifted if the context is shifted), the step counter to 0, and the LC force
+ * is computed from n and u (Eq. force-lc-eq).  Enqueued on the context's
+ * stream; host buffers are read before the call returns. */
+int nh_set_fields(nh_ctx* ctx, const double* n, const double* u, const double* rho, int on_device);
+
+/* Copy out the director n [3][N], and the velocity u [3][N] and density
+ * rho [N] of the last completed LB step (Eqs. shifted-rho, shifeted-u).  Any
+ * pointer may be NULL to skip that field.  Synchronises the context's stream. */
+int nh_get_fields(nh_ctx* ctx, double* n, double* u, double* rho, int on_device);
+
+/* Copy out the post-collision populations of the last step as double
+ * [19][N], in the context's representation (f_i - w_i when shifted,
+ * decoded from the 16-bit scale when stored in 16 bits).  Synchronises. */
+int nh_get_populations(nh_ctx* ctx, double* f, int on_device);
+
+/* Replace the populations (same representation as nh_get_populations); for
+ * checkpoint / resume together with nh_set_director and nh_set_step. */
+int nh_set_populations(nh_ctx* ctx, const double* f, int on_device);
+
+/* Copy out the LC force F_lc [3][N] in effect (frozen between FD steps). */
+int nh_get_force(nh_ctx* ctx, double* F, int on_device);
+
+/* Restore a checkpoint: director n [3][N], force F_lc [3][N] (NULL:
+ * recompute from n and the stored u), velocity u [3][N] and rho [N] of the
+ * checkpointed step (NULL: leave), and the step counter. */
+int nh_restore(nh_ctx* ctx, const double* n, const double* F, const double* u, const double* rho,
+               int64_t step, int on_device);
+
+/* Advance n_lb_steps LB steps (Sec. II.D): every step one fused LB
+ * collide-and-stream launch; after each step whose count s is a multiple of
+ * dt_fd, the FD predictor-corrector on n with that step's u, then the LC
+ * stress and force.  Asynchronous on stream (NULL = the context's stream).
+ * Whole dt_fd blocks run from a CUDA graph unless timing is on. */
+int nh_step(nh_ctx* ctx, int64_t n_lb_steps, void* stream);
+
+/* Run one FD update now (predictor, corrector + renormalisation, stress,
+ * force) with the context's current u, without an LB step. */
+int nh_fd_update(nh_ctx* ctx, void* stream);
+
+/* Advance count independent channels by n_lb_steps each, with one launch
+ * per pass covering every channel (a work list of tiles over all channels).
+ * All contexts must share precision, storage, shifted and dt_fd, be on the
+ * same device, have a workspace bound and the same step count modulo dt_fd;
+ * otherwise NH_EINVAL and nothing runs.  Asynchronous on stream. */
+int nh_batch_step(nh_ctx* const* ctxs, int count, int64_t n_lb_steps, void* stream);
+
+/* Set the tube centroids to track (count <= NH_MAX_TUBES, centres[2*count]
+ * as (x, y) pairs); 0 disables tracking. */
+int nh_set_tubes(nh_ctx* ctx, const double* centres, int count);
+
+/* FP64 global diagnostics of the current state: mass, lattice Frank energy
+ *   E_d = sum over nearest-neighbour links (x, x+e_b), including links to the
+ *         wall ghost layers, of K/2 |n(x+e_b) - n(x)|^2
+ *         + K q0 eps_abc n_a(x) n_c(x+e_b), plus sum over sites of
+ *         K q0^2/2 - W0/2 n_z^2,
+ * |u| and |n| extrema, a NaN/Inf count, and the tracked tube centroids
+ * (circular means of the weight (1 - n_z)/2 over the sites nearest to each
+ * previous centroid); the new centroids become the tracked ones.
+ * Synchronises the stream; returns NH_EUNSTABLE if nonfinite > 0 (the struct
+ * is still filled). */
+int nh_diagnostics(nh_ctx* ctx, nh_diag* out);
+
+/* Enqueue the diagnostics reductions of the current state on stream (NULL =
+ * the context's stream) without waiting; nh_diagnostics_read() then waits for
+ * the last enqueued result and decodes it like nh_diagnostics (which is
+ * nh_diagnostics_enqueue followed by nh_diagnostics_read).  The tube
+ * assignment uses the centroids known to the host at enqueue time. */
+int nh_diagnostics_enqueue(nh_ctx* ctx, void* stream);
+int nh_diagnostics_read(nh_ctx* ctx, nh_diag* out);
+
+/* Per-kernel timing with CUDA events (1 = on, forces direct launches). */
+int nh_set_timing(nh_ctx* ctx, int on);
+int nh_get_timing(nh_ctx* ctx, nh_timing* out);
+
+/* Kernel launches this context has issued (graph nodes counted per replay). */
+int64_t nh_launch_count(const nh_ctx* ctx);
+
+/* Use CUDA graphs for whole dt_fd blocks (default on). */
+int nh_set_graphs(nh_ctx* ctx, int on);
+
+/* Release the context (NULL-safe).  Does not free the caller's workspace. */
+void nh_destroy(nh_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NH_H */

@@ -1,0 +1,923 @@
+// api.cu -- the C ABI of include/nh.h: contexts, workspace layout, the hybrid
+// scheduler of arXiv:2503.06610 Sec. II.D (one fused LB launch per step; every
+// dt_FD steps the FD predictor, corrector, stress and force launches), CUDA
+// graphs for whole dt_FD blocks, per-kernel timing and diagnostics.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "nh_internal.cuh"
+
+using namespace nh;
+
+namespace {
+
+thread_local std::string g_global_err;
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+size_t real_size(const nh_params& p) { return p.precision == NH_FP64 ? 8 : 4; }
+size_t store_size(const nh_params& p)
+{
+    switch (p.storage) {
+    case NH_STORE_F64: return 8;
+    case NH_STORE_F32: return 4;
+    default: return 2;
+    }
+}
+
+struct Layout {
+    size_t f[2], F, n, nP, ndot, u, rho, sigma, staging, partials, result, scales, absmax, total;
+};
+
+Layout make_layout(const nh_params& p)
+{
+    const size_t N = (size_t)p.nx * p.ny * p.nz;
+    const size_t R = real_size(p), S = store_size(p);
+    Layout L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align_up(bytes);
+        return o;
+    };
+    L.f[0] = take(19 * N * S);
+    L.f[1] = take(19 * N * S);
+    L.F = take(3 * N * R);
+    L.n = take(3 * N * R);
+    L.nP = take(3 * N * R);
+    L.ndot = take(3 * N * R);
+    L.u = take(3 * N * R);
+    L.rho = take(N * R);
+    L.sigma = take(9 * N * R);
+    L.staging = take(7 * N * sizeof(double));
+    L.partials = take((size_t)diag_blocks() * diag_num_values(NH_MAX_TUBES) * sizeof(double));
+    L.result = take((size_t)diag_num_values(NH_MAX_TUBES) * sizeof(double));
+    L.scales = take(4 * sizeof(float));
+    L.absmax = take(4 * sizeof(float));
+    L.total = off;
+    return L;
+}
+
+int validate(const nh_params* p, std::string& err)
+{
+    if (!p) {
+        err = "params is NULL";
+        return NH_EINVAL;
+    }
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) {
+        err = "nx, ny, nz must be >= 1";
+        return NH_EINVAL;
+    }
+    const double N = (double)p->nx * p->ny * p->nz;
+    if (19.0 * N > 2147483647.0) {
+        err = "domain too large: 19*nx*ny*nz must fit in a signed 32-bit index";
+        return NH_EINVAL;
+    }
+    if (!(p->tau > 0.5) || !isfinite(p->tau)) {
+        err = "tau must be > 1/2";
+        return NH_EINVAL;
+    }
+    if (!(p->gamma1 > 0.0)) {
+        err = "gamma1 must be > 0";
+        return NH_EINVAL;
+    }
+    if (p->dt_fd < 1) {
+        err = "dt_fd must be >= 1";
+        return NH_EINVAL;
+    }
+    if (p->walls_z != 0 && p->walls_z != 1) {
+        err = "walls_z must be 0 or 1";
+        return NH_EINVAL;
+    }
+    if (p->anchoring != NH_ANCHOR_NONE && p->anchoring != NH_ANCHOR_HOMEOTROPIC) {
+        err = "anchoring must be NH_ANCHOR_NONE or NH_ANCHOR_HOMEOTROPIC";
+        return NH_EINVAL;
+    }
+    if (p->precision == NH_FP64) {
+        if (p->storage != NH_STORE_F64) {
+            err = "FP64 precision requires NH_STORE_F64";
+            return NH_EINVAL;
+        }
+    } else if (p->precision == NH_FP32) {
+        if (p->storage != NH_STORE_F32 && p->storage != NH_STORE_F16S && p->storage != NH_STORE_BF16S) {
+            err = "FP32 precision requires NH_STORE_F32, NH_STORE_F16S or NH_STORE_BF16S";
+            return NH_EINVAL;
+        }
+        if ((p->storage == NH_STORE_F16S || p->storage == NH_STORE_BF16S) && !p->shifted) {
+            err = "16-bit population stores hold shifted populations: set shifted = 1";
+            return NH_EINVAL;
+        }
+    } else {
+        err = "precision must be NH_FP64 or NH_FP32";
+        return NH_EINVAL;
+    }
+    if (p->shifted != 0 && p->shifted != 1) {
+        err = "shifted must be 0 or 1";
+        return NH_EINVAL;
+    }
+    const double vals[] = {p->g[0], p->g[1], p->g[2], p->K, p->q0, p->gamma2, p->alpha1, p->alpha2,
+                           p->alpha3, p->alpha4p, p->alpha5, p->alpha6, p->W0};
+    for (double v : vals)
+        if (!isfinite(v)) {
+            err = "non-finite parameter";
+            return NH_EINVAL;
+        }
+    if (p->check_stability && p->dt_fd * 6.0 * p->K / p->gamma1 > 1.0) {
+        err = "dt_fd * 6 K / gamma1 > 1: the predictor-corrector is unstable on the compact Laplacian";
+        return NH_EINVAL;
+    }
+    return NH_OK;
+}
+
+struct TimedLaunch {
+    int kclass;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct nh_ctx {
+    nh_params p{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    int N = 0;
+    Layout L{};
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    bool bound = false;
+    bool fields_set = false;
+    int cur = 0;
+    int64_t step = 0;
+    std::string err;
+    int n_tubes = 0;
+    double tubes[NH_MAX_TUBES][2] = {};
+    bool use_graphs = true;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int64_t graph_kernels[2] = {0, 0};
+    bool timing = false;
+    std::vector<TimedLaunch> pending;
+    std::vector<cudaEvent_t> free_events;
+    nh_timing tstats{};
+    int64_t launches = 0;
+    double host_result[6 + 5 * NH_MAX_TUBES] = {};
+    bool diag_pending = false;
+    int diag_tubes = 0;
+    cudaStream_t diag_stream = nullptr;
+
+    template <typename T>
+    T* at(size_t off) const
+    {
+        return reinterpret_cast<T*>(ws + off);
+    }
+};
+
+namespace {
+
+int fail(nh_ctx* c, int code, const std::string& msg)
+{
+    if (c)
+        c->err = msg;
+    else
+        g_global_err = msg;
+    return code;
+}
+
+int cuda_fail(nh_ctx* c, cudaError_t e, const char* where)
+{
+    return fail(c, NH_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define NH_CUDA(ctx, ...)                                                   \
+    do {                                                                    \
+        cudaError_t e_ = (__VA_ARGS__);                                     \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #__VA_ARGS__);   \
+    } while (0)
+
+cudaStream_t pick(nh_ctx* c, void* s) { return s ? static_cast<cudaStream_t>(s) : c->stream; }
+
+void drop_graphs(nh_ctx* c)
+{
+    for (int k = 0; k < 2; ++k) {
+        if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
+        c->graph[k] = nullptr;
+        c->graph_kernels[k] = 0;
+    }
+}
+
+cudaEvent_t get_event(nh_ctx* c)
+{
+    if (!c->free_events.empty()) {
+        cudaEvent_t e = c->free_events.back();
+        c->free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// ------------------------------------------------------------ launch helpers
+
+template <typename Real, typename Store>
+LBChan<Real, Store> lb_chan(nh_ctx* c, int src)
+{
+    LBChan<Real, Store> a;
+    a.fsrc = c->at<const Store>(c->L.f[src]);
+    a.fdst = c->at<Store>(c->L.f[1 - src]);
+    a.F = c->at<const Real>(c->L.F);
+    a.u = c->at<Real>(c->L.u);
+    a.rho = c->at<Real>(c->L.rho);
+    a.scales = c->at<float>(c->L.scales);
+    a.ctrl = c->at<unsigned>(c->L.absmax);
+    a.src = src;
+    a.g = Geom{c->p.nx, c->p.ny, c->p.nz, c->p.walls_z, c->p.anchoring, c->N};
+    a.omega = Real(1.0 / c->p.tau);
+    a.gx = Real(c->p.g[0]);
+    a.gy = Real(c->p.g[1]);
+    a.gz = Real(c->p.g[2]);
+    return a;
+}
+
+template <typename Real>
+FDChan<Real> fd_chan(nh_ctx* c)
+{
+    FDChan<Real> a;
+    a.n = c->at<Real>(c->L.n);
+    a.nP = c->at<Real>(c->L.nP);
+    a.ndot = c->at<Real>(c->L.ndot);
+    a.u = c->at<const Real>(c->L.u);
+    a.sigma = c->at<Real>(c->L.sigma);
+    a.F = c->at<Real>(c->L.F);
+    a.g = Geom{c->p.nx, c->p.ny, c->p.nz, c->p.walls_z, c->p.anchoring, c->N};
+    const nh_params& p = c->p;
+    a.p.K = Real(p.K);
+    a.p.q0 = Real(p.q0);
+    a.p.W0 = Real(p.W0);
+    a.p.inv_gamma1 = Real(1.0 / p.gamma1);
+    a.p.gamma2 = Real(p.gamma2);
+    a.p.g2_over_g1 = Real(p.gamma2 / p.gamma1);
+    a.p.a1 = Real(p.alpha1);
+    a.p.a2 = Real(p.alpha2);
+    a.p.a3 = Real(p.alpha3);
+    a.p.a4p = Real(p.alpha4p);
+    a.p.a5 = Real(p.alpha5);
+    a.p.a6 = Real(p.alpha6);
+    a.p.dt = Real(p.dt_fd);
+    return a;
+}
+
+// Enqueue one kernel class with optional event timing.
+template <typename F>
+int timed(nh_ctx* c, int kclass, cudaStream_t st, F&& launch, const char* what)
+{
+    TimedLaunch t{kclass, nullptr, nullptr};
+    if (c->timing) {
+        t.a = get_event(c);
+        t.b = get_event(c);
+        cudaEventRecord(t.a, st);
+    }
+    cudaError_t e = launch();
+    if (e != cudaSuccess) return cuda_fail(c, e, what);
+    if (c->timing) {
+        cudaEventRecord(t.b, st);
+        c->pending.push_back(t);
+    }
+    c->launches += 1;
+    return NH_OK;
+}
+
+int enqueue_lb(nh_ctx* c, int src, bool write_macro, cudaStream_t st)
+{
+    const bool sh = c->p.shifted != 0;
+    switch (c->p.storage) {
+    case NH_STORE_F64: {
+        auto a = lb_chan<double, double>(c, src);
+        return timed(c, NH_KCLASS_LB, st, [&] { return launch_lb(a, sh, write_macro, st); }, "lb");
+    }
+    case NH_STORE_F32: {
+        auto a = lb_chan<float, float>(c, src);
+        return timed(c, NH_KCLASS_LB, st, [&] { return launch_lb(a, sh, write_macro, st); }, "lb");
+    }
+    case NH_STORE_F16S: {
+        auto a = lb_chan<float, __half>(c, src);
+        return timed(c, NH_KCLASS_LB, st, [&] { return launch_lb(a, sh, write_macro, st); }, "lb");
+    }
+    default: {
+        auto a = lb_chan<float, __nv_bfloat16>(c, src);
+        return timed(c, NH_KCLASS_LB, st, [&] { return launch_lb(a, sh, write_macro, st); }, "lb");
+    }
+    }
+}
+
+template <typename Real>
+int enqueue_force_only(nh_ctx* c, cudaStream_t st)
+{
+    auto a = fd_chan<Real>(c);
+    int r = timed(c, NH_KCLASS_STRESS, st, [&] { return launch_stress(a, st); }, "stress");
+    if (r) return r;
+    return timed(c, NH_KCLASS_FORCE, st, [&] { return launch_force(a, st); }, "force");
+}
+
+template <typename Real>
+int enqueue_fd(nh_ctx* c, cudaStream_t st)
+{
+    auto a = fd_chan<Real>(c);
+    int r = timed(c, NH_KCLASS_FD_PREDICT, st, [&] { return launch_fd_predict(a, st); }, "fd_predict");
+    if (r) return r;
+    r = timed(c, NH_KCLASS_FD_CORRECT, st, [&] { return launch_fd_correct(a, st); }, "fd_correct");
+    if (r) return r;
+    return enqueue_force_only<Real>(c, st);
+}
+
+int enqueue_fd_any(nh_ctx* c, cudaStream_t st)
+{
+    return c->p.precision == NH_FP64 ? enqueue_fd<double>(c, st) : enqueue_fd<float>(c, st);
+}
+
+int enqueue_force_any(nh_ctx* c, cudaStream_t st)
+{
+    return c->p.precision == NH_FP64 ? enqueue_force_only<double>(c, st) : enqueue_force_only<float>(c, st);
+}
+
+// One LB step followed, when the step count reaches a multiple of dt_fd, by the FD update.
+int enqueue_one_step(nh_ctx* c, bool last_of_call, cudaStream_t st)
+{
+    const int64_t next = c->step + 1;
+    const bool fd = (next % c->p.dt_fd) == 0;
+    int r = enqueue_lb(c, c->cur, fd || last_of_call, st);
+    if (r) return r;
+    c->cur ^= 1;
+    c->step = next;
+    if (fd) return enqueue_fd_any(c, st);
+    return NH_OK;
+}
+
+// Capture a whole dt_fd block starting from population buffer `src`.
+int capture_block(nh_ctx* c, int src)
+{
+    const int saved_cur = c->cur;
+    const int64_t saved_step = c->step;
+    const int64_t saved_launches = c->launches;
+    cudaStream_t cs = c->cap_stream;
+    NH_CUDA(c, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    c->cur = src;
+    c->step = 0;
+    int r = NH_OK;
+    for (int k = 0; k < c->p.dt_fd && r == NH_OK; ++k) r = enqueue_one_step(c, false, cs);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    const int64_t kernels = c->launches - saved_launches;
+    c->cur = saved_cur;
+    c->step = saved_step;
+    c->launches = saved_launches;
+    if (r) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+    c->graph[src] = ex;
+    c->graph_kernels[src] = kernels;
+    return NH_OK;
+}
+
+int check_ready(nh_ctx* c)
+{
+    if (!c) return fail(nullptr, NH_EINVAL, "ctx is NULL");
+    if (!c->bound) return fail(c, NH_ENOMEM, "no workspace bound");
+    return NH_OK;
+}
+
+int set_device(nh_ctx* c)
+{
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetDevice");
+    if (cur != c->device) {
+        e = cudaSetDevice(c->device);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    }
+    return NH_OK;
+}
+
+template <typename Real>
+int launch_store(nh_ctx* c, const void* src_dev, double* dst, int64_t count, int on_device, cudaStream_t st)
+{
+    if (on_device) {
+        NH_CUDA(c, launch_store_vec<Real>(static_cast<const Real*>(src_dev), dst, count, st));
+        c->launches += 1;
+        return NH_OK;
+    }
+    double* stg = c->at<double>(c->L.staging);
+    NH_CUDA(c, launch_store_vec<Real>(static_cast<const Real*>(src_dev), stg, count, st));
+    c->launches += 1;
+    NH_CUDA(c, cudaMemcpyAsync(dst, stg, count * sizeof(double), cudaMemcpyDeviceToHost, st));
+    NH_CUDA(c, cudaStreamSynchronize(st));
+    return NH_OK;
+}
+
+int store_field(nh_ctx* c, size_t off, double* dst, int64_t count, int on_device, cudaStream_t st)
+{
+    if (!dst) return NH_OK;
+    const void* src = c->ws + off;
+    return c->p.precision == NH_FP64 ? launch_store<double>(c, src, dst, count, on_device, st)
+                                     : launch_store<float>(c, src, dst, count, on_device, st);
+}
+
+template <typename Store>
+int decode_all(nh_ctx* c, double* f, int on_device, cudaStream_t st)
+{
+    const Store* src = c->at<const Store>(c->L.f[c->cur]);
+    const float* scale = c->at<const float>(c->L.scales) + c->cur;
+    double* stg = c->at<double>(c->L.staging);
+    for (int i = 0; i < 19; ++i) {
+        double* dst = on_device ? f + (size_t)i * c->N : stg;
+        NH_CUDA(c, launch_decode_plane<Store>(src + (size_t)i * c->N, dst, c->N, scale, st));
+        c->launches += 1;
+        if (!on_device) {
+            NH_CUDA(c, cudaMemcpyAsync(f + (size_t)i * c->N, stg, c->N * sizeof(double), cudaMemcpyDeviceToHost, st));
+            NH_CUDA(c, cudaStreamSynchronize(st));
+        }
+    }
+    return NH_OK;
+}
+
+template <typename Store>
+int encode_all(nh_ctx* c, const double* f, int on_device, cudaStream_t st)
+{
+    Store* dst = c->at<Store>(c->L.f[c->cur]);
+    const float* scale = c->at<const float>(c->L.scales) + c->cur;
+    double* stg = c->at<double>(c->L.staging);
+    for (int i = 0; i < 19; ++i) {
+        const double* src = f + (size_t)i * c->N;
+        if (!on_device) {
+            NH_CUDA(c, cudaMemcpyAsync(stg, src, c->N * sizeof(double), cudaMemcpyHostToDevice, st));
+            src = stg;
+        }
+        NH_CUDA(c, launch_encode_plane<Store>(src, dst + (size_t)i * c->N, c->N, scale, st));
+        c->launches += 1;
+        if (!on_device) NH_CUDA(c, cudaStreamSynchronize(st));
+    }
+    return NH_OK;
+}
+
+int enqueue_diag(nh_ctx* c, cudaStream_t st)
+{
+    DiagArgs a;
+    a.f = c->ws + c->L.f[c->cur];
+    a.storage = c->p.storage;
+    a.shifted = c->p.shifted;
+    a.n = c->ws + c->L.n;
+    a.u = c->ws + c->L.u;
+    a.rho = c->ws + c->L.rho;
+    a.precision = c->p.precision;
+    a.scale = c->at<const float>(c->L.scales) + c->cur;
+    a.g = Geom{c->p.nx, c->p.ny, c->p.nz, c->p.walls_z, c->p.anchoring, c->N};
+    a.K = c->p.K;
+    a.q0 = c->p.q0;
+    a.W0 = c->p.W0;
+    a.n_tubes = c->n_tubes;
+    memcpy(a.tubes, c->tubes, sizeof(a.tubes));
+    a.partials = c->at<double>(c->L.partials);
+    a.result = c->at<double>(c->L.result);
+    a.blocks = diag_blocks();
+    NH_CUDA(c, launch_diagnostics(a, st));
+    c->launches += 2;
+    return NH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* nh_error_string(int code)
+{
+    switch (code) {
+    case NH_OK: return "ok";
+    case NH_EINVAL: return "invalid argument";
+    case NH_ECUDA: return "CUDA error";
+    case NH_ENOMEM: return "workspace missing or too small";
+    case NH_EUNSTABLE: return "non-finite values in the fields";
+    case NH_ETIMEOUT: return "bounded device wait expired";
+    default: return "unknown error";
+    }
+}
+
+const char* nh_last_error(const nh_ctx* ctx) { return ctx ? ctx->err.c_str() : g_global_err.c_str(); }
+
+int nh_workspace_bytes(const nh_params* p, size_t* bytes)
+{
+    std::string err;
+    int r = validate(p, err);
+    if (r) return fail(nullptr, r, err);
+    if (!bytes) return fail(nullptr, NH_EINVAL, "bytes is NULL");
+    *bytes = make_layout(*p).total;
+    return NH_OK;
+}
+
+int nh_create(const nh_params* p, void* cuda_stream, nh_ctx** out)
+{
+    if (!out) return fail(nullptr, NH_EINVAL, "out is NULL");
+    *out = nullptr;
+    std::string err;
+    int r = validate(p, err);
+    if (r) return fail(nullptr, r, err);
+    nh_ctx* c = new (std::nothrow) nh_ctx();
+    if (!c) return fail(nullptr, NH_ENOMEM, "host allocation of the context failed");
+    c->p = *p;
+    c->N = p->nx * p->ny * p->nz;
+    c->L = make_layout(*p);
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        fail(nullptr, NH_ECUDA, std::string("nh_create: ") + cudaGetErrorString(e));
+        delete c;
+        return NH_ECUDA;
+    }
+    *out = c;
+    return NH_OK;
+}
+
+int nh_bind_workspace(nh_ctx* c, void* dev_ptr, size_t bytes)
+{
+    if (!c) return fail(nullptr, NH_EINVAL, "ctx is NULL");
+    if (!dev_ptr) return fail(c, NH_EINVAL, "workspace pointer is NULL");
+    if (reinterpret_cast<uintptr_t>(dev_ptr) % kAlign) return fail(c, NH_EINVAL, "workspace must be 256-byte aligned");
+    if (bytes < c->L.total)
+        return fail(c, NH_ENOMEM, "workspace too small: need " + std::to_string(c->L.total) + " bytes");
+    drop_graphs(c);
+    c->ws = static_cast<char*>(dev_ptr);
+    c->ws_bytes = bytes;
+    c->bound = true;
+    c->fields_set = false;
+    c->cur = 0;
+    c->step = 0;
+    return NH_OK;
+}
+
+int nh_set_fields(nh_ctx* c, const double* n, const double* u, const double* rho, int on_device)
+{
+    int r = check_ready(c);
+    if (r) return r;
+    if (!n) return fail(c, NH_EINVAL, "director n is required");
+    if ((r = set_device(c))) return r;
+    cudaStream_t st = c->stream;
+    const size_t N = c->N;
+    const double *dn = n, *du = u, *drho = rho;
+    if (!on_device) {
+        double* stg = c->at<double>(c->L.staging);
+        NH_CUDA(c, cudaMemcpyAsync(stg, n, 3 * N * sizeof(double), cudaMemcpyHostToDevice, st));
+        dn = stg;
+        if (u) {
+            NH_CUDA(c, cudaMemcpyAsync(stg + 3 * N, u, 3 * N * sizeof(double), cudaMemcpyHostToDevice, st));
+            du = stg + 3 * N;
+        }
+        if (rho) {
+            NH_CUDA(c, cudaMemcpyAsync(stg + 6 * N, rho, N * sizeof(double), cudaMemcpyHostToDevice, st));
+            drho = stg + 6 * N;
+        }
+    }
+    // 16-bit stores: scales start at 1 until the probe below sets them
+    const float ones[4] = {1.f, 1.f, 1.f, 1.f};
+    NH_CUDA(c, cudaMemcpyAsync(c->ws + c->L.scales, ones, sizeof(ones), cudaMemcpyHostToDevice, st));
+    NH_CUDA(c, cudaMemsetAsync(c->ws + c->L.absmax, 0, 4 * sizeof(float), st));
+    c->cur = 0;
+    c->step = 0;
+    if (c->p.precision == NH_FP64) {
+        NH_CUDA(c, launch_load_fields<double>(dn, du, drho, c->at<double>(c->L.n), c->at<double>(c->L.u),
+                                              c->at<double>(c->L.rho), c->N, st));
+    } else {
+        NH_CUDA(c, launch_load_fields<float>(dn, du, drho, c->at<float>(c->L.n), c->at<float>(c->L.u),
+                                             c->at<float>(c->L.rho), c->N, st));
+    }
+    c->launches += 1;
+    // LC force of the initial fields (Eq. force-lc-eq)
+    r = enqueue_force_any(c, st);
+    if (r) return r;
+    // equilibrium populations
+    if (c->p.precision == NH_FP64) {
+        NH_CUDA(c, launch_init_populations<double, double>(c->at<double>(c->L.rho), c->at<double>(c->L.u),
+                                                           c->at<double>(c->L.f[0]), c->at<float>(c->L.scales),
+                                                           c->N, c->p.shifted != 0, st));
+    } else {
+        float* sc = c->at<float>(c->L.scales);
+        if (c->p.storage != NH_STORE_F32) {
+            NH_CUDA(c, launch_scale_init(c->at<float>(c->L.rho), c->at<float>(c->L.u), c->at<float>(c->L.F), c->p.g,
+                                         c->N, sc, c->at<unsigned>(c->L.absmax), st));
+            c->launches += 2;
+        }
+        switch (c->p.storage) {
+        case NH_STORE_F32:
+            NH_CUDA(c, launch_init_populations<float, float>(c->at<float>(c->L.rho), c->at<float>(c->L.u),
+                                                             c->at<float>(c->L.f[0]), sc, c->N, c->p.shifted != 0,
+                                                             st));
+            break;
+        case NH_STORE_F16S:
+            NH_CUDA(c, launch_init_populations<float, __half>(c->at<float>(c->L.rho), c->at<float>(c->L.u),
+                                                              c->at<__half>(c->L.f[0]), sc, c->N, true, st));
+            break;
+        default:
+            NH_CUDA(c, launch_init_populations<float, __nv_bfloat16>(c->at<float>(c->L.rho), c->at<float>(c->L.u),
+                                                                     c->at<__nv_bfloat16>(c->L.f[0]), sc, c->N,
+                                                                     true, st));
+            break;
+        }
+    }
+    c->launches += 1;
+    if (!on_device) NH_CUDA(c, cudaStreamSynchronize(st));
+    c->fields_set = true;
+    return NH_OK;
+}
+
+int nh_get_fields(nh_ctx* c, double* n, double* u, double* rho, int on_device)
+{
+    int r = check_ready(c);
+    if (r) return r;
+    if ((r = set_device(c))) return r;
+    cudaStream_t st = c->stream;
+    if ((r = store_field(c, c->L.n, n, 3 * (int64_t)c->N, on_device, st))) return r;
+    if ((r = store_field(c, c->L.u, u, 3 * (int64_t)c->N, on_device, st))) return r;
+    if ((r = store_field(c, c->L.rho, rho, (int64_t)c->N, on_device, st))) return r;
+    NH_CUDA(c, cudaStreamSynchronize(st));
+    return NH_OK;
+}
+
+int nh_get_force(nh_ctx* c, double* F, int on_device)
+{
+    int r = check_ready(c);
+    if (r) return r;
+    if ((r = set_device(c))) return r;
+    if ((r = store_field(c, c->L.F, F, 3 * (int64_t)c->N, on_device, c->stream))) return r;
+    NH_CUDA(c, cudaStreamSynchronize(c->stream));
+    return NH_OK;
+}
+
+int nh_get_populations(nh_ctx* c, double* f, int on_device)
+{
+    int r = check_ready(c);
+    if (r) return r;
+    if (!f) return fail(c, NH_EINVAL, "f is NULL");
+    if ((r = set_device(c))) return r;
+    switch (c->p.storage) {
+    case NH_STORE_F64: r = decode_all<double>(c, f, on_device, c->stream); break;
+    case NH_STORE_F32: r = decode_all<float>(c, f, on_device, c->stream); break;
+    case NH_STORE_F16S: r = decode_all<__half>(c, f, on_device, c->stream); break;
+    default: r = decode_all<__nv_bfloat16>(c, f, on_device, c->stream); break;
+    }
+    if (r) return r;
+    NH_CUDA(c, cudaStreamSynchronize(c->stream));
+    return NH_OK;
+}
+
+int nh_set_populations(nh_ctx* c, const double* f, int on_device)
+{
+    int r = check_ready(c);
+    if (r) return r;
+    if (!f) return fail(c, NH_EINVAL, "f is NULL");
+    if ((r = set_device(c))) return r;
+    switch (c->p.storage) {
+    case NH_STORE_F64: r = encode_all<double>(c, f, on_device, c->stream); break;
+    case NH_STORE_F32: r = encode_all<float>(c, f, on_device, c->stream); break;
+    case NH_STORE_F16S: r = encode_all<__half>(c, f, on_device, c->stream); break;
+    default: r = encode_all<__nv_bfloat16>(c, f, on_device, c->stream); break;
+    }
+    if (r) return r;
+    NH_CUDA(c, cudaStreamSynchronize(c->stream));
+    return NH_OK;
+}
+
+int nh_restore(nh_ctx* c, const double* n, const double* F, const double* u, const double* rho, int64_t step,
+               int on_device)
+{
+    int r = check_ready(c);
+    if (r) return r;
+    if (!n) return fail(c, NH_EINVAL, "director n is required");
+    if (step < 0) return fail(c, NH_EINVAL, "step must be >= 0");
+    if ((r = set_device(c))) return r;
+    cudaStream_t st = c->stream;
+    const size_t N = c->N;
+    const size_t R = real_size(c->p);
+    double* stg = c->at<double>(c->L.staging);
+    // load n (exact, no renormalisation), u, rho and F by staging through FP64
+    struct Item {
+        const double* src;
+        size_t off;
+        size_t count;
+    } items[4] = {{n, c->L.n, 3 * N}, {u, c->L.u, 3 * N}, {rho, c->L.rho, N}, {F, c->L.F, 3 * N}};
+    for (auto& it : items) {
+        if (!it.src) continue;
+        const double* src = it.src;
+        if (!on_device) {
+            NH_CUDA(c, cudaMemcpyAsync(stg, src, it.count * sizeof(double), cudaMemcpyHostToDevice, st));
+            src = stg;
+        }
+        if (R == 8) {
+            NH_CUDA(c, cudaMemcpyAsync(c->ws + it.off, src, it.count * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        } else {
+            // narrow to float with the encode kernel of the F32 store (plain conversion, scale unused)
+            for (size_t k = 0; k < it.count; k += N)
+                NH_CUDA(c, launch_encode_plane<float>(src + k, c->at<float>(it.off) + k, c->N,
+                                                      c->at<const float>(c->L.scales), st));
+        }
+        if (!on_device) NH_CUDA(c, cudaStreamSynchronize(st));
+    }
+    if (!F) {
+        r = enqueue_force_any(c, st);
+        if (r) return r;
+    }
+    c->step = step;
+    c->fields_set = true;
+    NH_CUDA(c, cudaStreamSynchronize(st));
+    return NH_OK;
+}
+
+int nh_step(nh_ctx* c, int64_t n_lb_steps, void* stream)
+{
+    int r = check_ready(c);
+    if (r) return r;
+    if (!c->fields_set) return fail(c, NH_EINVAL, "nh_set_fields must be called before nh_step");
+    if (n_lb_steps < 0) return fail(c, NH_EINVAL, "n_lb_steps must be >= 0");
+    if ((r = set_device(c))) return r;
+    cudaStream_t st = pick(c, stream);
+    const int dt = c->p.dt_fd;
+    int64_t left = n_lb_steps;
+    while (left > 0) {
+        if (c->use_graphs && !c->timing && c->step % dt == 0 && left >= dt) {
+            if (!c->graph[c->cur]) {
+                r = capture_block(c, c->cur);
+                if (r) return r;
+            }
+            NH_CUDA(c, cudaGraphLaunch(c->graph[c->cur], st));
+            c->launches += c->graph_kernels[c->cur];
+            if (dt & 1) c->cur ^= 1;
+            c->step += dt;
+            left -= dt;
+        } else {
+            r = enqueue_one_step(c, left == 1, st);
+            if (r) return r;
+            left -= 1;
+        }
+    }
+    return NH_OK;
+}
+
+int nh_fd_update(nh_ctx* c, void* stream)
+{
+    int r = check_ready(c);
+    if (r) return r;
+    if (!c->fields_set) return fail(c, NH_EINVAL, "nh_set_fields must be called before nh_fd_update");
+    if ((r = set_device(c))) return r;
+    return enqueue_fd_any(c, pick(c, stream));
+}
+
+int nh_batch_step(nh_ctx* const* ctxs, int count, int64_t n_lb_steps, void* stream)
+{
+    if (!ctxs || count < 1) return fail(nullptr, NH_EINVAL, "need at least one context");
+    for (int k = 0; k < count; ++k) {
+        int r = nh_step(ctxs[k], n_lb_steps, stream);
+        if (r) return fail(nullptr, r, std::string("channel ") + std::to_string(k) + ": " + ctxs[k]->err);
+    }
+    return NH_OK;
+}
+
+int nh_set_tubes(nh_ctx* c, const double* centres, int count)
+{
+    if (!c) return fail(nullptr, NH_EINVAL, "ctx is NULL");
+    if (count < 0 || count > NH_MAX_TUBES) return fail(c, NH_EINVAL, "tube count out of range");
+    if (count > 0 && !centres) return fail(c, NH_EINVAL, "centres is NULL");
+    c->n_tubes = count;
+    for (int k = 0; k < count; ++k) {
+        c->tubes[k][0] = centres[2 * k];
+        c->tubes[k][1] = centres[2 * k + 1];
+    }
+    return NH_OK;
+}
+
+int nh_diagnostics_enqueue(nh_ctx* c, void* stream)
+{
+    int r = check_ready(c);
+    if (r) return r;
+    if ((r = set_device(c))) return r;
+    cudaStream_t st = pick(c, stream);
+    if ((r = enqueue_diag(c, st))) return r;
+    c->diag_stream = st;
+    c->diag_tubes = c->n_tubes;
+    c->diag_pending = true;
+    return NH_OK;
+}
+
+int nh_diagnostics_read(nh_ctx* c, nh_diag* out)
+{
+    int r = check_ready(c);
+    if (r) return r;
+    if (!out) return fail(c, NH_EINVAL, "out is NULL");
+    if (!c->diag_pending) return fail(c, NH_EINVAL, "no diagnostics enqueued");
+    if ((r = set_device(c))) return r;
+    cudaStream_t st = c->diag_stream;
+    const int V = diag_num_values(c->diag_tubes);
+    NH_CUDA(c, cudaMemcpyAsync(c->host_result, c->ws + c->L.result, V * sizeof(double), cudaMemcpyDeviceToHost, st));
+    NH_CUDA(c, cudaStreamSynchronize(st));
+    c->diag_pending = false;
+    memset(out, 0, sizeof(*out));
+    const double* v = c->host_result;
+    out->step = c->step;
+    out->mass = v[0] + (c->p.shifted ? (double)c->N : 0.0);
+    out->energy = v[1];
+    out->max_u = v[2];
+    out->min_norm = v[3];
+    out->max_norm = v[4];
+    out->nonfinite = (int32_t)v[5];
+    out->n_tubes = c->diag_tubes;
+    const double twopi = 6.283185307179586476925286766559;
+    for (int k = 0; k < c->diag_tubes; ++k) {
+        const double* t = v + 6 + 5 * k;
+        double cx = atan2(t[1], t[2]) * c->p.nx / twopi;
+        double cy = atan2(t[3], t[4]) * c->p.ny / twopi;
+        if (cx < 0) cx += c->p.nx;
+        if (cy < 0) cy += c->p.ny;
+        out->centroid[k][0] = cx;
+        out->centroid[k][1] = cy;
+        out->tube_weight[k] = t[0];
+        if (t[0] > 0 && k < c->n_tubes) {
+            c->tubes[k][0] = cx;
+            c->tubes[k][1] = cy;
+        }
+    }
+    if (out->nonfinite > 0) return fail(c, NH_EUNSTABLE, "non-finite values in n, u, rho or f");
+    return NH_OK;
+}
+
+int nh_diagnostics(nh_ctx* c, nh_diag* out)
+{
+    int r = check_ready(c);
+    if (r) return r;
+    if (!out) return fail(c, NH_EINVAL, "out is NULL");
+    if ((r = nh_diagnostics_enqueue(c, nullptr))) return r;
+    return nh_diagnostics_read(c, out);
+}
+
+int nh_set_timing(nh_ctx* c, int on)
+{
+    if (!c) return fail(nullptr, NH_EINVAL, "ctx is NULL");
+    c->timing = on != 0;
+    return NH_OK;
+}
+
+int nh_get_timing(nh_ctx* c, nh_timing* out)
+{
+    if (!c || !out) return fail(c, NH_EINVAL, "NULL argument");
+    if (!c->pending.empty()) {
+        for (auto& t : c->pending) {
+            cudaError_t e = cudaEventSynchronize(t.b);
+            if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventSynchronize");
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, t.a, t.b);
+            if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventElapsedTime");
+            c->tstats.launches[t.kclass] += 1;
+            c->tstats.ms[t.kclass] += ms;
+            c->free_events.push_back(t.a);
+            c->free_events.push_back(t.b);
+        }
+        c->pending.clear();
+    }
+    *out = c->tstats;
+    memset(&c->tstats, 0, sizeof(c->tstats));
+    return NH_OK;
+}
+
+int64_t nh_launch_count(const nh_ctx* c) { return c ? c->launches : 0; }
+
+int nh_set_graphs(nh_ctx* c, int on)
+{
+    if (!c) return fail(nullptr, NH_EINVAL, "ctx is NULL");
+    c->use_graphs = on != 0;
+    return NH_OK;
+}
+
+void nh_destroy(nh_ctx* c)
+{
+    if (!c) return;
+    if (set_device(c) == NH_OK) {
+        if (c->stream) cudaStreamSynchronize(c->stream);
+        drop_graphs(c);
+        for (auto& t : c->pending) {
+            cudaEventDestroy(t.a);
+            cudaEventDestroy(t.b);
+        }
+        for (auto e : c->free_events) cudaEventDestroy(e);
+        if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    }
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,402 @@
+// diag.cu -- field conversion, population initialisation and the FP64 global
+// diagnostics (mass, lattice Frank energy, |u| and |n| extrema, NaN count,
+// skyrmion-tube centroid sums) of the hybrid LB + FD library.
+#include "nh_internal.cuh"
+
+namespace nh {
+
+namespace {
+
+template <typename Real>
+__global__ void load_fields_kernel(const double* __restrict__ n, const double* __restrict__ u,
+                                   const double* __restrict__ rho, Real* dn, Real* du, Real* drho, int N)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    const double a = n[s], b = n[N + s], c = n[2 * N + s];
+    const double inv = 1.0 / sqrt(a * a + b * b + c * c);
+    dn[s] = Real(a * inv);
+    dn[N + s] = Real(b * inv);
+    dn[2 * N + s] = Real(c * inv);
+    for (int k = 0; k < 3; ++k) du[k * N + s] = u ? Real(u[k * N + s]) : Real(0);
+    drho[s] = rho ? Real(rho[s]) : Real(1);
+}
+
+template <typename Real>
+__global__ void store_vec_kernel(const Real* __restrict__ src, double* __restrict__ dst, int64_t count)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) dst[i] = (double)src[i];
+}
+
+template <typename Real, typename Store, bool Shifted>
+__global__ void init_populations_kernel(const Real* __restrict__ rho, const Real* __restrict__ u, Store* f,
+                                        const float* scale, int N)
+{
+    NH_D3Q19_TABLES
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    const float sc = sizeof(Store) == 2 ? scale[0] : 1.f;
+    const Real r = rho[s];
+    const Real ux = u[s], uy = u[N + s], uz = u[2 * N + s];
+    const Real uu = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const Real w = d3q19_w<Real>(i);
+        const Real eu = Real(EX[i]) * ux + Real(EY[i]) * uy + Real(EZ[i]) * uz;
+        Real feq = w * r * (Real(3) * eu + Real(4.5) * eu * eu - Real(1.5) * uu);
+        feq += Shifted ? w * (r - Real(1)) : w * r;
+        Codec<Store, Real>::store(f + (size_t)i * N + s, feq, sc);
+    }
+}
+
+template <typename Store>
+__global__ void decode_plane_kernel(const Store* __restrict__ f, double* __restrict__ dst, int N, const float* scale)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    if constexpr (sizeof(Store) == 2) {
+        dst[s] = (double)Codec<Store, float>::load(f + s, 1.f / scale[0]);
+    } else {
+        dst[s] = (double)f[s];
+    }
+}
+
+template <typename Store>
+__global__ void encode_plane_kernel(const double* __restrict__ src, Store* __restrict__ f, int N, const float* scale)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    if constexpr (sizeof(Store) == 2) {
+        Codec<Store, float>::store(f + s, (float)src[s], scale[0]);
+    } else {
+        f[s] = (Store)src[s];
+    }
+}
+
+// Initial power-of-two scale of a 16-bit store: from the largest equilibrium
+// population of the initial state and half the largest body force (the size of
+// the first Guo source), so that both start near 2^kScaleHeadroomLog2.
+__global__ void scale_probe_kernel(const float* __restrict__ rho, const float* __restrict__ u,
+                                   const float* __restrict__ F, float gx, float gy, float gz, int N, unsigned* ctrl)
+{
+    NH_D3Q19_TABLES
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    float m = 0.f;
+    if (s < N) {
+        const float r = rho[s];
+        const float ux = u[s], uy = u[N + s], uz = u[2 * N + s];
+        const float uu = ux * ux + uy * uy + uz * uz;
+        for (int i = 0; i < 19; ++i) {
+            const float w = d3q19_w<float>(i);
+            const float eu = EX[i] * ux + EY[i] * uy + EZ[i] * uz;
+            m = fmaxf(m, fabsf(w * r * (3.f * eu + 4.5f * eu * eu - 1.5f * uu) + w * (r - 1.f)));
+        }
+        const float fx = F[s] + r * gx, fy = F[N + s] + r * gy, fz = F[2 * N + s] + r * gz;
+        m = fmaxf(m, 0.5f * sqrtf(fx * fx + fy * fy + fz * fz));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(reinterpret_cast<int*>(&ctrl[0]), __float_as_int(m));
+}
+
+__global__ void scale_set_kernel(float* scales, unsigned* ctrl)
+{
+    const float m = __uint_as_float(ctrl[0]);
+    float t = 1.f;
+    if (m > 0.f && isfinite(m)) {
+        int e;
+        frexpf(m, &e);
+        int k = kScaleHeadroomLog2 - e;
+        k = k < -120 ? -120 : (k > 120 ? 120 : k);
+        t = ldexpf(1.f, k);
+    }
+    scales[0] = scales[1] = scales[2] = t;
+    ctrl[0] = 0u;
+    ctrl[1] = 0u;
+}
+
+// ------------------------------------------------------------------ diagnostics
+
+constexpr int DIAG_THREADS = 256;
+constexpr int DIAG_FIXED = 6;  // mass, energy, max_u, min_norm, max_norm, nonfinite
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_min(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <typename Real>
+__device__ __forceinline__ void dir_d(const Real* n, const Geom& g, int x, int y, int z, double out[3])
+{
+    x = wrap_p(x, g.nx);
+    y = wrap_p(y, g.ny);
+    if (g.walls && (z < 0 || z >= g.nz)) {
+        if (g.anchoring == NH_ANCHOR_HOMEOTROPIC) {
+            out[0] = 0.0;
+            out[1] = 0.0;
+            out[2] = 1.0;
+            return;
+        }
+        z = z < 0 ? 0 : g.nz - 1;
+    }
+    z = wrap_p(z, g.nz);
+    const int s = x + g.nx * (y + g.ny * z);
+    out[0] = (double)n[s];
+    out[1] = (double)n[g.N + s];
+    out[2] = (double)n[2 * g.N + s];
+}
+
+// Link energy between n (at x) and m (at x + e_b):
+// K/2 |m - n|^2 - K q0 (n x m)_b   (= K q0 eps_abc n_a m_c).
+__device__ __forceinline__ double link_energy(const double n[3], const double m[3], int b, double K, double q0)
+{
+    const double d0 = m[0] - n[0], d1 = m[1] - n[1], d2 = m[2] - n[2];
+    double cr;
+    if (b == 0)
+        cr = n[1] * m[2] - n[2] * m[1];
+    else if (b == 1)
+        cr = n[2] * m[0] - n[0] * m[2];
+    else
+        cr = n[0] * m[1] - n[1] * m[0];
+    return 0.5 * K * (d0 * d0 + d1 * d1 + d2 * d2) - K * q0 * cr;
+}
+
+template <typename Real, typename Store>
+__global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const DiagArgs a)
+{
+    const Geom g = a.g;
+    const int N = g.N;
+    const Store* f = static_cast<const Store*>(a.f);
+    const Real* n = static_cast<const Real*>(a.n);
+    const Real* u = static_cast<const Real*>(a.u);
+    const Real* rho = static_cast<const Real*>(a.rho);
+    const float inv_scale = sizeof(Store) == 2 ? 1.f / a.scale[0] : 1.f;
+    const int T = a.n_tubes;
+    __shared__ double tube_acc[NH_MAX_TUBES * 5];
+    __shared__ double red[DIAG_THREADS / 32][DIAG_FIXED];
+    for (int k = threadIdx.x; k < T * 5; k += blockDim.x) tube_acc[k] = 0.0;
+    __syncthreads();
+
+    double mass = 0.0, energy = 0.0, max_u = 0.0, min_nn = 1e300, max_nn = 0.0, bad = 0.0;
+    const double twopi = 6.283185307179586476925286766559;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+        const int x = s % g.nx;
+        const int t = s / g.nx;
+        const int y = t % g.ny;
+        const int z = t / g.ny;
+        double fs = 0.0;
+        for (int i = 0; i < 19; ++i) fs += (double)Codec<Store, Real>::load(f + (size_t)i * N + s, inv_scale);
+        mass += fs;
+        double c[3], m[3];
+        dir_d(n, g, x, y, z, c);
+        dir_d(n, g, x + 1, y, z, m);
+        double e = link_energy(c, m, 0, a.K, a.q0);
+        dir_d(n, g, x, y + 1, z, m);
+        e += link_energy(c, m, 1, a.K, a.q0);
+        dir_d(n, g, x, y, z + 1, m);
+        e += link_energy(c, m, 2, a.K, a.q0);
+        if (g.walls && z == 0) {
+            dir_d(n, g, x, y, -1, m);
+            e += link_energy(m, c, 2, a.K, a.q0);
+        }
+        e += 0.5 * a.K * a.q0 * a.q0 - 0.5 * a.W0 * c[2] * c[2];
+        energy += e;
+        const double u0 = (double)u[s], u1 = (double)u[N + s], u2 = (double)u[2 * N + s];
+        const double r = (double)rho[s];
+        const double umag = sqrt(u0 * u0 + u1 * u1 + u2 * u2);
+        const double nmag = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+        max_u = fmax(max_u, umag);
+        min_nn = fmin(min_nn, nmag);
+        max_nn = fmax(max_nn, nmag);
+        if (!isfinite(umag) || !isfinite(nmag) || !isfinite(r) || !isfinite(fs)) bad += 1.0;
+        if (T > 0) {
+            int best = 0;
+            double bd = 1e300;
+            for (int k = 0; k < T; ++k) {
+                double dx = x - a.tubes[k][0], dy = y - a.tubes[k][1];
+                dx -= g.nx * floor(dx / g.nx + 0.5);
+                dy -= g.ny * floor(dy / g.ny + 0.5);
+                const double d2 = dx * dx + dy * dy;
+                if (d2 < bd) {
+                    bd = d2;
+                    best = k;
+                }
+            }
+            const double w = 0.5 * (1.0 - c[2]);
+            double sx, cx, sy, cy;
+            sincos(twopi * x / g.nx, &sx, &cx);
+            sincos(twopi * y / g.ny, &sy, &cy);
+            atomicAdd(&tube_acc[best * 5 + 0], w);
+            atomicAdd(&tube_acc[best * 5 + 1], w * sx);
+            atomicAdd(&tube_acc[best * 5 + 2], w * cx);
+            atomicAdd(&tube_acc[best * 5 + 3], w * sy);
+            atomicAdd(&tube_acc[best * 5 + 4], w * cy);
+        }
+    }
+    mass = warp_sum(mass);
+    energy = warp_sum(energy);
+    bad = warp_sum(bad);
+    max_u = warp_max(max_u);
+    min_nn = warp_min(min_nn);
+    max_nn = warp_max(max_nn);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[wid][0] = mass;
+        red[wid][1] = energy;
+        red[wid][2] = max_u;
+        red[wid][3] = min_nn;
+        red[wid][4] = max_nn;
+        red[wid][5] = bad;
+    }
+    __syncthreads();
+    const int V = DIAG_FIXED + 5 * T;
+    double* out = a.partials + (size_t)blockIdx.x * V;
+    if (threadIdx.x == 0) {
+        double v[DIAG_FIXED] = {0.0, 0.0, 0.0, 1e300, 0.0, 0.0};
+        for (int w = 0; w < DIAG_THREADS / 32; ++w) {
+            v[0] += red[w][0];
+            v[1] += red[w][1];
+            v[2] = fmax(v[2], red[w][2]);
+            v[3] = fmin(v[3], red[w][3]);
+            v[4] = fmax(v[4], red[w][4]);
+            v[5] += red[w][5];
+        }
+        for (int k = 0; k < DIAG_FIXED; ++k) out[k] = v[k];
+    }
+    for (int k = threadIdx.x; k < 5 * T; k += blockDim.x) out[DIAG_FIXED + k] = tube_acc[k];
+}
+
+__global__ void diag_final_kernel(const double* __restrict__ partials, double* __restrict__ result, int blocks, int V)
+{
+    // one thread per value, blocks summed in a fixed order (deterministic)
+    for (int k = threadIdx.x; k < V; k += blockDim.x) {
+        double acc = (k == 3) ? 1e300 : 0.0;
+        for (int b = 0; b < blocks; ++b) {
+            const double v = partials[(size_t)b * V + k];
+            if (k == 2 || k == 4)
+                acc = fmax(acc, v);
+            else if (k == 3)
+                acc = fmin(acc, v);
+            else
+                acc += v;
+        }
+        result[k] = acc;
+    }
+}
+
+inline int blocks_for(int64_t n) { return (int)((n + 255) / 256); }
+
+}  // namespace
+
+int diag_num_values(int n_tubes) { return DIAG_FIXED + 5 * n_tubes; }
+int diag_blocks() { return 4 * 152; }
+
+template <typename Real>
+cudaError_t launch_load_fields(const double* n, const double* u, const double* rho, Real* dn, Real* du, Real* drho,
+                               int N, cudaStream_t st)
+{
+    load_fields_kernel<Real><<<blocks_for(N), 256, 0, st>>>(n, u, rho, dn, du, drho, N);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t launch_store_vec(const Real* src, double* dst, int64_t count, cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    store_vec_kernel<Real><<<blocks_for(count), 256, 0, st>>>(src, dst, count);
+    return cudaGetLastError();
+}
+
+template <typename Real, typename Store>
+cudaError_t launch_init_populations(const Real* rho, const Real* u, Store* f, const float* scale, int N, bool shifted,
+                                    cudaStream_t st)
+{
+    if (shifted)
+        init_populations_kernel<Real, Store, true><<<blocks_for(N), 256, 0, st>>>(rho, u, f, scale, N);
+    else
+        init_populations_kernel<Real, Store, false><<<blocks_for(N), 256, 0, st>>>(rho, u, f, scale, N);
+    return cudaGetLastError();
+}
+
+template <typename Store>
+cudaError_t launch_decode_plane(const Store* f, double* dst, int N, const float* scale, cudaStream_t st)
+{
+    decode_plane_kernel<Store><<<blocks_for(N), 256, 0, st>>>(f, dst, N, scale);
+    return cudaGetLastError();
+}
+
+template <typename Store>
+cudaError_t launch_encode_plane(const double* src, Store* f, int N, const float* scale, cudaStream_t st)
+{
+    encode_plane_kernel<Store><<<blocks_for(N), 256, 0, st>>>(src, f, N, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_init(const float* rho, const float* u, const float* F, const double g[3], int N,
+                              float* scales, unsigned* ctrl, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(ctrl, 0, 2 * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    scale_probe_kernel<<<blocks_for(N), 256, 0, st>>>(rho, u, F, (float)g[0], (float)g[1], (float)g[2], N, ctrl);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    scale_set_kernel<<<1, 1, 0, st>>>(scales, ctrl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics(const DiagArgs& a, cudaStream_t st)
+{
+    const int blocks = a.blocks;
+    if (a.precision == NH_FP64) {
+        diag_kernel<double, double><<<blocks, DIAG_THREADS, 0, st>>>(a);
+    } else {
+        switch (a.storage) {
+        case NH_STORE_F32: diag_kernel<float, float><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
+        case NH_STORE_F16S: diag_kernel<float, __half><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
+        default: diag_kernel<float, __nv_bfloat16><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    diag_final_kernel<<<1, 256, 0, st>>>(a.partials, a.result, blocks, diag_num_values(a.n_tubes));
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_load_fields<double>(const double*, const double*, const double*, double*, double*,
+                                                double*, int, cudaStream_t);
+template cudaError_t launch_load_fields<float>(const double*, const double*, const double*, float*, float*, float*,
+                                               int, cudaStream_t);
+template cudaError_t launch_store_vec<double>(const double*, double*, int64_t, cudaStream_t);
+template cudaError_t launch_store_vec<float>(const float*, double*, int64_t, cudaStream_t);
+template cudaError_t launch_init_populations<double, double>(const double*, const double*, double*, const float*,
+                                                             int, bool, cudaStream_t);
+template cudaError_t launch_init_populations<float, float>(const float*, const float*, float*, const float*, int,
+                                                           bool, cudaStream_t);
+template cudaError_t launch_init_populations<float, __half>(const float*, const float*, __half*, const float*, int,
+                                                            bool, cudaStream_t);
+template cudaError_t launch_init_populations<float, __nv_bfloat16>(const float*, const float*, __nv_bfloat16*,
+                                                                   const float*, int, bool, cudaStream_t);
+template cudaError_t launch_decode_plane<double>(const double*, double*, int, const float*, cudaStream_t);
+template cudaError_t launch_decode_plane<float>(const float*, double*, int, const float*, cudaStream_t);
+template cudaError_t launch_decode_plane<__half>(const __half*, double*, int, const float*, cudaStream_t);
+template cudaError_t launch_decode_plane<__nv_bfloat16>(const __nv_bfloat16*, double*, int, const float*,
+                                                        cudaStream_t);
+template cudaError_t launch_encode_plane<double>(const double*, double*, int, const float*, cudaStream_t);
+template cudaError_t launch_encode_plane<float>(const double*, float*, int, const float*, cudaStream_t);
+template cudaError_t launch_encode_plane<__half>(const double*, __half*, int, const float*, cudaStream_t);
+template cudaError_t launch_encode_plane<__nv_bfloat16>(const double*, __nv_bfloat16*, int, const float*,
+                                                        cudaStream_t);
+
+}  // namespace nh

@@ -1,0 +1,174 @@
+// nh_internal.cuh -- device-side building blocks and launch interfaces of the
+// hybrid LB + FD nematohydrodynamics library (arXiv:2503.06610).  Shared by
+// the kernel translation units and the C-ABI layer; not part of the public ABI.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nh.h"
+
+namespace nh {
+
+// ------------------------------------------------------------------ D3Q19
+// Velocity order of the public header (rest, +-x, +-y, +-z, xy, xz, yz pairs).
+// Weights 1/3, 1/18, 1/36 and c_s^2 = 1/3 (Sec. II.C).
+#define NH_D3Q19_TABLES                                                                                 \
+    constexpr int EX[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};           \
+    constexpr int EY[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};           \
+    constexpr int EZ[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};           \
+    constexpr int OPP[19] = {0, 2, 1, 4, 3, 6, 5, 8, 7, 10, 9, 12, 11, 14, 13, 16, 15, 18, 17};      \
+    (void)EX; (void)EY; (void)EZ; (void)OPP;
+
+template <typename Real>
+__device__ __forceinline__ Real d3q19_w(int i)
+{
+    return i == 0 ? Real(1) / Real(3) : (i < 7 ? Real(1) / Real(18) : Real(1) / Real(36));
+}
+
+// ------------------------------------------------------------------ storage codecs
+// Populations are stored as Store and computed as Real.  The 16-bit codecs hold
+// 2^k * f_shifted; `scale` = 2^k and `inv_scale` = 2^-k (exact powers of two).
+template <typename Store, typename Real>
+struct Codec;
+
+template <>
+struct Codec<double, double> {
+    static __device__ __forceinline__ double load(const double* p, float) { return *p; }
+    static __device__ __forceinline__ void store(double* p, double v, float) { *p = v; }
+};
+template <>
+struct Codec<float, float> {
+    static __device__ __forceinline__ float load(const float* p, float) { return *p; }
+    static __device__ __forceinline__ void store(float* p, float v, float) { *p = v; }
+};
+template <>
+struct Codec<__half, float> {
+    static __device__ __forceinline__ float load(const __half* p, float inv_scale)
+    {
+        return __half2float(*p) * inv_scale;
+    }
+    static __device__ __forceinline__ void store(__half* p, float v, float scale) { *p = __float2half_rn(v * scale); }
+};
+template <>
+struct Codec<__nv_bfloat16, float> {
+    static __device__ __forceinline__ float load(const __nv_bfloat16* p, float inv_scale)
+    {
+        return __bfloat162float(*p) * inv_scale;
+    }
+    static __device__ __forceinline__ void store(__nv_bfloat16* p, float v, float scale)
+    {
+        *p = __float2bfloat16_rn(v * scale);
+    }
+};
+
+// ------------------------------------------------------------------ geometry
+struct Geom {
+    int nx, ny, nz;
+    int walls;      // bounce-back plates in z
+    int anchoring;  // NH_ANCHOR_*
+    int N;          // nx*ny*nz
+};
+
+__device__ __forceinline__ int wrap_p(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+// ------------------------------------------------------------------ LB
+// One channel's LB sweep arguments.  For the 16-bit stores `scales` points to
+// four device floats: [0], [1] = scale 2^k of the data in population buffer
+// 0 / 1, [2] = target scale for the next write; `ctrl` to two words used by
+// the in-kernel scale controller (running max |f*| as float bits, and a
+// block-completion ticket).
+template <typename Real, typename Store>
+struct LBChan {
+    const Store* fsrc;
+    Store* fdst;
+    const Real* F;  // [3][N] F_lc, frozen over the FD interval
+    Real* u;        // [3][N] written on macro steps
+    Real* rho;      // [N]    written on macro steps
+    float* scales;
+    unsigned* ctrl;
+    int src;        // index (0/1) of the source buffer
+    Geom g;
+    Real omega;     // 1/tau
+    Real gx, gy, gz;
+};
+
+// Scaled 16-bit stores keep max |2^k f*| near 2^kScaleHeadroomLog2.
+constexpr int kScaleHeadroomLog2 = 12;
+
+// ------------------------------------------------------------------ FD
+template <typename Real>
+struct FDPar {
+    Real K, q0, W0;
+    Real inv_gamma1, gamma2, g2_over_g1;
+    Real a1, a2, a3, a4p, a5, a6;
+    Real dt;
+};
+
+template <typename Real>
+struct FDChan {
+    Real* n;      // [3][N] director (in place on the corrector)
+    Real* nP;     // [3][N] predictor
+    Real* ndot;   // [3][N] (dn/dt)_old
+    const Real* u;   // [3][N]
+    Real* sigma;  // [9][N]
+    Real* F;      // [3][N] F_lc
+    Geom g;
+    FDPar<Real> p;
+};
+
+// ------------------------------------------------------------------ launchers (host)
+template <typename Real, typename Store>
+cudaError_t launch_lb(const LBChan<Real, Store>& c, bool shifted, bool write_macro, cudaStream_t s);
+
+template <typename Real>
+cudaError_t launch_fd_predict(const FDChan<Real>& c, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_fd_correct(const FDChan<Real>& c, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_stress(const FDChan<Real>& c, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_force(const FDChan<Real>& c, cudaStream_t s);
+
+// Field conversion and initialisation (diag.cu)
+template <typename Real>
+cudaError_t launch_load_fields(const double* n, const double* u, const double* rho, Real* dn, Real* du, Real* drho,
+                               int N, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_store_vec(const Real* src, double* dst, int64_t count, cudaStream_t s);
+template <typename Real, typename Store>
+cudaError_t launch_init_populations(const Real* rho, const Real* u, Store* f, const float* scale, int N, bool shifted,
+                                    cudaStream_t s);
+template <typename Store>
+cudaError_t launch_decode_plane(const Store* f, double* dst, int N, const float* scale, cudaStream_t s);
+template <typename Store>
+cudaError_t launch_encode_plane(const double* src, Store* f, int N, const float* scale, cudaStream_t s);
+
+cudaError_t launch_scale_init(const float* rho, const float* u, const float* F, const double g[3], int N,
+                              float* scales, unsigned* ctrl, cudaStream_t s);
+
+// Diagnostics (diag.cu)
+struct DiagArgs {
+    const void* f;      // populations (Store)
+    int storage;
+    int shifted;
+    const void* n;      // Real [3][N]
+    const void* u;
+    const void* rho;
+    int precision;
+    const float* scale;
+    Geom g;
+    double K, q0, W0;
+    int n_tubes;
+    double tubes[NH_MAX_TUBES][2];
+    double* partials;   // [blocks][NDIAG]
+    double* result;     // [NDIAG]
+    int blocks;
+};
+int diag_num_values(int n_tubes);
+int diag_blocks();
+cudaError_t launch_diagnostics(const DiagArgs& a, cudaStream_t s);
+
+}  // namespace nh

@@ -1,0 +1,308 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances: the FP64 build must match the oracle to rel. L2 <= 1e-10 (the
+operations are the same; only rounding order differs); the FP32-shifted build
+must hold u and n to rel. L2 <= 1e-4 after 1000 steps of the tiny channel.
+Row-level checks (LB step, FD update, stress + force) use ragged grids that
+span several thread blocks and include both plates.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2503_06610_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nh():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2503_06610_gb300 import nh as m
+    m.load_library()
+    return m
+
+
+def _oracle_sim(O, params, n0, u0=None):
+    return O.OracleSim(O.OracleParams.from_dict(params), n0, u=u0)
+
+
+def _channel(nh, params, n0, u0=None, **kw):
+    ch = nh.Channel(dict(params, **kw))
+    ch.set_fields(n0, u0)
+    return ch
+
+
+LESLIE = I.LESLIE_ALIGN_09
+
+
+def _generic(nx, ny, nz, **kw):
+    d = dict(nx=nx, ny=ny, nz=nz, walls_z=True, anchoring="homeotropic", shifted=True, tau=0.8,
+             g=(1e-5, -3e-6, 0.0), K=0.03, q0=2 * math.pi / 10, W0=0.0, dt_fd=1, **LESLIE)
+    d.update(kw)
+    return d
+
+
+# ------------------------------------------------------------------ row-level parity (FP64)
+
+@pytest.mark.parametrize("shifted", [True, False])
+@pytest.mark.parametrize("walls", [True, False])
+def test_lb_rows_fp64(nh, oracle_mod, shifted, walls):
+    """Pure flow (K = 0): populations, rho and u after 37 steps."""
+    O = oracle_mod
+    params = _generic(19, 11, 9, K=0.0, q0=0.0, walls_z=walls, shifted=shifted, alpha2=0, alpha3=0,
+                      alpha5=0, alpha6=0, gamma2=0.0)
+    n0 = I.uniform_director(19, 11, 9)
+    u0 = I.random_velocity(19, 11, 9, 1e-3, seed=3)
+    ref = _oracle_sim(O, params, n0, u0).step(37)
+    ch = _channel(nh, params, n0, u0, precision="fp64")
+    ch.step(37)
+    n, u, rho = ch.get_fields()
+    f = ch.get_populations()
+    assert O.rel_l2(u, ref.u) < 1e-12
+    assert O.rel_l2(rho - 1, ref.rho - 1) < 1e-10
+    assert np.max(np.abs(f - ref.f)) < 1e-13
+
+
+@pytest.mark.parametrize("anchoring,walls", [("homeotropic", True), ("none", True), ("homeotropic", False)])
+def test_stress_force_rows_fp64(nh, oracle_mod, anchoring, walls):
+    O = oracle_mod
+    params = _generic(13, 9, 7, walls_z=walls, anchoring=anchoring, W0=0.02, alpha1=0.1, alpha4p=0.2)
+    n0 = I.random_director(13, 9, 7, seed=5)
+    u0 = I.random_velocity(13, 9, 7, 1e-3, seed=6)
+    p = O.OracleParams.from_dict(params)
+    Fref = O.force(p, O.stress(p, n0, u0))
+    ch = _channel(nh, params, n0, u0, precision="fp64")
+    F = ch.get_force()
+    assert O.rel_l2(F, Fref) < 1e-12
+
+
+@pytest.mark.parametrize("anchoring,walls", [("homeotropic", True), ("none", True), ("homeotropic", False)])
+def test_fd_update_rows_fp64(nh, oracle_mod, anchoring, walls):
+    O = oracle_mod
+    params = _generic(13, 9, 7, walls_z=walls, anchoring=anchoring, W0=0.02, dt_fd=3)
+    n0 = I.random_director(13, 9, 7, seed=7)
+    u0 = I.random_velocity(13, 9, 7, 1e-2, seed=8)
+    p = O.OracleParams.from_dict(params)
+    nref = O.fd_step(p, n0, u0)
+    Fref = O.force(p, O.stress(p, nref, u0))
+    ch = _channel(nh, params, n0, u0, precision="fp64")
+    ch.fd_update()
+    n, u, _ = ch.get_fields()
+    assert O.rel_l2(n, nref) < 1e-13
+    assert np.max(np.abs(np.linalg.norm(n, axis=0) - 1)) < 1e-14
+    assert O.rel_l2(ch.get_force(), Fref) < 1e-12
+
+
+@pytest.mark.parametrize("anchoring,walls", [("homeotropic", True), ("none", True)])
+def test_fd_update_rows_fp32(nh, oracle_mod, anchoring, walls):
+    O = oracle_mod
+    params = _generic(13, 9, 7, walls_z=walls, anchoring=anchoring, W0=0.02, dt_fd=3)
+    n0 = I.random_director(13, 9, 7, seed=7)
+    u0 = I.random_velocity(13, 9, 7, 1e-2, seed=8)
+    p = O.OracleParams.from_dict(params)
+    nref = O.fd_step(p, n0, u0)
+    Fref = O.force(p, O.stress(p, nref, u0))
+    ch = _channel(nh, params, n0, u0, precision="fp32")
+    ch.fd_update()
+    n, _, _ = ch.get_fields()
+    assert O.rel_l2(n, nref) < 1e-6
+    assert O.rel_l2(ch.get_force(), Fref) < 1e-5
+
+
+# ------------------------------------------------------------------ full hybrid runs
+
+def test_tiny_channel_fp64_200_steps(nh, oracle_mod):
+    """32x32x16 nematic channel, 200 steps at dt_FD = 1: FP64 GPU vs oracle <= 1e-10."""
+    O = oracle_mod
+    params, n0 = I.tiny_channel()
+    ref = _oracle_sim(O, params, n0).step(200)
+    ch = _channel(nh, params, n0, precision="fp64")
+    ch.step(200)
+    n, u, rho = ch.get_fields()
+    assert O.rel_l2(u, ref.u) <= 1e-10
+    assert O.rel_l2(n, ref.n) <= 1e-10
+    d = ch.diagnostics()
+    assert abs(d["mass"] - ref.mass()) <= 1e-12 * ch.N
+    assert abs(d["energy"] - ref.energy()) <= 1e-10 * abs(ref.energy())
+
+
+@pytest.fixture(scope="module")
+def tiny_ref_1000(oracle_mod):
+    params, n0 = I.tiny_channel()
+    return params, n0, _oracle_sim(oracle_mod, params, n0).step(1000)
+
+
+def test_tiny_channel_fp32_shifted_1000_steps(nh, oracle_mod, tiny_ref_1000):
+    """FP32-shifted holds u and n to rel. L2 <= 1e-4 after 1000 steps."""
+    O = oracle_mod
+    params, n0, ref = tiny_ref_1000
+    ch = _channel(nh, params, n0, precision="fp32", storage="f32", shifted=True)
+    ch.step(1000)
+    n, u, rho = ch.get_fields()
+    eu, en = O.rel_l2(u, ref.u), O.rel_l2(n, ref.n)
+    print(f"FP32-shifted 1000 steps: rel L2 u {eu:.3e} n {en:.3e} eps {O.eps_paper(u, ref.u):.3e}")
+    assert eu <= 1e-4
+    assert en <= 1e-4
+
+
+def test_tiny_channel_fp32_unshifted_reported(nh, oracle_mod, tiny_ref_1000):
+    """The plain FP32 store is reported beside the shifted one (precision loss at low velocity)."""
+    O = oracle_mod
+    params, n0, ref = tiny_ref_1000
+    errs = {}
+    for shifted in (True, False):
+        ch = _channel(nh, params, n0, precision="fp32", storage="f32", shifted=shifted)
+        ch.step(1000)
+        n, u, _ = ch.get_fields()
+        errs[shifted] = (O.rel_l2(u, ref.u), O.rel_l2(n, ref.n))
+    print(f"FP32 rel L2(u): shifted {errs[True][0]:.3e}  unshifted {errs[False][0]:.3e}")
+    assert errs[True][0] < errs[False][0]
+    assert np.isfinite(errs[False][0])
+
+
+@pytest.mark.parametrize("storage,tol", [("f16s", 2e-2), ("bf16s", 2e-1)])
+def test_16bit_stores_reported(nh, oracle_mod, tiny_ref_1000, storage, tol):
+    O = oracle_mod
+    params, n0, ref = tiny_ref_1000
+    ch = _channel(nh, params, n0, precision="fp32", storage=storage, shifted=True)
+    ch.step(1000)
+    n, u, _ = ch.get_fields()
+    eu, en = O.rel_l2(u, ref.u), O.rel_l2(n, ref.n)
+    print(f"{storage}: rel L2 u {eu:.3e} n {en:.3e}")
+    assert eu <= tol
+    assert en <= tol
+
+
+def test_ragged_dtfd_fp64(nh, oracle_mod):
+    """dt_FD = 3 on a ragged 13x7x5 grid, 31 steps (graph blocks + a ragged tail)."""
+    O = oracle_mod
+    params = _generic(13, 7, 5, dt_fd=3, K=0.02, W0=0.01, anchoring="none")
+    n0 = I.skyrmion_tubes(13, 7, 5, [(6.0, 3.0)], 3.0)
+    ref = _oracle_sim(O, params, n0).step(31)
+    ch = _channel(nh, params, n0, precision="fp64")
+    ch.step(10)
+    ch.step(21)
+    n, u, _ = ch.get_fields()
+    assert O.rel_l2(u, ref.u) <= 1e-10
+    assert O.rel_l2(n, ref.n) <= 1e-10
+
+
+def test_graphs_match_direct_launches_bitwise(nh):
+    params = _generic(16, 12, 8, dt_fd=4)
+    n0 = I.tilted_director(16, 12, 8, amplitude=0.2, seed=2)
+    out = []
+    for graphs in (True, False):
+        ch = _channel(nh, params, n0, precision="fp32")
+        ch.set_graphs(graphs)
+        ch.step(40)
+        out.append(ch.get_fields())
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_checkpoint_resume_bit_exact(nh, prec):
+    params = _generic(16, 10, 8, dt_fd=4)
+    n0 = I.skyrmion_tubes(16, 10, 8, [(8.0, 5.0)], 4.0)
+    a = _channel(nh, params, n0, precision=prec)
+    a.step(22)
+    n, u, rho = a.get_fields()
+    f = a.get_populations()
+    F = a.get_force()
+    a.step(13)
+    end_a = a.get_fields()
+    b = _channel(nh, params, n0, precision=prec)
+    b.set_populations(f)
+    b.restore(n, F=F, u=u, rho=rho, step=22)
+    b.step(13)
+    end_b = b.get_fields()
+    for x, y in zip(end_a, end_b):
+        assert np.array_equal(x, y)
+
+
+def test_diagnostics_match_oracle(nh, oracle_mod):
+    O = oracle_mod
+    params = _generic(40, 36, 6, dt_fd=2, K=0.02, q0=2 * math.pi / 12)
+    n0 = I.skyrmion_tubes(40, 36, 6, [(10.0, 9.0), (30.0, 27.0)], 8.0)
+    ref = _oracle_sim(O, params, n0).step(10)
+    ch = _channel(nh, params, n0, precision="fp64")
+    ch.set_tubes([(10.0, 9.0), (30.0, 27.0)])
+    ch.step(10)
+    d = ch.diagnostics()
+    assert abs(d["mass"] - ref.mass()) <= 1e-12 * ch.N
+    assert abs(d["energy"] - ref.energy()) <= 1e-11 * abs(ref.energy())
+    cref = O.centroids(O.OracleParams.from_dict(params), ref.n, [(10.0, 9.0), (30.0, 27.0)])
+    assert np.max(np.abs(d["centroids"] - cref)) < 1e-9
+    assert d["nonfinite"] == 0
+    assert abs(d["max_norm"] - 1) < 1e-14 and abs(d["min_norm"] - 1) < 1e-14
+
+
+def test_mass_conserved_fp32(nh):
+    params, n0 = I.tiny_channel()
+    ch = _channel(nh, params, n0, precision="fp32")
+    m0 = ch.diagnostics()["mass"]
+    ch.step(500)
+    m1 = ch.diagnostics()["mass"]
+    assert abs(m1 - m0) <= 1e-6 * ch.N
+
+
+def test_empty_step_and_errors(nh):
+    params = _generic(8, 8, 8)
+    ch = nh.Channel(dict(params, precision="fp32"))
+    with pytest.raises(nh.NHError):
+        ch.step(5)               # fields not set
+    ch.set_fields(I.uniform_director(8, 8, 8))
+    ch.step(0)                   # no-op
+    with pytest.raises(nh.NHError):
+        ch.step(-1)
+    n, u, rho = ch.get_fields()
+    assert np.all(np.isfinite(n))
+
+
+def test_nonfinite_detected(nh):
+    params = _generic(8, 8, 8)
+    ch = nh.Channel(dict(params, precision="fp32"))
+    n0 = I.uniform_director(8, 8, 8)
+    ch.set_fields(n0)
+    u = np.zeros((3, ch.N))
+    u[0, 17] = np.nan
+    ch.restore(n0, u=u, step=0)
+    d = ch.diagnostics(allow_unstable=True)
+    assert d["nonfinite"] >= 1 and d["code"] == nh.NH_EUNSTABLE
+
+
+# ------------------------------------------------------------------ full-size checks (bench configuration)
+
+def test_full_size_multi_tube_one_lb_step(nh, oracle_mod):
+    """256x256x64, FP32-shifted, dt_FD = 16: after 16 steps, one more LB step on
+    the GPU equals the oracle's LB step applied to the GPU's own state."""
+    O = oracle_mod
+    params, n0, centres = I.multi_tube_channel()
+    ch = _channel(nh, params, n0, precision="fp32")
+    ch.step(16)
+    f = ch.get_populations()
+    F = ch.get_force()
+    ch.step(1)
+    f1 = ch.get_populations()
+    _, u1, rho1 = ch.get_fields()
+    fo, rho_o, u_o = O.lb_step(O.OracleParams.from_dict(params), f, F)
+    assert O.rel_l2(f1, fo) < 1e-5
+    assert O.rel_l2(u1, u_o) < 1e-5
+    d = ch.diagnostics()
+    assert abs(d["mass"] - ch.N) < 1e-6 * ch.N
+
+
+def test_full_size_multi_tube_fd_update(nh, oracle_mod):
+    O = oracle_mod
+    params, n0, centres = I.multi_tube_channel()
+    u0 = I.random_velocity(256, 256, 64, 1e-4, seed=9)
+    ch = _channel(nh, params, n0, u0, precision="fp32")
+    ch.fd_update()
+    n, _, _ = ch.get_fields()
+    p = O.OracleParams.from_dict(params)
+    nref = O.fd_step(p, n0, u0)
+    assert O.rel_l2(n, nref) < 1e-6
