@@ -117,7 +117,7 @@ __global__ void scale_set_kernel(float* scales, unsigned* ctrl)
 
 // ------------------------------------------------------------------ diagnostics
 
-constexpr int DIAG_THREADS = 256;
+constexpr int DIAG_THREADS = 128;
 constexpr int DIAG_FIXED = 6;  // mass, energy, max_u, min_norm, max_norm, nonfinite
 
 template <typename T>
@@ -137,53 +137,63 @@ __device__ __forceinline__ double warp_min(double v)
     return v;
 }
 
+// Director with the ghost-layer reading (x, y wrapped here; z may be -1 or nz).
 template <typename Real>
-__device__ __forceinline__ void dir_d(const Real* n, const Geom& g, int x, int y, int z, double out[3])
+__device__ __forceinline__ void dir_r(const Real* n, const Geom& g, int x, int y, int z, Real out[3])
 {
     x = wrap_p(x, g.nx);
     y = wrap_p(y, g.ny);
     if (g.walls && (z < 0 || z >= g.nz)) {
         if (g.anchoring == NH_ANCHOR_HOMEOTROPIC) {
-            out[0] = 0.0;
-            out[1] = 0.0;
-            out[2] = 1.0;
+            out[0] = Real(0);
+            out[1] = Real(0);
+            out[2] = Real(1);
             return;
         }
         z = z < 0 ? 0 : g.nz - 1;
     }
     z = wrap_p(z, g.nz);
     const int s = x + g.nx * (y + g.ny * z);
-    out[0] = (double)n[s];
-    out[1] = (double)n[g.N + s];
-    out[2] = (double)n[2 * g.N + s];
+    out[0] = n[s];
+    out[1] = n[g.N + s];
+    out[2] = n[2 * g.N + s];
 }
 
-// Link energy between n (at x) and m (at x + e_b):
-// K/2 |m - n|^2 - K q0 (n x m)_b   (= K q0 eps_abc n_a m_c).
-__device__ __forceinline__ double link_energy(const double n[3], const double m[3], int b, double K, double q0)
+// Energy of the link from n (at x) to m (at x + e_b):
+// K/2 |m - n|^2 + K q0 eps_abc n_a m_c  (= K/2 |m - n|^2 - K q0 (n x m)_b).
+template <typename Real>
+__device__ __forceinline__ Real link_energy(const Real n[3], const Real m[3], int b, Real K, Real q0)
 {
-    const double d0 = m[0] - n[0], d1 = m[1] - n[1], d2 = m[2] - n[2];
-    double cr;
+    const Real d0 = m[0] - n[0], d1 = m[1] - n[1], d2 = m[2] - n[2];
+    Real cr;
     if (b == 0)
         cr = n[1] * m[2] - n[2] * m[1];
     else if (b == 1)
         cr = n[2] * m[0] - n[0] * m[2];
     else
         cr = n[0] * m[1] - n[1] * m[0];
-    return 0.5 * K * (d0 * d0 + d1 * d1 + d2 * d2) - K * q0 * cr;
+    return Real(0.5) * K * (d0 * d0 + d1 * d1 + d2 * d2) - K * q0 * cr;
 }
 
+// One thread per (x, y) column, looping over z.  Per-site terms are evaluated
+// in the build's precision (Real) and accumulated in FP64.  Tube sums use the
+// column weight sum_z (1 - n_z)/2, the column's nearest previous centroid, and
+// warp-aggregated shared-memory accumulation (one atomic per tube per warp).
 template <typename Real, typename Store>
 __global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const DiagArgs a)
 {
     const Geom g = a.g;
     const int N = g.N;
+    const int cols = g.nx * g.ny;
     const Store* f = static_cast<const Store*>(a.f);
     const Real* n = static_cast<const Real*>(a.n);
     const Real* u = static_cast<const Real*>(a.u);
     const Real* rho = static_cast<const Real*>(a.rho);
     const float inv_scale = sizeof(Store) == 2 ? 1.f / a.scale[0] : 1.f;
+    const Real K = Real(a.K), q0 = Real(a.q0), W0 = Real(a.W0);
+    const Real site_const = Real(0.5) * K * q0 * q0;
     const int T = a.n_tubes;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __shared__ double tube_acc[NH_MAX_TUBES * 5];
     __shared__ double red[DIAG_THREADS / 32][DIAG_FIXED];
     for (int k = threadIdx.x; k < T * 5; k += blockDim.x) tube_acc[k] = 0.0;
@@ -191,58 +201,82 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const DiagArgs a)
 
     double mass = 0.0, energy = 0.0, max_u = 0.0, min_nn = 1e300, max_nn = 0.0, bad = 0.0;
     const double twopi = 6.283185307179586476925286766559;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
-        const int x = s % g.nx;
-        const int t = s / g.nx;
-        const int y = t % g.ny;
-        const int z = t / g.ny;
-        double fs = 0.0;
-        for (int i = 0; i < 19; ++i) fs += (double)Codec<Store, Real>::load(f + (size_t)i * N + s, inv_scale);
-        mass += fs;
-        double c[3], m[3];
-        dir_d(n, g, x, y, z, c);
-        dir_d(n, g, x + 1, y, z, m);
-        double e = link_energy(c, m, 0, a.K, a.q0);
-        dir_d(n, g, x, y + 1, z, m);
-        e += link_energy(c, m, 1, a.K, a.q0);
-        dir_d(n, g, x, y, z + 1, m);
-        e += link_energy(c, m, 2, a.K, a.q0);
-        if (g.walls && z == 0) {
-            dir_d(n, g, x, y, -1, m);
-            e += link_energy(m, c, 2, a.K, a.q0);
+    for (int base = blockIdx.x * blockDim.x; base < cols; base += gridDim.x * blockDim.x) {
+        const int col = base + threadIdx.x;
+        const bool valid = col < cols;
+        double wcol = 0.0;
+        int x = 0, y = 0;
+        if (valid) {
+            x = col % g.nx;
+            y = col / g.nx;
+            for (int z = 0; z < g.nz; ++z) {
+                const int s = col + cols * z;
+                Real fs = 0;
+#pragma unroll
+                for (int i = 0; i < 19; ++i) fs += Codec<Store, Real>::load(f + (size_t)i * N + s, inv_scale);
+                mass += (double)fs;
+                Real c[3], m[3];
+                c[0] = n[s];
+                c[1] = n[N + s];
+                c[2] = n[2 * N + s];
+                dir_r(n, g, x + 1, y, z, m);
+                Real e = link_energy(c, m, 0, K, q0);
+                dir_r(n, g, x, y + 1, z, m);
+                e += link_energy(c, m, 1, K, q0);
+                dir_r(n, g, x, y, z + 1, m);
+                e += link_energy(c, m, 2, K, q0);
+                if (g.walls && z == 0) {
+                    dir_r(n, g, x, y, -1, m);
+                    e += link_energy(m, c, 2, K, q0);
+                }
+                e += site_const - Real(0.5) * W0 * c[2] * c[2];
+                energy += (double)e;
+                const Real u0 = u[s], u1 = u[N + s], u2 = u[2 * N + s];
+                const Real r = rho[s];
+                const Real umag = sqrt(u0 * u0 + u1 * u1 + u2 * u2);
+                const Real nmag = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+                max_u = fmax(max_u, (double)umag);
+                min_nn = fmin(min_nn, (double)nmag);
+                max_nn = fmax(max_nn, (double)nmag);
+                if (!isfinite(umag) || !isfinite(nmag) || !isfinite(r) || !isfinite(fs)) bad += 1.0;
+                wcol += (double)(Real(0.5) * (Real(1) - c[2]));
+            }
         }
-        e += 0.5 * a.K * a.q0 * a.q0 - 0.5 * a.W0 * c[2] * c[2];
-        energy += e;
-        const double u0 = (double)u[s], u1 = (double)u[N + s], u2 = (double)u[2 * N + s];
-        const double r = (double)rho[s];
-        const double umag = sqrt(u0 * u0 + u1 * u1 + u2 * u2);
-        const double nmag = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
-        max_u = fmax(max_u, umag);
-        min_nn = fmin(min_nn, nmag);
-        max_nn = fmax(max_nn, nmag);
-        if (!isfinite(umag) || !isfinite(nmag) || !isfinite(r) || !isfinite(fs)) bad += 1.0;
         if (T > 0) {
-            int best = 0;
-            double bd = 1e300;
-            for (int k = 0; k < T; ++k) {
-                double dx = x - a.tubes[k][0], dy = y - a.tubes[k][1];
-                dx -= g.nx * floor(dx / g.nx + 0.5);
-                dy -= g.ny * floor(dy / g.ny + 0.5);
-                const double d2 = dx * dx + dy * dy;
-                if (d2 < bd) {
-                    bd = d2;
-                    best = k;
+            int owner = -1;
+            double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+            if (valid) {
+                double bd = 1e300;
+                for (int k = 0; k < T; ++k) {
+                    double dx = x - a.tubes[k][0], dy = y - a.tubes[k][1];
+                    dx -= g.nx * floor(dx / g.nx + 0.5);
+                    dy -= g.ny * floor(dy / g.ny + 0.5);
+                    const double d2 = dx * dx + dy * dy;
+                    if (d2 < bd) {
+                        bd = d2;
+                        owner = k;
+                    }
+                }
+                double sx, cx, sy, cy;
+                sincos(twopi * x / g.nx, &sx, &cx);
+                sincos(twopi * y / g.ny, &sy, &cy);
+                v[0] = wcol;
+                v[1] = wcol * sx;
+                v[2] = wcol * cx;
+                v[3] = wcol * sy;
+                v[4] = wcol * cy;
+            }
+            unsigned pending = __ballot_sync(0xffffffffu, owner >= 0);
+            while (pending) {
+                const int t = __shfl_sync(0xffffffffu, owner, __ffs(pending) - 1);
+                const bool mine = owner == t;
+                pending &= ~__ballot_sync(0xffffffffu, mine);
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    const double sum = warp_sum(mine ? v[k] : 0.0);
+                    if (lane == 0) atomicAdd(&tube_acc[t * 5 + k], sum);
                 }
             }
-            const double w = 0.5 * (1.0 - c[2]);
-            double sx, cx, sy, cy;
-            sincos(twopi * x / g.nx, &sx, &cx);
-            sincos(twopi * y / g.ny, &sy, &cy);
-            atomicAdd(&tube_acc[best * 5 + 0], w);
-            atomicAdd(&tube_acc[best * 5 + 1], w * sx);
-            atomicAdd(&tube_acc[best * 5 + 2], w * cx);
-            atomicAdd(&tube_acc[best * 5 + 3], w * sy);
-            atomicAdd(&tube_acc[best * 5 + 4], w * cy);
         }
     }
     mass = warp_sum(mass);
@@ -251,7 +285,6 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const DiagArgs a)
     max_u = warp_max(max_u);
     min_nn = warp_min(min_nn);
     max_nn = warp_max(max_nn);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) {
         red[wid][0] = mass;
         red[wid][1] = energy;
@@ -358,7 +391,9 @@ cudaError_t launch_scale_init(const float* rho, const float* u, const float* F, 
 
 cudaError_t launch_diagnostics(const DiagArgs& a, cudaStream_t st)
 {
-    const int blocks = a.blocks;
+    const int cols = a.g.nx * a.g.ny;
+    int blocks = (cols + DIAG_THREADS - 1) / DIAG_THREADS;
+    if (blocks > a.blocks) blocks = a.blocks;
     if (a.precision == NH_FP64) {
         diag_kernel<double, double><<<blocks, DIAG_THREADS, 0, st>>>(a);
     } else {
