@@ -188,6 +188,7 @@ def run_ours(args):
         ch.step(dt)
         ch.diagnostics_enqueue()
 
+    lb_variant = ch.autotune()
     for _ in range(args.warmup):
         block()
     ch.diagnostics_read()
@@ -250,6 +251,7 @@ def run_ours(args):
     total_kernel_ms = sum(v[1] for v in kt.values())
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": None, "kernel": "lb_kernel (fused collide+stream)", "peak_source": peak_src,
+                "lb_variant": lb_variant,
                 "bytes_per_launch": bytes_per_launch, "avg_launch_us": lb_avg_s * 1e6,
                 "share_of_kernel_time": lb_ms / total_kernel_ms if total_kernel_ms else None}
 

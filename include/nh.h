@@ -217,6 +217,17 @@ int nh_get_timing(nh_ctx* ctx, nh_timing* out);
 /* Kernel launches this context has issued (graph nodes counted per replay). */
 int64_t nh_launch_count(const nh_ctx* ctx);
 
+/* Select the launch shape of the fused LB kernel: 0 = two sites per thread,
+ * 256 threads (default; needs even nx), 1 = one site per thread, 256 threads,
+ * 2 = two sites, 128 threads, 3 = one site, 128 threads.  All variants compute
+ * the same arithmetic.  NH_EINVAL if the variant does not fit the domain. */
+int nh_set_lb_variant(nh_ctx* ctx, int variant);
+
+/* Autotuner: time every valid LB variant on the context's own domain (a few
+ * launches each, CUDA events on stream; the state is not advanced), keep the
+ * fastest and return its index in *chosen (may be NULL).  Synchronises. */
+int nh_autotune(nh_ctx* ctx, void* stream, int* chosen);
+
 /* Use CUDA graphs for whole dt_fd blocks (default on). */
 int nh_set_graphs(nh_ctx* ctx, int on);
 

@@ -31,7 +31,7 @@ size_t store_size(const nh_params& p)
 }
 
 struct Layout {
-    size_t f[2], F, n, nP, ndot, u, rho, sigma, staging, partials, result, scales, absmax, total;
+    size_t f[2], F, n, nP, ndot, u, rho, sigma, staging, partials, result, scales, absmax, trig, total;
 };
 
 Layout make_layout(const nh_params& p)
@@ -59,6 +59,7 @@ Layout make_layout(const nh_params& p)
     L.result = take((size_t)diag_num_values(NH_MAX_TUBES) * sizeof(double));
     L.scales = take(4 * sizeof(float));
     L.absmax = take(4 * sizeof(float));
+    L.trig = take(2 * ((size_t)p.nx + p.ny) * sizeof(double));
     L.total = off;
     return L;
 }
@@ -158,6 +159,7 @@ struct nh_ctx {
     int n_tubes = 0;
     double tubes[NH_MAX_TUBES][2] = {};
     bool use_graphs = true;
+    int lb_variant = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t graph_kernels[2] = {0, 0};
     bool timing = false;
@@ -298,19 +300,19 @@ int enqueue_lb(nh_ctx* c, int src, bool write_macro, cudaStream_t st)
     switch (c->p.storage) {
     case NH_STORE_F64: {
         auto a = lb_chan<double, double>(c, src);
-        return timed(c, NH_KCLASS_LB, st, [&] { return launch_lb(a, sh, write_macro, st); }, "lb");
+        return timed(c, NH_KCLASS_LB, st, [&] { return launch_lb(a, sh, write_macro, c->lb_variant, st); }, "lb");
     }
     case NH_STORE_F32: {
         auto a = lb_chan<float, float>(c, src);
-        return timed(c, NH_KCLASS_LB, st, [&] { return launch_lb(a, sh, write_macro, st); }, "lb");
+        return timed(c, NH_KCLASS_LB, st, [&] { return launch_lb(a, sh, write_macro, c->lb_variant, st); }, "lb");
     }
     case NH_STORE_F16S: {
         auto a = lb_chan<float, __half>(c, src);
-        return timed(c, NH_KCLASS_LB, st, [&] { return launch_lb(a, sh, write_macro, st); }, "lb");
+        return timed(c, NH_KCLASS_LB, st, [&] { return launch_lb(a, sh, write_macro, c->lb_variant, st); }, "lb");
     }
     default: {
         auto a = lb_chan<float, __nv_bfloat16>(c, src);
-        return timed(c, NH_KCLASS_LB, st, [&] { return launch_lb(a, sh, write_macro, st); }, "lb");
+        return timed(c, NH_KCLASS_LB, st, [&] { return launch_lb(a, sh, write_macro, c->lb_variant, st); }, "lb");
     }
     }
 }
@@ -487,6 +489,7 @@ int enqueue_diag(nh_ctx* c, cudaStream_t st)
     a.W0 = c->p.W0;
     a.n_tubes = c->n_tubes;
     memcpy(a.tubes, c->tubes, sizeof(a.tubes));
+    a.trig = c->at<const double>(c->L.trig);
     a.partials = c->at<double>(c->L.partials);
     a.result = c->at<double>(c->L.result);
     a.blocks = diag_blocks();
@@ -535,6 +538,7 @@ int nh_create(const nh_params* p, void* cuda_stream, nh_ctx** out)
     if (!c) return fail(nullptr, NH_ENOMEM, "host allocation of the context failed");
     c->p = *p;
     c->N = p->nx * p->ny * p->nz;
+    c->lb_variant = lb_variant_valid(0, p->nx) ? 0 : 1;
     c->L = make_layout(*p);
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = cudaGetDevice(&c->device);
@@ -558,6 +562,12 @@ int nh_bind_workspace(nh_ctx* c, void* dev_ptr, size_t bytes)
     drop_graphs(c);
     c->ws = static_cast<char*>(dev_ptr);
     c->ws_bytes = bytes;
+    {
+        int r = set_device(c);
+        if (r) return r;
+        NH_CUDA(c, launch_trig_table(c->at<double>(c->L.trig), c->p.nx, c->p.ny, c->stream));
+        c->launches += 1;
+    }
     c->bound = true;
     c->fields_set = false;
     c->cur = 0;
@@ -896,6 +906,57 @@ int nh_get_timing(nh_ctx* c, nh_timing* out)
 }
 
 int64_t nh_launch_count(const nh_ctx* c) { return c ? c->launches : 0; }
+
+int nh_set_lb_variant(nh_ctx* c, int variant)
+{
+    if (!c) return fail(nullptr, NH_EINVAL, "ctx is NULL");
+    if (!lb_variant_valid(variant, c->p.nx)) return fail(c, NH_EINVAL, "LB variant not valid for this domain");
+    if (variant != c->lb_variant) drop_graphs(c);
+    c->lb_variant = variant;
+    return NH_OK;
+}
+
+int nh_autotune(nh_ctx* c, void* stream, int* chosen)
+{
+    int r = check_ready(c);
+    if (r) return r;
+    if (!c->fields_set) return fail(c, NH_EINVAL, "nh_set_fields must be called before nh_autotune");
+    if ((r = set_device(c))) return r;
+    cudaStream_t st = pick(c, stream);
+    const bool saved_timing = c->timing;
+    const int saved_variant = c->lb_variant;
+    c->timing = false;
+    cudaEvent_t e0 = get_event(c), e1 = get_event(c);
+    float best_ms = 1e30f;
+    int best = saved_variant;
+    const int reps = 5;
+    // Each trial streams the current buffer into the other one without
+    // advancing the state (no macro write, no buffer swap).
+    for (int v = 0; v < kLBVariantCount && r == NH_OK; ++v) {
+        if (!lb_variant_valid(v, c->p.nx)) continue;
+        c->lb_variant = v;
+        r = enqueue_lb(c, c->cur, false, st);
+        if (r) break;
+        cudaEventRecord(e0, st);
+        for (int k = 0; k < reps && r == NH_OK; ++k) r = enqueue_lb(c, c->cur, false, st);
+        cudaEventRecord(e1, st);
+        if (r) break;
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) r = cuda_fail(c, e, "cudaEventSynchronize");
+        float ms = 0.f;
+        if (r == NH_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    c->free_events.push_back(e0);
+    c->free_events.push_back(e1);
+    c->timing = saved_timing;
+    c->lb_variant = best;
+    if (best != saved_variant) drop_graphs(c);
+    if (chosen) *chosen = best;
+    return r;
+}
 
 int nh_set_graphs(nh_ctx* c, int on)
 {

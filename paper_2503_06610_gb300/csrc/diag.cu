@@ -117,7 +117,7 @@ __global__ void scale_set_kernel(float* scales, unsigned* ctrl)
 
 // ------------------------------------------------------------------ diagnostics
 
-constexpr int DIAG_THREADS = 128;
+constexpr int DIAG_THREADS = 256;
 constexpr int DIAG_FIXED = 6;  // mass, energy, max_u, min_norm, max_norm, nonfinite
 
 template <typename T>
@@ -175,16 +175,22 @@ __device__ __forceinline__ Real link_energy(const Real n[3], const Real m[3], in
     return Real(0.5) * K * (d0 * d0 + d1 * d1 + d2 * d2) - K * q0 * cr;
 }
 
-// One thread per (x, y) column, looping over z.  Per-site terms are evaluated
-// in the build's precision (Real) and accumulated in FP64.  Tube sums use the
-// column weight sum_z (1 - n_z)/2, the column's nearest previous centroid, and
-// warp-aggregated shared-memory accumulation (one atomic per tube per warp).
+// Work item = (x, y) column x a chunk of kDiagChunk layers; one thread per item
+// (grid-stride).  Per-site terms are evaluated and summed over the chunk in the
+// build's precision (Real); each item's sums are then accumulated in FP64.
+// Tube sums use the item's weight sum_z (1 - n_z)/2, the column's nearest
+// previous centroid (FP64 periodic distance), FP64 sin/cos tables of the
+// column position, and warp-aggregated shared-memory accumulation.
+constexpr int kDiagChunk = 16;
+
 template <typename Real, typename Store>
 __global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const DiagArgs a)
 {
     const Geom g = a.g;
     const int N = g.N;
     const int cols = g.nx * g.ny;
+    const int chunks = (g.nz + kDiagChunk - 1) / kDiagChunk;
+    const int items = cols * chunks;
     const Store* f = static_cast<const Store*>(a.f);
     const Real* n = static_cast<const Real*>(a.n);
     const Real* u = static_cast<const Real*>(a.u);
@@ -199,22 +205,27 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const DiagArgs a)
     for (int k = threadIdx.x; k < T * 5; k += blockDim.x) tube_acc[k] = 0.0;
     __syncthreads();
 
-    double mass = 0.0, energy = 0.0, max_u = 0.0, min_nn = 1e300, max_nn = 0.0, bad = 0.0;
-    const double twopi = 6.283185307179586476925286766559;
-    for (int base = blockIdx.x * blockDim.x; base < cols; base += gridDim.x * blockDim.x) {
-        const int col = base + threadIdx.x;
-        const bool valid = col < cols;
-        double wcol = 0.0;
+    double mass = 0.0, energy = 0.0;
+    Real max_u = 0, min_nn = Real(1e30), max_nn = 0;
+    int bad = 0;
+    for (int base = blockIdx.x * blockDim.x; base < items; base += gridDim.x * blockDim.x) {
+        const int item = base + threadIdx.x;
+        const bool valid = item < items;
+        Real wsum = 0;
         int x = 0, y = 0;
         if (valid) {
+            const int col = item % cols;
+            const int z0 = (item / cols) * kDiagChunk;
+            const int z1 = min(z0 + kDiagChunk, g.nz);
             x = col % g.nx;
             y = col / g.nx;
-            for (int z = 0; z < g.nz; ++z) {
+            Real msum = 0, esum = 0;
+            for (int z = z0; z < z1; ++z) {
                 const int s = col + cols * z;
                 Real fs = 0;
 #pragma unroll
                 for (int i = 0; i < 19; ++i) fs += Codec<Store, Real>::load(f + (size_t)i * N + s, inv_scale);
-                mass += (double)fs;
+                msum += fs;
                 Real c[3], m[3];
                 c[0] = n[s];
                 c[1] = n[N + s];
@@ -229,18 +240,19 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const DiagArgs a)
                     dir_r(n, g, x, y, -1, m);
                     e += link_energy(m, c, 2, K, q0);
                 }
-                e += site_const - Real(0.5) * W0 * c[2] * c[2];
-                energy += (double)e;
+                esum += e + site_const - Real(0.5) * W0 * c[2] * c[2];
                 const Real u0 = u[s], u1 = u[N + s], u2 = u[2 * N + s];
                 const Real r = rho[s];
                 const Real umag = sqrt(u0 * u0 + u1 * u1 + u2 * u2);
                 const Real nmag = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
-                max_u = fmax(max_u, (double)umag);
-                min_nn = fmin(min_nn, (double)nmag);
-                max_nn = fmax(max_nn, (double)nmag);
-                if (!isfinite(umag) || !isfinite(nmag) || !isfinite(r) || !isfinite(fs)) bad += 1.0;
-                wcol += (double)(Real(0.5) * (Real(1) - c[2]));
+                max_u = max(max_u, umag);
+                min_nn = min(min_nn, nmag);
+                max_nn = max(max_nn, nmag);
+                if (!isfinite(umag) || !isfinite(nmag) || !isfinite(r) || !isfinite(fs)) bad += 1;
+                wsum += Real(0.5) * (Real(1) - c[2]);
             }
+            mass += (double)msum;
+            energy += (double)esum;
         }
         if (T > 0) {
             int owner = -1;
@@ -257,14 +269,12 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const DiagArgs a)
                         owner = k;
                     }
                 }
-                double sx, cx, sy, cy;
-                sincos(twopi * x / g.nx, &sx, &cx);
-                sincos(twopi * y / g.ny, &sy, &cy);
-                v[0] = wcol;
-                v[1] = wcol * sx;
-                v[2] = wcol * cx;
-                v[3] = wcol * sy;
-                v[4] = wcol * cy;
+                const double w = (double)wsum;
+                v[0] = w;
+                v[1] = w * a.trig[x];                    // sin(2 pi x / nx)
+                v[2] = w * a.trig[g.nx + x];             // cos(2 pi x / nx)
+                v[3] = w * a.trig[2 * g.nx + y];         // sin(2 pi y / ny)
+                v[4] = w * a.trig[2 * g.nx + g.ny + y];  // cos(2 pi y / ny)
             }
             unsigned pending = __ballot_sync(0xffffffffu, owner >= 0);
             while (pending) {
@@ -279,19 +289,20 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const DiagArgs a)
             }
         }
     }
+    double dmax_u = (double)max_u, dmin_nn = (double)min_nn, dmax_nn = (double)max_nn, dbad = (double)bad;
     mass = warp_sum(mass);
     energy = warp_sum(energy);
-    bad = warp_sum(bad);
-    max_u = warp_max(max_u);
-    min_nn = warp_min(min_nn);
-    max_nn = warp_max(max_nn);
+    dbad = warp_sum(dbad);
+    dmax_u = warp_max(dmax_u);
+    dmin_nn = warp_min(dmin_nn);
+    dmax_nn = warp_max(dmax_nn);
     if (lane == 0) {
         red[wid][0] = mass;
         red[wid][1] = energy;
-        red[wid][2] = max_u;
-        red[wid][3] = min_nn;
-        red[wid][4] = max_nn;
-        red[wid][5] = bad;
+        red[wid][2] = dmax_u;
+        red[wid][3] = dmin_nn;
+        red[wid][4] = dmax_nn;
+        red[wid][5] = dbad;
     }
     __syncthreads();
     const int V = DIAG_FIXED + 5 * T;
@@ -311,21 +322,42 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const DiagArgs a)
     for (int k = threadIdx.x; k < 5 * T; k += blockDim.x) out[DIAG_FIXED + k] = tube_acc[k];
 }
 
+// One warp per reduced value; lanes stride over the block partials and combine
+// with a fixed shuffle tree, so the result is deterministic.
 __global__ void diag_final_kernel(const double* __restrict__ partials, double* __restrict__ result, int blocks, int V)
 {
-    // one thread per value, blocks summed in a fixed order (deterministic)
-    for (int k = threadIdx.x; k < V; k += blockDim.x) {
-        double acc = (k == 3) ? 1e300 : 0.0;
-        for (int b = 0; b < blocks; ++b) {
+    const int lane = threadIdx.x & 31;
+    for (int k = threadIdx.x >> 5; k < V; k += blockDim.x >> 5) {
+        const int kind = (k == 2 || k == 4) ? 1 : (k == 3 ? 2 : 0);  // 0 sum, 1 max, 2 min
+        double acc = kind == 2 ? 1e300 : 0.0;
+        for (int b = lane; b < blocks; b += 32) {
             const double v = partials[(size_t)b * V + k];
-            if (k == 2 || k == 4)
-                acc = fmax(acc, v);
-            else if (k == 3)
-                acc = fmin(acc, v);
-            else
-                acc += v;
+            acc = kind == 0 ? acc + v : (kind == 1 ? fmax(acc, v) : fmin(acc, v));
         }
-        result[k] = acc;
+        for (int o = 16; o > 0; o >>= 1) {
+            const double w = __shfl_xor_sync(0xffffffffu, acc, o);
+            acc = kind == 0 ? acc + w : (kind == 1 ? fmax(acc, w) : fmin(acc, w));
+        }
+        if (lane == 0) result[k] = acc;
+    }
+}
+
+// sin / cos of 2 pi x / nx and 2 pi y / ny in FP64, laid out [sx | cx | sy | cy].
+__global__ void trig_table_kernel(double* t, int nx, int ny)
+{
+    const double twopi = 6.283185307179586476925286766559;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nx + ny; i += gridDim.x * blockDim.x) {
+        double sv, cv;
+        if (i < nx) {
+            sincos(twopi * i / nx, &sv, &cv);
+            t[i] = sv;
+            t[nx + i] = cv;
+        } else {
+            const int j = i - nx;
+            sincos(twopi * j / ny, &sv, &cv);
+            t[2 * nx + j] = sv;
+            t[2 * nx + ny + j] = cv;
+        }
     }
 }
 
@@ -389,10 +421,16 @@ cudaError_t launch_scale_init(const float* rho, const float* u, const float* F, 
     return cudaGetLastError();
 }
 
+cudaError_t launch_trig_table(double* t, int nx, int ny, cudaStream_t st)
+{
+    trig_table_kernel<<<(nx + ny + 255) / 256, 256, 0, st>>>(t, nx, ny);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_diagnostics(const DiagArgs& a, cudaStream_t st)
 {
-    const int cols = a.g.nx * a.g.ny;
-    int blocks = (cols + DIAG_THREADS - 1) / DIAG_THREADS;
+    const int items = a.g.nx * a.g.ny * ((a.g.nz + kDiagChunk - 1) / kDiagChunk);
+    int blocks = (items + DIAG_THREADS - 1) / DIAG_THREADS;
     if (blocks > a.blocks) blocks = a.blocks;
     if (a.precision == NH_FP64) {
         diag_kernel<double, double><<<blocks, DIAG_THREADS, 0, st>>>(a);
@@ -405,7 +443,7 @@ cudaError_t launch_diagnostics(const DiagArgs& a, cudaStream_t st)
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    diag_final_kernel<<<1, 256, 0, st>>>(a.partials, a.result, blocks, diag_num_values(a.n_tubes));
+    diag_final_kernel<<<1, 1024, 0, st>>>(a.partials, a.result, blocks, diag_num_values(a.n_tubes));
     return cudaGetLastError();
 }
 

@@ -1,7 +1,8 @@
 // lb.cu -- fused D3Q19 lattice-Boltzmann collide-and-stream sweep
 // (arXiv:2503.06610, Sec. II.C).
 //
-// One thread owns one site and performs, in registers:
+// One thread owns SPT consecutive sites of an x-row (SPT = 2 when nx is even)
+// and performs, in registers:
 //   1. streaming by pull: f_i(x) <- f*_i(x - e_i) of the previous step, or the
 //      half-way bounce-back f*_opp(i)(x) when x - e_i lies in a plate;
 //   2. moments, Eqs. shifted-rho / shifeted-u (or the plain ones):
@@ -9,13 +10,20 @@
 //   3. equilibrium (Eq. shifted-feq or Eq. feq-eq) and Guo source S_i^F;
 //   4. SRT relaxation (Eq. shifted-lbe): f*_i = f_i - (f_i - f^eq_i)/tau
 //      + (1 - 1/(2 tau)) S_i^F, written to the other population buffer.
-// Populations are structure-of-arrays planes [19][N] so every warp reads and
-// writes 19 runs of consecutive sites (x fastest): coalesced, with the +-1 x
-// shift of the pulled planes served from L1/L2.  u and rho are written only on
-// steps that feed an FD update (or end a call).
+// Populations are structure-of-arrays planes [19][N]: every warp reads and
+// writes 19 runs of consecutive sites, coalesced.  Planes with e_x = 0 are
+// read and all planes written as aligned 2-site vectors; the +-1 x shift of
+// the other planes is served from L1/L2.  The relaxation uses the symmetry of
+// each pair (e_i, -e_i): the parts of f^eq and S_i that are even in e_i are
+// computed once per pair and the odd parts change sign.  u and rho are written
+// only on steps that feed an FD update (or end a call).
+#include <type_traits>
+
 #include "nh_internal.cuh"
 
 namespace nh {
+
+constexpr int kLBThreads = 256;
 
 // Power-of-two scale that puts m near 2^kScaleHeadroomLog2 (exact in float).
 __device__ __forceinline__ float scale_for(float m, float fallback)
@@ -28,89 +36,193 @@ __device__ __forceinline__ float scale_for(float m, float fallback)
     return ldexpf(1.f, k);
 }
 
-template <typename Real, typename Store, bool Shifted, bool WriteMacro>
-__global__ void __launch_bounds__(256) lb_kernel(const LBChan<Real, Store> c)
+template <typename Store>
+struct Vec2;
+template <>
+struct Vec2<double> {
+    using T = double2;
+};
+template <>
+struct Vec2<float> {
+    using T = float2;
+};
+template <>
+struct Vec2<__half> {
+    using T = __half2;
+};
+template <>
+struct Vec2<__nv_bfloat16> {
+    using T = __nv_bfloat162;
+};
+
+template <typename Store, typename Real>
+__device__ __forceinline__ void load2(const Store* p, float inv, Real& a, Real& b)
+{
+    const typename Vec2<Store>::T v = *reinterpret_cast<const typename Vec2<Store>::T*>(p);
+    if constexpr (std::is_same<Store, __half>::value) {
+        const float2 fv = __half22float2(v);
+        a = fv.x * inv;
+        b = fv.y * inv;
+    } else if constexpr (std::is_same<Store, __nv_bfloat16>::value) {
+        const float2 fv = __bfloat1622float2(v);
+        a = fv.x * inv;
+        b = fv.y * inv;
+    } else {
+        a = v.x;
+        b = v.y;
+    }
+}
+
+template <typename Store, typename Real>
+__device__ __forceinline__ void store2(Store* p, Real a, Real b, float scale)
+{
+    typename Vec2<Store>::T v;
+    if constexpr (std::is_same<Store, __half>::value) {
+        v = __floats2half2_rn(a * scale, b * scale);
+    } else if constexpr (std::is_same<Store, __nv_bfloat16>::value) {
+        v = __floats2bfloat162_rn(a * scale, b * scale);
+    } else {
+        v.x = a;
+        v.y = b;
+    }
+    *reinterpret_cast<typename Vec2<Store>::T*>(p) = v;
+}
+
+template <typename Real, typename Store, bool Shifted, bool WriteMacro, int SPT>
+__global__ void __launch_bounds__(kLBThreads) lb_kernel(const LBChan<Real, Store> c)
 {
     NH_D3Q19_TABLES
     constexpr bool kScaled = sizeof(Store) == 2;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int N = c.g.N;
+    const int s0 = (blockIdx.x * blockDim.x + threadIdx.x) * SPT;
     float amax = 0.f;
     float scale_out = 1.f;
     if (kScaled) scale_out = c.scales[2];
-    if (s < N) {
+    if (s0 < N) {
         const int nx = c.g.nx, ny = c.g.ny, nz = c.g.nz;
-        const int x = s % nx;
-        const int t = s / nx;
-        const int y = t % ny;
-        const int z = t / ny;
+        const int x0 = s0 % nx;
+        const int r = s0 / nx;
+        const int y = r % ny;
+        const int z = r / ny;
         const float inv_in = kScaled ? 1.f / c.scales[c.src] : 1.f;
+        const int plane_xy = nx * ny;
+
+        // site deltas of the pull sources x - e (periodic in x and y; in z
+        // periodic or replaced by bounce-back at the plates)
+        int dxm[SPT], dxp[SPT];  // source x-1 (e_x = +1), x+1 (e_x = -1)
+#pragma unroll
+        for (int j = 0; j < SPT; ++j) {
+            const int x = x0 + j;
+            dxm[j] = x == 0 ? nx - 1 : -1;
+            dxp[j] = x == nx - 1 ? -(nx - 1) : 1;
+        }
+        const int dym = (y == 0 ? ny - 1 : -1) * nx;
+        const int dyp = (y == ny - 1 ? -(ny - 1) : 1) * nx;
+        const int dzm = (z == 0 ? nz - 1 : -1) * plane_xy;
+        const int dzp = (z == nz - 1 ? -(nz - 1) : 1) * plane_xy;
+        const bool bb_lo = c.g.walls && z == 0;
+        const bool bb_hi = c.g.walls && z == nz - 1;
 
         // 1. pull streaming with half-way bounce-back
-        Real f[19];
+        Real f[SPT][19];
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
-            const int zs = z - EZ[i];
-            size_t off;
-            if (EZ[i] != 0 && c.g.walls && (zs < 0 || zs >= nz)) {
-                off = (size_t)OPP[i] * N + s;
+            const bool bb = (EZ[i] > 0 && bb_lo) || (EZ[i] < 0 && bb_hi);
+            const int row = (EY[i] > 0 ? dym : (EY[i] < 0 ? dyp : 0)) + (EZ[i] > 0 ? dzm : (EZ[i] < 0 ? dzp : 0));
+            const Store* plane = c.fsrc + (size_t)(bb ? OPP[i] : i) * N;
+            if (SPT == 2 && EX[i] == 0) {
+                load2(plane + (bb ? s0 : s0 + row), inv_in, f[0][i], f[SPT - 1][i]);
             } else {
-                const int xs = wrap_p(x - EX[i], nx);
-                const int ys = wrap_p(y - EY[i], ny);
-                const int zz = wrap_p(zs, nz);
-                off = (size_t)i * N + (xs + nx * (ys + ny * zz));
+#pragma unroll
+                for (int j = 0; j < SPT; ++j) {
+                    const int dx = EX[i] > 0 ? dxm[j] : (EX[i] < 0 ? dxp[j] : 0);
+                    f[j][i] = Codec<Store, Real>::load(plane + (bb ? s0 + j : s0 + j + row + dx), inv_in);
+                }
             }
-            f[i] = Codec<Store, Real>::load(c.fsrc + off, inv_in);
         }
 
-        // 2. moments
-        Real sum = 0, mx = 0, my = 0, mz = 0;
+        Real fo[SPT][19];
 #pragma unroll
-        for (int i = 0; i < 19; ++i) {
-            sum += f[i];
-            if (EX[i] != 0) mx += EX[i] > 0 ? f[i] : -f[i];
-            if (EY[i] != 0) my += EY[i] > 0 ? f[i] : -f[i];
-            if (EZ[i] != 0) mz += EZ[i] > 0 ? f[i] : -f[i];
-        }
-        const Real rho = Shifted ? Real(1) + sum : sum;
-        const Real drho = Shifted ? sum : sum - Real(1);
-        const Real Fx = c.F[s] + rho * c.gx;
-        const Real Fy = c.F[N + s] + rho * c.gy;
-        const Real Fz = c.F[2 * N + s] + rho * c.gz;
-        const Real inv_rho = Real(1) / rho;
-        const Real ux = (mx + Real(0.5) * Fx) * inv_rho;
-        const Real uy = (my + Real(0.5) * Fy) * inv_rho;
-        const Real uz = (mz + Real(0.5) * Fz) * inv_rho;
-        if (WriteMacro) {
-            c.u[s] = ux;
-            c.u[N + s] = uy;
-            c.u[2 * N + s] = uz;
-            c.rho[s] = rho;
+        for (int j = 0; j < SPT; ++j) {
+            const int s = s0 + j;
+            // 2. moments: pair sums and differences of (e_i, -e_i)
+            Real sum = f[j][0], mx = 0, my = 0, mz = 0;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const int i = 2 * k + 1;
+                sum += f[j][i] + f[j][i + 1];
+                const Real d = f[j][i] - f[j][i + 1];
+                if (EX[i] != 0) mx += EX[i] > 0 ? d : -d;
+                if (EY[i] != 0) my += EY[i] > 0 ? d : -d;
+                if (EZ[i] != 0) mz += EZ[i] > 0 ? d : -d;
+            }
+            const Real rho = Shifted ? Real(1) + sum : sum;
+            const Real drho = Shifted ? sum : sum - Real(1);
+            const Real Fx = c.F[s] + rho * c.gx;
+            const Real Fy = c.F[N + s] + rho * c.gy;
+            const Real Fz = c.F[2 * N + s] + rho * c.gz;
+            const Real inv_rho = Real(1) / rho;
+            const Real ux = (mx + Real(0.5) * Fx) * inv_rho;
+            const Real uy = (my + Real(0.5) * Fy) * inv_rho;
+            const Real uz = (mz + Real(0.5) * Fz) * inv_rho;
+            if (WriteMacro) {
+                c.u[s] = ux;
+                c.u[N + s] = uy;
+                c.u[2 * N + s] = uz;
+                c.rho[s] = rho;
+            }
+
+            // 3-4. equilibrium, Guo source and relaxation, per (e_i, -e_i) pair:
+            //   f^eq = w rho [3 eu + 4.5 eu^2 - 1.5 u.u] + w (rho - 1 | rho)
+            //   S    = w [3 eF + 9 eu eF - 3 u.F]
+            //   f*   = (1 - omega) f + omega f^eq + (1 - omega/2) S
+            const Real omega = c.omega;
+            const Real omc = Real(1) - omega;
+            const Real cS = Real(1) - Real(0.5) * omega;
+            const Real uu15 = Real(1.5) * (ux * ux + uy * uy + uz * uz);
+            const Real uF3 = Real(3) * (ux * Fx + uy * Fy + uz * Fz);
+            const Real base = Shifted ? drho : rho;
+            // rest population (w = 1/3)
+            {
+                const Real w = Real(1) / Real(3);
+                fo[j][0] = omc * f[j][0] + omega * w * (base - rho * uu15) - cS * w * uF3;
+            }
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const int i = 2 * k + 1;
+                const Real w = i < 7 ? Real(1) / Real(18) : Real(1) / Real(36);
+                const Real A = omega * w * rho;
+                const Real B = omega * w * base;
+                const Real C = cS * w;
+                const Real eu = Real(EX[i]) * ux + Real(EY[i]) * uy + Real(EZ[i]) * uz;
+                const Real eF = Real(EX[i]) * Fx + Real(EY[i]) * Fy + Real(EZ[i]) * Fz;
+                const Real even = A * (Real(4.5) * eu * eu - uu15) + B + C * (Real(9) * eu * eF - uF3);
+                const Real odd = Real(3) * (A * eu + C * eF);
+                fo[j][i] = omc * f[j][i] + even + odd;
+                fo[j][i + 1] = omc * f[j][i + 1] + even - odd;
+            }
+            if (kScaled) {
+#pragma unroll
+                for (int i = 0; i < 19; ++i) amax = fmaxf(amax, fabsf((float)fo[j][i]));
+            }
         }
 
-        // 3-4. equilibrium, Guo source, relaxation
-        const Real omega = c.omega;
-        const Real cS = Real(1) - Real(0.5) * omega;
-        const Real uu = ux * ux + uy * uy + uz * uz;
-        const Real uF = ux * Fx + uy * Fy + uz * Fz;
+        // store (aligned 2-site vectors when SPT = 2)
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
-            const Real w = d3q19_w<Real>(i);
-            const Real eu = Real(EX[i]) * ux + Real(EY[i]) * uy + Real(EZ[i]) * uz;
-            const Real eF = Real(EX[i]) * Fx + Real(EY[i]) * Fy + Real(EZ[i]) * Fz;
-            Real feq = w * rho * (Real(3) * eu + Real(4.5) * eu * eu - Real(1.5) * uu);
-            feq += Shifted ? w * drho : w * rho;
-            const Real S = w * (Real(3) * eF + Real(9) * eu * eF - Real(3) * uF);
-            const Real fo = f[i] + omega * (feq - f[i]) + cS * S;
-            if (kScaled) amax = fmaxf(amax, fabsf((float)fo));
-            Codec<Store, Real>::store(c.fdst + (size_t)i * N + s, fo, scale_out);
+            Store* dst = c.fdst + (size_t)i * N + s0;
+            if (SPT == 2) {
+                store2(dst, fo[0][i], fo[SPT - 1][i], scale_out);
+            } else {
+                Codec<Store, Real>::store(dst, fo[0][i], scale_out);
+            }
         }
     }
     if (kScaled) {
         // In-kernel scale controller: block max -> global running max; the last
         // block to finish records the scale of the buffer just written and sets
         // the target of the next step from this step's max |f*|.
-        __shared__ float wmax[8];
+        __shared__ float wmax[kLBThreads / 32];
         __shared__ bool last;
         for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
         if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = amax;
@@ -118,7 +230,8 @@ __global__ void __launch_bounds__(256) lb_kernel(const LBChan<Real, Store> c)
         if (threadIdx.x == 0) {
             float b = 0.f;
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = fmaxf(b, wmax[w]);
-            if (b > __int_as_float((int)__ldcg(&c.ctrl[0]))) atomicMax(reinterpret_cast<int*>(&c.ctrl[0]), __float_as_int(b));
+            if (b > __int_as_float((int)__ldcg(&c.ctrl[0])))
+                atomicMax(reinterpret_cast<int*>(&c.ctrl[0]), __float_as_int(b));
             __threadfence();
             const unsigned ticket = atomicAdd(&c.ctrl[1], 1u);
             last = ticket == gridDim.x - 1;
@@ -134,28 +247,47 @@ __global__ void __launch_bounds__(256) lb_kernel(const LBChan<Real, Store> c)
     }
 }
 
-template <typename Real, typename Store>
-cudaError_t launch_lb(const LBChan<Real, Store>& c, bool shifted, bool write_macro, cudaStream_t st)
+// Launch variants: sites per thread x threads per block.
+struct LBVariantShape {
+    int spt, threads;
+};
+constexpr LBVariantShape kLBVariants[kLBVariantCount] = {{2, 256}, {1, 256}, {2, 128}, {1, 128}};
+
+bool lb_variant_valid(int variant, int nx)
 {
-    const int threads = 256;
-    const int blocks = (c.g.N + threads - 1) / threads;
-    if (shifted) {
-        if (write_macro)
-            lb_kernel<Real, Store, true, true><<<blocks, threads, 0, st>>>(c);
-        else
-            lb_kernel<Real, Store, true, false><<<blocks, threads, 0, st>>>(c);
-    } else {
-        if (write_macro)
-            lb_kernel<Real, Store, false, true><<<blocks, threads, 0, st>>>(c);
-        else
-            lb_kernel<Real, Store, false, false><<<blocks, threads, 0, st>>>(c);
-    }
+    if (variant < 0 || variant >= kLBVariantCount) return false;
+    return kLBVariants[variant].spt == 1 || nx % 2 == 0;
+}
+
+template <typename Real, typename Store, bool Shifted, bool WriteMacro>
+cudaError_t launch_lb_spt(const LBChan<Real, Store>& c, int variant, cudaStream_t st)
+{
+    const LBVariantShape v = kLBVariants[variant];
+    const int threads_needed = (c.g.N + v.spt - 1) / v.spt;
+    const int blocks = (threads_needed + v.threads - 1) / v.threads;
+    if (v.spt == 2)
+        lb_kernel<Real, Store, Shifted, WriteMacro, 2><<<blocks, v.threads, 0, st>>>(c);
+    else
+        lb_kernel<Real, Store, Shifted, WriteMacro, 1><<<blocks, v.threads, 0, st>>>(c);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_lb<double, double>(const LBChan<double, double>&, bool, bool, cudaStream_t);
-template cudaError_t launch_lb<float, float>(const LBChan<float, float>&, bool, bool, cudaStream_t);
-template cudaError_t launch_lb<float, __half>(const LBChan<float, __half>&, bool, bool, cudaStream_t);
-template cudaError_t launch_lb<float, __nv_bfloat16>(const LBChan<float, __nv_bfloat16>&, bool, bool, cudaStream_t);
+template <typename Real, typename Store>
+cudaError_t launch_lb(const LBChan<Real, Store>& c, bool shifted, bool write_macro, int variant, cudaStream_t st)
+{
+    if (!lb_variant_valid(variant, c.g.nx)) return cudaErrorInvalidValue;
+    if (shifted) {
+        if (write_macro) return launch_lb_spt<Real, Store, true, true>(c, variant, st);
+        return launch_lb_spt<Real, Store, true, false>(c, variant, st);
+    }
+    if (write_macro) return launch_lb_spt<Real, Store, false, true>(c, variant, st);
+    return launch_lb_spt<Real, Store, false, false>(c, variant, st);
+}
+
+template cudaError_t launch_lb<double, double>(const LBChan<double, double>&, bool, bool, int, cudaStream_t);
+template cudaError_t launch_lb<float, float>(const LBChan<float, float>&, bool, bool, int, cudaStream_t);
+template cudaError_t launch_lb<float, __half>(const LBChan<float, __half>&, bool, bool, int, cudaStream_t);
+template cudaError_t launch_lb<float, __nv_bfloat16>(const LBChan<float, __nv_bfloat16>&, bool, bool, int,
+                                                     cudaStream_t);
 
 }  // namespace nh

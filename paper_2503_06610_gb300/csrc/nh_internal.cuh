@@ -120,8 +120,11 @@ struct FDChan {
 };
 
 // ------------------------------------------------------------------ launchers (host)
+// LB launch variants (sites per thread x block size); variant 0 is the default.
+constexpr int kLBVariantCount = 4;
+bool lb_variant_valid(int variant, int nx);
 template <typename Real, typename Store>
-cudaError_t launch_lb(const LBChan<Real, Store>& c, bool shifted, bool write_macro, cudaStream_t s);
+cudaError_t launch_lb(const LBChan<Real, Store>& c, bool shifted, bool write_macro, int variant, cudaStream_t s);
 
 template <typename Real>
 cudaError_t launch_fd_predict(const FDChan<Real>& c, cudaStream_t s);
@@ -163,6 +166,7 @@ struct DiagArgs {
     double K, q0, W0;
     int n_tubes;
     double tubes[NH_MAX_TUBES][2];
+    const double* trig; // [sin x | cos x | sin y | cos y] of 2 pi x/nx, 2 pi y/ny
     double* partials;   // [blocks][NDIAG]
     double* result;     // [NDIAG]
     int blocks;
@@ -170,5 +174,6 @@ struct DiagArgs {
 int diag_num_values(int n_tubes);
 int diag_blocks();
 cudaError_t launch_diagnostics(const DiagArgs& a, cudaStream_t s);
+cudaError_t launch_trig_table(double* t, int nx, int ny, cudaStream_t s);
 
 }  // namespace nh

@@ -98,6 +98,8 @@ SIGNATURES = {
     "nh_get_timing": ([_VP, ctypes.POINTER(nh_timing)], ctypes.c_int),
     "nh_launch_count": ([_VP], ctypes.c_int64),
     "nh_set_graphs": ([_VP, ctypes.c_int], ctypes.c_int),
+    "nh_set_lb_variant": ([_VP, ctypes.c_int], ctypes.c_int),
+    "nh_autotune": ([_VP, _VP, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "nh_destroy": ([_VP], None),
 }
 
@@ -278,6 +280,16 @@ def nh_set_graphs(ctx, on: bool):
     _check(load_library().nh_set_graphs(ctx, 1 if on else 0), ctx)
 
 
+def nh_set_lb_variant(ctx, variant: int):
+    _check(load_library().nh_set_lb_variant(ctx, int(variant)), ctx)
+
+
+def nh_autotune(ctx, stream=None) -> int:
+    out = ctypes.c_int(-1)
+    _check(load_library().nh_autotune(ctx, _VP(stream or 0), ctypes.byref(out)), ctx)
+    return int(out.value)
+
+
 def nh_destroy(ctx):
     if ctx:
         load_library().nh_destroy(ctx)
@@ -366,6 +378,12 @@ class Channel:
 
     def set_graphs(self, on=True):
         nh_set_graphs(self.ctx, on)
+
+    def set_lb_variant(self, variant):
+        nh_set_lb_variant(self.ctx, variant)
+
+    def autotune(self):
+        return nh_autotune(self.ctx, self.stream.cuda_stream)
 
     def launch_count(self):
         return nh_launch_count(self.ctx)

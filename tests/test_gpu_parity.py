@@ -306,3 +306,34 @@ def test_full_size_multi_tube_fd_update(nh, oracle_mod):
     p = O.OracleParams.from_dict(params)
     nref = O.fd_step(p, n0, u0)
     assert O.rel_l2(n, nref) < 1e-6
+
+
+@pytest.mark.parametrize("nx", [16, 13])
+def test_lb_variants_agree_and_autotune_keeps_state(nh, oracle_mod, nx):
+    """Every LB launch shape gives the oracle's result; the autotuner picks a
+    valid shape without advancing the state."""
+    O = oracle_mod
+    params = _generic(nx, 6, 5, dt_fd=2)
+    n0 = I.tilted_director(nx, 6, 5, amplitude=0.3, seed=4)
+    ref = _oracle_sim(O, params, n0).step(9)
+    variants = [0, 1, 2, 3] if nx % 2 == 0 else [1, 3]
+    for v in variants:
+        ch = _channel(nh, params, n0, precision="fp64")
+        ch.set_lb_variant(v)
+        ch.step(9)
+        n, u, _ = ch.get_fields()
+        assert O.rel_l2(u, ref.u) <= 1e-12, v
+        assert O.rel_l2(n, ref.n) <= 1e-12, v
+    if nx % 2:
+        ch = nh.Channel(dict(params, precision="fp64"))
+        with pytest.raises(nh.NHError):
+            ch.set_lb_variant(0)
+    ch = _channel(nh, params, n0, precision="fp64")
+    ch.step(4)
+    before = ch.get_populations()
+    chosen = ch.autotune()
+    assert chosen in variants
+    assert np.array_equal(before, ch.get_populations())
+    ch.step(5)
+    n, u, _ = ch.get_fields()
+    assert O.rel_l2(u, ref.u) <= 1e-12
