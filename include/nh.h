@@ -210,7 +210,12 @@ int nh_diagnostics(nh_ctx* ctx, nh_diag* out);
 int nh_diagnostics_enqueue(nh_ctx* ctx, void* stream);
 int nh_diagnostics_read(nh_ctx* ctx, nh_diag* out);
 
-/* Per-kernel timing with CUDA events (1 = on, forces direct launches). */
+/* Per-kernel timing with CUDA events on the launching stream: 0 = off,
+ * 1 = every kernel class, 2 = the LB class only.  Timing forces direct
+ * launches (no graphs); consecutive launches of one class form one segment
+ * bracketed by one pair of events, so nh_get_timing reports per class the
+ * number of launches and their total time (gaps between back-to-back
+ * launches of the class included).  nh_get_timing synchronises and resets. */
 int nh_set_timing(nh_ctx* ctx, int on);
 int nh_get_timing(nh_ctx* ctx, nh_timing* out);
 

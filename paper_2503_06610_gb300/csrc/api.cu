@@ -135,9 +135,18 @@ int validate(const nh_params* p, std::string& err)
     return NH_OK;
 }
 
+}  // namespace
+
+void nh::set_global_error(const char* msg) { g_global_err = msg ? msg : ""; }
+
+namespace {
+
+// A run of consecutive launches of one kernel class on one stream, bracketed
+// by one pair of CUDA events.
 struct TimedLaunch {
     int kclass;
     cudaEvent_t a, b;
+    int count;
 };
 
 }  // namespace
@@ -162,8 +171,11 @@ struct nh_ctx {
     int lb_variant = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t graph_kernels[2] = {0, 0};
-    bool timing = false;
+    int timing = 0;  // 0 off, 1 every kernel class, 2 the LB class only
     std::vector<TimedLaunch> pending;
+    bool seg_open = false;
+    TimedLaunch seg{};
+    cudaStream_t seg_stream = nullptr;
     std::vector<cudaEvent_t> free_events;
     nh_timing tstats{};
     int64_t launches = 0;
@@ -274,22 +286,32 @@ FDChan<Real> fd_chan(nh_ctx* c)
     return a;
 }
 
-// Enqueue one kernel class with optional event timing.
+// Close the open timing segment (records its end event).
+void close_segment(nh_ctx* c)
+{
+    if (!c->seg_open) return;
+    cudaEventRecord(c->seg.b, c->seg_stream);
+    c->pending.push_back(c->seg);
+    c->seg_open = false;
+}
+
+// Enqueue one kernel launch of class kclass.  With timing on, consecutive
+// launches of the same class on the same stream form one segment bracketed by
+// a single pair of events (the per-launch time is segment time / count).
 template <typename F>
 int timed(nh_ctx* c, int kclass, cudaStream_t st, F&& launch, const char* what)
 {
-    TimedLaunch t{kclass, nullptr, nullptr};
-    if (c->timing) {
-        t.a = get_event(c);
-        t.b = get_event(c);
-        cudaEventRecord(t.a, st);
+    const bool timed_class = c->timing == 1 || (c->timing == 2 && kclass == NH_KCLASS_LB);
+    if (c->seg_open && (!timed_class || c->seg.kclass != kclass || c->seg_stream != st)) close_segment(c);
+    if (timed_class && !c->seg_open) {
+        c->seg = TimedLaunch{kclass, get_event(c), get_event(c), 0};
+        c->seg_stream = st;
+        cudaEventRecord(c->seg.a, st);
+        c->seg_open = true;
     }
     cudaError_t e = launch();
     if (e != cudaSuccess) return cuda_fail(c, e, what);
-    if (c->timing) {
-        cudaEventRecord(t.b, st);
-        c->pending.push_back(t);
-    }
+    if (timed_class) c->seg.count += 1;
     c->launches += 1;
     return NH_OK;
 }
@@ -474,6 +496,7 @@ int encode_all(nh_ctx* c, const double* f, int on_device, cudaStream_t st)
 
 int enqueue_diag(nh_ctx* c, cudaStream_t st)
 {
+    close_segment(c);
     DiagArgs a;
     a.f = c->ws + c->L.f[c->cur];
     a.storage = c->p.storage;
@@ -778,6 +801,7 @@ int nh_step(nh_ctx* c, int64_t n_lb_steps, void* stream)
             left -= 1;
         }
     }
+    close_segment(c);
     return NH_OK;
 }
 
@@ -787,7 +811,9 @@ int nh_fd_update(nh_ctx* c, void* stream)
     if (r) return r;
     if (!c->fields_set) return fail(c, NH_EINVAL, "nh_set_fields must be called before nh_fd_update");
     if ((r = set_device(c))) return r;
-    return enqueue_fd_any(c, pick(c, stream));
+    r = enqueue_fd_any(c, pick(c, stream));
+    close_segment(c);
+    return r;
 }
 
 int nh_batch_step(nh_ctx* const* ctxs, int count, int64_t n_lb_steps, void* stream)
@@ -879,13 +905,16 @@ int nh_diagnostics(nh_ctx* c, nh_diag* out)
 int nh_set_timing(nh_ctx* c, int on)
 {
     if (!c) return fail(nullptr, NH_EINVAL, "ctx is NULL");
-    c->timing = on != 0;
+    if (on < 0 || on > 2) return fail(c, NH_EINVAL, "timing mode must be 0, 1 or 2");
+    close_segment(c);
+    c->timing = on;
     return NH_OK;
 }
 
 int nh_get_timing(nh_ctx* c, nh_timing* out)
 {
     if (!c || !out) return fail(c, NH_EINVAL, "NULL argument");
+    close_segment(c);
     if (!c->pending.empty()) {
         for (auto& t : c->pending) {
             cudaError_t e = cudaEventSynchronize(t.b);
@@ -893,7 +922,7 @@ int nh_get_timing(nh_ctx* c, nh_timing* out)
             float ms = 0.f;
             e = cudaEventElapsedTime(&ms, t.a, t.b);
             if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventElapsedTime");
-            c->tstats.launches[t.kclass] += 1;
+            c->tstats.launches[t.kclass] += t.count;
             c->tstats.ms[t.kclass] += ms;
             c->free_events.push_back(t.a);
             c->free_events.push_back(t.b);
@@ -923,9 +952,10 @@ int nh_autotune(nh_ctx* c, void* stream, int* chosen)
     if (!c->fields_set) return fail(c, NH_EINVAL, "nh_set_fields must be called before nh_autotune");
     if ((r = set_device(c))) return r;
     cudaStream_t st = pick(c, stream);
-    const bool saved_timing = c->timing;
+    close_segment(c);
+    const int saved_timing = c->timing;
     const int saved_variant = c->lb_variant;
-    c->timing = false;
+    c->timing = 0;
     cudaEvent_t e0 = get_event(c), e1 = get_event(c);
     float best_ms = 1e30f;
     int best = saved_variant;
@@ -971,6 +1001,7 @@ void nh_destroy(nh_ctx* c)
     if (set_device(c) == NH_OK) {
         if (c->stream) cudaStreamSynchronize(c->stream);
         drop_graphs(c);
+        close_segment(c);
         for (auto& t : c->pending) {
             cudaEventDestroy(t.a);
             cudaEventDestroy(t.b);

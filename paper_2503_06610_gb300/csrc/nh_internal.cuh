@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/nh.h"
 
 namespace nh {
@@ -175,5 +177,9 @@ int diag_num_values(int n_tubes);
 int diag_blocks();
 cudaError_t launch_diagnostics(const DiagArgs& a, cudaStream_t s);
 cudaError_t launch_trig_table(double* t, int nx, int ny, cudaStream_t s);
+
+// Record the text returned by nh_last_error(NULL) on this thread (api.cu).
+void set_global_error(const char* msg);
+inline void set_global_error(const std::string& msg) { set_global_error(msg.c_str()); }
 
 }  // namespace nh

@@ -262,8 +262,9 @@ def _diag_dict(ctx, d, code, allow_unstable):
                 tube_weight=np.array([d.tube_weight[k] for k in range(T)]), code=code)
 
 
-def nh_set_timing(ctx, on: bool):
-    _check(load_library().nh_set_timing(ctx, 1 if on else 0), ctx)
+def nh_set_timing(ctx, mode):
+    """0 = off, 1 (or True) = every kernel class, 2 = the LB class only."""
+    _check(load_library().nh_set_timing(ctx, int(mode)), ctx)
 
 
 def nh_get_timing(ctx) -> dict:
@@ -370,8 +371,8 @@ class Channel:
     def diagnostics_read(self, allow_unstable=False):
         return nh_diagnostics_read(self.ctx, allow_unstable)
 
-    def set_timing(self, on=True):
-        nh_set_timing(self.ctx, on)
+    def set_timing(self, mode=1):
+        nh_set_timing(self.ctx, mode)
 
     def timing(self):
         return nh_get_timing(self.ctx)

@@ -63,7 +63,12 @@ def test_lb_rows_fp64(nh, oracle_mod, shifted, walls):
     n, u, rho = ch.get_fields()
     f = ch.get_populations()
     assert O.rel_l2(u, ref.u) < 1e-12
-    assert O.rel_l2(rho - 1, ref.rho - 1) < 1e-10
+    if shifted:
+        assert O.rel_l2(rho - 1, ref.rho - 1) < 1e-10
+    else:
+        # the plain store forms rho - 1 ~ 1e-5 as sum f - 1 with f ~ w_i: its
+        # rounding is absolute (~1e-16 per addition), which is what the shift cures
+        assert np.max(np.abs(rho - ref.rho)) < 1e-14
     assert np.max(np.abs(f - ref.f)) < 1e-13
 
 
@@ -337,3 +342,21 @@ def test_lb_variants_agree_and_autotune_keeps_state(nh, oracle_mod, nx):
     ch.step(5)
     n, u, _ = ch.get_fields()
     assert O.rel_l2(u, ref.u) <= 1e-12
+
+
+def test_timing_segments_count_every_launch(nh):
+    params = _generic(16, 12, 8, dt_fd=4)
+    n0 = I.tilted_director(16, 12, 8, amplitude=0.2, seed=2)
+    ch = _channel(nh, params, n0, precision="fp32")
+    ch.set_timing(1)
+    ch.step(10)
+    t = ch.timing()
+    assert t["lb"][0] == 10 and t["fd_predict"][0] == 2 and t["force"][0] == 2
+    assert all(v[1] > 0 for v in t.values())
+    ch.set_timing(2)
+    ch.step(8)
+    t = ch.timing()
+    assert t["lb"][0] == 8 and t["fd_predict"][0] == 0
+    ch.set_timing(0)
+    ch.step(4)
+    assert ch.timing()["lb"][0] == 0
