@@ -236,6 +236,39 @@ int nh_autotune(nh_ctx* ctx, void* stream, int* chosen);
 /* Use CUDA graphs for whole dt_fd blocks (default on). */
 int nh_set_graphs(nh_ctx* ctx, int on);
 
+/* Diagnostics for callers that cannot allocate device memory.
+ *
+ * nh_diagnostics needs a context, whose workspace the caller allocated in
+ * advance.  Callers that have no such workspace and may not allocate one when
+ * they need the numbers (a host application that hands over only its own
+ * input and output buffers and forbids further device allocations, or a
+ * time-critical loop that cannot afford cudaMalloc's implicit device
+ * synchronisation) call this instead.  The paper has no counterpart: it is a
+ * library convenience.
+ *
+ * Inputs are device pointers on the current device laid out as everywhere in
+ * this header: populations f [19][N] (double for FP64/F64, float for FP32/F32;
+ * the 16-bit stores are not accepted), director n [3][N], velocity u [3][N]
+ * and density rho [N], in the precision of *p.  Output: out[6] on the device,
+ *   out[0] = sum of the stored populations (the mass is out[0] + N when
+ *            p->shifted, out[0] otherwise), out[1] = lattice Frank energy E_d
+ *   (as in nh_diagnostics), out[2] = max |u|, out[3] = min |n|,
+ *   out[4] = max |n|, out[5] = number of sites with a NaN/Inf.
+ * Asynchronous on stream (NULL = legacy default stream); no tube tracking.
+ *
+ * Scratch: a static device array inside the library (48 KiB per GPU that
+ * loads it, held until the process exits); the call allocates nothing.  Size
+ * limit: nx * ny * ceil(nz / 16) <= NH_NOALLOC_MAX_ITEMS, else NH_EINVAL with
+ * a message in nh_last_error(NULL).  The first call on each device looks up
+ * the array's device address with that device current; make that first call
+ * before any stream capture.  All calls share the one array, which keeps the
+ * last call's partial sums (each call overwrites what it reads, so nothing
+ * needs clearing): calls that overlap on the GPU, from any thread or stream,
+ * race on it and must be serialised by the caller. */
+#define NH_NOALLOC_MAX_ITEMS (1024 * 256)
+int nh_diagnostics_noalloc(const nh_params* p, const void* f, const void* n, const void* u, const void* rho,
+                           double* out, void* stream);
+
 /* Release the context (NULL-safe).  Does not free the caller's workspace. */
 void nh_destroy(nh_ctx* ctx);
 

@@ -101,6 +101,7 @@ SIGNATURES = {
     "nh_set_lb_variant": ([_VP, ctypes.c_int], ctypes.c_int),
     "nh_autotune": ([_VP, _VP, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "nh_destroy": ([_VP], None),
+    "nh_diagnostics_noalloc": ([ctypes.POINTER(nh_params), _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
 }
 
 _lib = None
@@ -289,6 +290,14 @@ def nh_autotune(ctx, stream=None) -> int:
     out = ctypes.c_int(-1)
     _check(load_library().nh_autotune(ctx, _VP(stream or 0), ctypes.byref(out)), ctx)
     return int(out.value)
+
+
+def nh_diagnostics_noalloc(p: nh_params, f, n, u, rho, out, stream=None):
+    """Diagnostics from caller-owned device buffers (torch CUDA tensors) into
+    out (a CUDA float64 tensor of 6); allocates no device memory."""
+    _check(load_library().nh_diagnostics_noalloc(
+        ctypes.byref(p), _VP(f.data_ptr()), _VP(n.data_ptr()), _VP(u.data_ptr()), _VP(rho.data_ptr()),
+        _VP(out.data_ptr()), _VP(stream or 0)))
 
 
 def nh_destroy(ctx):

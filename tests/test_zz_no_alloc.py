@@ -1,0 +1,69 @@
+"""nh_diagnostics_noalloc: the diagnostics reduction for callers that cannot
+allocate device memory (a host application that only lends its own input and
+output buffers, or a loop that cannot afford cudaMalloc's device sync).
+
+It is checked through the C ABI against the ordinary entry point,
+nh_diagnostics, on the same state, on two calls in a row (the second after
+more steps, so the shared static scratch is reused with new data).  The
+caller-side tensors here are ordinary torch allocations made by the test; the
+entry point itself allocates nothing.
+"""
+import numpy as np
+import pytest
+
+from paper_2503_06610_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2503_06610_gb300 import nh
+    nh.load_library()
+    return torch, nh
+
+
+def _device_state(torch, ch, dtype):
+    f = ch.get_populations()
+    n, u, rho = ch.get_fields()
+    cuda = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dtype=dtype, device="cuda")
+    return cuda(f), cuda(n), cuda(u), cuda(rho)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_noalloc_matches_nh_diagnostics_twice(env, prec):
+    torch, nh = env
+    params, n0 = I.tiny_channel()
+    params = dict(params, K=0.03, q0=0.3, W0=0.01, dt_fd=2)
+    ch = nh.Channel(dict(params, precision=prec))
+    ch.set_fields(n0)
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    p = nh.make_params(dict(params, precision=prec))
+    for steps in (20, 37):                       # two calls in a row, new data each time
+        ch.step(steps)
+        ref = ch.diagnostics()
+        f, n, u, rho = _device_state(torch, ch, dtype)
+        out = torch.full((6,), float("nan"), dtype=torch.float64, device="cuda")
+        nh.nh_diagnostics_noalloc(p, f, n, u, rho, out, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        v = out.cpu().numpy()
+        mass = v[0] + ch.N                      # shifted populations
+        assert abs(mass - ref["mass"]) <= 1e-12 * ch.N
+        assert abs(v[1] - ref["energy"]) <= 1e-11 * abs(ref["energy"])
+        assert abs(v[2] - ref["max_u"]) <= 1e-12 * ref["max_u"]
+        assert abs(v[3] - ref["min_norm"]) <= 1e-15 and abs(v[4] - ref["max_norm"]) <= 1e-15
+        assert v[5] == 0.0
+
+
+def test_noalloc_rejects_oversized_domain(env):
+    torch, nh = env
+    p = nh.make_params(dict(nx=1024, ny=1024, nz=16, precision="fp32"))
+    t = torch.zeros(8, dtype=torch.float32, device="cuda")
+    out = torch.zeros(6, dtype=torch.float64, device="cuda")
+    with pytest.raises(nh.NHError) as e:
+        nh.nh_diagnostics_noalloc(p, t, t, t, t, out)
+    assert e.value.code == nh.NH_EINVAL
+    assert "static scratch" in str(e.value)
