@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--small", action="store_true", help="64x64x32 case (profiling only)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-channel sweep")
+    ap.add_argument("--batch-blocks", type=int, default=20, help="dt_FD blocks timed in the batched sweep")
     return ap.parse_args()
 
 
@@ -154,6 +156,46 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+
+def batched_sweep(nh, torch, store, blocks):
+    """64 channels (L in {32,48,64,96}, Lz in {16,24,32}, one tube each, FP32
+    shifted, dt_FD = 16): one batched launch per pass vs a per-channel loop."""
+    from paper_2503_06610_gb300 import inputs
+    sweep = inputs.batched_sweep(64, seed=0, dt_fd=16)
+    chans = []
+    for params, n0, centre in sweep:
+        ch = nh.Channel(dict(params, precision="fp32", storage=store, shifted=True))
+        ch.set_fields(n0)
+        chans.append(ch)
+    sites = sum(c.N for c in chans)
+    dt = sweep[0][0]["dt_fd"]
+    variant = nh.batch_autotune(chans)
+    nh.batch_step(chans, dt)
+    for c in chans:
+        c.step(dt)
+    torch.cuda.synchronize()
+    st = chans[0].stream
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    launches0 = chans[0].launch_count()
+    e[0].record(st)
+    nh.batch_step(chans, dt * blocks)
+    e[1].record(st)
+    torch.cuda.synchronize()
+    batch_launches = chans[0].launch_count() - launches0
+    e[2].record(st)
+    for _ in range(blocks):
+        for c in chans:
+            c.step(dt)
+    e[3].record(st)
+    torch.cuda.synchronize()
+    t_b = e[0].elapsed_time(e[1]) * 1e-3
+    t_s = e[2].elapsed_time(e[3]) * 1e-3
+    for c in chans:
+        c.close()
+    return {"channels": len(chans), "sites": sites, "lb_steps": dt * blocks, "lb_variant": variant,
+            "batched_mlups": sites * dt * blocks / t_b / 1e6, "sequential_mlups": sites * dt * blocks / t_s / 1e6,
+            "speedup": t_s / t_b, "batched_launches": batch_launches}
+
 
 def run_ours(args):
     import torch
@@ -307,6 +349,11 @@ def run_ours(args):
                "api": "nh_set_fields(host) + nh_step + nh_get_fields(host)"}
         ce.close()
 
+    # batched sweep: 64 independent channels of uneven size in one launch per pass
+    batched = None
+    if rank == 0 and not args.no_batch:
+        batched = batched_sweep(nh, torch, store, args.batch_blocks)
+
     if rank == 0:
         out = {
             "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
@@ -323,6 +370,7 @@ def run_ours(args):
             "value_graphs_no_kernel_events": value_graphs,
             "kernel_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in kt.items()},
             "fp64_compare": compare,
+            "batched_sweep": batched,
             "diagnostics": {"mass_minus_N": diag["mass"] - N, "energy": diag["energy"], "max_u": diag["max_u"],
                             "centroids": diag["centroids"].tolist()[:8], "nonfinite": diag["nonfinite"]},
         }

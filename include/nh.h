@@ -179,12 +179,24 @@ int nh_step(nh_ctx* ctx, int64_t n_lb_steps, void* stream);
  * force) with the context's current u, without an LB step. */
 int nh_fd_update(nh_ctx* ctx, void* stream);
 
-/* Advance count independent channels by n_lb_steps each, with one launch
- * per pass covering every channel (a work list of tiles over all channels).
- * All contexts must share precision, storage, shifted and dt_fd, be on the
- * same device, have a workspace bound and the same step count modulo dt_fd;
- * otherwise NH_EINVAL and nothing runs.  Asynchronous on stream. */
+/* Advance count independent channels (uneven sizes and parameters allowed)
+ * by n_lb_steps each.  Every pass (LB sweep, FD predict, correct, stress,
+ * force) is one persistent launch per group of up to 64 channels: the grid
+ * walks a work list of (channel, tile) pairs, and the channel descriptors
+ * travel as kernel parameters.  Whole dt_fd blocks are replayed from a CUDA
+ * graph cached per list of contexts (dropped when a context is rebound,
+ * re-tuned or destroyed).  All contexts must share precision, storage,
+ * shifted and dt_fd, be on one device, have fields set and be at the same
+ * step phase (step mod dt_fd and buffer parity); otherwise NH_EINVAL and
+ * nothing runs.  Launch counts and timing are recorded on ctxs[0]; the launch
+ * shape is ctxs[0]'s LB variant (see nh_batch_autotune).  Asynchronous on
+ * stream (NULL = ctxs[0]'s stream). */
 int nh_batch_step(nh_ctx* const* ctxs, int count, int64_t n_lb_steps, void* stream);
+
+/* Autotuner of the batched LB launch: times every launch shape valid for all
+ * channels on the batch itself (the state is not advanced), keeps the fastest
+ * for this list of contexts and returns it in *chosen.  Synchronises. */
+int nh_batch_autotune(nh_ctx* const* ctxs, int count, void* stream, int* chosen);
 
 /* Set the tube centroids to track (count <= NH_MAX_TUBES, centres[2*count]
  * as (x, y) pairs); 0 disables tracking. */

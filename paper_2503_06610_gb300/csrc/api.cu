@@ -5,6 +5,9 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -169,6 +172,8 @@ struct nh_ctx {
     double tubes[NH_MAX_TUBES][2] = {};
     bool use_graphs = true;
     int lb_variant = 0;
+    int sm_count = 152;
+    int64_t epoch = 0;  // bumped whenever buffers or launch shapes change (invalidates batch plans)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t graph_kernels[2] = {0, 0};
     int timing = 0;  // 0 off, 1 every kernel class, 2 the LB class only
@@ -215,8 +220,12 @@ int cuda_fail(nh_ctx* c, cudaError_t e, const char* where)
 
 cudaStream_t pick(nh_ctx* c, void* s) { return s ? static_cast<cudaStream_t>(s) : c->stream; }
 
+void drop_batch_plans(const nh_ctx* c);
+
 void drop_graphs(nh_ctx* c)
 {
+    c->epoch += 1;
+    drop_batch_plans(c);
     for (int k = 0; k < 2; ++k) {
         if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
         c->graph[k] = nullptr;
@@ -523,6 +532,197 @@ int enqueue_diag(nh_ctx* c, cudaStream_t st)
 
 }  // namespace
 
+namespace {
+
+// ------------------------------------------------------------ batched channels
+
+struct BatchPlan {
+    std::vector<nh_ctx*> ctxs;
+    std::vector<int64_t> epochs;
+    int variant = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int64_t graph_kernels[2] = {0, 0};
+};
+
+std::mutex g_batch_mu;
+std::map<std::vector<nh_ctx*>, BatchPlan*> g_batch_plans;
+
+void batch_drop_graphs(BatchPlan* b)
+{
+    for (int k = 0; k < 2; ++k) {
+        if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
+        b->graph[k] = nullptr;
+        b->graph_kernels[k] = 0;
+    }
+}
+
+void drop_batch_plans(const nh_ctx* c)
+{
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    for (auto it = g_batch_plans.begin(); it != g_batch_plans.end();) {
+        if (std::find(it->first.begin(), it->first.end(), c) != it->first.end()) {
+            batch_drop_graphs(it->second);
+            delete it->second;
+            it = g_batch_plans.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+// Validate a batch and find (or build) its plan.
+int batch_prepare(nh_ctx* const* ctxs, int count, int64_t n_lb_steps, BatchPlan** out)
+{
+    if (!ctxs || count < 1) return fail(nullptr, NH_EINVAL, "need at least one context");
+    if (n_lb_steps < 0) return fail(nullptr, NH_EINVAL, "n_lb_steps must be >= 0");
+    nh_ctx* c0 = ctxs[0];
+    for (int k = 0; k < count; ++k) {
+        nh_ctx* c = ctxs[k];
+        if (!c) return fail(nullptr, NH_EINVAL, "NULL context in batch");
+        if (!c->bound || !c->fields_set)
+            return fail(nullptr, NH_EINVAL, "channel " + std::to_string(k) + ": workspace or fields not set");
+        if (c->p.precision != c0->p.precision || c->p.storage != c0->p.storage || c->p.shifted != c0->p.shifted ||
+            c->p.dt_fd != c0->p.dt_fd)
+            return fail(nullptr, NH_EINVAL, "channels must share precision, storage, shifted and dt_fd");
+        if (c->device != c0->device) return fail(nullptr, NH_EINVAL, "channels must be on one device");
+        if (c->cur != c0->cur || c->step % c0->p.dt_fd != c0->step % c0->p.dt_fd)
+            return fail(nullptr, NH_EINVAL, "channels must be at the same step phase (step mod dt_fd, buffer parity)");
+        for (int j = 0; j < k; ++j)
+            if (ctxs[j] == c) return fail(nullptr, NH_EINVAL, "a context appears twice in the batch");
+    }
+    int r = set_device(c0);
+    if (r) return fail(nullptr, r, c0->err);
+    std::vector<nh_ctx*> key(ctxs, ctxs + count);
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    BatchPlan*& plan = g_batch_plans[key];
+    std::vector<int64_t> epochs;
+    for (nh_ctx* c : key) epochs.push_back(c->epoch);
+    if (plan && plan->epochs != epochs) {
+        batch_drop_graphs(plan);
+        delete plan;
+        plan = nullptr;
+    }
+    if (!plan) {
+        plan = new (std::nothrow) BatchPlan();
+        if (!plan) return fail(nullptr, NH_ENOMEM, "host allocation of the batch plan failed");
+        plan->ctxs = key;
+        plan->epochs = epochs;
+        int v = c0->lb_variant;
+        bool ok = true;
+        for (nh_ctx* c : key) ok = ok && lb_variant_valid(v, c->p.nx);
+        if (!ok) v = 1;  // one site per thread fits every domain
+        plan->variant = v;
+    }
+    *out = plan;
+    return NH_OK;
+}
+
+template <typename Real, typename Store>
+int batch_lb_typed(BatchPlan* b, bool write_macro, cudaStream_t st)
+{
+    nh_ctx* c0 = b->ctxs[0];
+    const int n = (int)b->ctxs.size();
+    static thread_local LBBatch<Real, Store> batch;  // large parameter block, kept off the stack
+    for (int g0 = 0; g0 < n; g0 += kMaxBatch) {
+        batch.count = std::min(kMaxBatch, n - g0);
+        for (int k = 0; k < batch.count; ++k) batch.ch[k] = lb_chan<Real, Store>(b->ctxs[g0 + k], b->ctxs[g0 + k]->cur);
+        const int grid = 8 * c0->sm_count;
+        int r = timed(c0, NH_KCLASS_LB, st,
+                      [&] { return launch_lb_batch(batch, c0->p.shifted != 0, write_macro, b->variant, grid, st); },
+                      "lb_batch");
+        if (r) return r;
+    }
+    return NH_OK;
+}
+
+int batch_enqueue_lb(BatchPlan* b, bool write_macro, cudaStream_t st)
+{
+    switch (b->ctxs[0]->p.storage) {
+    case NH_STORE_F64: return batch_lb_typed<double, double>(b, write_macro, st);
+    case NH_STORE_F32: return batch_lb_typed<float, float>(b, write_macro, st);
+    case NH_STORE_F16S: return batch_lb_typed<float, __half>(b, write_macro, st);
+    default: return batch_lb_typed<float, __nv_bfloat16>(b, write_macro, st);
+    }
+}
+
+template <typename Real>
+int batch_fd_typed(BatchPlan* b, cudaStream_t st)
+{
+    nh_ctx* c0 = b->ctxs[0];
+    const int n = (int)b->ctxs.size();
+    static thread_local FDBatch<Real> batch;
+    const int classes[4] = {NH_KCLASS_FD_PREDICT, NH_KCLASS_FD_CORRECT, NH_KCLASS_STRESS, NH_KCLASS_FORCE};
+    for (int stage = 0; stage < 4; ++stage) {
+        for (int g0 = 0; g0 < n; g0 += kMaxBatch) {
+            batch.count = std::min(kMaxBatch, n - g0);
+            for (int k = 0; k < batch.count; ++k) batch.ch[k] = fd_chan<Real>(b->ctxs[g0 + k]);
+            const int grid = 8 * c0->sm_count;
+            int r = timed(c0, classes[stage], st, [&] { return launch_fd_batch(batch, stage, grid, st); }, "fd_batch");
+            if (r) return r;
+        }
+    }
+    return NH_OK;
+}
+
+// One batched LB step (+ the batched FD update when the step count reaches a
+// multiple of dt_fd) for every channel of the plan.
+int batch_one_step(BatchPlan* b, bool last_of_call, cudaStream_t st)
+{
+    nh_ctx* c0 = b->ctxs[0];
+    const int64_t next = c0->step + 1;
+    const bool fd = (next % c0->p.dt_fd) == 0;
+    int r = batch_enqueue_lb(b, fd || last_of_call, st);
+    if (r) return r;
+    for (nh_ctx* c : b->ctxs) {
+        c->cur ^= 1;
+        c->step += 1;
+    }
+    if (fd) return c0->p.precision == NH_FP64 ? batch_fd_typed<double>(b, st) : batch_fd_typed<float>(b, st);
+    return NH_OK;
+}
+
+int batch_capture(BatchPlan* b, int parity)
+{
+    nh_ctx* c0 = b->ctxs[0];
+    std::vector<int> cur;
+    std::vector<int64_t> step;
+    for (nh_ctx* c : b->ctxs) {
+        cur.push_back(c->cur);
+        step.push_back(c->step);
+        c->cur = parity;
+        c->step = 0;
+    }
+    const int64_t saved_launches = c0->launches;
+    cudaStream_t cs = c0->cap_stream;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    int r = e == cudaSuccess ? NH_OK : cuda_fail(c0, e, "cudaStreamBeginCapture");
+    if (r == NH_OK) {
+        for (int k = 0; k < c0->p.dt_fd && r == NH_OK; ++k) r = batch_one_step(b, false, cs);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(cs, &g);
+        if (r == NH_OK && e != cudaSuccess) r = cuda_fail(c0, e, "cudaStreamEndCapture");
+        if (r == NH_OK) {
+            cudaGraphExec_t ex = nullptr;
+            e = cudaGraphInstantiate(&ex, g, 0);
+            if (e != cudaSuccess)
+                r = cuda_fail(c0, e, "cudaGraphInstantiate");
+            else {
+                b->graph[parity] = ex;
+                b->graph_kernels[parity] = c0->launches - saved_launches;
+            }
+        }
+        if (g) cudaGraphDestroy(g);
+    }
+    c0->launches = saved_launches;
+    for (size_t k = 0; k < b->ctxs.size(); ++k) {
+        b->ctxs[k]->cur = cur[k];
+        b->ctxs[k]->step = step[k];
+    }
+    return r;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* nh_error_string(int code)
@@ -565,6 +765,7 @@ int nh_create(const nh_params* p, void* cuda_stream, nh_ctx** out)
     c->L = make_layout(*p);
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         fail(nullptr, NH_ECUDA, std::string("nh_create: ") + cudaGetErrorString(e));
@@ -818,12 +1019,80 @@ int nh_fd_update(nh_ctx* c, void* stream)
 
 int nh_batch_step(nh_ctx* const* ctxs, int count, int64_t n_lb_steps, void* stream)
 {
-    if (!ctxs || count < 1) return fail(nullptr, NH_EINVAL, "need at least one context");
-    for (int k = 0; k < count; ++k) {
-        int r = nh_step(ctxs[k], n_lb_steps, stream);
-        if (r) return fail(nullptr, r, std::string("channel ") + std::to_string(k) + ": " + ctxs[k]->err);
+    BatchPlan* plan = nullptr;
+    int r = batch_prepare(ctxs, count, n_lb_steps, &plan);
+    if (r) return r;
+    nh_ctx* c0 = ctxs[0];
+    cudaStream_t st = pick(c0, stream);
+    const int dt = c0->p.dt_fd;
+    int64_t left = n_lb_steps;
+    while (left > 0) {
+        if (c0->use_graphs && !c0->timing && c0->step % dt == 0 && left >= dt) {
+            const int parity = c0->cur;
+            if (!plan->graph[parity]) {
+                r = batch_capture(plan, parity);
+                if (r) return fail(nullptr, r, "batch graph capture: " + c0->err);
+            }
+            cudaError_t e = cudaGraphLaunch(plan->graph[parity], st);
+            if (e != cudaSuccess) return fail(nullptr, NH_ECUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+            c0->launches += plan->graph_kernels[parity];
+            for (nh_ctx* c : plan->ctxs) {
+                if (dt & 1) c->cur ^= 1;
+                c->step += dt;
+            }
+            left -= dt;
+        } else {
+            r = batch_one_step(plan, left == 1, st);
+            if (r) return fail(nullptr, r, "batch step: " + c0->err);
+            left -= 1;
+        }
     }
+    close_segment(c0);
     return NH_OK;
+}
+
+int nh_batch_autotune(nh_ctx* const* ctxs, int count, void* stream, int* chosen)
+{
+    BatchPlan* plan = nullptr;
+    int r = batch_prepare(ctxs, count, 1, &plan);
+    if (r) return r;
+    nh_ctx* c0 = ctxs[0];
+    cudaStream_t st = pick(c0, stream);
+    close_segment(c0);
+    const int saved_timing = c0->timing;
+    c0->timing = 0;
+    cudaEvent_t e0 = get_event(c0), e1 = get_event(c0);
+    float best_ms = 1e30f;
+    int best = plan->variant;
+    const int saved = plan->variant;
+    for (int v = 0; v < kLBVariantCount && r == NH_OK; ++v) {
+        bool ok = true;
+        for (nh_ctx* c : plan->ctxs) ok = ok && lb_variant_valid(v, c->p.nx);
+        if (!ok) continue;
+        plan->variant = v;
+        r = batch_enqueue_lb(plan, false, st);  // streams the current buffers into the others, no swap
+        if (r) break;
+        cudaEventRecord(e0, st);
+        for (int k = 0; k < 5 && r == NH_OK; ++k) r = batch_enqueue_lb(plan, false, st);
+        cudaEventRecord(e1, st);
+        if (r) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            r = fail(nullptr, NH_ECUDA, "cudaEventSynchronize");
+            break;
+        }
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    c0->free_events.push_back(e0);
+    c0->free_events.push_back(e1);
+    c0->timing = saved_timing;
+    plan->variant = best;
+    if (best != saved) batch_drop_graphs(plan);
+    if (chosen) *chosen = best;
+    return r;
 }
 
 int nh_set_tubes(nh_ctx* c, const double* centres, int count)

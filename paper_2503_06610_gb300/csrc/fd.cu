@@ -137,10 +137,8 @@ __device__ __forceinline__ void director_rate(const Real nn[7][3], const Real uu
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(256) fd_predict_kernel(const FDChan<Real> c)
+__device__ __forceinline__ void fd_predict_site(const FDChan<Real>& c, int s)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= c.g.N) return;
     int x, y, z;
     site_xyz<Real>(c.g, s, x, y, z);
     Real nn[7][3], uu[7][3], r[3];
@@ -156,10 +154,8 @@ __global__ void __launch_bounds__(256) fd_predict_kernel(const FDChan<Real> c)
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(256) fd_correct_kernel(const FDChan<Real> c)
+__device__ __forceinline__ void fd_correct_site(const FDChan<Real>& c, int s)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= c.g.N) return;
     int x, y, z;
     site_xyz<Real>(c.g, s, x, y, z);
     Real nn[7][3], uu[7][3], r[3];
@@ -176,10 +172,8 @@ __global__ void __launch_bounds__(256) fd_correct_kernel(const FDChan<Real> c)
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(256) stress_kernel(const FDChan<Real> c)
+__device__ __forceinline__ void stress_site(const FDChan<Real>& c, int s)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= c.g.N) return;
     int x, y, z;
     site_xyz<Real>(c.g, s, x, y, z);
     Real nn[7][3], uu[7][3];
@@ -220,10 +214,8 @@ __global__ void __launch_bounds__(256) stress_kernel(const FDChan<Real> c)
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(256) force_kernel(const FDChan<Real> c)
+__device__ __forceinline__ void force_site(const FDChan<Real>& c, int s)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= c.g.N) return;
     int x, y, z;
     site_xyz<Real>(c.g, s, x, y, z);
     const Geom& g = c.g;
@@ -252,32 +244,89 @@ __global__ void __launch_bounds__(256) force_kernel(const FDChan<Real> c)
     }
 }
 
+template <typename Real, int Stage>
+__device__ __forceinline__ void fd_stage_site(const FDChan<Real>& c, int s)
+{
+    if (Stage == 0)
+        fd_predict_site(c, s);
+    else if (Stage == 1)
+        fd_correct_site(c, s);
+    else if (Stage == 2)
+        stress_site(c, s);
+    else
+        force_site(c, s);
+}
+
+template <typename Real, int Stage>
+__global__ void __launch_bounds__(256) fd_kernel(const FDChan<Real> c)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < c.g.N) fd_stage_site<Real, Stage>(c, s);
+}
+
+// Batched FD stage: a persistent grid walks the (channel, tile) work list.
+template <typename Real, int Stage>
+__global__ void __launch_bounds__(256) fd_batch_kernel(const FDBatch<Real> b)
+{
+    const int total = b.prefix[b.count];
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        int lo = 0, hi = b.count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (b.prefix[mid] <= t)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const int s = (t - b.prefix[lo]) * blockDim.x + threadIdx.x;
+        if (s < b.ch[lo].g.N) fd_stage_site<Real, Stage>(b.ch[lo], s);
+    }
+}
+
 inline int blocks_for(int N) { return (N + 255) / 256; }
 
 }  // namespace
 
 template <typename Real>
+cudaError_t launch_fd_batch(FDBatch<Real>& b, int stage, int grid, cudaStream_t st)
+{
+    if (b.count < 1 || b.count > kMaxBatch) return cudaErrorInvalidValue;
+    b.prefix[0] = 0;
+    for (int k = 0; k < b.count; ++k) b.prefix[k + 1] = b.prefix[k] + blocks_for(b.ch[k].g.N);
+    const int blocks = grid < b.prefix[b.count] ? grid : b.prefix[b.count];
+    switch (stage) {
+    case 0: fd_batch_kernel<Real, 0><<<blocks, 256, 0, st>>>(b); break;
+    case 1: fd_batch_kernel<Real, 1><<<blocks, 256, 0, st>>>(b); break;
+    case 2: fd_batch_kernel<Real, 2><<<blocks, 256, 0, st>>>(b); break;
+    default: fd_batch_kernel<Real, 3><<<blocks, 256, 0, st>>>(b); break;
+    }
+    return cudaGetLastError();
+}
+template cudaError_t launch_fd_batch<double>(FDBatch<double>&, int, int, cudaStream_t);
+template cudaError_t launch_fd_batch<float>(FDBatch<float>&, int, int, cudaStream_t);
+
+template <typename Real>
 cudaError_t launch_fd_predict(const FDChan<Real>& c, cudaStream_t st)
 {
-    fd_predict_kernel<Real><<<blocks_for(c.g.N), 256, 0, st>>>(c);
+    fd_kernel<Real, 0><<<blocks_for(c.g.N), 256, 0, st>>>(c);
     return cudaGetLastError();
 }
 template <typename Real>
 cudaError_t launch_fd_correct(const FDChan<Real>& c, cudaStream_t st)
 {
-    fd_correct_kernel<Real><<<blocks_for(c.g.N), 256, 0, st>>>(c);
+    fd_kernel<Real, 1><<<blocks_for(c.g.N), 256, 0, st>>>(c);
     return cudaGetLastError();
 }
 template <typename Real>
 cudaError_t launch_stress(const FDChan<Real>& c, cudaStream_t st)
 {
-    stress_kernel<Real><<<blocks_for(c.g.N), 256, 0, st>>>(c);
+    fd_kernel<Real, 2><<<blocks_for(c.g.N), 256, 0, st>>>(c);
     return cudaGetLastError();
 }
 template <typename Real>
 cudaError_t launch_force(const FDChan<Real>& c, cudaStream_t st)
 {
-    force_kernel<Real><<<blocks_for(c.g.N), 256, 0, st>>>(c);
+    fd_kernel<Real, 3><<<blocks_for(c.g.N), 256, 0, st>>>(c);
     return cudaGetLastError();
 }
 

@@ -88,13 +88,16 @@ __device__ __forceinline__ void store2(Store* p, Real a, Real b, float scale)
     *reinterpret_cast<typename Vec2<Store>::T*>(p) = v;
 }
 
+// One tile (one thread block's worth of sites) of one channel.  `tile` is the
+// tile index within the channel and `ntiles` the channel's tile count (used by
+// the 16-bit scale controller to find the channel's last tile).
 template <typename Real, typename Store, bool Shifted, bool WriteMacro, int SPT>
-__global__ void __launch_bounds__(kLBThreads) lb_kernel(const LBChan<Real, Store> c)
+__device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, int ntiles)
 {
     NH_D3Q19_TABLES
     constexpr bool kScaled = sizeof(Store) == 2;
     const int N = c.g.N;
-    const int s0 = (blockIdx.x * blockDim.x + threadIdx.x) * SPT;
+    const int s0 = (tile * blockDim.x + threadIdx.x) * SPT;
     float amax = 0.f;
     float scale_out = 1.f;
     if (kScaled) scale_out = c.scales[2];
@@ -234,7 +237,7 @@ __global__ void __launch_bounds__(kLBThreads) lb_kernel(const LBChan<Real, Store
                 atomicMax(reinterpret_cast<int*>(&c.ctrl[0]), __float_as_int(b));
             __threadfence();
             const unsigned ticket = atomicAdd(&c.ctrl[1], 1u);
-            last = ticket == gridDim.x - 1;
+            last = ticket == (unsigned)ntiles - 1;
         }
         __syncthreads();
         if (last && threadIdx.x == 0) {
@@ -244,6 +247,32 @@ __global__ void __launch_bounds__(kLBThreads) lb_kernel(const LBChan<Real, Store
             c.scales[2] = scale_for(m, scale_out);
             c.ctrl[1] = 0u;
         }
+        __syncthreads();  // the shared controller state is reused by the next tile
+    }
+}
+
+template <typename Real, typename Store, bool Shifted, bool WriteMacro, int SPT>
+__global__ void __launch_bounds__(kLBThreads) lb_kernel(const LBChan<Real, Store> c)
+{
+    lb_tile<Real, Store, Shifted, WriteMacro, SPT>(c, blockIdx.x, gridDim.x);
+}
+
+// Batched sweep: a persistent grid walks the (channel, tile) work list of up to
+// kMaxBatch channels; tiles of channel k are [prefix[k], prefix[k+1]).
+template <typename Real, typename Store, bool Shifted, bool WriteMacro, int SPT>
+__global__ void __launch_bounds__(kLBThreads) lb_batch_kernel(const LBBatch<Real, Store> b)
+{
+    const int total = b.prefix[b.count];
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        int lo = 0, hi = b.count - 1;  // channel k with prefix[k] <= t < prefix[k+1]
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (b.prefix[mid] <= t)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        lb_tile<Real, Store, Shifted, WriteMacro, SPT>(b.ch[lo], t - b.prefix[lo], b.prefix[lo + 1] - b.prefix[lo]);
     }
 }
 
@@ -283,6 +312,44 @@ cudaError_t launch_lb(const LBChan<Real, Store>& c, bool shifted, bool write_mac
     if (write_macro) return launch_lb_spt<Real, Store, false, true>(c, variant, st);
     return launch_lb_spt<Real, Store, false, false>(c, variant, st);
 }
+
+template <typename Real, typename Store, bool Shifted, bool WriteMacro>
+cudaError_t launch_lb_batch_spt(LBBatch<Real, Store>& b, int variant, int grid, cudaStream_t st)
+{
+    const LBVariantShape v = kLBVariants[variant];
+    b.prefix[0] = 0;
+    for (int k = 0; k < b.count; ++k) {
+        const int threads_needed = (b.ch[k].g.N + v.spt - 1) / v.spt;
+        b.prefix[k + 1] = b.prefix[k] + (threads_needed + v.threads - 1) / v.threads;
+    }
+    const int blocks = grid < b.prefix[b.count] ? grid : b.prefix[b.count];
+    if (v.spt == 2)
+        lb_batch_kernel<Real, Store, Shifted, WriteMacro, 2><<<blocks, v.threads, 0, st>>>(b);
+    else
+        lb_batch_kernel<Real, Store, Shifted, WriteMacro, 1><<<blocks, v.threads, 0, st>>>(b);
+    return cudaGetLastError();
+}
+
+template <typename Real, typename Store>
+cudaError_t launch_lb_batch(LBBatch<Real, Store>& b, bool shifted, bool write_macro, int variant, int grid,
+                            cudaStream_t st)
+{
+    if (b.count < 1 || b.count > kMaxBatch) return cudaErrorInvalidValue;
+    for (int k = 0; k < b.count; ++k)
+        if (!lb_variant_valid(variant, b.ch[k].g.nx)) return cudaErrorInvalidValue;
+    if (shifted) {
+        if (write_macro) return launch_lb_batch_spt<Real, Store, true, true>(b, variant, grid, st);
+        return launch_lb_batch_spt<Real, Store, true, false>(b, variant, grid, st);
+    }
+    if (write_macro) return launch_lb_batch_spt<Real, Store, false, true>(b, variant, grid, st);
+    return launch_lb_batch_spt<Real, Store, false, false>(b, variant, grid, st);
+}
+
+template cudaError_t launch_lb_batch<double, double>(LBBatch<double, double>&, bool, bool, int, int, cudaStream_t);
+template cudaError_t launch_lb_batch<float, float>(LBBatch<float, float>&, bool, bool, int, int, cudaStream_t);
+template cudaError_t launch_lb_batch<float, __half>(LBBatch<float, __half>&, bool, bool, int, int, cudaStream_t);
+template cudaError_t launch_lb_batch<float, __nv_bfloat16>(LBBatch<float, __nv_bfloat16>&, bool, bool, int, int,
+                                                           cudaStream_t);
 
 template cudaError_t launch_lb<double, double>(const LBChan<double, double>&, bool, bool, int, cudaStream_t);
 template cudaError_t launch_lb<float, float>(const LBChan<float, float>&, bool, bool, int, cudaStream_t);

@@ -122,11 +122,37 @@ struct FDChan {
 };
 
 // ------------------------------------------------------------------ launchers (host)
+// Batched launches: up to kMaxBatch channel descriptors travel as kernel
+// parameters (no device allocation); prefix[k] is the first tile of channel k.
+constexpr int kMaxBatch = 64;
+template <typename Real, typename Store>
+struct LBBatch {
+    int count;
+    int prefix[kMaxBatch + 1];
+    LBChan<Real, Store> ch[kMaxBatch];
+};
+template <typename Real>
+struct FDBatch {
+    int count;
+    int prefix[kMaxBatch + 1];
+    FDChan<Real> ch[kMaxBatch];
+};
+
 // LB launch variants (sites per thread x block size); variant 0 is the default.
 constexpr int kLBVariantCount = 4;
 bool lb_variant_valid(int variant, int nx);
 template <typename Real, typename Store>
 cudaError_t launch_lb(const LBChan<Real, Store>& c, bool shifted, bool write_macro, int variant, cudaStream_t s);
+
+// Batched LB sweep over b.count channels with a persistent grid of at most
+// `grid` blocks (fills b.prefix).
+template <typename Real, typename Store>
+cudaError_t launch_lb_batch(LBBatch<Real, Store>& b, bool shifted, bool write_macro, int variant, int grid,
+                            cudaStream_t s);
+
+// Batched FD kernels: stage 0 predict, 1 correct, 2 stress, 3 force.
+template <typename Real>
+cudaError_t launch_fd_batch(FDBatch<Real>& b, int stage, int grid, cudaStream_t s);
 
 template <typename Real>
 cudaError_t launch_fd_predict(const FDChan<Real>& c, cudaStream_t s);

@@ -90,6 +90,7 @@ SIGNATURES = {
     "nh_step": ([_VP, ctypes.c_int64, _VP], ctypes.c_int),
     "nh_fd_update": ([_VP, _VP], ctypes.c_int),
     "nh_batch_step": ([ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int64, _VP], ctypes.c_int),
+    "nh_batch_autotune": ([ctypes.POINTER(_VP), ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "nh_set_tubes": ([_VP, _DP, ctypes.c_int], ctypes.c_int),
     "nh_diagnostics": ([_VP, ctypes.POINTER(nh_diag)], ctypes.c_int),
     "nh_diagnostics_enqueue": ([_VP, _VP], ctypes.c_int),
@@ -230,6 +231,13 @@ def nh_fd_update(ctx, stream=None):
 def nh_batch_step(ctxs, n_lb_steps: int, stream=None):
     arr = (_VP * len(ctxs))(*[c.value if isinstance(c, _VP) else c for c in ctxs])
     _check(load_library().nh_batch_step(arr, len(ctxs), int(n_lb_steps), _VP(stream or 0)))
+
+
+def nh_batch_autotune(ctxs, stream=None) -> int:
+    arr = (_VP * len(ctxs))(*[c.value if isinstance(c, _VP) else c for c in ctxs])
+    out = ctypes.c_int(-1)
+    _check(load_library().nh_batch_autotune(arr, len(ctxs), _VP(stream or 0), ctypes.byref(out)))
+    return int(out.value)
 
 
 def nh_set_tubes(ctx, centres):
@@ -413,3 +421,8 @@ class Channel:
 def batch_step(channels, n_lb_steps: int, stream=None):
     s = stream or channels[0].stream
     nh_batch_step([c.ctx for c in channels], n_lb_steps, s.cuda_stream)
+
+
+def batch_autotune(channels, stream=None) -> int:
+    s = stream or channels[0].stream
+    return nh_batch_autotune([c.ctx for c in channels], s.cuda_stream)

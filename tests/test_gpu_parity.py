@@ -360,3 +360,83 @@ def test_timing_segments_count_every_launch(nh):
     ch.set_timing(0)
     ch.step(4)
     assert ch.timing()["lb"][0] == 0
+
+
+# ------------------------------------------------------------------ batched channels (one launch per pass)
+
+def _batch_channels(nh, prec, specs, dt_fd=3):
+    chans, refs = [], []
+    for k, (nx, ny, nz) in enumerate(specs):
+        params = _generic(nx, ny, nz, dt_fd=dt_fd, g=(10 ** (-6 + 0.3 * k), 0.0, 0.0), q0=2 * math.pi / (nz + k))
+        n0 = I.skyrmion_tubes(nx, ny, nz, [(nx / 2, ny / 2)], nx / 4)
+        chans.append(_channel(nh, params, n0, precision=prec))
+        refs.append((params, n0))
+    return chans, refs
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_matches_oracle_and_single_channels(nh, oracle_mod, prec):
+    O = oracle_mod
+    specs = [(16, 12, 6), (13, 9, 5), (24, 8, 7), (10, 10, 4), (32, 6, 3)]
+    batch, refs = _batch_channels(nh, prec, specs)
+    nh.batch_step(batch, 7)
+    nh.batch_step(batch, 11)
+    singles, _ = _batch_channels(nh, prec, specs)
+    for ch in singles:
+        ch.step(18)
+    tol = 1e-10 if prec == "fp64" else 1e-5
+    for chb, chs, (params, n0) in zip(batch, singles, refs):
+        nb, ub, _ = chb.get_fields()
+        ns, us, _ = chs.get_fields()
+        assert O.rel_l2(ub, us) <= (1e-13 if prec == "fp64" else 1e-6)
+        assert O.rel_l2(nb, ns) <= (1e-13 if prec == "fp64" else 1e-6)
+        if prec == "fp64":
+            ref = _oracle_sim(O, params, n0).step(18)
+            assert O.rel_l2(ub, ref.u) <= tol
+            assert O.rel_l2(nb, ref.n) <= tol
+
+
+def test_batch_graphs_bitwise_and_autotune(nh):
+    specs = [(16, 12, 6), (20, 10, 8), (8, 8, 4)]
+    out = []
+    for graphs in (True, False):
+        chans, _ = _batch_channels(nh, "fp32", specs, dt_fd=4)
+        chans[0].set_graphs(graphs)
+        nh.batch_step(chans, 12)
+        out.append([c.get_fields()[1] for c in chans])
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+    chans, _ = _batch_channels(nh, "fp32", specs, dt_fd=4)
+    nh.batch_step(chans, 4)
+    before = [c.get_populations() for c in chans]
+    v = nh.batch_autotune(chans)
+    assert v in (0, 1, 2, 3)
+    for c, f in zip(chans, before):
+        assert np.array_equal(c.get_populations(), f)
+
+
+def test_batch_rejects_mismatched_channels(nh):
+    a, _ = _batch_channels(nh, "fp32", [(8, 8, 4)], dt_fd=2)
+    b, _ = _batch_channels(nh, "fp32", [(8, 8, 4)], dt_fd=3)
+    with pytest.raises(nh.NHError):
+        nh.batch_step(a + b, 2)
+    with pytest.raises(nh.NHError):
+        nh.batch_step(a + a, 2)
+    c, _ = _batch_channels(nh, "fp32", [(8, 8, 4)], dt_fd=2)
+    c[0].step(1)
+    with pytest.raises(nh.NHError):
+        nh.batch_step(a + c, 2)
+
+
+def test_batch_of_65_channels_spans_two_launch_groups(nh):
+    specs = [(8, 6, 3)] * 65
+    chans, _ = _batch_channels(nh, "fp32", [(8, 6, 3)], dt_fd=2)
+    params = _generic(8, 6, 3, dt_fd=2)
+    n0 = I.skyrmion_tubes(8, 6, 3, [(4.0, 3.0)], 2.0)
+    chans = [_channel(nh, params, n0, precision="fp32") for _ in specs]
+    nh.batch_step(chans, 6)
+    single = _channel(nh, params, n0, precision="fp32")
+    single.step(6)
+    ref = single.get_fields()[1]
+    for c in (chans[0], chans[63], chans[64]):
+        assert np.allclose(c.get_fields()[1], ref, rtol=1e-6, atol=1e-12)
