@@ -62,6 +62,26 @@ def workload(args):
     return params, n0, centres, name
 
 
+def ncu_traffic():
+    """DRAM read+write bytes per LB launch from the committed ncu summary, or
+    None when csrc/lb.cu changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "lb_kernel_multitube_256x256x64_fp32.md")
+    src = os.path.join(ROOT, "paper_2503_06610_gb300", "csrc", "lb.cu")
+    try:
+        vals = {}
+        for line in open(path):
+            line = line.strip()
+            if line.startswith("traffic_bytes_per_launch:") or line.startswith("lb_source_sha256_16:"):
+                k, v = line.split(":", 1)
+                vals[k] = v.strip()
+        if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != vals.get("lb_source_sha256_16"):
+            return None
+        return int(vals["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+
+
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
@@ -291,8 +311,9 @@ def run_ours(args):
     except Exception:
         peak, peak_src = 6800.0, "fallback"
     total_kernel_ms = sum(v[1] for v in kt.values())
+    traffic = ncu_traffic() if (store == "f32" and not args.small and dt == 16) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "lb_kernel (fused collide+stream)", "peak_source": peak_src,
+                "traffic": traffic, "kernel": "lb_kernel (fused collide+stream)", "peak_source": peak_src,
                 "lb_variant": lb_variant,
                 "bytes_per_launch": bytes_per_launch, "avg_launch_us": lb_avg_s * 1e6,
                 "share_of_kernel_time": lb_ms / total_kernel_ms if total_kernel_ms else None}

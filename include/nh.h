@@ -198,6 +198,20 @@ int nh_batch_step(nh_ctx* const* ctxs, int count, int64_t n_lb_steps, void* stre
  * for this list of contexts and returns it in *chosen.  Synchronises. */
 int nh_batch_autotune(nh_ctx* const* ctxs, int count, void* stream, int* chosen);
 
+/* Director-only relaxation (the plain method that relaxes an ansatz, Sec. II.A
+ * "minimizing its free energy"): sets u = 0 and runs n_fd_steps
+ * predictor-corrector steps of length dt_fd of Eq. director-time-eq, which
+ * at rest is the gradient flow dn/dt = h/gamma1 of the Frank energy, each
+ * followed by |n| = 1.  No LB step, stress or force is computed: after it the
+ * populations and F_lc are stale until nh_set_fields.  Asynchronous. */
+int nh_relax(nh_ctx* ctx, int64_t n_fd_steps, void* stream);
+
+/* nh_relax for count channels at once, one launch per pass per group of up to
+ * 64 channels (same work-list kernels as nh_batch_step).  Channels must share
+ * precision and device; sizes and parameters may differ.  Launches and timing
+ * are recorded on ctxs[0]. */
+int nh_batch_relax(nh_ctx* const* ctxs, int count, int64_t n_fd_steps, void* stream);
+
 /* Set the tube centroids to track (count <= NH_MAX_TUBES, centres[2*count]
  * as (x, y) pairs); 0 disables tracking. */
 int nh_set_tubes(nh_ctx* ctx, const double* centres, int count);

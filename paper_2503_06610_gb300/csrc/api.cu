@@ -368,6 +368,15 @@ int enqueue_fd(nh_ctx* c, cudaStream_t st)
     return enqueue_force_only<Real>(c, st);
 }
 
+template <typename Real>
+int enqueue_predict_correct(nh_ctx* c, cudaStream_t st)
+{
+    auto a = fd_chan<Real>(c);
+    int r = timed(c, NH_KCLASS_FD_PREDICT, st, [&] { return launch_fd_predict(a, st); }, "fd_predict");
+    if (r) return r;
+    return timed(c, NH_KCLASS_FD_CORRECT, st, [&] { return launch_fd_correct(a, st); }, "fd_correct");
+}
+
 int enqueue_fd_any(nh_ctx* c, cudaStream_t st)
 {
     return c->p.precision == NH_FP64 ? enqueue_fd<double>(c, st) : enqueue_fd<float>(c, st);
@@ -617,6 +626,31 @@ int batch_prepare(nh_ctx* const* ctxs, int count, int64_t n_lb_steps, BatchPlan*
     return NH_OK;
 }
 
+// Batch of director-only relaxations: the channels must share the precision
+// and the device (their step phase is irrelevant: no LB step runs).
+int batch_prepare_relax(nh_ctx* const* ctxs, int count, int64_t n_fd_steps, BatchPlan** out)
+{
+    if (!ctxs || count < 1) return fail(nullptr, NH_EINVAL, "need at least one context");
+    if (n_fd_steps < 0) return fail(nullptr, NH_EINVAL, "n_fd_steps must be >= 0");
+    nh_ctx* c0 = ctxs[0];
+    for (int k = 0; k < count; ++k) {
+        nh_ctx* c = ctxs[k];
+        if (!c) return fail(nullptr, NH_EINVAL, "NULL context in batch");
+        if (!c->bound || !c->fields_set)
+            return fail(nullptr, NH_EINVAL, "channel " + std::to_string(k) + ": workspace or fields not set");
+        if (c->p.precision != c0->p.precision) return fail(nullptr, NH_EINVAL, "channels must share the precision");
+        if (c->device != c0->device) return fail(nullptr, NH_EINVAL, "channels must be on one device");
+        for (int j = 0; j < k; ++j)
+            if (ctxs[j] == c) return fail(nullptr, NH_EINVAL, "a context appears twice in the batch");
+    }
+    int r = set_device(c0);
+    if (r) return fail(nullptr, r, c0->err);
+    static thread_local BatchPlan plan;
+    plan.ctxs.assign(ctxs, ctxs + count);
+    *out = &plan;
+    return NH_OK;
+}
+
 template <typename Real, typename Store>
 int batch_lb_typed(BatchPlan* b, bool write_macro, cudaStream_t st)
 {
@@ -646,13 +680,13 @@ int batch_enqueue_lb(BatchPlan* b, bool write_macro, cudaStream_t st)
 }
 
 template <typename Real>
-int batch_fd_typed(BatchPlan* b, cudaStream_t st)
+int batch_fd_typed(BatchPlan* b, cudaStream_t st, int stages = 4)
 {
     nh_ctx* c0 = b->ctxs[0];
     const int n = (int)b->ctxs.size();
     static thread_local FDBatch<Real> batch;
     const int classes[4] = {NH_KCLASS_FD_PREDICT, NH_KCLASS_FD_CORRECT, NH_KCLASS_STRESS, NH_KCLASS_FORCE};
-    for (int stage = 0; stage < 4; ++stage) {
+    for (int stage = 0; stage < stages; ++stage) {
         for (int g0 = 0; g0 < n; g0 += kMaxBatch) {
             batch.count = std::min(kMaxBatch, n - g0);
             for (int k = 0; k < batch.count; ++k) batch.ch[k] = fd_chan<Real>(b->ctxs[g0 + k]);
@@ -1093,6 +1127,39 @@ int nh_batch_autotune(nh_ctx* const* ctxs, int count, void* stream, int* chosen)
     if (best != saved) batch_drop_graphs(plan);
     if (chosen) *chosen = best;
     return r;
+}
+
+int nh_relax(nh_ctx* c, int64_t n_fd_steps, void* stream)
+{
+    int r = check_ready(c);
+    if (r) return r;
+    if (!c->fields_set) return fail(c, NH_EINVAL, "nh_set_fields must be called before nh_relax");
+    if (n_fd_steps < 0) return fail(c, NH_EINVAL, "n_fd_steps must be >= 0");
+    if ((r = set_device(c))) return r;
+    cudaStream_t st = pick(c, stream);
+    NH_CUDA(c, cudaMemsetAsync(c->ws + c->L.u, 0, 3 * (size_t)c->N * real_size(c->p), st));
+    for (int64_t k = 0; k < n_fd_steps && r == NH_OK; ++k)
+        r = c->p.precision == NH_FP64 ? enqueue_predict_correct<double>(c, st) : enqueue_predict_correct<float>(c, st);
+    close_segment(c);
+    return r;
+}
+
+int nh_batch_relax(nh_ctx* const* ctxs, int count, int64_t n_fd_steps, void* stream)
+{
+    BatchPlan* plan = nullptr;
+    int r = batch_prepare_relax(ctxs, count, n_fd_steps, &plan);
+    if (r) return r;
+    nh_ctx* c0 = ctxs[0];
+    cudaStream_t st = pick(c0, stream);
+    for (nh_ctx* c : plan->ctxs) {
+        cudaError_t e = cudaMemsetAsync(c->ws + c->L.u, 0, 3 * (size_t)c->N * real_size(c->p), st);
+        if (e != cudaSuccess) return fail(nullptr, NH_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+    }
+    for (int64_t k = 0; k < n_fd_steps && r == NH_OK; ++k)
+        r = c0->p.precision == NH_FP64 ? batch_fd_typed<double>(plan, st, 2) : batch_fd_typed<float>(plan, st, 2);
+    close_segment(c0);
+    if (r) return fail(nullptr, r, "batch relax: " + c0->err);
+    return NH_OK;
 }
 
 int nh_set_tubes(nh_ctx* c, const double* centres, int count)

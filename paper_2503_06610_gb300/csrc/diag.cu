@@ -258,16 +258,38 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const DiagArgs a)
             int owner = -1;
             double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
             if (valid) {
-                double bd = 1e300;
+                // nearest previous centroid: FP32 squared distances with the
+                // periodic minimum image; a near-tie of the two best is settled
+                // in FP64 so that the choice equals the FP64 one.
+                float bd = 3.0e38f, bd2 = 3.0e38f;
+                int second = -1;
+                const float hx = 0.5f * g.nx, hy = 0.5f * g.ny;
                 for (int k = 0; k < T; ++k) {
-                    double dx = x - a.tubes[k][0], dy = y - a.tubes[k][1];
-                    dx -= g.nx * floor(dx / g.nx + 0.5);
-                    dy -= g.ny * floor(dy / g.ny + 0.5);
-                    const double d2 = dx * dx + dy * dy;
+                    float dx = (float)x - (float)a.tubes[k][0], dy = (float)y - (float)a.tubes[k][1];
+                    dx = dx > hx ? dx - g.nx : (dx < -hx ? dx + g.nx : dx);
+                    dy = dy > hy ? dy - g.ny : (dy < -hy ? dy + g.ny : dy);
+                    const float d2 = dx * dx + dy * dy;
                     if (d2 < bd) {
+                        bd2 = bd;
+                        second = owner;
                         bd = d2;
                         owner = k;
+                    } else if (d2 < bd2) {
+                        bd2 = d2;
+                        second = k;
                     }
+                }
+                if (second >= 0 && bd2 - bd <= 1e-3f * (1.f + bd)) {
+                    double d2[2];
+                    const int cand[2] = {owner, second};
+                    for (int j = 0; j < 2; ++j) {
+                        double dx = x - a.tubes[cand[j]][0], dy = y - a.tubes[cand[j]][1];
+                        dx = dx > 0.5 * g.nx ? dx - g.nx : (dx < -0.5 * g.nx ? dx + g.nx : dx);
+                        dy = dy > 0.5 * g.ny ? dy - g.ny : (dy < -0.5 * g.ny ? dy + g.ny : dy);
+                        d2[j] = dx * dx + dy * dy;
+                    }
+                    // lowest index wins an exact tie, as in a first-minimum search
+                    if (d2[1] < d2[0] || (d2[1] == d2[0] && cand[1] < cand[0])) owner = cand[1];
                 }
                 const double w = (double)wsum;
                 v[0] = w;

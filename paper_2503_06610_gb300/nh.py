@@ -92,6 +92,8 @@ SIGNATURES = {
     "nh_batch_step": ([ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int64, _VP], ctypes.c_int),
     "nh_batch_autotune": ([ctypes.POINTER(_VP), ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "nh_set_tubes": ([_VP, _DP, ctypes.c_int], ctypes.c_int),
+    "nh_relax": ([_VP, ctypes.c_int64, _VP], ctypes.c_int),
+    "nh_batch_relax": ([ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int64, _VP], ctypes.c_int),
     "nh_diagnostics": ([_VP, ctypes.POINTER(nh_diag)], ctypes.c_int),
     "nh_diagnostics_enqueue": ([_VP, _VP], ctypes.c_int),
     "nh_diagnostics_read": ([_VP, ctypes.POINTER(nh_diag)], ctypes.c_int),
@@ -240,6 +242,15 @@ def nh_batch_autotune(ctxs, stream=None) -> int:
     return int(out.value)
 
 
+def nh_relax(ctx, n_fd_steps: int, stream=None):
+    _check(load_library().nh_relax(ctx, int(n_fd_steps), _VP(stream or 0)), ctx)
+
+
+def nh_batch_relax(ctxs, n_fd_steps: int, stream=None):
+    arr = (_VP * len(ctxs))(*[c.value if isinstance(c, _VP) else c for c in ctxs])
+    _check(load_library().nh_batch_relax(arr, len(ctxs), int(n_fd_steps), _VP(stream or 0)))
+
+
 def nh_set_tubes(ctx, centres):
     c = np.ascontiguousarray(np.asarray(centres, dtype=np.float64).reshape(-1))
     _check(load_library().nh_set_tubes(ctx, c.ctypes.data_as(_DP), len(c) // 2), ctx)
@@ -376,6 +387,9 @@ class Channel:
     def fd_update(self):
         nh_fd_update(self.ctx, self.stream.cuda_stream)
 
+    def relax(self, n_fd_steps: int, stream=None):
+        nh_relax(self.ctx, n_fd_steps, (stream or self.stream).cuda_stream)
+
     def set_tubes(self, centres):
         nh_set_tubes(self.ctx, centres)
 
@@ -421,6 +435,11 @@ class Channel:
 def batch_step(channels, n_lb_steps: int, stream=None):
     s = stream or channels[0].stream
     nh_batch_step([c.ctx for c in channels], n_lb_steps, s.cuda_stream)
+
+
+def batch_relax(channels, n_fd_steps: int, stream=None):
+    s = stream or channels[0].stream
+    nh_batch_relax([c.ctx for c in channels], n_fd_steps, s.cuda_stream)
 
 
 def batch_autotune(channels, stream=None) -> int:

@@ -1,0 +1,116 @@
+"""Precision x dt_FD sweep of the hybrid step (the experiment of Secs. III.A-III.B).
+
+For one workload (by default the 96x96x32 single skyrmion tube in Poiseuille
+flow, g_x in {1e-6, 1e-5}) every combination of arithmetic / population store
+(FP64, FP32 plain, FP32 shifted, FP16 and BF16 shifted) and dt_FD is run on the
+GPU through the C ABI; each run reports
+
+* MLUPS of the timed run (LB + FD + force, CUDA events),
+* the errors of u and n against the reference run - FP64, shifted, dt_FD = 1,
+  as in the paper - as relative L2 and as the paper's epsilon (Sec. III.A) and
+  its per-component form (Sec. III.B),
+* the tube centroid and its distance from the reference centroid.
+
+Usage:  python -m paper_2503_06610_gb300.sweep [--steps 5000] [--gx 1e-5] [--out sweep.json]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import inputs
+from . import nh
+
+SETTINGS = [
+    ("fp64", "f64", True),
+    ("fp32", "f32", False),
+    ("fp32", "f32", True),
+    ("fp32", "f16s", True),
+    ("fp32", "bf16s", True),
+]
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def eps(u, uref):
+    return float(np.sum(np.linalg.norm(u - uref, axis=0)) / np.sum(np.linalg.norm(uref, axis=0)))
+
+
+def eps_component(u, uref, a):
+    return float(np.sum(np.abs(u[a] - uref[a])) / np.sum(np.abs(uref[a])))
+
+
+def run_one(params, n0, centre, precision, storage, shifted, steps):
+    import torch
+    ch = nh.Channel(dict(params, precision=precision, storage=storage, shifted=shifted))
+    ch.set_fields(n0)
+    ch.set_tubes([centre])
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(ch.stream)
+    ch.step(steps)
+    e1.record(ch.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    n, u, rho = ch.get_fields()
+    d = ch.diagnostics(allow_unstable=True)
+    ch.close()
+    return {"mlups": ch.N * steps / (ms * 1e-3) / 1e6, "n": n, "u": u, "centroid": d["centroids"][0].tolist(),
+            "nonfinite": d["nonfinite"], "energy": d["energy"]}
+
+
+def sweep(steps=5000, gx=1e-5, dts=(1, 2, 4, 8, 16), settings=SETTINGS, nx=96, ny=96, nz=32, radius=12.0):
+    base, n0 = inputs.skyrmion_channel(gx=gx, dt_fd=1, nx=nx, ny=ny, nz=nz, radius=radius)
+    centre = (nx / 2, ny / 2)
+    ref = run_one(dict(base, dt_fd=1), n0, centre, "fp64", "f64", True, steps)
+    rows = []
+    for dt in dts:
+        for precision, storage, shifted in settings:
+            if (precision, storage, shifted, dt) == ("fp64", "f64", True, 1):
+                r = ref
+            else:
+                r = run_one(dict(base, dt_fd=dt), n0, centre, precision, storage, shifted, steps)
+            dx = (np.array(r["centroid"]) - np.array(ref["centroid"]) + 0.5 * np.array([nx, ny])) % np.array(
+                [nx, ny]) - 0.5 * np.array([nx, ny])
+            rows.append({
+                "dt_fd": dt, "precision": precision, "storage": storage, "shifted": shifted,
+                "mlups": r["mlups"], "rel_l2_u": rel_l2(r["u"], ref["u"]), "rel_l2_n": rel_l2(r["n"], ref["n"]),
+                "eps_u": eps(r["u"], ref["u"]), "eps_ux": eps_component(r["u"], ref["u"], 0),
+                "eps_uy": eps_component(r["u"], ref["u"], 1), "eps_uz": eps_component(r["u"], ref["u"], 2),
+                "centroid": r["centroid"], "centroid_shift": float(np.hypot(*dx)), "nonfinite": r["nonfinite"],
+            })
+    return {"workload": f"skyrmion channel {nx}x{ny}x{nz}, R={radius}, q0=2pi/32, gx={gx}, K={base['K']}",
+            "steps": steps, "reference": "fp64 shifted dt_FD=1", "reference_centroid": ref["centroid"],
+            "rows": rows}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--gx", type=float, nargs="+", default=[1e-6, 1e-5])
+    ap.add_argument("--dts", type=int, nargs="+", default=[1, 2, 4, 8, 16])
+    ap.add_argument("--out", default=None)
+    args = ap.parse_args()
+    results = []
+    for gx in args.gx:
+        t0 = time.time()
+        res = sweep(steps=args.steps, gx=gx, dts=tuple(args.dts))
+        res["wall_s"] = time.time() - t0
+        results.append(res)
+        for r in res["rows"]:
+            print(f"gx={gx:g} dt={r['dt_fd']:3d} {r['precision']}/{r['storage']}/{'s' if r['shifted'] else 'p'}: "
+                  f"{r['mlups']:9.1f} MLUPS  eps_u {r['eps_u']:.3e}  relL2 n {r['rel_l2_n']:.3e}  "
+                  f"centroid shift {r['centroid_shift']:.3e}")
+    if args.out:
+        with open(args.out, "w") as f:
+            json.dump(results, f, indent=1)
+
+
+if __name__ == "__main__":
+    main()

@@ -440,3 +440,25 @@ def test_batch_of_65_channels_spans_two_launch_groups(nh):
     ref = single.get_fields()[1]
     for c in (chans[0], chans[63], chans[64]):
         assert np.allclose(c.get_fields()[1], ref, rtol=1e-6, atol=1e-12)
+
+
+@pytest.mark.parametrize("anchoring", ["homeotropic", "none"])
+def test_relax_matches_oracle_gradient_flow(nh, oracle_mod, anchoring):
+    """Director-only relaxation = predictor-corrector at u = 0 (FP64 <= 1e-12)."""
+    O = oracle_mod
+    params = _generic(16, 12, 8, dt_fd=5, K=0.01, W0=0.002, anchoring=anchoring)
+    n0 = I.skyrmion_tubes(16, 12, 8, [(8.0, 6.0)], 5.0)
+    p = O.OracleParams.from_dict(params)
+    n = n0.copy()
+    u = np.zeros_like(n0)
+    for _ in range(12):
+        n = O.fd_step(p, n, u)
+    ch = _channel(nh, params, n0, I.random_velocity(16, 12, 8, 1e-3, seed=1), precision="fp64")
+    ch.relax(12)
+    ng, ug, _ = ch.get_fields()
+    assert O.rel_l2(ng, n) < 1e-12
+    assert np.max(np.abs(ug)) == 0.0
+    chans = [_channel(nh, params, n0, precision="fp64") for _ in range(3)]
+    nh.batch_relax(chans, 12)
+    for c in chans:
+        assert O.rel_l2(c.get_fields()[0], n) < 1e-12
