@@ -295,6 +295,41 @@ int nh_set_graphs(nh_ctx* ctx, int on);
 int nh_diagnostics_noalloc(const nh_params* p, const void* f, const void* n, const void* u, const void* rho,
                            double* out, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Learned warm start (spec axis 4): a 3D U-Net (4 levels, widths
+ * 16/16/32/64, 394 419 parameters) that maps the extruded skyrmion ansatz and
+ * the channel parameters (q0, Lz, W0) to the relaxed director; the plain
+ * relaxation (nh_relax) continues from its prediction and judges it.
+ * Activations are BF16, accumulation FP32, convolutions run on the tensor
+ * cores; parameters, gradients and Adam moments are caller-owned FP32 device
+ * vectors in the layout: per conv layer W[tap][cout][cin] (tap = 9 kz + 3 ky
+ * + kx, offsets -1..1) then bias[cout], layers enc1a enc1b enc2a enc2b enc3a
+ * enc3b bota botb dec3a dec3b dec2a dec2b dec1a dec1b, then the head
+ * W[3][16], bias[3].  Convolutions are periodic in x, y and zero-padded in z.
+ * Fields are FP32 device arrays [batch][3][nx*ny*nz] (site order as above);
+ * scalars [batch][3] = (q0, Lz, W0). */
+typedef struct nh_unet nh_unet;
+int64_t nh_unet_param_count(void);
+/* A network instance for batch x nx x ny x nz inputs (nx, ny multiples of 8,
+ * >= 16; nz a multiple of 8).  Its device workspace is caller-owned. */
+int nh_unet_create(int batch, int nx, int ny, int nz, nh_unet** out);
+int nh_unet_workspace_bytes(const nh_unet* net, size_t* bytes);
+int nh_unet_bind(nh_unet* net, void* dev_ptr, size_t bytes);
+/* Refresh the BF16 (and transposed BF16) weight copies from the FP32 params;
+ * call after every parameter change. */
+int nh_unet_set_params(nh_unet* net, const float* params, void* stream);
+/* Forward pass; keeps the activations for nh_unet_backward.  n_out may be NULL. */
+int nh_unet_forward(nh_unet* net, const float* params, const float* n_ansatz, const float* scalars, float* n_out,
+                    void* stream);
+/* Loss mean |n - target|^2 over all sites into *loss (device float) and its
+ * gradient with respect to the parameters into grad (overwritten), for the
+ * activations of the last forward pass. */
+int nh_unet_backward(nh_unet* net, const float* params, const float* n_ansatz, const float* target, float* grad,
+                     float* loss, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected, step >= 1). */
+int nh_unet_adam(float* params, const float* grad, float* m, float* v, int64_t count, int step, float lr, void* stream);
+void nh_unet_destroy(nh_unet* net);
+
 /* Release the context (NULL-safe).  Does not free the caller's workspace. */
 void nh_destroy(nh_ctx* ctx);
 

@@ -1,0 +1,882 @@
+// wsnet.cu -- the learned warm start: a 3D U-Net that maps the extruded
+// skyrmion-tube ansatz (plus q0, Lz, W0) to the relaxed director field, with
+// hand-written BF16 training and inference kernels (FP32 accumulation).
+//
+// Network (4 levels, widths 16/16/32/64, 394 419 parameters): two 3x3x3
+// convolutions + ReLU per level, 2x2x2 mean pooling down, nearest x2 upsampling
+// and channel concatenation up, a 1x1x1 head 16 -> 3 whose output corrects the
+// ansatz, n = normalise(n_ansatz + delta).  Convolutions are cross-correlations,
+// periodic in x and y and zero-padded in z.
+//
+// Layouts: activations are channels-last BF16 [batch][z][y][x][c]; activation
+// gradients are channels-last FP32.  Parameters are one flat FP32 vector, layer
+// by layer W[tap][cout][cin] (tap = 9 kz + 3 ky + kx) then bias[cout]; the head
+// is W[3][16] then bias[3].
+//
+// Convolutions run on the tensor cores as implicit GEMMs with
+// mma.sync.m16n8k16 (BF16 inputs, FP32 accumulators):
+//   forward       M = voxels (16 per warp), N = cout, K = 27 taps x cin
+//   data grad     M = voxels, N = cin, K = 27 taps x cout (transposed weights)
+//   weight grad   M = cout, N = cin, K = voxels (per tap; shared-memory tiles,
+//                 FP32 atomics across voxel chunks)
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "nh_internal.cuh"
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+// ------------------------------------------------------------------ architecture
+
+struct LayerDesc {
+    int cin, cout;
+};
+constexpr int kLayers = 14;
+constexpr LayerDesc kConv[kLayers] = {{16, 16}, {16, 16}, {16, 16}, {16, 16}, {16, 32}, {32, 32}, {32, 64},
+                                      {64, 64}, {96, 32}, {32, 32}, {48, 16}, {16, 16}, {32, 16}, {16, 16}};
+enum { ENC1A, ENC1B, ENC2A, ENC2B, ENC3A, ENC3B, BOTA, BOTB, DEC3A, DEC3B, DEC2A, DEC2B, DEC1A, DEC1B };
+constexpr int kHeadIn = 16, kHeadOut = 3, kInCh = 16;
+
+int64_t layer_offset(int l)
+{
+    int64_t off = 0;
+    for (int k = 0; k < l; ++k) off += 27LL * kConv[k].cin * kConv[k].cout + kConv[k].cout;
+    return off;
+}
+int64_t head_offset() { return layer_offset(kLayers); }
+int64_t total_params() { return head_offset() + kHeadIn * kHeadOut + kHeadOut; }
+
+// ------------------------------------------------------------------ device helpers
+
+__device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], const uint32_t b[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ uint32_t ld_pair(const bf16* p) { return __ldg(reinterpret_cast<const unsigned int*>(p)); }
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ uint32_t pack_raw(bf16 lo, bf16 hi)
+{
+    __nv_bfloat162 v;
+    v.x = lo;
+    v.y = hi;
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+struct Dims {
+    int nx, ny, nz, nvox, batch;
+};
+
+// Voxel index of v shifted by (dx, dy, dz), periodic in x, y; -1 outside in z.
+__device__ __forceinline__ int shifted(const Dims& d, int v, int dx, int dy, int dz)
+{
+    const int b = v / d.nvox;
+    const int r = v - b * d.nvox;
+    const int x = r % d.nx;
+    const int t = r / d.nx;
+    const int y = t % d.ny;
+    const int z = t / d.ny;
+    const int zs = z + dz;
+    if (zs < 0 || zs >= d.nz) return -1;
+    int xs = x + dx, ys = y + dy;
+    xs = xs < 0 ? xs + d.nx : (xs >= d.nx ? xs - d.nx : xs);
+    ys = ys < 0 ? ys + d.ny : (ys >= d.ny ? ys - d.ny : ys);
+    return b * d.nvox + xs + d.nx * (ys + d.ny * zs);
+}
+
+// ------------------------------------------------------------------ convolution: forward
+
+struct ConvFwd {
+    const bf16* src1;
+    int c1;
+    const bf16* src2;  // concatenated after src1 (may be null, c2 = 0)
+    int c2;
+    const bf16* w;     // [27][cout][cin]
+    const float* bias; // [cout]
+    bf16* dst;         // [vox][cout]
+    Dims d;
+    int relu;
+};
+
+template <int COUT>
+__global__ void __launch_bounds__(128) conv_fwd_kernel(const ConvFwd a)
+{
+    const int lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int total = a.d.nvox * a.d.batch;
+    const int v0 = tile * 16;
+    if (v0 >= total) return;
+    const int cin = a.c1 + a.c2;
+    const int vA = v0 + g, vB = v0 + g + 8;
+    float acc[COUT / 8][4];
+#pragma unroll
+    for (int j = 0; j < COUT / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    for (int tap = 0; tap < 27; ++tap) {
+        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+        const int sA = shifted(a.d, vA, dx, dy, dz);
+        const int sB = shifted(a.d, vB, dx, dy, dz);
+        const bf16* wt = a.w + (size_t)tap * COUT * cin;
+        for (int c = 0; c < cin; c += 16) {
+            const bool first = c < a.c1;
+            const bf16* base = first ? a.src1 : a.src2;
+            const int cs = first ? a.c1 : a.c2;
+            const int co = first ? c : c - a.c1;
+            uint32_t fa[4];
+            fa[0] = sA >= 0 ? ld_pair(base + (size_t)sA * cs + co + 2 * t) : 0u;
+            fa[1] = sB >= 0 ? ld_pair(base + (size_t)sB * cs + co + 2 * t) : 0u;
+            fa[2] = sA >= 0 ? ld_pair(base + (size_t)sA * cs + co + 8 + 2 * t) : 0u;
+            fa[3] = sB >= 0 ? ld_pair(base + (size_t)sB * cs + co + 8 + 2 * t) : 0u;
+#pragma unroll
+            for (int j = 0; j < COUT / 8; ++j) {
+                const bf16* wr = wt + (size_t)(j * 8 + g) * cin + c;
+                const uint32_t fb[2] = {ld_pair(wr + 2 * t), ld_pair(wr + 8 + 2 * t)};
+                mma16816(acc[j], fa, fb);
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < COUT / 8; ++j) {
+        const int co = j * 8 + 2 * t;
+        const float b0 = a.bias[co], b1 = a.bias[co + 1];
+        float r0 = acc[j][0] + b0, r1 = acc[j][1] + b1, r2 = acc[j][2] + b0, r3 = acc[j][3] + b1;
+        if (a.relu) {
+            r0 = fmaxf(r0, 0.f);
+            r1 = fmaxf(r1, 0.f);
+            r2 = fmaxf(r2, 0.f);
+            r3 = fmaxf(r3, 0.f);
+        }
+        *reinterpret_cast<uint32_t*>(a.dst + (size_t)vA * COUT + co) = pack_bf16(r0, r1);
+        *reinterpret_cast<uint32_t*>(a.dst + (size_t)vB * COUT + co) = pack_bf16(r2, r3);
+    }
+}
+
+// ------------------------------------------------------------------ convolution: data gradient
+
+struct ConvBwdData {
+    const float* gout;  // [vox][cout] gradient of the layer output (post-ReLU)
+    const bf16* out;    // [vox][cout] layer output, for the ReLU mask
+    const bf16* wt;     // [27][cin][cout] transposed weights
+    float* dst1;        // [vox][c1] gradient of source 1 (overwritten)
+    int c1;
+    float* dst2;        // [vox][c2] gradient of source 2 (accumulated)
+    int c2;
+    int cout;
+    Dims d;
+    int relu;
+};
+
+template <int CIN>
+__global__ void __launch_bounds__(128) conv_bwd_data_kernel(const ConvBwdData a)
+{
+    const int lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int total = a.d.nvox * a.d.batch;
+    const int v0 = tile * 16;
+    if (v0 >= total) return;
+    const int vA = v0 + g, vB = v0 + g + 8;
+    const int cout = a.cout;
+    float acc[CIN / 8][4];
+#pragma unroll
+    for (int j = 0; j < CIN / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    for (int tap = 0; tap < 27; ++tap) {
+        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+        // the output voxel that reads v through this tap sits at v - offset
+        const int sA = shifted(a.d, vA, -dx, -dy, -dz);
+        const int sB = shifted(a.d, vB, -dx, -dy, -dz);
+        const bf16* wt = a.wt + (size_t)tap * CIN * cout;
+        for (int c = 0; c < cout; c += 16) {
+            uint32_t fa[4];
+            const int cols[4] = {c + 2 * t, c + 2 * t, c + 8 + 2 * t, c + 8 + 2 * t};
+            const int src[4] = {sA, sB, sA, sB};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float g0 = 0.f, g1 = 0.f;
+                if (src[q] >= 0) {
+                    const size_t o = (size_t)src[q] * cout + cols[q];
+                    const float2 gv = *reinterpret_cast<const float2*>(a.gout + o);
+                    g0 = gv.x;
+                    g1 = gv.y;
+                    if (a.relu) {
+                        const __nv_bfloat162 y = *reinterpret_cast<const __nv_bfloat162*>(a.out + o);
+                        g0 = __bfloat162float(y.x) > 0.f ? g0 : 0.f;
+                        g1 = __bfloat162float(y.y) > 0.f ? g1 : 0.f;
+                    }
+                }
+                fa[q] = pack_bf16(g0, g1);
+            }
+#pragma unroll
+            for (int j = 0; j < CIN / 8; ++j) {
+                const bf16* wr = wt + (size_t)(j * 8 + g) * cout + c;
+                const uint32_t fb[2] = {ld_pair(wr + 2 * t), ld_pair(wr + 8 + 2 * t)};
+                mma16816(acc[j], fa, fb);
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < CIN / 8; ++j) {
+        const int ci = j * 8 + 2 * t;
+        const float r[4] = {acc[j][0], acc[j][1], acc[j][2], acc[j][3]};
+        const int vv[2] = {vA, vB};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            for (int e = 0; e < 2; ++e) {
+                const int cc = ci + e;
+                const float val = r[2 * h + e];
+                if (cc < a.c1)
+                    a.dst1[(size_t)vv[h] * a.c1 + cc] = val;
+                else
+                    a.dst2[(size_t)vv[h] * a.c2 + (cc - a.c1)] += val;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ convolution: weight gradient
+
+struct ConvBwdW {
+    const float* gout;  // [vox][cout]
+    const bf16* out;    // [vox][cout] for the ReLU mask
+    const bf16* src1;   // [vox][c1]
+    int c1;
+    const bf16* src2;   // [vox][c2]
+    int c2;
+    int cout;
+    float* gw;          // [27][cout][cin] (accumulated)
+    Dims d;
+    int relu;
+    int chunk;          // voxels per block
+};
+
+constexpr int kWChunkSub = 32;  // voxels staged per shared-memory round
+
+// grid = (voxel chunks, 27 taps); 8 warps share the (cout/16) x (cin/8) tiles.
+__global__ void __launch_bounds__(256) conv_bwd_w_kernel(const ConvBwdW a)
+{
+    extern __shared__ unsigned char smem_raw[];
+    const int cin = a.c1 + a.c2;
+    const int cout = a.cout;
+    bf16* Gs = reinterpret_cast<bf16*>(smem_raw);  // [kWChunkSub][cout]
+    bf16* Xs = Gs + kWChunkSub * cout;              // [kWChunkSub][cin]
+    const int tap = blockIdx.y;
+    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+    const int total = a.d.nvox * a.d.batch;
+    const int vbeg = blockIdx.x * a.chunk;
+    const int vend = min(vbeg + a.chunk, total);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int mt = cout / 16, nt = cin / 8, tiles = mt * nt;
+    constexpr int kMaxTiles = 6;  // per warp: up to 48 tiles / 8 warps (cout 64 x cin 96 -> 4 x 12)
+    float acc[kMaxTiles][4];
+#pragma unroll
+    for (int k = 0; k < kMaxTiles; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0.f;
+    for (int s0 = vbeg; s0 < vend; s0 += kWChunkSub) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < kWChunkSub * cout; e += blockDim.x) {
+            const int r = e / cout, col = e - r * cout;
+            const int v = s0 + r;
+            float gv = 0.f;
+            if (v < vend) {
+                gv = a.gout[(size_t)v * cout + col];
+                if (a.relu && !(__bfloat162float(a.out[(size_t)v * cout + col]) > 0.f)) gv = 0.f;
+            }
+            Gs[e] = __float2bfloat16_rn(gv);
+        }
+        for (int e = threadIdx.x; e < kWChunkSub * cin; e += blockDim.x) {
+            const int r = e / cin, col = e - r * cin;
+            const int v = s0 + r;
+            bf16 xv = __float2bfloat16_rn(0.f);
+            if (v < vend) {
+                const int sv = shifted(a.d, v, dx, dy, dz);
+                if (sv >= 0)
+                    xv = col < a.c1 ? a.src1[(size_t)sv * a.c1 + col] : a.src2[(size_t)sv * a.c2 + (col - a.c1)];
+            }
+            Xs[e] = xv;
+        }
+        __syncthreads();
+        for (int kk = 0; kk < kWChunkSub; kk += 16) {
+#pragma unroll
+            for (int q = 0; q < kMaxTiles; ++q) {
+                const int tile = warp + 8 * q;
+                if (tile >= tiles) break;
+                const int m0 = (tile / nt) * 16, n0 = (tile % nt) * 8;
+                // A[co][v] = G[v][co]; B[v][ci] = X[v][ci]
+                uint32_t fa[4], fb[2];
+                fa[0] = pack_raw(Gs[(kk + 2 * t) * cout + m0 + g], Gs[(kk + 2 * t + 1) * cout + m0 + g]);
+                fa[1] = pack_raw(Gs[(kk + 2 * t) * cout + m0 + g + 8], Gs[(kk + 2 * t + 1) * cout + m0 + g + 8]);
+                fa[2] = pack_raw(Gs[(kk + 8 + 2 * t) * cout + m0 + g], Gs[(kk + 9 + 2 * t) * cout + m0 + g]);
+                fa[3] = pack_raw(Gs[(kk + 8 + 2 * t) * cout + m0 + g + 8], Gs[(kk + 9 + 2 * t) * cout + m0 + g + 8]);
+                fb[0] = pack_raw(Xs[(kk + 2 * t) * cin + n0 + g], Xs[(kk + 2 * t + 1) * cin + n0 + g]);
+                fb[1] = pack_raw(Xs[(kk + 8 + 2 * t) * cin + n0 + g], Xs[(kk + 9 + 2 * t) * cin + n0 + g]);
+                mma16816(acc[q], fa, fb);
+            }
+        }
+    }
+    float* gw = a.gw + (size_t)tap * cout * cin;
+#pragma unroll
+    for (int q = 0; q < kMaxTiles; ++q) {
+        const int tile = warp + 8 * q;
+        if (tile >= tiles) break;
+        const int m0 = (tile / nt) * 16, n0 = (tile % nt) * 8;
+        atomicAdd(&gw[(size_t)(m0 + g) * cin + n0 + 2 * t], acc[q][0]);
+        atomicAdd(&gw[(size_t)(m0 + g) * cin + n0 + 2 * t + 1], acc[q][1]);
+        atomicAdd(&gw[(size_t)(m0 + g + 8) * cin + n0 + 2 * t], acc[q][2]);
+        atomicAdd(&gw[(size_t)(m0 + g + 8) * cin + n0 + 2 * t + 1], acc[q][3]);
+    }
+}
+
+// bias gradient: gb[co] += sum_v G'[v][co]
+__global__ void bias_grad_kernel(const float* __restrict__ gout, const bf16* __restrict__ out, float* gb, int cout,
+                                 int total, int relu)
+{
+    const int co = threadIdx.x % cout;
+    const int lanes = blockDim.x / cout;
+    float s = 0.f;
+    for (int v = blockIdx.x * lanes + threadIdx.x / cout; v < total; v += gridDim.x * lanes) {
+        float gv = gout[(size_t)v * cout + co];
+        if (relu && !(__bfloat162float(out[(size_t)v * cout + co]) > 0.f)) gv = 0.f;
+        s += gv;
+    }
+    if (threadIdx.x < lanes * cout) atomicAdd(&gb[co], s);
+}
+
+// ------------------------------------------------------------------ pooling / upsampling
+
+// dst (coarse) = mean of the 2x2x2 children in src (fine), channels-last, C channels
+__global__ void pool_fwd_kernel(const bf16* __restrict__ src, bf16* __restrict__ dst, Dims fine, int C)
+{
+    const int cx = fine.nx / 2, cy = fine.ny / 2, cz = fine.nz / 2, cvox = cx * cy * cz;
+    const int64_t total = (int64_t)cvox * fine.batch * C;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const int64_t v = i / C;
+        const int b = (int)(v / cvox);
+        const int r = (int)(v - (int64_t)b * cvox);
+        const int x = r % cx, y = (r / cx) % cy, z = r / (cx * cy);
+        float s = 0.f;
+        for (int k = 0; k < 8; ++k) {
+            const int fx = 2 * x + (k & 1), fy = 2 * y + ((k >> 1) & 1), fz = 2 * z + (k >> 2);
+            s += __bfloat162float(src[((size_t)b * fine.nvox + fx + fine.nx * (fy + fine.ny * fz)) * C + c]);
+        }
+        dst[(size_t)v * C + c] = __float2bfloat16_rn(0.125f * s);
+    }
+}
+
+// gsrc (fine) += gdst (coarse) / 8
+__global__ void pool_bwd_kernel(const float* __restrict__ gdst, float* __restrict__ gsrc, Dims fine, int C)
+{
+    const int cx = fine.nx / 2, cy = fine.ny / 2;
+    const int64_t total = (int64_t)fine.nvox * fine.batch * C;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const int64_t v = i / C;
+        const int b = (int)(v / fine.nvox);
+        const int r = (int)(v - (int64_t)b * fine.nvox);
+        const int x = r % fine.nx, y = (r / fine.nx) % fine.ny, z = r / (fine.nx * fine.ny);
+        const size_t cv = (size_t)b * (fine.nvox / 8) + x / 2 + cx * (y / 2 + cy * (z / 2));
+        gsrc[i] += 0.125f * gdst[cv * C + c];
+    }
+}
+
+// dst (fine) = src (coarse) nearest
+__global__ void up_fwd_kernel(const bf16* __restrict__ src, bf16* __restrict__ dst, Dims fine, int C)
+{
+    const int cx = fine.nx / 2, cy = fine.ny / 2;
+    const int64_t total = (int64_t)fine.nvox * fine.batch * C;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const int64_t v = i / C;
+        const int b = (int)(v / fine.nvox);
+        const int r = (int)(v - (int64_t)b * fine.nvox);
+        const int x = r % fine.nx, y = (r / fine.nx) % fine.ny, z = r / (fine.nx * fine.ny);
+        const size_t cv = (size_t)b * (fine.nvox / 8) + x / 2 + cx * (y / 2 + cy * (z / 2));
+        dst[i] = src[cv * C + c];
+    }
+}
+
+// gsrc (coarse) = sum of gdst over the 8 children (overwrites)
+__global__ void up_bwd_kernel(const float* __restrict__ gdst, float* __restrict__ gsrc, Dims fine, int C)
+{
+    const int cx = fine.nx / 2, cy = fine.ny / 2, cz = fine.nz / 2, cvox = cx * cy * cz;
+    const int64_t total = (int64_t)cvox * fine.batch * C;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const int64_t v = i / C;
+        const int b = (int)(v / cvox);
+        const int r = (int)(v - (int64_t)b * cvox);
+        const int x = r % cx, y = (r / cx) % cy, z = r / (cx * cy);
+        float s = 0.f;
+        for (int k = 0; k < 8; ++k) {
+            const int fx = 2 * x + (k & 1), fy = 2 * y + ((k >> 1) & 1), fz = 2 * z + (k >> 2);
+            s += gdst[((size_t)b * fine.nvox + fx + fine.nx * (fy + fine.ny * fz)) * C + c];
+        }
+        gsrc[i] = s;
+    }
+}
+
+// ------------------------------------------------------------------ input, head, loss, optimiser
+
+// x[v][0..2] = n_ansatz, x[v][3] = q0 Lz / 2 pi, [4] = Lz / 32, [5] = W0 / 1e-3, rest 0.
+__global__ void input_kernel(const float* __restrict__ n, const float* __restrict__ scal, bf16* __restrict__ x, Dims d)
+{
+    const int total = d.nvox * d.batch;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < total; v += gridDim.x * blockDim.x) {
+        const int b = v / d.nvox, r = v - b * d.nvox;
+        const float* nb = n + (size_t)b * 3 * d.nvox;
+        float vals[kInCh];
+        for (int c = 0; c < kInCh; ++c) vals[c] = 0.f;
+        vals[0] = nb[r];
+        vals[1] = nb[d.nvox + r];
+        vals[2] = nb[2 * d.nvox + r];
+        const float q0 = scal[3 * b], lz = scal[3 * b + 1], w0 = scal[3 * b + 2];
+        vals[3] = q0 * lz / 6.283185307179586f;
+        vals[4] = lz / 32.f;
+        vals[5] = w0 / 1e-3f;
+        uint32_t* dst = reinterpret_cast<uint32_t*>(x + (size_t)v * kInCh);
+        for (int c = 0; c < kInCh; c += 2) dst[c / 2] = pack_bf16(vals[c], vals[c + 1]);
+    }
+}
+
+// Head (1x1x1 conv 16 -> 3), residual on the ansatz, normalisation; optionally
+// the loss mean |n - target|^2 and the gradients of d1, W_head, b_head.
+__global__ void __launch_bounds__(256) head_kernel(const bf16* __restrict__ d1, const float* __restrict__ n_ans,
+                                                   const float* __restrict__ params_head, float* __restrict__ n_out,
+                                                   const float* __restrict__ target, float* __restrict__ g_d1,
+                                                   float* __restrict__ g_head, float* __restrict__ loss, Dims d)
+{
+    __shared__ float sh[kHeadOut * kHeadIn + kHeadOut];
+    __shared__ float red[kHeadOut * kHeadIn + kHeadOut + 1][8];
+    for (int k = threadIdx.x; k < kHeadOut * kHeadIn + kHeadOut; k += blockDim.x) sh[k] = params_head[k];
+    __syncthreads();
+    const int total = d.nvox * d.batch;
+    const float inv_total = 1.f / (float)total;
+    float gacc[kHeadOut * kHeadIn + kHeadOut + 1];
+    for (int k = 0; k < kHeadOut * kHeadIn + kHeadOut + 1; ++k) gacc[k] = 0.f;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < total; v += gridDim.x * blockDim.x) {
+        const int b = v / d.nvox, r = v - b * d.nvox;
+        float h[kHeadIn];
+        for (int c = 0; c < kHeadIn; ++c) h[c] = __bfloat162float(d1[(size_t)v * kHeadIn + c]);
+        float vv[3];
+        for (int o = 0; o < 3; ++o) {
+            float s = sh[kHeadOut * kHeadIn + o];
+            for (int c = 0; c < kHeadIn; ++c) s += sh[o * kHeadIn + c] * h[c];
+            vv[o] = n_ans[(size_t)b * 3 * d.nvox + o * d.nvox + r] + s;
+        }
+        const float len = sqrtf(vv[0] * vv[0] + vv[1] * vv[1] + vv[2] * vv[2]);
+        const float nn[3] = {vv[0] / len, vv[1] / len, vv[2] / len};
+        if (n_out)
+            for (int o = 0; o < 3; ++o) n_out[(size_t)b * 3 * d.nvox + o * d.nvox + r] = nn[o];
+        if (target) {
+            float gn[3], dot = 0.f, l = 0.f;
+            for (int o = 0; o < 3; ++o) {
+                const float diff = nn[o] - target[(size_t)b * 3 * d.nvox + o * d.nvox + r];
+                l += diff * diff;
+                gn[o] = 2.f * diff * inv_total;
+                dot += gn[o] * nn[o];
+            }
+            gacc[kHeadOut * kHeadIn + kHeadOut] += l * inv_total;
+            float gd[3];
+            for (int o = 0; o < 3; ++o) gd[o] = (gn[o] - dot * nn[o]) / len;  // d/dv of v/|v|
+            for (int c = 0; c < kHeadIn; ++c) {
+                float s = 0.f;
+                for (int o = 0; o < 3; ++o) {
+                    s += sh[o * kHeadIn + c] * gd[o];
+                    gacc[o * kHeadIn + c] += gd[o] * h[c];
+                }
+                g_d1[(size_t)v * kHeadIn + c] = s;
+            }
+            for (int o = 0; o < 3; ++o) gacc[kHeadOut * kHeadIn + o] += gd[o];
+        }
+    }
+    if (!target) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 0; k < kHeadOut * kHeadIn + kHeadOut + 1; ++k) {
+        float s = gacc[k];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[k][warp] = s;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kHeadOut * kHeadIn + kHeadOut + 1; k += blockDim.x) {
+        float s = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[k][w];
+        if (k < kHeadOut * kHeadIn + kHeadOut)
+            atomicAdd(&g_head[k], s);
+        else
+            atomicAdd(loss, s);
+    }
+}
+
+__global__ void cast_params_kernel(const float* __restrict__ p, bf16* __restrict__ w, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        w[i] = __float2bfloat16_rn(p[i]);
+}
+
+// wt[tap][ci][co] = w[tap][co][ci]
+__global__ void transpose_kernel(const float* __restrict__ p, bf16* __restrict__ wt, int cin, int cout)
+{
+    const int n = 27 * cin * cout;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int tap = i / (cin * cout);
+        const int r = i - tap * cin * cout;
+        const int ci = r / cout, co = r - ci * cout;
+        wt[i] = __float2bfloat16_rn(p[(size_t)tap * cout * cin + (size_t)co * cin + ci]);
+    }
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1,
+                            float c2)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+inline int grid_for(int64_t n, int threads = 256)
+{
+    int64_t b = (n + threads - 1) / threads;
+    return (int)(b > 4096 ? 4096 : b);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ network runner
+
+struct nh_unet {
+    Dims lv[4];           // level dims (fine to coarse)
+    int batch;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    size_t need = 0;
+    // offsets into the workspace
+    size_t wbf, wt[kLayers], x, act[kLayers], pool_[3], up_[3], grad_a, grad_b, grad_skip[3], gd1;
+    std::string err;
+};
+
+namespace {
+
+int unet_fail(nh_unet* u, int code, const std::string& m)
+{
+    if (u) u->err = m;
+    nh::set_global_error(m);
+    return code;
+}
+
+size_t al(size_t v) { return (v + 255) / 256 * 256; }
+
+void plan(nh_unet* u)
+{
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        size_t o = off;
+        off += al(b);
+        return o;
+    };
+    const int64_t P = total_params();
+    u->wbf = take(P * sizeof(bf16));
+    for (int l = 0; l < kLayers; ++l) u->wt[l] = take(27 * (size_t)kConv[l].cin * kConv[l].cout * sizeof(bf16));
+    const size_t V0 = (size_t)u->lv[0].nvox * u->batch;
+    u->x = take(V0 * kInCh * sizeof(bf16));
+    const int level_of[kLayers] = {0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0};
+    for (int l = 0; l < kLayers; ++l)
+        u->act[l] = take((size_t)u->lv[level_of[l]].nvox * u->batch * kConv[l].cout * sizeof(bf16));
+    // pooled inputs of levels 1..3 and upsampled inputs of decoder levels 2..0
+    const int pool_c[3] = {16, 16, 32};
+    for (int k = 0; k < 3; ++k) u->pool_[k] = take((size_t)u->lv[k + 1].nvox * u->batch * pool_c[k] * sizeof(bf16));
+    const int up_c[3] = {64, 32, 16};
+    for (int k = 0; k < 3; ++k) u->up_[k] = take((size_t)u->lv[2 - k].nvox * u->batch * up_c[k] * sizeof(bf16));
+    // gradient scratch: two ping-pong buffers large enough for any [vox][96] level-0..3 tensor,
+    // three skip-gradient buffers (e1, e2, e3) and the head-input gradient
+    size_t gmax = 0;
+    for (int k = 0; k < 4; ++k) gmax = std::max(gmax, (size_t)u->lv[k].nvox * u->batch * 96);
+    u->grad_a = take(gmax * sizeof(float));
+    u->grad_b = take(gmax * sizeof(float));
+    const int skip_c[3] = {16, 16, 32};
+    for (int k = 0; k < 3; ++k) u->grad_skip[k] = take((size_t)u->lv[k].nvox * u->batch * skip_c[k] * sizeof(float));
+    u->gd1 = take(V0 * kHeadIn * sizeof(float));
+    u->need = off;
+}
+
+template <typename T>
+T* P(nh_unet* u, size_t off)
+{
+    return reinterpret_cast<T*>(u->ws + off);
+}
+
+cudaError_t conv_fwd(nh_unet* u, int l, int level, const bf16* s1, int c1, const bf16* s2, int c2,
+                     const float* params, cudaStream_t st)
+{
+    ConvFwd a;
+    a.src1 = s1;
+    a.c1 = c1;
+    a.src2 = s2;
+    a.c2 = c2;
+    a.w = P<bf16>(u, u->wbf) + layer_offset(l);
+    a.bias = params + layer_offset(l) + 27LL * kConv[l].cin * kConv[l].cout;
+    a.dst = P<bf16>(u, u->act[l]);
+    a.d = u->lv[level];
+    a.relu = 1;
+    const int tiles = a.d.nvox * a.d.batch / 16;
+    const int blocks = (tiles + 3) / 4;
+    switch (kConv[l].cout) {
+    case 16: conv_fwd_kernel<16><<<blocks, 128, 0, st>>>(a); break;
+    case 32: conv_fwd_kernel<32><<<blocks, 128, 0, st>>>(a); break;
+    default: conv_fwd_kernel<64><<<blocks, 128, 0, st>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+// Backward of conv layer l: gout (FP32 [vox][cout]) -> data gradient into
+// dst1 (c1 channels, overwritten) and dst2 (c2, accumulated); weight and bias
+// gradients accumulated into grad.
+cudaError_t conv_bwd(nh_unet* u, int l, int level, const float* gout, const bf16* s1, int c1, const bf16* s2, int c2,
+                     float* dst1, float* dst2, float* grad, bool need_data, cudaStream_t st)
+{
+    const Dims d = u->lv[level];
+    const int total = d.nvox * d.batch;
+    const int cout = kConv[l].cout, cin = kConv[l].cin;
+    const bf16* out = P<bf16>(u, u->act[l]);
+    ConvBwdW w;
+    w.gout = gout;
+    w.out = out;
+    w.src1 = s1;
+    w.c1 = c1;
+    w.src2 = s2;
+    w.c2 = c2;
+    w.cout = cout;
+    w.gw = grad + layer_offset(l);
+    w.d = d;
+    w.relu = 1;
+    w.chunk = 1024;
+    dim3 grid((total + w.chunk - 1) / w.chunk, 27);
+    const size_t smem = (size_t)kWChunkSub * (cin + cout) * sizeof(bf16);
+    conv_bwd_w_kernel<<<grid, 256, smem, st>>>(w);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    bias_grad_kernel<<<std::min(64, grid_for(total / 8, 256)), 256, 0, st>>>(
+        gout, out, grad + layer_offset(l) + 27LL * cin * cout, cout, total, 1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || !need_data) return e;
+    ConvBwdData b;
+    b.gout = gout;
+    b.out = out;
+    b.wt = P<bf16>(u, u->wt[l]);
+    b.dst1 = dst1;
+    b.c1 = c1;
+    b.dst2 = dst2;
+    b.c2 = c2;
+    b.cout = cout;
+    b.d = d;
+    b.relu = 1;
+    const int blocks = (total / 16 + 3) / 4;
+    switch (cin) {
+    case 16: conv_bwd_data_kernel<16><<<blocks, 128, 0, st>>>(b); break;
+    case 32: conv_bwd_data_kernel<32><<<blocks, 128, 0, st>>>(b); break;
+    case 48: conv_bwd_data_kernel<48><<<blocks, 128, 0, st>>>(b); break;
+    case 64: conv_bwd_data_kernel<64><<<blocks, 128, 0, st>>>(b); break;
+    default: conv_bwd_data_kernel<96><<<blocks, 128, 0, st>>>(b); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+#define UNET_CUDA(u, ...)                                                                      \
+    do {                                                                                       \
+        cudaError_t e_ = (__VA_ARGS__);                                                        \
+        if (e_ != cudaSuccess) return unet_fail((u), NH_ECUDA, std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+extern "C" {
+
+int64_t nh_unet_param_count(void) { return total_params(); }
+
+int nh_unet_create(int batch, int nx, int ny, int nz, nh_unet** out)
+{
+    if (!out) return unet_fail(nullptr, NH_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (batch < 1 || nx < 16 || ny < 16 || nz < 8 || nx % 8 || ny % 8 || nz % 8)
+        return unet_fail(nullptr, NH_EINVAL, "batch >= 1; nx, ny multiples of 8 and >= 16; nz a multiple of 8");
+    if ((int64_t)nx * ny * nz * batch * 96 > 2000000000LL) return unet_fail(nullptr, NH_EINVAL, "problem too large");
+    nh_unet* u = new (std::nothrow) nh_unet();
+    if (!u) return unet_fail(nullptr, NH_ENOMEM, "host allocation failed");
+    u->batch = batch;
+    for (int k = 0; k < 4; ++k) {
+        const int s = 1 << k;
+        u->lv[k] = Dims{nx / s, ny / s, nz / s, (nx / s) * (ny / s) * (nz / s), batch};
+    }
+    if ((u->lv[3].nvox * batch) % 16) {
+        delete u;
+        return unet_fail(nullptr, NH_EINVAL, "the coarsest level must hold a multiple of 16 voxels");
+    }
+    plan(u);
+    *out = u;
+    return NH_OK;
+}
+
+int nh_unet_workspace_bytes(const nh_unet* u, size_t* bytes)
+{
+    if (!u || !bytes) return unet_fail(nullptr, NH_EINVAL, "NULL argument");
+    *bytes = u->need;
+    return NH_OK;
+}
+
+int nh_unet_bind(nh_unet* u, void* ws, size_t bytes)
+{
+    if (!u || !ws) return unet_fail(u, NH_EINVAL, "NULL argument");
+    if (reinterpret_cast<uintptr_t>(ws) % 256) return unet_fail(u, NH_EINVAL, "workspace must be 256-byte aligned");
+    if (bytes < u->need) return unet_fail(u, NH_ENOMEM, "workspace too small: need " + std::to_string(u->need));
+    u->ws = static_cast<char*>(ws);
+    u->ws_bytes = bytes;
+    return NH_OK;
+}
+
+int nh_unet_set_params(nh_unet* u, const float* params, void* stream)
+{
+    if (!u || !u->ws || !params) return unet_fail(u, NH_EINVAL, "unbound network or NULL params");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t n = total_params();
+    cast_params_kernel<<<grid_for(n), 256, 0, st>>>(params, P<bf16>(u, u->wbf), n);
+    UNET_CUDA(u, cudaGetLastError());
+    for (int l = 0; l < kLayers; ++l) {
+        transpose_kernel<<<grid_for(27LL * kConv[l].cin * kConv[l].cout), 256, 0, st>>>(
+            params + layer_offset(l), P<bf16>(u, u->wt[l]), kConv[l].cin, kConv[l].cout);
+        UNET_CUDA(u, cudaGetLastError());
+    }
+    return NH_OK;
+}
+
+int nh_unet_forward(nh_unet* u, const float* params, const float* n_ansatz, const float* scalars, float* n_out,
+                    void* stream)
+{
+    if (!u || !u->ws || !params || !n_ansatz || !scalars) return unet_fail(u, NH_EINVAL, "NULL argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const Dims d0 = u->lv[0];
+    input_kernel<<<grid_for((int64_t)d0.nvox * d0.batch), 256, 0, st>>>(n_ansatz, scalars, P<bf16>(u, u->x), d0);
+    UNET_CUDA(u, cudaGetLastError());
+    auto act = [&](int l) { return P<bf16>(u, u->act[l]); };
+    auto pool = [&](int k) { return P<bf16>(u, u->pool_[k]); };
+    auto upb = [&](int k) { return P<bf16>(u, u->up_[k]); };
+    UNET_CUDA(u, conv_fwd(u, ENC1A, 0, P<bf16>(u, u->x), 16, nullptr, 0, params, st));
+    UNET_CUDA(u, conv_fwd(u, ENC1B, 0, act(ENC1A), 16, nullptr, 0, params, st));
+    pool_fwd_kernel<<<grid_for((int64_t)u->lv[1].nvox * u->batch * 16), 256, 0, st>>>(act(ENC1B), pool(0), u->lv[0], 16);
+    UNET_CUDA(u, conv_fwd(u, ENC2A, 1, pool(0), 16, nullptr, 0, params, st));
+    UNET_CUDA(u, conv_fwd(u, ENC2B, 1, act(ENC2A), 16, nullptr, 0, params, st));
+    pool_fwd_kernel<<<grid_for((int64_t)u->lv[2].nvox * u->batch * 16), 256, 0, st>>>(act(ENC2B), pool(1), u->lv[1], 16);
+    UNET_CUDA(u, conv_fwd(u, ENC3A, 2, pool(1), 16, nullptr, 0, params, st));
+    UNET_CUDA(u, conv_fwd(u, ENC3B, 2, act(ENC3A), 32, nullptr, 0, params, st));
+    pool_fwd_kernel<<<grid_for((int64_t)u->lv[3].nvox * u->batch * 32), 256, 0, st>>>(act(ENC3B), pool(2), u->lv[2], 32);
+    UNET_CUDA(u, conv_fwd(u, BOTA, 3, pool(2), 32, nullptr, 0, params, st));
+    UNET_CUDA(u, conv_fwd(u, BOTB, 3, act(BOTA), 64, nullptr, 0, params, st));
+    up_fwd_kernel<<<grid_for((int64_t)u->lv[2].nvox * u->batch * 64), 256, 0, st>>>(act(BOTB), upb(0), u->lv[2], 64);
+    UNET_CUDA(u, conv_fwd(u, DEC3A, 2, upb(0), 64, act(ENC3B), 32, params, st));
+    UNET_CUDA(u, conv_fwd(u, DEC3B, 2, act(DEC3A), 32, nullptr, 0, params, st));
+    up_fwd_kernel<<<grid_for((int64_t)u->lv[1].nvox * u->batch * 32), 256, 0, st>>>(act(DEC3B), upb(1), u->lv[1], 32);
+    UNET_CUDA(u, conv_fwd(u, DEC2A, 1, upb(1), 32, act(ENC2B), 16, params, st));
+    UNET_CUDA(u, conv_fwd(u, DEC2B, 1, act(DEC2A), 16, nullptr, 0, params, st));
+    up_fwd_kernel<<<grid_for((int64_t)u->lv[0].nvox * u->batch * 16), 256, 0, st>>>(act(DEC2B), upb(2), u->lv[0], 16);
+    UNET_CUDA(u, conv_fwd(u, DEC1A, 0, upb(2), 16, act(ENC1B), 16, params, st));
+    UNET_CUDA(u, conv_fwd(u, DEC1B, 0, act(DEC1A), 16, nullptr, 0, params, st));
+    head_kernel<<<grid_for((int64_t)d0.nvox * d0.batch), 256, 0, st>>>(act(DEC1B), n_ansatz, params + head_offset(), n_out,
+                                                                        nullptr, nullptr, nullptr, nullptr, d0);
+    UNET_CUDA(u, cudaGetLastError());
+    return NH_OK;
+}
+
+int nh_unet_backward(nh_unet* u, const float* params, const float* n_ansatz, const float* target, float* grad,
+                     float* loss, void* stream)
+{
+    if (!u || !u->ws || !params || !n_ansatz || !target || !grad || !loss)
+        return unet_fail(u, NH_EINVAL, "NULL argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const Dims d0 = u->lv[0];
+    UNET_CUDA(u, cudaMemsetAsync(grad, 0, total_params() * sizeof(float), st));
+    UNET_CUDA(u, cudaMemsetAsync(loss, 0, sizeof(float), st));
+    auto act = [&](int l) { return P<bf16>(u, u->act[l]); };
+    auto pool = [&](int k) { return P<bf16>(u, u->pool_[k]); };
+    auto upb = [&](int k) { return P<bf16>(u, u->up_[k]); };
+    float* ga = P<float>(u, u->grad_a);
+    float* gb = P<float>(u, u->grad_b);
+    float* gskip[3] = {P<float>(u, u->grad_skip[0]), P<float>(u, u->grad_skip[1]), P<float>(u, u->grad_skip[2])};
+    float* gd1 = P<float>(u, u->gd1);
+    head_kernel<<<std::min(256, grid_for((int64_t)d0.nvox * d0.batch)), 256, 0, st>>>(
+        act(DEC1B), n_ansatz, params + head_offset(), nullptr, target, gd1, grad + head_offset(), loss, d0);
+    UNET_CUDA(u, cudaGetLastError());
+    // decoder level 0: dec1b <- gd1, dec1a <- ga  (sources [up2 | e1])
+    UNET_CUDA(u, conv_bwd(u, DEC1B, 0, gd1, act(DEC1A), 16, nullptr, 0, ga, nullptr, grad, true, st));
+    UNET_CUDA(u, cudaMemsetAsync(gskip[0], 0, (size_t)d0.nvox * d0.batch * 16 * sizeof(float), st));
+    UNET_CUDA(u, conv_bwd(u, DEC1A, 0, ga, upb(2), 16, act(ENC1B), 16, gb, gskip[0], grad, true, st));
+    up_bwd_kernel<<<grid_for((int64_t)u->lv[1].nvox * u->batch * 16), 256, 0, st>>>(gb, ga, u->lv[0], 16);  // -> g(dec2b)
+    UNET_CUDA(u, cudaGetLastError());
+    // decoder level 1
+    UNET_CUDA(u, conv_bwd(u, DEC2B, 1, ga, act(DEC2A), 16, nullptr, 0, gb, nullptr, grad, true, st));
+    UNET_CUDA(u, cudaMemsetAsync(gskip[1], 0, (size_t)u->lv[1].nvox * u->batch * 16 * sizeof(float), st));
+    UNET_CUDA(u, conv_bwd(u, DEC2A, 1, gb, upb(1), 32, act(ENC2B), 16, ga, gskip[1], grad, true, st));
+    up_bwd_kernel<<<grid_for((int64_t)u->lv[2].nvox * u->batch * 32), 256, 0, st>>>(ga, gb, u->lv[1], 32);  // -> g(dec3b)
+    UNET_CUDA(u, cudaGetLastError());
+    // decoder level 2
+    UNET_CUDA(u, conv_bwd(u, DEC3B, 2, gb, act(DEC3A), 32, nullptr, 0, ga, nullptr, grad, true, st));
+    UNET_CUDA(u, cudaMemsetAsync(gskip[2], 0, (size_t)u->lv[2].nvox * u->batch * 32 * sizeof(float), st));
+    UNET_CUDA(u, conv_bwd(u, DEC3A, 2, ga, upb(0), 64, act(ENC3B), 32, gb, gskip[2], grad, true, st));
+    up_bwd_kernel<<<grid_for((int64_t)u->lv[3].nvox * u->batch * 64), 256, 0, st>>>(gb, ga, u->lv[2], 64);  // -> g(botb)
+    UNET_CUDA(u, cudaGetLastError());
+    // bottleneck
+    UNET_CUDA(u, conv_bwd(u, BOTB, 3, ga, act(BOTA), 64, nullptr, 0, gb, nullptr, grad, true, st));
+    UNET_CUDA(u, conv_bwd(u, BOTA, 3, gb, pool(2), 32, nullptr, 0, ga, nullptr, grad, true, st));   // ga = g(pool2 out)
+    pool_bwd_kernel<<<grid_for((int64_t)u->lv[2].nvox * u->batch * 32), 256, 0, st>>>(ga, gskip[2], u->lv[2], 32);
+    UNET_CUDA(u, cudaGetLastError());
+    // encoder level 2 (e3 gradient complete in gskip[2])
+    UNET_CUDA(u, conv_bwd(u, ENC3B, 2, gskip[2], act(ENC3A), 32, nullptr, 0, ga, nullptr, grad, true, st));
+    UNET_CUDA(u, conv_bwd(u, ENC3A, 2, ga, pool(1), 16, nullptr, 0, gb, nullptr, grad, true, st));
+    pool_bwd_kernel<<<grid_for((int64_t)u->lv[1].nvox * u->batch * 16), 256, 0, st>>>(gb, gskip[1], u->lv[1], 16);
+    UNET_CUDA(u, cudaGetLastError());
+    // encoder level 1
+    UNET_CUDA(u, conv_bwd(u, ENC2B, 1, gskip[1], act(ENC2A), 16, nullptr, 0, ga, nullptr, grad, true, st));
+    UNET_CUDA(u, conv_bwd(u, ENC2A, 1, ga, pool(0), 16, nullptr, 0, gb, nullptr, grad, true, st));
+    pool_bwd_kernel<<<grid_for((int64_t)d0.nvox * d0.batch * 16), 256, 0, st>>>(gb, gskip[0], u->lv[0], 16);
+    UNET_CUDA(u, cudaGetLastError());
+    // encoder level 0 (the input needs no gradient)
+    UNET_CUDA(u, conv_bwd(u, ENC1B, 0, gskip[0], act(ENC1A), 16, nullptr, 0, ga, nullptr, grad, true, st));
+    UNET_CUDA(u, conv_bwd(u, ENC1A, 0, ga, P<bf16>(u, u->x), 16, nullptr, 0, nullptr, nullptr, grad, false, st));
+    return NH_OK;
+}
+
+int nh_unet_adam(float* params, const float* grad, float* m, float* v, int64_t count, int step, float lr, void* stream)
+{
+    if (!params || !grad || !m || !v || count < 1 || step < 1) return unet_fail(nullptr, NH_EINVAL, "bad Adam arguments");
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+    adam_kernel<<<grid_for(count), 256, 0, static_cast<cudaStream_t>(stream)>>>(params, grad, m, v, count, lr, b1, b2,
+                                                                                 1e-8f, c1, c2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return unet_fail(nullptr, NH_ECUDA, std::string("adam: ") + cudaGetErrorString(e));
+    return NH_OK;
+}
+
+void nh_unet_destroy(nh_unet* u) { delete u; }
+
+}  // extern "C"

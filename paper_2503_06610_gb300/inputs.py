@@ -181,3 +181,48 @@ def batched_sweep(count=64, seed=0, K=0.005, dt_fd=16):
         n0 = skyrmion_tubes(L, L, Lz, [(L / 2, L / 2)], R)
         out.append((params, n0, (L / 2, L / 2)))
     return out
+
+
+# ------------------------------------------------------------------ warm-start network inputs
+
+# Layer widths of the warm-start U-Net (name, cin, cout) in parameter order; the
+# head is a 1x1x1 convolution 16 -> 3.  Weights are W[tap][cout][cin] then bias.
+UNET_CONV_LAYERS = [
+    ("enc1a", 16, 16), ("enc1b", 16, 16), ("enc2a", 16, 16), ("enc2b", 16, 16),
+    ("enc3a", 16, 32), ("enc3b", 32, 32), ("bota", 32, 64), ("botb", 64, 64),
+    ("dec3a", 96, 32), ("dec3b", 32, 32), ("dec2a", 48, 16), ("dec2b", 16, 16),
+    ("dec1a", 32, 16), ("dec1b", 16, 16),
+]
+UNET_HEAD = (16, 3)
+
+
+def unet_init_params(seed=0):
+    """He-normal conv weights (std sqrt(2 / (27 cin))), zero biases, a small head (std 1e-2)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for _, ci, co in UNET_CONV_LAYERS:
+        parts.append(rng.normal(0.0, np.sqrt(2.0 / (27 * ci)), size=27 * co * ci))
+        parts.append(np.zeros(co))
+    ci, co = UNET_HEAD
+    parts.append(rng.normal(0.0, 1e-2, size=ci * co))
+    parts.append(np.zeros(co))
+    return np.concatenate(parts)
+
+
+def warmstart_samples(count, seed=0, nx=64, ny=64, lz_choices=(16, 24, 32), K=0.005, dt_fd=30):
+    """Seeded relaxation problems for the learned warm start: per sample the
+    cell thickness Lz, pitch P ~ U[Lz, 2 Lz] (q0 = 2 pi / P), bulk anchoring
+    W0 ~ logU[1e-4, 1e-2] x K, tube radius R ~ U[10, 18], one centred tube,
+    homeotropic plates, fluid at rest."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(count):
+        lz = int(rng.choice(lz_choices))
+        pitch = float(rng.uniform(lz, 2 * lz))
+        w0 = float(10 ** rng.uniform(-4, -2) * K)
+        radius = float(rng.uniform(10.0, 18.0))
+        params = dict(nx=nx, ny=ny, nz=lz, walls_z=True, anchoring="homeotropic", shifted=True, tau=1.0,
+                      g=(0.0, 0.0, 0.0), K=K, q0=2 * math.pi / pitch, W0=w0, dt_fd=dt_fd, **LESLIE_ALIGN_09)
+        n0 = skyrmion_tubes(nx, ny, lz, [(nx / 2, ny / 2)], radius)
+        out.append((params, n0))
+    return out

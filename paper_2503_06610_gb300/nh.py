@@ -104,6 +104,15 @@ SIGNATURES = {
     "nh_set_lb_variant": ([_VP, ctypes.c_int], ctypes.c_int),
     "nh_autotune": ([_VP, _VP, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "nh_destroy": ([_VP], None),
+    "nh_unet_param_count": ([], ctypes.c_int64),
+    "nh_unet_create": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_VP)], ctypes.c_int),
+    "nh_unet_workspace_bytes": ([_VP, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "nh_unet_bind": ([_VP, _VP, ctypes.c_size_t], ctypes.c_int),
+    "nh_unet_set_params": ([_VP, _VP, _VP], ctypes.c_int),
+    "nh_unet_forward": ([_VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "nh_unet_backward": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "nh_unet_adam": ([_VP, _VP, _VP, _VP, ctypes.c_int64, ctypes.c_int, ctypes.c_float, _VP], ctypes.c_int),
+    "nh_unet_destroy": ([_VP], None),
     "nh_diagnostics_noalloc": ([ctypes.POINTER(nh_params), _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
 }
 
@@ -445,3 +454,59 @@ def batch_relax(channels, n_fd_steps: int, stream=None):
 def batch_autotune(channels, stream=None) -> int:
     s = stream or channels[0].stream
     return nh_batch_autotune([c.ctx for c in channels], s.cuda_stream)
+
+
+# ------------------------------------------------------------------ learned warm start network
+
+def _dp(t):
+    return None if t is None else _VP(t.data_ptr())
+
+
+class UNet:
+    """One warm-start network instance for a fixed (batch, nx, ny, nz); the FP32
+    parameters (and Adam state) are shared torch CUDA tensors owned by the caller."""
+
+    def __init__(self, batch, nx, ny, nz, device=0):
+        import torch
+        lib = load_library()
+        self.torch = torch
+        self.shape = (batch, nx, ny, nz)
+        h = _VP()
+        _check(lib.nh_unet_create(batch, nx, ny, nz, ctypes.byref(h)))
+        self.h = h
+        nb = ctypes.c_size_t(0)
+        _check(lib.nh_unet_workspace_bytes(h, ctypes.byref(nb)))
+        self.workspace = torch.empty(nb.value + 256, dtype=torch.uint8, device=torch.device("cuda", device))
+        base = (self.workspace.data_ptr() + 255) // 256 * 256
+        _check(lib.nh_unet_bind(h, _VP(base), nb.value))
+
+    @staticmethod
+    def param_count():
+        return int(load_library().nh_unet_param_count())
+
+    def set_params(self, params, stream=None):
+        _check(load_library().nh_unet_set_params(self.h, _dp(params), _VP(stream or 0)))
+
+    def forward(self, params, n_ansatz, scalars, n_out=None, stream=None):
+        _check(load_library().nh_unet_forward(self.h, _dp(params), _dp(n_ansatz), _dp(scalars), _dp(n_out),
+                                              _VP(stream or 0)))
+
+    def backward(self, params, n_ansatz, target, grad, loss, stream=None):
+        _check(load_library().nh_unet_backward(self.h, _dp(params), _dp(n_ansatz), _dp(target), _dp(grad),
+                                               _dp(loss), _VP(stream or 0)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load_library().nh_unet_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def nh_unet_adam(params, grad, m, v, step, lr, stream=None):
+    _check(load_library().nh_unet_adam(_dp(params), _dp(grad), _dp(m), _dp(v), params.numel(), int(step),
+                                       float(lr), _VP(stream or 0)))

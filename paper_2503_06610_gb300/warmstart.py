@@ -1,0 +1,246 @@
+"""Learned warm start for skyrmion-tube relaxations (spec axis 4).
+
+The plain method relaxes an extruded skyrmion ansatz by the director-only
+gradient flow (``nh_relax``: the predictor-corrector of Sec. II.B at u = 0)
+until the lattice Frank energy changes by less than ``tol`` per site per unit
+time (measured over ``check_every`` FD steps).  A 3D U-Net with BF16 kernels
+(``nh_unet_*``) is trained on such relaxations to predict the relaxed field
+from the ansatz and (q0, Lz, W0); the plain relaxation then continues from the
+prediction and judges it: the result must match the relaxation from the ansatz
+within ``max |dn| <= 1e-4``, and the saving is reported in FD steps and wall
+time.
+
+Usage:  python -m paper_2503_06610_gb300.warmstart --samples 2000 --held-out 200 --out ws.json
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import inputs
+from . import nh
+
+
+class WarmStartNet:
+    """FP32 master parameters + Adam state (torch CUDA tensors) and cached
+    network instances per input shape."""
+
+    def __init__(self, seed=0, device=0):
+        import torch
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        P = nh.UNet.param_count()
+        flat = inputs.unet_init_params(seed)
+        assert flat.size == P
+        self.params = torch.tensor(flat, dtype=torch.float32, device=self.device)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.grad = torch.zeros_like(self.params)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+        self.steps = 0
+        self.nets = {}
+
+    def net(self, shape):
+        if shape not in self.nets:
+            self.nets[shape] = nh.UNet(*shape)
+        return self.nets[shape]
+
+    def _stream(self):
+        return self.torch.cuda.current_stream(self.device).cuda_stream
+
+    def predict(self, n_ansatz, scalars, dims):
+        """n_ansatz [B][3][N] and scalars [B][3] (FP32 CUDA) -> predicted n [B][3][N]."""
+        B = n_ansatz.shape[0]
+        net = self.net((B,) + tuple(dims))
+        out = self.torch.empty_like(n_ansatz)
+        net.set_params(self.params, self._stream())
+        net.forward(self.params, n_ansatz, scalars, out, self._stream())
+        return out
+
+    def loss_and_grad(self, n_ansatz, scalars, target, dims):
+        B = n_ansatz.shape[0]
+        net = self.net((B,) + tuple(dims))
+        s = self._stream()
+        net.set_params(self.params, s)
+        net.forward(self.params, n_ansatz, scalars, None, s)
+        net.backward(self.params, n_ansatz, target, self.grad, self.loss, s)
+        return self.loss, self.grad
+
+    def train_step(self, n_ansatz, scalars, target, dims, lr=1e-3):
+        self.loss_and_grad(n_ansatz, scalars, target, dims)
+        self.steps += 1
+        nh.nh_unet_adam(self.params, self.grad, self.m, self.v, self.steps, lr, self._stream())
+        return self.loss
+
+
+# ------------------------------------------------------------------ plain relaxation
+
+def relax(chans, tol=1e-8, check_every=100, max_steps=200000):
+    """Relax every channel (batched) until |dE/dt| per site < tol; returns the
+    FD steps each one needed (capped at max_steps) and the wall time."""
+    import torch
+    active = list(range(len(chans)))
+    steps = [0] * len(chans)
+    e_prev = [c.diagnostics()["energy"] for c in chans]
+    t0 = time.perf_counter()
+    while active:
+        nh.batch_relax([chans[k] for k in active], check_every)
+        still = []
+        for k in active:
+            steps[k] += check_every
+            e = chans[k].diagnostics()["energy"]
+            rate = abs(e - e_prev[k]) / (check_every * chans[k].params["dt_fd"] * chans[k].N)
+            e_prev[k] = e
+            if rate >= tol and steps[k] < max_steps:
+                still.append(k)
+        active = still
+    torch.cuda.synchronize()
+    return steps, time.perf_counter() - t0
+
+
+def make_channels(samples, fields=None):
+    chans = []
+    for k, (params, n0) in enumerate(samples):
+        ch = nh.Channel(dict(params, precision="fp32", storage="f32", shifted=True))
+        ch.set_fields(n0 if fields is None else fields[k])
+        chans.append(ch)
+    return chans
+
+
+def scalars_of(params):
+    return [params["q0"], float(params["nz"]), params["W0"]]
+
+
+def generate(samples, batch=64, **relax_kw):
+    """Relax each sample from its ansatz; returns targets, steps and wall time."""
+    targets, steps, wall = [], [], 0.0
+    for b0 in range(0, len(samples), batch):
+        chans = make_channels(samples[b0:b0 + batch])
+        st, w = relax(chans, **relax_kw)
+        wall += w
+        steps += st
+        for c in chans:
+            targets.append(c.get_fields()[0].astype(np.float32))
+            c.close()
+    return targets, steps, wall
+
+
+def group_by_shape(indices, samples):
+    groups = {}
+    for i in indices:
+        p = samples[i][0]
+        groups.setdefault((p["nx"], p["ny"], p["nz"]), []).append(i)
+    return groups
+
+
+def train(net, samples, targets, train_idx, epochs=20, batch=8, lr=1e-3, seed=0, log=None):
+    torch = net.torch
+    rng = np.random.Generator(np.random.PCG64(seed))
+    groups = group_by_shape(train_idx, samples)
+    dev = net.device
+    cache = {}
+    for shape, idx in groups.items():
+        cache[shape] = (
+            torch.tensor(np.stack([samples[i][1] for i in idx]).astype(np.float32), device=dev),
+            torch.tensor(np.array([scalars_of(samples[i][0]) for i in idx], dtype=np.float32), device=dev),
+            torch.tensor(np.stack([targets[i] for i in idx]), device=dev))
+    history = []
+    for ep in range(epochs):
+        losses = []
+        order = [(shape, j) for shape, idx in groups.items() for j in range(0, len(idx) - batch + 1, batch)]
+        rng.shuffle(order)
+        perms = {shape: rng.permutation(len(idx)) for shape, idx in groups.items()}
+        for shape, j in order:
+            sel = torch.tensor(perms[shape][j:j + batch], device=dev)
+            na, sc, tg = (t.index_select(0, sel) for t in cache[shape])
+            losses.append(net.train_step(na.contiguous(), sc.contiguous(), tg.contiguous(), shape, lr).clone())
+        mean = float(torch.stack(losses).mean())
+        history.append(mean)
+        if log:
+            log(f"epoch {ep}: loss {mean:.3e}")
+    return history
+
+
+def evaluate(net, samples, targets, steps_ansatz, test_idx, batch=64, **relax_kw):
+    """Relax the held-out samples from the network's prediction; compare with the
+    relaxations from the ansatz (steps, wall time, final-field difference)."""
+    torch = net.torch
+    dev = net.device
+    t0 = time.perf_counter()
+    preds = {}
+    for shape, idx in group_by_shape(test_idx, samples).items():
+        for j in range(0, len(idx), 8):
+            sub = idx[j:j + 8]
+            na = torch.tensor(np.stack([samples[i][1] for i in sub]).astype(np.float32), device=dev)
+            sc = torch.tensor(np.array([scalars_of(samples[i][0]) for i in sub], dtype=np.float32), device=dev)
+            out = net.predict(na, sc, shape).cpu().numpy().astype(np.float64)
+            for k, i in enumerate(sub):
+                preds[i] = out[k]
+    torch.cuda.synchronize()
+    t_pred = time.perf_counter() - t0
+    steps_p, wall_p, dn, dn_pred = [], 0.0, [], []
+    for b0 in range(0, len(test_idx), batch):
+        sub = test_idx[b0:b0 + batch]
+        chans = make_channels([samples[i] for i in sub], [preds[i] for i in sub])
+        st, w = relax(chans, **relax_kw)
+        wall_p += w
+        steps_p += st
+        for c, i in zip(chans, sub):
+            n = c.get_fields()[0]
+            dn.append(float(np.max(np.abs(n - targets[i]))))
+            dn_pred.append(float(np.max(np.abs(preds[i] - targets[i]))))
+            c.close()
+    # the same held-out relaxations from the ansatz, timed the same way
+    wall_a = 0.0
+    for b0 in range(0, len(test_idx), batch):
+        sub = test_idx[b0:b0 + batch]
+        chans = make_channels([samples[i] for i in sub])
+        _, w = relax(chans, **relax_kw)
+        wall_a += w
+        for c in chans:
+            c.close()
+    sa = np.array([steps_ansatz[i] for i in test_idx], dtype=float)
+    sp = np.array(steps_p, dtype=float)
+    return {"held_out": len(test_idx), "mean_steps_from_ansatz": float(sa.mean()),
+            "mean_steps_from_prediction": float(sp.mean()), "step_ratio": float(sp.sum() / sa.sum()),
+            "wall_s_prediction_inference": t_pred, "wall_s_relax_from_prediction": wall_p,
+            "wall_s_relax_from_ansatz": wall_a, "wall_ratio": (t_pred + wall_p) / wall_a,
+            "max_dn_final": float(np.max(dn)), "frac_final_within_1e-4": float(np.mean(np.array(dn) <= 1e-4)),
+            "median_max_dn_prediction_vs_relaxed": float(np.median(dn_pred))}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--samples", type=int, default=2000)
+    ap.add_argument("--held-out", type=int, default=200)
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--max-steps", type=int, default=200000)
+    ap.add_argument("--out", default=None)
+    args = ap.parse_args()
+    samples = inputs.warmstart_samples(args.samples, seed=0)
+    kw = dict(tol=args.tol, max_steps=args.max_steps)
+    t0 = time.perf_counter()
+    targets, steps, wall = generate(samples, **kw)
+    print(f"generated {len(samples)} relaxations in {wall:.1f} s; mean FD steps {np.mean(steps):.0f}", flush=True)
+    n_test = args.held_out
+    test_idx = list(range(len(samples) - n_test, len(samples)))
+    train_idx = list(range(len(samples) - n_test))
+    net = WarmStartNet(seed=0)
+    t1 = time.perf_counter()
+    hist = train(net, samples, targets, train_idx, epochs=args.epochs, log=lambda s: print(s, flush=True))
+    t_train = time.perf_counter() - t1
+    res = evaluate(net, samples, targets, steps, test_idx, **kw)
+    res.update({"samples": len(samples), "train_epochs": args.epochs, "train_wall_s": t_train,
+                "loss_history": hist, "generation_wall_s": wall, "mean_steps_generation": float(np.mean(steps)),
+                "total_wall_s": time.perf_counter() - t0})
+    print(json.dumps(res), flush=True)
+    if args.out:
+        json.dump(res, open(args.out, "w"), indent=1)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,142 @@
+"""Warm-start network kernels (BF16 activations, FP32 accumulation, tensor
+cores) against the FP64 CPU oracle network, and the training / relaxation
+driver.
+
+The oracle runs with the same BF16-rounded weights and inputs; the remaining
+differences come from rounding every activation to BF16 (2^-9 relative per
+layer), so the tolerances are a few per cent.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2503_06610_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2503_06610_gb300 import nh, warmstart
+    from oracle import unet as U
+    nh.load_library()
+    return torch, nh, warmstart, U
+
+
+def _bf16(a):
+    import torch
+    return torch.tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def _problem(B=2, nx=16, ny=16, nz=16, seed=0):
+    rng = np.random.default_rng(seed)
+    flat = I.unet_init_params(seed)
+    hs = len(flat) - 51
+    flat[hs:hs + 48] = rng.normal(0, 0.3, size=48)        # a head large enough to move n
+    flat[:hs] += 0.02 * rng.normal(size=hs) * (rng.random(hs) < 0.01)
+    n_ans = np.stack([I.skyrmion_tubes(nx, ny, nz, [(nx / 2 + k, ny / 2)], 5.0) for k in range(B)])
+    target = np.stack([I.random_director(nx, ny, nz, seed=10 + k) for k in range(B)])
+    scal = np.array([[2 * math.pi / (12 + 4 * k), float(nz), 1e-5 * (k + 1)] for k in range(B)])
+    return flat, n_ans, target, scal
+
+
+def _oracle(U, flat, n_ans, target, scal, dims):
+    import torch
+    B = n_ans.shape[0]
+    nx, ny, nz = dims
+    fr = flat.copy()
+    # the GPU convolves with BF16 weights and adds FP32 biases; the head is FP32
+    off = 0
+    for _, ci, co in U.CONV_LAYERS:
+        fr[off:off + 27 * ci * co] = _bf16(flat[off:off + 27 * ci * co])
+        off += 27 * ci * co + co
+    na5 = torch.tensor(n_ans.reshape(B, 3, nz, ny, nx))
+    x = U.make_input(na5.numpy(), scal[:, 0], scal[:, 1], scal[:, 2])
+    x = torch.tensor(_bf16(x.numpy()))
+    tg = torch.tensor(target.reshape(B, 3, nz, ny, nx))
+    loss, grad, n_pred = U.loss_and_grad(fr, x, na5, tg)
+    return loss, grad, n_pred.numpy().reshape(B, 3, -1)
+
+
+def test_forward_and_gradients_match_oracle(env):
+    torch, nh, ws, U = env
+    dims = (16, 16, 16)
+    flat, n_ans, target, scal = _problem(B=2)
+    loss_o, grad_o, npred_o = _oracle(U, flat, n_ans, target, scal, dims)
+    dev = torch.device("cuda")
+    net = nh.UNet(2, *dims)
+    params = torch.tensor(flat, dtype=torch.float32, device=dev)
+    na = torch.tensor(n_ans, dtype=torch.float32, device=dev)
+    sc = torch.tensor(scal, dtype=torch.float32, device=dev)
+    tg = torch.tensor(target, dtype=torch.float32, device=dev)
+    out = torch.empty_like(na)
+    grad = torch.zeros_like(params)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    net.set_params(params)
+    net.forward(params, na, sc, out)
+    net.backward(params, na, tg, grad, loss)
+    torch.cuda.synchronize()
+    npred = out.cpu().numpy().astype(np.float64)
+    delta_o = npred_o - n_ans
+    delta_g = npred - n_ans
+    assert np.linalg.norm(delta_g - delta_o) / np.linalg.norm(delta_o) < 3e-2
+    assert abs(float(loss) - loss_o) / loss_o < 1e-2
+    g = grad.cpu().numpy().astype(np.float64)
+    off = 0
+    for name, ci, co in U.CONV_LAYERS:
+        n_w = 27 * ci * co
+        for part, sl in (("W", slice(off, off + n_w)), ("b", slice(off + n_w, off + n_w + co))):
+            ref = grad_o[sl]
+            err = np.linalg.norm(g[sl] - ref) / max(np.linalg.norm(ref), 1e-30)
+            assert err < 8e-2, (name, part, err)
+        off += n_w + co
+    ref = grad_o[off:]
+    assert np.linalg.norm(g[off:] - ref) / np.linalg.norm(ref) < 2e-2
+
+
+def test_adam_matches_oracle(env):
+    torch, nh, ws, U = env
+    rng = np.random.default_rng(3)
+    n = 1000
+    p = rng.normal(size=n)
+    g = rng.normal(size=n)
+    m = np.zeros(n)
+    v = np.zeros(n)
+    dev = torch.device("cuda")
+    tp, tg, tm, tv = (torch.tensor(a, dtype=torch.float32, device=dev) for a in (p, g, m, v))
+    for step in (1, 2, 3):
+        nh.nh_unet_adam(tp, tg, tm, tv, step, 1e-3)
+        p, m, v = U.adam(p, g, m, v, step, 1e-3)
+    torch.cuda.synchronize()
+    assert np.allclose(tp.cpu().numpy(), p, rtol=1e-6, atol=1e-7)
+
+
+def test_training_reduces_loss(env):
+    torch, nh, ws, U = env
+    dims = (16, 16, 8)
+    flat, n_ans, target, scal = _problem(B=4, nz=8, seed=1)
+    target = np.stack([I.skyrmion_tubes(16, 16, 8, [(8.0 + k, 8.0)], 6.5) for k in range(4)])
+    net = ws.WarmStartNet(seed=2)
+    dev = net.device
+    na = torch.tensor(n_ans, dtype=torch.float32, device=dev)
+    sc = torch.tensor(scal, dtype=torch.float32, device=dev)
+    tg = torch.tensor(target, dtype=torch.float32, device=dev)
+    first = float(net.train_step(na, sc, tg, dims, lr=2e-3))
+    for _ in range(60):
+        last = float(net.train_step(na, sc, tg, dims, lr=2e-3))
+    assert last < 0.5 * first
+
+
+def test_relaxation_driver_converges(env):
+    torch, nh, ws, U = env
+    samples = I.warmstart_samples(3, seed=5, nx=16, ny=16, lz_choices=(8,))
+    chans = ws.make_channels(samples)
+    steps, wall = ws.relax(chans, tol=1e-6, check_every=50, max_steps=5000)
+    assert all(50 <= s <= 5000 for s in steps)
+    for c in chans:
+        d = c.diagnostics()
+        assert abs(d["max_norm"] - 1) < 1e-6 and d["nonfinite"] == 0
