@@ -212,6 +212,12 @@ int nh_relax(nh_ctx* ctx, int64_t n_fd_steps, void* stream);
  * are recorded on ctxs[0]. */
 int nh_batch_relax(nh_ctx* const* ctxs, int count, int64_t n_fd_steps, void* stream);
 
+/* Largest change of the director since the previous call: *max_change =
+ * max over sites of |n - n_snapshot| (INFINITY on the first call after
+ * nh_set_fields), then the snapshot is replaced by the current n.  Used to
+ * decide when a relaxation has converged.  Synchronises the stream. */
+int nh_director_change(nh_ctx* ctx, double* max_change);
+
 /* Set the tube centroids to track (count <= NH_MAX_TUBES, centres[2*count]
  * as (x, y) pairs); 0 disables tracking. */
 int nh_set_tubes(nh_ctx* ctx, const double* centres, int count);

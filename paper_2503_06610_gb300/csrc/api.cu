@@ -34,7 +34,7 @@ size_t store_size(const nh_params& p)
 }
 
 struct Layout {
-    size_t f[2], F, n, nP, ndot, u, rho, sigma, staging, partials, result, scales, absmax, trig, total;
+    size_t f[2], F, n, nP, ndot, u, rho, sigma, snap, staging, partials, result, scales, absmax, trig, total;
 };
 
 Layout make_layout(const nh_params& p)
@@ -57,6 +57,7 @@ Layout make_layout(const nh_params& p)
     L.u = take(3 * N * R);
     L.rho = take(N * R);
     L.sigma = take(9 * N * R);
+    L.snap = take(3 * N * R);
     L.staging = take(7 * N * sizeof(double));
     L.partials = take((size_t)diag_blocks() * diag_num_values(NH_MAX_TUBES) * sizeof(double));
     L.result = take((size_t)diag_num_values(NH_MAX_TUBES) * sizeof(double));
@@ -186,6 +187,7 @@ struct nh_ctx {
     int64_t launches = 0;
     double host_result[6 + 5 * NH_MAX_TUBES] = {};
     bool diag_pending = false;
+    bool snap_valid = false;  // a director snapshot exists (nh_director_change)
     int diag_tubes = 0;
     cudaStream_t diag_stream = nullptr;
 
@@ -904,6 +906,7 @@ int nh_set_fields(nh_ctx* c, const double* n, const double* u, const double* rho
     c->launches += 1;
     if (!on_device) NH_CUDA(c, cudaStreamSynchronize(st));
     c->fields_set = true;
+    c->snap_valid = false;
     return NH_OK;
 }
 
@@ -1005,6 +1008,7 @@ int nh_restore(nh_ctx* c, const double* n, const double* F, const double* u, con
     }
     c->step = step;
     c->fields_set = true;
+    c->snap_valid = false;
     NH_CUDA(c, cudaStreamSynchronize(st));
     return NH_OK;
 }
@@ -1159,6 +1163,29 @@ int nh_batch_relax(nh_ctx* const* ctxs, int count, int64_t n_fd_steps, void* str
         r = c0->p.precision == NH_FP64 ? batch_fd_typed<double>(plan, st, 2) : batch_fd_typed<float>(plan, st, 2);
     close_segment(c0);
     if (r) return fail(nullptr, r, "batch relax: " + c0->err);
+    return NH_OK;
+}
+
+int nh_director_change(nh_ctx* c, double* max_change)
+{
+    int r = check_ready(c);
+    if (r) return r;
+    if (!max_change) return fail(c, NH_EINVAL, "max_change is NULL");
+    if (!c->fields_set) return fail(c, NH_EINVAL, "nh_set_fields must be called before nh_director_change");
+    if ((r = set_device(c))) return r;
+    cudaStream_t st = c->stream;
+    double* out = c->at<double>(c->L.result);
+    double* partial = c->at<double>(c->L.partials);
+    if (c->p.precision == NH_FP64)
+        NH_CUDA(c, launch_director_change<double>(c->at<double>(c->L.n), c->at<double>(c->L.snap), partial, out, c->N, st));
+    else
+        NH_CUDA(c, launch_director_change<float>(c->at<float>(c->L.n), c->at<float>(c->L.snap), partial, out, c->N, st));
+    c->launches += 2;
+    double v = 0.0;
+    NH_CUDA(c, cudaMemcpyAsync(&v, out, sizeof(double), cudaMemcpyDeviceToHost, st));
+    NH_CUDA(c, cudaStreamSynchronize(st));
+    *max_change = c->snap_valid ? v : INFINITY;
+    c->snap_valid = true;
     return NH_OK;
 }
 

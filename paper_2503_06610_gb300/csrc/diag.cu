@@ -383,9 +383,58 @@ __global__ void trig_table_kernel(double* t, int nx, int ny)
     }
 }
 
+// max over sites of |n - snap| (the largest change of the director since the
+// snapshot), then snap <- n.  Per-block maxima go to partial[block].
+template <typename Real>
+__global__ void director_change_kernel(const Real* __restrict__ n, Real* __restrict__ snap, double* partial, int N)
+{
+    double m = 0.0;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+        double d2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const Real v = n[(size_t)a * N + s];
+            const double d = (double)v - (double)snap[(size_t)a * N + s];
+            d2 += d * d;
+            snap[(size_t)a * N + s] = v;
+        }
+        m = fmax(m, sqrt(d2));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ double wm[8];
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = fmax(b, wm[w]);
+        partial[blockIdx.x] = b;
+    }
+}
+
+__global__ void max_final_kernel(const double* __restrict__ partial, double* __restrict__ out, int blocks)
+{
+    double m = 0.0;
+    for (int b = threadIdx.x; b < blocks; b += 32) m = fmax(m, partial[b]);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) *out = m;
+}
+
 inline int blocks_for(int64_t n) { return (int)((n + 255) / 256); }
 
 }  // namespace
+
+template <typename Real>
+cudaError_t launch_director_change(const Real* n, Real* snap, double* partial, double* out, int N, cudaStream_t st)
+{
+    int blocks = blocks_for(N);
+    if (blocks > diag_blocks()) blocks = diag_blocks();
+    director_change_kernel<Real><<<blocks, 256, 0, st>>>(n, snap, partial, N);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    max_final_kernel<<<1, 32, 0, st>>>(partial, out, blocks);
+    return cudaGetLastError();
+}
+template cudaError_t launch_director_change<double>(const double*, double*, double*, double*, int, cudaStream_t);
+template cudaError_t launch_director_change<float>(const float*, float*, double*, double*, int, cudaStream_t);
 
 int diag_num_values(int n_tubes) { return DIAG_FIXED + 5 * n_tubes; }
 int diag_blocks() { return 4 * 152; }

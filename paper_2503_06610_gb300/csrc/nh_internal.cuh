@@ -204,6 +204,10 @@ int diag_blocks();
 cudaError_t launch_diagnostics(const DiagArgs& a, cudaStream_t s);
 cudaError_t launch_trig_table(double* t, int nx, int ny, cudaStream_t s);
 
+// max |n - snap| over sites into *out (device), then snap <- n (diag.cu)
+template <typename Real>
+cudaError_t launch_director_change(const Real* n, Real* snap, double* partial, double* out, int N, cudaStream_t s);
+
 // Record the text returned by nh_last_error(NULL) on this thread (api.cu).
 void set_global_error(const char* msg);
 inline void set_global_error(const std::string& msg) { set_global_error(msg.c_str()); }

@@ -93,6 +93,7 @@ SIGNATURES = {
     "nh_batch_autotune": ([ctypes.POINTER(_VP), ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "nh_set_tubes": ([_VP, _DP, ctypes.c_int], ctypes.c_int),
     "nh_relax": ([_VP, ctypes.c_int64, _VP], ctypes.c_int),
+    "nh_director_change": ([_VP, _DP], ctypes.c_int),
     "nh_batch_relax": ([ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int64, _VP], ctypes.c_int),
     "nh_diagnostics": ([_VP, ctypes.POINTER(nh_diag)], ctypes.c_int),
     "nh_diagnostics_enqueue": ([_VP, _VP], ctypes.c_int),
@@ -255,6 +256,12 @@ def nh_relax(ctx, n_fd_steps: int, stream=None):
     _check(load_library().nh_relax(ctx, int(n_fd_steps), _VP(stream or 0)), ctx)
 
 
+def nh_director_change(ctx) -> float:
+    out = ctypes.c_double(0.0)
+    _check(load_library().nh_director_change(ctx, ctypes.byref(out)), ctx)
+    return float(out.value)
+
+
 def nh_batch_relax(ctxs, n_fd_steps: int, stream=None):
     arr = (_VP * len(ctxs))(*[c.value if isinstance(c, _VP) else c for c in ctxs])
     _check(load_library().nh_batch_relax(arr, len(ctxs), int(n_fd_steps), _VP(stream or 0)))
@@ -398,6 +405,9 @@ class Channel:
 
     def relax(self, n_fd_steps: int, stream=None):
         nh_relax(self.ctx, n_fd_steps, (stream or self.stream).cuda_stream)
+
+    def director_change(self):
+        return nh_director_change(self.ctx)
 
     def set_tubes(self, centres):
         nh_set_tubes(self.ctx, centres)

@@ -462,3 +462,17 @@ def test_relax_matches_oracle_gradient_flow(nh, oracle_mod, anchoring):
     nh.batch_relax(chans, 12)
     for c in chans:
         assert O.rel_l2(c.get_fields()[0], n) < 1e-12
+
+
+def test_director_change_tracks_relaxation(nh):
+    params = _generic(16, 12, 8, dt_fd=5, K=0.01)
+    n0 = I.skyrmion_tubes(16, 12, 8, [(8.0, 6.0)], 5.0)
+    ch = _channel(nh, params, n0, precision="fp32")
+    assert math.isinf(ch.director_change())
+    assert ch.director_change() == 0.0
+    ch.relax(20)
+    d = ch.director_change()
+    n1 = ch.get_fields()[0]
+    assert 0.0 < d <= np.max(np.linalg.norm(n1 - n0, axis=0)) + 1e-6
+    assert abs(d - np.max(np.linalg.norm(n1 - n0, axis=0))) < 1e-5
+    assert ch.director_change() == 0.0
