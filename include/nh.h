@@ -260,6 +260,13 @@ int64_t nh_launch_count(const nh_ctx* ctx);
  * the same arithmetic.  NH_EINVAL if the variant does not fit the domain. */
 int nh_set_lb_variant(nh_ctx* ctx, int variant);
 
+/* Select the FD kernels: 1 = fused (default): one 2.5D shared-memory kernel
+ * for predictor + corrector + renormalisation and one for stress + force
+ * (the stress never leaves the chip); 0 = one kernel per stage.  Same
+ * arithmetic.  With the fused kernels the timing classes FD_PREDICT and
+ * STRESS hold the two fused kernels. */
+int nh_set_fd_variant(nh_ctx* ctx, int fused);
+
 /* Autotuner: time every valid LB variant on the context's own domain (a few
  * launches each, CUDA events on stream; the state is not advanced), keep the
  * fastest and return its index in *chosen (may be NULL).  Synchronises. */

@@ -173,6 +173,7 @@ struct nh_ctx {
     double tubes[NH_MAX_TUBES][2] = {};
     bool use_graphs = true;
     int lb_variant = 0;
+    int fd_fused = 1;  // 1: fused 2.5D FD kernels; 0: per-site kernels
     int sm_count = 152;
     int64_t epoch = 0;  // bumped whenever buffers or launch shapes change (invalidates batch plans)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -354,6 +355,9 @@ template <typename Real>
 int enqueue_force_only(nh_ctx* c, cudaStream_t st)
 {
     auto a = fd_chan<Real>(c);
+    if (c->fd_fused)
+        return timed(c, NH_KCLASS_STRESS, st, [&] { return launch_fd_fused_b<Real>(a, a.n, nullptr, st); },
+                     "stress_force");
     int r = timed(c, NH_KCLASS_STRESS, st, [&] { return launch_stress(a, st); }, "stress");
     if (r) return r;
     return timed(c, NH_KCLASS_FORCE, st, [&] { return launch_force(a, st); }, "force");
@@ -363,6 +367,14 @@ template <typename Real>
 int enqueue_fd(nh_ctx* c, cudaStream_t st)
 {
     auto a = fd_chan<Real>(c);
+    if (c->fd_fused) {
+        // predictor + corrector: n -> nP; stress + force from nP, which is copied back into n
+        int r = timed(c, NH_KCLASS_FD_PREDICT, st, [&] { return launch_fd_fused_a<Real>(a, a.n, a.nP, st); },
+                      "fd_fused");
+        if (r) return r;
+        return timed(c, NH_KCLASS_STRESS, st, [&] { return launch_fd_fused_b<Real>(a, a.nP, a.n, st); },
+                     "stress_force");
+    }
     int r = timed(c, NH_KCLASS_FD_PREDICT, st, [&] { return launch_fd_predict(a, st); }, "fd_predict");
     if (r) return r;
     r = timed(c, NH_KCLASS_FD_CORRECT, st, [&] { return launch_fd_correct(a, st); }, "fd_correct");
@@ -374,9 +386,34 @@ template <typename Real>
 int enqueue_predict_correct(nh_ctx* c, cudaStream_t st)
 {
     auto a = fd_chan<Real>(c);
+    if (c->fd_fused) {
+        int r = timed(c, NH_KCLASS_FD_PREDICT, st, [&] { return launch_fd_fused_a<Real>(a, a.n, a.nP, st); },
+                      "fd_fused");
+        if (r) return r;
+        return cudaMemcpyAsync(a.n, a.nP, 3 * (size_t)c->N * sizeof(Real), cudaMemcpyDeviceToDevice, st) == cudaSuccess
+                   ? NH_OK
+                   : fail(c, NH_ECUDA, "copy of the relaxed director");
+    }
     int r = timed(c, NH_KCLASS_FD_PREDICT, st, [&] { return launch_fd_predict(a, st); }, "fd_predict");
     if (r) return r;
     return timed(c, NH_KCLASS_FD_CORRECT, st, [&] { return launch_fd_correct(a, st); }, "fd_correct");
+}
+
+// Relaxation with the fused kernel, alternating n -> nP -> n; an odd count
+// ends with one copy back into n.
+template <typename Real>
+int relax_fused(nh_ctx* c, int64_t steps, cudaStream_t st)
+{
+    auto a = fd_chan<Real>(c);
+    for (int64_t k = 0; k < steps; ++k) {
+        const bool even = (k & 1) == 0;
+        int r = timed(c, NH_KCLASS_FD_PREDICT, st,
+                      [&] { return even ? launch_fd_fused_a<Real>(a, a.n, a.nP, st) : launch_fd_fused_a<Real>(a, a.nP, a.n, st); },
+                      "fd_fused");
+        if (r) return r;
+    }
+    if (steps & 1) NH_CUDA(c, cudaMemcpyAsync(a.n, a.nP, 3 * (size_t)c->N * sizeof(Real), cudaMemcpyDeviceToDevice, st));
+    return NH_OK;
 }
 
 int enqueue_fd_any(nh_ctx* c, cudaStream_t st)
@@ -687,6 +724,28 @@ int batch_fd_typed(BatchPlan* b, cudaStream_t st, int stages = 4)
     nh_ctx* c0 = b->ctxs[0];
     const int n = (int)b->ctxs.size();
     static thread_local FDBatch<Real> batch;
+    if (c0->fd_fused) {
+        // stages == 4: full FD update (A: n -> nP, B: nP -> F and n); stages == 2: one relaxation step (A, copy back)
+        const int fstages[2] = {0, 1};
+        const int classes[2] = {NH_KCLASS_FD_PREDICT, NH_KCLASS_STRESS};
+        for (int k = 0; k < (stages == 4 ? 2 : 1); ++k) {
+            for (int g0 = 0; g0 < n; g0 += kMaxBatch) {
+                batch.count = std::min(kMaxBatch, n - g0);
+                for (int j = 0; j < batch.count; ++j) batch.ch[j] = fd_chan<Real>(b->ctxs[g0 + j]);
+                const int grid = 8 * c0->sm_count;
+                int r = timed(c0, classes[k], st, [&] { return launch_fd_fused_batch(batch, fstages[k], grid, st); },
+                              "fd_fused_batch");
+                if (r) return r;
+            }
+        }
+        if (stages != 4)
+            for (nh_ctx* c : b->ctxs) {
+                cudaError_t e = cudaMemcpyAsync(c->ws + c->L.n, c->ws + c->L.nP, 3 * (size_t)c->N * sizeof(Real),
+                                                cudaMemcpyDeviceToDevice, st);
+                if (e != cudaSuccess) return fail(c0, NH_ECUDA, "copy of the relaxed director");
+            }
+        return NH_OK;
+    }
     const int classes[4] = {NH_KCLASS_FD_PREDICT, NH_KCLASS_FD_CORRECT, NH_KCLASS_STRESS, NH_KCLASS_FORCE};
     for (int stage = 0; stage < stages; ++stage) {
         for (int g0 = 0; g0 < n; g0 += kMaxBatch) {
@@ -1142,8 +1201,13 @@ int nh_relax(nh_ctx* c, int64_t n_fd_steps, void* stream)
     if ((r = set_device(c))) return r;
     cudaStream_t st = pick(c, stream);
     NH_CUDA(c, cudaMemsetAsync(c->ws + c->L.u, 0, 3 * (size_t)c->N * real_size(c->p), st));
-    for (int64_t k = 0; k < n_fd_steps && r == NH_OK; ++k)
-        r = c->p.precision == NH_FP64 ? enqueue_predict_correct<double>(c, st) : enqueue_predict_correct<float>(c, st);
+    if (c->fd_fused) {
+        r = c->p.precision == NH_FP64 ? relax_fused<double>(c, n_fd_steps, st) : relax_fused<float>(c, n_fd_steps, st);
+    } else {
+        for (int64_t k = 0; k < n_fd_steps && r == NH_OK; ++k)
+            r = c->p.precision == NH_FP64 ? enqueue_predict_correct<double>(c, st)
+                                          : enqueue_predict_correct<float>(c, st);
+    }
     close_segment(c);
     return r;
 }
@@ -1305,6 +1369,15 @@ int nh_set_lb_variant(nh_ctx* c, int variant)
     if (!lb_variant_valid(variant, c->p.nx)) return fail(c, NH_EINVAL, "LB variant not valid for this domain");
     if (variant != c->lb_variant) drop_graphs(c);
     c->lb_variant = variant;
+    return NH_OK;
+}
+
+int nh_set_fd_variant(nh_ctx* c, int fused)
+{
+    if (!c) return fail(nullptr, NH_EINVAL, "ctx is NULL");
+    if (fused != 0 && fused != 1) return fail(c, NH_EINVAL, "FD variant must be 0 or 1");
+    if (fused != c->fd_fused) drop_graphs(c);
+    c->fd_fused = fused;
     return NH_OK;
 }
 

@@ -171,18 +171,15 @@ __device__ __forceinline__ void fd_correct_site(const FDChan<Real>& c, int s)
     for (int a = 0; a < 3; ++a) c.n[a * N + s] = nw[a] * inv;
 }
 
+// LC stress (Eq. force-lc-eq, bracket) at one point from its 7-point
+// neighbourhood of n and u: sigma[3a+b].
 template <typename Real>
-__device__ __forceinline__ void stress_site(const FDChan<Real>& c, int s)
+__device__ __forceinline__ void stress_point(const Real nn[7][3], const Real uu[7][3], const FDPar<Real>& p,
+                                             Real sig[9])
 {
-    int x, y, z;
-    site_xyz<Real>(c.g, s, x, y, z);
-    Real nn[7][3], uu[7][3];
-    gather7(c.n, c.g, x, y, z, nn, true);
-    gather7(c.u, c.g, x, y, z, uu, false);
     Real dn[3][3], du[3][3], h[3];
-    local_fields(nn, uu, c.p, dn, du, h);
+    local_fields(nn, uu, p, dn, du, h);
     const Real* n = nn[0];
-    const FDPar<Real>& p = c.p;
     Real D[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -199,7 +196,6 @@ __device__ __forceinline__ void stress_site(const FDChan<Real>& c, int s)
     for (int m = 0; m < 3; ++m) Nv[m] = ((h[m] - hn * n[m]) - p.gamma2 * (Dn[m] - n[m] * nDn)) * p.inv_gamma1;
     // chi[b][g] = eps_{c b g} n_c
     const Real chi[3][3] = {{0, n[2], -n[1]}, {-n[2], 0, n[0]}, {n[1], -n[0], 0}};
-    const int N = c.g.N;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -209,8 +205,22 @@ __device__ __forceinline__ void stress_site(const FDChan<Real>& c, int s)
             Real se = 0;
 #pragma unroll
             for (int gg = 0; gg < 3; ++gg) se -= dn[a][gg] * (p.K * dn[b][gg] + p.K * p.q0 * chi[b][gg]);
-            c.sigma[(3 * a + b) * N + s] = sv + se;
+            sig[3 * a + b] = sv + se;
         }
+}
+
+template <typename Real>
+__device__ __forceinline__ void stress_site(const FDChan<Real>& c, int s)
+{
+    int x, y, z;
+    site_xyz<Real>(c.g, s, x, y, z);
+    Real nn[7][3], uu[7][3], sig[9];
+    gather7(c.n, c.g, x, y, z, nn, true);
+    gather7(c.u, c.g, x, y, z, uu, false);
+    stress_point(nn, uu, c.p, sig);
+    const int N = c.g.N;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) c.sigma[k * N + s] = sig[k];
 }
 
 template <typename Real>
@@ -283,6 +293,310 @@ __global__ void __launch_bounds__(256) fd_batch_kernel(const FDBatch<Real> b)
     }
 }
 
+// ------------------------------------------------------------------ fused 2.5D kernels
+//
+// A block owns a tile of kTX x kTY columns and marches up a chunk of kZC
+// layers.  Planes of n and u with a 2-site halo in x and y sit in a ring of 4
+// shared-memory slots; the predictor (kernel A) or the stress (kernel B) is
+// evaluated on each plane with a 1-site halo into a ring of 3 slots, so every
+// stencil reads shared memory at fixed offsets and the ghost layers are
+// resolved once, at load time.
+//   kernel A: n, u -> n_new   (predictor, corrector, renormalisation)
+//   kernel B: n_new, u -> F   (stress, divergence; sigma never leaves the SM)
+
+constexpr int kTX = 32, kTY = 8, kZC = 16;
+constexpr int kHX2 = kTX + 4, kHY2 = kTY + 4, kP2 = kHX2 * kHY2;  // plane with a 2-site halo
+constexpr int kHX1 = kTX + 2, kHY1 = kTY + 2, kP1 = kHX1 * kHY1;  // plane with a 1-site halo
+constexpr int kFusedThreads = 256;
+
+__device__ __forceinline__ int wrapm(int a, int n)
+{
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+__device__ __forceinline__ int slot4(int p) { return ((p % 4) + 4) % 4; }
+__device__ __forceinline__ int slot3(int p) { return ((p % 3) + 3) % 3; }
+
+template <typename Real>
+size_t fused_a_smem() { return (size_t)(4 * 6 * kP2 + 3 * 6 * kP1) * sizeof(Real); }
+template <typename Real>
+size_t fused_b_smem() { return (size_t)(4 * 6 * kP2 + 3 * 9 * kP1) * sizeof(Real); }
+
+// Plane zp of n (ghost reading) and u (zero beyond the plates) into one
+// input slot: [n_x | n_y | n_z | u_x | u_y | u_z] x kP2.
+template <typename Real>
+__device__ void load_plane(const Real* __restrict__ n, const Real* __restrict__ u, const Geom& g, int x0, int y0,
+                           int zp, Real* slot)
+{
+    bool ghost = false;
+    int zz;
+    if (g.walls) {
+        ghost = zp < 0 || zp >= g.nz;
+        zz = zp < 0 ? 0 : (zp >= g.nz ? g.nz - 1 : zp);
+    } else {
+        zz = wrapm(zp, g.nz);
+    }
+    const bool fixed_dir = ghost && g.anchoring == NH_ANCHOR_HOMEOTROPIC;
+    const size_t N = (size_t)g.N;
+    for (int i = threadIdx.x; i < kP2; i += blockDim.x) {
+        const int hx = i % kHX2, hy = i / kHX2;
+        const int x = wrapm(x0 - 2 + hx, g.nx), y = wrapm(y0 - 2 + hy, g.ny);
+        const size_t s = (size_t)x + (size_t)g.nx * ((size_t)y + (size_t)g.ny * zz);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            slot[a * kP2 + i] = fixed_dir ? Real(a == 2 ? 1 : 0) : n[a * N + s];
+            slot[(3 + a) * kP2 + i] = ghost ? Real(0) : u[a * N + s];
+        }
+    }
+}
+
+// 7-point neighbourhoods of n (components 0..2 of the slots) and u (3..5)
+// around P2 index i2 of the middle plane.
+template <typename Real>
+__device__ __forceinline__ void gather_slots(const Real* lo, const Real* mid, const Real* hi, int i2, Real nn[7][3],
+                                             Real uu[7][3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        nn[0][a] = mid[a * kP2 + i2];
+        nn[1][a] = mid[a * kP2 + i2 + 1];
+        nn[2][a] = mid[a * kP2 + i2 - 1];
+        nn[3][a] = mid[a * kP2 + i2 + kHX2];
+        nn[4][a] = mid[a * kP2 + i2 - kHX2];
+        nn[5][a] = hi[a * kP2 + i2];
+        nn[6][a] = lo[a * kP2 + i2];
+        uu[0][a] = mid[(3 + a) * kP2 + i2];
+        uu[1][a] = mid[(3 + a) * kP2 + i2 + 1];
+        uu[2][a] = mid[(3 + a) * kP2 + i2 - 1];
+        uu[3][a] = mid[(3 + a) * kP2 + i2 + kHX2];
+        uu[4][a] = mid[(3 + a) * kP2 + i2 - kHX2];
+        uu[5][a] = hi[(3 + a) * kP2 + i2];
+        uu[6][a] = lo[(3 + a) * kP2 + i2];
+    }
+}
+
+__device__ __forceinline__ bool is_ghost_plane(const Geom& g, int p) { return g.walls && (p < 0 || p >= g.nz); }
+
+// Kernel A tile: predictor on plane p into ring slot [nP x3 | rate x3] x kP1.
+template <typename Real>
+__device__ void predict_plane(const FDPar<Real>& par, Real* in, int p, Real* pslot)
+{
+    const Real* lo = in + slot4(p - 1) * 6 * kP2;
+    const Real* mid = in + slot4(p) * 6 * kP2;
+    const Real* hi = in + slot4(p + 1) * 6 * kP2;
+    for (int i1 = threadIdx.x; i1 < kP1; i1 += blockDim.x) {
+        const int hx1 = i1 % kHX1, hy1 = i1 / kHX1;
+        const int i2 = (hx1 + 1) + kHX2 * (hy1 + 1);
+        Real nn[7][3], uu[7][3], r[3];
+        gather_slots(lo, mid, hi, i2, nn, uu);
+        director_rate(nn, uu, par, r);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            pslot[a * kP1 + i1] = nn[0][a] + par.dt * r[a];
+            pslot[(3 + a) * kP1 + i1] = r[a];
+        }
+    }
+}
+
+template <typename Real>
+__device__ void fused_a_tile(const FDChan<Real>& c, const Real* __restrict__ nin, Real* __restrict__ nout, int tile)
+{
+    extern __shared__ __align__(16) unsigned char smem_fd[];
+    Real* in = reinterpret_cast<Real*>(smem_fd);  // 4 slots x 6 x kP2
+    Real* pr = in + 4 * 6 * kP2;                  // 3 slots x 6 x kP1
+    const Geom& g = c.g;
+    const int ntx = (g.nx + kTX - 1) / kTX, nty = (g.ny + kTY - 1) / kTY;
+    const int tx_t = tile % ntx, ty_t = (tile / ntx) % nty, zc = tile / (ntx * nty);
+    const int x0 = tx_t * kTX, y0 = ty_t * kTY;
+    const int zb = zc * kZC, ze = min(zb + kZC, g.nz);
+    const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
+    const bool active = threadIdx.x < kTX * kTY && x0 + tx < g.nx && y0 + ty < g.ny;
+    const size_t N = (size_t)g.N;
+    for (int p = zb - 2; p <= zb + 1; ++p) load_plane(nin, c.u, g, x0, y0, p, in + slot4(p) * 6 * kP2);
+    __syncthreads();
+    for (int p = zb - 1; p <= zb; ++p)
+        if (!is_ghost_plane(g, p)) predict_plane(c.p, in, p, pr + slot3(p) * 6 * kP1);
+    __syncthreads();
+    for (int z = zb; z < ze; ++z) {
+        load_plane(nin, c.u, g, x0, y0, z + 2, in + slot4(z + 2) * 6 * kP2);
+        __syncthreads();
+        if (!is_ghost_plane(g, z + 1)) predict_plane(c.p, in, z + 1, pr + slot3(z + 1) * 6 * kP1);
+        __syncthreads();
+        if (active) {
+            const int i1 = (tx + 1) + kHX1 * (ty + 1);
+            const int i2 = (tx + 2) + kHX2 * (ty + 2);
+            const Real* mid = pr + slot3(z) * 6 * kP1;
+            // predictor of the planes above and below; at a plate the ghost
+            // value (z_hat, or the adjacent fluid layer without anchoring)
+            const bool glo = is_ghost_plane(g, z - 1), ghi = is_ghost_plane(g, z + 1);
+            const bool homeo = g.anchoring == NH_ANCHOR_HOMEOTROPIC;
+            const Real* lo = glo ? mid : pr + slot3(z - 1) * 6 * kP1;
+            const Real* hi = ghi ? mid : pr + slot3(z + 1) * 6 * kP1;
+            const Real* inm = in + slot4(z) * 6 * kP2;
+            const Real* inl = in + slot4(z - 1) * 6 * kP2;
+            const Real* inh = in + slot4(z + 1) * 6 * kP2;
+            Real nn[7][3], uu[7][3], r[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                nn[0][a] = mid[a * kP1 + i1];
+                nn[1][a] = mid[a * kP1 + i1 + 1];
+                nn[2][a] = mid[a * kP1 + i1 - 1];
+                nn[3][a] = mid[a * kP1 + i1 + kHX1];
+                nn[4][a] = mid[a * kP1 + i1 - kHX1];
+                nn[5][a] = (ghi && homeo) ? Real(a == 2 ? 1 : 0) : hi[a * kP1 + i1];
+                nn[6][a] = (glo && homeo) ? Real(a == 2 ? 1 : 0) : lo[a * kP1 + i1];
+                uu[0][a] = inm[(3 + a) * kP2 + i2];
+                uu[1][a] = inm[(3 + a) * kP2 + i2 + 1];
+                uu[2][a] = inm[(3 + a) * kP2 + i2 - 1];
+                uu[3][a] = inm[(3 + a) * kP2 + i2 + kHX2];
+                uu[4][a] = inm[(3 + a) * kP2 + i2 - kHX2];
+                uu[5][a] = inh[(3 + a) * kP2 + i2];
+                uu[6][a] = inl[(3 + a) * kP2 + i2];
+            }
+            director_rate(nn, uu, c.p, r);
+            Real nw[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) nw[a] = inm[a * kP2 + i2] + c.p.dt * Real(0.5) * (mid[(3 + a) * kP1 + i1] + r[a]);
+            const Real inv = Real(1) / sqrt(nw[0] * nw[0] + nw[1] * nw[1] + nw[2] * nw[2]);
+            const size_t s = (size_t)(x0 + tx) + (size_t)g.nx * ((size_t)(y0 + ty) + (size_t)g.ny * z);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) nout[a * N + s] = nw[a] * inv;
+        }
+        __syncthreads();
+    }
+}
+
+// Kernel B tile: stress on plane p into ring slot [sigma x9] x kP1 (zero at ghosts).
+template <typename Real>
+__device__ void stress_plane(const FDChan<Real>& c, Real* in, int p, Real* sslot)
+{
+    if (is_ghost_plane(c.g, p)) {
+        for (int i = threadIdx.x; i < 9 * kP1; i += blockDim.x) sslot[i] = Real(0);
+        return;
+    }
+    const Real* lo = in + slot4(p - 1) * 6 * kP2;
+    const Real* mid = in + slot4(p) * 6 * kP2;
+    const Real* hi = in + slot4(p + 1) * 6 * kP2;
+    for (int i1 = threadIdx.x; i1 < kP1; i1 += blockDim.x) {
+        const int hx1 = i1 % kHX1, hy1 = i1 / kHX1;
+        const int i2 = (hx1 + 1) + kHX2 * (hy1 + 1);
+        Real nn[7][3], uu[7][3], sig[9];
+        gather_slots(lo, mid, hi, i2, nn, uu);
+        stress_point(nn, uu, c.p, sig);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) sslot[k * kP1 + i1] = sig[k];
+    }
+}
+
+template <typename Real>
+__device__ void fused_b_tile(const FDChan<Real>& c, const Real* __restrict__ nin, Real* __restrict__ ncopy, int tile)
+{
+    extern __shared__ __align__(16) unsigned char smem_fd[];
+    Real* in = reinterpret_cast<Real*>(smem_fd);  // 4 slots x 6 x kP2
+    Real* sg = in + 4 * 6 * kP2;                  // 3 slots x 9 x kP1
+    const Geom& g = c.g;
+    const int ntx = (g.nx + kTX - 1) / kTX, nty = (g.ny + kTY - 1) / kTY;
+    const int tx_t = tile % ntx, ty_t = (tile / ntx) % nty, zc = tile / (ntx * nty);
+    const int x0 = tx_t * kTX, y0 = ty_t * kTY;
+    const int zb = zc * kZC, ze = min(zb + kZC, g.nz);
+    const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
+    const bool active = threadIdx.x < kTX * kTY && x0 + tx < g.nx && y0 + ty < g.ny;
+    const size_t N = (size_t)g.N;
+    for (int p = zb - 2; p <= zb + 1; ++p) load_plane(nin, c.u, g, x0, y0, p, in + slot4(p) * 6 * kP2);
+    __syncthreads();
+    for (int p = zb - 1; p <= zb; ++p) stress_plane(c, in, p, sg + slot3(p) * 9 * kP1);
+    __syncthreads();
+    for (int z = zb; z < ze; ++z) {
+        load_plane(nin, c.u, g, x0, y0, z + 2, in + slot4(z + 2) * 6 * kP2);
+        __syncthreads();
+        stress_plane(c, in, z + 1, sg + slot3(z + 1) * 9 * kP1);
+        __syncthreads();
+        if (active) {
+            const int i1 = (tx + 1) + kHX1 * (ty + 1);
+            const Real* mid = sg + slot3(z) * 9 * kP1;
+            const Real* lo = sg + slot3(z - 1) * 9 * kP1;
+            const Real* hi = sg + slot3(z + 1) * 9 * kP1;
+            const size_t s = (size_t)(x0 + tx) + (size_t)g.nx * ((size_t)(y0 + ty) + (size_t)g.ny * z);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const Real dx = mid[(3 * a + 0) * kP1 + i1 + 1] - mid[(3 * a + 0) * kP1 + i1 - 1];
+                const Real dy = mid[(3 * a + 1) * kP1 + i1 + kHX1] - mid[(3 * a + 1) * kP1 + i1 - kHX1];
+                const Real dz = hi[(3 * a + 2) * kP1 + i1] - lo[(3 * a + 2) * kP1 + i1];
+                c.F[a * N + s] = Real(0.5) * (dx + dy + dz);
+            }
+            if (ncopy) {
+                const Real* inm = in + slot4(z) * 6 * kP2;
+                const int i2 = (tx + 2) + kHX2 * (ty + 2);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) ncopy[a * N + s] = inm[a * kP2 + i2];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(kFusedThreads) fused_a_kernel(const FDChan<Real> c, const Real* nin, Real* nout)
+{
+    fused_a_tile(c, nin, nout, blockIdx.x);
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(kFusedThreads) fused_b_kernel(const FDChan<Real> c, const Real* nin, Real* ncopy)
+{
+    fused_b_tile(c, nin, ncopy, blockIdx.x);
+}
+
+// Batched fused kernels: a persistent grid walks the (channel, tile) work
+// list; stage 0 = kernel A (n -> nP), 1 = kernel B (nP -> F, copy into n),
+// 2 = kernel A (nP -> n), for relaxations that alternate the two buffers.
+template <typename Real, int Stage>
+__global__ void __launch_bounds__(kFusedThreads) fused_batch_kernel(const FDBatch<Real> b)
+{
+    const int total = b.prefix[b.count];
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        int lo = 0, hi = b.count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (b.prefix[mid] <= t)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const FDChan<Real>& c = b.ch[lo];
+        if (Stage == 0)
+            fused_a_tile(c, c.n, c.nP, t - b.prefix[lo]);
+        else if (Stage == 1)
+            fused_b_tile(c, c.nP, c.n, t - b.prefix[lo]);
+        else
+            fused_a_tile(c, c.nP, c.n, t - b.prefix[lo]);
+        __syncthreads();
+    }
+}
+
+inline int fused_tiles(const Geom& g)
+{
+    return ((g.nx + kTX - 1) / kTX) * ((g.ny + kTY - 1) / kTY) * ((g.nz + kZC - 1) / kZC);
+}
+
+template <typename Real>
+cudaError_t prepare_fused()
+{
+    static bool done = false;  // the attribute is per function; setting it twice is harmless
+    if (done) return cudaSuccess;
+    const int a = (int)fused_a_smem<Real>(), b = (int)fused_b_smem<Real>();
+    cudaError_t e = cudaFuncSetAttribute(fused_a_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, a);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fused_b_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        const int bytes = k == 1 ? b : a;
+        if (k == 0) e = cudaFuncSetAttribute(fused_batch_kernel<Real, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (k == 1) e = cudaFuncSetAttribute(fused_batch_kernel<Real, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (k == 2) e = cudaFuncSetAttribute(fused_batch_kernel<Real, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    }
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
 inline int blocks_for(int N) { return (N + 255) / 256; }
 
 }  // namespace
@@ -329,6 +643,49 @@ cudaError_t launch_force(const FDChan<Real>& c, cudaStream_t st)
     fd_kernel<Real, 3><<<blocks_for(c.g.N), 256, 0, st>>>(c);
     return cudaGetLastError();
 }
+
+template <typename Real>
+cudaError_t launch_fd_fused_a(const FDChan<Real>& c, const Real* nin, Real* nout, cudaStream_t st)
+{
+    cudaError_t e = prepare_fused<Real>();
+    if (e != cudaSuccess) return e;
+    fused_a_kernel<Real><<<fused_tiles(c.g), kFusedThreads, fused_a_smem<Real>(), st>>>(c, nin, nout);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t launch_fd_fused_b(const FDChan<Real>& c, const Real* nin, Real* ncopy, cudaStream_t st)
+{
+    cudaError_t e = prepare_fused<Real>();
+    if (e != cudaSuccess) return e;
+    fused_b_kernel<Real><<<fused_tiles(c.g), kFusedThreads, fused_b_smem<Real>(), st>>>(c, nin, ncopy);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t launch_fd_fused_batch(FDBatch<Real>& b, int stage, int grid, cudaStream_t st)
+{
+    if (b.count < 1 || b.count > kMaxBatch) return cudaErrorInvalidValue;
+    cudaError_t e = prepare_fused<Real>();
+    if (e != cudaSuccess) return e;
+    b.prefix[0] = 0;
+    for (int k = 0; k < b.count; ++k) b.prefix[k + 1] = b.prefix[k] + fused_tiles(b.ch[k].g);
+    const int blocks = grid < b.prefix[b.count] ? grid : b.prefix[b.count];
+    const size_t smem = stage == 1 ? fused_b_smem<Real>() : fused_a_smem<Real>();
+    switch (stage) {
+    case 0: fused_batch_kernel<Real, 0><<<blocks, kFusedThreads, smem, st>>>(b); break;
+    case 1: fused_batch_kernel<Real, 1><<<blocks, kFusedThreads, smem, st>>>(b); break;
+    default: fused_batch_kernel<Real, 2><<<blocks, kFusedThreads, smem, st>>>(b); break;
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_fd_fused_a<double>(const FDChan<double>&, const double*, double*, cudaStream_t);
+template cudaError_t launch_fd_fused_a<float>(const FDChan<float>&, const float*, float*, cudaStream_t);
+template cudaError_t launch_fd_fused_b<double>(const FDChan<double>&, const double*, double*, cudaStream_t);
+template cudaError_t launch_fd_fused_b<float>(const FDChan<float>&, const float*, float*, cudaStream_t);
+template cudaError_t launch_fd_fused_batch<double>(FDBatch<double>&, int, int, cudaStream_t);
+template cudaError_t launch_fd_fused_batch<float>(FDBatch<float>&, int, int, cudaStream_t);
 
 template cudaError_t launch_fd_predict<double>(const FDChan<double>&, cudaStream_t);
 template cudaError_t launch_fd_predict<float>(const FDChan<float>&, cudaStream_t);

@@ -154,6 +154,17 @@ cudaError_t launch_lb_batch(LBBatch<Real, Store>& b, bool shifted, bool write_ma
 template <typename Real>
 cudaError_t launch_fd_batch(FDBatch<Real>& b, int stage, int grid, cudaStream_t s);
 
+// Fused FD kernels (2.5D shared-memory tiles): A = predictor + corrector +
+// renormalisation (nin, u -> nout), B = stress + force (nin, u -> F; copies
+// nin into ncopy when ncopy is not null); batched stages 0 = A (n -> nP),
+// 1 = B (nP -> F, n), 2 = A (nP -> n).
+template <typename Real>
+cudaError_t launch_fd_fused_a(const FDChan<Real>& c, const Real* nin, Real* nout, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_fd_fused_b(const FDChan<Real>& c, const Real* nin, Real* ncopy, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_fd_fused_batch(FDBatch<Real>& b, int stage, int grid, cudaStream_t s);
+
 template <typename Real>
 cudaError_t launch_fd_predict(const FDChan<Real>& c, cudaStream_t s);
 template <typename Real>

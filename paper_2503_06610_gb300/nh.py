@@ -103,6 +103,7 @@ SIGNATURES = {
     "nh_launch_count": ([_VP], ctypes.c_int64),
     "nh_set_graphs": ([_VP, ctypes.c_int], ctypes.c_int),
     "nh_set_lb_variant": ([_VP, ctypes.c_int], ctypes.c_int),
+    "nh_set_fd_variant": ([_VP, ctypes.c_int], ctypes.c_int),
     "nh_autotune": ([_VP, _VP, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "nh_destroy": ([_VP], None),
     "nh_unet_param_count": ([], ctypes.c_int64),
@@ -321,6 +322,10 @@ def nh_set_lb_variant(ctx, variant: int):
     _check(load_library().nh_set_lb_variant(ctx, int(variant)), ctx)
 
 
+def nh_set_fd_variant(ctx, fused: int):
+    _check(load_library().nh_set_fd_variant(ctx, int(fused)), ctx)
+
+
 def nh_autotune(ctx, stream=None) -> int:
     out = ctypes.c_int(-1)
     _check(load_library().nh_autotune(ctx, _VP(stream or 0), ctypes.byref(out)), ctx)
@@ -432,6 +437,9 @@ class Channel:
 
     def set_lb_variant(self, variant):
         nh_set_lb_variant(self.ctx, variant)
+
+    def set_fd_variant(self, fused):
+        nh_set_fd_variant(self.ctx, fused)
 
     def autotune(self):
         return nh_autotune(self.ctx, self.stream.cuda_stream)

@@ -72,29 +72,40 @@ def test_lb_rows_fp64(nh, oracle_mod, shifted, walls):
     assert np.max(np.abs(f - ref.f)) < 1e-13
 
 
+GRIDS = [(13, 9, 7), (40, 20, 20)]   # ragged; several x-y tiles and two z chunks
+
+
+@pytest.mark.parametrize("fused", [1, 0])
+@pytest.mark.parametrize("grid", GRIDS)
 @pytest.mark.parametrize("anchoring,walls", [("homeotropic", True), ("none", True), ("homeotropic", False)])
-def test_stress_force_rows_fp64(nh, oracle_mod, anchoring, walls):
+def test_stress_force_rows_fp64(nh, oracle_mod, anchoring, walls, grid, fused):
     O = oracle_mod
-    params = _generic(13, 9, 7, walls_z=walls, anchoring=anchoring, W0=0.02, alpha1=0.1, alpha4p=0.2)
-    n0 = I.random_director(13, 9, 7, seed=5)
-    u0 = I.random_velocity(13, 9, 7, 1e-3, seed=6)
+    params = _generic(*grid, walls_z=walls, anchoring=anchoring, W0=0.02, alpha1=0.1, alpha4p=0.2)
+    n0 = I.random_director(*grid, seed=5)
+    u0 = I.random_velocity(*grid, 1e-3, seed=6)
     p = O.OracleParams.from_dict(params)
     Fref = O.force(p, O.stress(p, n0, u0))
-    ch = _channel(nh, params, n0, u0, precision="fp64")
+    ch = nh.Channel(dict(params, precision="fp64"))
+    ch.set_fd_variant(fused)
+    ch.set_fields(n0, u0)
     F = ch.get_force()
     assert O.rel_l2(F, Fref) < 1e-12
 
 
+@pytest.mark.parametrize("fused", [1, 0])
+@pytest.mark.parametrize("grid", GRIDS)
 @pytest.mark.parametrize("anchoring,walls", [("homeotropic", True), ("none", True), ("homeotropic", False)])
-def test_fd_update_rows_fp64(nh, oracle_mod, anchoring, walls):
+def test_fd_update_rows_fp64(nh, oracle_mod, anchoring, walls, grid, fused):
     O = oracle_mod
-    params = _generic(13, 9, 7, walls_z=walls, anchoring=anchoring, W0=0.02, dt_fd=3)
-    n0 = I.random_director(13, 9, 7, seed=7)
-    u0 = I.random_velocity(13, 9, 7, 1e-2, seed=8)
+    params = _generic(*grid, walls_z=walls, anchoring=anchoring, W0=0.02, dt_fd=3)
+    n0 = I.random_director(*grid, seed=7)
+    u0 = I.random_velocity(*grid, 1e-2, seed=8)
     p = O.OracleParams.from_dict(params)
     nref = O.fd_step(p, n0, u0)
     Fref = O.force(p, O.stress(p, nref, u0))
-    ch = _channel(nh, params, n0, u0, precision="fp64")
+    ch = nh.Channel(dict(params, precision="fp64"))
+    ch.set_fd_variant(fused)
+    ch.set_fields(n0, u0)
     ch.fd_update()
     n, u, _ = ch.get_fields()
     assert O.rel_l2(n, nref) < 1e-13
@@ -453,6 +464,13 @@ def test_relax_matches_oracle_gradient_flow(nh, oracle_mod, anchoring):
     u = np.zeros_like(n0)
     for _ in range(12):
         n = O.fd_step(p, n, u)
+    for fused in (0, 1):
+        chv = nh.Channel(dict(params, precision="fp64"))
+        chv.set_fd_variant(fused)
+        chv.set_fields(n0)
+        chv.relax(11)
+        chv.relax(1)
+        assert O.rel_l2(chv.get_fields()[0], n) < 1e-12
     ch = _channel(nh, params, n0, I.random_velocity(16, 12, 8, 1e-3, seed=1), precision="fp64")
     ch.relax(12)
     ng, ug, _ = ch.get_fields()
