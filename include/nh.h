@@ -218,6 +218,14 @@ int nh_batch_relax(nh_ctx* const* ctxs, int count, int64_t n_fd_steps, void* str
  * decide when a relaxation has converged.  Synchronises the stream. */
 int nh_director_change(nh_ctx* ctx, double* max_change);
 
+/* Project the director onto fields symmetric under rotations by 90 degrees
+ * about the z axis through the site (nx/2, nx/2) (requires nx == ny): the
+ * average of the four rotated images (site and vector rotated), normalised.
+ * Rotations about z are symmetries of the chiral Frank energy, the plates and
+ * the director equation at rest, so a tube centred on that axis stays
+ * centred.  Populations and F_lc are not updated.  Asynchronous. */
+int nh_symmetrize_c4(nh_ctx* ctx);
+
 /* Set the tube centroids to track (count <= NH_MAX_TUBES, centres[2*count]
  * as (x, y) pairs); 0 disables tracking. */
 int nh_set_tubes(nh_ctx* ctx, const double* centres, int count);

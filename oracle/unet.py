@@ -95,13 +95,48 @@ def up(x):
     return x.repeat_interleave(2, dim=2).repeat_interleave(2, dim=3).repeat_interleave(2, dim=4)
 
 
-def forward(params, x, n_ansatz):
-    """x [B][16][Z][Y][X], n_ansatz [B][3][Z][Y][X] -> (n_pred, delta)."""
-    r = lambda name, t: F.relu(conv3(t, *params[name]))
+def _bf16(t):
+    return t.to(torch.bfloat16).to(t.dtype)
+
+
+class _RoundAct(torch.autograd.Function):
+    """Rounds a stored activation to BF16 and the gradient arriving at it to
+    BF16 (a layer output kept in BF16 whose gradient enters BF16 matrix products)."""
+
+    @staticmethod
+    def forward(ctx, t):
+        return _bf16(t)
+
+    @staticmethod
+    def backward(ctx, g):
+        return _bf16(g)
+
+
+class _RoundFwd(torch.autograd.Function):
+    """Rounds to BF16 in the forward pass only (a BF16 copy whose gradient stays in FP32)."""
+
+    @staticmethod
+    def forward(ctx, t):
+        return _bf16(t)
+
+    @staticmethod
+    def backward(ctx, g):
+        return g
+
+
+def forward(params, x, n_ansatz, bf16_storage=False):
+    """x [B][16][Z][Y][X], n_ansatz [B][3][Z][Y][X] -> (n_pred, delta).
+
+    bf16_storage=True keeps every stored activation in BF16 and rounds the
+    gradient entering each convolution to BF16, as a BF16-activation
+    implementation does; the arithmetic itself stays float64."""
+    ra = _RoundAct.apply if bf16_storage else (lambda t: t)
+    rf = _RoundFwd.apply if bf16_storage else (lambda t: t)
+    r = lambda name, t: ra(F.relu(conv3(t, *params[name])))
     e1 = r("enc1b", r("enc1a", x))
-    e2 = r("enc2b", r("enc2a", pool(e1)))
-    e3 = r("enc3b", r("enc3a", pool(e2)))
-    bt = r("botb", r("bota", pool(e3)))
+    e2 = r("enc2b", r("enc2a", rf(pool(e1))))
+    e3 = r("enc3b", r("enc3a", rf(pool(e2))))
+    bt = r("botb", r("bota", rf(pool(e3))))
     d3 = r("dec3b", r("dec3a", torch.cat([up(bt), e3], dim=1)))
     d2 = r("dec2b", r("dec2a", torch.cat([up(d3), e2], dim=1)))
     d1 = r("dec1b", r("dec1a", torch.cat([up(d2), e1], dim=1)))
@@ -116,11 +151,11 @@ def loss_fn(n_pred, n_target):
     return ((n_pred - n_target) ** 2).sum(dim=1).mean()
 
 
-def loss_and_grad(flat, x, n_ansatz, n_target):
+def loss_and_grad(flat, x, n_ansatz, n_target, bf16_storage=False):
     """Loss and d loss / d params (flat layout) by autograd in float64."""
     flat_t = torch.tensor(np.asarray(flat, dtype=np.float64), requires_grad=True)
     params = unpack_tensor(flat_t)
-    n_pred, _ = forward(params, x, n_ansatz)
+    n_pred, _ = forward(params, x, n_ansatz, bf16_storage)
     loss = loss_fn(n_pred, n_target)
     loss.backward()
     return float(loss), flat_t.grad.numpy().copy(), n_pred.detach()

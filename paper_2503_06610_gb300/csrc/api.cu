@@ -1253,6 +1253,24 @@ int nh_director_change(nh_ctx* c, double* max_change)
     return NH_OK;
 }
 
+int nh_symmetrize_c4(nh_ctx* c)
+{
+    int r = check_ready(c);
+    if (r) return r;
+    if (!c->fields_set) return fail(c, NH_EINVAL, "nh_set_fields must be called before nh_symmetrize_c4");
+    if (c->p.nx != c->p.ny) return fail(c, NH_EINVAL, "C4 symmetrisation needs nx == ny");
+    if ((r = set_device(c))) return r;
+    cudaStream_t st = c->stream;
+    const size_t bytes = 3 * (size_t)c->N * real_size(c->p);
+    if (c->p.precision == NH_FP64)
+        NH_CUDA(c, launch_symmetrize_c4<double>(c->at<double>(c->L.n), c->at<double>(c->L.nP), c->p.nx, c->p.nz, st));
+    else
+        NH_CUDA(c, launch_symmetrize_c4<float>(c->at<float>(c->L.n), c->at<float>(c->L.nP), c->p.nx, c->p.nz, st));
+    c->launches += 1;
+    NH_CUDA(c, cudaMemcpyAsync(c->ws + c->L.n, c->ws + c->L.nP, bytes, cudaMemcpyDeviceToDevice, st));
+    return NH_OK;
+}
+
 int nh_set_tubes(nh_ctx* c, const double* centres, int count)
 {
     if (!c) return fail(nullptr, NH_EINVAL, "ctx is NULL");

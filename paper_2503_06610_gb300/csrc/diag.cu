@@ -418,9 +418,54 @@ __global__ void max_final_kernel(const double* __restrict__ partial, double* __r
     if (threadIdx.x == 0) *out = m;
 }
 
+// Average of the four images of n under rotations by 90 degrees about the
+// z axis through the site (c, c), c = nx / 2 (requires nx == ny): with
+// X = x - c, Y = y - c and R n = (-n_y, n_x, n_z),
+//   out(p) = 1/4 sum_k R^k n(R^-k p),  R^-1 (X, Y) = (Y, -X),
+// then normalised.
+template <typename Real>
+__global__ void symmetrize_c4_kernel(const Real* __restrict__ n, Real* __restrict__ out, int nx, int nz)
+{
+    const int N = nx * nx * nz;
+    const int c = nx / 2;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+        const int x = s % nx, y = (s / nx) % nx, z = s / (nx * nx);
+        const int X = x - c, Y = y - c;
+        const int px[4] = {x, c + Y, c - X, c - Y};
+        const int py[4] = {y, c - X, c - Y, c + X};
+        double v[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < 4; ++k) {
+            const int xs = ((px[k] % nx) + nx) % nx, ys = ((py[k] % nx) + nx) % nx;
+            const size_t q = (size_t)xs + (size_t)nx * ((size_t)ys + (size_t)nx * z);
+            const double a = (double)n[q], b = (double)n[(size_t)N + q], w = (double)n[2 * (size_t)N + q];
+            if (k == 0) { v[0] += a; v[1] += b; }
+            if (k == 1) { v[0] -= b; v[1] += a; }
+            if (k == 2) { v[0] -= a; v[1] -= b; }
+            if (k == 3) { v[0] += b; v[1] -= a; }
+            v[2] += w;
+        }
+        const double inv = 1.0 / sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        out[s] = (Real)(v[0] * inv);
+        out[(size_t)N + s] = (Real)(v[1] * inv);
+        out[2 * (size_t)N + s] = (Real)(v[2] * inv);
+    }
+}
+
 inline int blocks_for(int64_t n) { return (int)((n + 255) / 256); }
 
 }  // namespace
+
+template <typename Real>
+cudaError_t launch_symmetrize_c4(const Real* n, Real* out, int nx, int nz, cudaStream_t st)
+{
+    const int N = nx * nx * nz;
+    int blocks = blocks_for(N);
+    if (blocks > 4096) blocks = 4096;
+    symmetrize_c4_kernel<Real><<<blocks, 256, 0, st>>>(n, out, nx, nz);
+    return cudaGetLastError();
+}
+template cudaError_t launch_symmetrize_c4<double>(const double*, double*, int, int, cudaStream_t);
+template cudaError_t launch_symmetrize_c4<float>(const float*, float*, int, int, cudaStream_t);
 
 template <typename Real>
 cudaError_t launch_director_change(const Real* n, Real* snap, double* partial, double* out, int N, cudaStream_t st)

@@ -219,6 +219,10 @@ cudaError_t launch_trig_table(double* t, int nx, int ny, cudaStream_t s);
 template <typename Real>
 cudaError_t launch_director_change(const Real* n, Real* snap, double* partial, double* out, int N, cudaStream_t s);
 
+// C4 projection of the director about the axis through (nx/2, nx/2) (diag.cu)
+template <typename Real>
+cudaError_t launch_symmetrize_c4(const Real* n, Real* out, int nx, int nz, cudaStream_t s);
+
 // Record the text returned by nh_last_error(NULL) on this thread (api.cu).
 void set_global_error(const char* msg);
 inline void set_global_error(const std::string& msg) { set_global_error(msg.c_str()); }

@@ -211,18 +211,39 @@ def unet_init_params(seed=0):
 
 def warmstart_samples(count, seed=0, nx=64, ny=64, lz_choices=(16, 24, 32), K=0.005, dt_fd=30):
     """Seeded relaxation problems for the learned warm start: per sample the
-    cell thickness Lz, pitch P ~ U[Lz, 2 Lz] (q0 = 2 pi / P), bulk anchoring
-    W0 ~ logU[1e-4, 1e-2] x K, tube radius R ~ U[10, 18], one centred tube,
-    homeotropic plates, fluid at rest."""
+    cell thickness Lz, pitch P ~ U[Lz, 1.25 Lz] (q0 = 2 pi / P; thickness over
+    pitch 0.8-1, where a tube between homeotropic plates is stable), bulk
+    anchoring W0 ~ logU[1e-4, 1e-3] x K, tube radius R = min(18, P x U[0.4, 0.6]),
+    one tube centred on the site (nx/2, ny/2), fluid at rest."""
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
     for _ in range(count):
         lz = int(rng.choice(lz_choices))
-        pitch = float(rng.uniform(lz, 2 * lz))
-        w0 = float(10 ** rng.uniform(-4, -2) * K)
-        radius = float(rng.uniform(10.0, 18.0))
+        pitch = float(rng.uniform(lz, 1.25 * lz))
+        w0 = float(10 ** rng.uniform(-4, -3) * K)
+        radius = float(min(18.0, pitch * rng.uniform(0.4, 0.6)))
         params = dict(nx=nx, ny=ny, nz=lz, walls_z=True, anchoring="homeotropic", shifted=True, tau=1.0,
                       g=(0.0, 0.0, 0.0), K=K, q0=2 * math.pi / pitch, W0=w0, dt_fd=dt_fd, **LESLIE_ALIGN_09)
-        n0 = skyrmion_tubes(nx, ny, lz, [(nx / 2, ny / 2)], radius)
+        n0 = skyrmion_tubes(nx, ny, lz, [(nx // 2, ny // 2)], radius)
         out.append((params, n0))
     return out
+
+
+# ------------------------------------------------------------------ paper regime (Table I)
+
+def table1_regime(nx=64, ny=64, nz=16, dt_fd=250, tau=1.0, radius=7.0, shifted=True):
+    """The paper's test case in lattice units: Table I (MBBA, doubled alpha4),
+    pitch P = 14, 64x64x16 (Sec. III.A), g = 2e-9, no anchoring at the plates
+    with bulk W0 = 1.5e-8.  The one-constant K is the mean of K11, K22, K33;
+    gamma1 = alpha3 - alpha2, gamma2 = alpha3 + alpha2; tau is not given in the
+    paper (tau = 1 here) and alpha4' = alpha4 - 2 rho c_s^2 (tau - 1/2).  The
+    tube is the radial pi-twist ansatz of radius P/2 (the cited ansatz is not
+    available)."""
+    K11, K22, K33 = 1.67e-7, 7.88e-8, 2.62e-7
+    a1, a2, a3, a4, a5, a6 = 0.0373, -0.4496, -0.0203, 0.9318, 0.3084, -0.1617
+    params = dict(nx=nx, ny=ny, nz=nz, walls_z=True, anchoring="none", shifted=shifted, tau=tau,
+                  g=(2e-9, 0.0, 0.0), K=(K11 + K22 + K33) / 3.0, q0=2 * math.pi / 14.0, W0=1.5e-8,
+                  dt_fd=dt_fd, gamma1=a3 - a2, gamma2=a3 + a2, alpha1=a1, alpha2=a2, alpha3=a3,
+                  alpha4p=a4 - 2.0 * (tau - 0.5) / 3.0, alpha5=a5, alpha6=a6)
+    n0 = skyrmion_tubes(nx, ny, nz, [(nx / 2, ny / 2)], radius)
+    return params, n0

@@ -94,6 +94,7 @@ SIGNATURES = {
     "nh_set_tubes": ([_VP, _DP, ctypes.c_int], ctypes.c_int),
     "nh_relax": ([_VP, ctypes.c_int64, _VP], ctypes.c_int),
     "nh_director_change": ([_VP, _DP], ctypes.c_int),
+    "nh_symmetrize_c4": ([_VP], ctypes.c_int),
     "nh_batch_relax": ([ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int64, _VP], ctypes.c_int),
     "nh_diagnostics": ([_VP, ctypes.POINTER(nh_diag)], ctypes.c_int),
     "nh_diagnostics_enqueue": ([_VP, _VP], ctypes.c_int),
@@ -263,6 +264,10 @@ def nh_director_change(ctx) -> float:
     return float(out.value)
 
 
+def nh_symmetrize_c4(ctx):
+    _check(load_library().nh_symmetrize_c4(ctx), ctx)
+
+
 def nh_batch_relax(ctxs, n_fd_steps: int, stream=None):
     arr = (_VP * len(ctxs))(*[c.value if isinstance(c, _VP) else c for c in ctxs])
     _check(load_library().nh_batch_relax(arr, len(ctxs), int(n_fd_steps), _VP(stream or 0)))
@@ -410,6 +415,9 @@ class Channel:
 
     def relax(self, n_fd_steps: int, stream=None):
         nh_relax(self.ctx, n_fd_steps, (stream or self.stream).cuda_stream)
+
+    def symmetrize_c4(self):
+        nh_symmetrize_c4(self.ctx)
 
     def director_change(self):
         return nh_director_change(self.ctx)

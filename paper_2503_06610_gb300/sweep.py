@@ -65,8 +65,13 @@ def run_one(params, n0, centre, precision, storage, shifted, steps):
             "nonfinite": d["nonfinite"], "energy": d["energy"]}
 
 
-def sweep(steps=5000, gx=1e-5, dts=(1, 2, 4, 8, 16), settings=SETTINGS, nx=96, ny=96, nz=32, radius=12.0):
-    base, n0 = inputs.skyrmion_channel(gx=gx, dt_fd=1, nx=nx, ny=ny, nz=nz, radius=radius)
+def sweep(steps=5000, gx=1e-5, dts=(1, 2, 4, 8, 16), settings=SETTINGS, nx=96, ny=96, nz=32, radius=12.0,
+          regime="skyrmion"):
+    if regime == "table1":
+        base, n0 = inputs.table1_regime(nx=nx, ny=ny, nz=nz, dt_fd=1)
+        radius = 7.0
+    else:
+        base, n0 = inputs.skyrmion_channel(gx=gx, dt_fd=1, nx=nx, ny=ny, nz=nz, radius=radius)
     centre = (nx / 2, ny / 2)
     ref = run_one(dict(base, dt_fd=1), n0, centre, "fp64", "f64", True, steps)
     rows = []
@@ -85,7 +90,9 @@ def sweep(steps=5000, gx=1e-5, dts=(1, 2, 4, 8, 16), settings=SETTINGS, nx=96, n
                 "eps_uy": eps_component(r["u"], ref["u"], 1), "eps_uz": eps_component(r["u"], ref["u"], 2),
                 "centroid": r["centroid"], "centroid_shift": float(np.hypot(*dx)), "nonfinite": r["nonfinite"],
             })
-    return {"workload": f"skyrmion channel {nx}x{ny}x{nz}, R={radius}, q0=2pi/32, gx={gx}, K={base['K']}",
+    name = ("Table I regime" if regime == "table1" else "skyrmion channel") + \
+        f" {nx}x{ny}x{nz}, R={radius}, q0={base['q0']:.4f}, gx={base['g'][0]}, K={base['K']:.3g}"
+    return {"workload": name,
             "steps": steps, "reference": "fp64 shifted dt_FD=1", "reference_centroid": ref["centroid"],
             "rows": rows}
 
@@ -96,11 +103,16 @@ def main():
     ap.add_argument("--gx", type=float, nargs="+", default=[1e-6, 1e-5])
     ap.add_argument("--dts", type=int, nargs="+", default=[1, 2, 4, 8, 16])
     ap.add_argument("--out", default=None)
+    ap.add_argument("--regime", default="skyrmion", choices=["skyrmion", "table1"])
+    ap.add_argument("--size", type=int, nargs=3, default=None, help="nx ny nz")
     args = ap.parse_args()
     results = []
-    for gx in args.gx:
+    size = args.size or ((64, 64, 16) if args.regime == "table1" else (96, 96, 32))
+    gxs = [2e-9] if args.regime == "table1" else args.gx
+    for gx in gxs:
         t0 = time.time()
-        res = sweep(steps=args.steps, gx=gx, dts=tuple(args.dts))
+        res = sweep(steps=args.steps, gx=gx, dts=tuple(args.dts), nx=size[0], ny=size[1], nz=size[2],
+                    regime=args.regime)
         res["wall_s"] = time.time() - t0
         results.append(res)
         for r in res["rows"]:

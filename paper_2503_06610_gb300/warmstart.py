@@ -78,7 +78,7 @@ class WarmStartNet:
 
 # ------------------------------------------------------------------ plain relaxation
 
-def relax(chans, tol=3e-10, check_every=100, max_steps=200000):
+def relax(chans, tol=2e-9, check_every=100, max_steps=200000):
     """Relax every channel (batched) until the director's largest rate of change,
     max |n(t) - n(t - T)| / T over the last check interval T = check_every
     FD steps, is below tol; returns the FD steps each one needed (capped at
@@ -102,11 +102,17 @@ def relax(chans, tol=3e-10, check_every=100, max_steps=200000):
     return steps, time.perf_counter() - t0
 
 
-def make_channels(samples, fields=None):
+def make_channels(samples, fields=None, symmetrize=True):
+    """One FP32 channel per sample, started from its ansatz or from fields[k];
+    the start is projected onto the C4-symmetric fields about the tube axis
+    (nh_symmetrize_c4), which pins the tube to the axis: its position is a
+    zero mode of the relaxation."""
     chans = []
     for k, (params, n0) in enumerate(samples):
         ch = nh.Channel(dict(params, precision="fp32", storage="f32", shifted=True))
         ch.set_fields(n0 if fields is None else fields[k])
+        if symmetrize and params["nx"] == params["ny"]:
+            ch.symmetrize_c4()
         chans.append(ch)
     return chans
 
@@ -218,7 +224,7 @@ def main():
     ap.add_argument("--samples", type=int, default=2000)
     ap.add_argument("--held-out", type=int, default=200)
     ap.add_argument("--epochs", type=int, default=20)
-    ap.add_argument("--tol", type=float, default=3e-10, help="stop when max |dn/dt| < tol")
+    ap.add_argument("--tol", type=float, default=2e-9, help="stop when max |dn/dt| < tol")
     ap.add_argument("--max-steps", type=int, default=200000)
     ap.add_argument("--out", default=None)
     args = ap.parse_args()

@@ -494,3 +494,25 @@ def test_director_change_tracks_relaxation(nh):
     assert 0.0 < d <= np.max(np.linalg.norm(n1 - n0, axis=0)) + 1e-6
     assert abs(d - np.max(np.linalg.norm(n1 - n0, axis=0))) < 1e-5
     assert ch.director_change() == 0.0
+
+
+def test_symmetrize_c4_projection(nh):
+    """A tube centred on (nx/2, ny/2) is C4-symmetric and unchanged (to FP
+    rounding); the projection of an off-axis field is idempotent."""
+    params = _generic(24, 24, 6, dt_fd=2)
+    centred = I.skyrmion_tubes(24, 24, 6, [(12, 12)], 7.0)
+    ch = _channel(nh, params, centred, precision="fp64")
+    ch.symmetrize_c4()
+    assert np.max(np.abs(ch.get_fields()[0] - centred)) < 1e-12
+    off = I.skyrmion_tubes(24, 24, 6, [(13.5, 11.0)], 7.0)
+    ch = _channel(nh, params, off, precision="fp64")
+    ch.symmetrize_c4()
+    once = ch.get_fields()[0]
+    ch.symmetrize_c4()
+    assert np.max(np.abs(ch.get_fields()[0] - once)) < 1e-12
+    n3 = once.reshape(3, 6, 24, 24)
+    # rotate the field by 90 degrees about (12, 12): n'(x, y) = R n(R^-1 (x, y))
+    x, y = np.meshgrid(np.arange(24), np.arange(24), indexing="xy")
+    xs, ys = (12 + (y - 12)) % 24, (12 - (x - 12)) % 24
+    rot = np.stack([-n3[1][:, ys, xs], n3[0][:, ys, xs], n3[2][:, ys, xs]])
+    assert np.max(np.abs(rot - n3)) < 1e-12

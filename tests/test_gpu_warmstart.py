@@ -44,7 +44,7 @@ def _problem(B=2, nx=16, ny=16, nz=16, seed=0):
     return flat, n_ans, target, scal
 
 
-def _oracle(U, flat, n_ans, target, scal, dims):
+def _oracle(U, flat, n_ans, target, scal, dims, bf16_storage=False):
     import torch
     B = n_ans.shape[0]
     nx, ny, nz = dims
@@ -58,7 +58,7 @@ def _oracle(U, flat, n_ans, target, scal, dims):
     x = U.make_input(na5.numpy(), scal[:, 0], scal[:, 1], scal[:, 2])
     x = torch.tensor(_bf16(x.numpy()))
     tg = torch.tensor(target.reshape(B, 3, nz, ny, nx))
-    loss, grad, n_pred = U.loss_and_grad(fr, x, na5, tg)
+    loss, grad, n_pred = U.loss_and_grad(fr, x, na5, tg, bf16_storage)
     return loss, grad, n_pred.numpy().reshape(B, 3, -1)
 
 
@@ -98,11 +98,26 @@ def test_forward_and_gradients_match_oracle(env):
     report.append(("head", "Wb", rel(g[off:], grad_o[off:]), cos(g[off:], grad_o[off:])))
     for r in report:
         print("grad %-6s %-2s rel %.3e cos %.6f" % r)
-    # BF16 activations (forward) and BF16 output gradients (backward) give a few
-    # per cent per layer; the direction must agree closely everywhere
-    assert rel(g, grad_o) < 5e-2
-    assert all(r[2] < 0.15 and r[3] > 0.99 for r in report), report
+    # against the float64 network the BF16 activations and BF16 output
+    # gradients cost several per cent per layer, but the direction must agree
+    assert rel(g, grad_o) < 0.12
+    assert all(r[2] < 0.25 and r[3] > 0.97 for r in report), report
     assert report[-1][2] < 2e-2
+    # against the oracle that keeps activations and the gradients entering
+    # each convolution in BF16 (float64 arithmetic otherwise) the kernels
+    # must agree to FP32-accumulation level
+    loss_e, grad_e, npred_e = _oracle(U, flat, n_ans, target, scal, dims, bf16_storage=True)
+    worst = 0.0
+    off = 0
+    for name, ci, co in U.CONV_LAYERS:
+        n_w = 27 * ci * co
+        for sl in (slice(off, off + n_w), slice(off + n_w, off + n_w + co)):
+            worst = max(worst, rel(g[sl], grad_e[sl]))
+        off += n_w + co
+    print("worst layer vs BF16-storage oracle: %.3e" % worst)
+    assert np.linalg.norm(npred - npred_e) / np.linalg.norm(npred_e - n_ans) < 1e-2
+    assert worst < 3e-2
+    assert rel(g, grad_e) < 1e-2
 
 
 def test_adam_matches_oracle(env):
