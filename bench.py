@@ -175,6 +175,24 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------------ multi-rank reduction
+
+def max_over_ranks(ms, dist=None, device="cpu"):
+    """The slowest rank's time: all ranks time the same replica workload, so
+    the job's throughput is set by the maximum."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_mlups(world, sites_per_rank, lb_steps, ms_max):
+    """Whole-job MLUPS: every rank updates sites_per_rank sites lb_steps times
+    (weak scaling, independent replicas) within ms_max milliseconds."""
+    return world * sites_per_rank * lb_steps / (ms_max * 1e-3) / 1e6
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def batched_sweep(nh, torch, store, blocks):
@@ -293,12 +311,9 @@ def run_ours(args):
     ch.diagnostics_read()
     value_graphs = ch.N * dt * args.steps / (g0.elapsed_time(g1) * 1e-3) / 1e6
 
-    ms_t = torch.tensor([ms], device="cuda")
-    if dist:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = max_over_ranks(ms, dist, device="cuda")
     N = ch.N
-    value = world * N * dt * args.steps / (ms_max * 1e-3) / 1e6
+    value = aggregate_mlups(world, N, dt * args.steps, ms_max)
 
     lb_n, lb_ms = kt["lb"]
     lb_avg_s = lb_ms / max(lb_n, 1) * 1e-3
