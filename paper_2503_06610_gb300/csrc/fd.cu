@@ -322,11 +322,35 @@ size_t fused_a_smem() { return (size_t)(4 * 6 * kP2 + 3 * 6 * kP1) * sizeof(Real
 template <typename Real>
 size_t fused_b_smem() { return (size_t)(4 * 6 * kP2 + 3 * 9 * kP1) * sizeof(Real); }
 
-// Plane zp of n (ghost reading) and u (zero beyond the plates) into one
-// input slot: [n_x | n_y | n_z | u_x | u_y | u_z] x kP2.
+// Each thread owns at most kPts points of a P2 plane (indices threadIdx.x +
+// k * blockDim.x); their wrapped x-y site offsets are computed once per tile.
+constexpr int kPts = (kP2 + kFusedThreads - 1) / kFusedThreads;
+
+struct PlaneMap {
+    int off[kPts];  // x + nx * y of the point, or -1 if the thread owns no such point
+};
+
+__device__ __forceinline__ PlaneMap plane_map(const Geom& g, int x0, int y0)
+{
+    PlaneMap m;
+#pragma unroll
+    for (int k = 0; k < kPts; ++k) {
+        const int i = threadIdx.x + k * blockDim.x;
+        if (i < kP2) {
+            const int hx = i % kHX2, hy = i / kHX2;
+            m.off[k] = wrapm(x0 - 2 + hx, g.nx) + g.nx * wrapm(y0 - 2 + hy, g.ny);
+        } else {
+            m.off[k] = -1;
+        }
+    }
+    return m;
+}
+
+// Plane zp of n (ghost reading) and u (zero beyond the plates), fetched into
+// registers: v[k][0..2] = n, v[k][3..5] = u of the thread's k-th point.
 template <typename Real>
-__device__ void load_plane(const Real* __restrict__ n, const Real* __restrict__ u, const Geom& g, int x0, int y0,
-                           int zp, Real* slot)
+__device__ __forceinline__ void prefetch_plane(const Real* __restrict__ n, const Real* __restrict__ u, const Geom& g,
+                                               const PlaneMap& m, int zp, Real v[kPts][6])
 {
     bool ghost = false;
     int zz;
@@ -338,15 +362,28 @@ __device__ void load_plane(const Real* __restrict__ n, const Real* __restrict__ 
     }
     const bool fixed_dir = ghost && g.anchoring == NH_ANCHOR_HOMEOTROPIC;
     const size_t N = (size_t)g.N;
-    for (int i = threadIdx.x; i < kP2; i += blockDim.x) {
-        const int hx = i % kHX2, hy = i / kHX2;
-        const int x = wrapm(x0 - 2 + hx, g.nx), y = wrapm(y0 - 2 + hy, g.ny);
-        const size_t s = (size_t)x + (size_t)g.nx * ((size_t)y + (size_t)g.ny * zz);
+    const size_t zoff = (size_t)g.nx * g.ny * zz;
+#pragma unroll
+    for (int k = 0; k < kPts; ++k) {
+        if (m.off[k] < 0) continue;
+        const size_t s = zoff + (size_t)m.off[k];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            slot[a * kP2 + i] = fixed_dir ? Real(a == 2 ? 1 : 0) : n[a * N + s];
-            slot[(3 + a) * kP2 + i] = ghost ? Real(0) : u[a * N + s];
+            v[k][a] = fixed_dir ? Real(a == 2 ? 1 : 0) : n[a * N + s];
+            v[k][3 + a] = ghost ? Real(0) : u[a * N + s];
         }
+    }
+}
+
+template <typename Real>
+__device__ __forceinline__ void commit_plane(const PlaneMap& m, const Real v[kPts][6], Real* slot)
+{
+#pragma unroll
+    for (int k = 0; k < kPts; ++k) {
+        if (m.off[k] < 0) continue;
+        const int i = threadIdx.x + k * blockDim.x;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) slot[c * kP2 + i] = v[k][c];
     }
 }
 
@@ -412,14 +449,21 @@ __device__ void fused_a_tile(const FDChan<Real>& c, const Real* __restrict__ nin
     const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
     const bool active = threadIdx.x < kTX * kTY && x0 + tx < g.nx && y0 + ty < g.ny;
     const size_t N = (size_t)g.N;
-    for (int p = zb - 2; p <= zb + 1; ++p) load_plane(nin, c.u, g, x0, y0, p, in + slot4(p) * 6 * kP2);
+    const PlaneMap pm = plane_map(g, x0, y0);
+    Real v[kPts][6];
+    for (int p = zb - 2; p <= zb + 1; ++p) {
+        prefetch_plane(nin, c.u, g, pm, p, v);
+        commit_plane(pm, v, in + slot4(p) * 6 * kP2);
+    }
+    prefetch_plane(nin, c.u, g, pm, zb + 2, v);  // in flight during the prologue predictor
     __syncthreads();
     for (int p = zb - 1; p <= zb; ++p)
         if (!is_ghost_plane(g, p)) predict_plane(c.p, in, p, pr + slot3(p) * 6 * kP1);
-    __syncthreads();
     for (int z = zb; z < ze; ++z) {
-        load_plane(nin, c.u, g, x0, y0, z + 2, in + slot4(z + 2) * 6 * kP2);
+        __syncthreads();  // slot of plane z - 2 (= z + 2) is free; predictor planes are complete
+        commit_plane(pm, v, in + slot4(z + 2) * 6 * kP2);
         __syncthreads();
+        if (z + 1 < ze) prefetch_plane(nin, c.u, g, pm, z + 3, v);  // overlaps the two evaluations below
         if (!is_ghost_plane(g, z + 1)) predict_plane(c.p, in, z + 1, pr + slot3(z + 1) * 6 * kP1);
         __syncthreads();
         if (active) {
@@ -462,7 +506,6 @@ __device__ void fused_a_tile(const FDChan<Real>& c, const Real* __restrict__ nin
 #pragma unroll
             for (int a = 0; a < 3; ++a) nout[a * N + s] = nw[a] * inv;
         }
-        __syncthreads();
     }
 }
 
@@ -502,13 +545,20 @@ __device__ void fused_b_tile(const FDChan<Real>& c, const Real* __restrict__ nin
     const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
     const bool active = threadIdx.x < kTX * kTY && x0 + tx < g.nx && y0 + ty < g.ny;
     const size_t N = (size_t)g.N;
-    for (int p = zb - 2; p <= zb + 1; ++p) load_plane(nin, c.u, g, x0, y0, p, in + slot4(p) * 6 * kP2);
+    const PlaneMap pm = plane_map(g, x0, y0);
+    Real v[kPts][6];
+    for (int p = zb - 2; p <= zb + 1; ++p) {
+        prefetch_plane(nin, c.u, g, pm, p, v);
+        commit_plane(pm, v, in + slot4(p) * 6 * kP2);
+    }
+    prefetch_plane(nin, c.u, g, pm, zb + 2, v);
     __syncthreads();
     for (int p = zb - 1; p <= zb; ++p) stress_plane(c, in, p, sg + slot3(p) * 9 * kP1);
-    __syncthreads();
     for (int z = zb; z < ze; ++z) {
-        load_plane(nin, c.u, g, x0, y0, z + 2, in + slot4(z + 2) * 6 * kP2);
         __syncthreads();
+        commit_plane(pm, v, in + slot4(z + 2) * 6 * kP2);
+        __syncthreads();
+        if (z + 1 < ze) prefetch_plane(nin, c.u, g, pm, z + 3, v);
         stress_plane(c, in, z + 1, sg + slot3(z + 1) * 9 * kP1);
         __syncthreads();
         if (active) {
@@ -531,7 +581,6 @@ __device__ void fused_b_tile(const FDChan<Real>& c, const Real* __restrict__ nin
                 for (int a = 0; a < 3; ++a) ncopy[a * N + s] = inm[a * kP2 + i2];
             }
         }
-        __syncthreads();
     }
 }
 

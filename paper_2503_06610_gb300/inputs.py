@@ -210,20 +210,21 @@ def unet_init_params(seed=0):
 
 
 def warmstart_samples(count, seed=0, nx=64, ny=64, lz_choices=(16, 24, 32), K=0.005, dt_fd=30):
-    """Seeded relaxation problems for the learned warm start: per sample the
-    cell thickness Lz, pitch P ~ U[Lz, 1.25 Lz] (q0 = 2 pi / P; thickness over
-    pitch 0.8-1, where a tube between homeotropic plates is stable), bulk
-    anchoring W0 ~ logU[1e-4, 1e-3] x K, tube radius R = min(18, P x U[0.4, 0.6]),
-    one tube centred on the site (nx/2, ny/2), fluid at rest."""
+    """Seeded relaxation problems for the learned warm start, in the paper's
+    skyrmion setup (Sec. III.A): no anchoring at the plates and a weak bulk
+    anchoring W0 along z.  Per sample: cell thickness Lz, pitch P ~ U[16, 40]
+    (q0 = 2 pi / P), W0 = w K q0^2 with w ~ U[0.5, 1.5], tube radius
+    R ~ U[0.4, 0.6] P; one tube centred on the site (nx/2, ny/2), fluid at rest."""
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
     for _ in range(count):
         lz = int(rng.choice(lz_choices))
-        pitch = float(rng.uniform(lz, 1.25 * lz))
-        w0 = float(10 ** rng.uniform(-4, -3) * K)
-        radius = float(min(18.0, pitch * rng.uniform(0.4, 0.6)))
-        params = dict(nx=nx, ny=ny, nz=lz, walls_z=True, anchoring="homeotropic", shifted=True, tau=1.0,
-                      g=(0.0, 0.0, 0.0), K=K, q0=2 * math.pi / pitch, W0=w0, dt_fd=dt_fd, **LESLIE_ALIGN_09)
+        pitch = float(rng.uniform(16.0, 40.0))
+        q0 = 2 * math.pi / pitch
+        w0 = float(rng.uniform(0.5, 1.5) * K * q0 * q0)
+        radius = float(pitch * rng.uniform(0.4, 0.6))
+        params = dict(nx=nx, ny=ny, nz=lz, walls_z=True, anchoring="none", shifted=True, tau=1.0,
+                      g=(0.0, 0.0, 0.0), K=K, q0=q0, W0=w0, dt_fd=dt_fd, **LESLIE_ALIGN_09)
         n0 = skyrmion_tubes(nx, ny, lz, [(nx // 2, ny // 2)], radius)
         out.append((params, n0))
     return out

@@ -358,12 +358,16 @@ def test_lb_variants_agree_and_autotune_keeps_state(nh, oracle_mod, nx):
 def test_timing_segments_count_every_launch(nh):
     params = _generic(16, 12, 8, dt_fd=4)
     n0 = I.tilted_director(16, 12, 8, amplitude=0.2, seed=2)
-    ch = _channel(nh, params, n0, precision="fp32")
-    ch.set_timing(1)
-    ch.step(10)
-    t = ch.timing()
-    assert t["lb"][0] == 10 and t["fd_predict"][0] == 2 and t["force"][0] == 2
-    assert all(v[1] > 0 for v in t.values())
+    for fused in (0, 1):
+        ch = _channel(nh, params, n0, precision="fp32")
+        ch.set_fd_variant(fused)
+        ch.set_timing(1)
+        ch.step(10)
+        t = ch.timing()
+        assert t["lb"][0] == 10 and t["fd_predict"][0] == 2 and t["stress"][0] == 2
+        # the fused variant runs predictor+corrector and stress+force as two kernels
+        assert t["fd_correct"][0] == (0 if fused else 2) and t["force"][0] == (0 if fused else 2)
+        assert all(v[1] > 0 for k, v in t.items() if v[0] > 0)
     ch.set_timing(2)
     ch.step(8)
     t = ch.timing()
