@@ -347,6 +347,9 @@ int nh_unet_forward(nh_unet* net, const float* params, const float* n_ansatz, co
  * activations of the last forward pass. */
 int nh_unet_backward(nh_unet* net, const float* params, const float* n_ansatz, const float* target, float* grad,
                      float* loss, void* stream);
+/* Copy the stored output of conv layer `layer` (0..13 in the order above) of
+ * the last forward pass to out (FP32 device, channels-last [batch][z][y][x][c]). */
+int nh_unet_activation(nh_unet* net, int layer, float* out, void* stream);
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected, step >= 1). */
 int nh_unet_adam(float* params, const float* grad, float* m, float* v, int64_t count, int step, float lr, void* stream);
 void nh_unet_destroy(nh_unet* net);

@@ -124,7 +124,7 @@ class _RoundFwd(torch.autograd.Function):
         return g
 
 
-def forward(params, x, n_ansatz, bf16_storage=False):
+def forward(params, x, n_ansatz, bf16_storage=False, keep=None):
     """x [B][16][Z][Y][X], n_ansatz [B][3][Z][Y][X] -> (n_pred, delta).
 
     bf16_storage=True keeps every stored activation in BF16 and rounds the
@@ -132,7 +132,12 @@ def forward(params, x, n_ansatz, bf16_storage=False):
     implementation does; the arithmetic itself stays float64."""
     ra = _RoundAct.apply if bf16_storage else (lambda t: t)
     rf = _RoundFwd.apply if bf16_storage else (lambda t: t)
-    r = lambda name, t: ra(F.relu(conv3(t, *params[name])))
+    def r(name, t):
+        y = ra(F.relu(conv3(t, *params[name])))
+        if keep is not None:
+            keep[name] = y.detach()
+        return y
+
     e1 = r("enc1b", r("enc1a", x))
     e2 = r("enc2b", r("enc2a", rf(pool(e1))))
     e3 = r("enc3b", r("enc3a", rf(pool(e2))))

@@ -524,6 +524,12 @@ __global__ void __launch_bounds__(256) head_kernel(const bf16* __restrict__ d1, 
     }
 }
 
+__global__ void bf16_to_f32_kernel(const bf16* __restrict__ a, float* __restrict__ out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = __bfloat162float(a[i]);
+}
+
 __global__ void cast_params_kernel(const float* __restrict__ p, bf16* __restrict__ w, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -862,6 +868,16 @@ int nh_unet_backward(nh_unet* u, const float* params, const float* n_ansatz, con
     // encoder level 0 (the input needs no gradient)
     UNET_CUDA(u, conv_bwd(u, ENC1B, 0, gskip[0], act(ENC1A), 16, nullptr, 0, ga, nullptr, grad, true, st));
     UNET_CUDA(u, conv_bwd(u, ENC1A, 0, ga, P<bf16>(u, u->x), 16, nullptr, 0, nullptr, nullptr, grad, false, st));
+    return NH_OK;
+}
+
+int nh_unet_activation(nh_unet* u, int layer, float* out, void* stream)
+{
+    if (!u || !u->ws || !out || layer < 0 || layer >= kLayers) return unet_fail(u, NH_EINVAL, "bad arguments");
+    const int level_of[kLayers] = {0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0};
+    const int64_t n = (int64_t)u->lv[level_of[layer]].nvox * u->batch * kConv[layer].cout;
+    bf16_to_f32_kernel<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(P<bf16>(u, u->act[layer]), out, n);
+    UNET_CUDA(u, cudaGetLastError());
     return NH_OK;
 }
 

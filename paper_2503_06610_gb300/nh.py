@@ -114,6 +114,7 @@ SIGNATURES = {
     "nh_unet_set_params": ([_VP, _VP, _VP], ctypes.c_int),
     "nh_unet_forward": ([_VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "nh_unet_backward": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "nh_unet_activation": ([_VP, ctypes.c_int, _VP, _VP], ctypes.c_int),
     "nh_unet_adam": ([_VP, _VP, _VP, _VP, ctypes.c_int64, ctypes.c_int, ctypes.c_float, _VP], ctypes.c_int),
     "nh_unet_destroy": ([_VP], None),
     "nh_diagnostics_noalloc": ([ctypes.POINTER(nh_params), _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
@@ -520,6 +521,9 @@ class UNet:
     def backward(self, params, n_ansatz, target, grad, loss, stream=None):
         _check(load_library().nh_unet_backward(self.h, _dp(params), _dp(n_ansatz), _dp(target), _dp(grad),
                                                _dp(loss), _VP(stream or 0)))
+
+    def activation(self, layer, out, stream=None):
+        _check(load_library().nh_unet_activation(self.h, int(layer), _dp(out), _VP(stream or 0)))
 
     def close(self):
         if getattr(self, "h", None):

@@ -123,6 +123,44 @@ def test_forward_and_gradients_match_oracle(env):
     assert worst < 3e-2
 
 
+def test_forward_activations_match_bf16_oracle(env):
+    """Every stored layer output of the GPU forward equals the BF16-storage
+    oracle's (float64 arithmetic, BF16 storage) up to rare rounding flips."""
+    torch, nh, ws, U = env
+    dims = (16, 16, 16)
+    B = 2
+    flat, n_ans, target, scal = _problem(B=B)
+    nx, ny, nz = dims
+    fr = flat.copy()
+    off = 0
+    for _, ci, co in U.CONV_LAYERS:
+        fr[off:off + 27 * ci * co] = _bf16(flat[off:off + 27 * ci * co])
+        off += 27 * ci * co + co
+    na5 = torch.tensor(n_ans.reshape(B, 3, nz, ny, nx))
+    x = torch.tensor(_bf16(U.make_input(na5.numpy(), scal[:, 0], scal[:, 1], scal[:, 2]).numpy()))
+    keep = {}
+    with torch.no_grad():
+        U.forward(U.unpack(fr), x, na5, bf16_storage=True, keep=keep)
+    dev = torch.device("cuda")
+    net = nh.UNet(B, *dims)
+    params = torch.tensor(flat, dtype=torch.float32, device=dev)
+    net.set_params(params)
+    net.forward(params, torch.tensor(n_ans, dtype=torch.float32, device=dev),
+                torch.tensor(scal, dtype=torch.float32, device=dev), None)
+    levels = {"enc1": 1, "enc2": 2, "enc3": 4, "bot": 8, "dec3": 4, "dec2": 2, "dec1": 1}
+    for l, (name, ci, co) in enumerate(U.CONV_LAYERS):
+        s = levels[name[:-1]]
+        shape = (B, nz // s, ny // s, nx // s, co)
+        out = torch.empty(int(np.prod(shape)), dtype=torch.float32, device=dev)
+        net.activation(l, out)
+        torch.cuda.synchronize()
+        g = out.cpu().numpy().reshape(shape).transpose(0, 4, 1, 2, 3)
+        o = keep[name].numpy()
+        err = np.linalg.norm(g - o) / max(np.linalg.norm(o), 1e-30)
+        print("forward %-6s rel %.3e" % (name, err))
+        assert err < 5e-3, (name, err)
+
+
 def test_adam_matches_oracle(env):
     torch, nh, ws, U = env
     rng = np.random.default_rng(3)
