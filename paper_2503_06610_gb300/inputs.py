@@ -213,16 +213,19 @@ def warmstart_samples(count, seed=0, nx=64, ny=64, lz_choices=(16, 24, 32), K=0.
     """Seeded relaxation problems for the learned warm start, in the paper's
     skyrmion setup (Sec. III.A): no anchoring at the plates and a weak bulk
     anchoring W0 along z.  Per sample: cell thickness Lz, pitch P ~ U[16, 40]
-    (q0 = 2 pi / P), W0 = w K q0^2 with w ~ U[0.5, 1.5], tube radius
-    R ~ U[0.4, 0.6] P; one tube centred on the site (nx/2, ny/2), fluid at rest."""
+    (q0 = 2 pi / P), W0 = w K q0^2 with w ~ U[3, 6] (the uniform background is
+    then the ground state, kappa = pi^2 K q0^2 / (4 W0) < 1, and an isolated tube
+    is metastable; for w < pi^2/4 the ground state is helical and tubes unwind),
+    tube radius R ~ U[0.3, 0.5] P; one tube centred on the site (nx/2, ny/2),
+    fluid at rest."""
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
     for _ in range(count):
         lz = int(rng.choice(lz_choices))
         pitch = float(rng.uniform(16.0, 40.0))
         q0 = 2 * math.pi / pitch
-        w0 = float(rng.uniform(0.5, 1.5) * K * q0 * q0)
-        radius = float(pitch * rng.uniform(0.4, 0.6))
+        w0 = float(rng.uniform(3.0, 6.0) * K * q0 * q0)
+        radius = float(pitch * rng.uniform(0.3, 0.5))
         params = dict(nx=nx, ny=ny, nz=lz, walls_z=True, anchoring="none", shifted=True, tau=1.0,
                       g=(0.0, 0.0, 0.0), K=K, q0=q0, W0=w0, dt_fd=dt_fd, **LESLIE_ALIGN_09)
         n0 = skyrmion_tubes(nx, ny, lz, [(nx // 2, ny // 2)], radius)
