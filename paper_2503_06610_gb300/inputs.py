@@ -212,19 +212,20 @@ def unet_init_params(seed=0):
 def warmstart_samples(count, seed=0, nx=64, ny=64, lz_choices=(16, 24, 32), K=0.005, dt_fd=30):
     """Seeded relaxation problems for the learned warm start, in the paper's
     skyrmion setup (Sec. III.A): no anchoring at the plates and a weak bulk
-    anchoring W0 along z.  Per sample: cell thickness Lz, pitch P ~ U[16, 40]
-    (q0 = 2 pi / P), W0 = w K q0^2 with w ~ U[3, 6] (the uniform background is
+    anchoring W0 along z.  Per sample: cell thickness Lz, pitch P ~ U[20, 40]
+    (q0 = 2 pi / P), W0 = w K q0^2 with w ~ U[3, 3.8] (the uniform background is
     then the ground state, kappa = pi^2 K q0^2 / (4 W0) < 1, and an isolated tube
-    is metastable; for w < pi^2/4 the ground state is helical and tubes unwind),
-    tube radius R ~ U[0.3, 0.5] P; one tube centred on the site (nx/2, ny/2),
-    fluid at rest."""
+    is metastable; for w < pi^2/4 the ground state is helical and tubes unwind,
+    and for w above about 4 the relaxed tube is a few sites wide and collapses
+    on the lattice), tube radius R ~ U[0.3, 0.5] P; one tube centred on the
+    site (nx/2, ny/2), fluid at rest."""
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
     for _ in range(count):
         lz = int(rng.choice(lz_choices))
-        pitch = float(rng.uniform(16.0, 40.0))
+        pitch = float(rng.uniform(20.0, 40.0))
         q0 = 2 * math.pi / pitch
-        w0 = float(rng.uniform(3.0, 6.0) * K * q0 * q0)
+        w0 = float(rng.uniform(3.0, 3.8) * K * q0 * q0)
         radius = float(pitch * rng.uniform(0.3, 0.5))
         params = dict(nx=nx, ny=ny, nz=lz, walls_z=True, anchoring="none", shifted=True, tau=1.0,
                       g=(0.0, 0.0, 0.0), K=K, q0=q0, W0=w0, dt_fd=dt_fd, **LESLIE_ALIGN_09)
@@ -235,19 +236,22 @@ def warmstart_samples(count, seed=0, nx=64, ny=64, lz_choices=(16, 24, 32), K=0.
 
 # ------------------------------------------------------------------ paper regime (Table I)
 
-def table1_regime(nx=64, ny=64, nz=16, dt_fd=250, tau=1.0, radius=7.0, shifted=True):
+def table1_regime(nx=64, ny=64, nz=16, dt_fd=250, split=0.5, radius=7.0, shifted=True):
     """The paper's test case in lattice units: Table I (MBBA, doubled alpha4),
     pitch P = 14, 64x64x16 (Sec. III.A), g = 2e-9, no anchoring at the plates
     with bulk W0 = 1.5e-8.  The one-constant K is the mean of K11, K22, K33;
-    gamma1 = alpha3 - alpha2, gamma2 = alpha3 + alpha2; tau is not given in the
-    paper (tau = 1 here) and alpha4' = alpha4 - 2 rho c_s^2 (tau - 1/2).  The
+    gamma1 = alpha3 - alpha2, gamma2 = alpha3 + alpha2.  The isotropic viscosity
+    alpha4 is shared between the FD force (alpha4' = split * alpha4) and the
+    lattice Boltzmann fluid (2 rho c_s^2 (tau - 1/2) = (1 - split) alpha4, which
+    fixes tau; Sec. II.B keeps the same viscosity in both, split = 1/2).  The
     tube is the radial pi-twist ansatz of radius P/2 (the cited ansatz is not
     available)."""
     K11, K22, K33 = 1.67e-7, 7.88e-8, 2.62e-7
     a1, a2, a3, a4, a5, a6 = 0.0373, -0.4496, -0.0203, 0.9318, 0.3084, -0.1617
+    tau = 0.5 + 1.5 * (1.0 - split) * a4
     params = dict(nx=nx, ny=ny, nz=nz, walls_z=True, anchoring="none", shifted=shifted, tau=tau,
                   g=(2e-9, 0.0, 0.0), K=(K11 + K22 + K33) / 3.0, q0=2 * math.pi / 14.0, W0=1.5e-8,
                   dt_fd=dt_fd, gamma1=a3 - a2, gamma2=a3 + a2, alpha1=a1, alpha2=a2, alpha3=a3,
-                  alpha4p=a4 - 2.0 * (tau - 0.5) / 3.0, alpha5=a5, alpha6=a6)
+                  alpha4p=split * a4, alpha5=a5, alpha6=a6)
     n0 = skyrmion_tubes(nx, ny, nz, [(nx / 2, ny / 2)], radius)
     return params, n0

@@ -6,8 +6,9 @@ flow, g_x in {1e-6, 1e-5}) every combination of arithmetic / population store
 GPU through the C ABI; each run reports
 
 * MLUPS of the timed run (LB + FD + force, CUDA events),
-* the errors of u and n against the reference run - FP64, shifted, dt_FD = 1,
-  as in the paper - as relative L2 and as the paper's epsilon (Sec. III.A) and
+* the errors of u and n against the reference run - FP64, shifted, dt_FD = 1
+  as in the paper, or the smallest dt_FD that is stable for the workload
+  (``--ref-dt``) - as relative L2 and as the paper's epsilon (Sec. III.A) and
   its per-component form (Sec. III.B),
 * the tube centroid and its distance from the reference centroid.
 
@@ -66,18 +67,18 @@ def run_one(params, n0, centre, precision, storage, shifted, steps):
 
 
 def sweep(steps=5000, gx=1e-5, dts=(1, 2, 4, 8, 16), settings=SETTINGS, nx=96, ny=96, nz=32, radius=12.0,
-          regime="skyrmion"):
+          regime="skyrmion", ref_dt=1, split=0.5):
     if regime == "table1":
-        base, n0 = inputs.table1_regime(nx=nx, ny=ny, nz=nz, dt_fd=1)
+        base, n0 = inputs.table1_regime(nx=nx, ny=ny, nz=nz, dt_fd=1, split=split)
         radius = 7.0
     else:
         base, n0 = inputs.skyrmion_channel(gx=gx, dt_fd=1, nx=nx, ny=ny, nz=nz, radius=radius)
     centre = (nx / 2, ny / 2)
-    ref = run_one(dict(base, dt_fd=1), n0, centre, "fp64", "f64", True, steps)
+    ref = run_one(dict(base, dt_fd=ref_dt), n0, centre, "fp64", "f64", True, steps)
     rows = []
     for dt in dts:
         for precision, storage, shifted in settings:
-            if (precision, storage, shifted, dt) == ("fp64", "f64", True, 1):
+            if (precision, storage, shifted, dt) == ("fp64", "f64", True, ref_dt):
                 r = ref
             else:
                 r = run_one(dict(base, dt_fd=dt), n0, centre, precision, storage, shifted, steps)
@@ -93,7 +94,8 @@ def sweep(steps=5000, gx=1e-5, dts=(1, 2, 4, 8, 16), settings=SETTINGS, nx=96, n
     name = ("Table I regime" if regime == "table1" else "skyrmion channel") + \
         f" {nx}x{ny}x{nz}, R={radius}, q0={base['q0']:.4f}, gx={base['g'][0]}, K={base['K']:.3g}"
     return {"workload": name,
-            "steps": steps, "reference": "fp64 shifted dt_FD=1", "reference_centroid": ref["centroid"],
+            "steps": steps, "reference": f"fp64 shifted dt_FD={ref_dt}", "reference_centroid": ref["centroid"],
+            "tau": base["tau"], "alpha4p": base["alpha4p"], "reference_nonfinite": ref["nonfinite"],
             "rows": rows}
 
 
@@ -105,6 +107,8 @@ def main():
     ap.add_argument("--out", default=None)
     ap.add_argument("--regime", default="skyrmion", choices=["skyrmion", "table1"])
     ap.add_argument("--size", type=int, nargs=3, default=None, help="nx ny nz")
+    ap.add_argument("--ref-dt", type=int, default=1, help="dt_FD of the FP64 reference run")
+    ap.add_argument("--split", type=float, default=0.5, help="table1: share of alpha4 carried by the FD force")
     args = ap.parse_args()
     results = []
     size = args.size or ((64, 64, 16) if args.regime == "table1" else (96, 96, 32))
@@ -112,13 +116,13 @@ def main():
     for gx in gxs:
         t0 = time.time()
         res = sweep(steps=args.steps, gx=gx, dts=tuple(args.dts), nx=size[0], ny=size[1], nz=size[2],
-                    regime=args.regime)
+                    regime=args.regime, ref_dt=args.ref_dt, split=args.split)
         res["wall_s"] = time.time() - t0
         results.append(res)
         for r in res["rows"]:
             print(f"gx={gx:g} dt={r['dt_fd']:3d} {r['precision']}/{r['storage']}/{'s' if r['shifted'] else 'p'}: "
                   f"{r['mlups']:9.1f} MLUPS  eps_u {r['eps_u']:.3e}  relL2 n {r['rel_l2_n']:.3e}  "
-                  f"centroid shift {r['centroid_shift']:.3e}")
+                  f"centroid shift {r['centroid_shift']:.3e}  nonfinite {r['nonfinite']}")
     if args.out:
         with open(args.out, "w") as f:
             json.dump(results, f, indent=1)
