@@ -63,11 +63,12 @@ def run_one(params, n0, centre, precision, storage, shifted, steps):
     d = ch.diagnostics(allow_unstable=True)
     ch.close()
     return {"mlups": ch.N * steps / (ms * 1e-3) / 1e6, "n": n, "u": u, "centroid": d["centroids"][0].tolist(),
+            "max_u": float(np.nanmax(np.abs(u))) if np.isfinite(u).any() else float("nan"),
             "nonfinite": d["nonfinite"], "energy": d["energy"]}
 
 
 def sweep(steps=5000, gx=1e-5, dts=(1, 2, 4, 8, 16), settings=SETTINGS, nx=96, ny=96, nz=32, radius=12.0,
-          regime="skyrmion", ref_dt=1, split=0.5):
+          regime="skyrmion", ref_dt=1, split=0.15):
     if regime == "table1":
         base, n0 = inputs.table1_regime(nx=nx, ny=ny, nz=nz, dt_fd=1, split=split)
         radius = 7.0
@@ -90,6 +91,7 @@ def sweep(steps=5000, gx=1e-5, dts=(1, 2, 4, 8, 16), settings=SETTINGS, nx=96, n
                 "eps_u": eps(r["u"], ref["u"]), "eps_ux": eps_component(r["u"], ref["u"], 0),
                 "eps_uy": eps_component(r["u"], ref["u"], 1), "eps_uz": eps_component(r["u"], ref["u"], 2),
                 "centroid": r["centroid"], "centroid_shift": float(np.hypot(*dx)), "nonfinite": r["nonfinite"],
+                "max_u": r["max_u"], "max_u_ref": ref["max_u"],
             })
     name = ("Table I regime" if regime == "table1" else "skyrmion channel") + \
         f" {nx}x{ny}x{nz}, R={radius}, q0={base['q0']:.4f}, gx={base['g'][0]}, K={base['K']:.3g}"
@@ -107,8 +109,9 @@ def main():
     ap.add_argument("--out", default=None)
     ap.add_argument("--regime", default="skyrmion", choices=["skyrmion", "table1"])
     ap.add_argument("--size", type=int, nargs=3, default=None, help="nx ny nz")
-    ap.add_argument("--ref-dt", type=int, default=1, help="dt_FD of the FP64 reference run")
-    ap.add_argument("--split", type=float, default=0.5, help="table1: share of alpha4 carried by the FD force")
+    ap.add_argument("--ref-dt", type=int, default=None,
+                    help="dt_FD of the FP64 reference run (default 1; 2 for table1, where dt_FD = 1 is unstable)")
+    ap.add_argument("--split", type=float, default=0.15, help="table1: share of alpha4 carried by the FD force")
     args = ap.parse_args()
     results = []
     size = args.size or ((64, 64, 16) if args.regime == "table1" else (96, 96, 32))
@@ -116,13 +119,14 @@ def main():
     for gx in gxs:
         t0 = time.time()
         res = sweep(steps=args.steps, gx=gx, dts=tuple(args.dts), nx=size[0], ny=size[1], nz=size[2],
-                    regime=args.regime, ref_dt=args.ref_dt, split=args.split)
+                    regime=args.regime, split=args.split,
+                    ref_dt=args.ref_dt or (2 if args.regime == "table1" else 1))
         res["wall_s"] = time.time() - t0
         results.append(res)
         for r in res["rows"]:
             print(f"gx={gx:g} dt={r['dt_fd']:3d} {r['precision']}/{r['storage']}/{'s' if r['shifted'] else 'p'}: "
                   f"{r['mlups']:9.1f} MLUPS  eps_u {r['eps_u']:.3e}  relL2 n {r['rel_l2_n']:.3e}  "
-                  f"centroid shift {r['centroid_shift']:.3e}  nonfinite {r['nonfinite']}")
+                  f"centroid shift {r['centroid_shift']:.3e}  max|u| {r['max_u']:.3e}  nonfinite {r['nonfinite']}")
     if args.out:
         with open(args.out, "w") as f:
             json.dump(results, f, indent=1)
