@@ -137,28 +137,6 @@ __device__ __forceinline__ double warp_min(double v)
     return v;
 }
 
-// Director with the ghost-layer reading (x, y wrapped here; z may be -1 or nz).
-template <typename Real>
-__device__ __forceinline__ void dir_r(const Real* n, const Geom& g, int x, int y, int z, Real out[3])
-{
-    x = wrap_p(x, g.nx);
-    y = wrap_p(y, g.ny);
-    if (g.walls && (z < 0 || z >= g.nz)) {
-        if (g.anchoring == NH_ANCHOR_HOMEOTROPIC) {
-            out[0] = Real(0);
-            out[1] = Real(0);
-            out[2] = Real(1);
-            return;
-        }
-        z = z < 0 ? 0 : g.nz - 1;
-    }
-    z = wrap_p(z, g.nz);
-    const int s = x + g.nx * (y + g.ny * z);
-    out[0] = n[s];
-    out[1] = n[g.N + s];
-    out[2] = n[2 * g.N + s];
-}
-
 // Energy of the link from n (at x) to m (at x + e_b):
 // K/2 |m - n|^2 + K q0 eps_abc n_a m_c  (= K/2 |m - n|^2 - K q0 (n x m)_b).
 template <typename Real>
@@ -176,12 +154,25 @@ __device__ __forceinline__ Real link_energy(const Real n[3], const Real m[3], in
 }
 
 // Work item = (x, y) column x a chunk of kDiagChunk layers; one thread per item
-// (grid-stride).  Per-site terms are evaluated and summed over the chunk in the
+// (grid-stride; the items of a warp share the chunk, so z-branches are uniform).
+// A thread marches up its chunk: the director of the next layer is loaded one
+// site ahead and is both the z+1 link partner and the next centre, the x+1 and
+// y+1 partners are branch-free loads, and the loop is unrolled so that several
+// sites' loads are in flight.  Per-site terms are summed over the chunk in the
 // build's precision (Real); each item's sums are then accumulated in FP64.
 // Tube sums use the item's weight sum_z (1 - n_z)/2, the column's nearest
-// previous centroid (FP64 periodic distance), FP64 sin/cos tables of the
-// column position, and warp-aggregated shared-memory accumulation.
+// previous centroid (FP32 periodic distance with an FP64 tie check), the
+// FP64 sin/cos tables of the column position, a warp sum in Real per owner
+// and FP64 shared-memory accumulation.
 constexpr int kDiagChunk = 16;
+
+template <typename Real>
+__device__ __forceinline__ void load3(const Real* __restrict__ n, int N, int s, Real out[3])
+{
+    out[0] = __ldg(n + s);
+    out[1] = __ldg(n + N + s);
+    out[2] = __ldg(n + 2 * N + s);
+}
 
 template <typename Real, typename Store>
 __global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const DiagArgs a)
@@ -191,13 +182,14 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const DiagArgs a)
     const int cols = g.nx * g.ny;
     const int chunks = (g.nz + kDiagChunk - 1) / kDiagChunk;
     const int items = cols * chunks;
-    const Store* f = static_cast<const Store*>(a.f);
-    const Real* n = static_cast<const Real*>(a.n);
-    const Real* u = static_cast<const Real*>(a.u);
-    const Real* rho = static_cast<const Real*>(a.rho);
+    const Store* __restrict__ f = static_cast<const Store*>(a.f);
+    const Real* __restrict__ n = static_cast<const Real*>(a.n);
+    const Real* __restrict__ u = static_cast<const Real*>(a.u);
+    const Real* __restrict__ rho = static_cast<const Real*>(a.rho);
     const float inv_scale = sizeof(Store) == 2 ? 1.f / a.scale[0] : 1.f;
     const Real K = Real(a.K), q0 = Real(a.q0), W0 = Real(a.W0);
     const Real site_const = Real(0.5) * K * q0 * q0;
+    const bool homeo = g.walls && g.anchoring == NH_ANCHOR_HOMEOTROPIC;
     const int T = a.n_tubes;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __shared__ double tube_acc[NH_MAX_TUBES * 5];
@@ -219,30 +211,51 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const DiagArgs a)
             const int z1 = min(z0 + kDiagChunk, g.nz);
             x = col % g.nx;
             y = col / g.nx;
+            const int colx = (x + 1 == g.nx ? 0 : x + 1) + g.nx * y;
+            const int coly = x + g.nx * (y + 1 == g.ny ? 0 : y + 1);
             Real msum = 0, esum = 0;
+            Real c[3];
+            load3(n, N, col + cols * z0, c);
+            if (g.walls && z0 == 0) {
+                // link from the lower ghost layer to the first fluid layer
+                Real m[3] = {c[0], c[1], c[2]};
+                if (homeo) {
+                    m[0] = Real(0);
+                    m[1] = Real(0);
+                    m[2] = Real(1);
+                }
+                esum += link_energy(m, c, 2, K, q0);
+            }
+#pragma unroll 4
             for (int z = z0; z < z1; ++z) {
                 const int s = col + cols * z;
+                Real cn[3];
+                if (z + 1 < g.nz) {
+                    load3(n, N, s + cols, cn);
+                } else if (!g.walls) {
+                    load3(n, N, col, cn);  // periodic in z
+                } else if (homeo) {
+                    cn[0] = Real(0);
+                    cn[1] = Real(0);
+                    cn[2] = Real(1);
+                } else {
+                    cn[0] = c[0];
+                    cn[1] = c[1];
+                    cn[2] = c[2];
+                }
+                Real mx[3], my[3];
+                load3(n, N, colx + cols * z, mx);
+                load3(n, N, coly + cols * z, my);
                 Real fs = 0;
 #pragma unroll
                 for (int i = 0; i < 19; ++i) fs += Codec<Store, Real>::load(f + (size_t)i * N + s, inv_scale);
+                const Real u0 = __ldg(u + s), u1 = __ldg(u + N + s), u2 = __ldg(u + 2 * N + s);
+                const Real r = __ldg(rho + s);
                 msum += fs;
-                Real c[3], m[3];
-                c[0] = n[s];
-                c[1] = n[N + s];
-                c[2] = n[2 * N + s];
-                dir_r(n, g, x + 1, y, z, m);
-                Real e = link_energy(c, m, 0, K, q0);
-                dir_r(n, g, x, y + 1, z, m);
-                e += link_energy(c, m, 1, K, q0);
-                dir_r(n, g, x, y, z + 1, m);
-                e += link_energy(c, m, 2, K, q0);
-                if (g.walls && z == 0) {
-                    dir_r(n, g, x, y, -1, m);
-                    e += link_energy(m, c, 2, K, q0);
-                }
+                Real e = link_energy(c, mx, 0, K, q0);
+                e += link_energy(c, my, 1, K, q0);
+                e += link_energy(c, cn, 2, K, q0);
                 esum += e + site_const - Real(0.5) * W0 * c[2] * c[2];
-                const Real u0 = u[s], u1 = u[N + s], u2 = u[2 * N + s];
-                const Real r = rho[s];
                 const Real umag = sqrt(u0 * u0 + u1 * u1 + u2 * u2);
                 const Real nmag = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
                 max_u = max(max_u, umag);
@@ -250,13 +263,16 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const DiagArgs a)
                 max_nn = max(max_nn, nmag);
                 if (!isfinite(umag) || !isfinite(nmag) || !isfinite(r) || !isfinite(fs)) bad += 1;
                 wsum += Real(0.5) * (Real(1) - c[2]);
+                c[0] = cn[0];
+                c[1] = cn[1];
+                c[2] = cn[2];
             }
             mass += (double)msum;
             energy += (double)esum;
         }
         if (T > 0) {
             int owner = -1;
-            double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+            Real v[5] = {0, 0, 0, 0, 0};
             if (valid) {
                 // nearest previous centroid: FP32 squared distances with the
                 // periodic minimum image; a near-tie of the two best is settled
@@ -291,12 +307,11 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const DiagArgs a)
                     // lowest index wins an exact tie, as in a first-minimum search
                     if (d2[1] < d2[0] || (d2[1] == d2[0] && cand[1] < cand[0])) owner = cand[1];
                 }
-                const double w = (double)wsum;
-                v[0] = w;
-                v[1] = w * a.trig[x];                    // sin(2 pi x / nx)
-                v[2] = w * a.trig[g.nx + x];             // cos(2 pi x / nx)
-                v[3] = w * a.trig[2 * g.nx + y];         // sin(2 pi y / ny)
-                v[4] = w * a.trig[2 * g.nx + g.ny + y];  // cos(2 pi y / ny)
+                v[0] = wsum;
+                v[1] = wsum * Real(a.trig[x]);                    // sin(2 pi x / nx)
+                v[2] = wsum * Real(a.trig[g.nx + x]);             // cos(2 pi x / nx)
+                v[3] = wsum * Real(a.trig[2 * g.nx + y]);         // sin(2 pi y / ny)
+                v[4] = wsum * Real(a.trig[2 * g.nx + g.ny + y]);  // cos(2 pi y / ny)
             }
             unsigned pending = __ballot_sync(0xffffffffu, owner >= 0);
             while (pending) {
@@ -305,8 +320,8 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const DiagArgs a)
                 pending &= ~__ballot_sync(0xffffffffu, mine);
 #pragma unroll
                 for (int k = 0; k < 5; ++k) {
-                    const double sum = warp_sum(mine ? v[k] : 0.0);
-                    if (lane == 0) atomicAdd(&tube_acc[t * 5 + k], sum);
+                    const Real sum = warp_sum(mine ? v[k] : Real(0));
+                    if (lane == 0) atomicAdd(&tube_acc[t * 5 + k], (double)sum);
                 }
             }
         }

@@ -257,6 +257,35 @@ def test_diagnostics_match_oracle(nh, oracle_mod):
     assert abs(d["max_norm"] - 1) < 1e-14 and abs(d["min_norm"] - 1) < 1e-14
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("walls,anchoring", [(True, "homeotropic"), (True, "none"), (False, "homeotropic")])
+def test_diagnostics_match_oracle_variants(nh, oracle_mod, prec, walls, anchoring):
+    """Several 16-layer chunks with a ragged last one (nz = 37), a column count
+    that is not a multiple of the warp size, both wall anchorings and periodic
+    z, bulk W0; FP64 to rounding, FP32 to its per-site precision."""
+    O = oracle_mod
+    nx, ny, nz = 35, 33, 37
+    tubes = [(9.0, 8.0), (26.0, 24.0)]
+    params = _generic(nx, ny, nz, dt_fd=2, K=0.02, q0=2 * math.pi / 12, W0=0.002, walls_z=walls,
+                      anchoring=anchoring)
+    n0 = I.skyrmion_tubes(nx, ny, nz, tubes, 7.0)
+    ref = _oracle_sim(O, params, n0).step(6)
+    ch = _channel(nh, params, n0, precision=prec)
+    ch.set_tubes(tubes)
+    ch.step(6)
+    d = ch.diagnostics()
+    cref = O.centroids(O.OracleParams.from_dict(params), ref.n, tubes)
+    if prec == "fp64":
+        assert abs(d["mass"] - ref.mass()) <= 1e-12 * ch.N
+        assert abs(d["energy"] - ref.energy()) <= 1e-11 * abs(ref.energy())
+        assert np.max(np.abs(d["centroids"] - cref)) < 1e-9
+    else:
+        assert abs(d["mass"] - ref.mass()) <= 1e-5 * ch.N
+        assert abs(d["energy"] - ref.energy()) <= 1e-4 * abs(ref.energy())
+        assert np.max(np.abs(d["centroids"] - cref)) < 1e-3
+    assert d["nonfinite"] == 0
+
+
 def test_mass_conserved_fp32(nh):
     params, n0 = I.tiny_channel()
     ch = _channel(nh, params, n0, precision="fp32")
