@@ -83,6 +83,7 @@ class OracleParams:
     alpha6: float = 0.0
     W0: float = 0.0
     dt_fd: int = 1
+    paper_order: bool = False  # the loop order of Sec. II.D taken literally (see OracleSim)
 
     @property
     def N(self) -> int:
@@ -120,7 +121,7 @@ def lib():
         _lib.or_lattice.argtypes = [ctypes.POINTER(ctypes.c_int), dp, ctypes.POINTER(ctypes.c_int)]
         _lib.or_feq.argtypes = [ctypes.c_double, dp, ctypes.c_int, dp]
         _lib.or_guo_source.argtypes = [dp, dp, dp]
-        _lib.or_lb_step.argtypes = [pp, dp, dp, dp, dp, dp]
+        _lib.or_lb_step.argtypes = [pp, dp, dp, dp, dp, dp, dp]
         _lib.or_init_populations.argtypes = [pp, dp, dp, dp]
         _lib.or_molecular_field.argtypes = [pp, dp, dp]
         _lib.or_director_rate.argtypes = [pp, dp, dp, dp]
@@ -205,15 +206,18 @@ def init_populations(p: OracleParams, rho=None, u=None) -> np.ndarray:
     return f.reshape(19, N)
 
 
-def lb_step(p: OracleParams, f, Flc):
-    """One LB step; returns (f_new[19,N], rho[N], u[3,N])."""
+def lb_step(p: OracleParams, f, Flc, Fu=None):
+    """One LB step; returns (f_new[19,N], rho[N], u[3,N]).  Fu (optional) is
+    the LC force whose half shifts u; by default the collision's force Flc."""
     N = p.N
     f = _f64(f)
     fnew = np.empty_like(f)
     rho = np.empty(N)
     u = np.empty(3 * N)
     c = p.to_c()
-    lib().or_lb_step(ctypes.byref(c), _ptr(f), _ptr(fnew), _ptr(_vec(p, Flc)), _ptr(rho), _ptr(u))
+    fu = None if Fu is None else _vec(p, Fu)
+    lib().or_lb_step(ctypes.byref(c), _ptr(f), _ptr(fnew), _ptr(_vec(p, Flc)),
+                     _ptr(fu) if fu is not None else None, _ptr(rho), _ptr(u))
     return fnew.reshape(19, N), rho, u.reshape(3, N)
 
 
@@ -269,6 +273,12 @@ class OracleSim:
     ``s`` counts completed LB steps.  After LB step s, if s % dt_fd == 0, the
     predictor-corrector runs with the u of that step, then the force is
     recomputed from the new n and that u.
+
+    With ``paper_order`` the steps of Sec. II.D are taken in the printed order:
+    streaming, macroscopic fields (u with the force in effect), the FD update
+    and force when due, and only then the collision of that step, whose Guo
+    source therefore carries the new force while its u still carries half of
+    the old one.
     """
     p: OracleParams
     n: np.ndarray
@@ -289,9 +299,19 @@ class OracleSim:
 
     def step(self, count: int = 1):
         for _ in range(count):
+            due = (self.s + 1) % self.p.dt_fd == 0
+            if self.p.paper_order and due:
+                # macroscopic fields of this step (its collision result is not kept)
+                _, self.rho, self.u = lb_step(self.p, self.f, self.F)
+                self.n = fd_step(self.p, self.n, self.u)
+                F_old = self.F
+                self.F = force(self.p, stress(self.p, self.n, self.u))
+                self.f, _, _ = lb_step(self.p, self.f, self.F, Fu=F_old)
+                self.s += 1
+                continue
             self.f, self.rho, self.u = lb_step(self.p, self.f, self.F)
             self.s += 1
-            if self.s % self.p.dt_fd == 0:
+            if due:
                 self.n = fd_step(self.p, self.n, self.u)
                 self.F = force(self.p, stress(self.p, self.n, self.u))
         return self

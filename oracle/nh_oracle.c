@@ -144,11 +144,14 @@ void or_guo_source(const double* u, const double* F, double* S)
 /* One LB time step.  f holds the post-collision populations of the previous
  * step; fnew receives the new post-collision populations.  Streaming is done
  * by pulling f_i from x - e_i; a link that crosses a plate is replaced by the
- * half-way bounce-back f_i(x) <- f_opp(i)(x).  The moments use the force
- * F = F_lc + rho g of the current FD interval.  rho and u (the macroscopic
- * fields of this step, Eqs. shifted-rho / shifeted-u) are returned. */
-void or_lb_step(const or_params* p, const double* f, double* fnew, const double* Flc, double* rho_out,
-                double* u_out)
+ * half-way bounce-back f_i(x) <- f_opp(i)(x).  The collision's Guo source uses
+ * the force F = F_lc + rho g of the current FD interval.  The velocity
+ * u = (sum e_i f_i + H/2)/rho of Eq. shifeted-u takes H = Fu_lc + rho g when
+ * Fu_lc is given (the force in effect when the paper's loop computed the
+ * macroscopic fields, Sec. II.D), else H = F.  rho and u (the macroscopic
+ * fields used by the collision, Eqs. shifted-rho / shifeted-u) are returned. */
+void or_lb_step(const or_params* p, const double* f, double* fnew, const double* Flc, const double* Fu_lc,
+                double* rho_out, double* u_out)
 {
     const size_t N = (size_t)p->nx * p->ny * p->nz;
 #pragma omp parallel for schedule(static)
@@ -175,9 +178,10 @@ void or_lb_step(const or_params* p, const double* f, double* fnew, const double*
                     for (int a = 0; a < 3; ++a) mom[a] += E[i][a] * fin[i];
                 }
                 double rho = p->shifted ? 1.0 + sum : sum;
-                double F[3], u[3];
+                double F[3], H[3], u[3];
                 for (int a = 0; a < 3; ++a) F[a] = Flc[(size_t)a * N + s] + rho * p->g[a];
-                for (int a = 0; a < 3; ++a) u[a] = mom[a] / rho + F[a] / (2.0 * rho);
+                for (int a = 0; a < 3; ++a) H[a] = (Fu_lc ? Fu_lc[(size_t)a * N + s] + rho * p->g[a] : F[a]);
+                for (int a = 0; a < 3; ++a) u[a] = mom[a] / rho + H[a] / (2.0 * rho);
                 /* collision */
                 double feq[19], S[19];
                 or_feq(rho, u, p->shifted, feq);

@@ -164,7 +164,7 @@ __device__ __forceinline__ Real link_energy(const Real n[3], const Real m[3], in
 // previous centroid (FP32 periodic distance with an FP64 tie check), the
 // FP64 sin/cos tables of the column position, a warp sum in Real per owner
 // and FP64 shared-memory accumulation.
-constexpr int kDiagChunk = 16;
+constexpr int kDiagChunk = 8;
 
 template <typename Real>
 __device__ __forceinline__ void load3(const Real* __restrict__ n, int N, int s, Real out[3])
@@ -175,7 +175,7 @@ __device__ __forceinline__ void load3(const Real* __restrict__ n, int N, int s, 
 }
 
 template <typename Real, typename Store>
-__global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const DiagArgs a)
+__global__ void __launch_bounds__(DIAG_THREADS, sizeof(Real) == 4 ? 5 : 1) diag_kernel(const DiagArgs a)
 {
     const Geom g = a.g;
     const int N = g.N;
@@ -193,8 +193,13 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const DiagArgs a)
     const int T = a.n_tubes;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __shared__ double tube_acc[NH_MAX_TUBES * 5];
+    __shared__ float tube_xy[NH_MAX_TUBES][2];
     __shared__ double red[DIAG_THREADS / 32][DIAG_FIXED];
     for (int k = threadIdx.x; k < T * 5; k += blockDim.x) tube_acc[k] = 0.0;
+    for (int k = threadIdx.x; k < T; k += blockDim.x) {
+        tube_xy[k][0] = (float)a.tubes[k][0];
+        tube_xy[k][1] = (float)a.tubes[k][1];
+    }
     __syncthreads();
 
     double mass = 0.0, energy = 0.0;
@@ -281,7 +286,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const DiagArgs a)
                 int second = -1;
                 const float hx = 0.5f * g.nx, hy = 0.5f * g.ny;
                 for (int k = 0; k < T; ++k) {
-                    float dx = (float)x - (float)a.tubes[k][0], dy = (float)y - (float)a.tubes[k][1];
+                    float dx = (float)x - tube_xy[k][0], dy = (float)y - tube_xy[k][1];
                     dx = dx > hx ? dx - g.nx : (dx < -hx ? dx + g.nx : dx);
                     dy = dy > hy ? dy - g.ny : (dy < -hy ? dy + g.ny : dy);
                     const float d2 = dx * dx + dy * dy;
@@ -308,10 +313,21 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const DiagArgs a)
                     if (d2[1] < d2[0] || (d2[1] == d2[0] && cand[1] < cand[0])) owner = cand[1];
                 }
                 v[0] = wsum;
-                v[1] = wsum * Real(a.trig[x]);                    // sin(2 pi x / nx)
-                v[2] = wsum * Real(a.trig[g.nx + x]);             // cos(2 pi x / nx)
-                v[3] = wsum * Real(a.trig[2 * g.nx + y]);         // sin(2 pi y / ny)
-                v[4] = wsum * Real(a.trig[2 * g.nx + g.ny + y]);  // cos(2 pi y / ny)
+                if (sizeof(Real) == 8) {
+                    v[1] = wsum * Real(a.trig[x]);                    // sin(2 pi x / nx)
+                    v[2] = wsum * Real(a.trig[g.nx + x]);             // cos(2 pi x / nx)
+                    v[3] = wsum * Real(a.trig[2 * g.nx + y]);         // sin(2 pi y / ny)
+                    v[4] = wsum * Real(a.trig[2 * g.nx + g.ny + y]);  // cos(2 pi y / ny)
+                } else {
+                    // FP32 build: the angles in FP32 (sin/cos of pi * 2x/nx), no FP64 conversions
+                    float sx, cx, sy, cy;
+                    sincospif(2.f * (float)x / (float)g.nx, &sx, &cx);
+                    sincospif(2.f * (float)y / (float)g.ny, &sy, &cy);
+                    v[1] = wsum * Real(sx);
+                    v[2] = wsum * Real(cx);
+                    v[3] = wsum * Real(sy);
+                    v[4] = wsum * Real(cy);
+                }
             }
             unsigned pending = __ballot_sync(0xffffffffu, owner >= 0);
             while (pending) {
@@ -497,7 +513,7 @@ template cudaError_t launch_director_change<double>(const double*, double*, doub
 template cudaError_t launch_director_change<float>(const float*, float*, double*, double*, int, cudaStream_t);
 
 int diag_num_values(int n_tubes) { return DIAG_FIXED + 5 * n_tubes; }
-int diag_blocks() { return 4 * 152; }
+int diag_blocks() { return 5 * 152; }
 
 template <typename Real>
 cudaError_t launch_load_fields(const double* n, const double* u, const double* rho, Real* dn, Real* du, Real* drho,

@@ -260,7 +260,7 @@ def test_diagnostics_match_oracle(nh, oracle_mod):
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("walls,anchoring", [(True, "homeotropic"), (True, "none"), (False, "homeotropic")])
 def test_diagnostics_match_oracle_variants(nh, oracle_mod, prec, walls, anchoring):
-    """Several 16-layer chunks with a ragged last one (nz = 37), a column count
+    """Several 8-layer chunks with a ragged last one (nz = 37), a column count
     that is not a multiple of the warp size, both wall anchorings and periodic
     z, bulk W0; FP64 to rounding, FP32 to its per-site precision."""
     O = oracle_mod

@@ -176,3 +176,83 @@ def test_shifted_equals_unshifted_in_fp64(oracle_mod):
     b = oracle_mod.OracleSim(oracle_mod.OracleParams.from_dict(dict(params, shifted=False)), n0).step(60)
     assert oracle_mod.rel_l2(b.u, a.u) < 1e-9
     assert oracle_mod.rel_l2(b.n, a.n) < 1e-13
+
+
+@pytest.mark.parametrize("shifted", [False, True])
+def test_half_force_shift_closed_form(oracle_mod, shifted):
+    """u shifted by H/2 and a Guo source with force F: from the moments of f^eq
+    and of S (sum e S = F), the post-collision momentum of a uniform state is
+    m + F + (H - F) / (2 tau), and the mass is unchanged."""
+    O = oracle_mod
+    p = O.OracleParams(nx=4, ny=3, nz=2, walls_z=False, shifted=shifted, tau=0.7)
+    N = p.N
+    rho0, u0 = 1.03, np.array([2e-3, -1e-3, 5e-4])
+    f = O.init_populations(p, np.full(N, rho0), np.tile(u0[:, None], (1, N)))
+    e, _, _ = O.lattice()
+    m = e.T @ f[:, 0]
+    H, F = np.array([3e-4, -2e-4, 1e-4]), np.array([-1e-4, 4e-4, 2e-4])
+    fn, rho, u = O.lb_step(p, f, np.tile(F[:, None], (1, N)), Fu=np.tile(H[:, None], (1, N)))
+    m_new = e.T @ fn
+    expect = m + F + (H - F) / (2 * p.tau)
+    assert np.max(np.abs(m_new - expect[:, None])) < 1e-15
+    assert np.allclose(u[:, 0], (m + H / 2) / rho0, rtol=0, atol=1e-16)
+    assert abs(np.sum(fn) - np.sum(f)) < 1e-13
+
+
+def _push_paper_loop(O, p, n0, steps):
+    """The loop of Sec. II.D in the printed order, written independently of the
+    oracle's LB step: push streaming by array shifts on a periodic lattice,
+    macroscopic fields with the force in effect, the FD update and force when
+    due, then the collision (Eq. shifted-lbe with Guo's source).  The lattice
+    is the set of integer vectors with |e|^2 <= 2 and the printed weights; the
+    FD update and the force come from the oracle (pinned separately)."""
+    cs2, rows = _golden_lattice()
+    e, _, _ = O.lattice()           # the oracle's population order, checked against the golden file
+    w = np.array([rows[int(v @ v)][1] for v in e])
+    nz, ny, nx = p.nz, p.ny, p.nx
+    N = p.N
+    f = O.init_populations(p, np.ones(N), np.zeros((3, N)))
+    n = np.asarray(n0, dtype=np.float64).reshape(3, N).copy()
+    u = np.zeros((3, N))
+    F = O.force(p, O.stress(p, n, u))
+    g = np.array(p.g)[:, None]
+    for s in range(1, steps + 1):
+        fs = f.reshape(19, nz, ny, nx)
+        f = np.stack([np.roll(fs[i], shift=(e[i, 2], e[i, 1], e[i, 0]), axis=(0, 1, 2)) for i in range(19)])
+        f = f.reshape(19, N)
+        sm = f.sum(axis=0)
+        rho = 1.0 + sm if p.shifted else sm
+        Ft = F + rho * g
+        u = (e.T @ f + 0.5 * Ft) / rho
+        if s % p.dt_fd == 0:
+            n = O.fd_step(p, n, u)
+            F = O.force(p, O.stress(p, n, u))
+            Ft = F + rho * g
+        eu = e @ u
+        uu = np.sum(u * u, axis=0)
+        feq = w[:, None] * rho * (1 + eu / cs2 + eu ** 2 / (2 * cs2 ** 2) - uu / (2 * cs2))
+        if p.shifted:
+            feq = feq - w[:, None]
+        eF = e @ Ft
+        uF = np.sum(u * Ft, axis=0)
+        S = w[:, None] * (eF / cs2 + (eu * eF) / cs2 ** 2 - uF / cs2)
+        f = f - (f - feq) / p.tau + (1 - 1 / (2 * p.tau)) * S
+    return f, n, u
+
+
+@pytest.mark.parametrize("dt_fd", [1, 3])
+def test_paper_order_matches_push_form_loop(oracle_mod, dt_fd):
+    O = oracle_mod
+    d = dict(nx=10, ny=8, nz=6, walls_z=False, shifted=True, tau=0.8, g=(2e-5, 0.0, -1e-5), K=0.02,
+             q0=2 * math.pi / 8, gamma1=1.0, gamma2=-0.9, alpha1=0.01, alpha2=-0.95, alpha3=0.05,
+             alpha4p=0.02, alpha5=0.45, alpha6=-0.45, W0=0.003, dt_fd=dt_fd)
+    n0 = I.skyrmion_tubes(10, 8, 6, [(5.0, 4.0)], 3.0)
+    p = O.OracleParams(paper_order=True, **d)
+    steps = 7
+    f_ref, n_ref, u_ref = _push_paper_loop(O, p, n0, steps)
+    sim = O.OracleSim(p, n0).step(steps)
+    assert np.max(np.abs(sim.f - f_ref)) < 1e-14
+    assert np.max(np.abs(sim.n - n_ref)) < 1e-14
+    # the fused order (collision before the FD update) differs: the check discriminates
+    other = O.OracleSim(O.OracleParams(paper_order=False, **d), n0).step(steps)
+    assert np.max(np.abs(other.f - f_ref)) > 1e-9
