@@ -77,6 +77,13 @@ typedef struct nh_params {
     int32_t shifted;      /* 1: store f_i - w_i (Eq. shifted-feq); 0: plain f_i */
     int32_t dt_fd;        /* FD time step in LB steps, >= 1 (Sec. II.D) */
     int32_t check_stability; /* 1: reject dt_fd * 6 K / gamma1 > 1 (Heun limit of the 3D compact Laplacian) */
+    int32_t paper_order;  /* 1: the loop order of Sec. II.D taken literally: on a step that completes an
+                             FD interval the FD update runs between the macroscopic fields and the
+                             collision, so that collision's Guo source carries the new force while its
+                             u carries half of the old one (an extra LB launch per FD interval).
+                             0 (default): the collision of that step keeps the old force and the new
+                             force acts from the next step.  Not supported by nh_batch_step. */
+    int32_t reserved;     /* must be 0 */
     double tau;           /* SRT relaxation time, > 1/2; nu = (tau - 1/2)/3 */
     double g[3];          /* body acceleration g of Eq. NS-eq; the LB force is F_lc + rho g */
     double K;             /* one-constant Frank elasticity */

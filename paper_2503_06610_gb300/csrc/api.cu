@@ -14,7 +14,14 @@
 
 #include "nh_internal.cuh"
 
+#include <cstddef>
+
 using namespace nh;
+
+// The parameter block is passed by pointer from C and from Python's ctypes:
+// 12 int32 fields then 15 doubles, without padding.
+static_assert(sizeof(nh_params) == 12 * 4 + 15 * 8, "nh_params layout");
+static_assert(offsetof(nh_params, tau) == 48, "nh_params layout");
 
 namespace {
 
@@ -34,7 +41,7 @@ size_t store_size(const nh_params& p)
 }
 
 struct Layout {
-    size_t f[2], F, n, nP, ndot, u, rho, sigma, snap, staging, partials, result, scales, absmax, trig, total;
+    size_t f[2], F, Fprev, n, nP, ndot, u, rho, sigma, snap, staging, partials, result, scales, absmax, trig, total;
 };
 
 Layout make_layout(const nh_params& p)
@@ -51,6 +58,7 @@ Layout make_layout(const nh_params& p)
     L.f[0] = take(19 * N * S);
     L.f[1] = take(19 * N * S);
     L.F = take(3 * N * R);
+    L.Fprev = take(p.paper_order ? 3 * N * R : 0);  // the force of the previous FD interval
     L.n = take(3 * N * R);
     L.nP = take(3 * N * R);
     L.ndot = take(3 * N * R);
@@ -123,6 +131,14 @@ int validate(const nh_params* p, std::string& err)
     }
     if (p->shifted != 0 && p->shifted != 1) {
         err = "shifted must be 0 or 1";
+        return NH_EINVAL;
+    }
+    if (p->paper_order != 0 && p->paper_order != 1) {
+        err = "paper_order must be 0 or 1";
+        return NH_EINVAL;
+    }
+    if (p->reserved != 0) {
+        err = "reserved must be 0";
         return NH_EINVAL;
     }
     const double vals[] = {p->g[0], p->g[1], p->g[2], p->K, p->q0, p->gamma2, p->alpha1, p->alpha2,
@@ -257,6 +273,7 @@ LBChan<Real, Store> lb_chan(nh_ctx* c, int src)
     a.fsrc = c->at<const Store>(c->L.f[src]);
     a.fdst = c->at<Store>(c->L.f[1 - src]);
     a.F = c->at<const Real>(c->L.F);
+    a.Fu = nullptr;
     a.u = c->at<Real>(c->L.u);
     a.rho = c->at<Real>(c->L.rho);
     a.scales = c->at<float>(c->L.scales);
@@ -328,24 +345,30 @@ int timed(nh_ctx* c, int kclass, cudaStream_t st, F&& launch, const char* what)
     return NH_OK;
 }
 
-int enqueue_lb(nh_ctx* c, int src, bool write_macro, cudaStream_t st)
+// One LB launch from population buffer src.  stale_u: u is shifted by half of
+// the previous FD interval's force (Fprev) instead of the current one.
+int enqueue_lb(nh_ctx* c, int src, bool write_macro, cudaStream_t st, bool stale_u = false)
 {
     const bool sh = c->p.shifted != 0;
     switch (c->p.storage) {
     case NH_STORE_F64: {
         auto a = lb_chan<double, double>(c, src);
+        if (stale_u) a.Fu = c->at<const double>(c->L.Fprev);
         return timed(c, NH_KCLASS_LB, st, [&] { return launch_lb(a, sh, write_macro, c->lb_variant, st); }, "lb");
     }
     case NH_STORE_F32: {
         auto a = lb_chan<float, float>(c, src);
+        if (stale_u) a.Fu = c->at<const float>(c->L.Fprev);
         return timed(c, NH_KCLASS_LB, st, [&] { return launch_lb(a, sh, write_macro, c->lb_variant, st); }, "lb");
     }
     case NH_STORE_F16S: {
         auto a = lb_chan<float, __half>(c, src);
+        if (stale_u) a.Fu = c->at<const float>(c->L.Fprev);
         return timed(c, NH_KCLASS_LB, st, [&] { return launch_lb(a, sh, write_macro, c->lb_variant, st); }, "lb");
     }
     default: {
         auto a = lb_chan<float, __nv_bfloat16>(c, src);
+        if (stale_u) a.Fu = c->at<const float>(c->L.Fprev);
         return timed(c, NH_KCLASS_LB, st, [&] { return launch_lb(a, sh, write_macro, c->lb_variant, st); }, "lb");
     }
     }
@@ -427,10 +450,28 @@ int enqueue_force_any(nh_ctx* c, cudaStream_t st)
 }
 
 // One LB step followed, when the step count reaches a multiple of dt_fd, by the FD update.
+// With paper_order the FD update sits between the macroscopic fields and the
+// collision of that step (Sec. II.D): a first launch writes u and rho (its
+// populations are overwritten), the FD update computes the new force, and the
+// step is redone from the same source buffer with the new force in the Guo
+// source and u shifted by half of the old one.
 int enqueue_one_step(nh_ctx* c, bool last_of_call, cudaStream_t st)
 {
     const int64_t next = c->step + 1;
     const bool fd = (next % c->p.dt_fd) == 0;
+    if (fd && c->p.paper_order) {
+        int r = enqueue_lb(c, c->cur, true, st);
+        if (r) return r;
+        const size_t fbytes = 3 * (size_t)c->N * (c->p.precision == NH_FP64 ? sizeof(double) : sizeof(float));
+        NH_CUDA(c, cudaMemcpyAsync(c->ws + c->L.Fprev, c->ws + c->L.F, fbytes, cudaMemcpyDeviceToDevice, st));
+        r = enqueue_fd_any(c, st);
+        if (r) return r;
+        r = enqueue_lb(c, c->cur, false, st, true);
+        if (r) return r;
+        c->cur ^= 1;
+        c->step = next;
+        return NH_OK;
+    }
     int r = enqueue_lb(c, c->cur, fd || last_of_call, st);
     if (r) return r;
     c->cur ^= 1;
@@ -632,6 +673,8 @@ int batch_prepare(nh_ctx* const* ctxs, int count, int64_t n_lb_steps, BatchPlan*
         if (c->p.precision != c0->p.precision || c->p.storage != c0->p.storage || c->p.shifted != c0->p.shifted ||
             c->p.dt_fd != c0->p.dt_fd)
             return fail(nullptr, NH_EINVAL, "channels must share precision, storage, shifted and dt_fd");
+        if (c->p.paper_order)
+            return fail(nullptr, NH_EINVAL, "channel " + std::to_string(k) + ": paper_order is not supported in batches");
         if (c->device != c0->device) return fail(nullptr, NH_EINVAL, "channels must be on one device");
         if (c->cur != c0->cur || c->step % c0->p.dt_fd != c0->step % c0->p.dt_fd)
             return fail(nullptr, NH_EINVAL, "channels must be at the same step phase (step mod dt_fd, buffer parity)");

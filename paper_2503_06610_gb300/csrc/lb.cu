@@ -165,9 +165,15 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
             const Real Fy = c.F[N + s] + rho * c.gy;
             const Real Fz = c.F[2 * N + s] + rho * c.gz;
             const Real inv_rho = Real(1) / rho;
-            const Real ux = (mx + Real(0.5) * Fx) * inv_rho;
-            const Real uy = (my + Real(0.5) * Fy) * inv_rho;
-            const Real uz = (mz + Real(0.5) * Fz) * inv_rho;
+            Real Hx = Fx, Hy = Fy, Hz = Fz;  // force whose half shifts u
+            if (c.Fu != nullptr) {
+                Hx = c.Fu[s] + rho * c.gx;
+                Hy = c.Fu[N + s] + rho * c.gy;
+                Hz = c.Fu[2 * N + s] + rho * c.gz;
+            }
+            const Real ux = (mx + Real(0.5) * Hx) * inv_rho;
+            const Real uy = (my + Real(0.5) * Hy) * inv_rho;
+            const Real uz = (mz + Real(0.5) * Hz) * inv_rho;
             if (WriteMacro) {
                 c.u[s] = ux;
                 c.u[N + s] = uy;

@@ -87,6 +87,7 @@ struct LBChan {
     const Store* fsrc;
     Store* fdst;
     const Real* F;  // [3][N] F_lc, frozen over the FD interval
+    const Real* Fu; // [3][N] F_lc whose half shifts u, or null: F (paper ordering of Sec. II.D)
     Real* u;        // [3][N] written on macro steps
     Real* rho;      // [N]    written on macro steps
     float* scales;

@@ -49,6 +49,7 @@ class nh_params(ctypes.Structure):
         ("walls_z", ctypes.c_int32), ("anchoring", ctypes.c_int32),
         ("precision", ctypes.c_int32), ("storage", ctypes.c_int32), ("shifted", ctypes.c_int32),
         ("dt_fd", ctypes.c_int32), ("check_stability", ctypes.c_int32),
+        ("paper_order", ctypes.c_int32), ("reserved", ctypes.c_int32),
         ("tau", ctypes.c_double), ("g", ctypes.c_double * 3),
         ("K", ctypes.c_double), ("q0", ctypes.c_double),
         ("gamma1", ctypes.c_double), ("gamma2", ctypes.c_double),
@@ -169,6 +170,7 @@ def make_params(d: dict) -> nh_params:
     p.shifted = 1 if d.get("shifted", True) else 0
     p.dt_fd = int(d.get("dt_fd", 1))
     p.check_stability = 1 if d.get("check_stability", False) else 0
+    p.paper_order = 1 if d.get("paper_order", False) else 0
     p.tau = float(d.get("tau", 1.0))
     g = d.get("g", (0.0, 0.0, 0.0))
     p.g = (ctypes.c_double * 3)(*[float(v) for v in g])

@@ -32,9 +32,9 @@ def test_library_exports_every_declared_symbol(nh):
 
 def test_params_struct_layout_matches_header(nh):
     import ctypes
-    # 10 int32 then 15 doubles, no padding
-    assert ctypes.sizeof(nh.nh_params) == 10 * 4 + 15 * 8
-    assert nh.nh_params.tau.offset == 40
+    # 12 int32 then 15 doubles, no padding
+    assert ctypes.sizeof(nh.nh_params) == 12 * 4 + 15 * 8
+    assert nh.nh_params.tau.offset == 48
 
 
 def _base(**kw):

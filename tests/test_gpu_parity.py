@@ -549,3 +549,47 @@ def test_symmetrize_c4_projection(nh):
     xs, ys = (12 + (y - 12)) % 24, (12 - (x - 12)) % 24
     rot = np.stack([-n3[1][:, ys, xs], n3[0][:, ys, xs], n3[2][:, ys, xs]])
     assert np.max(np.abs(rot - n3)) < 1e-12
+
+
+# ------------------------------------------------------------------ paper ordering of the hybrid loop (Sec. II.D)
+
+@pytest.mark.parametrize("dt_fd", [1, 3])
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_paper_order_matches_oracle(nh, oracle_mod, dt_fd, storage):
+    """paper_order = 1: the FD update between the macroscopic fields and the
+    collision; populations, n and u against the oracle's literal loop."""
+    O = oracle_mod
+    params = _generic(13, 9, 7, dt_fd=dt_fd, alpha4p=0.02, W0=0.002, paper_order=True)
+    n0 = I.skyrmion_tubes(13, 9, 7, [(6.5, 4.5)], 3.5)
+    steps = 3 * dt_fd + 2  # ends mid-interval when dt_fd > 1
+    ref = _oracle_sim(O, params, n0).step(steps)
+    prec = "fp64" if storage == "f64" else "fp32"
+    ch = _channel(nh, params, n0, precision=prec, storage=storage)
+    ch.step(steps)
+    n, u, rho = ch.get_fields()
+    f = ch.get_populations()
+    tol = 1e-12 if storage == "f64" else 2e-5
+    assert O.rel_l2(n, ref.n) <= tol
+    assert O.rel_l2(u, ref.u) <= (1e-10 if storage == "f64" else 1e-4)
+    assert np.max(np.abs(f - ref.f)) <= (1e-14 if storage == "f64" else 1e-6)
+    if storage == "f64":
+        # the default order gives a different trajectory
+        other = _channel(nh, dict(params, paper_order=False), n0, precision=prec, storage=storage)
+        other.step(steps)
+        assert O.rel_l2(other.get_fields()[1], ref.u) > 1e-8
+
+
+def test_paper_order_graphs_bitwise_and_batch_rejected(nh):
+    params = _generic(16, 12, 8, dt_fd=4, paper_order=True)
+    n0 = I.skyrmion_tubes(16, 12, 8, [(8.0, 6.0)], 4.0)
+    out = []
+    for graphs in (False, True):
+        ch = _channel(nh, params, n0, precision="fp32")
+        ch.set_graphs(graphs)
+        ch.step(4 * 5 + 3)
+        out.append(ch.get_fields())
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+    chans = [_channel(nh, params, n0, precision="fp32") for _ in range(2)]
+    with pytest.raises(nh.NHError):
+        nh.batch_step(chans, 4)
