@@ -57,6 +57,8 @@ class _Params(ctypes.Structure):
         ("alpha1", ctypes.c_double), ("alpha2", ctypes.c_double), ("alpha3", ctypes.c_double),
         ("alpha4p", ctypes.c_double), ("alpha5", ctypes.c_double), ("alpha6", ctypes.c_double),
         ("W0", ctypes.c_double), ("dt_fd", ctypes.c_double),
+        ("K11", ctypes.c_double), ("K22", ctypes.c_double), ("K33", ctypes.c_double),
+        ("frank3", ctypes.c_int),
     ]
 
 
@@ -84,6 +86,13 @@ class OracleParams:
     W0: float = 0.0
     dt_fd: int = 1
     paper_order: bool = False  # the loop order of Sec. II.D taken literally (see OracleSim)
+    K11: float = None  # three-constant Frank energy when K11, K22, K33 are all given
+    K22: float = None
+    K33: float = None
+
+    @property
+    def frank3(self) -> bool:
+        return self.K11 is not None and self.K22 is not None and self.K33 is not None
 
     @property
     def N(self) -> int:
@@ -101,6 +110,8 @@ class OracleParams:
                   "alpha5", "alpha6", "W0"):
             setattr(c, k, float(getattr(self, k)))
         c.dt_fd = float(self.dt_fd)
+        if self.frank3:
+            c.K11, c.K22, c.K33, c.frank3 = self.K11, self.K22, self.K33, 1
         return c
 
     @classmethod
@@ -132,6 +143,10 @@ def lib():
         _lib.or_stress.argtypes = [pp, dp, dp, dp]
         _lib.or_force.argtypes = [pp, dp, dp]
         _lib.or_num_threads.restype = ctypes.c_int
+        _lib.or_frank3_field.argtypes = [pp, dp, dp]
+        _lib.or_frank3_field.restype = ctypes.c_double
+        _lib.or_frank3_point.argtypes = [pp, dp, dp, dp, dp]
+        _lib.or_frank3_point.restype = ctypes.c_double
     return _lib
 
 
@@ -344,7 +359,8 @@ def _ghosted(p: OracleParams, n) -> np.ndarray:
 
 
 def frank_energy(p: OracleParams, n) -> float:
-    """Lattice one-constant Frank energy (Eq. free-energy-eq with K11=K22=K33=K).
+    """Lattice Frank energy (Eq. free-energy-eq; one-constant form with K, plus
+    the three-constant correction when K11, K22, K33 are given).
 
     E_d = sum over nearest-neighbour links (x, x+e_b) of
             K/2 |n(x+e_b) - n(x)|^2 + K q0 eps_{a b c} n_a(x) n_c(x+e_b)
@@ -372,7 +388,31 @@ def frank_energy(p: OracleParams, n) -> float:
     E += K * q0 * float(np.sum(np.einsum("ac,a...,c...->...", eps[:, 2, :], lo, hi)))
     nz_ = np.asarray(n, dtype=np.float64).reshape(3, -1)[2]
     E += p.N * 0.5 * K * q0 ** 2 - 0.5 * p.W0 * float(np.sum(nz_ ** 2))
+    if p.frank3:
+        E += frank3_field(p, n)[0]
     return float(E)
+
+
+def frank3_point(p: OracleParams, n3, G):
+    """Delta f at one site for director n3[3] and gradient G[b][c] = d_b n_c:
+    (Delta f, d Delta f/dn [3], d Delta f/dG [3][3])."""
+    n3 = np.ascontiguousarray(n3, dtype=np.float64)
+    G = np.ascontiguousarray(np.asarray(G, dtype=np.float64).reshape(9))
+    dfdn = np.empty(3)
+    P = np.empty(9)
+    c = p.to_c()
+    f = lib().or_frank3_point(ctypes.byref(c), _ptr(n3), _ptr(G), _ptr(dfdn), _ptr(P))
+    return float(f), dfdn, P.reshape(3, 3)
+
+
+def frank3_field(p: OracleParams, n):
+    """Three-constant correction: (sum over fluid sites of Delta f, its field
+    -d(sum Delta f)/dn [3,N]).  Delta f = (K11-K)/2 (div n)^2 + (K22-K)/2
+    (n . curl n + q0)^2 + (K33-K)/2 |n x curl n|^2 with central differences."""
+    hd = np.empty(3 * p.N)
+    c = p.to_c()
+    E = lib().or_frank3_field(ctypes.byref(c), _ptr(_vec(p, n)), _ptr(hd))
+    return float(E), hd.reshape(3, p.N)
 
 
 def centroids(p: OracleParams, n, previous) -> np.ndarray:

@@ -34,13 +34,20 @@
  *   - ghost layers at z = -1 and z = nz when walls are present: u = 0,
  *     n = z_hat (infinite homeotropic anchoring) or n = adjacent fluid layer
  *     (no anchoring); stress = 0 at the ghosts;
- *   - the FD update renormalises n after the corrector only.
+ *   - the FD update renormalises n after the corrector only;
+ *   - three-constant energy (Eq. free-energy-eq with K11, K22, K33): the
+ *     one-constant lattice energy with K plus, at every fluid site,
+ *       Delta f = (K11-K)/2 (div n)^2 + (K22-K)/2 (n.curl n + q0)^2
+ *               + (K33-K)/2 |n x curl n|^2
+ *     with central differences; its molecular field is the exact
+ *     -d(sum Delta f)/dn, ghost layers included.
  *
  * Layouts: a scalar field is [N] with site index x + nx*(y + ny*z); a vector
  * field is [3][N]; a tensor field is [9][N] with component a*3+b; populations
  * are [19][N] in the velocity order of E[] below.
  */
 #include <math.h>
+#include <stdlib.h>
 #include <stddef.h>
 #include <string.h>
 
@@ -55,6 +62,8 @@ typedef struct {
     double alpha1, alpha2, alpha3, alpha4p, alpha5, alpha6;  /* alpha4p = alpha_4' of Eq. force-lc-eq */
     double W0;        /* bulk effective anchoring strength */
     double dt_fd;     /* FD time step, in LB time steps */
+    double K11, K22, K33; /* three-constant Frank energy (used when frank3 = 1) */
+    int frank3;       /* 1: add the three-constant correction Delta f (see frank3_point) */
 } or_params;
 
 /* D3Q19 velocity set (Sec. II.C): rest, 6 axis links, 12 face diagonals. */
@@ -280,6 +289,117 @@ static void molecular_field(const or_params* p, const double nc[3], const double
     h[2] += p->W0 * nc[2];
 }
 
+/* Three-constant correction at one site, from the director nc and its
+ * central gradient G[b][c] = d_b n_c (Eq. free-energy-eq minus its
+ * one-constant form with K):
+ *   div = G_aa,  w_a = eps_abc G_bc (curl),  t = n.w + q0,
+ *   Delta f = a1/2 div^2 + a2/2 t^2 + a3/2 (|n|^2 |w|^2 - (n.w)^2),
+ *   a1 = K11 - K, a2 = K22 - K, a3 = K33 - K
+ * (|n x w|^2 written by Lagrange's identity, valid for any n).  Returns
+ * Delta f, dfdn[c] = d Delta f / d n_c and P[b][c] = d Delta f / d G_bc. */
+static double frank3_point(const or_params* p, const double nc[3], const double G[3][3], double dfdn[3],
+                           double P[3][3])
+{
+    const double a1 = p->K11 - p->K, a2 = p->K22 - p->K, a3 = p->K33 - p->K;
+    double div = G[0][0] + G[1][1] + G[2][2];
+    double w[3];
+    for (int a = 0; a < 3; ++a) {
+        w[a] = 0.0;
+        for (int b = 0; b < 3; ++b)
+            for (int c = 0; c < 3; ++c) w[a] += levi(a, b, c) * G[b][c];
+    }
+    double nw = nc[0] * w[0] + nc[1] * w[1] + nc[2] * w[2];
+    double nn = nc[0] * nc[0] + nc[1] * nc[1] + nc[2] * nc[2];
+    double ww = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    double t = nw + p->q0;
+    double V[3];
+    for (int c = 0; c < 3; ++c) {
+        dfdn[c] = a2 * t * w[c] + a3 * (nc[c] * ww - nw * w[c]);
+        V[c] = a2 * t * nc[c] + a3 * (nn * w[c] - nw * nc[c]); /* d Delta f / d w_c */
+    }
+    for (int b = 0; b < 3; ++b)
+        for (int c = 0; c < 3; ++c) {
+            double v = (b == c) ? a1 * div : 0.0;
+            for (int a = 0; a < 3; ++a) v += levi(a, b, c) * V[a];
+            P[b][c] = v;
+        }
+    return 0.5 * a1 * div * div + 0.5 * a2 * t * t + 0.5 * a3 * (nn * ww - nw * nw);
+}
+
+/* Site that supplies the director at (x, y, z), which may lie in a ghost
+ * layer: -1 for a fixed ghost value (homeotropic plates). */
+static long n_source(const or_params* p, int x, int y, int z)
+{
+    x = wrap(x, p->nx);
+    y = wrap(y, p->ny);
+    if (p->walls_z && (z < 0 || z >= p->nz)) {
+        if (p->anchoring) return -1;
+        z = z < 0 ? 0 : p->nz - 1;
+    }
+    return (long)site(p, x, y, wrap(z, p->nz));
+}
+
+/* Central gradient G[b][c] = d_b n_c at a fluid site (ghost reading). */
+static void central_gradient(const or_params* p, const double* n, int x, int y, int z, double G[3][3])
+{
+    for (int b = 0; b < 3; ++b) {
+        int d[3] = {0, 0, 0};
+        d[b] = 1;
+        double np[3], nm[3];
+        n_at(p, n, x + d[0], y + d[1], z + d[2], np);
+        n_at(p, n, x - d[0], y - d[1], z - d[2], nm);
+        for (int c = 0; c < 3; ++c) G[b][c] = 0.5 * (np[c] - nm[c]);
+    }
+}
+
+/* Molecular field of the three-constant correction, hd = -d(sum_x Delta f)/dn,
+ * by scattering every site's derivatives onto the sites its gradient reads:
+ * G_bc(x) = [n_c(source(x + e_b)) - n_c(source(x - e_b))]/2.  Returns the sum
+ * of Delta f.  hd is [3][N]. */
+static double frank3_field(const or_params* p, const double* n, double* hd)
+{
+    const size_t N = (size_t)p->nx * p->ny * p->nz;
+    double E = 0.0;
+    memset(hd, 0, 3 * N * sizeof(double));
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                size_t s = site(p, x, y, z);
+                double nc[3], G[3][3], dfdn[3], P[3][3];
+                n_at(p, n, x, y, z, nc);
+                central_gradient(p, n, x, y, z, G);
+                E += frank3_point(p, nc, G, dfdn, P);
+                for (int c = 0; c < 3; ++c) hd[(size_t)c * N + s] -= dfdn[c];
+                for (int b = 0; b < 3; ++b) {
+                    int d[3] = {0, 0, 0};
+                    d[b] = 1;
+                    long sp = n_source(p, x + d[0], y + d[1], z + d[2]);
+                    long sm = n_source(p, x - d[0], y - d[1], z - d[2]);
+                    for (int c = 0; c < 3; ++c) {
+                        if (sp >= 0) hd[(size_t)c * N + (size_t)sp] -= 0.5 * P[b][c];
+                        if (sm >= 0) hd[(size_t)c * N + (size_t)sm] += 0.5 * P[b][c];
+                    }
+                }
+            }
+    return E;
+}
+
+/* Exported: Delta f at one site for a given director and gradient (tests);
+ * G, P are [3][3] row-major with G[3b+c] = d_b n_c. */
+double or_frank3_point(const or_params* p, const double* nc, const double* Gflat, double* dfdn, double* Pflat)
+{
+    double G[3][3], P[3][3];
+    for (int b = 0; b < 3; ++b)
+        for (int c = 0; c < 3; ++c) G[b][c] = Gflat[3 * b + c];
+    double f = frank3_point(p, nc, G, dfdn, P);
+    for (int b = 0; b < 3; ++b)
+        for (int c = 0; c < 3; ++c) Pflat[3 * b + c] = P[b][c];
+    return f;
+}
+
+/* Exported: the three-constant correction's energy sum and field (tests). */
+double or_frank3_field(const or_params* p, const double* n, double* hd) { return frank3_field(p, n, hd); }
+
 /* Strain rate D and vorticity W (Sec. II.A) from du[a][b] = d_a u_b. */
 static void strain_vorticity(const double du[3][3], double D[3][3], double W[3][3])
 {
@@ -294,6 +414,8 @@ static void strain_vorticity(const double du[3][3], double D[3][3], double W[3][
 void or_molecular_field(const or_params* p, const double* n, double* h_out)
 {
     const size_t N = (size_t)p->nx * p->ny * p->nz;
+    double* hd = p->frank3 ? (double*)malloc(3 * N * sizeof(double)) : NULL;
+    if (hd) frank3_field(p, n, hd);
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
@@ -302,8 +424,9 @@ void or_molecular_field(const or_params* p, const double* n, double* h_out)
                 n_at(p, n, x, y, z, nc);
                 local_derivs(p, n, NULL, x, y, z, dn, lap, du);
                 molecular_field(p, nc, dn, lap, h);
-                for (int a = 0; a < 3; ++a) h_out[(size_t)a * N + s] = h[a];
+                for (int a = 0; a < 3; ++a) h_out[(size_t)a * N + s] = h[a] + (hd ? hd[(size_t)a * N + s] : 0.0);
             }
+    free(hd);
 }
 
 /* Time derivative of the director, Eq. director-time-eq, evaluated for the
@@ -312,6 +435,8 @@ void or_molecular_field(const or_params* p, const double* n, double* h_out)
 void or_director_rate(const or_params* p, const double* n, const double* u, double* ndot)
 {
     const size_t N = (size_t)p->nx * p->ny * p->nz;
+    double* hd = p->frank3 ? (double*)malloc(3 * N * sizeof(double)) : NULL;
+    if (hd) frank3_field(p, n, hd);
 #pragma omp parallel for schedule(static)
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
@@ -322,6 +447,8 @@ void or_director_rate(const or_params* p, const double* n, const double* u, doub
                 u_at(p, u, x, y, z, uc);
                 local_derivs(p, n, u, x, y, z, dn, lap, du);
                 molecular_field(p, nc, dn, lap, h);
+                if (hd)
+                    for (int a = 0; a < 3; ++a) h[a] += hd[(size_t)a * N + s];
                 strain_vorticity(du, D, W);
                 for (int m = 0; m < 3; ++m) {
                     double r = h[m] / p->gamma1;
@@ -331,6 +458,7 @@ void or_director_rate(const or_params* p, const double* n, const double* u, doub
                     ndot[(size_t)m * N + s] = r;
                 }
             }
+    free(hd);
 }
 
 /* One FD step of length dt_fd with the predictor-corrector scheme of Sec. II.B,
@@ -413,6 +541,8 @@ void or_elastic_stress_point(const or_params* p, const double* n, const double* 
 void or_stress(const or_params* p, const double* n, const double* u, double* sigma)
 {
     const size_t N = (size_t)p->nx * p->ny * p->nz;
+    double* hd = p->frank3 ? (double*)malloc(3 * N * sizeof(double)) : NULL;
+    if (hd) frank3_field(p, n, hd);
 #pragma omp parallel for schedule(static)
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
@@ -422,6 +552,8 @@ void or_stress(const or_params* p, const double* n, const double* u, double* sig
                 n_at(p, n, x, y, z, nc);
                 local_derivs(p, n, u, x, y, z, dn, lap, du);
                 molecular_field(p, nc, dn, lap, h);
+                if (hd)
+                    for (int a = 0; a < 3; ++a) h[a] += hd[(size_t)a * N + s];
                 strain_vorticity(du, D, W);
                 double Dflat[9], dnflat[9], Nv[3], sv[9], se[9];
                 for (int a = 0; a < 3; ++a)
@@ -432,8 +564,17 @@ void or_stress(const or_params* p, const double* n, const double* u, double* sig
                 or_transport_point(nc, h, Dflat, p->gamma1, p->gamma2, Nv);
                 or_viscous_stress_point(p, nc, Dflat, Nv, sv);
                 or_elastic_stress_point(p, nc, dnflat, se);
+                if (hd) {
+                    /* Ericksen stress of the correction: -d_a n_g dDelta f/d(d_b n_g) */
+                    double dfdn[3], P[3][3];
+                    frank3_point(p, nc, dn, dfdn, P);
+                    for (int a = 0; a < 3; ++a)
+                        for (int b = 0; b < 3; ++b)
+                            for (int g = 0; g < 3; ++g) se[3 * a + b] -= dn[a][g] * P[b][g];
+                }
                 for (int k = 0; k < 9; ++k) sigma[(size_t)k * N + s] = sv[k] + se[k];
             }
+    free(hd);
 }
 
 /* F^LC_a = d_b sigma_ab with central differences; sigma = 0 at solid ghosts. */

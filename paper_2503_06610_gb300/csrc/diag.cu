@@ -383,8 +383,10 @@ __global__ void diag_final_kernel(const double* __restrict__ partials, double* _
     for (int k = threadIdx.x >> 5; k < V; k += blockDim.x >> 5) {
         const int kind = (k == 2 || k == 4) ? 1 : (k == 3 ? 2 : 0);  // 0 sum, 1 max, 2 min
         double acc = kind == 2 ? 1e300 : 0.0;
+        // loads unrolled ahead of the (fixed-order) combination
+#pragma unroll 8
         for (int b = lane; b < blocks; b += 32) {
-            const double v = partials[(size_t)b * V + k];
+            const double v = __ldg(partials + (size_t)b * V + k);
             acc = kind == 0 ? acc + v : (kind == 1 ? fmax(acc, v) : fmin(acc, v));
         }
         for (int o = 16; o > 0; o >>= 1) {

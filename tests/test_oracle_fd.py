@@ -284,3 +284,126 @@ def test_paper_table_parodi_relation():
         k, v = line.split()
         vals[k] = float(v)
     assert abs((vals["alpha6"] - vals["alpha5"]) - (vals["alpha2"] + vals["alpha3"])) < 5e-4
+
+
+# ------------------------------------------------------------------ three-constant Frank energy
+
+K3 = dict(K=0.01, K11=0.02, K22=0.005, K33=0.03)
+
+
+def test_frank3_closed_form_energies(oracle_mod):
+    """Delta f of a helix (pure twist: div = 0, w = -sin(q) n) and of a
+    splay-bend wave n = (sin kx, 0, cos kx) (n.w = 0) in closed form, with the
+    central-difference factors sin q, sin k."""
+    O = oracle_mod
+    q0 = 0.3
+    nz, q = 16, 2 * math.pi / 16
+    p = O.OracleParams(nx=2, ny=3, nz=nz, walls_z=False, q0=q0, **K3)
+    E, _ = O.frank3_field(p, I.helix(2, 3, nz, q))
+    assert abs(E - p.N * 0.5 * (p.K22 - p.K) * (q0 - math.sin(q)) ** 2) < 1e-15 * p.N
+    nx, k = 12, 2 * math.pi / 12
+    p = O.OracleParams(nx=nx, ny=2, nz=3, walls_z=False, q0=q0, **K3)
+    x = np.arange(nx)
+    n = np.zeros((3, 3, 2, nx))
+    n[0] = np.sin(k * x)
+    n[2] = np.cos(k * x)
+    E, _ = O.frank3_field(p, n.reshape(3, -1))
+    per_col = np.sum(0.5 * (p.K11 - p.K) * np.cos(k * x) ** 2 * math.sin(k) ** 2
+                     + 0.5 * (p.K22 - p.K) * q0 ** 2
+                     + 0.5 * (p.K33 - p.K) * np.sin(k * x) ** 2 * math.sin(k) ** 2)
+    assert abs(E - 6 * per_col) < 1e-15 * p.N
+
+
+def test_frank3_point_derivatives(oracle_mod):
+    """d Delta f / dn and d Delta f / d(d_b n_c) against central differences of Delta f."""
+    O = oracle_mod
+    p = O.OracleParams(nx=2, ny=2, nz=2, q0=0.4, **K3)
+    rng = np.random.default_rng(4)
+    for _ in range(5):
+        n3 = rng.normal(size=3)
+        G = 0.3 * rng.normal(size=(3, 3))
+        _, dfdn, P = O.frank3_point(p, n3, G)
+        d = 1e-6
+        for c in range(3):
+            e = np.zeros(3)
+            e[c] = d
+            num = (O.frank3_point(p, n3 + e, G)[0] - O.frank3_point(p, n3 - e, G)[0]) / (2 * d)
+            assert abs(num - dfdn[c]) < 1e-9
+        for b in range(3):
+            for c in range(3):
+                E = np.zeros((3, 3))
+                E[b, c] = d
+                num = (O.frank3_point(p, n3, G + E)[0] - O.frank3_point(p, n3, G - E)[0]) / (2 * d)
+                assert abs(num - P[b, c]) < 1e-9
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_frank3_field_is_energy_gradient(oracle_mod, walls):
+    """Full h (one-constant part + correction) = -dE_d/dn, periodic and with
+    homeotropic plates."""
+    O = oracle_mod
+    p = O.OracleParams(nx=4, ny=3, nz=4, walls_z=walls, anchoring="homeotropic", q0=0.9, W0=0.3,
+                       K=0.7, K11=1.1, K22=0.4, K33=1.6)
+    n = I.random_director(4, 3, 4, seed=5)
+    h = O.molecular_field(p, n)
+    g = _grad_energy(O, p, n)
+    assert np.max(np.abs(g + h)) < 1e-7 * np.max(np.abs(h))
+
+
+@pytest.mark.parametrize("anchoring", ["none", "homeotropic"])
+def test_frank3_correction_field_with_plates(oracle_mod, anchoring):
+    """The correction's field is -d(sum Delta f)/dn also when the ghost layer
+    copies the adjacent fluid layer (no anchoring): the copy's dependence on
+    that layer is part of the derivative."""
+    O = oracle_mod
+    p = O.OracleParams(nx=4, ny=3, nz=4, walls_z=True, anchoring=anchoring, q0=0.9, K=0.7, K11=1.1, K22=0.4,
+                       K33=1.6)
+    n = I.random_director(4, 3, 4, seed=6)
+    _, hd = O.frank3_field(p, n)
+    d = 1e-6
+    g = np.zeros_like(hd)
+    for a in range(3):
+        for s_ in range(p.N):
+            npl = n.copy()
+            npl[a, s_] += d
+            nm = n.copy()
+            nm[a, s_] -= d
+            g[a, s_] = (O.frank3_field(p, npl)[0] - O.frank3_field(p, nm)[0]) / (2 * d)
+    assert np.max(np.abs(g + hd)) < 1e-7 * np.max(np.abs(hd))
+
+
+def test_frank3_equal_constants_reduce_to_one_constant(oracle_mod):
+    O = oracle_mod
+    d = dict(nx=6, ny=5, nz=4, walls_z=True, K=0.02, q0=0.5, W0=0.01, tau=0.8, g=(1e-5, 0, 0), **LESLIE)
+    n0 = I.skyrmion_tubes(6, 5, 4, [(3.0, 2.5)], 2.0)
+    a = O.OracleSim(O.OracleParams(**d), n0).step(5)
+    b = O.OracleSim(O.OracleParams(K11=0.02, K22=0.02, K33=0.02, **d), n0).step(5)
+    assert np.array_equal(a.n, b.n) and np.array_equal(a.f, b.f)
+
+
+@pytest.mark.parametrize("axis,Kii", [(0, "K11"), (1, "K22"), (2, "K33")])
+def test_frank3_splay_twist_bend_decay(oracle_mod, axis, Kii):
+    """A small tilt dn_x = eps sin(k r_axis) of n = z_hat is a pure splay (along
+    x), twist (along y) or bend (along z) mode.  It decays at the discrete rate
+    lambda = [2 K (1 - cos k) + (K_ii - K) sin^2 k] / gamma1 (compact one-constant
+    part plus the central-difference correction), i.e. by the Heun factor per step."""
+    O = oracle_mod
+    L, g1, dt, eps, m = 8, 1.0, 5, 1e-6, 20
+    dims = [2, 2, 2]
+    dims[axis] = L
+    p = O.OracleParams(nx=dims[0], ny=dims[1], nz=dims[2], walls_z=False, gamma1=g1, dt_fd=dt, **K3)
+    k = 2 * math.pi / L
+    z, y, x = np.meshgrid(np.arange(dims[2]), np.arange(dims[1]), np.arange(dims[0]), indexing="ij")
+    r = (x, y, z)[axis]
+    n = np.zeros((3,) + x.shape)
+    n[0] = eps * np.sin(k * r)
+    n[2] = 1.0
+    n = (n / np.linalg.norm(n, axis=0)).reshape(3, -1)
+    u = np.zeros((3, p.N))
+    for _ in range(m):
+        n = O.fd_step(p, n, u)
+    lam = (2 * p.K * (1 - math.cos(k)) + (getattr(p, Kii) - p.K) * math.sin(k) ** 2) / g1
+    heun = eps * (1 - lam * dt + 0.5 * (lam * dt) ** 2) ** m
+    rr = r.reshape(-1)
+    amp = np.sum(n[0] * np.sin(k * rr)) * 2 / rr.size
+    assert abs(amp / heun - 1) < 1e-6
