@@ -83,7 +83,11 @@ typedef struct nh_params {
                              u carries half of the old one (an extra LB launch per FD interval).
                              0 (default): the collision of that step keeps the old force and the new
                              force acts from the next step.  Not supported by nh_batch_step. */
-    int32_t reserved;     /* must be 0 */
+    int32_t frank3;       /* 1: three-constant Frank energy (Eq. free-energy-eq with K11, K22, K33): the
+                             one-constant lattice energy with K plus, per fluid site,
+                             (K11-K)/2 (div n)^2 + (K22-K)/2 (n.curl n + q0)^2 + (K33-K)/2 |n x curl n|^2
+                             with central differences; h is its exact variational derivative.  Runs on the
+                             per-site FD kernels (nh_set_fd_variant 0); not supported by the batched calls. */
     double tau;           /* SRT relaxation time, > 1/2; nu = (tau - 1/2)/3 */
     double g[3];          /* body acceleration g of Eq. NS-eq; the LB force is F_lc + rho g */
     double K;             /* one-constant Frank elasticity */
@@ -92,6 +96,7 @@ typedef struct nh_params {
     double gamma2;        /* torsion coefficient alpha3 + alpha2 */
     double alpha1, alpha2, alpha3, alpha4p, alpha5, alpha6; /* Leslie viscosities; alpha4p = alpha_4' */
     double W0;            /* bulk effective anchoring: h += W0 n_z z_hat */
+    double K11, K22, K33; /* splay, twist, bend constants, used when frank3 = 1 (each > 0) */
 } nh_params;
 
 /* Result of nh_diagnostics.  Reductions are accumulated in FP64. */

@@ -19,8 +19,8 @@
 using namespace nh;
 
 // The parameter block is passed by pointer from C and from Python's ctypes:
-// 12 int32 fields then 15 doubles, without padding.
-static_assert(sizeof(nh_params) == 12 * 4 + 15 * 8, "nh_params layout");
+// 12 int32 fields then 18 doubles, without padding.
+static_assert(sizeof(nh_params) == 12 * 4 + 18 * 8, "nh_params layout");
 static_assert(offsetof(nh_params, tau) == 48, "nh_params layout");
 
 namespace {
@@ -41,7 +41,7 @@ size_t store_size(const nh_params& p)
 }
 
 struct Layout {
-    size_t f[2], F, Fprev, n, nP, ndot, u, rho, sigma, snap, staging, partials, result, scales, absmax, trig, total;
+    size_t f[2], F, Fprev, n, nP, ndot, u, rho, sigma, P3, snap, staging, partials, result, scales, absmax, trig, total;
 };
 
 Layout make_layout(const nh_params& p)
@@ -65,6 +65,7 @@ Layout make_layout(const nh_params& p)
     L.u = take(3 * N * R);
     L.rho = take(N * R);
     L.sigma = take(9 * N * R);
+    L.P3 = take(p.frank3 ? 9 * N * R : 0);  // d df/d(grad n) of the three-constant correction
     L.snap = take(3 * N * R);
     L.staging = take(7 * N * sizeof(double));
     L.partials = take((size_t)diag_blocks() * diag_num_values(NH_MAX_TUBES) * sizeof(double));
@@ -137,8 +138,13 @@ int validate(const nh_params* p, std::string& err)
         err = "paper_order must be 0 or 1";
         return NH_EINVAL;
     }
-    if (p->reserved != 0) {
-        err = "reserved must be 0";
+    if (p->frank3 != 0 && p->frank3 != 1) {
+        err = "frank3 must be 0 or 1";
+        return NH_EINVAL;
+    }
+    if (p->frank3 && !(p->K11 > 0 && p->K22 > 0 && p->K33 > 0 && isfinite(p->K11) && isfinite(p->K22) &&
+                       isfinite(p->K33))) {
+        err = "frank3 needs finite K11, K22, K33 > 0";
         return NH_EINVAL;
     }
     const double vals[] = {p->g[0], p->g[1], p->g[2], p->K, p->q0, p->gamma2, p->alpha1, p->alpha2,
@@ -297,6 +303,7 @@ FDChan<Real> fd_chan(nh_ctx* c)
     a.u = c->at<const Real>(c->L.u);
     a.sigma = c->at<Real>(c->L.sigma);
     a.F = c->at<Real>(c->L.F);
+    a.P3 = c->p.frank3 ? c->at<Real>(c->L.P3) : nullptr;
     a.g = Geom{c->p.nx, c->p.ny, c->p.nz, c->p.walls_z, c->p.anchoring, c->N};
     const nh_params& p = c->p;
     a.p.K = Real(p.K);
@@ -312,6 +319,9 @@ FDChan<Real> fd_chan(nh_ctx* c)
     a.p.a5 = Real(p.alpha5);
     a.p.a6 = Real(p.alpha6);
     a.p.dt = Real(p.dt_fd);
+    a.p.kd1 = Real(p.frank3 ? p.K11 - p.K : 0.0);
+    a.p.kd2 = Real(p.frank3 ? p.K22 - p.K : 0.0);
+    a.p.kd3 = Real(p.frank3 ? p.K33 - p.K : 0.0);
     return a;
 }
 
@@ -374,6 +384,21 @@ int enqueue_lb(nh_ctx* c, int src, bool write_macro, cudaStream_t st, bool stale
     }
 }
 
+// Per-site predictor and corrector; with the three-constant energy each is
+// preceded by the P stage of the field it differentiates.
+template <typename Real>
+int enqueue_predict_correct_sites(nh_ctx* c, const FDChan<Real>& a, cudaStream_t st)
+{
+    int r = NH_OK;
+    if (a.P3) r = timed(c, NH_KCLASS_FD_PREDICT, st, [&] { return launch_frank3_p(a, false, st); }, "frank3_p");
+    if (r) return r;
+    r = timed(c, NH_KCLASS_FD_PREDICT, st, [&] { return launch_fd_predict(a, st); }, "fd_predict");
+    if (r) return r;
+    if (a.P3) r = timed(c, NH_KCLASS_FD_CORRECT, st, [&] { return launch_frank3_p(a, true, st); }, "frank3_p");
+    if (r) return r;
+    return timed(c, NH_KCLASS_FD_CORRECT, st, [&] { return launch_fd_correct(a, st); }, "fd_correct");
+}
+
 template <typename Real>
 int enqueue_force_only(nh_ctx* c, cudaStream_t st)
 {
@@ -381,7 +406,10 @@ int enqueue_force_only(nh_ctx* c, cudaStream_t st)
     if (c->fd_fused)
         return timed(c, NH_KCLASS_STRESS, st, [&] { return launch_fd_fused_b<Real>(a, a.n, nullptr, st); },
                      "stress_force");
-    int r = timed(c, NH_KCLASS_STRESS, st, [&] { return launch_stress(a, st); }, "stress");
+    int r = NH_OK;
+    if (a.P3) r = timed(c, NH_KCLASS_STRESS, st, [&] { return launch_frank3_p(a, false, st); }, "frank3_p");
+    if (r) return r;
+    r = timed(c, NH_KCLASS_STRESS, st, [&] { return launch_stress(a, st); }, "stress");
     if (r) return r;
     return timed(c, NH_KCLASS_FORCE, st, [&] { return launch_force(a, st); }, "force");
 }
@@ -398,9 +426,7 @@ int enqueue_fd(nh_ctx* c, cudaStream_t st)
         return timed(c, NH_KCLASS_STRESS, st, [&] { return launch_fd_fused_b<Real>(a, a.nP, a.n, st); },
                      "stress_force");
     }
-    int r = timed(c, NH_KCLASS_FD_PREDICT, st, [&] { return launch_fd_predict(a, st); }, "fd_predict");
-    if (r) return r;
-    r = timed(c, NH_KCLASS_FD_CORRECT, st, [&] { return launch_fd_correct(a, st); }, "fd_correct");
+    int r = enqueue_predict_correct_sites<Real>(c, a, st);
     if (r) return r;
     return enqueue_force_only<Real>(c, st);
 }
@@ -417,9 +443,7 @@ int enqueue_predict_correct(nh_ctx* c, cudaStream_t st)
                    ? NH_OK
                    : fail(c, NH_ECUDA, "copy of the relaxed director");
     }
-    int r = timed(c, NH_KCLASS_FD_PREDICT, st, [&] { return launch_fd_predict(a, st); }, "fd_predict");
-    if (r) return r;
-    return timed(c, NH_KCLASS_FD_CORRECT, st, [&] { return launch_fd_correct(a, st); }, "fd_correct");
+    return enqueue_predict_correct_sites<Real>(c, a, st);
 }
 
 // Relaxation with the fused kernel, alternating n -> nP -> n; an odd count
@@ -608,6 +632,10 @@ int enqueue_diag(nh_ctx* c, cudaStream_t st)
     a.K = c->p.K;
     a.q0 = c->p.q0;
     a.W0 = c->p.W0;
+    a.frank3 = c->p.frank3;
+    a.kd1 = c->p.frank3 ? c->p.K11 - c->p.K : 0.0;
+    a.kd2 = c->p.frank3 ? c->p.K22 - c->p.K : 0.0;
+    a.kd3 = c->p.frank3 ? c->p.K33 - c->p.K : 0.0;
     a.n_tubes = c->n_tubes;
     memcpy(a.tubes, c->tubes, sizeof(a.tubes));
     a.trig = c->at<const double>(c->L.trig);
@@ -673,8 +701,9 @@ int batch_prepare(nh_ctx* const* ctxs, int count, int64_t n_lb_steps, BatchPlan*
         if (c->p.precision != c0->p.precision || c->p.storage != c0->p.storage || c->p.shifted != c0->p.shifted ||
             c->p.dt_fd != c0->p.dt_fd)
             return fail(nullptr, NH_EINVAL, "channels must share precision, storage, shifted and dt_fd");
-        if (c->p.paper_order)
-            return fail(nullptr, NH_EINVAL, "channel " + std::to_string(k) + ": paper_order is not supported in batches");
+        if (c->p.paper_order || c->p.frank3)
+            return fail(nullptr, NH_EINVAL,
+                        "channel " + std::to_string(k) + ": paper_order and frank3 are not supported in batches");
         if (c->device != c0->device) return fail(nullptr, NH_EINVAL, "channels must be on one device");
         if (c->cur != c0->cur || c->step % c0->p.dt_fd != c0->step % c0->p.dt_fd)
             return fail(nullptr, NH_EINVAL, "channels must be at the same step phase (step mod dt_fd, buffer parity)");
@@ -721,6 +750,8 @@ int batch_prepare_relax(nh_ctx* const* ctxs, int count, int64_t n_fd_steps, Batc
         if (!c->bound || !c->fields_set)
             return fail(nullptr, NH_EINVAL, "channel " + std::to_string(k) + ": workspace or fields not set");
         if (c->p.precision != c0->p.precision) return fail(nullptr, NH_EINVAL, "channels must share the precision");
+        if (c->p.frank3)
+            return fail(nullptr, NH_EINVAL, "channel " + std::to_string(k) + ": frank3 is not supported in batches");
         if (c->device != c0->device) return fail(nullptr, NH_EINVAL, "channels must be on one device");
         for (int j = 0; j < k; ++j)
             if (ctxs[j] == c) return fail(nullptr, NH_EINVAL, "a context appears twice in the batch");
@@ -900,6 +931,7 @@ int nh_create(const nh_params* p, void* cuda_stream, nh_ctx** out)
     c->p = *p;
     c->N = p->nx * p->ny * p->nz;
     c->lb_variant = lb_variant_valid(0, p->nx) ? 0 : 1;
+    if (p->frank3) c->fd_fused = 0;  // the three-constant correction runs on the per-site FD kernels
     c->L = make_layout(*p);
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = cudaGetDevice(&c->device);
@@ -1437,6 +1469,7 @@ int nh_set_fd_variant(nh_ctx* c, int fused)
 {
     if (!c) return fail(nullptr, NH_EINVAL, "ctx is NULL");
     if (fused != 0 && fused != 1) return fail(c, NH_EINVAL, "FD variant must be 0 or 1");
+    if (fused && c->p.frank3) return fail(c, NH_EINVAL, "the three-constant energy runs on the per-site FD kernels only");
     if (fused != c->fd_fused) drop_graphs(c);
     c->fd_fused = fused;
     return NH_OK;

@@ -174,8 +174,8 @@ __device__ __forceinline__ void load3(const Real* __restrict__ n, int N, int s, 
     out[2] = __ldg(n + 2 * N + s);
 }
 
-template <typename Real, typename Store>
-__global__ void __launch_bounds__(DIAG_THREADS, sizeof(Real) == 4 ? 5 : 1) diag_kernel(const DiagArgs a)
+template <typename Real, typename Store, bool F3>
+__global__ void __launch_bounds__(DIAG_THREADS, (sizeof(Real) == 4 && !F3) ? 5 : 1) diag_kernel(const DiagArgs a)
 {
     const Geom g = a.g;
     const int N = g.N;
@@ -218,9 +218,23 @@ __global__ void __launch_bounds__(DIAG_THREADS, sizeof(Real) == 4 ? 5 : 1) diag_
             y = col / g.nx;
             const int colx = (x + 1 == g.nx ? 0 : x + 1) + g.nx * y;
             const int coly = x + g.nx * (y + 1 == g.ny ? 0 : y + 1);
+            const int colxm = (x == 0 ? g.nx - 1 : x - 1) + g.nx * y;
+            const int colym = x + g.nx * (y == 0 ? g.ny - 1 : y - 1);
             Real msum = 0, esum = 0;
             Real c[3];
             load3(n, N, col + cols * z0, c);
+            Real cl[3] = {c[0], c[1], c[2]};  // director one layer below (three-constant gradient)
+            if (F3) {
+                if (z0 > 0) {
+                    load3(n, N, col + cols * (z0 - 1), cl);
+                } else if (!g.walls) {
+                    load3(n, N, col + cols * (g.nz - 1), cl);
+                } else if (homeo) {
+                    cl[0] = Real(0);
+                    cl[1] = Real(0);
+                    cl[2] = Real(1);
+                }
+            }
             if (g.walls && z0 == 0) {
                 // link from the lower ghost layer to the first fluid layer
                 Real m[3] = {c[0], c[1], c[2]};
@@ -261,6 +275,20 @@ __global__ void __launch_bounds__(DIAG_THREADS, sizeof(Real) == 4 ? 5 : 1) diag_
                 e += link_energy(c, my, 1, K, q0);
                 e += link_energy(c, cn, 2, K, q0);
                 esum += e + site_const - Real(0.5) * W0 * c[2] * c[2];
+                if (F3) {
+                    // three-constant correction with the central gradient
+                    Real mxm[3], mym[3];
+                    load3(n, N, colxm + cols * z, mxm);
+                    load3(n, N, colym + cols * z, mym);
+                    Real G[3][3], dfdn[3], P[3][3];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        G[0][k] = Real(0.5) * (mx[k] - mxm[k]);
+                        G[1][k] = Real(0.5) * (my[k] - mym[k]);
+                        G[2][k] = Real(0.5) * (cn[k] - cl[k]);
+                    }
+                    esum += frank3_site(c, G, Real(a.kd1), Real(a.kd2), Real(a.kd3), q0, dfdn, P);
+                }
                 const Real umag = sqrt(u0 * u0 + u1 * u1 + u2 * u2);
                 const Real nmag = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
                 max_u = max(max_u, umag);
@@ -268,6 +296,11 @@ __global__ void __launch_bounds__(DIAG_THREADS, sizeof(Real) == 4 ? 5 : 1) diag_
                 max_nn = max(max_nn, nmag);
                 if (!isfinite(umag) || !isfinite(nmag) || !isfinite(r) || !isfinite(fs)) bad += 1;
                 wsum += Real(0.5) * (Real(1) - c[2]);
+                if (F3) {
+                    cl[0] = c[0];
+                    cl[1] = c[1];
+                    cl[2] = c[2];
+                }
                 c[0] = cn[0];
                 c[1] = cn[1];
                 c[2] = cn[2];
@@ -582,12 +615,21 @@ cudaError_t launch_diagnostics(const DiagArgs& a, cudaStream_t st)
     int blocks = (items + DIAG_THREADS - 1) / DIAG_THREADS;
     if (blocks > a.blocks) blocks = a.blocks;
     if (a.precision == NH_FP64) {
-        diag_kernel<double, double><<<blocks, DIAG_THREADS, 0, st>>>(a);
+        if (a.frank3)
+            diag_kernel<double, double, true><<<blocks, DIAG_THREADS, 0, st>>>(a);
+        else
+            diag_kernel<double, double, false><<<blocks, DIAG_THREADS, 0, st>>>(a);
+    } else if (a.frank3) {
+        switch (a.storage) {
+        case NH_STORE_F32: diag_kernel<float, float, true><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
+        case NH_STORE_F16S: diag_kernel<float, __half, true><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
+        default: diag_kernel<float, __nv_bfloat16, true><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
+        }
     } else {
         switch (a.storage) {
-        case NH_STORE_F32: diag_kernel<float, float><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
-        case NH_STORE_F16S: diag_kernel<float, __half><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
-        default: diag_kernel<float, __nv_bfloat16><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
+        case NH_STORE_F32: diag_kernel<float, float, false><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
+        case NH_STORE_F16S: diag_kernel<float, __half, false><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
+        default: diag_kernel<float, __nv_bfloat16, false><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
         }
     }
     cudaError_t e = cudaGetLastError();

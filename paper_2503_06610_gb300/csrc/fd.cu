@@ -1,5 +1,6 @@
 // fd.cu -- finite-difference director update and LC stress / force
-// (arXiv:2503.06610, Secs. II.A-II.B, Eq. director-time-eq, Eq. force-lc-eq).
+// (arXiv:2503.06610, Secs. II.A-II.B, Eq. director-time-eq, Eq. force-lc-eq,
+// Eq. free-energy-eq).
 //
 // Kernels (one thread per site, radius-1 stencils, central differences):
 //   fd_predict : (dn/dt)_old from n and u;  n^P = n + dt_FD (dn/dt)_old
@@ -116,10 +117,14 @@ __device__ __forceinline__ void local_fields(const Real nn[7][3], const Real uu[
 // Eq. director-time-eq: dn_m/dt = h_m/g1 - (g2/g1) n_a D_am - u_g d_g n_m + W_mg n_g.
 template <typename Real>
 __device__ __forceinline__ void director_rate(const Real nn[7][3], const Real uu[7][3], const FDPar<Real>& p,
-                                              Real rate[3])
+                                              Real rate[3], const Real* hx = nullptr)
 {
     Real dn[3][3], du[3][3], h[3];
     local_fields(nn, uu, p, dn, du, h);
+    if (hx != nullptr) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) h[a] += hx[a];
+    }
     const Real* n = nn[0];
     const Real* u = uu[0];
 #pragma unroll
@@ -136,6 +141,79 @@ __device__ __forceinline__ void director_rate(const Real nn[7][3], const Real uu
     }
 }
 
+// ---- three-constant correction (per-site path)
+//
+// Stage P: P[b][c] = d df/d(d_b n_c) of the correction at every site, from the
+// central gradient of the field m (n or n^P).  The field of the correction at
+// site y is the exact -d(sum df)/dn_c(y):
+//   hx_c(y) = -d df/d n_c(y) + 1/2 sum_b [P_bc(y + e_b) - P_bc(y - e_b)]
+// with P = 0 at ghost sites; without anchoring the ghost layer copies the
+// adjacent fluid layer, which adds +P_zc(y)/2 on the lowest and -P_zc(y)/2 on
+// the highest layer.
+template <typename Real>
+__device__ __forceinline__ void frank3_p_site(const FDChan<Real>& c, const Real* m, int s)
+{
+    int x, y, z;
+    site_xyz<Real>(c.g, s, x, y, z);
+    Real nn[7][3];
+    gather7(m, c.g, x, y, z, nn, true);
+    Real G[3][3], dfdn[3], P[3][3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) G[b][k] = Real(0.5) * (nn[1 + 2 * b][k] - nn[2 + 2 * b][k]);
+    frank3_site(nn[0], G, c.p.kd1, c.p.kd2, c.p.kd3, c.p.q0, dfdn, P);
+    const int N = c.g.N;
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) c.P3[(3 * b + k) * N + s] = P[b][k];
+}
+
+template <typename Real>
+__device__ __forceinline__ void frank3_field_site(const FDChan<Real>& c, const Real nn[7][3], int x, int y, int z,
+                                                  Real hx[3])
+{
+    const Geom& g = c.g;
+    const int N = g.N;
+    Real G[3][3], dfdn[3], P[3][3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) G[b][k] = Real(0.5) * (nn[1 + 2 * b][k] - nn[2 + 2 * b][k]);
+    frank3_site(nn[0], G, c.p.kd1, c.p.kd2, c.p.kd3, c.p.q0, dfdn, P);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) hx[k] = -dfdn[k];
+    const int xp = wrap_p(x + 1, g.nx), xm = wrap_p(x - 1, g.nx);
+    const int yp = wrap_p(y + 1, g.ny), ym = wrap_p(y - 1, g.ny);
+    const int row = g.nx * (y + g.ny * z);
+    const int sxp = xp + row, sxm = xm + row;
+    const int syp = x + g.nx * (yp + g.ny * z), sym = x + g.nx * (ym + g.ny * z);
+    int zp = z + 1, zm = z - 1;
+    bool zp_ok = true, zm_ok = true;
+    if (g.walls) {
+        zp_ok = zp < g.nz;
+        zm_ok = zm >= 0;
+    } else {
+        zp = wrap_p(zp, g.nz);
+        zm = wrap_p(zm, g.nz);
+    }
+    const int szp = x + g.nx * (y + g.ny * (zp_ok ? zp : 0)), szm = x + g.nx * (y + g.ny * (zm_ok ? zm : 0));
+    const Real* P3 = c.P3;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        Real acc = P3[(0 + k) * N + sxp] - P3[(0 + k) * N + sxm];
+        acc += P3[(3 + k) * N + syp] - P3[(3 + k) * N + sym];
+        if (zp_ok) acc += P3[(6 + k) * N + szp];
+        if (zm_ok) acc -= P3[(6 + k) * N + szm];
+        if (g.walls && g.anchoring != NH_ANCHOR_HOMEOTROPIC) {
+            if (z == 0) acc += P[2][k];
+            if (z == g.nz - 1) acc -= P[2][k];
+        }
+        hx[k] += Real(0.5) * acc;
+    }
+}
+
 template <typename Real>
 __device__ __forceinline__ void fd_predict_site(const FDChan<Real>& c, int s)
 {
@@ -144,7 +222,13 @@ __device__ __forceinline__ void fd_predict_site(const FDChan<Real>& c, int s)
     Real nn[7][3], uu[7][3], r[3];
     gather7(c.n, c.g, x, y, z, nn, true);
     gather7(c.u, c.g, x, y, z, uu, false);
-    director_rate(nn, uu, c.p, r);
+    if (c.P3 != nullptr) {
+        Real hx[3];
+        frank3_field_site(c, nn, x, y, z, hx);
+        director_rate(nn, uu, c.p, r, hx);
+    } else {
+        director_rate(nn, uu, c.p, r);
+    }
     const int N = c.g.N;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -161,7 +245,13 @@ __device__ __forceinline__ void fd_correct_site(const FDChan<Real>& c, int s)
     Real nn[7][3], uu[7][3], r[3];
     gather7(c.nP, c.g, x, y, z, nn, true);
     gather7(c.u, c.g, x, y, z, uu, false);
-    director_rate(nn, uu, c.p, r);
+    if (c.P3 != nullptr) {
+        Real hx[3];
+        frank3_field_site(c, nn, x, y, z, hx);
+        director_rate(nn, uu, c.p, r, hx);
+    } else {
+        director_rate(nn, uu, c.p, r);
+    }
     const int N = c.g.N;
     Real nw[3];
 #pragma unroll
@@ -175,10 +265,14 @@ __device__ __forceinline__ void fd_correct_site(const FDChan<Real>& c, int s)
 // neighbourhood of n and u: sigma[3a+b].
 template <typename Real>
 __device__ __forceinline__ void stress_point(const Real nn[7][3], const Real uu[7][3], const FDPar<Real>& p,
-                                             Real sig[9])
+                                             Real sig[9], const Real* hx = nullptr, const Real* Pd = nullptr)
 {
     Real dn[3][3], du[3][3], h[3];
     local_fields(nn, uu, p, dn, du, h);
+    if (hx != nullptr) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) h[a] += hx[a];
+    }
     const Real* n = nn[0];
     Real D[3][3];
 #pragma unroll
@@ -204,7 +298,11 @@ __device__ __forceinline__ void stress_point(const Real nn[7][3], const Real uu[
                       p.a5 * n[b] * Dn[a] + p.a6 * n[a] * Dn[b];
             Real se = 0;
 #pragma unroll
-            for (int gg = 0; gg < 3; ++gg) se -= dn[a][gg] * (p.K * dn[b][gg] + p.K * p.q0 * chi[b][gg]);
+            for (int gg = 0; gg < 3; ++gg) {
+                Real dfdG = p.K * dn[b][gg] + p.K * p.q0 * chi[b][gg];
+                if (Pd != nullptr) dfdG += Pd[3 * b + gg];  // three-constant correction
+                se -= dn[a][gg] * dfdG;
+            }
             sig[3 * a + b] = sv + se;
         }
 }
@@ -217,7 +315,15 @@ __device__ __forceinline__ void stress_site(const FDChan<Real>& c, int s)
     Real nn[7][3], uu[7][3], sig[9];
     gather7(c.n, c.g, x, y, z, nn, true);
     gather7(c.u, c.g, x, y, z, uu, false);
-    stress_point(nn, uu, c.p, sig);
+    if (c.P3 != nullptr) {
+        Real hx[3], Pd[9];
+        frank3_field_site(c, nn, x, y, z, hx);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Pd[k] = c.P3[k * c.g.N + s];
+        stress_point(nn, uu, c.p, sig, hx, Pd);
+    } else {
+        stress_point(nn, uu, c.p, sig);
+    }
     const int N = c.g.N;
 #pragma unroll
     for (int k = 0; k < 9; ++k) c.sigma[k * N + s] = sig[k];
@@ -263,8 +369,12 @@ __device__ __forceinline__ void fd_stage_site(const FDChan<Real>& c, int s)
         fd_correct_site(c, s);
     else if (Stage == 2)
         stress_site(c, s);
-    else
+    else if (Stage == 3)
         force_site(c, s);
+    else if (Stage == 4)
+        frank3_p_site(c, c.n, s);
+    else
+        frank3_p_site(c, c.nP, s);
 }
 
 template <typename Real, int Stage>
@@ -692,6 +802,16 @@ cudaError_t launch_force(const FDChan<Real>& c, cudaStream_t st)
     fd_kernel<Real, 3><<<blocks_for(c.g.N), 256, 0, st>>>(c);
     return cudaGetLastError();
 }
+template <typename Real>
+cudaError_t launch_frank3_p(const FDChan<Real>& c, bool from_predictor, cudaStream_t st)
+{
+    if (c.P3 == nullptr) return cudaErrorInvalidValue;
+    if (from_predictor)
+        fd_kernel<Real, 5><<<blocks_for(c.g.N), 256, 0, st>>>(c);
+    else
+        fd_kernel<Real, 4><<<blocks_for(c.g.N), 256, 0, st>>>(c);
+    return cudaGetLastError();
+}
 
 template <typename Real>
 cudaError_t launch_fd_fused_a(const FDChan<Real>& c, const Real* nin, Real* nout, cudaStream_t st)
@@ -744,5 +864,7 @@ template cudaError_t launch_stress<double>(const FDChan<double>&, cudaStream_t);
 template cudaError_t launch_stress<float>(const FDChan<float>&, cudaStream_t);
 template cudaError_t launch_force<double>(const FDChan<double>&, cudaStream_t);
 template cudaError_t launch_force<float>(const FDChan<float>&, cudaStream_t);
+template cudaError_t launch_frank3_p<double>(const FDChan<double>&, bool, cudaStream_t);
+template cudaError_t launch_frank3_p<float>(const FDChan<float>&, bool, cudaStream_t);
 
 }  // namespace nh

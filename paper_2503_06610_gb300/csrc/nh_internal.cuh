@@ -108,7 +108,43 @@ struct FDPar {
     Real inv_gamma1, gamma2, g2_over_g1;
     Real a1, a2, a3, a4p, a5, a6;
     Real dt;
+    Real kd1, kd2, kd3;  // K11 - K, K22 - K, K33 - K (three-constant energy)
 };
+
+// Three-constant correction of the Frank energy density at one site
+// (Eq. free-energy-eq minus its one-constant form with K), from the director
+// n and its central gradient G[b][c] = d_b n_c:
+//   div = G_aa, w = curl n (w_a = eps_abc G_bc), t = n.w + q0,
+//   df = kd1/2 div^2 + kd2/2 t^2 + kd3/2 (|n|^2 |w|^2 - (n.w)^2).
+// Writes dfdn[c] = d df/d n_c and P[b][c] = d df/d G_bc; returns df.
+template <typename Real>
+__host__ __device__ __forceinline__ Real frank3_site(const Real n[3], const Real G[3][3], Real kd1, Real kd2, Real kd3,
+                                                    Real q0, Real dfdn[3], Real P[3][3])
+{
+    const Real div = G[0][0] + G[1][1] + G[2][2];
+    const Real w[3] = {G[1][2] - G[2][1], G[2][0] - G[0][2], G[0][1] - G[1][0]};
+    const Real nw = n[0] * w[0] + n[1] * w[1] + n[2] * w[2];
+    const Real nn = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+    const Real ww = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    const Real t = nw + q0;
+    Real V[3];  // d df / d w
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        dfdn[c] = kd2 * t * w[c] + kd3 * (n[c] * ww - nw * w[c]);
+        V[c] = kd2 * t * n[c] + kd3 * (nn * w[c] - nw * n[c]);
+    }
+    // P[b][c] = kd1 div delta_bc + eps_abc V_a
+    P[0][0] = kd1 * div;
+    P[1][1] = kd1 * div;
+    P[2][2] = kd1 * div;
+    P[1][2] = V[0];
+    P[2][1] = -V[0];
+    P[2][0] = V[1];
+    P[0][2] = -V[1];
+    P[0][1] = V[2];
+    P[1][0] = -V[2];
+    return Real(0.5) * kd1 * div * div + Real(0.5) * kd2 * t * t + Real(0.5) * kd3 * (nn * ww - nw * nw);
+}
 
 template <typename Real>
 struct FDChan {
@@ -118,6 +154,7 @@ struct FDChan {
     const Real* u;   // [3][N]
     Real* sigma;  // [9][N]
     Real* F;      // [3][N] F_lc
+    Real* P3;     // [9][N] d df/d(d_b n_c) of the three-constant correction, or null (one constant)
     Geom g;
     FDPar<Real> p;
 };
@@ -174,6 +211,9 @@ template <typename Real>
 cudaError_t launch_stress(const FDChan<Real>& c, cudaStream_t s);
 template <typename Real>
 cudaError_t launch_force(const FDChan<Real>& c, cudaStream_t s);
+// P = d df/d(d_b n_c) of the three-constant correction from n (or n^P) into c.P3
+template <typename Real>
+cudaError_t launch_frank3_p(const FDChan<Real>& c, bool from_predictor, cudaStream_t s);
 
 // Field conversion and initialisation (diag.cu)
 template <typename Real>
@@ -204,6 +244,8 @@ struct DiagArgs {
     const float* scale;
     Geom g;
     double K, q0, W0;
+    int frank3;         // add the three-constant correction to the energy
+    double kd1, kd2, kd3;
     int n_tubes;
     double tubes[NH_MAX_TUBES][2];
     const double* trig; // [sin x | cos x | sin y | cos y] of 2 pi x/nx, 2 pi y/ny

@@ -49,13 +49,14 @@ class nh_params(ctypes.Structure):
         ("walls_z", ctypes.c_int32), ("anchoring", ctypes.c_int32),
         ("precision", ctypes.c_int32), ("storage", ctypes.c_int32), ("shifted", ctypes.c_int32),
         ("dt_fd", ctypes.c_int32), ("check_stability", ctypes.c_int32),
-        ("paper_order", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("paper_order", ctypes.c_int32), ("frank3", ctypes.c_int32),
         ("tau", ctypes.c_double), ("g", ctypes.c_double * 3),
         ("K", ctypes.c_double), ("q0", ctypes.c_double),
         ("gamma1", ctypes.c_double), ("gamma2", ctypes.c_double),
         ("alpha1", ctypes.c_double), ("alpha2", ctypes.c_double), ("alpha3", ctypes.c_double),
         ("alpha4p", ctypes.c_double), ("alpha5", ctypes.c_double), ("alpha6", ctypes.c_double),
         ("W0", ctypes.c_double),
+        ("K11", ctypes.c_double), ("K22", ctypes.c_double), ("K33", ctypes.c_double),
     ]
 
 
@@ -171,6 +172,9 @@ def make_params(d: dict) -> nh_params:
     p.dt_fd = int(d.get("dt_fd", 1))
     p.check_stability = 1 if d.get("check_stability", False) else 0
     p.paper_order = 1 if d.get("paper_order", False) else 0
+    if d.get("K11") is not None and d.get("K22") is not None and d.get("K33") is not None:
+        p.frank3 = 1
+        p.K11, p.K22, p.K33 = float(d["K11"]), float(d["K22"]), float(d["K33"])
     p.tau = float(d.get("tau", 1.0))
     g = d.get("g", (0.0, 0.0, 0.0))
     p.g = (ctypes.c_double * 3)(*[float(v) for v in g])

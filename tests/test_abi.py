@@ -32,8 +32,8 @@ def test_library_exports_every_declared_symbol(nh):
 
 def test_params_struct_layout_matches_header(nh):
     import ctypes
-    # 12 int32 then 15 doubles, no padding
-    assert ctypes.sizeof(nh.nh_params) == 12 * 4 + 15 * 8
+    # 12 int32 then 18 doubles, no padding
+    assert ctypes.sizeof(nh.nh_params) == 12 * 4 + 18 * 8
     assert nh.nh_params.tau.offset == 48
 
 

@@ -593,3 +593,67 @@ def test_paper_order_graphs_bitwise_and_batch_rejected(nh):
     chans = [_channel(nh, params, n0, precision="fp32") for _ in range(2)]
     with pytest.raises(nh.NHError):
         nh.batch_step(chans, 4)
+
+
+# ------------------------------------------------------------------ three-constant Frank energy (Eq. free-energy-eq)
+
+FRANK3 = dict(K=0.03, K11=0.045, K22=0.015, K33=0.06)
+
+
+@pytest.mark.parametrize("grid", GRIDS)
+@pytest.mark.parametrize("anchoring,walls", [("homeotropic", True), ("none", True), ("homeotropic", False)])
+def test_frank3_fd_update_and_force_fp64(nh, oracle_mod, anchoring, walls, grid):
+    O = oracle_mod
+    params = _generic(*grid, walls_z=walls, anchoring=anchoring, W0=0.02, dt_fd=3, alpha1=0.1, alpha4p=0.2,
+                      **FRANK3)
+    n0 = I.random_director(*grid, seed=9)
+    u0 = I.random_velocity(*grid, 1e-2, seed=10)
+    p = O.OracleParams.from_dict(params)
+    assert p.frank3
+    F0 = O.force(p, O.stress(p, n0, u0))
+    nref = O.fd_step(p, n0, u0)
+    Fref = O.force(p, O.stress(p, nref, u0))
+    ch = nh.Channel(dict(params, precision="fp64"))
+    ch.set_fields(n0, u0)
+    assert O.rel_l2(ch.get_force(), F0) < 1e-12
+    ch.fd_update()
+    n, _, _ = ch.get_fields()
+    assert O.rel_l2(n, nref) < 1e-13
+    assert O.rel_l2(ch.get_force(), Fref) < 1e-12
+    # the correction matters: the one-constant update differs
+    p1 = O.OracleParams.from_dict({k: v for k, v in params.items() if k not in ("K11", "K22", "K33")})
+    assert O.rel_l2(O.fd_step(p1, n0, u0), nref) > 1e-6
+
+
+def test_frank3_channel_and_energy(nh, oracle_mod):
+    """Coupled run with a tube, FP64 to 1e-10 and FP32 to 1e-5, and the
+    diagnostics' three-constant energy against the oracle's."""
+    O = oracle_mod
+    params = _generic(24, 20, 10, dt_fd=2, K=0.02, K11=0.03, K22=0.01, K33=0.04, q0=2 * math.pi / 12,
+                      W0=0.002, walls_z=True, anchoring="none")
+    n0 = I.skyrmion_tubes(24, 20, 10, [(12.0, 10.0)], 5.0)
+    ref = _oracle_sim(O, params, n0).step(30)
+    for prec, tol in (("fp64", 1e-10), ("fp32", 1e-5)):
+        ch = _channel(nh, params, n0, precision=prec)
+        ch.set_tubes([(12.0, 10.0)])
+        ch.step(30)
+        n, u, _ = ch.get_fields()
+        assert O.rel_l2(n, ref.n) <= tol
+        assert O.rel_l2(u, ref.u) <= (tol if prec == "fp64" else 1e-4)
+        d = ch.diagnostics()
+        assert abs(d["energy"] - ref.energy()) <= (1e-11 if prec == "fp64" else 1e-5) * abs(ref.energy())
+
+
+def test_frank3_rejects_fused_and_batches(nh):
+    params = _generic(16, 12, 8, dt_fd=2, **FRANK3)
+    n0 = I.uniform_director(16, 12, 8)
+    ch = _channel(nh, params, n0, precision="fp32")
+    with pytest.raises(nh.NHError):
+        ch.set_fd_variant(1)
+    chans = [_channel(nh, params, n0, precision="fp32") for _ in range(2)]
+    with pytest.raises(nh.NHError):
+        nh.batch_step(chans, 2)
+    with pytest.raises(nh.NHError):
+        nh.batch_relax(chans, 2)
+    with pytest.raises(nh.NHError):
+        nh.Channel(dict(params, K22=0.0, precision="fp32"))
