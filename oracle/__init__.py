@@ -59,6 +59,7 @@ class _Params(ctypes.Structure):
         ("W0", ctypes.c_double), ("dt_fd", ctypes.c_double),
         ("K11", ctypes.c_double), ("K22", ctypes.c_double), ("K33", ctypes.c_double),
         ("frank3", ctypes.c_int),
+        ("solid", ctypes.c_void_p),
     ]
 
 
@@ -89,6 +90,16 @@ class OracleParams:
     K11: float = None  # three-constant Frank energy when K11, K22, K33 are all given
     K22: float = None
     K33: float = None
+    solid: object = None  # [N] uint8, 1 = solid node (obstacle); None: no obstacles
+
+    def __post_init__(self):
+        if self.solid is not None:
+            self.solid = np.ascontiguousarray(np.asarray(self.solid).reshape(-1), dtype=np.uint8)
+            assert self.solid.size == self.N
+
+    def fluid(self) -> np.ndarray:
+        """[N] bool, True at fluid sites."""
+        return np.ones(self.N, bool) if self.solid is None else self.solid == 0
 
     @property
     def frank3(self) -> bool:
@@ -112,6 +123,8 @@ class OracleParams:
         c.dt_fd = float(self.dt_fd)
         if self.frank3:
             c.K11, c.K22, c.K33, c.frank3 = self.K11, self.K22, self.K33, 1
+        if self.solid is not None:
+            c.solid = self.solid.ctypes.data  # the array lives as long as these params
         return c
 
     @classmethod
@@ -341,9 +354,10 @@ class OracleSim:
 # ------------------------------------------------------------------ diagnostics
 
 def mass(p: OracleParams, f) -> float:
-    """Total mass sum_x sum_i f_i (the shifted store adds rho0 = 1 per site)."""
-    total = float(np.sum(np.asarray(f, dtype=np.float64)))
-    return total + (p.N if p.shifted else 0.0)
+    """Total mass sum over fluid sites of sum_i f_i (the shifted store adds rho0 = 1 per site)."""
+    fl = p.fluid()
+    total = float(np.sum(np.asarray(f, dtype=np.float64).reshape(19, p.N)[:, fl]))
+    return total + (float(fl.sum()) if p.shifted else 0.0)
 
 
 def _ghosted(p: OracleParams, n) -> np.ndarray:
@@ -362,32 +376,39 @@ def frank_energy(p: OracleParams, n) -> float:
     """Lattice Frank energy (Eq. free-energy-eq; one-constant form with K, plus
     the three-constant correction when K11, K22, K33 are given).
 
-    E_d = sum over nearest-neighbour links (x, x+e_b) of
-            K/2 |n(x+e_b) - n(x)|^2 + K q0 eps_{a b c} n_a(x) n_c(x+e_b)
+    E_d = sum over nearest-neighbour links (x, x+e_b) with at least one fluid
+          end of  K/2 |n(x+e_b) - n(x)|^2 + K q0 eps_{a b c} n_a(x) n_c(x+e_b)
         + sum over fluid sites of  K q0^2 / 2 - (W0/2) n_z^2.
-    Links to the wall ghost layers are included.  In a periodic box the chiral
-    link sum equals sum_x n . curl_c n with the central curl, and -dE_d/dn is
-    the molecular field h used by the director equation.
+    Links to the wall ghost layers and to obstacle nodes (fixed directors) are
+    included.  In a periodic box the chiral link sum equals sum_x n . curl_c n
+    with the central curl, and -dE_d/dn is the molecular field h used by the
+    director equation.
     """
     K, q0 = p.K, p.q0
     ng = _ghosted(p, n)                         # (3, nz+2, ny, nx)
     core = ng[:, 1:-1]
+    solid = (~p.fluid()).reshape(p.nz, p.ny, p.nx)
+    sg = np.concatenate([np.ones((1, p.ny, p.nx), bool), solid, np.ones((1, p.ny, p.nx), bool)], axis=0)
     E = 0.0
     eps = np.zeros((3, 3, 3))
     eps[0, 1, 2] = eps[1, 2, 0] = eps[2, 0, 1] = 1.0
     eps[0, 2, 1] = eps[2, 1, 0] = eps[1, 0, 2] = -1.0
+
+    def links(lo, hi, keep, b):
+        e = 0.5 * K * np.sum((hi - lo) ** 2, axis=0) + K * q0 * np.einsum("ac,a...,c...->...", eps[:, b, :], lo, hi)
+        return float(np.sum(e[keep]))
     # x and y links (periodic)
     for b, axis in ((0, 3), (1, 2)):
         nb = np.roll(core, -1, axis=axis)
-        E += 0.5 * K * np.sum((nb - core) ** 2)
-        E += K * q0 * float(np.sum(np.einsum("ac,a...,c...->...", eps[:, b, :], core, nb)))
+        E += links(core, nb, ~(solid & np.roll(solid, -1, axis=axis - 1)), b)
     # z links: (z, z+1) for z = -1 .. nz-1 with walls, z = 0 .. nz-1 periodic
-    lo = ng[:, :-1] if p.walls_z else core
-    hi = ng[:, 1:] if p.walls_z else np.roll(core, -1, axis=1)
-    E += 0.5 * K * np.sum((hi - lo) ** 2)
-    E += K * q0 * float(np.sum(np.einsum("ac,a...,c...->...", eps[:, 2, :], lo, hi)))
+    if p.walls_z:
+        E += links(ng[:, :-1], ng[:, 1:], ~(sg[:-1] & sg[1:]), 2)
+    else:
+        E += links(core, np.roll(core, -1, axis=1), ~(solid & np.roll(solid, -1, axis=0)), 2)
+    fl = p.fluid()
     nz_ = np.asarray(n, dtype=np.float64).reshape(3, -1)[2]
-    E += p.N * 0.5 * K * q0 ** 2 - 0.5 * p.W0 * float(np.sum(nz_ ** 2))
+    E += float(fl.sum()) * 0.5 * K * q0 ** 2 - 0.5 * p.W0 * float(np.sum(nz_[fl] ** 2))
     if p.frank3:
         E += frank3_field(p, n)[0]
     return float(E)
@@ -423,7 +444,7 @@ def centroids(p: OracleParams, n, previous) -> np.ndarray:
     likewise y_bar.  ``previous`` is a (T, 2) array; returns a (T, 2) array in [0, L).
     """
     n = np.asarray(n, dtype=np.float64).reshape(3, p.nz, p.ny, p.nx)
-    w = 0.5 * (1.0 - n[2])
+    w = 0.5 * (1.0 - n[2]) * p.fluid().reshape(p.nz, p.ny, p.nx)  # fluid sites only
     z, y, x = np.meshgrid(np.arange(p.nz), np.arange(p.ny), np.arange(p.nx), indexing="ij")
     prev = np.asarray(previous, dtype=np.float64).reshape(-1, 2)
     d2 = []

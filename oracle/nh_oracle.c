@@ -35,6 +35,11 @@
  *     n = z_hat (infinite homeotropic anchoring) or n = adjacent fluid layer
  *     (no anchoring); stress = 0 at the ghosts;
  *   - the FD update renormalises n after the corrector only;
+ *   - obstacles (solid nodes): a link from a fluid site to a solid
+ *     one bounces back half-way like the plates; solid nodes keep their
+ *     director (infinite anchoring: the caller stores the surface normal
+ *     there), their velocity is zero and their stress is zero; their
+ *     populations are carried over unchanged;
  *   - three-constant energy (Eq. free-energy-eq with K11, K22, K33): the
  *     one-constant lattice energy with K plus, at every fluid site,
  *       Delta f = (K11-K)/2 (div n)^2 + (K22-K)/2 (n.curl n + q0)^2
@@ -64,6 +69,7 @@ typedef struct {
     double dt_fd;     /* FD time step, in LB time steps */
     double K11, K22, K33; /* three-constant Frank energy (used when frank3 = 1) */
     int frank3;       /* 1: add the three-constant correction Delta f (see frank3_point) */
+    const unsigned char* solid; /* [N] 1 = solid node (obstacle), or NULL: no obstacles */
 } or_params;
 
 /* D3Q19 velocity set (Sec. II.C): rest, 6 axis links, 12 face diagonals. */
@@ -99,6 +105,8 @@ static size_t site(const or_params* p, int x, int y, int z)
 {
     return (size_t)x + (size_t)p->nx * ((size_t)y + (size_t)p->ny * (size_t)z);
 }
+
+static int is_solid(const or_params* p, size_t s) { return p->solid != NULL && p->solid[s] != 0; }
 
 static double levi(int a, int b, int c)
 {
@@ -169,7 +177,14 @@ void or_lb_step(const or_params* p, const double* f, double* fnew, const double*
             for (int x = 0; x < p->nx; ++x) {
                 size_t s = site(p, x, y, z);
                 double fin[19];
-                /* streaming (pull) with half-way bounce-back */
+                if (is_solid(p, s)) {
+                    /* solid node: populations carried over, u = 0, rho = 1 */
+                    for (int i = 0; i < 19; ++i) fnew[(size_t)i * N + s] = f[(size_t)i * N + s];
+                    rho_out[s] = 1.0;
+                    for (int a = 0; a < 3; ++a) u_out[(size_t)a * N + s] = 0.0;
+                    continue;
+                }
+                /* streaming (pull) with half-way bounce-back at plates and obstacles */
                 for (int i = 0; i < 19; ++i) {
                     int zs = z - E[i][2];
                     if (p->walls_z && (zs < 0 || zs >= p->nz)) {
@@ -177,7 +192,8 @@ void or_lb_step(const or_params* p, const double* f, double* fnew, const double*
                     } else {
                         int xs = wrap(x - E[i][0], p->nx);
                         int ys = wrap(y - E[i][1], p->ny);
-                        fin[i] = f[(size_t)i * N + site(p, xs, ys, wrap(zs, p->nz))];
+                        size_t src = site(p, xs, ys, wrap(zs, p->nz));
+                        fin[i] = is_solid(p, src) ? f[(size_t)opposite(i) * N + s] : f[(size_t)i * N + src];
                     }
                 }
                 /* macroscopic quantities */
@@ -247,6 +263,10 @@ static void u_at(const or_params* p, const double* u, int x, int y, int z, doubl
         return;
     }
     size_t s = site(p, wrap(x, p->nx), wrap(y, p->ny), wrap(z, p->nz));
+    if (is_solid(p, s)) {
+        out[0] = out[1] = out[2] = 0.0;
+        return;
+    }
     for (int a = 0; a < 3; ++a) out[a] = u[(size_t)a * N + s];
 }
 
@@ -365,6 +385,7 @@ static double frank3_field(const or_params* p, const double* n, double* hd)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
                 size_t s = site(p, x, y, z);
+                if (is_solid(p, s)) continue; /* no energy at solid nodes */
                 double nc[3], G[3][3], dfdn[3], P[3][3];
                 n_at(p, n, x, y, z, nc);
                 central_gradient(p, n, x, y, z, G);
@@ -442,6 +463,10 @@ void or_director_rate(const or_params* p, const double* n, const double* u, doub
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
                 size_t s = site(p, x, y, z);
+                if (is_solid(p, s)) { /* fixed director */
+                    for (int m = 0; m < 3; ++m) ndot[(size_t)m * N + s] = 0.0;
+                    continue;
+                }
                 double nc[3], uc[3], dn[3][3], lap[3], du[3][3], h[3], D[3][3], W[3][3];
                 n_at(p, n, x, y, z, nc);
                 u_at(p, u, x, y, z, uc);
@@ -475,6 +500,7 @@ void or_fd_step(const or_params* p, double* n, const double* u, double* work)
     or_director_rate(p, nP, u, ndot_P);
     for (size_t k = 0; k < 3 * N; ++k) n[k] = n[k] + p->dt_fd * 0.5 * (ndot_old[k] + ndot_P[k]);
     for (size_t s = 0; s < N; ++s) {
+        if (is_solid(p, s)) continue;
         double len = sqrt(n[s] * n[s] + n[N + s] * n[N + s] + n[2 * N + s] * n[2 * N + s]);
         for (int a = 0; a < 3; ++a) n[(size_t)a * N + s] /= len;
     }
@@ -548,6 +574,10 @@ void or_stress(const or_params* p, const double* n, const double* u, double* sig
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
                 size_t s = site(p, x, y, z);
+                if (is_solid(p, s)) {
+                    for (int k = 0; k < 9; ++k) sigma[(size_t)k * N + s] = 0.0;
+                    continue;
+                }
                 double nc[3], dn[3][3], lap[3], du[3][3], h[3], D[3][3], W[3][3];
                 n_at(p, n, x, y, z, nc);
                 local_derivs(p, n, u, x, y, z, dn, lap, du);
@@ -586,6 +616,10 @@ void or_force(const or_params* p, const double* sigma, double* F)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
                 size_t s = site(p, x, y, z);
+                if (is_solid(p, s)) {
+                    for (int a = 0; a < 3; ++a) F[(size_t)a * N + s] = 0.0;
+                    continue;
+                }
                 for (int a = 0; a < 3; ++a) {
                     double div = 0.0;
                     for (int b = 0; b < 3; ++b) {
