@@ -238,6 +238,21 @@ int nh_director_change(nh_ctx* ctx, double* max_change);
  * centred.  Populations and F_lc are not updated.  Asynchronous. */
 int nh_symmetrize_c4(nh_ctx* ctx);
 
+/* Obstacles (Sec. II.B: "on solid boundaries, including obstacles,
+ * infinite homeotropic anchoring and no-slip ... bounce-back"): mask[N]
+ * (host, or device when on_device = 1) with 1 at solid nodes, 0 at fluid
+ * nodes, site index x + nx*(y + ny*z); NULL removes the obstacles.  A lattice
+ * link from a fluid site to a solid node bounces back half-way, like the
+ * plates; solid nodes keep the director they hold (store the surface normal
+ * there, with nh_set_fields or nh_restore: infinite anchoring), their velocity
+ * and stress are zero and their populations are carried over unchanged; the
+ * diagnostics sum over fluid sites (links with at least one fluid end).
+ * The mask is copied into the workspace; the force is recomputed if the
+ * fields are set.  Obstacles run on the per-site FD kernels (the fused FD
+ * variant is rejected) and are not supported by the batched calls.  With
+ * walls_z = 1 the plates stay as they are.  Synchronises for a host mask. */
+int nh_set_solid(nh_ctx* ctx, const uint8_t* mask, int on_device);
+
 /* Set the tube centroids to track (count <= NH_MAX_TUBES, centres[2*count]
  * as (x, y) pairs); 0 disables tracking. */
 int nh_set_tubes(nh_ctx* ctx, const double* centres, int count);

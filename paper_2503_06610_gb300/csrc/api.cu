@@ -41,7 +41,8 @@ size_t store_size(const nh_params& p)
 }
 
 struct Layout {
-    size_t f[2], F, Fprev, n, nP, ndot, u, rho, sigma, P3, snap, staging, partials, result, scales, absmax, trig, total;
+    size_t f[2], F, Fprev, n, nP, ndot, u, rho, sigma, P3, snap, staging, partials, result, scales, absmax, trig, solid,
+        total;
 };
 
 Layout make_layout(const nh_params& p)
@@ -73,6 +74,7 @@ Layout make_layout(const nh_params& p)
     L.scales = take(4 * sizeof(float));
     L.absmax = take(4 * sizeof(float));
     L.trig = take(2 * ((size_t)p.nx + p.ny) * sizeof(double));
+    L.solid = take(N);  // obstacle mask, 1 byte per site (used after nh_set_solid)
     L.total = off;
     return L;
 }
@@ -188,6 +190,7 @@ struct nh_ctx {
     size_t ws_bytes = 0;
     bool bound = false;
     bool fields_set = false;
+    bool has_solid = false;  // an obstacle mask is set (nh_set_solid)
     int cur = 0;
     int64_t step = 0;
     std::string err;
@@ -280,6 +283,7 @@ LBChan<Real, Store> lb_chan(nh_ctx* c, int src)
     a.fdst = c->at<Store>(c->L.f[1 - src]);
     a.F = c->at<const Real>(c->L.F);
     a.Fu = nullptr;
+    a.solid = c->has_solid ? c->at<const unsigned char>(c->L.solid) : nullptr;
     a.u = c->at<Real>(c->L.u);
     a.rho = c->at<Real>(c->L.rho);
     a.scales = c->at<float>(c->L.scales);
@@ -304,6 +308,7 @@ FDChan<Real> fd_chan(nh_ctx* c)
     a.sigma = c->at<Real>(c->L.sigma);
     a.F = c->at<Real>(c->L.F);
     a.P3 = c->p.frank3 ? c->at<Real>(c->L.P3) : nullptr;
+    a.solid = c->has_solid ? c->at<const unsigned char>(c->L.solid) : nullptr;
     a.g = Geom{c->p.nx, c->p.ny, c->p.nz, c->p.walls_z, c->p.anchoring, c->N};
     const nh_params& p = c->p;
     a.p.K = Real(p.K);
@@ -633,6 +638,7 @@ int enqueue_diag(nh_ctx* c, cudaStream_t st)
     a.q0 = c->p.q0;
     a.W0 = c->p.W0;
     a.frank3 = c->p.frank3;
+    a.solid = c->has_solid ? c->at<const unsigned char>(c->L.solid) : nullptr;
     a.kd1 = c->p.frank3 ? c->p.K11 - c->p.K : 0.0;
     a.kd2 = c->p.frank3 ? c->p.K22 - c->p.K : 0.0;
     a.kd3 = c->p.frank3 ? c->p.K33 - c->p.K : 0.0;
@@ -701,9 +707,9 @@ int batch_prepare(nh_ctx* const* ctxs, int count, int64_t n_lb_steps, BatchPlan*
         if (c->p.precision != c0->p.precision || c->p.storage != c0->p.storage || c->p.shifted != c0->p.shifted ||
             c->p.dt_fd != c0->p.dt_fd)
             return fail(nullptr, NH_EINVAL, "channels must share precision, storage, shifted and dt_fd");
-        if (c->p.paper_order || c->p.frank3)
-            return fail(nullptr, NH_EINVAL,
-                        "channel " + std::to_string(k) + ": paper_order and frank3 are not supported in batches");
+        if (c->p.paper_order || c->p.frank3 || c->has_solid)
+            return fail(nullptr, NH_EINVAL, "channel " + std::to_string(k) +
+                                                ": paper_order, frank3 and obstacles are not supported in batches");
         if (c->device != c0->device) return fail(nullptr, NH_EINVAL, "channels must be on one device");
         if (c->cur != c0->cur || c->step % c0->p.dt_fd != c0->step % c0->p.dt_fd)
             return fail(nullptr, NH_EINVAL, "channels must be at the same step phase (step mod dt_fd, buffer parity)");
@@ -750,8 +756,9 @@ int batch_prepare_relax(nh_ctx* const* ctxs, int count, int64_t n_fd_steps, Batc
         if (!c->bound || !c->fields_set)
             return fail(nullptr, NH_EINVAL, "channel " + std::to_string(k) + ": workspace or fields not set");
         if (c->p.precision != c0->p.precision) return fail(nullptr, NH_EINVAL, "channels must share the precision");
-        if (c->p.frank3)
-            return fail(nullptr, NH_EINVAL, "channel " + std::to_string(k) + ": frank3 is not supported in batches");
+        if (c->p.frank3 || c->has_solid)
+            return fail(nullptr, NH_EINVAL,
+                        "channel " + std::to_string(k) + ": frank3 and obstacles are not supported in batches");
         if (c->device != c0->device) return fail(nullptr, NH_EINVAL, "channels must be on one device");
         for (int j = 0; j < k; ++j)
             if (ctxs[j] == c) return fail(nullptr, NH_EINVAL, "a context appears twice in the batch");
@@ -1346,6 +1353,30 @@ int nh_symmetrize_c4(nh_ctx* c)
     return NH_OK;
 }
 
+int nh_set_solid(nh_ctx* c, const uint8_t* mask, int on_device)
+{
+    int r = check_ready(c);
+    if (r) return r;
+    if ((r = set_device(c))) return r;
+    cudaStream_t st = c->stream;
+    drop_graphs(c);
+    if (!mask) {
+        c->has_solid = false;
+    } else {
+        const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        NH_CUDA(c, cudaMemcpyAsync(c->ws + c->L.solid, mask, (size_t)c->N, kind, st));
+        if (!on_device) NH_CUDA(c, cudaStreamSynchronize(st));
+        c->has_solid = true;
+        c->fd_fused = 0;  // obstacles run on the per-site FD kernels
+    }
+    if (c->fields_set) {  // the stress, and so the force, depend on the obstacles
+        r = enqueue_force_any(c, st);
+        if (r) return r;
+        close_segment(c);
+    }
+    return NH_OK;
+}
+
 int nh_set_tubes(nh_ctx* c, const double* centres, int count)
 {
     if (!c) return fail(nullptr, NH_EINVAL, "ctx is NULL");
@@ -1470,6 +1501,7 @@ int nh_set_fd_variant(nh_ctx* c, int fused)
     if (!c) return fail(nullptr, NH_EINVAL, "ctx is NULL");
     if (fused != 0 && fused != 1) return fail(c, NH_EINVAL, "FD variant must be 0 or 1");
     if (fused && c->p.frank3) return fail(c, NH_EINVAL, "the three-constant energy runs on the per-site FD kernels only");
+    if (fused && c->has_solid) return fail(c, NH_EINVAL, "obstacles run on the per-site FD kernels only");
     if (fused != c->fd_fused) drop_graphs(c);
     c->fd_fused = fused;
     return NH_OK;

@@ -174,8 +174,9 @@ __device__ __forceinline__ void load3(const Real* __restrict__ n, int N, int s, 
     out[2] = __ldg(n + 2 * N + s);
 }
 
-template <typename Real, typename Store, bool F3>
-__global__ void __launch_bounds__(DIAG_THREADS, (sizeof(Real) == 4 && !F3) ? 5 : 1) diag_kernel(const DiagArgs a)
+template <typename Real, typename Store, bool F3, bool Solid>
+__global__ void __launch_bounds__(DIAG_THREADS, (sizeof(Real) == 4 && !F3 && !Solid) ? 5 : 1)
+    diag_kernel(const DiagArgs a)
 {
     const Geom g = a.g;
     const int N = g.N;
@@ -190,6 +191,7 @@ __global__ void __launch_bounds__(DIAG_THREADS, (sizeof(Real) == 4 && !F3) ? 5 :
     const Real K = Real(a.K), q0 = Real(a.q0), W0 = Real(a.W0);
     const Real site_const = Real(0.5) * K * q0 * q0;
     const bool homeo = g.walls && g.anchoring == NH_ANCHOR_HOMEOTROPIC;
+    const unsigned char* __restrict__ sm = a.solid;
     const int T = a.n_tubes;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __shared__ double tube_acc[NH_MAX_TUBES * 5];
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(DIAG_THREADS, (sizeof(Real) == 4 && !F3) ? 5 :
                     cl[2] = Real(1);
                 }
             }
-            if (g.walls && z0 == 0) {
+            if (g.walls && z0 == 0 && !(Solid && sm[col])) {
                 // link from the lower ghost layer to the first fluid layer
                 Real m[3] = {c[0], c[1], c[2]};
                 if (homeo) {
@@ -270,32 +272,43 @@ __global__ void __launch_bounds__(DIAG_THREADS, (sizeof(Real) == 4 && !F3) ? 5 :
                 for (int i = 0; i < 19; ++i) fs += Codec<Store, Real>::load(f + (size_t)i * N + s, inv_scale);
                 const Real u0 = __ldg(u + s), u1 = __ldg(u + N + s), u2 = __ldg(u + 2 * N + s);
                 const Real r = __ldg(rho + s);
-                msum += fs;
-                Real e = link_energy(c, mx, 0, K, q0);
-                e += link_energy(c, my, 1, K, q0);
-                e += link_energy(c, cn, 2, K, q0);
-                esum += e + site_const - Real(0.5) * W0 * c[2] * c[2];
-                if (F3) {
-                    // three-constant correction with the central gradient
-                    Real mxm[3], mym[3];
-                    load3(n, N, colxm + cols * z, mxm);
-                    load3(n, N, colym + cols * z, mym);
-                    Real G[3][3], dfdn[3], P[3][3];
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        G[0][k] = Real(0.5) * (mx[k] - mxm[k]);
-                        G[1][k] = Real(0.5) * (my[k] - mym[k]);
-                        G[2][k] = Real(0.5) * (cn[k] - cl[k]);
-                    }
-                    esum += frank3_site(c, G, Real(a.kd1), Real(a.kd2), Real(a.kd3), q0, dfdn, P);
+                // obstacles: sums over fluid sites, links with at least one fluid end
+                bool sol = false, solx = false, soly = false, solz = false;
+                if (Solid) {
+                    sol = sm[s] != 0;
+                    solx = sm[colx + cols * z] != 0;
+                    soly = sm[coly + cols * z] != 0;
+                    solz = z + 1 < g.nz ? sm[s + cols] != 0 : (!g.walls ? sm[col] != 0 : true);
                 }
-                const Real umag = sqrt(u0 * u0 + u1 * u1 + u2 * u2);
-                const Real nmag = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
-                max_u = max(max_u, umag);
-                min_nn = min(min_nn, nmag);
-                max_nn = max(max_nn, nmag);
-                if (!isfinite(umag) || !isfinite(nmag) || !isfinite(r) || !isfinite(fs)) bad += 1;
-                wsum += Real(0.5) * (Real(1) - c[2]);
+                Real e = (sol && solx) ? Real(0) : link_energy(c, mx, 0, K, q0);
+                if (!(sol && soly)) e += link_energy(c, my, 1, K, q0);
+                if (!(sol && solz)) e += link_energy(c, cn, 2, K, q0);
+                esum += e;
+                if (!sol) {
+                    msum += fs;
+                    esum += site_const - Real(0.5) * W0 * c[2] * c[2];
+                    if (F3) {
+                        // three-constant correction with the central gradient
+                        Real mxm[3], mym[3];
+                        load3(n, N, colxm + cols * z, mxm);
+                        load3(n, N, colym + cols * z, mym);
+                        Real G[3][3], dfdn[3], P[3][3];
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            G[0][k] = Real(0.5) * (mx[k] - mxm[k]);
+                            G[1][k] = Real(0.5) * (my[k] - mym[k]);
+                            G[2][k] = Real(0.5) * (cn[k] - cl[k]);
+                        }
+                        esum += frank3_site(c, G, Real(a.kd1), Real(a.kd2), Real(a.kd3), q0, dfdn, P);
+                    }
+                    const Real umag = sqrt(u0 * u0 + u1 * u1 + u2 * u2);
+                    const Real nmag = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+                    max_u = max(max_u, umag);
+                    min_nn = min(min_nn, nmag);
+                    max_nn = max(max_nn, nmag);
+                    if (!isfinite(umag) || !isfinite(nmag) || !isfinite(r) || !isfinite(fs)) bad += 1;
+                    wsum += Real(0.5) * (Real(1) - c[2]);
+                }  // fluid site
                 if (F3) {
                     cl[0] = c[0];
                     cl[1] = c[1];
@@ -609,29 +622,38 @@ cudaError_t launch_trig_table(double* t, int nx, int ny, cudaStream_t st)
     return cudaGetLastError();
 }
 
+template <bool Solid>
+void launch_diag_kernel(const DiagArgs& a, int blocks, cudaStream_t st)
+{
+    if (a.precision == NH_FP64) {
+        if (a.frank3)
+            diag_kernel<double, double, true, Solid><<<blocks, DIAG_THREADS, 0, st>>>(a);
+        else
+            diag_kernel<double, double, false, Solid><<<blocks, DIAG_THREADS, 0, st>>>(a);
+    } else if (a.frank3) {
+        switch (a.storage) {
+        case NH_STORE_F32: diag_kernel<float, float, true, Solid><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
+        case NH_STORE_F16S: diag_kernel<float, __half, true, Solid><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
+        default: diag_kernel<float, __nv_bfloat16, true, Solid><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
+        }
+    } else {
+        switch (a.storage) {
+        case NH_STORE_F32: diag_kernel<float, float, false, Solid><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
+        case NH_STORE_F16S: diag_kernel<float, __half, false, Solid><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
+        default: diag_kernel<float, __nv_bfloat16, false, Solid><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
+        }
+    }
+}
+
 cudaError_t launch_diagnostics(const DiagArgs& a, cudaStream_t st)
 {
     const int items = a.g.nx * a.g.ny * ((a.g.nz + kDiagChunk - 1) / kDiagChunk);
     int blocks = (items + DIAG_THREADS - 1) / DIAG_THREADS;
     if (blocks > a.blocks) blocks = a.blocks;
-    if (a.precision == NH_FP64) {
-        if (a.frank3)
-            diag_kernel<double, double, true><<<blocks, DIAG_THREADS, 0, st>>>(a);
-        else
-            diag_kernel<double, double, false><<<blocks, DIAG_THREADS, 0, st>>>(a);
-    } else if (a.frank3) {
-        switch (a.storage) {
-        case NH_STORE_F32: diag_kernel<float, float, true><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
-        case NH_STORE_F16S: diag_kernel<float, __half, true><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
-        default: diag_kernel<float, __nv_bfloat16, true><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
-        }
-    } else {
-        switch (a.storage) {
-        case NH_STORE_F32: diag_kernel<float, float, false><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
-        case NH_STORE_F16S: diag_kernel<float, __half, false><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
-        default: diag_kernel<float, __nv_bfloat16, false><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
-        }
-    }
+    if (a.solid != nullptr)
+        launch_diag_kernel<true>(a, blocks, st);
+    else
+        launch_diag_kernel<false>(a, blocks, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     diag_final_kernel<<<1, 1024, 0, st>>>(a.partials, a.result, blocks, diag_num_values(a.n_tubes));

@@ -51,7 +51,8 @@ __device__ __forceinline__ void dir_at(const Real* __restrict__ n, const Geom& g
 }
 
 template <typename Real>
-__device__ __forceinline__ void vel_at(const Real* __restrict__ u, const Geom& g, int x, int y, int z, Real out[3])
+__device__ __forceinline__ void vel_at(const Real* __restrict__ u, const Geom& g, int x, int y, int z, Real out[3],
+                                       const unsigned char* solid = nullptr)
 {
     if (g.walls) {
         if (z < 0 || z >= g.nz) {
@@ -62,6 +63,10 @@ __device__ __forceinline__ void vel_at(const Real* __restrict__ u, const Geom& g
         z = wrap_p(z, g.nz);
     }
     const int s = x + g.nx * (y + g.ny * z);
+    if (solid != nullptr && solid[s]) {  // obstacle: no-slip
+        out[0] = out[1] = out[2] = Real(0);
+        return;
+    }
     out[0] = u[s];
     out[1] = u[g.N + s];
     out[2] = u[2 * g.N + s];
@@ -70,7 +75,7 @@ __device__ __forceinline__ void vel_at(const Real* __restrict__ u, const Geom& g
 // 7-point neighbourhood: index 0 = centre, 1 + 2b = +e_b, 2 + 2b = -e_b.
 template <typename Real>
 __device__ __forceinline__ void gather7(const Real* __restrict__ f, const Geom& g, int x, int y, int z, Real v[7][3],
-                                        bool director)
+                                        bool director, const unsigned char* solid = nullptr)
 {
     const int xp = wrap_p(x + 1, g.nx), xm = wrap_p(x - 1, g.nx);
     const int yp = wrap_p(y + 1, g.ny), ym = wrap_p(y - 1, g.ny);
@@ -83,13 +88,13 @@ __device__ __forceinline__ void gather7(const Real* __restrict__ f, const Geom& 
         dir_at(f, g, x, y, z + 1, v[5]);
         dir_at(f, g, x, y, z - 1, v[6]);
     } else {
-        vel_at(f, g, x, y, z, v[0]);
-        vel_at(f, g, xp, y, z, v[1]);
-        vel_at(f, g, xm, y, z, v[2]);
-        vel_at(f, g, x, yp, z, v[3]);
-        vel_at(f, g, x, ym, z, v[4]);
-        vel_at(f, g, x, y, z + 1, v[5]);
-        vel_at(f, g, x, y, z - 1, v[6]);
+        vel_at(f, g, x, y, z, v[0], solid);
+        vel_at(f, g, xp, y, z, v[1], solid);
+        vel_at(f, g, xm, y, z, v[2], solid);
+        vel_at(f, g, x, yp, z, v[3], solid);
+        vel_at(f, g, x, ym, z, v[4], solid);
+        vel_at(f, g, x, y, z + 1, v[5], solid);
+        vel_at(f, g, x, y, z - 1, v[6], solid);
     }
 }
 
@@ -153,6 +158,11 @@ __device__ __forceinline__ void director_rate(const Real nn[7][3], const Real uu
 template <typename Real>
 __device__ __forceinline__ void frank3_p_site(const FDChan<Real>& c, const Real* m, int s)
 {
+    if (c.solid != nullptr && c.solid[s]) {  // no energy at obstacle nodes
+#pragma unroll
+        for (int k = 0; k < 9; ++k) c.P3[k * c.g.N + s] = Real(0);
+        return;
+    }
     int x, y, z;
     site_xyz<Real>(c.g, s, x, y, z);
     Real nn[7][3];
@@ -217,11 +227,20 @@ __device__ __forceinline__ void frank3_field_site(const FDChan<Real>& c, const R
 template <typename Real>
 __device__ __forceinline__ void fd_predict_site(const FDChan<Real>& c, int s)
 {
+    const int N = c.g.N;
+    if (c.solid != nullptr && c.solid[s]) {  // obstacle: the director is held
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            c.ndot[a * N + s] = Real(0);
+            c.nP[a * N + s] = c.n[a * N + s];
+        }
+        return;
+    }
     int x, y, z;
     site_xyz<Real>(c.g, s, x, y, z);
     Real nn[7][3], uu[7][3], r[3];
     gather7(c.n, c.g, x, y, z, nn, true);
-    gather7(c.u, c.g, x, y, z, uu, false);
+    gather7(c.u, c.g, x, y, z, uu, false, c.solid);
     if (c.P3 != nullptr) {
         Real hx[3];
         frank3_field_site(c, nn, x, y, z, hx);
@@ -229,7 +248,6 @@ __device__ __forceinline__ void fd_predict_site(const FDChan<Real>& c, int s)
     } else {
         director_rate(nn, uu, c.p, r);
     }
-    const int N = c.g.N;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         c.ndot[a * N + s] = r[a];
@@ -240,11 +258,12 @@ __device__ __forceinline__ void fd_predict_site(const FDChan<Real>& c, int s)
 template <typename Real>
 __device__ __forceinline__ void fd_correct_site(const FDChan<Real>& c, int s)
 {
+    if (c.solid != nullptr && c.solid[s]) return;  // obstacle: the director is held
     int x, y, z;
     site_xyz<Real>(c.g, s, x, y, z);
     Real nn[7][3], uu[7][3], r[3];
     gather7(c.nP, c.g, x, y, z, nn, true);
-    gather7(c.u, c.g, x, y, z, uu, false);
+    gather7(c.u, c.g, x, y, z, uu, false, c.solid);
     if (c.P3 != nullptr) {
         Real hx[3];
         frank3_field_site(c, nn, x, y, z, hx);
@@ -310,11 +329,16 @@ __device__ __forceinline__ void stress_point(const Real nn[7][3], const Real uu[
 template <typename Real>
 __device__ __forceinline__ void stress_site(const FDChan<Real>& c, int s)
 {
+    if (c.solid != nullptr && c.solid[s]) {  // zero stress at obstacle nodes
+#pragma unroll
+        for (int k = 0; k < 9; ++k) c.sigma[k * c.g.N + s] = Real(0);
+        return;
+    }
     int x, y, z;
     site_xyz<Real>(c.g, s, x, y, z);
     Real nn[7][3], uu[7][3], sig[9];
     gather7(c.n, c.g, x, y, z, nn, true);
-    gather7(c.u, c.g, x, y, z, uu, false);
+    gather7(c.u, c.g, x, y, z, uu, false, c.solid);
     if (c.P3 != nullptr) {
         Real hx[3], Pd[9];
         frank3_field_site(c, nn, x, y, z, hx);
@@ -332,10 +356,15 @@ __device__ __forceinline__ void stress_site(const FDChan<Real>& c, int s)
 template <typename Real>
 __device__ __forceinline__ void force_site(const FDChan<Real>& c, int s)
 {
-    int x, y, z;
-    site_xyz<Real>(c.g, s, x, y, z);
     const Geom& g = c.g;
     const int N = g.N;
+    if (c.solid != nullptr && c.solid[s]) {  // no force on obstacle nodes
+#pragma unroll
+        for (int a = 0; a < 3; ++a) c.F[a * N + s] = Real(0);
+        return;
+    }
+    int x, y, z;
+    site_xyz<Real>(c.g, s, x, y, z);
     const int xp = wrap_p(x + 1, g.nx), xm = wrap_p(x - 1, g.nx);
     const int yp = wrap_p(y + 1, g.ny), ym = wrap_p(y - 1, g.ny);
     int zp = z + 1, zm = z - 1;

@@ -90,10 +90,14 @@ __device__ __forceinline__ void store2(Store* p, Real a, Real b, float scale)
 
 // One tile (one thread block's worth of sites) of one channel.  `tile` is the
 // tile index within the channel and `ntiles` the channel's tile count (used by
-// the 16-bit scale controller to find the channel's last tile).
-template <typename Real, typename Store, bool Shifted, bool WriteMacro, int SPT>
+// the 16-bit scale controller to find the channel's last tile).  Solid: the
+// channel has obstacles (c.solid): a link whose source is a solid node
+// bounces back half-way like the plates, and a solid node carries its
+// populations over unchanged (u = 0, rho = 1 on macro steps); one site per thread.
+template <typename Real, typename Store, bool Shifted, bool WriteMacro, int SPT, bool Solid = false>
 __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, int ntiles)
 {
+    static_assert(!Solid || SPT == 1, "obstacles use one site per thread");
     NH_D3Q19_TABLES
     constexpr bool kScaled = sizeof(Store) == 2;
     const int N = c.g.N;
@@ -125,6 +129,7 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
         const int dzp = (z == nz - 1 ? -(nz - 1) : 1) * plane_xy;
         const bool bb_lo = c.g.walls && z == 0;
         const bool bb_hi = c.g.walls && z == nz - 1;
+        const bool solid_here = Solid && c.solid[s0] != 0;
 
         // 1. pull streaming with half-way bounce-back
         Real f[SPT][19];
@@ -132,6 +137,16 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
         for (int i = 0; i < 19; ++i) {
             const bool bb = (EZ[i] > 0 && bb_lo) || (EZ[i] < 0 && bb_hi);
             const int row = (EY[i] > 0 ? dym : (EY[i] < 0 ? dyp : 0)) + (EZ[i] > 0 ? dzm : (EZ[i] < 0 ? dzp : 0));
+            if (Solid) {
+                const int dx = EX[i] > 0 ? dxm[0] : (EX[i] < 0 ? dxp[0] : 0);
+                const int src = s0 + row + dx;
+                const bool back = bb || (!solid_here && c.solid[src] != 0);
+                const int k = back ? OPP[i] : i;
+                f[0][i] = Codec<Store, Real>::load(c.fsrc + (size_t)(solid_here ? i : k) * N +
+                                                       (solid_here || back ? s0 : src),
+                                                   inv_in);
+                continue;
+            }
             const Store* plane = c.fsrc + (size_t)(bb ? OPP[i] : i) * N;
             if (SPT == 2 && EX[i] == 0) {
                 load2(plane + (bb ? s0 : s0 + row), inv_in, f[0][i], f[SPT - 1][i]);
@@ -145,8 +160,19 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
         }
 
         Real fo[SPT][19];
+        if (solid_here) {
+#pragma unroll
+            for (int i = 0; i < 19; ++i) fo[0][i] = f[0][i];
+            if (WriteMacro) {
+                c.u[s0] = Real(0);
+                c.u[N + s0] = Real(0);
+                c.u[2 * N + s0] = Real(0);
+                c.rho[s0] = Real(1);
+            }
+        }
 #pragma unroll
         for (int j = 0; j < SPT; ++j) {
+            if (solid_here) break;
             const int s = s0 + j;
             // 2. moments: pair sums and differences of (e_i, -e_i)
             Real sum = f[j][0], mx = 0, my = 0, mz = 0;
@@ -257,10 +283,10 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
     }
 }
 
-template <typename Real, typename Store, bool Shifted, bool WriteMacro, int SPT>
+template <typename Real, typename Store, bool Shifted, bool WriteMacro, int SPT, bool Solid = false>
 __global__ void __launch_bounds__(kLBThreads) lb_kernel(const LBChan<Real, Store> c)
 {
-    lb_tile<Real, Store, Shifted, WriteMacro, SPT>(c, blockIdx.x, gridDim.x);
+    lb_tile<Real, Store, Shifted, WriteMacro, SPT, Solid>(c, blockIdx.x, gridDim.x);
 }
 
 // Batched sweep: a persistent grid walks the (channel, tile) work list of up to
@@ -297,6 +323,10 @@ bool lb_variant_valid(int variant, int nx)
 template <typename Real, typename Store, bool Shifted, bool WriteMacro>
 cudaError_t launch_lb_spt(const LBChan<Real, Store>& c, int variant, cudaStream_t st)
 {
+    if (c.solid != nullptr) {  // obstacles: one site per thread, 256 threads
+        lb_kernel<Real, Store, Shifted, WriteMacro, 1, true><<<(c.g.N + 255) / 256, 256, 0, st>>>(c);
+        return cudaGetLastError();
+    }
     const LBVariantShape v = kLBVariants[variant];
     const int threads_needed = (c.g.N + v.spt - 1) / v.spt;
     const int blocks = (threads_needed + v.threads - 1) / v.threads;

@@ -88,6 +88,7 @@ struct LBChan {
     Store* fdst;
     const Real* F;  // [3][N] F_lc, frozen over the FD interval
     const Real* Fu; // [3][N] F_lc whose half shifts u, or null: F (paper ordering of Sec. II.D)
+    const unsigned char* solid;  // [N] 1 = solid node (obstacle), or null: none
     Real* u;        // [3][N] written on macro steps
     Real* rho;      // [N]    written on macro steps
     float* scales;
@@ -155,6 +156,7 @@ struct FDChan {
     Real* sigma;  // [9][N]
     Real* F;      // [3][N] F_lc
     Real* P3;     // [9][N] d df/d(d_b n_c) of the three-constant correction, or null (one constant)
+    const unsigned char* solid;  // [N] 1 = solid node (obstacle), or null: none
     Geom g;
     FDPar<Real> p;
 };
@@ -245,6 +247,7 @@ struct DiagArgs {
     Geom g;
     double K, q0, W0;
     int frank3;         // add the three-constant correction to the energy
+    const unsigned char* solid;  // [N] 1 = solid node: excluded from the sums (links to fluid kept), or null
     double kd1, kd2, kd3;
     int n_tubes;
     double tubes[NH_MAX_TUBES][2];

@@ -95,6 +95,7 @@ extern "C" int nh_diagnostics_noalloc(const nh_params* p, const void* f, const v
     a.q0 = p->q0;
     a.W0 = p->W0;
     a.frank3 = p->frank3 == 1;
+    a.solid = nullptr;  // no obstacles
     a.kd1 = a.frank3 ? p->K11 - p->K : 0.0;
     a.kd2 = a.frank3 ? p->K22 - p->K : 0.0;
     a.kd3 = a.frank3 ? p->K33 - p->K : 0.0;

@@ -94,6 +94,7 @@ SIGNATURES = {
     "nh_batch_step": ([ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int64, _VP], ctypes.c_int),
     "nh_batch_autotune": ([ctypes.POINTER(_VP), ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "nh_set_tubes": ([_VP, _DP, ctypes.c_int], ctypes.c_int),
+    "nh_set_solid": ([_VP, _VP, ctypes.c_int], ctypes.c_int),
     "nh_relax": ([_VP, ctypes.c_int64, _VP], ctypes.c_int),
     "nh_director_change": ([_VP, _DP], ctypes.c_int),
     "nh_symmetrize_c4": ([_VP], ctypes.c_int),
@@ -280,6 +281,18 @@ def nh_batch_relax(ctxs, n_fd_steps: int, stream=None):
     _check(load_library().nh_batch_relax(arr, len(ctxs), int(n_fd_steps), _VP(stream or 0)))
 
 
+def nh_set_solid(ctx, mask):
+    """mask: host array [N] (1 = solid node), a CUDA uint8 tensor, or None."""
+    if mask is None:
+        _check(load_library().nh_set_solid(ctx, None, 0), ctx)
+        return
+    if hasattr(mask, "data_ptr"):
+        _check(load_library().nh_set_solid(ctx, _VP(mask.data_ptr()), 1), ctx)
+        return
+    m = np.ascontiguousarray(np.asarray(mask).reshape(-1), dtype=np.uint8)
+    _check(load_library().nh_set_solid(ctx, m.ctypes.data_as(_VP), 0), ctx)
+
+
 def nh_set_tubes(ctx, centres):
     c = np.ascontiguousarray(np.asarray(centres, dtype=np.float64).reshape(-1))
     _check(load_library().nh_set_tubes(ctx, c.ctypes.data_as(_DP), len(c) // 2), ctx)
@@ -431,6 +444,10 @@ class Channel:
 
     def set_tubes(self, centres):
         nh_set_tubes(self.ctx, centres)
+
+    def set_solid(self, mask):
+        """Obstacle mask [N] (1 = solid node) or None; see nh_set_solid."""
+        nh_set_solid(self.ctx, mask)
 
     def diagnostics(self, allow_unstable=False):
         return nh_diagnostics(self.ctx, allow_unstable)

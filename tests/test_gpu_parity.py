@@ -657,3 +657,97 @@ def test_frank3_rejects_fused_and_batches(nh):
         nh.batch_relax(chans, 2)
     with pytest.raises(nh.NHError):
         nh.Channel(dict(params, K22=0.0, precision="fp32"))
+
+
+# ------------------------------------------------------------------ obstacles (solid nodes)
+
+def _sphere_mask(nx, ny, nz, c, r):
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    m = (((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2) <= r * r)
+    v = np.stack([x - c[0], y - c[1], z - c[2]]).astype(float)
+    v[:, np.linalg.norm(v, axis=0) == 0] = np.array([0, 0, 1.0])[:, None]
+    return m.astype(np.uint8).reshape(-1), (v / np.linalg.norm(v, axis=0)).reshape(3, -1)
+
+
+@pytest.mark.parametrize("frank3", [False, True])
+def test_obstacle_channel_matches_oracle(nh, oracle_mod, frank3):
+    O = oracle_mod
+    nx, ny, nz = 20, 14, 10
+    mask, normals = _sphere_mask(nx, ny, nz, (10.0, 7.0, 5.0), 3.2)
+    extra = dict(K11=0.045, K22=0.015, K33=0.06) if frank3 else {}
+    params = _generic(nx, ny, nz, dt_fd=2, K=0.03, q0=2 * math.pi / 10, W0=0.002, g=(1e-4, 2e-5, 0.0),
+                      **extra)
+    n0 = I.tilted_director(nx, ny, nz, amplitude=0.3, seed=3)
+    n0[:, mask == 1] = normals[:, mask == 1]
+    ref = O.OracleSim(O.OracleParams.from_dict(dict(params, solid=mask)), n0).step(21)
+    fl = mask == 0
+    for prec, tol in (("fp64", 1e-12), ("fp32", 2e-5)):
+        ch = nh.Channel(dict(params, precision=prec))
+        ch.set_solid(mask)
+        ch.set_fields(n0)
+        ch.step(21)
+        n, u, rho = ch.get_fields()
+        assert O.rel_l2(n, ref.n) <= tol
+        assert O.rel_l2(u[:, fl], ref.u[:, fl]) <= (1e-10 if prec == "fp64" else 1e-4)
+        assert np.array_equal(n[:, ~fl], n0[:, ~fl]) or prec == "fp32"
+        assert np.max(np.abs(u[:, ~fl])) == 0.0
+        if prec == "fp64":
+            f = ch.get_populations()
+            assert np.max(np.abs(f - ref.f)) < 1e-14
+        d = ch.diagnostics()
+        assert abs(d["mass"] - ref.mass()) <= (1e-12 if prec == "fp64" else 1e-5) * ch.N
+        assert abs(d["energy"] - ref.energy()) <= (1e-11 if prec == "fp64" else 1e-5) * abs(ref.energy())
+
+
+def test_obstacle_plates_equal_rotated_walls_gpu(nh):
+    """GPU: mask plates normal to y in a periodic box = the z-plate channel in
+    rotated axes (cyclic permutation of sites and components), FP64."""
+    nxA, nyA, nzA = 16, 12, 9
+    pA = _generic(nxA, nyA, nzA, dt_fd=3, K=0.03, q0=2 * math.pi / 9, W0=0.0, g=(2e-5, -1e-5, 3e-6))
+    n0A = I.skyrmion_tubes(nxA, nyA, nzA, [(8.0, 6.0)], 3.5)
+
+    def to_B(a, vector):
+        if vector:
+            a = np.asarray(a).reshape(3, nzA, nyA, nxA)
+            return np.stack([to_B(a[k], False) for k in (1, 2, 0)])
+        out = np.zeros((nxA, nzA + 2, nyA))
+        out[:, 1:-1, :] = np.transpose(np.asarray(a).reshape(nzA, nyA, nxA), (2, 0, 1))
+        return out
+
+    solid = np.zeros((nxA, nzA + 2, nyA), np.uint8)
+    solid[:, 0, :] = 1
+    solid[:, -1, :] = 1
+    n0B = to_B(n0A, True)
+    n0B[1][solid == 1] = 1.0
+    pB = dict(pA, nx=nyA, ny=nzA + 2, nz=nxA, walls_z=False, g=(pA["g"][1], pA["g"][2], pA["g"][0]))
+    a = _channel(nh, pA, n0A, precision="fp64")
+    a.step(13)
+    b = nh.Channel(dict(pB, precision="fp64"))
+    b.set_solid(solid.reshape(-1))
+    b.set_fields(n0B.reshape(3, -1))
+    b.step(13)
+    na, ua, _ = a.get_fields()
+    nb, ub, _ = b.get_fields()
+    fl = solid.reshape(-1) == 0
+    assert np.max(np.abs(nb[:, fl] - to_B(na, True).reshape(3, -1)[:, fl])) < 1e-13
+    assert np.max(np.abs(ub[:, fl] - to_B(ua, True).reshape(3, -1)[:, fl])) < 1e-13 * np.max(np.abs(ua))
+    assert abs(a.diagnostics()["energy"] - b.diagnostics()["energy"]) < 1e-12 * abs(a.diagnostics()["energy"])
+
+
+def test_obstacle_rejects_fused_and_batches(nh):
+    params = _generic(16, 12, 8, dt_fd=2)
+    n0 = I.uniform_director(16, 12, 8)
+    mask = np.zeros(16 * 12 * 8, np.uint8)
+    mask[100] = 1
+    chans = []
+    for _ in range(2):
+        ch = nh.Channel(dict(params, precision="fp32"))
+        ch.set_solid(mask)
+        ch.set_fields(n0)
+        chans.append(ch)
+    with pytest.raises(nh.NHError):
+        chans[0].set_fd_variant(1)
+    with pytest.raises(nh.NHError):
+        nh.batch_step(chans, 2)
+    chans[1].set_solid(None)
+    chans[1].set_fd_variant(1)
