@@ -69,7 +69,7 @@ extern "C" {
 /* Parameters of one channel.  Table I of the paper lists a physical set; the
  * field names follow the paper's symbols. */
 typedef struct nh_params {
-    int32_t nx, ny, nz;   /* lattice size, each >= 1 (nz >= 2 with walls) */
+    int32_t nx, ny, nz;   /* lattice size, each >= 1, 19*nx*ny*nz < 2^31 */
     int32_t walls_z;      /* 1: bounce-back plates in z; 0: periodic in z */
     int32_t anchoring;    /* NH_ANCHOR_* (used only with walls_z = 1) */
     int32_t precision;    /* NH_FP64 or NH_FP32 */

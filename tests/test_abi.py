@@ -49,12 +49,19 @@ def _base(**kw):
     dict(storage="f16s", shifted=False), dict(storage="bf16s", shifted=False),
     dict(K=float("nan")), dict(nx=2000, ny=2000, nz=100),
     dict(K=0.04, dt_fd=8, check_stability=True),
+    dict(K11=0.0, K22=1.0, K33=1.0), dict(K11=1.0, K22=float("inf"), K33=1.0),
+    dict(nx=113025456, ny=1, nz=1),
 ])
 def test_invalid_params_rejected(nh, bad):
     p = nh.make_params(_base(**bad))
     with pytest.raises(nh.NHError) as e:
         nh.nh_workspace_bytes(p)
     assert e.value.code == nh.NH_EINVAL
+
+
+def test_largest_domain_accepted(nh):
+    """19 N must fit a signed 32-bit index: N = 113 025 455 is the largest channel."""
+    assert nh.nh_workspace_bytes(nh.make_params(_base(nx=113025455, ny=1, nz=1))) > 19 * 4 * 113025455
 
 
 def test_workspace_size_formula(nh):

@@ -751,3 +751,26 @@ def test_obstacle_rejects_fused_and_batches(nh):
         nh.batch_step(chans, 2)
     chans[1].set_solid(None)
     chans[1].set_fd_variant(1)
+
+
+# ------------------------------------------------------------------ degenerate lattices
+
+@pytest.mark.parametrize("fused", [1, 0])
+@pytest.mark.parametrize("dims,walls", [((1, 1, 2), True), ((2, 3, 1), True), ((1, 5, 3), True),
+                                        ((3, 1, 4), False), ((2, 2, 1), False), ((5, 4, 2), True)])
+def test_degenerate_lattices_fp64(nh, oracle_mod, dims, walls, fused):
+    """One-site-wide directions (a site is its own x or y neighbour), a single
+    layer between the plates, two-layer periodic boxes: FP64 against the oracle."""
+    O = oracle_mod
+    params = _generic(*dims, walls_z=walls, dt_fd=2, K=0.03, q0=0.7, W0=0.01, alpha4p=0.02)
+    n0 = I.random_director(*dims, seed=11)
+    u0 = I.random_velocity(*dims, 1e-3, seed=12)
+    ref = _oracle_sim(O, params, n0, u0).step(9)
+    ch = nh.Channel(dict(params, precision="fp64"))
+    ch.set_fd_variant(fused)
+    ch.set_fields(n0, u0)
+    ch.step(9)
+    n, u, rho = ch.get_fields()
+    assert np.max(np.abs(n - ref.n)) < 1e-13
+    assert np.max(np.abs(u - ref.u)) < 1e-13 * max(1e-3, np.max(np.abs(ref.u)))
+    assert np.max(np.abs(rho - ref.rho)) < 1e-13
