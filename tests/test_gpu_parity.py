@@ -774,3 +774,22 @@ def test_degenerate_lattices_fp64(nh, oracle_mod, dims, walls, fused):
     assert np.max(np.abs(n - ref.n)) < 1e-13
     assert np.max(np.abs(u - ref.u)) < 1e-13 * max(1e-3, np.max(np.abs(ref.u)))
     assert np.max(np.abs(rho - ref.rho)) < 1e-13
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16s", "bf16s"])
+@pytest.mark.parametrize("dims,walls", [((6, 5, 7), True), ((64, 4, 3), False), ((16, 6, 5), True)])
+def test_lb_launch_shapes_bitwise_equal(nh, storage, dims, walls):
+    """The two-site shapes (neighbour values by warp shuffle inside a row, scalar
+    loads at row ends, warp edges and the grid's last partial warp) read the same
+    values as the one-site shapes: identical populations and fields."""
+    params = _generic(*dims, walls_z=walls, dt_fd=3)
+    n0 = I.tilted_director(*dims, amplitude=0.3, seed=5)
+    out = []
+    for v in (0, 1, 2, 3):
+        ch = _channel(nh, params, n0, precision="fp32", storage=storage)
+        ch.set_lb_variant(v)
+        ch.step(10)
+        out.append((ch.get_populations(), *ch.get_fields()))
+    for other in out[1:]:
+        for a, b in zip(out[0], other):
+            assert np.array_equal(a, b)
