@@ -250,7 +250,8 @@ int nh_symmetrize_c4(nh_ctx* ctx);
  * The mask is copied into the workspace; the force is recomputed if the
  * fields are set.  Obstacles run on the per-site FD kernels (the fused FD
  * variant is rejected) and are not supported by the batched calls.  With
- * walls_z = 1 the plates stay as they are.  Synchronises for a host mask. */
+ * walls_z = 1 the plates stay as they are.  Synchronises the context's stream
+ * (the fluid sites are counted on the host). */
 int nh_set_solid(nh_ctx* ctx, const uint8_t* mask, int on_device);
 
 /* Set the tube centroids to track (count <= NH_MAX_TUBES, centres[2*count]

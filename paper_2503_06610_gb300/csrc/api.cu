@@ -191,6 +191,7 @@ struct nh_ctx {
     bool bound = false;
     bool fields_set = false;
     bool has_solid = false;  // an obstacle mask is set (nh_set_solid)
+    int64_t n_fluid = 0;     // fluid sites when has_solid
     int cur = 0;
     int64_t step = 0;
     std::string err;
@@ -1365,7 +1366,13 @@ int nh_set_solid(nh_ctx* c, const uint8_t* mask, int on_device)
     } else {
         const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
         NH_CUDA(c, cudaMemcpyAsync(c->ws + c->L.solid, mask, (size_t)c->N, kind, st));
-        if (!on_device) NH_CUDA(c, cudaStreamSynchronize(st));
+        // fluid-site count (the shifted store's rho0 = 1 per fluid site in the mass)
+        std::vector<uint8_t> host((size_t)c->N);
+        NH_CUDA(c, cudaMemcpyAsync(host.data(), c->ws + c->L.solid, (size_t)c->N, cudaMemcpyDeviceToHost, st));
+        NH_CUDA(c, cudaStreamSynchronize(st));
+        int64_t fluid = 0;
+        for (uint8_t b : host) fluid += b == 0;
+        c->n_fluid = fluid;
         c->has_solid = true;
         c->fd_fused = 0;  // obstacles run on the per-site FD kernels
     }
@@ -1418,7 +1425,7 @@ int nh_diagnostics_read(nh_ctx* c, nh_diag* out)
     memset(out, 0, sizeof(*out));
     const double* v = c->host_result;
     out->step = c->step;
-    out->mass = v[0] + (c->p.shifted ? (double)c->N : 0.0);
+    out->mass = v[0] + (c->p.shifted ? (double)(c->has_solid ? c->n_fluid : c->N) : 0.0);
     out->energy = v[1];
     out->max_u = v[2];
     out->min_norm = v[3];
