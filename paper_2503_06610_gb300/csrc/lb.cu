@@ -130,9 +130,6 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
         const bool bb_lo = c.g.walls && z == 0;
         const bool bb_hi = c.g.walls && z == nz - 1;
         const bool solid_here = Solid && c.solid[s0] != 0;
-        // all 32 lanes of this warp hold sites (only the grid's last warp may not)
-        const int lane = threadIdx.x & 31;
-        const bool full_warp = (s0 - SPT * lane) + SPT * 32 <= N;
 
         // 1. pull streaming with half-way bounce-back
         Real f[SPT][19];
@@ -153,33 +150,6 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
             const Store* plane = c.fsrc + (size_t)(bb ? OPP[i] : i) * N;
             if (SPT == 2 && EX[i] == 0) {
                 load2(plane + (bb ? s0 : s0 + row), inv_in, f[0][i], f[SPT - 1][i]);
-            } else if (SPT == 2 && full_warp) {
-                // e_x = +-1: every lane loads its own aligned pair (x0, x0+1) of the
-                // source row; the value one site outside the pair is the
-                // neighbouring lane's, except at a row end or a warp edge
-                const Store* pl = c.fsrc + (size_t)i * N;
-                Real a, b;
-                load2(pl + s0 + row, inv_in, a, b);
-                Real nb;
-                bool edge;
-                if (EX[i] > 0) {  // sources x0 - 1, x0
-                    nb = __shfl_up_sync(0xffffffffu, b, 1);
-                    edge = lane == 0 || x0 == 0;
-                    if (edge) nb = Codec<Store, Real>::load(pl + s0 + row + dxm[0], inv_in);
-                } else {  // sources x0 + 1, x0 + 2
-                    nb = __shfl_down_sync(0xffffffffu, a, 1);
-                    edge = lane == 31 || x0 + 2 >= nx;
-                    if (edge) nb = Codec<Store, Real>::load(pl + s0 + 1 + row + dxp[1], inv_in);
-                }
-                if (bb) {
-                    load2(plane + s0, inv_in, f[0][i], f[SPT - 1][i]);
-                } else if (EX[i] > 0) {
-                    f[0][i] = nb;
-                    f[SPT - 1][i] = a;
-                } else {
-                    f[0][i] = b;
-                    f[SPT - 1][i] = nb;
-                }
             } else {
 #pragma unroll
                 for (int j = 0; j < SPT; ++j) {
