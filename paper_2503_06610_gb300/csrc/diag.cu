@@ -159,7 +159,7 @@ __device__ __forceinline__ Real link_energy(const Real n[3], const Real m[3], in
 // site ahead and is both the z+1 link partner and the next centre, the x+1 and
 // y+1 partners are branch-free loads, and the loop is unrolled so that several
 // sites' loads are in flight.  Per-site terms are summed over the chunk in the
-// build's precision (Real); each item's sums are then accumulated in FP64.
+// build's precision (Real) over a thread's items, then in FP64 across threads.
 // Tube sums use the item's weight sum_z (1 - n_z)/2, the column's nearest
 // previous centroid (FP32 periodic distance with an FP64 tie check), the
 // FP64 sin/cos tables of the column position, a warp sum in Real per owner
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(DIAG_THREADS, (sizeof(Real) == 4 && !F3 && !So
     }
     __syncthreads();
 
-    double mass = 0.0, energy = 0.0;
+    Real mass_t = 0, energy_t = 0;  // this thread's sums over its items (build precision)
     Real max_u = 0, min_nn = Real(1e30), max_nn = 0;
     int bad = 0;
     for (int base = blockIdx.x * blockDim.x; base < items; base += gridDim.x * blockDim.x) {
@@ -318,8 +318,8 @@ __global__ void __launch_bounds__(DIAG_THREADS, (sizeof(Real) == 4 && !F3 && !So
                 c[1] = cn[1];
                 c[2] = cn[2];
             }
-            mass += (double)msum;
-            energy += (double)esum;
+            mass_t += msum;
+            energy_t += esum;
         }
         if (T > 0) {
             int owner = -1;
@@ -389,8 +389,8 @@ __global__ void __launch_bounds__(DIAG_THREADS, (sizeof(Real) == 4 && !F3 && !So
         }
     }
     double dmax_u = (double)max_u, dmin_nn = (double)min_nn, dmax_nn = (double)max_nn, dbad = (double)bad;
-    mass = warp_sum(mass);
-    energy = warp_sum(energy);
+    double mass = warp_sum((double)mass_t);
+    double energy = warp_sum((double)energy_t);
     dbad = warp_sum(dbad);
     dmax_u = warp_max(dmax_u);
     dmin_nn = warp_min(dmin_nn);
