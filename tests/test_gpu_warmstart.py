@@ -255,12 +255,13 @@ def test_relaxation_driver_converges(env):
 
 def test_trained_network_saves_relaxation_steps(env):
     """The gain over the method without the network, on a small version of the
-    warm-start experiment (32x32x16 cells): the plain relaxation continued from
-    the trained network's prediction ends on the field of the relaxation from
-    the ansatz (max |dn| <= 1e-4) in fewer FD steps."""
+    warm-start experiment (48x48x16 cells, wide enough that a tube does not feel
+    its periodic images): the plain relaxation continued from the trained
+    network's prediction ends on the field of the relaxation from the ansatz
+    (max |dn| <= 1e-4) in fewer FD steps."""
     torch, nh, ws, U = env
-    samples = I.warmstart_samples(96, seed=3, nx=32, ny=32, lz_choices=(16,))
-    kw = dict(tol=5e-10, max_steps=60000)
+    samples = I.warmstart_samples(96, seed=3, nx=48, ny=48, lz_choices=(16,))
+    kw = dict(tol=2e-10, max_steps=80000)
     targets, steps, _ = ws.generate(samples, **kw)
     valid = [i for i in range(len(samples)) if not ws.collapsed(targets[i], samples[i][0]["nz"])]
     train_idx = [i for i in valid if i < 80]
@@ -270,6 +271,6 @@ def test_trained_network_saves_relaxation_steps(env):
     hist = ws.train(net, samples, targets, train_idx, epochs=40)
     assert hist[-1] < 0.5 * hist[0]
     res = ws.evaluate(net, samples, targets, steps, test_idx, **kw)
-    print("warm start (32x32x16):", {k: v for k, v in res.items() if k != "per_sample"})
+    print("warm start (48x48x16):", {k: v for k, v in res.items() if k != "per_sample"})
     assert res["max_dn_final"] <= 1e-4
     assert res["step_ratio"] < 0.95
