@@ -404,8 +404,9 @@ __global__ void __launch_bounds__(DIAG_THREADS, (sizeof(Real) == 4 && !F3 && !So
         red[wid][5] = dbad;
     }
     __syncthreads();
-    const int V = DIAG_FIXED + 5 * T;
-    double* out = a.partials + (size_t)blockIdx.x * V;
+    // block partials, value-major: partials[k * gridDim.x + block]
+    double* out = a.partials + blockIdx.x;
+    const size_t stride = gridDim.x;
     if (threadIdx.x == 0) {
         double v[DIAG_FIXED] = {0.0, 0.0, 0.0, 1e300, 0.0, 0.0};
         for (int w = 0; w < DIAG_THREADS / 32; ++w) {
@@ -416,13 +417,14 @@ __global__ void __launch_bounds__(DIAG_THREADS, (sizeof(Real) == 4 && !F3 && !So
             v[4] = fmax(v[4], red[w][4]);
             v[5] += red[w][5];
         }
-        for (int k = 0; k < DIAG_FIXED; ++k) out[k] = v[k];
+        for (int k = 0; k < DIAG_FIXED; ++k) out[k * stride] = v[k];
     }
-    for (int k = threadIdx.x; k < 5 * T; k += blockDim.x) out[DIAG_FIXED + k] = tube_acc[k];
+    for (int k = threadIdx.x; k < 5 * T; k += blockDim.x) out[(DIAG_FIXED + k) * stride] = tube_acc[k];
 }
 
-// One warp per reduced value; lanes stride over the block partials and combine
-// with a fixed shuffle tree, so the result is deterministic.
+// One warp per reduced value; lanes stride over the block partials (stored
+// value-major, so the loads are contiguous) and combine with a fixed shuffle
+// tree, so the result is deterministic.
 __global__ void diag_final_kernel(const double* __restrict__ partials, double* __restrict__ result, int blocks, int V)
 {
     const int lane = threadIdx.x & 31;
@@ -432,7 +434,7 @@ __global__ void diag_final_kernel(const double* __restrict__ partials, double* _
         // loads unrolled ahead of the (fixed-order) combination
 #pragma unroll 8
         for (int b = lane; b < blocks; b += 32) {
-            const double v = __ldg(partials + (size_t)b * V + k);
+            const double v = __ldg(partials + (size_t)k * blocks + b);
             acc = kind == 0 ? acc + v : (kind == 1 ? fmax(acc, v) : fmin(acc, v));
         }
         for (int o = 16; o > 0; o >>= 1) {
