@@ -260,15 +260,15 @@ def test_trained_network_saves_relaxation_steps(env):
     network's prediction ends on the field of the relaxation from the ansatz
     (max |dn| <= 1e-4) in fewer FD steps."""
     torch, nh, ws, U = env
-    samples = I.warmstart_samples(96, seed=3, nx=48, ny=48, lz_choices=(16,))
+    samples = I.warmstart_samples(176, seed=3, nx=48, ny=48, lz_choices=(16,))
     kw = dict(tol=2e-10, max_steps=80000)
     targets, steps, _ = ws.generate(samples, **kw)
     valid = [i for i in range(len(samples)) if not ws.collapsed(targets[i], samples[i][0]["nz"])]
-    train_idx = [i for i in valid if i < 80]
-    test_idx = [i for i in valid if i >= 80]
-    assert len(train_idx) >= 70 and len(test_idx) >= 12
+    train_idx = [i for i in valid if i < 160]
+    test_idx = [i for i in valid if i >= 160]
+    assert len(train_idx) >= 150 and len(test_idx) >= 14
     net = ws.WarmStartNet(seed=0)
-    hist = ws.train(net, samples, targets, train_idx, epochs=40)
+    hist = ws.train(net, samples, targets, train_idx, epochs=60)
     assert hist[-1] < 0.5 * hist[0]
     res = ws.evaluate(net, samples, targets, steps, test_idx, **kw)
     print("warm start (48x48x16):", {k: v for k, v in res.items() if k != "per_sample"})
