@@ -194,10 +194,12 @@ __global__ void __launch_bounds__(DIAG_THREADS, (sizeof(Real) == 4 && !F3 && !So
     const unsigned char* __restrict__ sm = a.solid;
     const int T = a.n_tubes;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __shared__ double tube_acc[NH_MAX_TUBES * 5];
+    // tube sums per warp (lane 0 of each warp owns its row: no atomics)
+    __shared__ double tube_acc[DIAG_THREADS / 32][NH_MAX_TUBES * 5];
     __shared__ float tube_xy[NH_MAX_TUBES][2];
     __shared__ double red[DIAG_THREADS / 32][DIAG_FIXED];
-    for (int k = threadIdx.x; k < T * 5; k += blockDim.x) tube_acc[k] = 0.0;
+    for (int k = threadIdx.x; k < (DIAG_THREADS / 32) * NH_MAX_TUBES * 5; k += blockDim.x)
+        (&tube_acc[0][0])[k] = 0.0;
     for (int k = threadIdx.x; k < T; k += blockDim.x) {
         tube_xy[k][0] = (float)a.tubes[k][0];
         tube_xy[k][1] = (float)a.tubes[k][1];
@@ -383,7 +385,7 @@ __global__ void __launch_bounds__(DIAG_THREADS, (sizeof(Real) == 4 && !F3 && !So
 #pragma unroll
                 for (int k = 0; k < 5; ++k) {
                     const Real sum = warp_sum(mine ? v[k] : Real(0));
-                    if (lane == 0) atomicAdd(&tube_acc[t * 5 + k], (double)sum);
+                    if (lane == 0) tube_acc[wid][t * 5 + k] += (double)sum;
                 }
             }
         }
@@ -419,30 +421,41 @@ __global__ void __launch_bounds__(DIAG_THREADS, (sizeof(Real) == 4 && !F3 && !So
         }
         for (int k = 0; k < DIAG_FIXED; ++k) out[k * stride] = v[k];
     }
-    for (int k = threadIdx.x; k < 5 * T; k += blockDim.x) out[(DIAG_FIXED + k) * stride] = tube_acc[k];
+    for (int k = threadIdx.x; k < 5 * T; k += blockDim.x) {
+        double acc = 0.0;
+        for (int w = 0; w < DIAG_THREADS / 32; ++w) acc += tube_acc[w][k];  // fixed order
+        out[(DIAG_FIXED + k) * stride] = acc;
+    }
 }
 
-// One warp per reduced value; lanes stride over the block partials (stored
-// value-major, so the loads are contiguous) and combine with a fixed shuffle
-// tree, so the result is deterministic.
-__global__ void diag_final_kernel(const double* __restrict__ partials, double* __restrict__ result, int blocks, int V)
+// One block per reduced value: each thread combines a strided subset of the
+// block partials (stored value-major, so the loads are contiguous), then a
+// fixed shared-memory tree combines the threads, so the result is
+// deterministic.  Spread over V blocks because FP64 throughput per SM is low.
+constexpr int kFinalThreads = 256;
+__global__ void __launch_bounds__(kFinalThreads) diag_final_kernel(const double* __restrict__ partials,
+                                                                   double* __restrict__ result, int blocks, int V)
 {
-    const int lane = threadIdx.x & 31;
-    for (int k = threadIdx.x >> 5; k < V; k += blockDim.x >> 5) {
-        const int kind = (k == 2 || k == 4) ? 1 : (k == 3 ? 2 : 0);  // 0 sum, 1 max, 2 min
-        double acc = kind == 2 ? 1e300 : 0.0;
-        // loads unrolled ahead of the (fixed-order) combination
-#pragma unroll 8
-        for (int b = lane; b < blocks; b += 32) {
-            const double v = __ldg(partials + (size_t)k * blocks + b);
-            acc = kind == 0 ? acc + v : (kind == 1 ? fmax(acc, v) : fmin(acc, v));
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const double w = __shfl_xor_sync(0xffffffffu, acc, o);
-            acc = kind == 0 ? acc + w : (kind == 1 ? fmax(acc, w) : fmin(acc, w));
-        }
-        if (lane == 0) result[k] = acc;
+    const int k = blockIdx.x;
+    if (k >= V) return;
+    const int kind = (k == 2 || k == 4) ? 1 : (k == 3 ? 2 : 0);  // 0 sum, 1 max, 2 min
+    double acc = kind == 2 ? 1e300 : 0.0;
+    for (int b = threadIdx.x; b < blocks; b += kFinalThreads) {
+        const double v = __ldg(partials + (size_t)k * blocks + b);
+        acc = kind == 0 ? acc + v : (kind == 1 ? fmax(acc, v) : fmin(acc, v));
     }
+    __shared__ double sh[kFinalThreads];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = kFinalThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            const double w = sh[threadIdx.x + o];
+            const double a = sh[threadIdx.x];
+            sh[threadIdx.x] = kind == 0 ? a + w : (kind == 1 ? fmax(a, w) : fmin(a, w));
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) result[k] = sh[0];
 }
 
 // sin / cos of 2 pi x / nx and 2 pi y / ny in FP64, laid out [sx | cx | sy | cy].
@@ -658,7 +671,8 @@ cudaError_t launch_diagnostics(const DiagArgs& a, cudaStream_t st)
         launch_diag_kernel<false>(a, blocks, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    diag_final_kernel<<<1, 1024, 0, st>>>(a.partials, a.result, blocks, diag_num_values(a.n_tubes));
+    diag_final_kernel<<<diag_num_values(a.n_tubes), kFinalThreads, 0, st>>>(a.partials, a.result, blocks,
+                                                                           diag_num_values(a.n_tubes));
     return cudaGetLastError();
 }
 
