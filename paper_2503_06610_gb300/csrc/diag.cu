@@ -162,8 +162,8 @@ __device__ __forceinline__ Real link_energy(const Real n[3], const Real m[3], in
 // build's precision (Real) over a thread's items, then in FP64 across threads.
 // Tube sums use the item's weight sum_z (1 - n_z)/2, the column's nearest
 // previous centroid (FP32 periodic distance with an FP64 tie check), the
-// FP64 sin/cos tables of the column position, a warp sum in Real per owner
-// and FP64 shared-memory accumulation.
+// FP64 sin/cos tables of the column position, a warp sum and a per-warp
+// shared-memory sum in Real per owner, and FP64 accumulation across warps.
 constexpr int kDiagChunk = 8;
 
 template <typename Real>
@@ -194,12 +194,13 @@ __global__ void __launch_bounds__(DIAG_THREADS, (sizeof(Real) == 4 && !F3 && !So
     const unsigned char* __restrict__ sm = a.solid;
     const int T = a.n_tubes;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    // tube sums per warp (lane 0 of each warp owns its row: no atomics)
-    __shared__ double tube_acc[DIAG_THREADS / 32][NH_MAX_TUBES * 5];
+    // tube sums per warp in the build's precision (lane 0 of each warp owns its
+    // row: no atomics); combined in FP64 across warps and blocks
+    __shared__ Real tube_acc[DIAG_THREADS / 32][NH_MAX_TUBES * 5];
     __shared__ float tube_xy[NH_MAX_TUBES][2];
     __shared__ double red[DIAG_THREADS / 32][DIAG_FIXED];
     for (int k = threadIdx.x; k < (DIAG_THREADS / 32) * NH_MAX_TUBES * 5; k += blockDim.x)
-        (&tube_acc[0][0])[k] = 0.0;
+        (&tube_acc[0][0])[k] = Real(0);
     for (int k = threadIdx.x; k < T; k += blockDim.x) {
         tube_xy[k][0] = (float)a.tubes[k][0];
         tube_xy[k][1] = (float)a.tubes[k][1];
@@ -385,7 +386,7 @@ __global__ void __launch_bounds__(DIAG_THREADS, (sizeof(Real) == 4 && !F3 && !So
 #pragma unroll
                 for (int k = 0; k < 5; ++k) {
                     const Real sum = warp_sum(mine ? v[k] : Real(0));
-                    if (lane == 0) tube_acc[wid][t * 5 + k] += (double)sum;
+                    if (lane == 0) tube_acc[wid][t * 5 + k] += sum;
                 }
             }
         }
@@ -423,7 +424,7 @@ __global__ void __launch_bounds__(DIAG_THREADS, (sizeof(Real) == 4 && !F3 && !So
     }
     for (int k = threadIdx.x; k < 5 * T; k += blockDim.x) {
         double acc = 0.0;
-        for (int w = 0; w < DIAG_THREADS / 32; ++w) acc += tube_acc[w][k];  // fixed order
+        for (int w = 0; w < DIAG_THREADS / 32; ++w) acc += (double)tube_acc[w][k];  // fixed order
         out[(DIAG_FIXED + k) * stride] = acc;
     }
 }
