@@ -292,8 +292,10 @@ int64_t nh_launch_count(const nh_ctx* ctx);
 
 /* Select the launch shape of the fused LB kernel: 0 = two sites per thread,
  * 256 threads (default; needs even nx), 1 = one site per thread, 256 threads,
- * 2 = two sites, 128 threads, 3 = one site, 128 threads.  All variants compute
- * the same arithmetic.  NH_EINVAL if the variant does not fit the domain. */
+ * 2 = two sites, 128 threads, 3 = one site, 128 threads, 4 = four sites,
+ * 128 threads, 5 = four sites, 64 threads (4 and 5 need nx % 4 == 0).  All
+ * variants compute the same arithmetic.  NH_EINVAL if the variant does not fit
+ * the domain. */
 int nh_set_lb_variant(nh_ctx* ctx, int variant);
 
 /* Select the FD kernels: 1 = fused (default): one 2.5D shared-memory kernel

@@ -21,6 +21,8 @@
 
 #include "nh_internal.cuh"
 
+#include <string.h>
+
 namespace nh {
 
 constexpr int kLBThreads = 256;
@@ -88,6 +90,70 @@ __device__ __forceinline__ void store2(Store* p, Real a, Real b, float scale)
     *reinterpret_cast<typename Vec2<Store>::T*>(p) = v;
 }
 
+// Four consecutive sites (16-byte aligned for FP32, 8-byte for the 16-bit stores).
+template <typename Store>
+__device__ __forceinline__ float2 vec2_to_float2(typename Vec2<Store>::T v)
+{
+    if constexpr (std::is_same<Store, __half>::value)
+        return __half22float2(v);
+    else
+        return __bfloat1622float2(v);
+}
+
+template <typename Store, typename Real>
+__device__ __forceinline__ void load4(const Store* p, float inv, Real v[4])
+{
+    if constexpr (sizeof(Store) == 2) {
+        using V2 = typename Vec2<Store>::T;
+        const uint2 raw = *reinterpret_cast<const uint2*>(p);
+        V2 lo, hi;
+        memcpy(&lo, &raw.x, 4);
+        memcpy(&hi, &raw.y, 4);
+        const float2 a = vec2_to_float2<Store>(lo), b = vec2_to_float2<Store>(hi);
+        v[0] = a.x * inv;
+        v[1] = a.y * inv;
+        v[2] = b.x * inv;
+        v[3] = b.y * inv;
+    } else if constexpr (std::is_same<Store, float>::value) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[0] = q.x;
+        v[1] = q.y;
+        v[2] = q.z;
+        v[3] = q.w;
+    } else {
+        const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+        v[0] = a.x;
+        v[1] = a.y;
+        v[2] = b.x;
+        v[3] = b.y;
+    }
+}
+
+template <typename Store, typename Real>
+__device__ __forceinline__ void store4(Store* p, const Real v[4], float scale)
+{
+    if constexpr (std::is_same<Store, __half>::value || std::is_same<Store, __nv_bfloat16>::value) {
+        using V2 = typename Vec2<Store>::T;
+        V2 lo, hi;
+        if constexpr (std::is_same<Store, __half>::value) {
+            lo = __floats2half2_rn(v[0] * scale, v[1] * scale);
+            hi = __floats2half2_rn(v[2] * scale, v[3] * scale);
+        } else {
+            lo = __floats2bfloat162_rn(v[0] * scale, v[1] * scale);
+            hi = __floats2bfloat162_rn(v[2] * scale, v[3] * scale);
+        }
+        uint2 raw;
+        memcpy(&raw.x, &lo, 4);
+        memcpy(&raw.y, &hi, 4);
+        *reinterpret_cast<uint2*>(p) = raw;
+    } else if constexpr (std::is_same<Store, float>::value) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+    }
+}
+
 // One tile (one thread block's worth of sites) of one channel.  `tile` is the
 // tile index within the channel and `ntiles` the channel's tile count (used by
 // the 16-bit scale controller to find the channel's last tile).  Solid: the
@@ -148,6 +214,34 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
                 continue;
             }
             const Store* plane = c.fsrc + (size_t)(bb ? OPP[i] : i) * N;
+            if constexpr (SPT == 4) {
+                // four sites of a row (nx % 4 == 0): aligned 4-site chunks of the
+                // source row; e_x = +-1 reads two chunks and selects
+                Real a[4];
+                if (EX[i] == 0 || bb) {
+                    load4(plane + (bb ? s0 : s0 + row), inv_in, a);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) f[j][i] = a[j];
+                } else {
+                    const Store* src = plane + s0 + row;  // chunk x0 .. x0 + 3 of the source row
+                    Real b[4];
+                    load4(src, inv_in, a);
+                    if (EX[i] > 0) {  // sources x0 - 1 .. x0 + 2
+                        load4(src + (x0 == 0 ? nx - 4 : -4), inv_in, b);
+                        f[0][i] = b[3];
+                        f[1][i] = a[0];
+                        f[2][i] = a[1];
+                        f[3][i] = a[2];
+                    } else {  // sources x0 + 1 .. x0 + 4
+                        load4(src + (x0 + 4 == nx ? -(nx - 4) : 4), inv_in, b);
+                        f[0][i] = a[1];
+                        f[1][i] = a[2];
+                        f[2][i] = a[3];
+                        f[3][i] = b[0];
+                    }
+                }
+                continue;
+            }
             if (SPT == 2 && EX[i] == 0) {
                 load2(plane + (bb ? s0 : s0 + row), inv_in, f[0][i], f[SPT - 1][i]);
             } else {
@@ -246,7 +340,10 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
             Store* dst = c.fdst + (size_t)i * N + s0;
-            if (SPT == 2) {
+            if constexpr (SPT == 4) {
+                const Real v[4] = {fo[0][i], fo[1][i], fo[2][i], fo[3][i]};
+                store4(dst, v, scale_out);
+            } else if (SPT == 2) {
                 store2(dst, fo[0][i], fo[SPT - 1][i], scale_out);
             } else {
                 Codec<Store, Real>::store(dst, fo[0][i], scale_out);
@@ -312,12 +409,12 @@ __global__ void __launch_bounds__(kLBThreads) lb_batch_kernel(const LBBatch<Real
 struct LBVariantShape {
     int spt, threads;
 };
-constexpr LBVariantShape kLBVariants[kLBVariantCount] = {{2, 256}, {1, 256}, {2, 128}, {1, 128}};
+constexpr LBVariantShape kLBVariants[kLBVariantCount] = {{2, 256}, {1, 256}, {2, 128}, {1, 128}, {4, 128}, {4, 64}};
 
 bool lb_variant_valid(int variant, int nx)
 {
     if (variant < 0 || variant >= kLBVariantCount) return false;
-    return kLBVariants[variant].spt == 1 || nx % 2 == 0;
+    return nx % kLBVariants[variant].spt == 0;
 }
 
 template <typename Real, typename Store, bool Shifted, bool WriteMacro>
@@ -330,7 +427,9 @@ cudaError_t launch_lb_spt(const LBChan<Real, Store>& c, int variant, cudaStream_
     const LBVariantShape v = kLBVariants[variant];
     const int threads_needed = (c.g.N + v.spt - 1) / v.spt;
     const int blocks = (threads_needed + v.threads - 1) / v.threads;
-    if (v.spt == 2)
+    if (v.spt == 4)
+        lb_kernel<Real, Store, Shifted, WriteMacro, 4><<<blocks, v.threads, 0, st>>>(c);
+    else if (v.spt == 2)
         lb_kernel<Real, Store, Shifted, WriteMacro, 2><<<blocks, v.threads, 0, st>>>(c);
     else
         lb_kernel<Real, Store, Shifted, WriteMacro, 1><<<blocks, v.threads, 0, st>>>(c);
@@ -359,7 +458,9 @@ cudaError_t launch_lb_batch_spt(LBBatch<Real, Store>& b, int variant, int grid, 
         b.prefix[k + 1] = b.prefix[k] + (threads_needed + v.threads - 1) / v.threads;
     }
     const int blocks = grid < b.prefix[b.count] ? grid : b.prefix[b.count];
-    if (v.spt == 2)
+    if (v.spt == 4)
+        lb_batch_kernel<Real, Store, Shifted, WriteMacro, 4><<<blocks, v.threads, 0, st>>>(b);
+    else if (v.spt == 2)
         lb_batch_kernel<Real, Store, Shifted, WriteMacro, 2><<<blocks, v.threads, 0, st>>>(b);
     else
         lb_batch_kernel<Real, Store, Shifted, WriteMacro, 1><<<blocks, v.threads, 0, st>>>(b);

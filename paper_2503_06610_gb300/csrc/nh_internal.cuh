@@ -179,7 +179,7 @@ struct FDBatch {
 };
 
 // LB launch variants (sites per thread x block size); variant 0 is the default.
-constexpr int kLBVariantCount = 4;
+constexpr int kLBVariantCount = 6;
 bool lb_variant_valid(int variant, int nx);
 template <typename Real, typename Store>
 cudaError_t launch_lb(const LBChan<Real, Store>& c, bool shifted, bool write_macro, int variant, cudaStream_t s);

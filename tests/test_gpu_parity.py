@@ -361,7 +361,7 @@ def test_lb_variants_agree_and_autotune_keeps_state(nh, oracle_mod, nx):
     params = _generic(nx, 6, 5, dt_fd=2)
     n0 = I.tilted_director(nx, 6, 5, amplitude=0.3, seed=4)
     ref = _oracle_sim(O, params, n0).step(9)
-    variants = [0, 1, 2, 3] if nx % 2 == 0 else [1, 3]
+    variants = [v for v, spt in enumerate((2, 1, 2, 1, 4, 4)) if nx % spt == 0]
     for v in variants:
         ch = _channel(nh, params, n0, precision="fp64")
         ch.set_lb_variant(v)
@@ -780,13 +780,14 @@ def test_degenerate_lattices_fp64(nh, oracle_mod, dims, walls, fused):
 @pytest.mark.parametrize("storage", ["f32", "f16s", "bf16s"])
 @pytest.mark.parametrize("dims,walls", [((6, 5, 7), True), ((64, 4, 3), False), ((16, 6, 5), True)])
 def test_lb_launch_shapes_bitwise_equal(nh, storage, dims, walls):
-    """The two-site shapes (neighbour values by warp shuffle inside a row, scalar
-    loads at row ends, warp edges and the grid's last partial warp) read the same
-    values as the one-site shapes: identical populations and fields."""
+    """The two- and four-site shapes (vector loads of aligned pairs or 4-site
+    chunks, with the e_x = +-1 sources selected from two chunks, row ends
+    wrapped) read the same values as the one-site shapes: identical populations
+    and fields."""
     params = _generic(*dims, walls_z=walls, dt_fd=3)
     n0 = I.tilted_director(*dims, amplitude=0.3, seed=5)
     out = []
-    for v in (0, 1, 2, 3):
+    for v in [v for v, spt in enumerate((2, 1, 2, 1, 4, 4)) if dims[0] % spt == 0]:
         ch = _channel(nh, params, n0, precision="fp32", storage=storage)
         ch.set_lb_variant(v)
         ch.step(10)
