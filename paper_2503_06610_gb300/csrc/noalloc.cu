@@ -19,12 +19,13 @@
 
 namespace {
 
-constexpr int kNoallocMaxBlocks = NH_NOALLOC_MAX_ITEMS / 256;  // one partial row per 256 work items
+constexpr int kNoallocMaxBlocks = NH_NOALLOC_MAX_ITEMS / 256;  // at most 1024 reduction blocks
 constexpr int kNoallocValues = 6;                               // mass, energy, max|u|, min|n|, max|n|, nonfinite
 
-// Per-block partial results of the reduction.  Every GPU that loads the
-// library holds this array (48 KiB) until the process exits.  Each block
-// overwrites its own row, so nothing needs clearing between calls.
+// Per-block partial results of the reduction (value-major: value k of block b
+// at k * blocks + b).  Every GPU that loads the library holds this array
+// (48 KiB) until the process exits.  Each block overwrites its own entries,
+// so nothing needs clearing between calls.
 static __device__ __align__(256) double g_noalloc_partials[kNoallocMaxBlocks * kNoallocValues];
 
 constexpr int kMaxDevices = 64;
