@@ -553,6 +553,23 @@ __device__ __forceinline__ void gather_slots(const Real* lo, const Real* mid, co
 
 __device__ __forceinline__ bool is_ghost_plane(const Geom& g, int p) { return g.walls && (p < 0 || p >= g.nz); }
 
+// The kP1 points of a 1-halo plane in an order where a warp takes kTX = 32
+// consecutive columns of one row (contiguous in shared memory, no bank
+// conflicts): t < kHY1 * kTX -> row t / kTX, column t % kTX; the remaining
+// 2 * kHY1 points are the two last columns of every row.
+constexpr int kP1Main = kHY1 * kTX;
+__device__ __forceinline__ void p1_point(int t, int& hx1, int& hy1)
+{
+    if (t < kP1Main) {
+        hy1 = t / kTX;
+        hx1 = t % kTX;
+    } else {
+        const int e = t - kP1Main;
+        hy1 = e >> 1;
+        hx1 = kTX + (e & 1);
+    }
+}
+
 // Kernel A tile: predictor on plane p into ring slot [nP x3 | rate x3] x kP1.
 template <typename Real>
 __device__ void predict_plane(const FDPar<Real>& par, Real* in, int p, Real* pslot)
@@ -560,8 +577,10 @@ __device__ void predict_plane(const FDPar<Real>& par, Real* in, int p, Real* psl
     const Real* lo = in + slot4(p - 1) * 6 * kP2;
     const Real* mid = in + slot4(p) * 6 * kP2;
     const Real* hi = in + slot4(p + 1) * 6 * kP2;
-    for (int i1 = threadIdx.x; i1 < kP1; i1 += blockDim.x) {
-        const int hx1 = i1 % kHX1, hy1 = i1 / kHX1;
+    for (int t = threadIdx.x; t < kP1; t += blockDim.x) {
+        int hx1, hy1;
+        p1_point(t, hx1, hy1);
+        const int i1 = hx1 + kHX1 * hy1;
         const int i2 = (hx1 + 1) + kHX2 * (hy1 + 1);
         Real nn[7][3], uu[7][3], r[3];
         gather_slots(lo, mid, hi, i2, nn, uu);
@@ -659,8 +678,10 @@ __device__ void stress_plane(const FDChan<Real>& c, Real* in, int p, Real* sslot
     const Real* lo = in + slot4(p - 1) * 6 * kP2;
     const Real* mid = in + slot4(p) * 6 * kP2;
     const Real* hi = in + slot4(p + 1) * 6 * kP2;
-    for (int i1 = threadIdx.x; i1 < kP1; i1 += blockDim.x) {
-        const int hx1 = i1 % kHX1, hy1 = i1 / kHX1;
+    for (int t = threadIdx.x; t < kP1; t += blockDim.x) {
+        int hx1, hy1;
+        p1_point(t, hx1, hy1);
+        const int i1 = hx1 + kHX1 * hy1;
         const int i2 = (hx1 + 1) + kHX2 * (hy1 + 1);
         Real nn[7][3], uu[7][3], sig[9];
         gather_slots(lo, mid, hi, i2, nn, uu);
