@@ -178,6 +178,11 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
         const int y = r % ny;
         const int z = r / ny;
         const float inv_in = kScaled ? 1.f / c.scales[c.src] : 1.f;
+        // 16-bit stores: the populations are read raw (still scaled by 2^k) and
+        // the power-of-two factors inv_in and scale_out are folded into the
+        // moments and the collision constants below; products with powers of two
+        // are exact, so the results equal decoding, colliding and re-encoding
+        const float ld = 1.f;
         const int plane_xy = nx * ny;
 
         // site deltas of the pull sources x - e (periodic in x and y; in z
@@ -210,7 +215,7 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
                 const int k = back ? OPP[i] : i;
                 f[0][i] = Codec<Store, Real>::load(c.fsrc + (size_t)(solid_here ? i : k) * N +
                                                        (solid_here || back ? s0 : src),
-                                                   inv_in);
+                                                   ld);
                 continue;
             }
             const Store* plane = c.fsrc + (size_t)(bb ? OPP[i] : i) * N;
@@ -219,21 +224,21 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
                 // source row; e_x = +-1 reads two chunks and selects
                 Real a[4];
                 if (EX[i] == 0 || bb) {
-                    load4(plane + (bb ? s0 : s0 + row), inv_in, a);
+                    load4(plane + (bb ? s0 : s0 + row), ld, a);
 #pragma unroll
                     for (int j = 0; j < 4; ++j) f[j][i] = a[j];
                 } else {
                     const Store* src = plane + s0 + row;  // chunk x0 .. x0 + 3 of the source row
                     Real b[4];
-                    load4(src, inv_in, a);
+                    load4(src, ld, a);
                     if (EX[i] > 0) {  // sources x0 - 1 .. x0 + 2
-                        load4(src + (x0 == 0 ? nx - 4 : -4), inv_in, b);
+                        load4(src + (x0 == 0 ? nx - 4 : -4), ld, b);
                         f[0][i] = b[3];
                         f[1][i] = a[0];
                         f[2][i] = a[1];
                         f[3][i] = a[2];
                     } else {  // sources x0 + 1 .. x0 + 4
-                        load4(src + (x0 + 4 == nx ? -(nx - 4) : 4), inv_in, b);
+                        load4(src + (x0 + 4 == nx ? -(nx - 4) : 4), ld, b);
                         f[0][i] = a[1];
                         f[1][i] = a[2];
                         f[2][i] = a[3];
@@ -243,12 +248,12 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
                 continue;
             }
             if (SPT == 2 && EX[i] == 0) {
-                load2(plane + (bb ? s0 : s0 + row), inv_in, f[0][i], f[SPT - 1][i]);
+                load2(plane + (bb ? s0 : s0 + row), ld, f[0][i], f[SPT - 1][i]);
             } else {
 #pragma unroll
                 for (int j = 0; j < SPT; ++j) {
                     const int dx = EX[i] > 0 ? dxm[j] : (EX[i] < 0 ? dxp[j] : 0);
-                    f[j][i] = Codec<Store, Real>::load(plane + (bb ? s0 + j : s0 + j + row + dx), inv_in);
+                    f[j][i] = Codec<Store, Real>::load(plane + (bb ? s0 + j : s0 + j + row + dx), ld);
                 }
             }
         }
@@ -256,7 +261,7 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
         Real fo[SPT][19];
         if (solid_here) {
 #pragma unroll
-            for (int i = 0; i < 19; ++i) fo[0][i] = f[0][i];
+            for (int i = 0; i < 19; ++i) fo[0][i] = kScaled ? f[0][i] * Real(inv_in * scale_out) : f[0][i];
             if (WriteMacro) {
                 c.u[s0] = Real(0);
                 c.u[N + s0] = Real(0);
@@ -278,6 +283,12 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
                 if (EX[i] != 0) mx += EX[i] > 0 ? d : -d;
                 if (EY[i] != 0) my += EY[i] > 0 ? d : -d;
                 if (EZ[i] != 0) mz += EZ[i] > 0 ? d : -d;
+            }
+            if (kScaled) {  // raw populations: scale the sums once
+                sum *= Real(inv_in);
+                mx *= Real(inv_in);
+                my *= Real(inv_in);
+                mz *= Real(inv_in);
             }
             const Real rho = Shifted ? Real(1) + sum : sum;
             const Real drho = Shifted ? sum : sum - Real(1);
@@ -305,9 +316,12 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
             //   f^eq = w rho [3 eu + 4.5 eu^2 - 1.5 u.u] + w (rho - 1 | rho)
             //   S    = w [3 eF + 9 eu eF - 3 u.F]
             //   f*   = (1 - omega) f + omega f^eq + (1 - omega/2) S
-            const Real omega = c.omega;
-            const Real omc = Real(1) - omega;
-            const Real cS = Real(1) - Real(0.5) * omega;
+            // with a 16-bit store the constants carry scale_out (and omc the raw
+            // input's inv_in), so fo[] leaves here already in encoded units
+            const Real so = kScaled ? Real(scale_out) : Real(1);
+            const Real omega = c.omega * so;
+            const Real omc = (Real(1) - c.omega) * (kScaled ? Real(inv_in) * so : Real(1));
+            const Real cS = (Real(1) - Real(0.5) * c.omega) * so;
             const Real uu15 = Real(1.5) * (ux * ux + uy * uy + uz * uz);
             const Real uF3 = Real(3) * (ux * Fx + uy * Fy + uz * Fz);
             const Real base = Shifted ? drho : rho;
@@ -335,6 +349,7 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
                 for (int i = 0; i < 19; ++i) amax = fmaxf(amax, fabsf((float)fo[j][i]));
             }
         }
+        if (kScaled) amax /= scale_out;  // back to population units for the controller
 
         // store (aligned 2-site vectors when SPT = 2)
 #pragma unroll
@@ -342,11 +357,11 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
             Store* dst = c.fdst + (size_t)i * N + s0;
             if constexpr (SPT == 4) {
                 const Real v[4] = {fo[0][i], fo[1][i], fo[2][i], fo[3][i]};
-                store4(dst, v, scale_out);
+                store4(dst, v, kScaled ? 1.f : scale_out);
             } else if (SPT == 2) {
-                store2(dst, fo[0][i], fo[SPT - 1][i], scale_out);
+                store2(dst, fo[0][i], fo[SPT - 1][i], kScaled ? 1.f : scale_out);
             } else {
-                Codec<Store, Real>::store(dst, fo[0][i], scale_out);
+                Codec<Store, Real>::store(dst, fo[0][i], kScaled ? 1.f : scale_out);
             }
         }
     }
