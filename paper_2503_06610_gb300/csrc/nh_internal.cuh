@@ -119,7 +119,7 @@ struct FDPar {
 //   df = kd1/2 div^2 + kd2/2 t^2 + kd3/2 (|n|^2 |w|^2 - (n.w)^2).
 // Writes dfdn[c] = d df/d n_c and P[b][c] = d df/d G_bc; returns df.
 template <typename Real>
-__host__ __device__ __forceinline__ Real frank3_site(const Real n[3], const Real G[3][3], Real kd1, Real kd2, Real kd3,
+__device__ __forceinline__ Real frank3_site(const Real n[3], const Real G[3][3], Real kd1, Real kd2, Real kd3,
                                                     Real q0, Real dfdn[3], Real P[3][3])
 {
     const Real div = G[0][0] + G[1][1] + G[2][2];

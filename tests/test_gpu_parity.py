@@ -322,12 +322,19 @@ def test_nonfinite_detected(nh):
 
 # ------------------------------------------------------------------ full-size checks (bench configuration)
 
-def test_full_size_multi_tube_one_lb_step(nh, oracle_mod):
-    """256x256x64, FP32-shifted, dt_FD = 16: after 16 steps, one more LB step on
-    the GPU equals the oracle's LB step applied to the GPU's own state."""
+@pytest.mark.parametrize("shape", ["autotuned", 4])
+def test_full_size_multi_tube_one_lb_step(nh, oracle_mod, shape):
+    """256x256x64, FP32-shifted, dt_FD = 16, in the launch configuration the
+    bench times (autotuned) and with the four-site shape: after 16 steps, one
+    more LB step on the GPU equals the oracle's LB step applied to the GPU's
+    own state."""
     O = oracle_mod
     params, n0, centres = I.multi_tube_channel()
     ch = _channel(nh, params, n0, precision="fp32")
+    if shape == "autotuned":
+        ch.autotune()
+    else:
+        ch.set_lb_variant(shape)
     ch.step(16)
     f = ch.get_populations()
     F = ch.get_force()
