@@ -435,8 +435,9 @@ __global__ void __launch_bounds__(256) fd_batch_kernel(const FDBatch<Real> b)
 // ------------------------------------------------------------------ fused 2.5D kernels
 //
 // A block owns a tile of kTX x kTY columns and marches up a chunk of kZC
-// layers.  Planes of n and u with a 2-site halo in x and y sit in a ring of 4
-// shared-memory slots; the predictor (kernel A) or the stress (kernel B) is
+// layers.  Planes of n and u with a 2-site halo in x and y sit in a ring of
+// shared-memory slots (4 in kernel A, whose corrector also reads u one layer
+// below, 3 in kernel B); the predictor (kernel A) or the stress (kernel B) is
 // evaluated on each plane with a 1-site halo into a ring of 3 slots, so every
 // stencil reads shared memory at fixed offsets and the ghost layers are
 // resolved once, at load time.
@@ -459,7 +460,7 @@ __device__ __forceinline__ int slot3(int p) { return ((p % 3) + 3) % 3; }
 template <typename Real>
 size_t fused_a_smem() { return (size_t)(4 * 6 * kP2 + 3 * 6 * kP1) * sizeof(Real); }
 template <typename Real>
-size_t fused_b_smem() { return (size_t)(4 * 6 * kP2 + 3 * 9 * kP1) * sizeof(Real); }
+size_t fused_b_smem() { return (size_t)(3 * 6 * kP2 + 3 * 9 * kP1) * sizeof(Real); }
 
 // Each thread owns at most kPts points of a P2 plane (indices threadIdx.x +
 // k * blockDim.x); their wrapped x-y site offsets are computed once per tile.
@@ -667,7 +668,8 @@ __device__ void fused_a_tile(const FDChan<Real>& c, const Real* __restrict__ nin
     }
 }
 
-// Kernel B tile: stress on plane p into ring slot [sigma x9] x kP1 (zero at ghosts).
+// Kernel B tile: stress on plane p into ring slot [sigma x9] x kP1 (zero at
+// ghosts), from planes p - 1, p, p + 1 of the 3-slot input ring.
 template <typename Real>
 __device__ void stress_plane(const FDChan<Real>& c, Real* in, int p, Real* sslot)
 {
@@ -675,9 +677,9 @@ __device__ void stress_plane(const FDChan<Real>& c, Real* in, int p, Real* sslot
         for (int i = threadIdx.x; i < 9 * kP1; i += blockDim.x) sslot[i] = Real(0);
         return;
     }
-    const Real* lo = in + slot4(p - 1) * 6 * kP2;
-    const Real* mid = in + slot4(p) * 6 * kP2;
-    const Real* hi = in + slot4(p + 1) * 6 * kP2;
+    const Real* lo = in + slot3(p - 1) * 6 * kP2;
+    const Real* mid = in + slot3(p) * 6 * kP2;
+    const Real* hi = in + slot3(p + 1) * 6 * kP2;
     for (int t = threadIdx.x; t < kP1; t += blockDim.x) {
         int hx1, hy1;
         p1_point(t, hx1, hy1);
@@ -695,8 +697,8 @@ template <typename Real>
 __device__ void fused_b_tile(const FDChan<Real>& c, const Real* __restrict__ nin, Real* __restrict__ ncopy, int tile)
 {
     extern __shared__ __align__(16) unsigned char smem_fd[];
-    Real* in = reinterpret_cast<Real*>(smem_fd);  // 4 slots x 6 x kP2
-    Real* sg = in + 4 * 6 * kP2;                  // 3 slots x 9 x kP1
+    Real* in = reinterpret_cast<Real*>(smem_fd);  // 3 slots x 6 x kP2 (planes z, z + 1, z + 2)
+    Real* sg = in + 3 * 6 * kP2;                  // 3 slots x 9 x kP1
     const Geom& g = c.g;
     const int ntx = (g.nx + kTX - 1) / kTX, nty = (g.ny + kTY - 1) / kTY;
     const int tx_t = tile % ntx, ty_t = (tile / ntx) % nty, zc = tile / (ntx * nty);
@@ -707,16 +709,21 @@ __device__ void fused_b_tile(const FDChan<Real>& c, const Real* __restrict__ nin
     const size_t N = (size_t)g.N;
     const PlaneMap pm = plane_map(g, x0, y0);
     Real v[kPts][6];
-    for (int p = zb - 2; p <= zb + 1; ++p) {
+    for (int p = zb - 2; p <= zb; ++p) {
         prefetch_plane(nin, c.u, g, pm, p, v);
-        commit_plane(pm, v, in + slot4(p) * 6 * kP2);
+        commit_plane(pm, v, in + slot3(p) * 6 * kP2);
     }
+    prefetch_plane(nin, c.u, g, pm, zb + 1, v);  // in flight during the first stress plane
+    __syncthreads();
+    stress_plane(c, in, zb - 1, sg + slot3(zb - 1) * 9 * kP1);
+    __syncthreads();  // plane zb - 2 is no longer read
+    commit_plane(pm, v, in + slot3(zb + 1) * 6 * kP2);
     prefetch_plane(nin, c.u, g, pm, zb + 2, v);
     __syncthreads();
-    for (int p = zb - 1; p <= zb; ++p) stress_plane(c, in, p, sg + slot3(p) * 9 * kP1);
+    stress_plane(c, in, zb, sg + slot3(zb) * 9 * kP1);
     for (int z = zb; z < ze; ++z) {
-        __syncthreads();
-        commit_plane(pm, v, in + slot4(z + 2) * 6 * kP2);
+        __syncthreads();  // plane z - 1 is no longer read; its slot takes plane z + 2
+        commit_plane(pm, v, in + slot3(z + 2) * 6 * kP2);
         __syncthreads();
         if (z + 1 < ze) prefetch_plane(nin, c.u, g, pm, z + 3, v);
         stress_plane(c, in, z + 1, sg + slot3(z + 1) * 9 * kP1);
@@ -735,7 +742,7 @@ __device__ void fused_b_tile(const FDChan<Real>& c, const Real* __restrict__ nin
                 c.F[a * N + s] = Real(0.5) * (dx + dy + dz);
             }
             if (ncopy) {
-                const Real* inm = in + slot4(z) * 6 * kP2;
+                const Real* inm = in + slot3(z) * 6 * kP2;
                 const int i2 = (tx + 2) + kHX2 * (ty + 2);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) ncopy[a * N + s] = inm[a * kP2 + i2];
