@@ -458,7 +458,7 @@ __device__ __forceinline__ int slot4(int p) { return ((p % 4) + 4) % 4; }
 __device__ __forceinline__ int slot3(int p) { return ((p % 3) + 3) % 3; }
 
 template <typename Real>
-size_t fused_a_smem() { return (size_t)(4 * 6 * kP2 + 3 * 6 * kP1) * sizeof(Real); }
+size_t fused_a_smem() { return (size_t)(3 * 6 * kP2 + 3 * 3 * kP1 + 2 * 3 * kTX * kTY) * sizeof(Real); }
 template <typename Real>
 size_t fused_b_smem() { return (size_t)(3 * 6 * kP2 + 3 * 9 * kP1) * sizeof(Real); }
 
@@ -571,13 +571,16 @@ __device__ __forceinline__ void p1_point(int t, int& hx1, int& hy1)
     }
 }
 
-// Kernel A tile: predictor on plane p into ring slot [nP x3 | rate x3] x kP1.
+// Kernel A tile: predictor on plane p (from planes p - 1, p, p + 1 of the
+// 3-slot input ring) into ring slot [nP x3] x kP1, and its rate at the tile's
+// own kTX x kTY points into rslot [3] x (kTX kTY), the only ones the corrector
+// reads.
 template <typename Real>
-__device__ void predict_plane(const FDPar<Real>& par, Real* in, int p, Real* pslot)
+__device__ void predict_plane(const FDPar<Real>& par, Real* in, int p, Real* pslot, Real* rslot)
 {
-    const Real* lo = in + slot4(p - 1) * 6 * kP2;
-    const Real* mid = in + slot4(p) * 6 * kP2;
-    const Real* hi = in + slot4(p + 1) * 6 * kP2;
+    const Real* lo = in + slot3(p - 1) * 6 * kP2;
+    const Real* mid = in + slot3(p) * 6 * kP2;
+    const Real* hi = in + slot3(p + 1) * 6 * kP2;
     for (int t = threadIdx.x; t < kP1; t += blockDim.x) {
         int hx1, hy1;
         p1_point(t, hx1, hy1);
@@ -586,10 +589,12 @@ __device__ void predict_plane(const FDPar<Real>& par, Real* in, int p, Real* psl
         Real nn[7][3], uu[7][3], r[3];
         gather_slots(lo, mid, hi, i2, nn, uu);
         director_rate(nn, uu, par, r);
+        const bool own = hx1 >= 1 && hx1 <= kTX && hy1 >= 1 && hy1 <= kTY;
+        const int io = (hx1 - 1) + kTX * (hy1 - 1);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             pslot[a * kP1 + i1] = nn[0][a] + par.dt * r[a];
-            pslot[(3 + a) * kP1 + i1] = r[a];
+            if (own) rslot[a * (kTX * kTY) + io] = r[a];
         }
     }
 }
@@ -598,8 +603,9 @@ template <typename Real>
 __device__ void fused_a_tile(const FDChan<Real>& c, const Real* __restrict__ nin, Real* __restrict__ nout, int tile)
 {
     extern __shared__ __align__(16) unsigned char smem_fd[];
-    Real* in = reinterpret_cast<Real*>(smem_fd);  // 4 slots x 6 x kP2
-    Real* pr = in + 4 * 6 * kP2;                  // 3 slots x 6 x kP1
+    Real* in = reinterpret_cast<Real*>(smem_fd);  // 3 slots x 6 x kP2 (input planes)
+    Real* pr = in + 3 * 6 * kP2;                  // 3 slots x 3 x kP1 (predictor n^P)
+    Real* rt = pr + 3 * 3 * kP1;                  // 2 slots x 3 x kTX kTY (predictor rate)
     const Geom& g = c.g;
     const int ntx = (g.nx + kTX - 1) / kTX, nty = (g.ny + kTY - 1) / kTY;
     const int tx_t = tile % ntx, ty_t = (tile / ntx) % nty, zc = tile / (ntx * nty);
@@ -608,36 +614,46 @@ __device__ void fused_a_tile(const FDChan<Real>& c, const Real* __restrict__ nin
     const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
     const bool active = threadIdx.x < kTX * kTY && x0 + tx < g.nx && y0 + ty < g.ny;
     const size_t N = (size_t)g.N;
+    const int i1 = (tx + 1) + kHX1 * (ty + 1);
+    const int i2 = (tx + 2) + kHX2 * (ty + 2);
+    const int io = tx + kTX * ty;
     const PlaneMap pm = plane_map(g, x0, y0);
     Real v[kPts][6];
-    for (int p = zb - 2; p <= zb + 1; ++p) {
+    for (int p = zb - 2; p <= zb; ++p) {
         prefetch_plane(nin, c.u, g, pm, p, v);
-        commit_plane(pm, v, in + slot4(p) * 6 * kP2);
+        commit_plane(pm, v, in + slot3(p) * 6 * kP2);
     }
-    prefetch_plane(nin, c.u, g, pm, zb + 2, v);  // in flight during the prologue predictor
+    prefetch_plane(nin, c.u, g, pm, zb + 1, v);  // in flight during the first predictor plane
     __syncthreads();
-    for (int p = zb - 1; p <= zb; ++p)
-        if (!is_ghost_plane(g, p)) predict_plane(c.p, in, p, pr + slot3(p) * 6 * kP1);
+    if (!is_ghost_plane(g, zb - 1)) predict_plane(c.p, in, zb - 1, pr + slot3(zb - 1) * 3 * kP1, rt + ((zb - 1) & 1) * 3 * kTX * kTY);
+    // u one layer below the corrector's plane, at the thread's own point, carried in registers
+    Real ulo[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ulo[a] = active ? in[slot3(zb - 1) * 6 * kP2 + (3 + a) * kP2 + i2] : Real(0);
+    __syncthreads();  // plane zb - 2 is no longer read
+    commit_plane(pm, v, in + slot3(zb + 1) * 6 * kP2);
+    prefetch_plane(nin, c.u, g, pm, zb + 2, v);
+    __syncthreads();
+    if (!is_ghost_plane(g, zb)) predict_plane(c.p, in, zb, pr + slot3(zb) * 3 * kP1, rt + (zb & 1) * 3 * kTX * kTY);
     for (int z = zb; z < ze; ++z) {
-        __syncthreads();  // slot of plane z - 2 (= z + 2) is free; predictor planes are complete
-        commit_plane(pm, v, in + slot4(z + 2) * 6 * kP2);
+        __syncthreads();  // plane z - 1 is no longer read; its slot takes plane z + 2
+        commit_plane(pm, v, in + slot3(z + 2) * 6 * kP2);
         __syncthreads();
         if (z + 1 < ze) prefetch_plane(nin, c.u, g, pm, z + 3, v);  // overlaps the two evaluations below
-        if (!is_ghost_plane(g, z + 1)) predict_plane(c.p, in, z + 1, pr + slot3(z + 1) * 6 * kP1);
+        if (!is_ghost_plane(g, z + 1))
+            predict_plane(c.p, in, z + 1, pr + slot3(z + 1) * 3 * kP1, rt + ((z + 1) & 1) * 3 * kTX * kTY);
         __syncthreads();
         if (active) {
-            const int i1 = (tx + 1) + kHX1 * (ty + 1);
-            const int i2 = (tx + 2) + kHX2 * (ty + 2);
-            const Real* mid = pr + slot3(z) * 6 * kP1;
+            const Real* mid = pr + slot3(z) * 3 * kP1;
             // predictor of the planes above and below; at a plate the ghost
             // value (z_hat, or the adjacent fluid layer without anchoring)
             const bool glo = is_ghost_plane(g, z - 1), ghi = is_ghost_plane(g, z + 1);
             const bool homeo = g.anchoring == NH_ANCHOR_HOMEOTROPIC;
-            const Real* lo = glo ? mid : pr + slot3(z - 1) * 6 * kP1;
-            const Real* hi = ghi ? mid : pr + slot3(z + 1) * 6 * kP1;
-            const Real* inm = in + slot4(z) * 6 * kP2;
-            const Real* inl = in + slot4(z - 1) * 6 * kP2;
-            const Real* inh = in + slot4(z + 1) * 6 * kP2;
+            const Real* lo = glo ? mid : pr + slot3(z - 1) * 3 * kP1;
+            const Real* hi = ghi ? mid : pr + slot3(z + 1) * 3 * kP1;
+            const Real* inm = in + slot3(z) * 6 * kP2;
+            const Real* inh = in + slot3(z + 1) * 6 * kP2;
+            const Real* rate = rt + (z & 1) * 3 * kTX * kTY;
             Real nn[7][3], uu[7][3], r[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
@@ -654,16 +670,18 @@ __device__ void fused_a_tile(const FDChan<Real>& c, const Real* __restrict__ nin
                 uu[3][a] = inm[(3 + a) * kP2 + i2 + kHX2];
                 uu[4][a] = inm[(3 + a) * kP2 + i2 - kHX2];
                 uu[5][a] = inh[(3 + a) * kP2 + i2];
-                uu[6][a] = inl[(3 + a) * kP2 + i2];
+                uu[6][a] = ulo[a];
             }
             director_rate(nn, uu, c.p, r);
             Real nw[3];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) nw[a] = inm[a * kP2 + i2] + c.p.dt * Real(0.5) * (mid[(3 + a) * kP1 + i1] + r[a]);
+            for (int a = 0; a < 3; ++a) nw[a] = inm[a * kP2 + i2] + c.p.dt * Real(0.5) * (rate[a * kTX * kTY + io] + r[a]);
             const Real inv = Real(1) / sqrt(nw[0] * nw[0] + nw[1] * nw[1] + nw[2] * nw[2]);
             const size_t s = (size_t)(x0 + tx) + (size_t)g.nx * ((size_t)(y0 + ty) + (size_t)g.ny * z);
 #pragma unroll
             for (int a = 0; a < 3; ++a) nout[a * N + s] = nw[a] * inv;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) ulo[a] = uu[0][a];  // u of plane z: the next plane's lower neighbour
         }
     }
 }
