@@ -200,7 +200,7 @@ def evaluate(net, samples, targets, steps_ansatz, test_idx, batch=64, **relax_kw
                 preds[i] = out[k]
     torch.cuda.synchronize()
     t_pred = time.perf_counter() - t0
-    steps_p, wall_p, dn, dn_pred, dn_ans, per = [], 0.0, [], [], [], []
+    steps_p, wall_p, dn, dn_pred, dn_ans, rms_pred, rms_ans, per = [], 0.0, [], [], [], [], [], []
     for b0 in range(0, len(test_idx), batch):
         sub = test_idx[b0:b0 + batch]
         chans = make_channels([samples[i] for i in sub], [preds[i] for i in sub])
@@ -212,7 +212,10 @@ def evaluate(net, samples, targets, steps_ansatz, test_idx, batch=64, **relax_kw
             d = np.abs(n - targets[i]).max(axis=0)
             dn.append(float(d.max()))
             dn_pred.append(float(np.max(np.abs(preds[i] - targets[i]))))
-            dn_ans.append(float(np.max(np.abs(np.asarray(samples[i][1]).reshape(3, -1) - targets[i]))))
+            ans = np.asarray(samples[i][1]).reshape(3, -1)
+            dn_ans.append(float(np.max(np.abs(ans - targets[i]))))
+            rms_pred.append(float(np.sqrt(np.mean(np.sum((preds[i] - targets[i]) ** 2, axis=0)))))
+            rms_ans.append(float(np.sqrt(np.mean(np.sum((ans - targets[i]) ** 2, axis=0)))))
             p = samples[i][0]
             z, y, x = np.unravel_index(int(np.argmax(d)), (p["nz"], p["ny"], p["nx"]))
             per.append({"index": i, "max_dn": dn[-1], "argmax_zyx": [int(z), int(y), int(x)],
@@ -237,7 +240,9 @@ def evaluate(net, samples, targets, steps_ansatz, test_idx, batch=64, **relax_kw
             "wall_s_relax_from_ansatz": wall_a, "wall_ratio": (t_pred + wall_p) / wall_a,
             "max_dn_final": float(np.max(dn)), "frac_final_within_1e-4": float(np.mean(np.array(dn) <= 1e-4)),
             "median_max_dn_prediction_vs_relaxed": float(np.median(dn_pred)),
-            "median_max_dn_ansatz_vs_relaxed": float(np.median(dn_ans)), "per_sample": per}
+            "median_max_dn_ansatz_vs_relaxed": float(np.median(dn_ans)),
+            "median_rms_prediction_vs_relaxed": float(np.median(rms_pred)),
+            "median_rms_ansatz_vs_relaxed": float(np.median(rms_ans)), "per_sample": per}
 
 
 def main():

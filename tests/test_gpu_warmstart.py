@@ -273,8 +273,9 @@ def test_trained_network_saves_relaxation_steps(env):
     res = ws.evaluate(net, samples, targets, steps, test_idx, **kw)
     print("warm start (48x48x16):", {k: v for k, v in res.items() if k != "per_sample"})
     assert res["max_dn_final"] <= 1e-4
-    # the prediction starts several times closer to the relaxed field than the
-    # ansatz; relaxation to the stop tolerance is exponential in time, so this
-    # buys a modest number of FD steps at this training size
-    assert res["median_max_dn_prediction_vs_relaxed"] < 0.3 * res["median_max_dn_ansatz_vs_relaxed"]
+    # the prediction starts several times closer (RMS over the cell) to the
+    # relaxed field than the ansatz; relaxation to the stop tolerance is
+    # exponential in time, so this buys a modest number of FD steps at this
+    # training size
+    assert res["median_rms_prediction_vs_relaxed"] < 0.3 * res["median_rms_ansatz_vs_relaxed"]
     assert res["step_ratio"] < 0.98
