@@ -16,6 +16,8 @@
 
 #include <cstddef>
 
+#include <nvtx3/nvToolsExt.h>
+
 using namespace nh;
 
 // The parameter block is passed by pointer from C and from Python's ctypes:
@@ -248,6 +250,14 @@ int cuda_fail(nh_ctx* c, cudaError_t e, const char* where)
     } while (0)
 
 cudaStream_t pick(nh_ctx* c, void* s) { return s ? static_cast<cudaStream_t>(s) : c->stream; }
+
+// NVTX range around an API call that enqueues GPU work (visible in profilers).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 void drop_batch_plans(const nh_ctx* c);
 
@@ -979,6 +989,7 @@ int nh_bind_workspace(nh_ctx* c, void* dev_ptr, size_t bytes)
 
 int nh_set_fields(nh_ctx* c, const double* n, const double* u, const double* rho, int on_device)
 {
+    NvtxRange range_("nh_set_fields");
     int r = check_ready(c);
     if (r) return r;
     if (!n) return fail(c, NH_EINVAL, "director n is required");
@@ -1157,6 +1168,7 @@ int nh_restore(nh_ctx* c, const double* n, const double* F, const double* u, con
 
 int nh_step(nh_ctx* c, int64_t n_lb_steps, void* stream)
 {
+    NvtxRange range_("nh_step");
     int r = check_ready(c);
     if (r) return r;
     if (!c->fields_set) return fail(c, NH_EINVAL, "nh_set_fields must be called before nh_step");
@@ -1188,6 +1200,7 @@ int nh_step(nh_ctx* c, int64_t n_lb_steps, void* stream)
 
 int nh_fd_update(nh_ctx* c, void* stream)
 {
+    NvtxRange range_("nh_fd_update");
     int r = check_ready(c);
     if (r) return r;
     if (!c->fields_set) return fail(c, NH_EINVAL, "nh_set_fields must be called before nh_fd_update");
@@ -1199,6 +1212,7 @@ int nh_fd_update(nh_ctx* c, void* stream)
 
 int nh_batch_step(nh_ctx* const* ctxs, int count, int64_t n_lb_steps, void* stream)
 {
+    NvtxRange range_("nh_batch_step");
     BatchPlan* plan = nullptr;
     int r = batch_prepare(ctxs, count, n_lb_steps, &plan);
     if (r) return r;
@@ -1277,6 +1291,7 @@ int nh_batch_autotune(nh_ctx* const* ctxs, int count, void* stream, int* chosen)
 
 int nh_relax(nh_ctx* c, int64_t n_fd_steps, void* stream)
 {
+    NvtxRange range_("nh_relax");
     int r = check_ready(c);
     if (r) return r;
     if (!c->fields_set) return fail(c, NH_EINVAL, "nh_set_fields must be called before nh_relax");
@@ -1297,6 +1312,7 @@ int nh_relax(nh_ctx* c, int64_t n_fd_steps, void* stream)
 
 int nh_batch_relax(nh_ctx* const* ctxs, int count, int64_t n_fd_steps, void* stream)
 {
+    NvtxRange range_("nh_batch_relax");
     BatchPlan* plan = nullptr;
     int r = batch_prepare_relax(ctxs, count, n_fd_steps, &plan);
     if (r) return r;
@@ -1399,6 +1415,7 @@ int nh_set_tubes(nh_ctx* c, const double* centres, int count)
 
 int nh_diagnostics_enqueue(nh_ctx* c, void* stream)
 {
+    NvtxRange range_("nh_diagnostics_enqueue");
     int r = check_ready(c);
     if (r) return r;
     if ((r = set_device(c))) return r;

@@ -802,3 +802,37 @@ def test_lb_launch_shapes_bitwise_equal(nh, storage, dims, walls):
     for other in out[1:]:
         for a, b in zip(out[0], other):
             assert np.array_equal(a, b)
+
+
+# ------------------------------------------------------------------ auxiliary: run records, error paths
+
+def test_run_records_jsonl(nh, tmp_path):
+    import json
+    from paper_2503_06610_gb300 import runlog
+    params = _generic(16, 12, 8, dt_fd=4)
+    n0 = I.skyrmion_tubes(16, 12, 8, [(8.0, 6.0)], 4.0)
+    ch = _channel(nh, params, n0, precision="fp32")
+    ch.set_tubes([(8.0, 6.0)])
+    path = tmp_path / "run.jsonl"
+    recs = runlog.run(ch, 3, path=str(path))
+    lines = [json.loads(l) for l in open(path)]
+    assert lines == json.loads(json.dumps(recs)) and len(lines) == 3
+    assert [r["step"] for r in lines] == [4, 8, 12]
+    assert all(r["nonfinite"] == 0 and r["mlups"] > 0 for r in lines)
+    assert max(abs(r["mass"] - lines[0]["mass"]) for r in lines) < 1e-6 * ch.N
+    assert len(lines[-1]["centroids"]) == 1
+
+
+def test_workspace_too_small_is_enomem(nh):
+    import torch
+    p = nh.make_params(dict(_generic(8, 8, 8), precision="fp32"))
+    need = nh.nh_workspace_bytes(p)
+    ctx = nh.nh_create(p, torch.cuda.current_stream().cuda_stream)
+    try:
+        buf = torch.empty(need, dtype=torch.uint8, device="cuda")
+        aligned = (buf.data_ptr() + 255) // 256 * 256
+        with pytest.raises(nh.NHError) as e:
+            nh.nh_bind_workspace(ctx, aligned, need // 2)
+        assert e.value.code == nh.NH_ENOMEM
+    finally:
+        nh.nh_destroy(ctx)
