@@ -238,8 +238,8 @@ int nh_director_change(nh_ctx* ctx, double* max_change);
  * centred.  Populations and F_lc are not updated.  Asynchronous. */
 int nh_symmetrize_c4(nh_ctx* ctx);
 
-/* Obstacles (Sec. II.B: "on solid boundaries, including obstacles,
- * infinite homeotropic anchoring and no-slip ... bounce-back"): mask[N]
+/* Obstacles (Sec. II.B: solid boundaries, obstacles included, carry infinite
+ * homeotropic anchoring and no-slip by bounce-back): mask[N]
  * (host, or device when on_device = 1) with 1 at solid nodes, 0 at fluid
  * nodes, site index x + nx*(y + ny*z); NULL removes the obstacles.  A lattice
  * link from a fluid site to a solid node bounces back half-way, like the
@@ -347,7 +347,7 @@ int nh_diagnostics_noalloc(const nh_params* p, const void* f, const void* n, con
                            double* out, void* stream);
 
 /* ------------------------------------------------------------------------
- * Learned warm start (spec axis 4): a 3D U-Net (4 levels, widths
+ * Learned warm start (no counterpart in the paper): a 3D U-Net (4 levels, widths
  * 16/16/32/64, 394 419 parameters) that maps the extruded skyrmion ansatz and
  * the channel parameters (q0, Lz, W0) to the relaxed director; the plain
  * relaxation (nh_relax) continues from its prediction and judges it.

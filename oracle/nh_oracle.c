@@ -35,7 +35,7 @@
  *     n = z_hat (infinite homeotropic anchoring) or n = adjacent fluid layer
  *     (no anchoring); stress = 0 at the ghosts;
  *   - the FD update renormalises n after the corrector only;
- *   - obstacles (solid nodes): a link from a fluid site to a solid
+ *   - obstacles (solid nodes, Sec. II.B): a link from a fluid site to a solid
  *     one bounces back half-way like the plates; solid nodes keep their
  *     director (infinite anchoring: the caller stores the surface normal
  *     there), their velocity is zero and their stress is zero; their

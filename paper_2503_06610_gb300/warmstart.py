@@ -1,4 +1,4 @@
-"""Learned warm start for skyrmion-tube relaxations (spec axis 4).
+"""Learned warm start for skyrmion-tube relaxations.
 
 The plain method relaxes an extruded skyrmion ansatz by the director-only
 gradient flow (``nh_relax``: the predictor-corrector of Sec. II.B at u = 0)

@@ -666,7 +666,7 @@ def test_frank3_rejects_fused_and_batches(nh):
         nh.Channel(dict(params, K22=0.0, precision="fp32"))
 
 
-# ------------------------------------------------------------------ obstacles (solid nodes)
+# ------------------------------------------------------------------ obstacles (solid nodes, Sec. II.B)
 
 def _sphere_mask(nx, ny, nz, c, r):
     z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")

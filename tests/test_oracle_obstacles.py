@@ -1,5 +1,5 @@
 """Pins of the oracle's obstacles (solid nodes with bounce-back and fixed,
-infinitely anchored directors; P:L135 of arXiv:2503.06610, Sec. II.B).
+infinitely anchored directors; arXiv:2503.06610, Sec. II.B).
 
 * A channel whose plates are two layers of solid nodes normal to y, in a box
   periodic in every direction, is the z-plate channel (already pinned against
