@@ -836,3 +836,67 @@ def test_workspace_too_small_is_enomem(nh):
         assert e.value.code == nh.NH_ENOMEM
     finally:
         nh.nh_destroy(ctx)
+
+
+# ------------------------------------------------------------------ combinations of the reading flags
+
+@pytest.mark.parametrize("storage,tol", [("f16s", 3e-3), ("bf16s", 3e-2)])
+def test_paper_order_with_16bit_stores(nh, oracle_mod, storage, tol):
+    """paper_order runs the LB step of an FD interval twice (the scale controller
+    with it); the 16-bit stores stay within their usual error of the oracle."""
+    O = oracle_mod
+    params, n0 = I.tiny_channel()
+    params = dict(params, dt_fd=4, paper_order=True)
+    ref = _oracle_sim(O, params, n0).step(400)
+    ch = _channel(nh, params, n0, precision="fp32", storage=storage, shifted=True)
+    ch.step(400)
+    n, u, _ = ch.get_fields()
+    assert O.rel_l2(u, ref.u) <= tol
+    assert O.rel_l2(n, ref.n) <= tol
+
+
+def test_paper_order_with_obstacle_and_frank3_fp64(nh, oracle_mod):
+    O = oracle_mod
+    nx, ny, nz = 18, 12, 8
+    mask, normals = _sphere_mask(nx, ny, nz, (9.0, 6.0, 4.0), 2.6)
+    params = _generic(nx, ny, nz, dt_fd=3, K=0.03, K11=0.045, K22=0.015, K33=0.06, q0=0.5, W0=0.002,
+                      g=(1e-4, 0.0, 0.0), paper_order=True)
+    n0 = I.tilted_director(nx, ny, nz, amplitude=0.3, seed=8)
+    n0[:, mask == 1] = normals[:, mask == 1]
+    ref = O.OracleSim(O.OracleParams.from_dict(dict(params, solid=mask)), n0).step(17)
+    ch = nh.Channel(dict(params, precision="fp64"))
+    ch.set_solid(mask)
+    ch.set_fields(n0)
+    ch.step(17)
+    n, u, _ = ch.get_fields()
+    fl = mask == 0
+    assert O.rel_l2(n, ref.n) <= 1e-12
+    assert O.rel_l2(u[:, fl], ref.u[:, fl]) <= 1e-10
+    assert np.max(np.abs(ch.get_populations() - ref.f)) < 1e-14
+
+
+@pytest.mark.parametrize("case", ["obstacle", "frank3"])
+def test_relax_with_obstacle_or_frank3_fp64(nh, oracle_mod, case):
+    """Director-only relaxation on the per-site kernels: the predictor-corrector
+    at u = 0 of the oracle, with an obstacle (held directors) or the
+    three-constant energy."""
+    O = oracle_mod
+    nx, ny, nz = 16, 12, 8
+    extra = dict(K11=0.02, K22=0.006, K33=0.03) if case == "frank3" else {}
+    params = _generic(nx, ny, nz, dt_fd=5, K=0.01, q0=0.5, W0=0.002, anchoring="none", **extra)
+    n0 = I.skyrmion_tubes(nx, ny, nz, [(8.0, 6.0)], 5.0)
+    mask = None
+    if case == "obstacle":
+        mask, normals = _sphere_mask(nx, ny, nz, (3.0, 3.0, 4.0), 2.2)
+        n0[:, mask == 1] = normals[:, mask == 1]
+    p = O.OracleParams.from_dict(dict(params, solid=mask))
+    n = n0.copy()
+    u = np.zeros_like(n0)
+    for _ in range(12):
+        n = O.fd_step(p, n, u)
+    ch = nh.Channel(dict(params, precision="fp64"))
+    if mask is not None:
+        ch.set_solid(mask)
+    ch.set_fields(n0)
+    ch.relax(12)
+    assert O.rel_l2(ch.get_fields()[0], n) < 1e-12
