@@ -274,7 +274,7 @@ def run_ours(args):
     ch.diagnostics_read()
     torch.cuda.synchronize()
 
-    ch.set_timing(True)
+    ch.set_timing(2)  # events around the LB launches only (the roofline kernel)
     ch.timing()  # reset counters
     launches0 = ch.launch_count()
     clocks = ClockSampler(local)
@@ -311,6 +311,17 @@ def run_ours(args):
     ch.diagnostics_read()
     value_graphs = ch.N * dt * args.steps / (g0.elapsed_time(g1) * 1e-3) / 1e6
 
+    # per-class breakdown (events around every kernel class), untimed
+    breakdown_steps = min(args.steps, 20)
+    ch.set_timing(1)
+    ch.timing()
+    for _ in range(breakdown_steps):
+        block()
+    kt_all = ch.timing()
+    ch.diagnostics_read()
+    ch.set_timing(0)
+    ch.timing()
+
     ms_max = max_over_ranks(ms, dist, device="cuda")
     N = ch.N
     value = aggregate_mlups(world, N, dt * args.steps, ms_max)
@@ -325,19 +336,20 @@ def run_ours(args):
         peak, peak_src = float(peaks["hbm_gbs"]), "measured"
     except Exception:
         peak, peak_src = 6800.0, "fallback"
-    total_kernel_ms = sum(v[1] for v in kt.values())
+    total_kernel_ms = sum(v[1] for v in kt_all.values())
+    lb_share = kt_all["lb"][1] / total_kernel_ms if total_kernel_ms else None
     traffic = ncu_traffic() if (store == "f32" and not args.small and dt == 16) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "lb_kernel (fused collide+stream)", "peak_source": peak_src,
                 "lb_variant": lb_variant,
                 "bytes_per_launch": bytes_per_launch, "avg_launch_us": lb_avg_s * 1e6,
-                "share_of_kernel_time": lb_ms / total_kernel_ms if total_kernel_ms else None}
+                "share_of_kernel_time": lb_share}
 
     # FP64 comparison on the same workload: throughput and the FP32-shifted error
     compare = None
     if not args.no_compare and rank == 0:
         n32, u32, _ = ch.get_fields()
-        steps_done = (args.warmup + 2 * args.steps) * dt
+        steps_done = (args.warmup + 2 * args.steps + breakdown_steps) * dt
         c64 = nh.Channel(dict(params, precision="fp64", storage="f64", shifted=True))
         c64.set_fields(n0)
         pre = steps_done - 4 * dt
@@ -406,6 +418,8 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "value_graphs_no_kernel_events": value_graphs,
             "kernel_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in kt.items()},
+            "kernel_ms_breakdown": {"steps": breakdown_steps,
+                                    **{k: {"launches": v[0], "ms": v[1]} for k, v in kt_all.items()}},
             "fp64_compare": compare,
             "batched_sweep": batched,
             "diagnostics": {"mass_minus_N": diag["mass"] - N, "energy": diag["energy"], "max_u": diag["max_u"],
