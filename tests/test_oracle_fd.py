@@ -407,3 +407,33 @@ def test_frank3_splay_twist_bend_decay(oracle_mod, axis, Kii):
     rr = r.reshape(-1)
     amp = np.sum(n[0] * np.sin(k * rr)) * 2 / rr.size
     assert abs(amp / heun - 1) < 1e-6
+
+
+def test_flow_alignment_leslie_angle(oracle_mod):
+    """Without elasticity (K = 0) every site evolves on its own under the local
+    shear: for n = (sin t, 0, cos t) in u_x(z), the director equation gives
+    dt/dt = (g/2)(1 - lambda cos 2t), lambda = gamma2/gamma1, g = du_x/dz.  A
+    flow-aligning nematic (|lambda| > 1) settles at cos 2t = 1/lambda, with
+    sin 2t of the sign opposite to lambda g (the stable root) -- the Leslie angle.
+    The Heun map has the same fixed point, so the angle is exact."""
+    O = oracle_mod
+    nz = 16
+    lam = -1.5
+    p = O.OracleParams(nx=1, ny=1, nz=nz, walls_z=False, K=0.0, gamma1=1.0, gamma2=lam, dt_fd=1)
+    z = np.arange(nz)
+    k = 2 * math.pi / nz
+    u = np.zeros((3, nz))
+    u[0] = 0.05 * np.sin(k * z)
+    n = np.zeros((3, nz))
+    n[0] = n[2] = math.sqrt(0.5)
+    for _ in range(6000):
+        n = O.fd_step(p, n, u)
+    shear = 0.5 * (np.roll(u[0], -1) - np.roll(u[0], 1))   # central du_x/dz of the oracle
+    t = np.arctan2(n[0], n[2])
+    for zz in range(nz):
+        if abs(shear[zz]) < 1e-12:
+            continue
+        c2, s2 = math.cos(2 * t[zz]), math.sin(2 * t[zz])
+        assert abs(c2 - 1 / lam) < 1e-9, zz
+        assert s2 * lam * shear[zz] < 0, zz
+    assert np.max(np.abs(n[1])) < 1e-15
