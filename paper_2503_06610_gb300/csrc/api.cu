@@ -338,6 +338,20 @@ FDChan<Real> fd_chan(nh_ctx* c)
     a.p.kd1 = Real(p.frank3 ? p.K11 - p.K : 0.0);
     a.p.kd2 = Real(p.frank3 ? p.K22 - p.K : 0.0);
     a.p.kd3 = Real(p.frank3 ? p.K33 - p.K : 0.0);
+    const double lam = p.gamma2 / p.gamma1;
+    a.p.kg = Real(p.K / p.gamma1);
+    a.p.kqg = Real(p.K * p.q0 / p.gamma1);
+    a.p.w0g = Real(p.W0 / p.gamma1);
+    a.p.c1 = Real(0.25 * (1.0 - lam));
+    a.p.c2 = Real(-0.25 * (1.0 + lam));
+    a.p.kq = Real(p.K * p.q0);
+    a.p.g2q = Real(0.25 * lam);
+    a.p.a1q = Real(0.25 * p.alpha1);
+    a.p.a4q = Real(0.25 * p.alpha4p);
+    a.p.a5q = Real(0.25 * p.alpha5);
+    a.p.a6q = Real(0.25 * p.alpha6);
+    a.p.k4 = Real(0.25 * p.K);
+    a.p.kq2 = Real(0.5 * p.K * p.q0);
     return a;
 }
 

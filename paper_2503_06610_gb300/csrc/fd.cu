@@ -98,51 +98,62 @@ __device__ __forceinline__ void gather7(const Real* __restrict__ f, const Geom& 
     }
 }
 
-// dn[b][c] = d_b n_c, du[a][m] = d_a u_m (central), molecular field h.
+// Differences and sums of a 7-point neighbourhood: e[b][c] = n_c(+e_b) -
+// n_c(-e_b) (twice the central derivative d_b n_c), v[b][c] the same for u,
+// S[c] = sum of the six neighbours of n_c (compact Laplacian = S - 6 n_c) and
+// ce = curl of e (twice the central curl of n).
 template <typename Real>
-__device__ __forceinline__ void local_fields(const Real nn[7][3], const Real uu[7][3], const FDPar<Real>& p,
-                                             Real dn[3][3], Real du[3][3], Real h[3])
+__device__ __forceinline__ void stencil_diffs(const Real nn[7][3], const Real uu[7][3], Real e[3][3], Real v[3][3],
+                                              Real S[3], Real ce[3])
 {
-    Real lap[3] = {0, 0, 0};
 #pragma unroll
     for (int b = 0; b < 3; ++b)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            dn[b][c] = Real(0.5) * (nn[1 + 2 * b][c] - nn[2 + 2 * b][c]);
-            du[b][c] = Real(0.5) * (uu[1 + 2 * b][c] - uu[2 + 2 * b][c]);
-            lap[c] += nn[1 + 2 * b][c] + nn[2 + 2 * b][c] - Real(2) * nn[0][c];
+            e[b][c] = nn[1 + 2 * b][c] - nn[2 + 2 * b][c];
+            v[b][c] = uu[1 + 2 * b][c] - uu[2 + 2 * b][c];
         }
-    const Real curl[3] = {dn[1][2] - dn[2][1], dn[2][0] - dn[0][2], dn[0][1] - dn[1][0]};
-    const Real kq = Real(2) * p.K * p.q0;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) h[a] = p.K * lap[a] - kq * curl[a];
-    h[2] += p.W0 * nn[0][2];
+    for (int c = 0; c < 3; ++c) S[c] = ((nn[1][c] + nn[2][c]) + (nn[3][c] + nn[4][c])) + (nn[5][c] + nn[6][c]);
+    ce[0] = e[1][2] - e[2][1];
+    ce[1] = e[2][0] - e[0][2];
+    ce[2] = e[0][1] - e[1][0];
 }
 
-// Eq. director-time-eq: dn_m/dt = h_m/g1 - (g2/g1) n_a D_am - u_g d_g n_m + W_mg n_g.
+// Eq. director-time-eq: dn_m/dt = h_m/g1 - (g2/g1) n_a D_am - u_a d_a n_m + W_ma n_a,
+// with h = K lap n - 2 K q0 curl n + W0 n_z z_hat, D = (du + du^T)/2 and
+// W_ma = (d_a u_m - d_m u_a)/2.  In the differences above (lambda = g2/g1):
+//   h_m/g1 = kg (S_m - 6 n_m) - kqg ce_m + w0g n_z delta_mz,
+//   -lambda n_a D_am + W_ma n_a = sum_a n_a [(1 - lambda)/4 v[a][m] - (1 + lambda)/4 v[m][a]],
+//   -u_a d_a n_m = -1/2 sum_a u_a e[a][m].
+// hx (optional) is an extra molecular field (three-constant correction).
 template <typename Real>
 __device__ __forceinline__ void director_rate(const Real nn[7][3], const Real uu[7][3], const FDPar<Real>& p,
                                               Real rate[3], const Real* hx = nullptr)
 {
-    Real dn[3][3], du[3][3], h[3];
-    local_fields(nn, uu, p, dn, du, h);
-    if (hx != nullptr) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) h[a] += hx[a];
-    }
+    Real e[3][3], v[3][3], S[3], ce[3];
+    stencil_diffs(nn, uu, e, v, S, ce);
     const Real* n = nn[0];
-    const Real* u = uu[0];
+    Real w1[3], w2[3], hu[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        w1[a] = p.c1 * n[a];
+        w2[a] = p.c2 * n[a];
+        hu[a] = Real(-0.5) * uu[0][a];
+    }
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-        Real r = h[m] * p.inv_gamma1;
-        Real nD = 0, adv = 0, Wn = 0;
+        Real r = p.kg * (S[m] - Real(6) * n[m]);
+        r = fma(-p.kqg, ce[m], r);
+        if (m == 2) r = fma(p.w0g, n[2], r);
+        if (hx != nullptr) r = fma(hx[m], p.inv_gamma1, r);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            nD += n[a] * Real(0.5) * (du[a][m] + du[m][a]);   // n_a D_am
-            adv += u[a] * dn[a][m];                            // u_g d_g n_m
-            Wn += Real(0.5) * (du[a][m] - du[m][a]) * n[a];    // W_ma n_a, W_ma = (d_a u_m - d_m u_a)/2
+            r = fma(v[a][m], w1[a], r);
+            r = fma(v[m][a], w2[a], r);
+            r = fma(hu[a], e[a][m], r);
         }
-        rate[m] = r - p.g2_over_g1 * nD - adv + Wn;
+        rate[m] = r;
     }
 }
 
@@ -286,44 +297,69 @@ template <typename Real>
 __device__ __forceinline__ void stress_point(const Real nn[7][3], const Real uu[7][3], const FDPar<Real>& p,
                                              Real sig[9], const Real* hx = nullptr, const Real* Pd = nullptr)
 {
-    Real dn[3][3], du[3][3], h[3];
-    local_fields(nn, uu, p, dn, du, h);
-    if (hx != nullptr) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) h[a] += hx[a];
-    }
+    // In the differences of stencil_diffs (Ds = v + v^T = 4 D, Dn_a = Ds_am n_m = 4 D_am n_m):
+    //   N_m = [h_m - (h.n) n_m]/g1 - lambda/4 [Dn_m - (n.Dn) n_m]       (kinematic transport, normal to n)
+    //   sigma^v_ab = n_b P_a + n_a Q_b + a4'/4 Ds_ab,
+    //     P_a = a1/4 (n.Dn) n_a + a2 N_a + a5/4 Dn_a,   Q_b = a3 N_b + a6/4 Dn_b,
+    //   sigma^e_ab = -d_a n_g df/d(d_b n_g) = -K/4 e_a.e_b - K q0/2 (e_a x n)_b
+    //     (one-constant chiral density; e_a = row a of e), minus 1/2 e_ag Pd_bg for the
+    //     three-constant correction Pd = d(Delta f)/d(d n).
+    Real e[3][3], v[3][3], S[3], ce[3];
+    stencil_diffs(nn, uu, e, v, S, ce);
     const Real* n = nn[0];
-    Real D[3][3];
+    Real h[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        h[m] = fma(-p.kq, ce[m], p.K * (S[m] - Real(6) * n[m]));
+        if (hx != nullptr) h[m] += hx[m];
+    }
+    h[2] = fma(p.W0, n[2], h[2]);
+    Real Ds[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) D[a][b] = Real(0.5) * (du[a][b] + du[b][a]);
+        for (int b = a; b < 3; ++b) {
+            Ds[a][b] = v[a][b] + v[b][a];
+            Ds[b][a] = Ds[a][b];
+        }
     Real Dn[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) Dn[a] = D[a][0] * n[0] + D[a][1] * n[1] + D[a][2] * n[2];
-    const Real nDn = n[0] * Dn[0] + n[1] * Dn[1] + n[2] * Dn[2];
-    const Real hn = h[0] * n[0] + h[1] * n[1] + h[2] * n[2];
-    // kinematic transport from the director equation, projected normal to n
-    Real Nv[3];
+    for (int a = 0; a < 3; ++a) Dn[a] = fma(Ds[a][2], n[2], fma(Ds[a][1], n[1], Ds[a][0] * n[0]));
+    const Real nDn = fma(n[2], Dn[2], fma(n[1], Dn[1], n[0] * Dn[0]));
+    const Real hn = fma(n[2], h[2], fma(n[1], h[1], n[0] * h[0]));
+    Real P[3], Q[3];
 #pragma unroll
-    for (int m = 0; m < 3; ++m) Nv[m] = ((h[m] - hn * n[m]) - p.gamma2 * (Dn[m] - n[m] * nDn)) * p.inv_gamma1;
-    // chi[b][g] = eps_{c b g} n_c
-    const Real chi[3][3] = {{0, n[2], -n[1]}, {-n[2], 0, n[0]}, {n[1], -n[0], 0}};
+    for (int m = 0; m < 3; ++m) {
+        const Real Nm = p.inv_gamma1 * fma(-hn, n[m], h[m]) - p.g2q * fma(-nDn, n[m], Dn[m]);
+        P[m] = fma(p.a5q, Dn[m], fma(p.a2, Nm, p.a1q * nDn * n[m]));
+        Q[m] = fma(p.a6q, Dn[m], p.a3 * Nm);
+    }
+    Real G[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            Real sv = p.a1 * n[a] * n[b] * nDn + p.a2 * n[b] * Nv[a] + p.a3 * n[a] * Nv[b] + p.a4p * D[a][b] +
-                      p.a5 * n[b] * Dn[a] + p.a6 * n[a] * Dn[b];
-            Real se = 0;
-#pragma unroll
-            for (int gg = 0; gg < 3; ++gg) {
-                Real dfdG = p.K * dn[b][gg] + p.K * p.q0 * chi[b][gg];
-                if (Pd != nullptr) dfdG += Pd[3 * b + gg];  // three-constant correction
-                se -= dn[a][gg] * dfdG;
-            }
-            sig[3 * a + b] = sv + se;
+        for (int b = a; b < 3; ++b) {
+            G[a][b] = fma(e[a][2], e[b][2], fma(e[a][1], e[b][1], e[a][0] * e[b][0]));
+            G[b][a] = G[a][b];
         }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const Real X[3] = {e[a][1] * n[2] - e[a][2] * n[1], e[a][2] * n[0] - e[a][0] * n[2],
+                           e[a][0] * n[1] - e[a][1] * n[0]};
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            Real s = n[b] * P[a];
+            s = fma(n[a], Q[b], s);
+            s = fma(p.a4q, Ds[a][b], s);
+            s = fma(-p.k4, G[a][b], s);
+            s = fma(-p.kq2, X[b], s);
+            if (Pd != nullptr) {
+#pragma unroll
+                for (int g = 0; g < 3; ++g) s = fma(Real(-0.5) * e[a][g], Pd[3 * b + g], s);
+            }
+            sig[3 * a + b] = s;
+        }
+    }
 }
 
 template <typename Real>
@@ -458,9 +494,9 @@ __device__ __forceinline__ int slot4(int p) { return ((p % 4) + 4) % 4; }
 __device__ __forceinline__ int slot3(int p) { return ((p % 3) + 3) % 3; }
 
 template <typename Real>
-size_t fused_a_smem() { return (size_t)(3 * 6 * kP2 + 3 * 3 * kP1 + 2 * 3 * kTX * kTY) * sizeof(Real); }
+size_t fused_a_smem() { return (size_t)(3 * 6 * kP2 + 3 * 4 * kP1) * sizeof(Real); }
 template <typename Real>
-size_t fused_b_smem() { return (size_t)(3 * 6 * kP2 + 3 * 9 * kP1) * sizeof(Real); }
+size_t fused_b_smem() { return (size_t)(3 * 6 * kP2 + 2 * 8 * kP1) * sizeof(Real); }
 
 // Each thread owns at most kPts points of a P2 plane (indices threadIdx.x +
 // k * blockDim.x); their wrapped x-y site offsets are computed once per tile.
@@ -515,86 +551,144 @@ __device__ __forceinline__ void prefetch_plane(const Real* __restrict__ n, const
     }
 }
 
+// Shared-memory layout of an input plane slot (6 kP2 Reals): the six values
+// (n, u) of a point are read with two vector loads in FP32, (n0 n1 n2 u0) as
+// float4 [kP2] followed by (u1 u2) as float2 [kP2]; in FP64 as three double2
+// arrays (n0 n1), (n2 u0), (u1 u2).
+__device__ __forceinline__ void ld_pt(const float* slot, int i, float v[6])
+{
+    const float4 a = reinterpret_cast<const float4*>(slot)[i];
+    const float2 b = reinterpret_cast<const float2*>(slot + 4 * kP2)[i];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y;
+}
+__device__ __forceinline__ void st_pt(float* slot, int i, const float v[6])
+{
+    reinterpret_cast<float4*>(slot)[i] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float2*>(slot + 4 * kP2)[i] = make_float2(v[4], v[5]);
+}
+__device__ __forceinline__ void ld_pt(const double* slot, int i, double v[6])
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double2 a = reinterpret_cast<const double2*>(slot + 2 * k * kP2)[i];
+        v[2 * k] = a.x;
+        v[2 * k + 1] = a.y;
+    }
+}
+__device__ __forceinline__ void st_pt(double* slot, int i, const double v[6])
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) reinterpret_cast<double2*>(slot + 2 * k * kP2)[i] = make_double2(v[2 * k], v[2 * k + 1]);
+}
+
+// Predictor ring slot (4 kP1 Reals): n^P of a point as one float4 (n0 n1 n2 -)
+// in FP32, as three planes of kP1 doubles in FP64.
+__device__ __forceinline__ void ld3(const float* slot, int i, float v[3])
+{
+    const float4 a = reinterpret_cast<const float4*>(slot)[i];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z;
+}
+__device__ __forceinline__ void st3(float* slot, int i, const float v[3])
+{
+    reinterpret_cast<float4*>(slot)[i] = make_float4(v[0], v[1], v[2], 0.f);
+}
+__device__ __forceinline__ void ld3(const double* slot, int i, double v[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) v[a] = slot[a * kP1 + i];
+}
+__device__ __forceinline__ void st3(double* slot, int i, const double v[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) slot[a * kP1 + i] = v[a];
+}
+
 template <typename Real>
 __device__ __forceinline__ void commit_plane(const PlaneMap& m, const Real v[kPts][6], Real* slot)
 {
 #pragma unroll
     for (int k = 0; k < kPts; ++k) {
         if (m.off[k] < 0) continue;
-        const int i = threadIdx.x + k * blockDim.x;
-#pragma unroll
-        for (int c = 0; c < 6; ++c) slot[c * kP2 + i] = v[k][c];
+        st_pt(slot, threadIdx.x + k * blockDim.x, v[k]);
     }
 }
 
-// 7-point neighbourhoods of n (components 0..2 of the slots) and u (3..5)
-// around P2 index i2 of the middle plane.
+template <typename Real>
+__device__ __forceinline__ void split_pt(const Real* slot, int i, Real n[3], Real u[3])
+{
+    Real v[6];
+    ld_pt(slot, i, v);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        n[a] = v[a];
+        u[a] = v[3 + a];
+    }
+}
+
+// 7-point neighbourhoods of n and u around P2 index i2 of the middle plane.
 template <typename Real>
 __device__ __forceinline__ void gather_slots(const Real* lo, const Real* mid, const Real* hi, int i2, Real nn[7][3],
                                              Real uu[7][3])
 {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        nn[0][a] = mid[a * kP2 + i2];
-        nn[1][a] = mid[a * kP2 + i2 + 1];
-        nn[2][a] = mid[a * kP2 + i2 - 1];
-        nn[3][a] = mid[a * kP2 + i2 + kHX2];
-        nn[4][a] = mid[a * kP2 + i2 - kHX2];
-        nn[5][a] = hi[a * kP2 + i2];
-        nn[6][a] = lo[a * kP2 + i2];
-        uu[0][a] = mid[(3 + a) * kP2 + i2];
-        uu[1][a] = mid[(3 + a) * kP2 + i2 + 1];
-        uu[2][a] = mid[(3 + a) * kP2 + i2 - 1];
-        uu[3][a] = mid[(3 + a) * kP2 + i2 + kHX2];
-        uu[4][a] = mid[(3 + a) * kP2 + i2 - kHX2];
-        uu[5][a] = hi[(3 + a) * kP2 + i2];
-        uu[6][a] = lo[(3 + a) * kP2 + i2];
-    }
+    split_pt(mid, i2, nn[0], uu[0]);
+    split_pt(mid, i2 + 1, nn[1], uu[1]);
+    split_pt(mid, i2 - 1, nn[2], uu[2]);
+    split_pt(mid, i2 + kHX2, nn[3], uu[3]);
+    split_pt(mid, i2 - kHX2, nn[4], uu[4]);
+    split_pt(hi, i2, nn[5], uu[5]);
+    split_pt(lo, i2, nn[6], uu[6]);
 }
 
 __device__ __forceinline__ bool is_ghost_plane(const Geom& g, int p) { return g.walls && (p < 0 || p >= g.nz); }
 
-// The kP1 points of a 1-halo plane in an order where a warp takes kTX = 32
-// consecutive columns of one row (contiguous in shared memory, no bank
-// conflicts): t < kHY1 * kTX -> row t / kTX, column t % kTX; the remaining
-// 2 * kHY1 points are the two last columns of every row.
-constexpr int kP1Main = kHY1 * kTX;
+// The kP1 points of a 1-halo plane, the tile's own points first: t < kTX kTY
+// is the point of thread t (column t % kTX, row t / kTX; a warp reads one row,
+// contiguous in shared memory), so the value computed there stays in that
+// thread's registers; then the two halo rows and the two halo columns.
+constexpr int kOwn = kTX * kTY;
 __device__ __forceinline__ void p1_point(int t, int& hx1, int& hy1)
 {
-    if (t < kP1Main) {
-        hy1 = t / kTX;
-        hx1 = t % kTX;
+    if (t < kOwn) {
+        hx1 = t % kTX + 1;
+        hy1 = t / kTX + 1;
+        return;
+    }
+    const int e = t - kOwn;
+    if (e < 2 * kHX1) {
+        hy1 = e < kHX1 ? 0 : kHY1 - 1;
+        hx1 = e < kHX1 ? e : e - kHX1;
     } else {
-        const int e = t - kP1Main;
-        hy1 = e >> 1;
-        hx1 = kTX + (e & 1);
+        const int j = e - 2 * kHX1;
+        hy1 = 1 + (j >> 1);
+        hx1 = (j & 1) ? kHX1 - 1 : 0;
     }
 }
 
 // Kernel A tile: predictor on plane p (from planes p - 1, p, p + 1 of the
-// 3-slot input ring) into ring slot [nP x3] x kP1, and its rate at the tile's
-// own kTX x kTY points into rslot [3] x (kTX kTY), the only ones the corrector
-// reads.
+// 3-slot input ring) into ring slot pslot, and its rate at the thread's own
+// point into rown (blockDim.x == kOwn, so every thread's first point is its own).
+// npts = kOwn on the planes just below and above a chunk, where the corrector
+// reads n^P only at the tile's own points.
 template <typename Real>
-__device__ void predict_plane(const FDPar<Real>& par, Real* in, int p, Real* pslot, Real* rslot)
+__device__ void predict_plane(const FDPar<Real>& par, const Real* in, int p, Real* pslot, Real rown[3], int npts)
 {
     const Real* lo = in + slot3(p - 1) * 6 * kP2;
     const Real* mid = in + slot3(p) * 6 * kP2;
     const Real* hi = in + slot3(p + 1) * 6 * kP2;
-    for (int t = threadIdx.x; t < kP1; t += blockDim.x) {
+    for (int t = threadIdx.x; t < npts; t += blockDim.x) {
         int hx1, hy1;
         p1_point(t, hx1, hy1);
         const int i1 = hx1 + kHX1 * hy1;
         const int i2 = (hx1 + 1) + kHX2 * (hy1 + 1);
-        Real nn[7][3], uu[7][3], r[3];
+        Real nn[7][3], uu[7][3], r[3], np[3];
         gather_slots(lo, mid, hi, i2, nn, uu);
         director_rate(nn, uu, par, r);
-        const bool own = hx1 >= 1 && hx1 <= kTX && hy1 >= 1 && hy1 <= kTY;
-        const int io = (hx1 - 1) + kTX * (hy1 - 1);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            pslot[a * kP1 + i1] = nn[0][a] + par.dt * r[a];
-            if (own) rslot[a * (kTX * kTY) + io] = r[a];
+        for (int a = 0; a < 3; ++a) np[a] = nn[0][a] + par.dt * r[a];
+        st3(pslot, i1, np);
+        if (t < kOwn) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) rown[a] = r[a];
         }
     }
 }
@@ -604,8 +698,7 @@ __device__ void fused_a_tile(const FDChan<Real>& c, const Real* __restrict__ nin
 {
     extern __shared__ __align__(16) unsigned char smem_fd[];
     Real* in = reinterpret_cast<Real*>(smem_fd);  // 3 slots x 6 x kP2 (input planes)
-    Real* pr = in + 3 * 6 * kP2;                  // 3 slots x 3 x kP1 (predictor n^P)
-    Real* rt = pr + 3 * 3 * kP1;                  // 2 slots x 3 x kTX kTY (predictor rate)
+    Real* pr = in + 3 * 6 * kP2;                  // 3 slots x 4 x kP1 (predictor n^P)
     const Geom& g = c.g;
     const int ntx = (g.nx + kTX - 1) / kTX, nty = (g.ny + kTY - 1) / kTY;
     const int tx_t = tile % ntx, ty_t = (tile / ntx) % nty, zc = tile / (ntx * nty);
@@ -616,7 +709,6 @@ __device__ void fused_a_tile(const FDChan<Real>& c, const Real* __restrict__ nin
     const size_t N = (size_t)g.N;
     const int i1 = (tx + 1) + kHX1 * (ty + 1);
     const int i2 = (tx + 2) + kHX2 * (ty + 2);
-    const int io = tx + kTX * ty;
     const PlaneMap pm = plane_map(g, x0, y0);
     Real v[kPts][6];
     for (int p = zb - 2; p <= zb; ++p) {
@@ -625,57 +717,61 @@ __device__ void fused_a_tile(const FDChan<Real>& c, const Real* __restrict__ nin
     }
     prefetch_plane(nin, c.u, g, pm, zb + 1, v);  // in flight during the first predictor plane
     __syncthreads();
-    if (!is_ghost_plane(g, zb - 1)) predict_plane(c.p, in, zb - 1, pr + slot3(zb - 1) * 3 * kP1, rt + ((zb - 1) & 1) * 3 * kTX * kTY);
+    Real rcur[3] = {0, 0, 0}, rnext[3] = {0, 0, 0};  // predictor rate at the own point, planes z and z + 1
+    if (!is_ghost_plane(g, zb - 1)) predict_plane(c.p, in, zb - 1, pr + slot3(zb - 1) * 4 * kP1, rnext, kOwn);
     // u one layer below the corrector's plane, at the thread's own point, carried in registers
-    Real ulo[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) ulo[a] = active ? in[slot3(zb - 1) * 6 * kP2 + (3 + a) * kP2 + i2] : Real(0);
+    Real ulo[3], nc[3];
+    split_pt(in + slot3(zb - 1) * 6 * kP2, i2, nc, ulo);
     __syncthreads();  // plane zb - 2 is no longer read
     commit_plane(pm, v, in + slot3(zb + 1) * 6 * kP2);
     prefetch_plane(nin, c.u, g, pm, zb + 2, v);
     __syncthreads();
-    if (!is_ghost_plane(g, zb)) predict_plane(c.p, in, zb, pr + slot3(zb) * 3 * kP1, rt + (zb & 1) * 3 * kTX * kTY);
+    if (!is_ghost_plane(g, zb)) predict_plane(c.p, in, zb, pr + slot3(zb) * 4 * kP1, rcur, kP1);
     for (int z = zb; z < ze; ++z) {
         __syncthreads();  // plane z - 1 is no longer read; its slot takes plane z + 2
         commit_plane(pm, v, in + slot3(z + 2) * 6 * kP2);
         __syncthreads();
         if (z + 1 < ze) prefetch_plane(nin, c.u, g, pm, z + 3, v);  // overlaps the two evaluations below
         if (!is_ghost_plane(g, z + 1))
-            predict_plane(c.p, in, z + 1, pr + slot3(z + 1) * 3 * kP1, rt + ((z + 1) & 1) * 3 * kTX * kTY);
+            predict_plane(c.p, in, z + 1, pr + slot3(z + 1) * 4 * kP1, rnext, z + 1 < ze ? kP1 : kOwn);
         __syncthreads();
         if (active) {
-            const Real* mid = pr + slot3(z) * 3 * kP1;
+            const Real* mid = pr + slot3(z) * 4 * kP1;
             // predictor of the planes above and below; at a plate the ghost
             // value (z_hat, or the adjacent fluid layer without anchoring)
             const bool glo = is_ghost_plane(g, z - 1), ghi = is_ghost_plane(g, z + 1);
             const bool homeo = g.anchoring == NH_ANCHOR_HOMEOTROPIC;
-            const Real* lo = glo ? mid : pr + slot3(z - 1) * 3 * kP1;
-            const Real* hi = ghi ? mid : pr + slot3(z + 1) * 3 * kP1;
+            const Real* lo = glo ? mid : pr + slot3(z - 1) * 4 * kP1;
+            const Real* hi = ghi ? mid : pr + slot3(z + 1) * 4 * kP1;
             const Real* inm = in + slot3(z) * 6 * kP2;
             const Real* inh = in + slot3(z + 1) * 6 * kP2;
-            const Real* rate = rt + (z & 1) * 3 * kTX * kTY;
-            Real nn[7][3], uu[7][3], r[3];
+            Real nn[7][3], uu[7][3], r[3], n0[3], dummy[3];
+            ld3(mid, i1, nn[0]);
+            ld3(mid, i1 + 1, nn[1]);
+            ld3(mid, i1 - 1, nn[2]);
+            ld3(mid, i1 + kHX1, nn[3]);
+            ld3(mid, i1 - kHX1, nn[4]);
+            ld3(hi, i1, nn[5]);
+            ld3(lo, i1, nn[6]);
+            if (homeo) {
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                nn[0][a] = mid[a * kP1 + i1];
-                nn[1][a] = mid[a * kP1 + i1 + 1];
-                nn[2][a] = mid[a * kP1 + i1 - 1];
-                nn[3][a] = mid[a * kP1 + i1 + kHX1];
-                nn[4][a] = mid[a * kP1 + i1 - kHX1];
-                nn[5][a] = (ghi && homeo) ? Real(a == 2 ? 1 : 0) : hi[a * kP1 + i1];
-                nn[6][a] = (glo && homeo) ? Real(a == 2 ? 1 : 0) : lo[a * kP1 + i1];
-                uu[0][a] = inm[(3 + a) * kP2 + i2];
-                uu[1][a] = inm[(3 + a) * kP2 + i2 + 1];
-                uu[2][a] = inm[(3 + a) * kP2 + i2 - 1];
-                uu[3][a] = inm[(3 + a) * kP2 + i2 + kHX2];
-                uu[4][a] = inm[(3 + a) * kP2 + i2 - kHX2];
-                uu[5][a] = inh[(3 + a) * kP2 + i2];
-                uu[6][a] = ulo[a];
+                for (int a = 0; a < 3; ++a) {
+                    if (ghi) nn[5][a] = Real(a == 2 ? 1 : 0);
+                    if (glo) nn[6][a] = Real(a == 2 ? 1 : 0);
+                }
             }
+            split_pt(inm, i2, n0, uu[0]);
+            split_pt(inm, i2 + 1, dummy, uu[1]);
+            split_pt(inm, i2 - 1, dummy, uu[2]);
+            split_pt(inm, i2 + kHX2, dummy, uu[3]);
+            split_pt(inm, i2 - kHX2, dummy, uu[4]);
+            split_pt(inh, i2, dummy, uu[5]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) uu[6][a] = ulo[a];
             director_rate(nn, uu, c.p, r);
             Real nw[3];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) nw[a] = inm[a * kP2 + i2] + c.p.dt * Real(0.5) * (rate[a * kTX * kTY + io] + r[a]);
+            for (int a = 0; a < 3; ++a) nw[a] = n0[a] + c.p.dt * Real(0.5) * (rcur[a] + r[a]);
             const Real inv = Real(1) / sqrt(nw[0] * nw[0] + nw[1] * nw[1] + nw[2] * nw[2]);
             const size_t s = (size_t)(x0 + tx) + (size_t)g.nx * ((size_t)(y0 + ty) + (size_t)g.ny * z);
 #pragma unroll
@@ -683,22 +779,30 @@ __device__ void fused_a_tile(const FDChan<Real>& c, const Real* __restrict__ nin
 #pragma unroll
             for (int a = 0; a < 3; ++a) ulo[a] = uu[0][a];  // u of plane z: the next plane's lower neighbour
         }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) rcur[a] = rnext[a];
     }
 }
 
-// Kernel B tile: stress on plane p into ring slot [sigma x9] x kP1 (zero at
-// ghosts), from planes p - 1, p, p + 1 of the 3-slot input ring.
+// Kernel B tile: stress on plane p from planes p - 1, p, p + 1 of the 3-slot
+// input ring.  The divergence at a tile point needs sigma_ax at its x
+// neighbours and sigma_ay at its y neighbours in the same plane (into slot:
+// sigma_.x then sigma_.y, 4 kP1 Reals each), and sigma_az of the point itself
+// in the planes above and below, which stays in the registers of the thread
+// that owns the point (szown; zero on a ghost plane).  npts = kOwn on the
+// planes just below and above a chunk, which give only sigma_az.
 template <typename Real>
-__device__ void stress_plane(const FDChan<Real>& c, Real* in, int p, Real* sslot)
+__device__ void stress_plane(const FDChan<Real>& c, const Real* in, int p, Real* slot, Real szown[3], int npts)
 {
     if (is_ghost_plane(c.g, p)) {
-        for (int i = threadIdx.x; i < 9 * kP1; i += blockDim.x) sslot[i] = Real(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) szown[a] = Real(0);
         return;
     }
     const Real* lo = in + slot3(p - 1) * 6 * kP2;
     const Real* mid = in + slot3(p) * 6 * kP2;
     const Real* hi = in + slot3(p + 1) * 6 * kP2;
-    for (int t = threadIdx.x; t < kP1; t += blockDim.x) {
+    for (int t = threadIdx.x; t < npts; t += blockDim.x) {
         int hx1, hy1;
         p1_point(t, hx1, hy1);
         const int i1 = hx1 + kHX1 * hy1;
@@ -706,8 +810,14 @@ __device__ void stress_plane(const FDChan<Real>& c, Real* in, int p, Real* sslot
         Real nn[7][3], uu[7][3], sig[9];
         gather_slots(lo, mid, hi, i2, nn, uu);
         stress_point(nn, uu, c.p, sig);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) sslot[k * kP1 + i1] = sig[k];
+        const Real sx[3] = {sig[0], sig[3], sig[6]}, sy[3] = {sig[1], sig[4], sig[7]};
+        st3(slot, i1, sx);
+        st3(slot + 4 * kP1, i1, sy);
+        if (t < kOwn) {
+            szown[0] = sig[2];
+            szown[1] = sig[5];
+            szown[2] = sig[8];
+        }
     }
 }
 
@@ -716,7 +826,7 @@ __device__ void fused_b_tile(const FDChan<Real>& c, const Real* __restrict__ nin
 {
     extern __shared__ __align__(16) unsigned char smem_fd[];
     Real* in = reinterpret_cast<Real*>(smem_fd);  // 3 slots x 6 x kP2 (planes z, z + 1, z + 2)
-    Real* sg = in + 3 * 6 * kP2;                  // 3 slots x 9 x kP1
+    Real* sg = in + 3 * 6 * kP2;                  // 2 slots x 8 x kP1 (sigma_.x, sigma_.y)
     const Geom& g = c.g;
     const int ntx = (g.nx + kTX - 1) / kTX, nty = (g.ny + kTY - 1) / kTY;
     const int tx_t = tile % ntx, ty_t = (tile / ntx) % nty, zc = tile / (ntx * nty);
@@ -725,6 +835,8 @@ __device__ void fused_b_tile(const FDChan<Real>& c, const Real* __restrict__ nin
     const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
     const bool active = threadIdx.x < kTX * kTY && x0 + tx < g.nx && y0 + ty < g.ny;
     const size_t N = (size_t)g.N;
+    const int i1 = (tx + 1) + kHX1 * (ty + 1);
+    const int i2 = (tx + 2) + kHX2 * (ty + 2);
     const PlaneMap pm = plane_map(g, x0, y0);
     Real v[kPts][6];
     for (int p = zb - 2; p <= zb; ++p) {
@@ -733,50 +845,54 @@ __device__ void fused_b_tile(const FDChan<Real>& c, const Real* __restrict__ nin
     }
     prefetch_plane(nin, c.u, g, pm, zb + 1, v);  // in flight during the first stress plane
     __syncthreads();
-    stress_plane(c, in, zb - 1, sg + slot3(zb - 1) * 9 * kP1);
+    Real szlo[3], szmid[3], szhi[3];  // sigma_az at the own point, planes z - 1, z, z + 1
+    stress_plane(c, in, zb - 1, sg + ((zb - 1) & 1) * 8 * kP1, szlo, kOwn);
     __syncthreads();  // plane zb - 2 is no longer read
     commit_plane(pm, v, in + slot3(zb + 1) * 6 * kP2);
     prefetch_plane(nin, c.u, g, pm, zb + 2, v);
     __syncthreads();
-    stress_plane(c, in, zb, sg + slot3(zb) * 9 * kP1);
+    stress_plane(c, in, zb, sg + (zb & 1) * 8 * kP1, szmid, kP1);
     for (int z = zb; z < ze; ++z) {
-        __syncthreads();  // plane z - 1 is no longer read; its slot takes plane z + 2
+        __syncthreads();  // plane z - 1 is no longer read; its slots take planes z + 2 (input), z + 1 (sigma)
         commit_plane(pm, v, in + slot3(z + 2) * 6 * kP2);
         __syncthreads();
         if (z + 1 < ze) prefetch_plane(nin, c.u, g, pm, z + 3, v);
-        stress_plane(c, in, z + 1, sg + slot3(z + 1) * 9 * kP1);
+        stress_plane(c, in, z + 1, sg + ((z + 1) & 1) * 8 * kP1, szhi, z + 1 < ze ? kP1 : kOwn);
         __syncthreads();
         if (active) {
-            const int i1 = (tx + 1) + kHX1 * (ty + 1);
-            const Real* mid = sg + slot3(z) * 9 * kP1;
-            const Real* lo = sg + slot3(z - 1) * 9 * kP1;
-            const Real* hi = sg + slot3(z + 1) * 9 * kP1;
+            const Real* sx = sg + (z & 1) * 8 * kP1;
+            const Real* sy = sx + 4 * kP1;
+            Real xp[3], xm[3], yp[3], ym[3];
+            ld3(sx, i1 + 1, xp);
+            ld3(sx, i1 - 1, xm);
+            ld3(sy, i1 + kHX1, yp);
+            ld3(sy, i1 - kHX1, ym);
             const size_t s = (size_t)(x0 + tx) + (size_t)g.nx * ((size_t)(y0 + ty) + (size_t)g.ny * z);
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const Real dx = mid[(3 * a + 0) * kP1 + i1 + 1] - mid[(3 * a + 0) * kP1 + i1 - 1];
-                const Real dy = mid[(3 * a + 1) * kP1 + i1 + kHX1] - mid[(3 * a + 1) * kP1 + i1 - kHX1];
-                const Real dz = hi[(3 * a + 2) * kP1 + i1] - lo[(3 * a + 2) * kP1 + i1];
-                c.F[a * N + s] = Real(0.5) * (dx + dy + dz);
-            }
+            for (int a = 0; a < 3; ++a) c.F[a * N + s] = Real(0.5) * ((xp[a] - xm[a]) + (yp[a] - ym[a]) + (szhi[a] - szlo[a]));
             if (ncopy) {
-                const Real* inm = in + slot3(z) * 6 * kP2;
-                const int i2 = (tx + 2) + kHX2 * (ty + 2);
+                Real n0[3], u0[3];
+                split_pt(in + slot3(z) * 6 * kP2, i2, n0, u0);
 #pragma unroll
-                for (int a = 0; a < 3; ++a) ncopy[a * N + s] = inm[a * kP2 + i2];
+                for (int a = 0; a < 3; ++a) ncopy[a * N + s] = n0[a];
             }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            szlo[a] = szmid[a];
+            szmid[a] = szhi[a];
         }
     }
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(kFusedThreads) fused_a_kernel(const FDChan<Real> c, const Real* nin, Real* nout)
+__global__ void __launch_bounds__(kFusedThreads, sizeof(Real) == 4 ? 4 : 2) fused_a_kernel(const FDChan<Real> c, const Real* nin, Real* nout)
 {
     fused_a_tile(c, nin, nout, blockIdx.x);
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(kFusedThreads) fused_b_kernel(const FDChan<Real> c, const Real* nin, Real* ncopy)
+__global__ void __launch_bounds__(kFusedThreads, sizeof(Real) == 4 ? 4 : 2) fused_b_kernel(const FDChan<Real> c, const Real* nin, Real* ncopy)
 {
     fused_b_tile(c, nin, ncopy, blockIdx.x);
 }
@@ -785,7 +901,7 @@ __global__ void __launch_bounds__(kFusedThreads) fused_b_kernel(const FDChan<Rea
 // list; stage 0 = kernel A (n -> nP), 1 = kernel B (nP -> F, copy into n),
 // 2 = kernel A (nP -> n), for relaxations that alternate the two buffers.
 template <typename Real, int Stage>
-__global__ void __launch_bounds__(kFusedThreads) fused_batch_kernel(const FDBatch<Real> b)
+__global__ void __launch_bounds__(kFusedThreads, sizeof(Real) == 4 ? 3 : 2) fused_batch_kernel(const FDBatch<Real> b)
 {
     const int total = b.prefix[b.count];
     for (int t = blockIdx.x; t < total; t += gridDim.x) {

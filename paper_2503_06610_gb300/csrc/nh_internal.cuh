@@ -110,6 +110,10 @@ struct FDPar {
     Real a1, a2, a3, a4p, a5, a6;
     Real dt;
     Real kd1, kd2, kd3;  // K11 - K, K22 - K, K33 - K (three-constant energy)
+    // The same constants with the factors 1/2 of the central differences and
+    // of the strain-rate and vorticity tensors folded in (lambda = g2/g1):
+    Real kg, kqg, w0g, c1, c2;            // K/g1, K q0/g1, W0/g1, (1 - lambda)/4, -(1 + lambda)/4
+    Real kq, g2q, a1q, a4q, a5q, a6q, k4, kq2;  // K q0, lambda/4, a1/4, a4'/4, a5/4, a6/4, K/4, K q0/2
 };
 
 // Three-constant correction of the Frank energy density at one site
