@@ -537,16 +537,18 @@ __device__ __forceinline__ void prefetch_plane(const Real* __restrict__ n, const
         zz = wrapm(zp, g.nz);
     }
     const bool fixed_dir = ghost && g.anchoring == NH_ANCHOR_HOMEOTROPIC;
-    const size_t N = (size_t)g.N;
+    const int N = g.N;  // 3 N < 2^31: 32-bit offsets
     const size_t zoff = (size_t)g.nx * g.ny * zz;
+    const Real* __restrict__ nz = n + zoff;
+    const Real* __restrict__ uz = u + zoff;
 #pragma unroll
     for (int k = 0; k < kPts; ++k) {
         if (m.off[k] < 0) continue;
-        const size_t s = zoff + (size_t)m.off[k];
+        const int s = m.off[k];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            v[k][a] = fixed_dir ? Real(a == 2 ? 1 : 0) : n[a * N + s];
-            v[k][3 + a] = ghost ? Real(0) : u[a * N + s];
+            v[k][a] = fixed_dir ? Real(a == 2 ? 1 : 0) : nz[a * N + s];
+            v[k][3 + a] = ghost ? Real(0) : uz[a * N + s];
         }
     }
 }
@@ -664,35 +666,55 @@ __device__ __forceinline__ void p1_point(int t, int& hx1, int& hy1)
     }
 }
 
-// Kernel A tile: predictor on plane p (from planes p - 1, p, p + 1 of the
-// 3-slot input ring) into ring slot pslot, and its rate at the thread's own
-// point into rown (blockDim.x == kOwn, so every thread's first point is its own).
-// npts = kOwn on the planes just below and above a chunk, where the corrector
-// reads n^P only at the tile's own points.
-template <typename Real>
-__device__ void predict_plane(const FDPar<Real>& par, const Real* in, int p, Real* pslot, Real rown[3], int npts)
+// The point of a 1-halo plane that a thread evaluates besides its own
+// (threads below kP1 - kOwn): P1 index i1 and P2 index i2 of p1_point(kOwn + t).
+struct HaloPoint {
+    bool has;
+    int i1, i2;
+};
+__device__ __forceinline__ HaloPoint halo_point()
 {
-    const Real* lo = in + slot3(p - 1) * 6 * kP2;
-    const Real* mid = in + slot3(p) * 6 * kP2;
-    const Real* hi = in + slot3(p + 1) * 6 * kP2;
-    for (int t = threadIdx.x; t < npts; t += blockDim.x) {
+    HaloPoint h{threadIdx.x < kP1 - kOwn, 0, 0};
+    if (h.has) {
         int hx1, hy1;
-        p1_point(t, hx1, hy1);
-        const int i1 = hx1 + kHX1 * hy1;
-        const int i2 = (hx1 + 1) + kHX2 * (hy1 + 1);
-        Real nn[7][3], uu[7][3], r[3], np[3];
-        gather_slots(lo, mid, hi, i2, nn, uu);
-        director_rate(nn, uu, par, r);
+        p1_point(kOwn + threadIdx.x, hx1, hy1);
+        h.i1 = hx1 + kHX1 * hy1;
+        h.i2 = (hx1 + 1) + kHX2 * (hy1 + 1);
+    }
+    return h;
+}
+
+// Predictor at one point of the plane whose input neighbourhood is (lo, mid,
+// hi): n^P into pslot[i1], the rate into r.
+template <typename Real>
+__device__ __forceinline__ void predict_point(const FDPar<Real>& par, const Real* lo, const Real* mid, const Real* hi,
+                                              int i1, int i2, Real* pslot, Real r[3])
+{
+    Real nn[7][3], uu[7][3], np[3];
+    gather_slots(lo, mid, hi, i2, nn, uu);
+    director_rate(nn, uu, par, r);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) np[a] = nn[0][a] + par.dt * r[a];
-        st3(pslot, i1, np);
-        if (t < kOwn) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) rown[a] = r[a];
-        }
+    for (int a = 0; a < 3; ++a) np[a] = nn[0][a] + par.dt * r[a];
+    st3(pslot, i1, np);
+}
+
+// Kernel A, predictor on one plane: the thread's own point (rate kept in
+// rown) and, with halo, its halo point.  The planes just below and above a
+// chunk need n^P only at the tile's own points (halo = false).
+template <typename Real>
+__device__ __forceinline__ void predict_plane(const FDPar<Real>& par, const Real* lo, const Real* mid, const Real* hi,
+                                              Real* pslot, int i1, int i2, const HaloPoint& hp, bool halo, Real rown[3])
+{
+    predict_point(par, lo, mid, hi, i1, i2, pslot, rown);
+    if (halo && hp.has) {
+        Real r[3];
+        predict_point(par, lo, mid, hi, hp.i1, hp.i2, pslot, r);
     }
 }
 
+// Ring slots: plane p of the input ring (6 kP2 Reals) and of the predictor
+// ring (4 kP1 Reals) sits in slot slot3(p); the kernels rotate three slot
+// indices (planes z - 1, z, z + 1) instead of recomputing them.
 template <typename Real>
 __device__ void fused_a_tile(const FDChan<Real>& c, const Real* __restrict__ nin, Real* __restrict__ nout, int tile)
 {
@@ -706,45 +728,51 @@ __device__ void fused_a_tile(const FDChan<Real>& c, const Real* __restrict__ nin
     const int zb = zc * kZC, ze = min(zb + kZC, g.nz);
     const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
     const bool active = threadIdx.x < kTX * kTY && x0 + tx < g.nx && y0 + ty < g.ny;
-    const size_t N = (size_t)g.N;
+    const int N = g.N;
     const int i1 = (tx + 1) + kHX1 * (ty + 1);
     const int i2 = (tx + 2) + kHX2 * (ty + 2);
+    const HaloPoint hp = halo_point();
     const PlaneMap pm = plane_map(g, x0, y0);
+    const bool homeo = g.anchoring == NH_ANCHOR_HOMEOTROPIC;
+    auto IN = [&](int sl) { return in + sl * (6 * kP2); };
+    auto PR = [&](int sl) { return pr + sl * (4 * kP1); };
+    const int s0 = slot3(zb - 2), s1 = slot3(zb - 1), s2 = slot3(zb);
     Real v[kPts][6];
-    for (int p = zb - 2; p <= zb; ++p) {
-        prefetch_plane(nin, c.u, g, pm, p, v);
-        commit_plane(pm, v, in + slot3(p) * 6 * kP2);
-    }
+    prefetch_plane(nin, c.u, g, pm, zb - 2, v);
+    commit_plane(pm, v, IN(s0));
+    prefetch_plane(nin, c.u, g, pm, zb - 1, v);
+    commit_plane(pm, v, IN(s1));
+    prefetch_plane(nin, c.u, g, pm, zb, v);
+    commit_plane(pm, v, IN(s2));
     prefetch_plane(nin, c.u, g, pm, zb + 1, v);  // in flight during the first predictor plane
     __syncthreads();
     Real rcur[3] = {0, 0, 0}, rnext[3] = {0, 0, 0};  // predictor rate at the own point, planes z and z + 1
-    if (!is_ghost_plane(g, zb - 1)) predict_plane(c.p, in, zb - 1, pr + slot3(zb - 1) * 4 * kP1, rnext, kOwn);
+    if (!is_ghost_plane(g, zb - 1)) predict_plane(c.p, IN(s0), IN(s1), IN(s2), PR(s1), i1, i2, hp, false, rnext);
     // u one layer below the corrector's plane, at the thread's own point, carried in registers
     Real ulo[3], nc[3];
-    split_pt(in + slot3(zb - 1) * 6 * kP2, i2, nc, ulo);
+    split_pt(IN(s1), i2, nc, ulo);
     __syncthreads();  // plane zb - 2 is no longer read
-    commit_plane(pm, v, in + slot3(zb + 1) * 6 * kP2);
+    commit_plane(pm, v, IN(s0));  // plane zb + 1
     prefetch_plane(nin, c.u, g, pm, zb + 2, v);
     __syncthreads();
-    if (!is_ghost_plane(g, zb)) predict_plane(c.p, in, zb, pr + slot3(zb) * 4 * kP1, rcur, kP1);
+    if (!is_ghost_plane(g, zb)) predict_plane(c.p, IN(s1), IN(s2), IN(s0), PR(s2), i1, i2, hp, true, rcur);
+    int sa = s1, sb = s2, sc = s0;  // slots of planes z - 1, z, z + 1 (plane z + 2 takes sa)
     for (int z = zb; z < ze; ++z) {
         __syncthreads();  // plane z - 1 is no longer read; its slot takes plane z + 2
-        commit_plane(pm, v, in + slot3(z + 2) * 6 * kP2);
+        commit_plane(pm, v, IN(sa));
         __syncthreads();
         if (z + 1 < ze) prefetch_plane(nin, c.u, g, pm, z + 3, v);  // overlaps the two evaluations below
-        if (!is_ghost_plane(g, z + 1))
-            predict_plane(c.p, in, z + 1, pr + slot3(z + 1) * 4 * kP1, rnext, z + 1 < ze ? kP1 : kOwn);
+        if (!is_ghost_plane(g, z + 1)) predict_plane(c.p, IN(sb), IN(sc), IN(sa), PR(sc), i1, i2, hp, z + 1 < ze, rnext);
         __syncthreads();
         if (active) {
-            const Real* mid = pr + slot3(z) * 4 * kP1;
+            const Real* mid = PR(sb);
             // predictor of the planes above and below; at a plate the ghost
             // value (z_hat, or the adjacent fluid layer without anchoring)
             const bool glo = is_ghost_plane(g, z - 1), ghi = is_ghost_plane(g, z + 1);
-            const bool homeo = g.anchoring == NH_ANCHOR_HOMEOTROPIC;
-            const Real* lo = glo ? mid : pr + slot3(z - 1) * 4 * kP1;
-            const Real* hi = ghi ? mid : pr + slot3(z + 1) * 4 * kP1;
-            const Real* inm = in + slot3(z) * 6 * kP2;
-            const Real* inh = in + slot3(z + 1) * 6 * kP2;
+            const Real* lo = glo ? mid : PR(sa);
+            const Real* hi = ghi ? mid : PR(sc);
+            const Real* inm = IN(sb);
+            const Real* inh = IN(sc);
             Real nn[7][3], uu[7][3], r[3], n0[3], dummy[3];
             ld3(mid, i1, nn[0]);
             ld3(mid, i1 + 1, nn[1]);
@@ -773,7 +801,7 @@ __device__ void fused_a_tile(const FDChan<Real>& c, const Real* __restrict__ nin
 #pragma unroll
             for (int a = 0; a < 3; ++a) nw[a] = n0[a] + c.p.dt * Real(0.5) * (rcur[a] + r[a]);
             const Real inv = Real(1) / sqrt(nw[0] * nw[0] + nw[1] * nw[1] + nw[2] * nw[2]);
-            const size_t s = (size_t)(x0 + tx) + (size_t)g.nx * ((size_t)(y0 + ty) + (size_t)g.ny * z);
+            const int s = (x0 + tx) + g.nx * ((y0 + ty) + g.ny * z);
 #pragma unroll
             for (int a = 0; a < 3; ++a) nout[a * N + s] = nw[a] * inv;
 #pragma unroll
@@ -781,6 +809,10 @@ __device__ void fused_a_tile(const FDChan<Real>& c, const Real* __restrict__ nin
         }
 #pragma unroll
         for (int a = 0; a < 3; ++a) rcur[a] = rnext[a];
+        const int t = sa;
+        sa = sb;
+        sb = sc;
+        sc = t;
     }
 }
 
@@ -789,35 +821,39 @@ __device__ void fused_a_tile(const FDChan<Real>& c, const Real* __restrict__ nin
 // neighbours and sigma_ay at its y neighbours in the same plane (into slot:
 // sigma_.x then sigma_.y, 4 kP1 Reals each), and sigma_az of the point itself
 // in the planes above and below, which stays in the registers of the thread
-// that owns the point (szown; zero on a ghost plane).  npts = kOwn on the
-// planes just below and above a chunk, which give only sigma_az.
+// that owns the point (szown).
 template <typename Real>
-__device__ void stress_plane(const FDChan<Real>& c, const Real* in, int p, Real* slot, Real szown[3], int npts)
+__device__ __forceinline__ void stress_point_plane(const FDPar<Real>& par, const Real* lo, const Real* mid,
+                                                   const Real* hi, int i1, int i2, Real* slot, Real sz[3])
+{
+    Real nn[7][3], uu[7][3], sig[9];
+    gather_slots(lo, mid, hi, i2, nn, uu);
+    stress_point(nn, uu, par, sig);
+    const Real sx[3] = {sig[0], sig[3], sig[6]}, sy[3] = {sig[1], sig[4], sig[7]};
+    st3(slot, i1, sx);
+    st3(slot + 4 * kP1, i1, sy);
+    sz[0] = sig[2];
+    sz[1] = sig[5];
+    sz[2] = sig[8];
+}
+
+// Stress on one plane: zero sigma_az on a ghost plane; otherwise the own point
+// and, with halo, the thread's halo point (the planes just below and above a
+// chunk give only sigma_az: halo = false).
+template <typename Real>
+__device__ __forceinline__ void stress_plane(const FDChan<Real>& c, int p, const Real* lo, const Real* mid,
+                                             const Real* hi, Real* slot, int i1, int i2, bool halo, Real szown[3])
 {
     if (is_ghost_plane(c.g, p)) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) szown[a] = Real(0);
         return;
     }
-    const Real* lo = in + slot3(p - 1) * 6 * kP2;
-    const Real* mid = in + slot3(p) * 6 * kP2;
-    const Real* hi = in + slot3(p + 1) * 6 * kP2;
-    for (int t = threadIdx.x; t < npts; t += blockDim.x) {
-        int hx1, hy1;
-        p1_point(t, hx1, hy1);
-        const int i1 = hx1 + kHX1 * hy1;
-        const int i2 = (hx1 + 1) + kHX2 * (hy1 + 1);
-        Real nn[7][3], uu[7][3], sig[9];
-        gather_slots(lo, mid, hi, i2, nn, uu);
-        stress_point(nn, uu, c.p, sig);
-        const Real sx[3] = {sig[0], sig[3], sig[6]}, sy[3] = {sig[1], sig[4], sig[7]};
-        st3(slot, i1, sx);
-        st3(slot + 4 * kP1, i1, sy);
-        if (t < kOwn) {
-            szown[0] = sig[2];
-            szown[1] = sig[5];
-            szown[2] = sig[8];
-        }
+    stress_point_plane(c.p, lo, mid, hi, i1, i2, slot, szown);
+    const HaloPoint hp = halo_point();  // recomputed here: kernel B runs at the register limit
+    if (halo && hp.has) {
+        Real sz[3];
+        stress_point_plane(c.p, lo, mid, hi, hp.i1, hp.i2, slot, sz);
     }
 }
 
@@ -825,8 +861,8 @@ template <typename Real>
 __device__ void fused_b_tile(const FDChan<Real>& c, const Real* __restrict__ nin, Real* __restrict__ ncopy, int tile)
 {
     extern __shared__ __align__(16) unsigned char smem_fd[];
-    Real* in = reinterpret_cast<Real*>(smem_fd);  // 3 slots x 6 x kP2 (planes z, z + 1, z + 2)
-    Real* sg = in + 3 * 6 * kP2;                  // 2 slots x 8 x kP1 (sigma_.x, sigma_.y)
+    Real* in = reinterpret_cast<Real*>(smem_fd);  // 3 slots x 6 x kP2 (input planes)
+    Real* sg = in + 3 * 6 * kP2;                  // 2 slots x 8 x kP1 (sigma_.x, sigma_.y), slot z & 1
     const Geom& g = c.g;
     const int ntx = (g.nx + kTX - 1) / kTX, nty = (g.ny + kTY - 1) / kTY;
     const int tx_t = tile % ntx, ty_t = (tile / ntx) % nty, zc = tile / (ntx * nty);
@@ -834,45 +870,51 @@ __device__ void fused_b_tile(const FDChan<Real>& c, const Real* __restrict__ nin
     const int zb = zc * kZC, ze = min(zb + kZC, g.nz);
     const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
     const bool active = threadIdx.x < kTX * kTY && x0 + tx < g.nx && y0 + ty < g.ny;
-    const size_t N = (size_t)g.N;
+    const int N = g.N;
     const int i1 = (tx + 1) + kHX1 * (ty + 1);
     const int i2 = (tx + 2) + kHX2 * (ty + 2);
     const PlaneMap pm = plane_map(g, x0, y0);
+    auto IN = [&](int sl) { return in + sl * (6 * kP2); };
+    auto SG = [&](int p) { return sg + (p & 1) * (8 * kP1); };
+    const int s0 = slot3(zb - 2), s1 = slot3(zb - 1), s2 = slot3(zb);
     Real v[kPts][6];
-    for (int p = zb - 2; p <= zb; ++p) {
-        prefetch_plane(nin, c.u, g, pm, p, v);
-        commit_plane(pm, v, in + slot3(p) * 6 * kP2);
-    }
+    prefetch_plane(nin, c.u, g, pm, zb - 2, v);
+    commit_plane(pm, v, IN(s0));
+    prefetch_plane(nin, c.u, g, pm, zb - 1, v);
+    commit_plane(pm, v, IN(s1));
+    prefetch_plane(nin, c.u, g, pm, zb, v);
+    commit_plane(pm, v, IN(s2));
     prefetch_plane(nin, c.u, g, pm, zb + 1, v);  // in flight during the first stress plane
     __syncthreads();
     Real szlo[3], szmid[3], szhi[3];  // sigma_az at the own point, planes z - 1, z, z + 1
-    stress_plane(c, in, zb - 1, sg + ((zb - 1) & 1) * 8 * kP1, szlo, kOwn);
+    stress_plane(c, zb - 1, IN(s0), IN(s1), IN(s2), SG(zb - 1), i1, i2, false, szlo);
     __syncthreads();  // plane zb - 2 is no longer read
-    commit_plane(pm, v, in + slot3(zb + 1) * 6 * kP2);
+    commit_plane(pm, v, IN(s0));  // plane zb + 1
     prefetch_plane(nin, c.u, g, pm, zb + 2, v);
     __syncthreads();
-    stress_plane(c, in, zb, sg + (zb & 1) * 8 * kP1, szmid, kP1);
+    stress_plane(c, zb, IN(s1), IN(s2), IN(s0), SG(zb), i1, i2, true, szmid);
+    int sa = s1, sb = s2, sc = s0;  // input slots of planes z - 1, z, z + 1 (plane z + 2 takes sa)
     for (int z = zb; z < ze; ++z) {
         __syncthreads();  // plane z - 1 is no longer read; its slots take planes z + 2 (input), z + 1 (sigma)
-        commit_plane(pm, v, in + slot3(z + 2) * 6 * kP2);
+        commit_plane(pm, v, IN(sa));
         __syncthreads();
         if (z + 1 < ze) prefetch_plane(nin, c.u, g, pm, z + 3, v);
-        stress_plane(c, in, z + 1, sg + ((z + 1) & 1) * 8 * kP1, szhi, z + 1 < ze ? kP1 : kOwn);
+        stress_plane(c, z + 1, IN(sb), IN(sc), IN(sa), SG(z + 1), i1, i2, z + 1 < ze, szhi);
         __syncthreads();
         if (active) {
-            const Real* sx = sg + (z & 1) * 8 * kP1;
+            const Real* sx = SG(z);
             const Real* sy = sx + 4 * kP1;
             Real xp[3], xm[3], yp[3], ym[3];
             ld3(sx, i1 + 1, xp);
             ld3(sx, i1 - 1, xm);
             ld3(sy, i1 + kHX1, yp);
             ld3(sy, i1 - kHX1, ym);
-            const size_t s = (size_t)(x0 + tx) + (size_t)g.nx * ((size_t)(y0 + ty) + (size_t)g.ny * z);
+            const int s = (x0 + tx) + g.nx * ((y0 + ty) + g.ny * z);
 #pragma unroll
             for (int a = 0; a < 3; ++a) c.F[a * N + s] = Real(0.5) * ((xp[a] - xm[a]) + (yp[a] - ym[a]) + (szhi[a] - szlo[a]));
             if (ncopy) {
                 Real n0[3], u0[3];
-                split_pt(in + slot3(z) * 6 * kP2, i2, n0, u0);
+                split_pt(IN(sb), i2, n0, u0);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) ncopy[a * N + s] = n0[a];
             }
@@ -882,6 +924,10 @@ __device__ void fused_b_tile(const FDChan<Real>& c, const Real* __restrict__ nin
             szlo[a] = szmid[a];
             szmid[a] = szhi[a];
         }
+        const int t = sa;
+        sa = sb;
+        sb = sc;
+        sc = t;
     }
 }
 
