@@ -153,6 +153,135 @@ __device__ __forceinline__ Real link_energy(const Real n[3], const Real m[3], in
     return Real(0.5) * K * (d0 * d0 + d1 * d1 + d2 * d2) - K * q0 * cr;
 }
 
+// Nearest previous tube centroid of column (x, y) (-1 without tubes): FP32
+// squared distances with the periodic minimum image; a near-tie of the two
+// best is settled in FP64 so that the choice equals the FP64 one.
+__device__ __forceinline__ int nearest_tube(const DiagArgs& a, const float (*txy)[2], int T, int x, int y)
+{
+    const Geom& g = a.g;
+    int owner = -1, second = -1;
+    float bd = 3.0e38f, bd2 = 3.0e38f;
+    const float hx = 0.5f * g.nx, hy = 0.5f * g.ny;
+    for (int k = 0; k < T; ++k) {
+        float dx = (float)x - txy[k][0], dy = (float)y - txy[k][1];
+        dx = dx > hx ? dx - g.nx : (dx < -hx ? dx + g.nx : dx);
+        dy = dy > hy ? dy - g.ny : (dy < -hy ? dy + g.ny : dy);
+        const float d2 = dx * dx + dy * dy;
+        if (d2 < bd) {
+            bd2 = bd;
+            second = owner;
+            bd = d2;
+            owner = k;
+        } else if (d2 < bd2) {
+            bd2 = d2;
+            second = k;
+        }
+    }
+    if (second >= 0 && bd2 - bd <= 1e-3f * (1.f + bd)) {
+        double d2[2];
+        const int cand[2] = {owner, second};
+        for (int j = 0; j < 2; ++j) {
+            double dx = x - a.tubes[cand[j]][0], dy = y - a.tubes[cand[j]][1];
+            dx = dx > 0.5 * g.nx ? dx - g.nx : (dx < -0.5 * g.nx ? dx + g.nx : dx);
+            dy = dy > 0.5 * g.ny ? dy - g.ny : (dy < -0.5 * g.ny ? dy + g.ny : dy);
+            d2[j] = dx * dx + dy * dy;
+        }
+        // lowest index wins an exact tie, as in a first-minimum search
+        if (d2[1] < d2[0] || (d2[1] == d2[0] && cand[1] < cand[0])) owner = cand[1];
+    }
+    return owner;
+}
+
+// Centroid sums of one column with tube weight wsum: wsum and wsum times
+// sin / cos of 2 pi x / nx and 2 pi y / ny (FP64 tables in the FP64 build,
+// sincospi in FP32 in the FP32 build).
+template <typename Real>
+__device__ __forceinline__ void tube_values(const DiagArgs& a, int x, int y, Real wsum, Real v[5])
+{
+    const Geom& g = a.g;
+    v[0] = wsum;
+    if (sizeof(Real) == 8) {
+        v[1] = wsum * Real(a.trig[x]);                    // sin(2 pi x / nx)
+        v[2] = wsum * Real(a.trig[g.nx + x]);             // cos(2 pi x / nx)
+        v[3] = wsum * Real(a.trig[2 * g.nx + y]);         // sin(2 pi y / ny)
+        v[4] = wsum * Real(a.trig[2 * g.nx + g.ny + y]);  // cos(2 pi y / ny)
+    } else {
+        float sx, cx, sy, cy;
+        sincospif(2.f * (float)x / (float)g.nx, &sx, &cx);
+        sincospif(2.f * (float)y / (float)g.ny, &sy, &cy);
+        v[1] = wsum * Real(sx);
+        v[2] = wsum * Real(cx);
+        v[3] = wsum * Real(sy);
+        v[4] = wsum * Real(cy);
+    }
+}
+
+// Adds each lane's five tube values to its owner's row of the warp's
+// accumulator (lane 0 writes; one warp sum per distinct owner in the warp).
+// Every lane of the warp calls it (owner -1: nothing to add).
+template <typename Real>
+__device__ __forceinline__ void warp_tube_accumulate(int owner, const Real v[5], int lane, Real* acc)
+{
+    unsigned pending = __ballot_sync(0xffffffffu, owner >= 0);
+    while (pending) {
+        const int t = __shfl_sync(0xffffffffu, owner, __ffs(pending) - 1);
+        const bool mine = owner == t;
+        pending &= ~__ballot_sync(0xffffffffu, mine);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const Real sum = warp_sum(mine ? v[k] : Real(0));
+            if (lane == 0) acc[t * 5 + k] += sum;
+        }
+    }
+}
+
+// Block partials, value-major (partials[k * gridDim.x + block]): FP64 sums
+// of the threads' mass and energy, extrema, NaN count, then the tube sums
+// combined across the block's warps in a fixed order.
+template <typename Real>
+__device__ __forceinline__ void diag_block_partials(const DiagArgs& a, Real mass_t, Real energy_t, Real max_u,
+                                                    Real min_nn, Real max_nn, int bad,
+                                                    const Real (*tube_acc)[NH_MAX_TUBES * 5], int T)
+{
+    __shared__ double red[DIAG_THREADS / 32][DIAG_FIXED];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double dmax_u = (double)max_u, dmin_nn = (double)min_nn, dmax_nn = (double)max_nn, dbad = (double)bad;
+    double mass = warp_sum((double)mass_t);
+    double energy = warp_sum((double)energy_t);
+    dbad = warp_sum(dbad);
+    dmax_u = warp_max(dmax_u);
+    dmin_nn = warp_min(dmin_nn);
+    dmax_nn = warp_max(dmax_nn);
+    if (lane == 0) {
+        red[wid][0] = mass;
+        red[wid][1] = energy;
+        red[wid][2] = dmax_u;
+        red[wid][3] = dmin_nn;
+        red[wid][4] = dmax_nn;
+        red[wid][5] = dbad;
+    }
+    __syncthreads();
+    double* out = a.partials + blockIdx.x;
+    const size_t stride = gridDim.x;
+    if (threadIdx.x == 0) {
+        double v[DIAG_FIXED] = {0.0, 0.0, 0.0, 1e300, 0.0, 0.0};
+        for (int w = 0; w < DIAG_THREADS / 32; ++w) {
+            v[0] += red[w][0];
+            v[1] += red[w][1];
+            v[2] = fmax(v[2], red[w][2]);
+            v[3] = fmin(v[3], red[w][3]);
+            v[4] = fmax(v[4], red[w][4]);
+            v[5] += red[w][5];
+        }
+        for (int k = 0; k < DIAG_FIXED; ++k) out[k * stride] = v[k];
+    }
+    for (int k = threadIdx.x; k < 5 * T; k += blockDim.x) {
+        double acc = 0.0;
+        for (int w = 0; w < DIAG_THREADS / 32; ++w) acc += (double)tube_acc[w][k];  // fixed order
+        out[(DIAG_FIXED + k) * stride] = acc;
+    }
+}
+
 // Work item = (x, y) column x a chunk of kDiagChunk layers; one thread per item
 // (grid-stride; the items of a warp share the chunk, so z-branches are uniform).
 // A thread marches up its chunk: the director of the next layer is loaded one
@@ -198,7 +327,6 @@ __global__ void __launch_bounds__(DIAG_THREADS, (sizeof(Real) == 4 && !F3 && !So
     // row: no atomics); combined in FP64 across warps and blocks
     __shared__ Real tube_acc[DIAG_THREADS / 32][NH_MAX_TUBES * 5];
     __shared__ float tube_xy[NH_MAX_TUBES][2];
-    __shared__ double red[DIAG_THREADS / 32][DIAG_FIXED];
     for (int k = threadIdx.x; k < (DIAG_THREADS / 32) * NH_MAX_TUBES * 5; k += blockDim.x)
         (&tube_acc[0][0])[k] = Real(0);
     for (int k = threadIdx.x; k < T; k += blockDim.x) {
@@ -328,105 +456,203 @@ __global__ void __launch_bounds__(DIAG_THREADS, (sizeof(Real) == 4 && !F3 && !So
             int owner = -1;
             Real v[5] = {0, 0, 0, 0, 0};
             if (valid) {
-                // nearest previous centroid: FP32 squared distances with the
-                // periodic minimum image; a near-tie of the two best is settled
-                // in FP64 so that the choice equals the FP64 one.
-                float bd = 3.0e38f, bd2 = 3.0e38f;
-                int second = -1;
-                const float hx = 0.5f * g.nx, hy = 0.5f * g.ny;
-                for (int k = 0; k < T; ++k) {
-                    float dx = (float)x - tube_xy[k][0], dy = (float)y - tube_xy[k][1];
-                    dx = dx > hx ? dx - g.nx : (dx < -hx ? dx + g.nx : dx);
-                    dy = dy > hy ? dy - g.ny : (dy < -hy ? dy + g.ny : dy);
-                    const float d2 = dx * dx + dy * dy;
-                    if (d2 < bd) {
-                        bd2 = bd;
-                        second = owner;
-                        bd = d2;
-                        owner = k;
-                    } else if (d2 < bd2) {
-                        bd2 = d2;
-                        second = k;
-                    }
-                }
-                if (second >= 0 && bd2 - bd <= 1e-3f * (1.f + bd)) {
-                    double d2[2];
-                    const int cand[2] = {owner, second};
-                    for (int j = 0; j < 2; ++j) {
-                        double dx = x - a.tubes[cand[j]][0], dy = y - a.tubes[cand[j]][1];
-                        dx = dx > 0.5 * g.nx ? dx - g.nx : (dx < -0.5 * g.nx ? dx + g.nx : dx);
-                        dy = dy > 0.5 * g.ny ? dy - g.ny : (dy < -0.5 * g.ny ? dy + g.ny : dy);
-                        d2[j] = dx * dx + dy * dy;
-                    }
-                    // lowest index wins an exact tie, as in a first-minimum search
-                    if (d2[1] < d2[0] || (d2[1] == d2[0] && cand[1] < cand[0])) owner = cand[1];
-                }
-                v[0] = wsum;
-                if (sizeof(Real) == 8) {
-                    v[1] = wsum * Real(a.trig[x]);                    // sin(2 pi x / nx)
-                    v[2] = wsum * Real(a.trig[g.nx + x]);             // cos(2 pi x / nx)
-                    v[3] = wsum * Real(a.trig[2 * g.nx + y]);         // sin(2 pi y / ny)
-                    v[4] = wsum * Real(a.trig[2 * g.nx + g.ny + y]);  // cos(2 pi y / ny)
-                } else {
-                    // FP32 build: the angles in FP32 (sin/cos of pi * 2x/nx), no FP64 conversions
-                    float sx, cx, sy, cy;
-                    sincospif(2.f * (float)x / (float)g.nx, &sx, &cx);
-                    sincospif(2.f * (float)y / (float)g.ny, &sy, &cy);
-                    v[1] = wsum * Real(sx);
-                    v[2] = wsum * Real(cx);
-                    v[3] = wsum * Real(sy);
-                    v[4] = wsum * Real(cy);
-                }
+                owner = nearest_tube(a, tube_xy, T, x, y);
+                tube_values(a, x, y, wsum, v);
             }
-            unsigned pending = __ballot_sync(0xffffffffu, owner >= 0);
-            while (pending) {
-                const int t = __shfl_sync(0xffffffffu, owner, __ffs(pending) - 1);
-                const bool mine = owner == t;
-                pending &= ~__ballot_sync(0xffffffffu, mine);
-#pragma unroll
-                for (int k = 0; k < 5; ++k) {
-                    const Real sum = warp_sum(mine ? v[k] : Real(0));
-                    if (lane == 0) tube_acc[wid][t * 5 + k] += sum;
-                }
-            }
+            warp_tube_accumulate(owner, v, lane, tube_acc[wid]);
         }
     }
-    double dmax_u = (double)max_u, dmin_nn = (double)min_nn, dmax_nn = (double)max_nn, dbad = (double)bad;
-    double mass = warp_sum((double)mass_t);
-    double energy = warp_sum((double)energy_t);
-    dbad = warp_sum(dbad);
-    dmax_u = warp_max(dmax_u);
-    dmin_nn = warp_min(dmin_nn);
-    dmax_nn = warp_max(dmax_nn);
-    if (lane == 0) {
-        red[wid][0] = mass;
-        red[wid][1] = energy;
-        red[wid][2] = dmax_u;
-        red[wid][3] = dmin_nn;
-        red[wid][4] = dmax_nn;
-        red[wid][5] = dbad;
+    diag_block_partials(a, mass_t, energy_t, max_u, min_nn, max_nn, bad, tube_acc, T);
+}
+
+// Two-column variant of the plain path (one-constant energy, no obstacles,
+// nx even): an item is the x-pair of columns (x, x + 1), x even, times a
+// chunk of kDiagPairChunk layers.  Populations, n, u and rho of the pair are
+// read as one 2-vector each (s even, so the vectors are aligned), the x + 1
+// partner of the first site is the second site, and only the second site's
+// x + 1 partner is a scalar load: half the load instructions per site of the
+// one-column kernel, twice the bytes in flight per thread.  The same sums.
+constexpr int kDiagPairChunk = 4;
+
+template <typename Real>
+struct Pair;
+template <>
+struct Pair<float> {
+    using T = float2;
+};
+template <>
+struct Pair<double> {
+    using T = double2;
+};
+
+template <typename Real>
+__device__ __forceinline__ void load3_pair(const Real* __restrict__ n, int N, int s, Real p[3], Real q[3])
+{
+    using V = typename Pair<Real>::T;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const V v = __ldg(reinterpret_cast<const V*>(n + k * N + s));
+        p[k] = v.x;
+        q[k] = v.y;
+    }
+}
+
+// Two consecutive populations (sites s, s + 1 of one plane), decoded as Codec does.
+template <typename Real>
+__device__ __forceinline__ void pop_pair(const Real* p, float, Real& a, Real& b)
+{
+    const typename Pair<Real>::T v = __ldg(reinterpret_cast<const typename Pair<Real>::T*>(p));
+    a = v.x;
+    b = v.y;
+}
+__device__ __forceinline__ void pop_pair(const __half* p, float inv_scale, float& a, float& b)
+{
+    const __half2 h = __ldg(reinterpret_cast<const __half2*>(p));
+    a = __low2float(h) * inv_scale;
+    b = __high2float(h) * inv_scale;
+}
+__device__ __forceinline__ void pop_pair(const __nv_bfloat16* p, float inv_scale, float& a, float& b)
+{
+    const __nv_bfloat162 h = __ldg(reinterpret_cast<const __nv_bfloat162*>(p));
+    a = __low2float(h) * inv_scale;
+    b = __high2float(h) * inv_scale;
+}
+
+template <typename Real, typename Store>
+__global__ void __launch_bounds__(DIAG_THREADS, sizeof(Real) == 4 ? 4 : 1) diag_pair_kernel(const DiagArgs a)
+{
+    const Geom g = a.g;
+    const int N = g.N;
+    const int cols = g.nx * g.ny;
+    const int hx = g.nx >> 1;  // pairs per row
+    const int pcols = hx * g.ny;
+    const int chunks = (g.nz + kDiagPairChunk - 1) / kDiagPairChunk;
+    const int items = pcols * chunks;
+    const Store* __restrict__ f = static_cast<const Store*>(a.f);
+    const Real* __restrict__ n = static_cast<const Real*>(a.n);
+    const Real* __restrict__ u = static_cast<const Real*>(a.u);
+    const Real* __restrict__ rho = static_cast<const Real*>(a.rho);
+    const float inv_scale = sizeof(Store) == 2 ? 1.f / a.scale[0] : 1.f;
+    const Real K = Real(a.K), q0 = Real(a.q0), W0 = Real(a.W0);
+    const Real site_const = Real(0.5) * K * q0 * q0;
+    const bool homeo = g.walls && g.anchoring == NH_ANCHOR_HOMEOTROPIC;
+    const int T = a.n_tubes;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __shared__ Real tube_acc[DIAG_THREADS / 32][NH_MAX_TUBES * 5];
+    __shared__ float tube_xy[NH_MAX_TUBES][2];
+    for (int k = threadIdx.x; k < (DIAG_THREADS / 32) * NH_MAX_TUBES * 5; k += blockDim.x)
+        (&tube_acc[0][0])[k] = Real(0);
+    for (int k = threadIdx.x; k < T; k += blockDim.x) {
+        tube_xy[k][0] = (float)a.tubes[k][0];
+        tube_xy[k][1] = (float)a.tubes[k][1];
     }
     __syncthreads();
-    // block partials, value-major: partials[k * gridDim.x + block]
-    double* out = a.partials + blockIdx.x;
-    const size_t stride = gridDim.x;
-    if (threadIdx.x == 0) {
-        double v[DIAG_FIXED] = {0.0, 0.0, 0.0, 1e300, 0.0, 0.0};
-        for (int w = 0; w < DIAG_THREADS / 32; ++w) {
-            v[0] += red[w][0];
-            v[1] += red[w][1];
-            v[2] = fmax(v[2], red[w][2]);
-            v[3] = fmin(v[3], red[w][3]);
-            v[4] = fmax(v[4], red[w][4]);
-            v[5] += red[w][5];
+
+    Real mass_t = 0, energy_t = 0;
+    Real max_u = 0, min_nn = Real(1e30), max_nn = 0;
+    int bad = 0;
+    for (int base = blockIdx.x * blockDim.x; base < items; base += gridDim.x * blockDim.x) {
+        const int item = base + threadIdx.x;
+        const bool valid = item < items;
+        Real wsum0 = 0, wsum1 = 0;
+        int x = 0, y = 0;
+        if (valid) {
+            const int pc = item % pcols;
+            const int z0 = (item / pcols) * kDiagPairChunk;
+            const int z1 = min(z0 + kDiagPairChunk, g.nz);
+            x = 2 * (pc % hx);
+            y = pc / hx;
+            const int col = x + g.nx * y;
+            const int colx2 = (x + 2 == g.nx ? 0 : x + 2) + g.nx * y;  // x + 1 partner of the second site
+            const int coly = x + g.nx * (y + 1 == g.ny ? 0 : y + 1);
+            Real msum = 0, esum = 0;
+            Real c0[3], c1[3];
+            load3_pair(n, N, col + cols * z0, c0, c1);
+            if (g.walls && z0 == 0) {
+                // links from the lower ghost layer to the first fluid layer
+                Real m0[3] = {c0[0], c0[1], c0[2]}, m1[3] = {c1[0], c1[1], c1[2]};
+                if (homeo) {
+                    m0[0] = m0[1] = m1[0] = m1[1] = Real(0);
+                    m0[2] = m1[2] = Real(1);
+                }
+                esum += link_energy(m0, c0, 2, K, q0);
+                esum += link_energy(m1, c1, 2, K, q0);
+            }
+#pragma unroll 2
+            for (int z = z0; z < z1; ++z) {
+                const int s = col + cols * z;
+                Real n0[3], n1[3];  // z + 1 partners
+                if (z + 1 < g.nz) {
+                    load3_pair(n, N, s + cols, n0, n1);
+                } else if (!g.walls) {
+                    load3_pair(n, N, col, n0, n1);  // periodic in z
+                } else if (homeo) {
+                    n0[0] = n0[1] = n1[0] = n1[1] = Real(0);
+                    n0[2] = n1[2] = Real(1);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        n0[k] = c0[k];
+                        n1[k] = c1[k];
+                    }
+                }
+                Real y0[3], y1[3], x2[3];
+                load3_pair(n, N, coly + cols * z, y0, y1);
+                load3(n, N, colx2 + cols * z, x2);
+                Real fs0 = 0, fs1 = 0;
+#pragma unroll
+                for (int i = 0; i < 19; ++i) {
+                    Real p0, p1;
+                    pop_pair(f + (size_t)i * N + s, inv_scale, p0, p1);
+                    fs0 += p0;
+                    fs1 += p1;
+                }
+                Real ua[3], ub[3];
+                load3_pair(u, N, s, ua, ub);
+                const typename Pair<Real>::T r = __ldg(reinterpret_cast<const typename Pair<Real>::T*>(rho + s));
+                Real e = link_energy(c0, c1, 0, K, q0);
+                e += link_energy(c0, y0, 1, K, q0);
+                e += link_energy(c0, n0, 2, K, q0);
+                e += link_energy(c1, x2, 0, K, q0);
+                e += link_energy(c1, y1, 1, K, q0);
+                e += link_energy(c1, n1, 2, K, q0);
+                esum += e;
+                msum += fs0 + fs1;
+                esum += Real(2) * site_const - Real(0.5) * W0 * (c0[2] * c0[2] + c1[2] * c1[2]);
+                const Real umag0 = sqrt(ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2]);
+                const Real umag1 = sqrt(ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
+                const Real nmag0 = sqrt(c0[0] * c0[0] + c0[1] * c0[1] + c0[2] * c0[2]);
+                const Real nmag1 = sqrt(c1[0] * c1[0] + c1[1] * c1[1] + c1[2] * c1[2]);
+                max_u = max(max_u, max(umag0, umag1));
+                min_nn = min(min_nn, min(nmag0, nmag1));
+                max_nn = max(max_nn, max(nmag0, nmag1));
+                if (!isfinite(umag0) || !isfinite(nmag0) || !isfinite(r.x) || !isfinite(fs0)) bad += 1;
+                if (!isfinite(umag1) || !isfinite(nmag1) || !isfinite(r.y) || !isfinite(fs1)) bad += 1;
+                wsum0 += Real(0.5) * (Real(1) - c0[2]);
+                wsum1 += Real(0.5) * (Real(1) - c1[2]);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    c0[k] = n0[k];
+                    c1[k] = n1[k];
+                }
+            }
+            mass_t += msum;
+            energy_t += esum;
         }
-        for (int k = 0; k < DIAG_FIXED; ++k) out[k * stride] = v[k];
+        if (T > 0) {
+#pragma unroll 1
+            for (int j = 0; j < 2; ++j) {
+                int owner = -1;
+                Real v[5] = {0, 0, 0, 0, 0};
+                if (valid) {
+                    owner = nearest_tube(a, tube_xy, T, x + j, y);
+                    tube_values(a, x + j, y, j ? wsum1 : wsum0, v);
+                }
+                warp_tube_accumulate(owner, v, lane, tube_acc[wid]);
+            }
+        }
     }
-    for (int k = threadIdx.x; k < 5 * T; k += blockDim.x) {
-        double acc = 0.0;
-        for (int w = 0; w < DIAG_THREADS / 32; ++w) acc += (double)tube_acc[w][k];  // fixed order
-        out[(DIAG_FIXED + k) * stride] = acc;
-    }
+    diag_block_partials(a, mass_t, energy_t, max_u, min_nn, max_nn, bad, tube_acc, T);
 }
 
 // One block per reduced value: each thread combines a strided subset of the
@@ -638,6 +864,32 @@ cudaError_t launch_trig_table(double* t, int nx, int ny, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// The two-column kernel takes the plain path (no three-constant energy, no
+// obstacles) when nx is even and every field pointer is aligned to its 2-vector
+// (caller-owned buffers, as in the no-allocation entry point, may not be);
+// otherwise the one-column kernel runs.
+inline bool aligned_to(const void* p, size_t bytes) { return reinterpret_cast<uintptr_t>(p) % bytes == 0; }
+inline bool diag_pairs(const DiagArgs& a)
+{
+    if (a.solid != nullptr || a.frank3 || a.g.nx % 2 != 0) return false;
+    const size_t real2 = a.precision == NH_FP64 ? 16 : 8;
+    const size_t store2 = a.precision == NH_FP64 ? 16 : (a.storage == NH_STORE_F32 ? 8 : 4);
+    return aligned_to(a.f, store2) && aligned_to(a.n, real2) && aligned_to(a.u, real2) && aligned_to(a.rho, real2);
+}
+
+void launch_diag_pair_kernel(const DiagArgs& a, int blocks, cudaStream_t st)
+{
+    if (a.precision == NH_FP64) {
+        diag_pair_kernel<double, double><<<blocks, DIAG_THREADS, 0, st>>>(a);
+        return;
+    }
+    switch (a.storage) {
+    case NH_STORE_F32: diag_pair_kernel<float, float><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
+    case NH_STORE_F16S: diag_pair_kernel<float, __half><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
+    default: diag_pair_kernel<float, __nv_bfloat16><<<blocks, DIAG_THREADS, 0, st>>>(a); break;
+    }
+}
+
 template <bool Solid>
 void launch_diag_kernel(const DiagArgs& a, int blocks, cudaStream_t st)
 {
@@ -663,10 +915,15 @@ void launch_diag_kernel(const DiagArgs& a, int blocks, cudaStream_t st)
 
 cudaError_t launch_diagnostics(const DiagArgs& a, cudaStream_t st)
 {
-    const int items = a.g.nx * a.g.ny * ((a.g.nz + kDiagChunk - 1) / kDiagChunk);
+    const bool pairs = diag_pairs(a);
+    const int items = pairs ? (a.g.nx / 2) * a.g.ny * ((a.g.nz + kDiagPairChunk - 1) / kDiagPairChunk)
+                            : a.g.nx * a.g.ny * ((a.g.nz + kDiagChunk - 1) / kDiagChunk);
     int blocks = (items + DIAG_THREADS - 1) / DIAG_THREADS;
     if (blocks > a.blocks) blocks = a.blocks;
-    if (a.solid != nullptr)
+    if (pairs && blocks > 4 * 152) blocks = 4 * 152;  // the two-column kernel keeps 4 blocks per SM resident
+    if (pairs)
+        launch_diag_pair_kernel(a, blocks, st);
+    else if (a.solid != nullptr)
         launch_diag_kernel<true>(a, blocks, st);
     else
         launch_diag_kernel<false>(a, blocks, st);
