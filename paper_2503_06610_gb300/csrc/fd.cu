@@ -472,11 +472,13 @@ __global__ void __launch_bounds__(256) fd_batch_kernel(const FDBatch<Real> b)
 //
 // A block owns a tile of kTX x kTY columns and marches up a chunk of kZC
 // layers.  Planes of n and u with a 2-site halo in x and y sit in a ring of
-// shared-memory slots (4 in kernel A, whose corrector also reads u one layer
-// below, 3 in kernel B); the predictor (kernel A) or the stress (kernel B) is
-// evaluated on each plane with a 1-site halo into a ring of 3 slots, so every
-// stencil reads shared memory at fixed offsets and the ghost layers are
-// resolved once, at load time.
+// three shared-memory slots; the predictor (kernel A) or the stress (kernel
+// B) is evaluated on each plane with a 1-site halo, so every stencil reads
+// shared memory at fixed offsets and the ghost layers are resolved once, at
+// load time.  Kernel A keeps the predicted planes in a ring of three slots;
+// kernel B keeps sigma_.x and sigma_.y of two planes.  What only a thread's
+// own point needs (u one layer below, the predictor's rate, sigma_.z) stays in
+// that thread's registers.
 //   kernel A: n, u -> n_new   (predictor, corrector, renormalisation)
 //   kernel B: n_new, u -> F   (stress, divergence; sigma never leaves the SM)
 
@@ -490,7 +492,6 @@ __device__ __forceinline__ int wrapm(int a, int n)
     a %= n;
     return a < 0 ? a + n : a;
 }
-__device__ __forceinline__ int slot4(int p) { return ((p % 4) + 4) % 4; }
 __device__ __forceinline__ int slot3(int p) { return ((p % 3) + 3) % 3; }
 
 template <typename Real>
