@@ -920,7 +920,7 @@ cudaError_t launch_diagnostics(const DiagArgs& a, cudaStream_t st)
                             : a.g.nx * a.g.ny * ((a.g.nz + kDiagChunk - 1) / kDiagChunk);
     int blocks = (items + DIAG_THREADS - 1) / DIAG_THREADS;
     if (blocks > a.blocks) blocks = a.blocks;
-    if (pairs && blocks > 4 * 152) blocks = 4 * 152;  // the two-column kernel keeps 4 blocks per SM resident
+    if (pairs && blocks > 4 * 152) blocks = 4 * 152;  // two-column kernel: 4 resident blocks on each of 152 SMs
     if (pairs)
         launch_diag_pair_kernel(a, blocks, st);
     else if (a.solid != nullptr)
