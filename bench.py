@@ -13,7 +13,7 @@ inside the timed region.  With --gpus N (torchrun) every rank runs its own
 replica of the workload (independent channels, no data-path collective):
 weak scaling, value = sum over ranks.
 
---impl reference times the FP64 CPU oracle on the machine's host cores on the same
+--impl reference times the FP64 CPU oracle on the host's CPU cores on the same
 workload (one LB step per bench step plus the FD update every dt_FD steps).
 """
 from __future__ import annotations

@@ -350,7 +350,8 @@ int nh_diagnostics_noalloc(const nh_params* p, const void* f, const void* n, con
  * Learned warm start (no counterpart in the paper): a 3D U-Net (4 levels, widths
  * 16/16/32/64, 394 419 parameters) that maps the extruded skyrmion ansatz and
  * the channel parameters (q0, Lz, W0) to the relaxed director; the plain
- * relaxation (nh_relax) continues from its prediction and judges it.
+ * relaxation (nh_relax) continues from its prediction, which counts only if
+ * that run ends where the relaxation from the ansatz ends.
  * Activations are BF16, accumulation FP32, convolutions run on the tensor
  * cores; parameters, gradients and Adam moments are caller-owned FP32 device
  * vectors in the layout: per conv layer W[tap][cout][cin] (tap = 9 kz + 3 ky

@@ -6,7 +6,7 @@ until the director's largest rate of change, measured over ``check_every`` FD
 steps, is below ``tol`` (``nh_director_change``).  A 3D U-Net with BF16 kernels
 (``nh_unet_*``) is trained on such relaxations to predict the relaxed field
 from the ansatz and (q0, Lz, W0); the plain relaxation then continues from the
-prediction and judges it: the result must match the relaxation from the ansatz
+prediction, and the prediction counts only if the result matches the relaxation from the ansatz
 within ``max |dn| <= 1e-4``, and the saving is reported in FD steps and wall
 time.
 
