@@ -85,24 +85,99 @@ def ncu_traffic():
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clocks and throttle reasons, one line every 200 ms, started
+    before the warm-up so that it samples from the first timed step on.  The
+    lines carry nvidia-smi's timestamp; stop() reports the samples taken between
+    region_start() and region_end() (host wall clock), or, when none fell inside
+    (a region shorter than the interval), the sample nearest to the region."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
-    def __init__(self, gpu_index):
-        self.gpu = gpu_index
+    def __init__(self, gpu_index, interval_ms=200):
+        self.gpu = self.smi_id(gpu_index)
+        self.interval_ms = interval_ms
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                ["nvidia-smi", "-i", self.gpu, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", str(self.interval_ms)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+
+    def region_start(self):
+        self.t0 = time.time()
+
+    def region_end(self):
+        self.t1 = time.time()
+
+    @staticmethod
+    def smi_id(local):
+        """nvidia-smi's -i argument for CUDA device `local` of this process: its
+        UUID, else its CUDA_VISIBLE_DEVICES entry, else the index -- the first
+        that nvidia-smi accepts (the index alone when nvidia-smi is missing)."""
+        cands = []
+        try:
+            import torch
+            u = str(torch.cuda.get_device_properties(local).uuid)
+            cands.append(u if u.startswith("GPU-") else "GPU-" + u)
+        except Exception:
+            pass
+        ids = [v.strip() for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+        if local < len(ids):
+            cands.append(ids[local])
+        cands.append(str(local))
+        for c in cands:
+            try:
+                r = subprocess.run(["nvidia-smi", "-i", c, "--query-gpu=index", "--format=csv,noheader"],
+                                   capture_output=True, timeout=20)
+            except Exception:
+                break  # no nvidia-smi
+            if r.returncode == 0 and r.stdout.strip():
+                return c
+        return str(local)
+
+    @staticmethod
+    def _stamp(text):
+        """nvidia-smi's local-time stamp 'YYYY/MM/DD HH:MM:SS.mmm' in seconds since the epoch."""
+        try:
+            whole, _, frac = text.partition(".")
+            return time.mktime(time.strptime(whole, "%Y/%m/%d %H:%M:%S")) + (float("0." + frac) if frac else 0.0)
+        except ValueError:
+            return None
+
+    def parse(self, lines):
+        samples = []  # (time or None, sm MHz, max sm MHz, reasons)
+        for line in lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                sm, smax = float(parts[2]), float(parts[3])
+            except ValueError:
+                continue
+            reasons = {nm for nm, v in zip(self.REASONS, parts[6:10]) if v.lower() in ("active", "1")}
+            samples.append((self._stamp(parts[0]), sm, smax, reasons))
+        inside, use = [], samples
+        stamped = [x for x in samples if x[0] is not None]
+        if self.t0 is not None and self.t1 is not None and stamped:
+            inside = [x for x in stamped if self.t0 <= x[0] <= self.t1]
+            # a region shorter than the interval: the sample nearest to it
+            use = inside or [min(stamped, key=lambda x: max(self.t0 - x[0], x[0] - self.t1))]
+        if not use:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median([x[1] for x in use])), "sm_max_mhz": float(max(x[2] for x in use)),
+                "reasons": sorted(set().union(*[x[3] for x in use])), "samples": len(use),
+                "samples_in_region": len(inside)}
 
     def stop(self):
         if self.proc is None:
@@ -112,25 +187,10 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-            except ValueError:
-                continue
-            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() in ("active", "1"):
-                    reasons.add(nm)
+        with open(self.path) as fh:
+            lines = fh.readlines()
         os.unlink(self.path)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return self.parse(lines)
 
 
 # ------------------------------------------------------------------ CPU oracle baseline
@@ -268,6 +328,8 @@ def run_ours(args):
         ch.step(dt)
         ch.diagnostics_enqueue()
 
+    clocks = ClockSampler(local)
+    clocks.start()  # sampling from before the autotuner and the warm-up on
     lb_variant = ch.autotune()
     for _ in range(args.warmup):
         block()
@@ -277,18 +339,18 @@ def run_ours(args):
     ch.set_timing(2)  # events around the LB launches only (the roofline kernel)
     ch.timing()  # reset counters
     launches0 = ch.launch_count()
-    clocks = ClockSampler(local)
-    clocks.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    clocks.region_start()
     e0.record(stream)
     for _ in range(args.steps):
         block()
     e1.record(stream)
     torch.cuda.synchronize()
+    clocks.region_end()
     if dist:
         dist.barrier()
     clk = clocks.stop()
