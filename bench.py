@@ -85,7 +85,7 @@ def ncu_traffic():
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons, one line every 200 ms, started
+    """nvidia-smi clocks and throttle reasons, one line every 50 ms, started
     before the warm-up so that it samples from the first timed step on.  The
     lines carry nvidia-smi's timestamp; stop() reports the samples taken between
     region_start() and region_end() (host wall clock), or, when none fell inside
@@ -95,7 +95,7 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
     REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
-    def __init__(self, gpu_index, interval_ms=200):
+    def __init__(self, gpu_index, interval_ms=50):
         self.gpu = self.smi_id(gpu_index)
         self.interval_ms = interval_ms
         self.proc = None
