@@ -437,3 +437,40 @@ def test_flow_alignment_leslie_angle(oracle_mod):
         assert abs(c2 - 1 / lam) < 1e-9, zz
         assert s2 * lam * shear[zz] < 0, zz
     assert np.max(np.abs(n[1])) < 1e-15
+
+
+def test_effective_shear_viscosity_at_rest_director(oracle_mod):
+    """Assembled stress under shear u_x(z) with a director that the director
+    equation leaves at rest (K = 0): at the Leslie angle (n = (sin t, 0, cos t),
+    cos 2t = gamma1/gamma2) and along the vorticity axis (n = y_hat), N = -W n, and
+    the shear stress is the effective viscosity of a held director (de Gennes &
+    Prost, Sec. 5.1) times the local rate g = du_x/dz:
+        eta(t) = a1 sin^2 t cos^2 t + [a4' + (a5 - a2) cos^2 t + (a3 + a6) sin^2 t] / 2,
+        eta(y_hat) = a4' / 2,
+    with sigma_xz = sigma_zx (no torque).  Swapping a2 with a3 or a5 with a6, a
+    transposed strain or vorticity, or a wrong coupling gamma2/gamma1 in N breaks it."""
+    O = oracle_mod
+    nz = 16
+    a = dict(alpha1=0.3, alpha2=-1.25, alpha3=-0.25, alpha4p=0.4, alpha5=1.0, alpha6=-0.5)
+    g1, g2 = a["alpha3"] - a["alpha2"], a["alpha3"] + a["alpha2"]   # Parodi: gamma1 = a3 - a2, gamma2 = a6 - a5
+    assert abs(g2 - (a["alpha6"] - a["alpha5"])) < 1e-15
+    p = O.OracleParams(nx=1, ny=1, nz=nz, walls_z=False, K=0.0, q0=0.0, W0=0.0, gamma1=g1, gamma2=g2, **a)
+    z = np.arange(nz)
+    u = np.zeros((3, nz))
+    u[0] = 0.01 * np.sin(2 * math.pi * z / nz)
+    rate = 0.5 * (np.roll(u[0], -1) - np.roll(u[0], 1))   # central du_x/dz
+    t = 0.5 * math.acos(g1 / g2)
+    s, c = math.sin(t), math.cos(t)
+    eta = a["alpha1"] * s * s * c * c + 0.5 * (a["alpha4p"] + (a["alpha5"] - a["alpha2"]) * c * c
+                                               + (a["alpha3"] + a["alpha6"]) * s * s)
+    for n_vec, eta_ref in (((s, 0.0, c), eta), ((0.0, 1.0, 0.0), 0.5 * a["alpha4p"])):
+        n = np.tile(np.asarray(n_vec)[:, None], (1, nz))
+        sig = O.stress(p, n, u)
+        sxz, szx = sig[3 * 0 + 2], sig[3 * 2 + 0]
+        assert np.max(np.abs(sxz - eta_ref * rate)) < 1e-15
+        assert np.max(np.abs(szx - eta_ref * rate)) < 1e-15
+    # away from a rest state the held-director formula does not apply
+    n = np.tile(np.array([math.sin(0.3), 0.0, math.cos(0.3)])[:, None], (1, nz))
+    eta03 = a["alpha1"] * math.sin(0.3) ** 2 * math.cos(0.3) ** 2 + 0.5 * (
+        a["alpha4p"] + (a["alpha5"] - a["alpha2"]) * math.cos(0.3) ** 2 + (a["alpha3"] + a["alpha6"]) * math.sin(0.3) ** 2)
+    assert np.max(np.abs(O.stress(p, n, u)[2] - eta03 * rate)) > 1e-6
