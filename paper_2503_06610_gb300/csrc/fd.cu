@@ -649,6 +649,7 @@ __device__ __forceinline__ bool is_ghost_plane(const Geom& g, int p) { return g.
 // contiguous in shared memory), so the value computed there stays in that
 // thread's registers; then the two halo rows and the two halo columns.
 constexpr int kOwn = kTX * kTY;
+static_assert(kFusedThreads == kOwn, "the fused kernels run one thread per own tile point");
 __device__ __forceinline__ void p1_point(int t, int& hx1, int& hy1)
 {
     if (t < kOwn) {
