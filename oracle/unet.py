@@ -163,7 +163,7 @@ def loss_and_grad(flat, x, n_ansatz, n_target, bf16_storage=False):
     n_pred, _ = forward(params, x, n_ansatz, bf16_storage)
     loss = loss_fn(n_pred, n_target)
     loss.backward()
-    return float(loss), flat_t.grad.numpy().copy(), n_pred.detach()
+    return float(loss.detach()), flat_t.grad.numpy().copy(), n_pred.detach()
 
 
 def unpack_tensor(flat_t):
