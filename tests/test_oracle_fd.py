@@ -474,3 +474,31 @@ def test_effective_shear_viscosity_at_rest_director(oracle_mod):
     eta03 = a["alpha1"] * math.sin(0.3) ** 2 * math.cos(0.3) ** 2 + 0.5 * (
         a["alpha4p"] + (a["alpha5"] - a["alpha2"]) * math.cos(0.3) ** 2 + (a["alpha3"] + a["alpha6"]) * math.sin(0.3) ** 2)
     assert np.max(np.abs(O.stress(p, n, u)[2] - eta03 * rate)) > 1e-6
+
+
+def test_frank_energy_closed_forms(oracle_mod):
+    """Absolute lattice Frank energy (the diagnostic) of states with a closed
+    form.  Helix n = (cos qz, sin qz, 0): every z-link carries
+    K/2 |m - n|^2 = K (1 - cos q) and the chiral term -K q0 (n x m)_z = -K q0 sin q,
+    so E/N = K (1 - cos q) - K q0 sin q + K q0^2/2 (-> K/2 (q - q0)^2 for small q,
+    the continuum cholesteric); without anchoring the two ghost links of a column
+    carry nothing.  Uniform z_hat: E/N = K q0^2/2 - W0/2."""
+    O = oracle_mod
+    K, q0, W0 = 0.02, 0.4, 3e-3
+    nx, ny, nz = 3, 2, 12
+    for m in (1, 2, -1):
+        q = 2 * math.pi * m / nz
+        n = I.helix(nx, ny, nz, q)
+        link = K * (1 - math.cos(q)) - K * q0 * math.sin(q)
+        p = O.OracleParams(nx=nx, ny=ny, nz=nz, walls_z=False, K=K, q0=q0)
+        assert abs(O.frank_energy(p, n) - nx * ny * nz * (link + 0.5 * K * q0 ** 2)) < 1e-13
+        p = O.OracleParams(nx=nx, ny=ny, nz=nz, walls_z=True, anchoring="none", K=K, q0=q0)
+        assert abs(O.frank_energy(p, n) - nx * ny * ((nz - 1) * link + nz * 0.5 * K * q0 ** 2)) < 1e-13
+    # the right-handed helix (q = q0 > 0) is the lower one
+    q = 2 * math.pi / nz
+    p = O.OracleParams(nx=nx, ny=ny, nz=nz, walls_z=False, K=K, q0=q0)
+    assert O.frank_energy(p, I.helix(nx, ny, nz, q)) < O.frank_energy(p, I.helix(nx, ny, nz, -q))
+    for walls, anch in ((False, "none"), (True, "homeotropic")):
+        p = O.OracleParams(nx=nx, ny=ny, nz=nz, walls_z=walls, anchoring=anch, K=K, q0=q0, W0=W0)
+        E = O.frank_energy(p, I.uniform_director(nx, ny, nz))
+        assert abs(E - nx * ny * nz * (0.5 * K * q0 ** 2 - 0.5 * W0)) < 1e-13
