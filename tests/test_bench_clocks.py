@@ -70,9 +70,9 @@ def test_sampler_with_fake_nvidia_smi(tmp_path, monkeypatch):
     _fake_smi(tmp_path, monkeypatch)
     c = bench.ClockSampler(0, interval_ms=50)
     c.start()
-    time.sleep(0.3)  # the first (idle) sample lies before the region
+    time.sleep(0.5)  # the first (idle) sample lies before the region, even with a slow interpreter start
     c.region_start()
-    time.sleep(0.4)
+    time.sleep(0.5)
     c.region_end()
     r = c.stop()
     assert r["samples_in_region"] >= 3
