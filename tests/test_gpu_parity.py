@@ -257,14 +257,16 @@ def test_diagnostics_match_oracle(nh, oracle_mod):
     assert abs(d["max_norm"] - 1) < 1e-14 and abs(d["min_norm"] - 1) < 1e-14
 
 
+@pytest.mark.parametrize("nx", [35, 36])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("walls,anchoring", [(True, "homeotropic"), (True, "none"), (False, "homeotropic")])
-def test_diagnostics_match_oracle_variants(nh, oracle_mod, prec, walls, anchoring):
-    """Several 8-layer chunks with a ragged last one (nz = 37), a column count
+def test_diagnostics_match_oracle_variants(nh, oracle_mod, prec, walls, anchoring, nx):
+    """Several layer chunks with a ragged last one (nz = 37), a column count
     that is not a multiple of the warp size, both wall anchorings and periodic
-    z, bulk W0; FP64 to rounding, FP32 to its per-site precision."""
+    z, bulk W0; odd nx takes the one-column diagnostics kernel, even nx the
+    two-column one; FP64 to rounding, FP32 to its per-site precision."""
     O = oracle_mod
-    nx, ny, nz = 35, 33, 37
+    ny, nz = 33, 37
     tubes = [(9.0, 8.0), (26.0, 24.0)]
     params = _generic(nx, ny, nz, dt_fd=2, K=0.02, q0=2 * math.pi / 12, W0=0.002, walls_z=walls,
                       anchoring=anchoring)
