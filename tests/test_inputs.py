@@ -96,3 +96,24 @@ def test_generators_are_seeded():
     assert np.array_equal(w, I.unet_init_params(seed=0))
     n_params = sum(27 * ci * co + co for _, ci, co in I.UNET_CONV_LAYERS) + 16 * 3 + 3
     assert w.size == n_params == 394419
+
+
+def test_table1_regime_uses_the_printed_table():
+    """The preset's material constants are Table I's (tests/golden/table1_mbba.txt):
+    the Leslie alpha's (alpha4 split between the LB fluid and alpha4'), the
+    one-constant K as the mean of K11, K22, K33, the pitch P and the thickness Lz.
+    The lateral size follows the text of Sec. III.A (64), not Table I (56)."""
+    import os
+    vals = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "table1_mbba.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, v = line.split()
+        vals[k] = float(v)
+    p, _ = I.table1_regime(split=0.15)
+    for k in ("alpha1", "alpha2", "alpha3", "alpha5", "alpha6"):
+        assert p[k] == vals[k], k
+    assert abs(p["alpha4p"] + 2.0 * (p["tau"] - 0.5) / 3.0 - vals["alpha4"]) < 1e-15
+    assert abs(p["K"] - (vals["K11"] + vals["K22"] + vals["K33"]) / 3.0) < 1e-22
+    assert abs(2 * math.pi / p["q0"] - vals["P"]) < 1e-12
+    assert p["nz"] == int(vals["Lz"]) and (p["nx"], p["ny"]) == (64, 64)
