@@ -332,6 +332,10 @@ int nh_set_graphs(nh_ctx* ctx, int on);
  *   (as in nh_diagnostics), out[2] = max |u|, out[3] = min |n|,
  *   out[4] = max |n|, out[5] = number of sites with a NaN/Inf.
  * Asynchronous on stream (NULL = legacy default stream); no tube tracking.
+ * The sums are deterministic for given inputs and pointer alignment: with
+ * even nx and every field pointer aligned to two elements the reduction reads
+ * x-pairs of sites (as nh_diagnostics does), otherwise single sites, so two
+ * calls that differ only in alignment agree to rounding, not bit for bit.
  *
  * Scratch: a static device array inside the library (48 KiB per GPU that
  * loads it, held until the process exits); the call allocates nothing.  Size
