@@ -25,9 +25,12 @@
  * Where the paper is silent the readings are:
  *   - molecular field in one-constant form with chirality,
  *       h = K lap(n) - 2 K q0 curl(n) + W0 n_z z_hat,
- *     lap = compact 3-point Laplacian per axis, curl = central differences
- *     (this h is exactly minus the derivative of the lattice energy that the
- *     Python side of the oracle evaluates);
+ *     lap = compact 3-point Laplacian per axis, curl = central differences,
+ *     written as the exact minus derivative of the lattice energy that the
+ *     Python side of the oracle evaluates (a sum over nearest-neighbour
+ *     links); a plate without anchoring is a free surface whose links carry
+ *     no energy, so at the two plate layers the chiral term lacks its link
+ *     to the ghost layer;
  *   - the kinematic transport inside the stress is
  *       N = [h_perp - gamma2 (I - n n) D n] / gamma1,   h_perp = h - (h.n) n,
  *     i.e. the director equation solved for N and projected normal to n;
@@ -296,16 +299,55 @@ static void local_derivs(const or_params* p, const double* n, const double* u, i
     }
 }
 
-/* Molecular field h = K lap n - 2 K q0 curl n + W0 n_z z_hat. */
-static void molecular_field(const or_params* p, const double nc[3], const double dn[3][3], const double lap[3],
-                            double h[3])
+/* Does the lattice link between layer z and layer zn (= z +- 1) carry energy?
+ * Inside the channel, and towards a plate with infinite homeotropic anchoring
+ * (a fixed ghost director), yes.  Towards a plate without anchoring, no: the
+ * plate is a free surface, and with the ghost director copied from the
+ * adjacent layer the link's elastic and chiral energies are both zero. */
+static int link_exists(const or_params* p, int zn)
 {
-    for (int a = 0; a < 3; ++a) {
-        double curl = 0.0;
-        for (int b = 0; b < 3; ++b)
-            for (int c = 0; c < 3; ++c) curl += levi(a, b, c) * dn[b][c];
-        h[a] = p->K * lap[a] - 2.0 * p->K * p->q0 * curl;
+    if (!p->walls_z) return 1;
+    if (zn >= 0 && zn < p->nz) return 1;
+    return p->anchoring != 0;
+}
+
+/* Chiral part of the molecular field at (x, y, z): minus the derivative of the
+ * chiral link energy K q0 sum_links eps_abc n_a(x) n_c(x + e_b) with respect
+ * to n(x, y, z).  A site is the first end of the link (y, y + e_b) and the
+ * second end of the link (y - e_b, y), so
+ *   hc_m = -K q0 sum_b [ eps_mbc n_c(y + e_b) + eps_abm n_a(y - e_b) ]
+ * over the links that exist.  In the bulk this is -2 K q0 (curl n)_m with
+ * the central curl. */
+static void chiral_field(const or_params* p, const double* n, int x, int y, int z, double hc[3])
+{
+    for (int m = 0; m < 3; ++m) hc[m] = 0.0;
+    for (int b = 0; b < 3; ++b) {
+        int d[3] = {0, 0, 0};
+        d[b] = 1;
+        double np[3], nm[3];
+        if (link_exists(p, z + d[2])) {
+            n_at(p, n, x + d[0], y + d[1], z + d[2], np);
+            for (int m = 0; m < 3; ++m)
+                for (int c = 0; c < 3; ++c) hc[m] -= p->K * p->q0 * levi(m, b, c) * np[c];
+        }
+        if (link_exists(p, z - d[2])) {
+            n_at(p, n, x - d[0], y - d[1], z - d[2], nm);
+            for (int m = 0; m < 3; ++m)
+                for (int a = 0; a < 3; ++a) hc[m] -= p->K * p->q0 * levi(a, b, m) * nm[a];
+        }
     }
+}
+
+/* Molecular field h = -dE_d/dn of the one-constant lattice energy (Sec. II.A):
+ * h = K lap n + hc + W0 n_z z_hat, with the compact Laplacian (the elastic
+ * link energy; a copied ghost contributes nothing) and the chiral part hc of
+ * chiral_field (-2 K q0 curl n in the bulk). */
+static void molecular_field(const or_params* p, const double* n, int x, int y, int z, const double nc[3],
+                            const double lap[3], double h[3])
+{
+    double hc[3];
+    chiral_field(p, n, x, y, z, hc);
+    for (int a = 0; a < 3; ++a) h[a] = p->K * lap[a] + hc[a];
     h[2] += p->W0 * nc[2];
 }
 
@@ -444,7 +486,7 @@ void or_molecular_field(const or_params* p, const double* n, double* h_out)
                 double nc[3], dn[3][3], lap[3], du[3][3], h[3];
                 n_at(p, n, x, y, z, nc);
                 local_derivs(p, n, NULL, x, y, z, dn, lap, du);
-                molecular_field(p, nc, dn, lap, h);
+                molecular_field(p, n, x, y, z, nc, lap, h);
                 for (int a = 0; a < 3; ++a) h_out[(size_t)a * N + s] = h[a] + (hd ? hd[(size_t)a * N + s] : 0.0);
             }
     free(hd);
@@ -471,7 +513,7 @@ void or_director_rate(const or_params* p, const double* n, const double* u, doub
                 n_at(p, n, x, y, z, nc);
                 u_at(p, u, x, y, z, uc);
                 local_derivs(p, n, u, x, y, z, dn, lap, du);
-                molecular_field(p, nc, dn, lap, h);
+                molecular_field(p, n, x, y, z, nc, lap, h);
                 if (hd)
                     for (int a = 0; a < 3; ++a) h[a] += hd[(size_t)a * N + s];
                 strain_vorticity(du, D, W);
@@ -581,7 +623,7 @@ void or_stress(const or_params* p, const double* n, const double* u, double* sig
                 double nc[3], dn[3][3], lap[3], du[3][3], h[3], D[3][3], W[3][3];
                 n_at(p, n, x, y, z, nc);
                 local_derivs(p, n, u, x, y, z, dn, lap, du);
-                molecular_field(p, nc, dn, lap, h);
+                molecular_field(p, n, x, y, z, nc, lap, h);
                 if (hd)
                     for (int a = 0; a < 3; ++a) h[a] += hd[(size_t)a * N + s];
                 strain_vorticity(du, D, W);

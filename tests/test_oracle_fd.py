@@ -37,11 +37,17 @@ def _grad_energy(O, p, n, d=1e-6):
     return g
 
 
-@pytest.mark.parametrize("walls", [False, True])
-def test_molecular_field_is_energy_gradient(oracle_mod, walls):
+@pytest.mark.parametrize("walls,anchoring,nz", [(False, "homeotropic", 4), (True, "homeotropic", 4),
+                                                (True, "none", 4), (True, "none", 1), (True, "none", 2)])
+def test_molecular_field_is_energy_gradient(oracle_mod, walls, anchoring, nz):
+    """h = -dE_d/dn at every site (Sec. II.A), plate layers included.  Without
+    anchoring the plates carry no link energy (a free surface), so the chiral
+    term at the two plate layers lacks its link to the ghost layer; a central
+    curl over copied ghosts would add a spurious tangential torque K q0 (z x n)
+    there, which this comparison rejects (q0 and W0 are nonzero)."""
     O = oracle_mod
-    p = O.OracleParams(nx=4, ny=3, nz=4, walls_z=walls, anchoring="homeotropic", K=0.7, q0=0.9, W0=0.3)
-    n = I.random_director(4, 3, 4, seed=3)
+    p = O.OracleParams(nx=4, ny=3, nz=nz, walls_z=walls, anchoring=anchoring, K=0.7, q0=0.9, W0=0.3)
+    n = I.random_director(4, 3, nz, seed=3)
     h = O.molecular_field(p, n)
     g = _grad_energy(O, p, n)
     assert np.max(np.abs(g + h)) < 1e-7 * np.max(np.abs(h))
@@ -88,10 +94,14 @@ def test_uniform_homeotropic_channel_is_stationary(oracle_mod):
     assert np.max(np.abs(sim.u)) == 0.0
 
 
-@pytest.mark.parametrize("q0", [0.0, 2 * math.pi / 8])
-def test_energy_non_increasing_at_rest(oracle_mod, q0):
+@pytest.mark.parametrize("q0,anchoring,W0", [(0.0, "homeotropic", 0.0), (2 * math.pi / 8, "homeotropic", 0.0),
+                                            (2 * math.pi / 8, "none", 0.0), (2 * math.pi / 8, "none", 0.01)])
+def test_energy_non_increasing_at_rest(oracle_mod, q0, anchoring, W0):
+    """At rest the director equation is the gradient flow of E_d: E_d does not
+    increase, plates without anchoring (and the bulk W0 term) included."""
     O = oracle_mod
-    p = O.OracleParams(nx=8, ny=8, nz=6, walls_z=True, K=0.04, q0=q0, gamma1=1.0, dt_fd=2)
+    p = O.OracleParams(nx=8, ny=8, nz=6, walls_z=True, anchoring=anchoring, K=0.04, q0=q0, W0=W0, gamma1=1.0,
+                       dt_fd=2)
     n = I.tilted_director(8, 8, 6, amplitude=0.5, seed=4)
     u = np.zeros((3, p.N))
     E = [O.frank_energy(p, n)]
