@@ -51,7 +51,7 @@ extern "C" {
 #define NH_ECUDA (-2)     /* a CUDA runtime call failed */
 #define NH_ENOMEM (-3)    /* workspace missing or too small */
 #define NH_EUNSTABLE (-4) /* a NaN or Inf was found in the fields */
-#define NH_ETIMEOUT (-5)  /* a bounded device-side wait expired */
+#define NH_ETIMEOUT (-5)  /* a bounded wait expired (nh_set_wait_limit) */
 
 #define NH_FP64 0 /* arithmetic precision */
 #define NH_FP32 1
@@ -88,6 +88,25 @@ typedef struct nh_params {
                              (K11-K)/2 (div n)^2 + (K22-K)/2 (n.curl n + q0)^2 + (K33-K)/2 |n x curl n|^2
                              with central differences; h is its exact variational derivative.  Runs on the
                              per-site FD kernels (nh_set_fd_variant 0); not supported by the batched calls. */
+    /* Reading flags.  The paper is silent on each choice below; 0 is the default reading.  Each
+       flag is 0 or 1; any other value is NH_EINVAL. */
+    int32_t renorm_predictor; /* 1: also renormalise the predictor n^P to |n^P| = 1 before the corrector
+                             evaluates its rate (Sec. II.B lists no renormalisation; 0: only the corrected
+                             director is renormalised).  All FD kernels and the batched calls. */
+    int32_t lap_wide;     /* 1: the second derivatives of the molecular field are central differences of
+                             central differences, (n(x+2e) - 2 n(x) + n(x-2e))/4 per axis (the first-
+                             derivative stencil of Sec. II.B applied twice), reading the ghost rule at
+                             distance 2 as at distance 1; 0: the compact 3-point Laplacian, which makes h
+                             the exact derivative of the lattice energy.  Per-site FD kernels only. */
+    int32_t n_from_rate;  /* 1: the kinematic transport N of the viscous stress (Sec. II.A, N = dn/dt +
+                             u.grad n - W n) takes dn/dt from the corrector's averaged rate of the FD update
+                             that produced n, and the sum is projected normal to n; 0: N from the director equation,
+                             [h_perp - gamma2 (I - n n) D n]/gamma1.  A force computed without an FD update
+                             (nh_set_fields, nh_restore) uses the 0 reading.  Per-site FD kernels only. */
+    int32_t ghost_sigma;  /* stress at the plates' ghost layers in the force divergence (Sec. II.B computes
+                             gradients at fluid nodes only): 0 = zero stress; 1 = mirror, the stress of the
+                             adjacent fluid layer (zero normal gradient; the total force then equals the
+                             stress difference across the channel).  All FD kernels. */
     double tau;           /* SRT relaxation time, > 1/2; nu = (tau - 1/2)/3 */
     double g[3];          /* body acceleration g of Eq. NS-eq; the LB force is F_lc + rho g */
     double K;             /* one-constant Frank elasticity */
@@ -210,6 +229,56 @@ int nh_batch_step(nh_ctx* const* ctxs, int count, int64_t n_lb_steps, void* stre
  * for this list of contexts and returns it in *chosen.  Synchronises. */
 int nh_batch_autotune(nh_ctx* const* ctxs, int count, void* stream, int* chosen);
 
+/* ------------------------------------------------------------------------
+ * Slabs along y: one channel split over several contexts (the domain
+ * decomposition of a channel across devices; here every slab sits on the one
+ * device of the run and the halos move by device copies).
+ *
+ * Slab k of count (k = 0 lowest in y, periodic: the last is below the first)
+ * holds ny_local[k] >= 1 interior rows of the global channel plus one ghost
+ * row on each side: its context is created with ny = ny_local[k] + 2 and its
+ * row r is global row y0_k + r - 1 (y0_k = sum of the ny_local below it).
+ * Every kernel runs over the whole slab; the ghost rows are overwritten with
+ * the neighbours' interior rows before anything reads them:
+ *   - after every LB step, the populations the interior pulls across each
+ *     face: the five with e_y = +1 (3, 7, 10, 15, 17) into the lower ghost
+ *     row and the five with e_y = -1 (4, 8, 9, 16, 18) into the upper one
+ *     (pull streaming, Sec. II.C);
+ *   - in an FD update, u before the predictor, n^P before the corrector, n
+ *     before the stress and the stress before its divergence (the radius-1
+ *     central differences of Sec. II.B).
+ * The interior rows then follow the single-channel run exactly (the same
+ * kernels on the same operands).  Slabs use the per-site FD kernels. */
+#define NH_HALO_POPULATIONS 0 /* populations after an LB step */
+#define NH_HALO_VECTOR 1      /* n, n^P or u: three components */
+#define NH_HALO_STRESS 2      /* sigma: nine components */
+typedef struct nh_row_copy {
+    int32_t src_slab, src_row; /* copy row src_row of slab src_slab ... */
+    int32_t dst_slab, dst_row; /* ... into row dst_row of slab dst_slab (rows 0 and ny_local + 1 are ghosts) */
+    uint32_t comp_mask;        /* bit c: component c (population plane, vector or stress component) */
+} nh_row_copy;
+
+/* The halo plan of count (1 .. 64) slabs for one kind of exchange: the row
+ * copies, two per slab (its lower and its upper ghost row), written to out
+ * (capacity entries; out may be NULL to ask for the count in *n_out).  Host
+ * only: needs no device, so a multi-process transport can follow the same
+ * plan.  NH_EINVAL for a bad count, kind or ny_local < 1. */
+int nh_slab_plan(int count, const int32_t* ny_local, int kind, nh_row_copy* out, int capacity, int* n_out);
+
+/* Make the slabs consistent after nh_set_fields on each: exchange the ghost
+ * rows of the populations, n and u, then recompute every slab's stress,
+ * exchange its ghost rows and recompute the force.  The slabs must share
+ * every parameter but ny, be on one device at the same step, use F64 or F32
+ * stores, and not use paper_order, frank3, lap_wide or obstacles (NH_EINVAL
+ * otherwise).  Asynchronous on stream (NULL = slabs[0]'s stream). */
+int nh_slab_init(nh_ctx* const* slabs, int count, void* stream);
+
+/* Advance every slab by n_lb_steps hybrid steps (as nh_step) with the halo
+ * exchanges above; direct launches on stream (NULL = slabs[0]'s stream).
+ * Same requirements as nh_slab_init.  Launch counts go to each slab (row
+ * copies to slabs[0]). */
+int nh_slab_step(nh_ctx* const* slabs, int count, int64_t n_lb_steps, void* stream);
+
 /* Director-only relaxation (the plain method that relaxes an ansatz, Sec. II.A
  * "minimizing its free energy"): sets u = 0 and runs n_fd_steps
  * predictor-corrector steps of length dt_fd of Eq. director-time-eq, which
@@ -313,6 +382,14 @@ int nh_autotune(nh_ctx* ctx, void* stream, int* chosen);
 /* Use CUDA graphs for whole dt_fd blocks (default on). */
 int nh_set_graphs(nh_ctx* ctx, int on);
 
+/* Bound the host-side waits of this context (nh_get_fields, nh_get_populations, nh_get_force,
+ * nh_diagnostics, nh_diagnostics_read, nh_director_change): with seconds > 0 a wait that has
+ * not seen the context's stream finish within that time returns NH_ETIMEOUT and leaves the
+ * work running (the output buffers are then not written, and a later call waits again);
+ * seconds <= 0 (the default) waits without a limit.  Failure detection for callers that must
+ * not block on a GPU that stopped making progress; the paper has no counterpart. */
+int nh_set_wait_limit(nh_ctx* ctx, double seconds);
+
 /* Diagnostics for callers that cannot allocate device memory.
  *
  * nh_diagnostics needs a context, whose workspace the caller allocated in
@@ -338,9 +415,11 @@ int nh_set_graphs(nh_ctx* ctx, int on);
  * calls that differ only in alignment agree to rounding, not bit for bit.
  *
  * Scratch: a static device array inside the library (48 KiB per GPU that
- * loads it, held until the process exits); the call allocates nothing.  Size
- * limit: nx * ny * ceil(nz / 16) <= NH_NOALLOC_MAX_ITEMS, else NH_EINVAL with
- * a message in nh_last_error(NULL).  The first call on each device looks up
+ * loads it, held until the process exits); the call allocates nothing.  The
+ * parameters get the checks of nh_create (NH_EINVAL otherwise).  Size limit, a
+ * bound on the work of one call rather than on the scratch (at most 1024
+ * reduction blocks stride over the domain): nx * ny * ceil(nz / 16) <=
+ * NH_NOALLOC_MAX_ITEMS, else NH_EINVAL with a message in nh_last_error(NULL).  The first call on each device looks up
  * the array's device address with that device current; make that first call
  * before any stream capture.  All calls share the one array, which keeps the
  * last call's partial sums (each call overwrites what it reads, so nothing

@@ -60,6 +60,8 @@ class _Params(ctypes.Structure):
         ("K11", ctypes.c_double), ("K22", ctypes.c_double), ("K33", ctypes.c_double),
         ("frank3", ctypes.c_int),
         ("solid", ctypes.c_void_p),
+        ("renorm_predictor", ctypes.c_int), ("lap_wide", ctypes.c_int),
+        ("n_from_rate", ctypes.c_int), ("ghost_sigma", ctypes.c_int),
     ]
 
 
@@ -91,6 +93,11 @@ class OracleParams:
     K22: float = None
     K33: float = None
     solid: object = None  # [N] uint8, 1 = solid node (obstacle); None: no obstacles
+    # readings where the paper is silent (see nh_oracle.c)
+    renorm_predictor: bool = False  # renormalise the predictor n^P too
+    lap_wide: bool = False          # second derivatives as central differences of central differences
+    n_from_rate: bool = False       # N of the stress from the corrector's averaged rate
+    ghost_sigma: str = "zero"       # "zero" | "mirror": stress at the plates' ghost layers
 
     def __post_init__(self):
         if self.solid is not None:
@@ -125,6 +132,11 @@ class OracleParams:
             c.K11, c.K22, c.K33, c.frank3 = self.K11, self.K22, self.K33, 1
         if self.solid is not None:
             c.solid = self.solid.ctypes.data  # the array lives as long as these params
+        c.renorm_predictor = 1 if self.renorm_predictor else 0
+        c.lap_wide = 1 if self.lap_wide else 0
+        c.n_from_rate = 1 if self.n_from_rate else 0
+        c.ghost_sigma = {"zero": 0, "mirror": 1}[self.ghost_sigma] if isinstance(self.ghost_sigma, str) \
+            else int(self.ghost_sigma)
         return c
 
     @classmethod
@@ -153,7 +165,7 @@ def lib():
         _lib.or_transport_point.argtypes = [dp, dp, dp, ctypes.c_double, ctypes.c_double, dp]
         _lib.or_viscous_stress_point.argtypes = [pp, dp, dp, dp, dp]
         _lib.or_elastic_stress_point.argtypes = [pp, dp, dp, dp]
-        _lib.or_stress.argtypes = [pp, dp, dp, dp]
+        _lib.or_stress.argtypes = [pp, dp, dp, dp, dp]
         _lib.or_force.argtypes = [pp, dp, dp]
         _lib.or_num_threads.restype = ctypes.c_int
         _lib.or_frank3_field.argtypes = [pp, dp, dp]
@@ -263,19 +275,25 @@ def director_rate(p: OracleParams, n, u) -> np.ndarray:
     return out.reshape(3, p.N)
 
 
-def fd_step(p: OracleParams, n, u) -> np.ndarray:
-    """One predictor-corrector FD step (Sec. II.B) + renormalisation; returns new n."""
+def fd_step(p: OracleParams, n, u, return_rate: bool = False):
+    """One predictor-corrector FD step (Sec. II.B) + renormalisation; returns new n
+    (and, with return_rate, the averaged time derivative that advanced it)."""
     n = _f64(n).copy()
     work = np.empty(9 * p.N)
     c = p.to_c()
     lib().or_fd_step(ctypes.byref(c), _ptr(n), _ptr(_vec(p, u)), _ptr(work))
+    if return_rate:
+        return n.reshape(3, p.N), work[:3 * p.N].reshape(3, p.N).copy()
     return n.reshape(3, p.N)
 
 
-def stress(p: OracleParams, n, u) -> np.ndarray:
+def stress(p: OracleParams, n, u, ndot=None) -> np.ndarray:
+    """LC stress; ndot (the corrector's averaged rate) is used for N when p.n_from_rate."""
     out = np.empty(9 * p.N)
     c = p.to_c()
-    lib().or_stress(ctypes.byref(c), _ptr(_vec(p, n)), _ptr(_vec(p, u)), _ptr(out))
+    nd = None if ndot is None else _vec(p, ndot)
+    lib().or_stress(ctypes.byref(c), _ptr(_vec(p, n)), _ptr(_vec(p, u)), _ptr(nd) if nd is not None else None,
+                    _ptr(out))
     return out.reshape(9, p.N)
 
 
@@ -315,6 +333,7 @@ class OracleSim:
     f: np.ndarray = field(default=None, repr=False)
     F: np.ndarray = field(default=None, repr=False)
     s: int = 0
+    ndot: np.ndarray = field(default=None, repr=False)  # averaged rate of the last FD update (n_from_rate)
 
     def __post_init__(self):
         N = self.p.N
@@ -331,18 +350,23 @@ class OracleSim:
             if self.p.paper_order and due:
                 # macroscopic fields of this step (its collision result is not kept)
                 _, self.rho, self.u = lb_step(self.p, self.f, self.F)
-                self.n = fd_step(self.p, self.n, self.u)
+                self._fd_update()
                 F_old = self.F
-                self.F = force(self.p, stress(self.p, self.n, self.u))
+                self.F = force(self.p, stress(self.p, self.n, self.u, self.ndot))
                 self.f, _, _ = lb_step(self.p, self.f, self.F, Fu=F_old)
                 self.s += 1
                 continue
             self.f, self.rho, self.u = lb_step(self.p, self.f, self.F)
             self.s += 1
             if due:
-                self.n = fd_step(self.p, self.n, self.u)
-                self.F = force(self.p, stress(self.p, self.n, self.u))
+                self._fd_update()
+                self.F = force(self.p, stress(self.p, self.n, self.u, self.ndot))
         return self
+
+    def _fd_update(self):
+        """Predictor-corrector on n with the current u; keeps the averaged rate for N (n_from_rate)."""
+        self.n, rate = fd_step(self.p, self.n, self.u, return_rate=True)
+        self.ndot = rate if self.p.n_from_rate else None
 
     def mass(self) -> float:
         return mass(self.p, self.f)

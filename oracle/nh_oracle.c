@@ -37,7 +37,15 @@
  *   - ghost layers at z = -1 and z = nz when walls are present: u = 0,
  *     n = z_hat (infinite homeotropic anchoring) or n = adjacent fluid layer
  *     (no anchoring); stress = 0 at the ghosts;
- *   - the FD update renormalises n after the corrector only;
+ *   - the FD update renormalises n after the corrector only (renorm_predictor
+ *     also renormalises the predictor);
+ *   - second derivatives: the compact Laplacian (lap_wide: the central
+ *     difference of the central difference, n at distance 2 read with the
+ *     same ghost rule as at distance 1);
+ *   - N in the stress from the director equation (n_from_rate: dn/dt +
+ *     u.grad n - W n as Sec. II.A defines N, with dn/dt the averaged time
+ *     derivative of the corrector, Sec. II.B, projected normal to n);
+ *   - ghost stress zero (ghost_sigma = 1: the stress of the adjacent layer);
  *   - obstacles (solid nodes, Sec. II.B): a link from a fluid site to a solid
  *     one bounces back half-way like the plates; solid nodes keep their
  *     director (infinite anchoring: the caller stores the surface normal
@@ -73,6 +81,11 @@ typedef struct {
     double K11, K22, K33; /* three-constant Frank energy (used when frank3 = 1) */
     int frank3;       /* 1: add the three-constant correction Delta f (see frank3_point) */
     const unsigned char* solid; /* [N] 1 = solid node (obstacle), or NULL: no obstacles */
+    /* readings where the paper is silent (0 = default) */
+    int renorm_predictor; /* 1: the predictor n^P is also renormalised */
+    int lap_wide;     /* 1: second derivatives in h as central differences of central differences */
+    int n_from_rate;  /* 1: N in the stress from the corrector's averaged rate (see or_stress) */
+    int ghost_sigma;  /* 0: zero stress at the plates' ghost layers; 1: the adjacent layer's stress */
 } or_params;
 
 /* D3Q19 velocity set (Sec. II.C): rest, 6 axis links, 12 face diagonals. */
@@ -294,7 +307,14 @@ static void local_derivs(const or_params* p, const double* n, const double* u, i
         for (int k = 0; k < 3; ++k) {
             dn[b][k] = 0.5 * (np[k] - nm[k]);
             du[b][k] = 0.5 * (up[k] - um[k]);
-            lap[k] += np[k] + nm[k] - 2.0 * c[k];
+            if (!p->lap_wide) lap[k] += np[k] + nm[k] - 2.0 * c[k];
+        }
+        if (p->lap_wide) {
+            /* d_b (d_b n) with both derivatives central: [n(x+2e) - 2 n(x) + n(x-2e)]/4 */
+            double n2p[3], n2m[3];
+            n_at(p, n, x + 2 * d[0], y + 2 * d[1], z + 2 * d[2], n2p);
+            n_at(p, n, x - 2 * d[0], y - 2 * d[1], z - 2 * d[2], n2m);
+            for (int k = 0; k < 3; ++k) lap[k] += 0.25 * (n2p[k] + n2m[k] - 2.0 * c[k]);
         }
     }
 }
@@ -528,9 +548,21 @@ void or_director_rate(const or_params* p, const double* n, const double* u, doub
     free(hd);
 }
 
+/* Scale the director at every fluid site to unit length. */
+static void normalise(const or_params* p, double* n)
+{
+    const size_t N = (size_t)p->nx * p->ny * p->nz;
+    for (size_t s = 0; s < N; ++s) {
+        if (is_solid(p, s)) continue;
+        double len = sqrt(n[s] * n[s] + n[N + s] * n[N + s] + n[2 * N + s] * n[2 * N + s]);
+        for (int a = 0; a < 3; ++a) n[(size_t)a * N + s] /= len;
+    }
+}
+
 /* One FD step of length dt_fd with the predictor-corrector scheme of Sec. II.B,
  * followed by renormalisation |n| = 1.  u is held fixed during the step.
- * work must hold 9*N doubles. */
+ * work must hold 9*N doubles; on return work[0 .. 3N) holds the averaged time
+ * derivative (1/2)[(dn/dt)_old + (dn/dt)_P] that advanced n. */
 void or_fd_step(const or_params* p, double* n, const double* u, double* work)
 {
     const size_t N = (size_t)p->nx * p->ny * p->nz;
@@ -539,8 +571,10 @@ void or_fd_step(const or_params* p, double* n, const double* u, double* work)
     double* ndot_P = work + 6 * N;
     or_director_rate(p, n, u, ndot_old);
     for (size_t k = 0; k < 3 * N; ++k) nP[k] = n[k] + p->dt_fd * ndot_old[k];
+    if (p->renorm_predictor) normalise(p, nP);
     or_director_rate(p, nP, u, ndot_P);
-    for (size_t k = 0; k < 3 * N; ++k) n[k] = n[k] + p->dt_fd * 0.5 * (ndot_old[k] + ndot_P[k]);
+    for (size_t k = 0; k < 3 * N; ++k) ndot_old[k] = 0.5 * (ndot_old[k] + ndot_P[k]); /* averaged rate */
+    for (size_t k = 0; k < 3 * N; ++k) n[k] = n[k] + p->dt_fd * ndot_old[k];
     for (size_t s = 0; s < N; ++s) {
         if (is_solid(p, s)) continue;
         double len = sqrt(n[s] * n[s] + n[N + s] * n[N + s] + n[2 * N + s] * n[2 * N + s]);
@@ -605,8 +639,12 @@ void or_elastic_stress_point(const or_params* p, const double* n, const double* 
 }
 
 /* LC stress tensor at every fluid site: sigma = sigma^v(alpha_4') + sigma^e,
- * from the director n, its molecular field h and the velocity u. */
-void or_stress(const or_params* p, const double* n, const double* u, double* sigma)
+ * from the director n, its molecular field h and the velocity u.  With
+ * n_from_rate and a rate field ndot (the corrector's averaged dn/dt) the
+ * kinematic transport is N = (I - n n)(ndot + u.grad n - W n) (Sec. II.A,
+ * projected normal to n as the director-equation form is);
+ * otherwise (or when ndot is NULL) N comes from the director equation. */
+void or_stress(const or_params* p, const double* n, const double* u, const double* ndot, double* sigma)
 {
     const size_t N = (size_t)p->nx * p->ny * p->nz;
     double* hd = p->frank3 ? (double*)malloc(3 * N * sizeof(double)) : NULL;
@@ -633,7 +671,18 @@ void or_stress(const or_params* p, const double* n, const double* u, double* sig
                         Dflat[3 * a + b] = D[a][b];
                         dnflat[3 * a + b] = dn[a][b];
                     }
-                or_transport_point(nc, h, Dflat, p->gamma1, p->gamma2, Nv);
+                if (p->n_from_rate && ndot != NULL) {
+                    double t[3], uc[3], nt = 0.0;
+                    u_at(p, u, x, y, z, uc);
+                    for (int m = 0; m < 3; ++m) {
+                        t[m] = ndot[(size_t)m * N + s];
+                        for (int g = 0; g < 3; ++g) t[m] += uc[g] * dn[g][m] - W[m][g] * nc[g];
+                    }
+                    for (int m = 0; m < 3; ++m) nt += nc[m] * t[m];
+                    for (int m = 0; m < 3; ++m) Nv[m] = t[m] - nt * nc[m];
+                } else {
+                    or_transport_point(nc, h, Dflat, p->gamma1, p->gamma2, Nv);
+                }
                 or_viscous_stress_point(p, nc, Dflat, Nv, sv);
                 or_elastic_stress_point(p, nc, dnflat, se);
                 if (hd) {
@@ -649,7 +698,9 @@ void or_stress(const or_params* p, const double* n, const double* u, double* sig
     free(hd);
 }
 
-/* F^LC_a = d_b sigma_ab with central differences; sigma = 0 at solid ghosts. */
+/* F^LC_a = d_b sigma_ab with central differences; sigma = 0 at solid ghosts
+ * (ghost_sigma = 1: the stress of the adjacent fluid layer at the plates'
+ * ghost layers). */
 void or_force(const or_params* p, const double* sigma, double* F)
 {
     const size_t N = (size_t)p->nx * p->ny * p->nz;
@@ -667,7 +718,8 @@ void or_force(const or_params* p, const double* sigma, double* F)
                     for (int b = 0; b < 3; ++b) {
                         int d[3] = {0, 0, 0};
                         d[b] = 1;
-                        double sp = 0.0, sm = 0.0;
+                        const double ghost = p->ghost_sigma ? sigma[(size_t)(3 * a + b) * N + s] : 0.0;
+                        double sp = ghost, sm = ghost;
                         int zp = z + d[2], zm = z - d[2];
                         if (!(p->walls_z && (zp < 0 || zp >= p->nz)))
                             sp = sigma[(size_t)(3 * a + b) * N +

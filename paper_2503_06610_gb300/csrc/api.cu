@@ -6,10 +6,12 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <map>
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "nh_internal.cuh"
@@ -21,9 +23,9 @@
 using namespace nh;
 
 // The parameter block is passed by pointer from C and from Python's ctypes:
-// 12 int32 fields then 18 doubles, without padding.
-static_assert(sizeof(nh_params) == 12 * 4 + 18 * 8, "nh_params layout");
-static_assert(offsetof(nh_params, tau) == 48, "nh_params layout");
+// 16 int32 fields then 18 doubles, without padding.
+static_assert(sizeof(nh_params) == 16 * 4 + 18 * 8, "nh_params layout");
+static_assert(offsetof(nh_params, tau) == 64, "nh_params layout");
 
 namespace {
 
@@ -146,6 +148,12 @@ int validate(const nh_params* p, std::string& err)
         err = "frank3 must be 0 or 1";
         return NH_EINVAL;
     }
+    const int32_t flags[] = {p->renorm_predictor, p->lap_wide, p->n_from_rate, p->ghost_sigma};
+    for (int32_t f : flags)
+        if (f != 0 && f != 1) {
+            err = "renorm_predictor, lap_wide, n_from_rate and ghost_sigma must be 0 or 1";
+            return NH_EINVAL;
+        }
     if (p->frank3 && !(p->K11 > 0 && p->K22 > 0 && p->K33 > 0 && isfinite(p->K11) && isfinite(p->K22) &&
                        isfinite(p->K33))) {
         err = "frank3 needs finite K11, K22, K33 > 0";
@@ -168,6 +176,8 @@ int validate(const nh_params* p, std::string& err)
 }  // namespace
 
 void nh::set_global_error(const char* msg) { g_global_err = msg ? msg : ""; }
+
+int nh::validate_params(const nh_params* p, std::string& err) { return validate(p, err); }
 
 namespace {
 
@@ -219,6 +229,7 @@ struct nh_ctx {
     bool snap_valid = false;  // a director snapshot exists (nh_director_change)
     int diag_tubes = 0;
     cudaStream_t diag_stream = nullptr;
+    double wait_limit = 0.0;  // seconds; > 0 bounds the host-side waits (nh_set_wait_limit)
 
     template <typename T>
     T* at(size_t off) const
@@ -250,6 +261,25 @@ int cuda_fail(nh_ctx* c, cudaError_t e, const char* where)
     } while (0)
 
 cudaStream_t pick(nh_ctx* c, void* s) { return s ? static_cast<cudaStream_t>(s) : c->stream; }
+
+// Wait for the work enqueued on st, for at most the context's wait limit:
+// NH_ETIMEOUT (work left running) when the limit passes first.  Without a
+// limit this returns at once and the caller's own synchronisation waits.
+int bounded_wait(nh_ctx* c, cudaStream_t st)
+{
+    if (!(c->wait_limit > 0.0)) return NH_OK;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t e = cudaStreamQuery(st);
+        if (e == cudaSuccess) return NH_OK;
+        if (e != cudaErrorNotReady) return cuda_fail(c, e, "cudaStreamQuery");
+        const double waited = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (waited > c->wait_limit)
+            return fail(c, NH_ETIMEOUT,
+                        "the stream did not finish within the wait limit of " + std::to_string(c->wait_limit) + " s");
+        std::this_thread::sleep_for(std::chrono::microseconds(100));
+    }
+}
 
 // NVTX range around an API call that enqueues GPU work (visible in profilers).
 struct NvtxRange {
@@ -352,6 +382,10 @@ FDChan<Real> fd_chan(nh_ctx* c)
     a.p.a6q = Real(0.25 * p.alpha6);
     a.p.k4 = Real(0.25 * p.K);
     a.p.kq2 = Real(0.5 * p.K * p.q0);
+    a.p.renorm_p = p.renorm_predictor;
+    a.p.lap_wide = p.lap_wide;
+    a.p.n_rate = 0;  // set by the caller for the force that follows an FD update
+    a.p.mirror = p.ghost_sigma;
     return a;
 }
 
@@ -429,10 +463,14 @@ int enqueue_predict_correct_sites(nh_ctx* c, const FDChan<Real>& a, cudaStream_t
     return timed(c, NH_KCLASS_FD_CORRECT, st, [&] { return launch_fd_correct(a, st); }, "fd_correct");
 }
 
+// Stress and force from the current n and u.  after_update: the force that
+// follows an FD update, whose corrector left its averaged rate in ndot (used
+// for N with the n_from_rate reading).
 template <typename Real>
-int enqueue_force_only(nh_ctx* c, cudaStream_t st)
+int enqueue_force_only(nh_ctx* c, cudaStream_t st, bool after_update = false)
 {
     auto a = fd_chan<Real>(c);
+    a.p.n_rate = after_update && c->p.n_from_rate;
     if (c->fd_fused)
         return timed(c, NH_KCLASS_STRESS, st, [&] { return launch_fd_fused_b<Real>(a, a.n, nullptr, st); },
                      "stress_force");
@@ -456,9 +494,10 @@ int enqueue_fd(nh_ctx* c, cudaStream_t st)
         return timed(c, NH_KCLASS_STRESS, st, [&] { return launch_fd_fused_b<Real>(a, a.nP, a.n, st); },
                      "stress_force");
     }
+    a.p.n_rate = c->p.n_from_rate;  // the corrector keeps its averaged rate
     int r = enqueue_predict_correct_sites<Real>(c, a, st);
     if (r) return r;
-    return enqueue_force_only<Real>(c, st);
+    return enqueue_force_only<Real>(c, st, true);
 }
 
 template <typename Real>
@@ -732,9 +771,10 @@ int batch_prepare(nh_ctx* const* ctxs, int count, int64_t n_lb_steps, BatchPlan*
         if (c->p.precision != c0->p.precision || c->p.storage != c0->p.storage || c->p.shifted != c0->p.shifted ||
             c->p.dt_fd != c0->p.dt_fd)
             return fail(nullptr, NH_EINVAL, "channels must share precision, storage, shifted and dt_fd");
-        if (c->p.paper_order || c->p.frank3 || c->has_solid)
+        if (c->p.paper_order || c->p.frank3 || c->has_solid || c->p.lap_wide || c->p.n_from_rate)
             return fail(nullptr, NH_EINVAL, "channel " + std::to_string(k) +
-                                                ": paper_order, frank3 and obstacles are not supported in batches");
+                                                ": paper_order, frank3, obstacles, lap_wide and n_from_rate are not "
+                                                "supported in batches");
         if (c->device != c0->device) return fail(nullptr, NH_EINVAL, "channels must be on one device");
         if (c->cur != c0->cur || c->step % c0->p.dt_fd != c0->step % c0->p.dt_fd)
             return fail(nullptr, NH_EINVAL, "channels must be at the same step phase (step mod dt_fd, buffer parity)");
@@ -781,9 +821,9 @@ int batch_prepare_relax(nh_ctx* const* ctxs, int count, int64_t n_fd_steps, Batc
         if (!c->bound || !c->fields_set)
             return fail(nullptr, NH_EINVAL, "channel " + std::to_string(k) + ": workspace or fields not set");
         if (c->p.precision != c0->p.precision) return fail(nullptr, NH_EINVAL, "channels must share the precision");
-        if (c->p.frank3 || c->has_solid)
-            return fail(nullptr, NH_EINVAL,
-                        "channel " + std::to_string(k) + ": frank3 and obstacles are not supported in batches");
+        if (c->p.frank3 || c->has_solid || c->p.lap_wide)
+            return fail(nullptr, NH_EINVAL, "channel " + std::to_string(k) +
+                                                ": frank3, obstacles and lap_wide are not supported in batches");
         if (c->device != c0->device) return fail(nullptr, NH_EINVAL, "channels must be on one device");
         for (int j = 0; j < k; ++j)
             if (ctxs[j] == c) return fail(nullptr, NH_EINVAL, "a context appears twice in the batch");
@@ -922,9 +962,212 @@ int batch_capture(BatchPlan* b, int parity)
     return r;
 }
 
+// ------------------------------------------------------------ slabs along y
+
+// Halo plan of `count` slabs stacked along y (slab k below slab k + 1, the
+// last below the first: periodic).  Slab k has interior rows 1 .. ny[k] and
+// ghost rows 0 and ny[k] + 1.  Its lower ghost row is the last interior row of
+// the slab below, its upper ghost row the first interior row of the slab
+// above.  Populations: only the planes the interior pulls across each face,
+// e_y = +1 (3, 7, 10, 15, 17) from below and e_y = -1 (4, 8, 9, 16, 18) from
+// above; fields: every component.
+int slab_plan(int count, const int32_t* ny, int kind, std::vector<nh_row_copy>& out)
+{
+    if (count < 1 || count > kMaxSlabs || !ny) return NH_EINVAL;
+    if (kind != NH_HALO_POPULATIONS && kind != NH_HALO_VECTOR && kind != NH_HALO_STRESS) return NH_EINVAL;
+    for (int k = 0; k < count; ++k)
+        if (ny[k] < 1) return NH_EINVAL;
+    const uint32_t up = (1u << 3) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 17);
+    const uint32_t down = (1u << 4) | (1u << 8) | (1u << 9) | (1u << 16) | (1u << 18);
+    const uint32_t all = kind == NH_HALO_VECTOR ? 0x7u : 0x1FFu;
+    out.clear();
+    for (int k = 0; k < count; ++k) {
+        const int below = (k + count - 1) % count, above = (k + 1) % count;
+        out.push_back(nh_row_copy{below, ny[below], k, 0, kind == NH_HALO_POPULATIONS ? up : all});
+        out.push_back(nh_row_copy{above, 1, k, ny[k] + 1, kind == NH_HALO_POPULATIONS ? down : all});
+    }
+    return NH_OK;
+}
+
+// Enqueue the row copies of a plan on one workspace region of every slab
+// (the field `field` of each slab's own layout, or with populations the
+// buffer each slab wrote last; elements of elem bytes, component c of slab k
+// at c * N_k).
+int slab_copy(nh_ctx* const* slabs, int count, int kind, size_t Layout::*field, bool populations, int elem,
+              cudaStream_t st)
+{
+    std::vector<int32_t> ny(count);
+    for (int k = 0; k < count; ++k) ny[k] = slabs[k]->p.ny - 2;
+    std::vector<nh_row_copy> plan;
+    int r = slab_plan(count, ny.data(), kind, plan);
+    if (r) return fail(nullptr, r, "slab plan");
+    static thread_local RowCopyList list;
+    list.count = 0;
+    auto flush = [&]() -> int {
+        cudaError_t e = launch_row_copies(list, elem, st);
+        slabs[0]->launches += list.count > 0 ? 1 : 0;
+        list.count = 0;
+        return e == cudaSuccess ? NH_OK : fail(nullptr, NH_ECUDA, std::string("row copies: ") + cudaGetErrorString(e));
+    };
+    for (const nh_row_copy& c : plan) {
+        nh_ctx* a = slabs[c.src_slab];
+        nh_ctx* b = slabs[c.dst_slab];
+        const size_t oa = populations ? a->L.f[a->cur] : a->L.*field;
+        const size_t ob = populations ? b->L.f[b->cur] : b->L.*field;
+        const int nx = a->p.nx, nz = a->p.nz;
+        for (int comp = 0; comp < 19; ++comp) {
+            if (!(c.comp_mask >> comp & 1u)) continue;
+            RowCopyItem it;
+            const int first = populations ? comp : 0;  // populations: one plane per item; fields: all components
+            it.src = a->ws + oa + ((size_t)first * a->N + (size_t)nx * c.src_row) * elem;
+            it.dst = b->ws + ob + ((size_t)first * b->N + (size_t)nx * c.dst_row) * elem;
+            it.nx = nx;
+            it.nz = nz;
+            it.comps = populations ? 1 : (kind == NH_HALO_VECTOR ? 3 : 9);
+            it.src_zstride = nx * a->p.ny;
+            it.dst_zstride = nx * b->p.ny;
+            it.src_cstride = a->N;
+            it.dst_cstride = b->N;
+            list.item[list.count++] = it;
+            if (list.count == kMaxRowCopies && (r = flush())) return r;
+            if (!populations) break;
+        }
+    }
+    return flush();
+}
+
+int slab_validate(nh_ctx* const* slabs, int count)
+{
+    if (!slabs || count < 1 || count > kMaxSlabs) return fail(nullptr, NH_EINVAL, "need 1 to 64 slabs");
+    nh_ctx* c0 = slabs[0];
+    for (int k = 0; k < count; ++k) {
+        nh_ctx* c = slabs[k];
+        if (!c) return fail(nullptr, NH_EINVAL, "NULL slab");
+        if (!c->bound || !c->fields_set)
+            return fail(nullptr, NH_EINVAL, "slab " + std::to_string(k) + ": workspace or fields not set");
+        if (c->p.ny < 3) return fail(nullptr, NH_EINVAL, "a slab needs ny >= 3 (two ghost rows and an interior row)");
+        nh_params a = c->p, b = c0->p;
+        a.ny = b.ny = 0;
+        if (memcmp(&a, &b, sizeof(a)) != 0)
+            return fail(nullptr, NH_EINVAL, "slabs must share every parameter but ny");
+        if (c->p.paper_order || c->p.frank3 || c->p.lap_wide || c->has_solid)
+            return fail(nullptr, NH_EINVAL, "paper_order, frank3, lap_wide and obstacles are not supported in slabs");
+        if (c->p.storage != NH_STORE_F64 && c->p.storage != NH_STORE_F32)
+            return fail(nullptr, NH_EINVAL, "slabs exchange raw populations: F64 or F32 stores only");
+        if (c->device != c0->device) return fail(nullptr, NH_EINVAL, "slabs must be on one device");
+        if (c->cur != c0->cur || c->step != c0->step)
+            return fail(nullptr, NH_EINVAL, "slabs must be at the same step and buffer parity");
+        for (int j = 0; j < k; ++j)
+            if (slabs[j] == c) return fail(nullptr, NH_EINVAL, "a context appears twice among the slabs");
+    }
+    return set_device(c0);
+}
+
+// Stress of every slab, sigma halo, force of every slab (per-site kernels).
+template <typename Real>
+int slab_force(nh_ctx* const* slabs, int count, bool after_update, cudaStream_t st)
+{
+    for (int k = 0; k < count; ++k) {
+        auto a = fd_chan<Real>(slabs[k]);
+        a.p.n_rate = after_update && slabs[k]->p.n_from_rate;
+        NH_CUDA(slabs[0], launch_stress(a, st));
+        slabs[k]->launches += 1;
+    }
+    int r = slab_copy(slabs, count, NH_HALO_STRESS, &Layout::sigma, false, sizeof(Real), st);
+    if (r) return r;
+    for (int k = 0; k < count; ++k) {
+        NH_CUDA(slabs[0], launch_force(fd_chan<Real>(slabs[k]), st));
+        slabs[k]->launches += 1;
+    }
+    return NH_OK;
+}
+
+// One FD update of every slab with the halo exchanges between the stages.
+template <typename Real>
+int slab_fd(nh_ctx* const* slabs, int count, cudaStream_t st)
+{
+    const int E = sizeof(Real);
+    int r = slab_copy(slabs, count, NH_HALO_VECTOR, &Layout::u, false, E, st);
+    for (int k = 0; k < count && !r; ++k) {
+        NH_CUDA(slabs[0], launch_fd_predict(fd_chan<Real>(slabs[k]), st));
+        slabs[k]->launches += 1;
+    }
+    if (!r) r = slab_copy(slabs, count, NH_HALO_VECTOR, &Layout::nP, false, E, st);
+    for (int k = 0; k < count && !r; ++k) {
+        auto a = fd_chan<Real>(slabs[k]);
+        a.p.n_rate = slabs[k]->p.n_from_rate;
+        NH_CUDA(slabs[0], launch_fd_correct(a, st));
+        slabs[k]->launches += 1;
+    }
+    if (!r) r = slab_copy(slabs, count, NH_HALO_VECTOR, &Layout::n, false, E, st);
+    if (!r) r = slab_force<Real>(slabs, count, true, st);
+    return r;
+}
+
 }  // namespace
 
 extern "C" {
+
+int nh_slab_plan(int count, const int32_t* ny_local, int kind, nh_row_copy* out, int capacity, int* n_out)
+{
+    std::vector<nh_row_copy> plan;
+    int r = slab_plan(count, ny_local, kind, plan);
+    if (r) return fail(nullptr, r, "nh_slab_plan: need 1 to 64 slabs with ny_local >= 1 and a known kind");
+    if (n_out) *n_out = (int)plan.size();
+    if (out) {
+        if (capacity < (int)plan.size()) return fail(nullptr, NH_EINVAL, "nh_slab_plan: capacity too small");
+        std::copy(plan.begin(), plan.end(), out);
+    }
+    return NH_OK;
+}
+
+int nh_slab_init(nh_ctx* const* slabs, int count, void* stream)
+{
+    NvtxRange range_("nh_slab_init");
+    int r = slab_validate(slabs, count);
+    if (r) return r;
+    nh_ctx* c0 = slabs[0];
+    cudaStream_t st = pick(c0, stream);
+    const int E = (int)real_size(c0->p);
+    const int S = (int)store_size(c0->p);
+    if ((r = slab_copy(slabs, count, NH_HALO_POPULATIONS, nullptr, true, S, st))) return r;
+    if ((r = slab_copy(slabs, count, NH_HALO_VECTOR, &Layout::n, false, E, st))) return r;
+    if ((r = slab_copy(slabs, count, NH_HALO_VECTOR, &Layout::u, false, E, st))) return r;
+    r = c0->p.precision == NH_FP64 ? slab_force<double>(slabs, count, false, st) : slab_force<float>(slabs, count, false, st);
+    if (r) return fail(nullptr, r, "nh_slab_init: " + std::string(nh_last_error(nullptr)));
+    return NH_OK;
+}
+
+int nh_slab_step(nh_ctx* const* slabs, int count, int64_t n_lb_steps, void* stream)
+{
+    NvtxRange range_("nh_slab_step");
+    int r = slab_validate(slabs, count);
+    if (r) return r;
+    if (n_lb_steps < 0) return fail(nullptr, NH_EINVAL, "n_lb_steps must be >= 0");
+    nh_ctx* c0 = slabs[0];
+    cudaStream_t st = pick(c0, stream);
+    const int E = (int)real_size(c0->p);
+    const int S = (int)store_size(c0->p);
+    for (int64_t s = 0; s < n_lb_steps; ++s) {
+        const int64_t next = c0->step + 1;
+        const bool fd = (next % c0->p.dt_fd) == 0;
+        const bool last = s + 1 == n_lb_steps;
+        for (int k = 0; k < count; ++k) {
+            if ((r = enqueue_lb(slabs[k], slabs[k]->cur, fd || last, st))) return fail(nullptr, r, slabs[k]->err);
+            slabs[k]->cur ^= 1;
+            slabs[k]->step = next;
+        }
+        if ((r = slab_copy(slabs, count, NH_HALO_POPULATIONS, nullptr, true, S, st))) return r;
+        if (fd) {
+            r = c0->p.precision == NH_FP64 ? slab_fd<double>(slabs, count, st) : slab_fd<float>(slabs, count, st);
+            if (r) return fail(nullptr, r, "nh_slab_step: " + std::string(nh_last_error(nullptr)) + c0->err);
+        } else if (last) {
+            if ((r = slab_copy(slabs, count, NH_HALO_VECTOR, &Layout::u, false, E, st))) return r;
+        }
+    }
+    for (int k = 0; k < count; ++k) close_segment(slabs[k]);
+    return NH_OK;
+}
 
 const char* nh_error_string(int code)
 {
@@ -934,7 +1177,7 @@ const char* nh_error_string(int code)
     case NH_ECUDA: return "CUDA error";
     case NH_ENOMEM: return "workspace missing or too small";
     case NH_EUNSTABLE: return "non-finite values in the fields";
-    case NH_ETIMEOUT: return "bounded device wait expired";
+    case NH_ETIMEOUT: return "bounded wait expired";
     default: return "unknown error";
     }
 }
@@ -963,7 +1206,8 @@ int nh_create(const nh_params* p, void* cuda_stream, nh_ctx** out)
     c->p = *p;
     c->N = p->nx * p->ny * p->nz;
     c->lb_variant = lb_variant_valid(0, p->nx) ? 0 : 1;
-    if (p->frank3) c->fd_fused = 0;  // the three-constant correction runs on the per-site FD kernels
+    // the three-constant correction, the wide Laplacian and N from the rate run on the per-site FD kernels
+    if (p->frank3 || p->lap_wide || p->n_from_rate) c->fd_fused = 0;
     c->L = make_layout(*p);
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = cudaGetDevice(&c->device);
@@ -1083,6 +1327,7 @@ int nh_get_fields(nh_ctx* c, double* n, double* u, double* rho, int on_device)
     if (r) return r;
     if ((r = set_device(c))) return r;
     cudaStream_t st = c->stream;
+    if ((r = bounded_wait(c, st))) return r;
     if ((r = store_field(c, c->L.n, n, 3 * (int64_t)c->N, on_device, st))) return r;
     if ((r = store_field(c, c->L.u, u, 3 * (int64_t)c->N, on_device, st))) return r;
     if ((r = store_field(c, c->L.rho, rho, (int64_t)c->N, on_device, st))) return r;
@@ -1095,6 +1340,7 @@ int nh_get_force(nh_ctx* c, double* F, int on_device)
     int r = check_ready(c);
     if (r) return r;
     if ((r = set_device(c))) return r;
+    if ((r = bounded_wait(c, c->stream))) return r;
     if ((r = store_field(c, c->L.F, F, 3 * (int64_t)c->N, on_device, c->stream))) return r;
     NH_CUDA(c, cudaStreamSynchronize(c->stream));
     return NH_OK;
@@ -1106,6 +1352,7 @@ int nh_get_populations(nh_ctx* c, double* f, int on_device)
     if (r) return r;
     if (!f) return fail(c, NH_EINVAL, "f is NULL");
     if ((r = set_device(c))) return r;
+    if ((r = bounded_wait(c, c->stream))) return r;
     switch (c->p.storage) {
     case NH_STORE_F64: r = decode_all<double>(c, f, on_device, c->stream); break;
     case NH_STORE_F32: r = decode_all<float>(c, f, on_device, c->stream); break;
@@ -1351,6 +1598,7 @@ int nh_director_change(nh_ctx* c, double* max_change)
     if (!c->fields_set) return fail(c, NH_EINVAL, "nh_set_fields must be called before nh_director_change");
     if ((r = set_device(c))) return r;
     cudaStream_t st = c->stream;
+    if ((r = bounded_wait(c, st))) return r;
     double* out = c->at<double>(c->L.result);
     double* partial = c->at<double>(c->L.partials);
     if (c->p.precision == NH_FP64)
@@ -1449,6 +1697,7 @@ int nh_diagnostics_read(nh_ctx* c, nh_diag* out)
     if (!c->diag_pending) return fail(c, NH_EINVAL, "no diagnostics enqueued");
     if ((r = set_device(c))) return r;
     cudaStream_t st = c->diag_stream;
+    if ((r = bounded_wait(c, st))) return r;  // the result stays pending: a later call reads it
     const int V = diag_num_values(c->diag_tubes);
     NH_CUDA(c, cudaMemcpyAsync(c->host_result, c->ws + c->L.result, V * sizeof(double), cudaMemcpyDeviceToHost, st));
     NH_CUDA(c, cudaStreamSynchronize(st));
@@ -1534,12 +1783,22 @@ int nh_set_lb_variant(nh_ctx* c, int variant)
     return NH_OK;
 }
 
+int nh_set_wait_limit(nh_ctx* c, double seconds)
+{
+    if (!c) return fail(nullptr, NH_EINVAL, "ctx is NULL");
+    if (isnan(seconds)) return fail(c, NH_EINVAL, "wait limit is NaN");
+    c->wait_limit = seconds > 0.0 ? seconds : 0.0;
+    return NH_OK;
+}
+
 int nh_set_fd_variant(nh_ctx* c, int fused)
 {
     if (!c) return fail(nullptr, NH_EINVAL, "ctx is NULL");
     if (fused != 0 && fused != 1) return fail(c, NH_EINVAL, "FD variant must be 0 or 1");
     if (fused && c->p.frank3) return fail(c, NH_EINVAL, "the three-constant energy runs on the per-site FD kernels only");
     if (fused && c->has_solid) return fail(c, NH_EINVAL, "obstacles run on the per-site FD kernels only");
+    if (fused && (c->p.lap_wide || c->p.n_from_rate))
+        return fail(c, NH_EINVAL, "lap_wide and n_from_rate run on the per-site FD kernels only");
     if (fused != c->fd_fused) drop_graphs(c);
     c->fd_fused = fused;
     return NH_OK;

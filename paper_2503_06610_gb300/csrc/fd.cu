@@ -10,8 +10,13 @@
 //   force      : F_lc,a = d_b sigma_ab, zero stress at solid ghost layers
 // The molecular field is the one-constant chiral form
 //   h = K lap n - 2 K q0 curl n + W0 n_z z_hat
-// (compact Laplacian, central curl).  Beyond the plates the ghost velocity is
-// zero and the ghost director is z_hat (homeotropic) or the adjacent layer.
+// (compact Laplacian, central curl), the exact -dE/dn of the lattice energy
+// (a sum over nearest-neighbour links).  Beyond the plates the ghost velocity
+// is zero and the ghost director is z_hat (homeotropic) or the adjacent layer.
+// A plate without anchoring is a free surface: its links carry no energy, so
+// on the two plate layers the chiral term lacks the link to the ghost layer,
+// which the central curl over the copied ghost would contribute; the kernels
+// take that link out again (free_plate_side).
 #include "nh_internal.cuh"
 
 namespace nh {
@@ -72,6 +77,42 @@ __device__ __forceinline__ void vel_at(const Real* __restrict__ u, const Geom& g
     out[2] = u[2 * g.N + s];
 }
 
+// Sum over the six sites at distance 2 along the axes, S2[c] = sum_b
+// n_c(x + 2 e_b) + n_c(x - 2 e_b), with the ghost rule of dir_at beyond the
+// plates (reading flag lap_wide: the second derivative of the molecular field
+// as the central difference of the central difference,
+// (S2 - 6 n)/4 = sum_b [n(x + 2e_b) - 2 n(x) + n(x - 2e_b)]/4).
+template <typename Real>
+__device__ __forceinline__ void wide_sum(const Real* __restrict__ n, const Geom& g, int x, int y, int z, Real S2[3])
+{
+    auto wrapf = [](int a, int m) {
+        a %= m;
+        return a < 0 ? a + m : a;
+    };
+    Real v[6][3];
+    dir_at(n, g, wrapf(x + 2, g.nx), y, z, v[0]);
+    dir_at(n, g, wrapf(x - 2, g.nx), y, z, v[1]);
+    dir_at(n, g, x, wrapf(y + 2, g.ny), z, v[2]);
+    dir_at(n, g, x, wrapf(y - 2, g.ny), z, v[3]);
+    const int zp = g.walls ? z + 2 : wrapf(z + 2, g.nz), zm = g.walls ? z - 2 : wrapf(z - 2, g.nz);
+    dir_at(n, g, x, y, zp, v[4]);
+    dir_at(n, g, x, y, zm, v[5]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) S2[c] = ((v[0][c] + v[1][c]) + (v[2][c] + v[3][c])) + (v[4][c] + v[5][c]);
+}
+
+// Plate layer of a channel whose plates have no anchoring: -1 on the lowest
+// layer, +1 on the highest, 0 elsewhere (and 0 when nz = 1, where both apply
+// and cancel).  The central curl over the copied ghost layer there holds the
+// term of a link that carries no energy; removing it adds
+//   dh = side K q0 (-n_y, n_x, 0)
+// to the molecular field (-K q0 z x n below, +K q0 z x n above).
+__device__ __forceinline__ int free_plate_side(const Geom& g, int z)
+{
+    if (!g.walls || g.anchoring != NH_ANCHOR_NONE) return 0;
+    return (z == g.nz - 1 ? 1 : 0) - (z == 0 ? 1 : 0);
+}
+
 // 7-point neighbourhood: index 0 = centre, 1 + 2b = +e_b, 2 + 2b = -e_b.
 template <typename Real>
 __device__ __forceinline__ void gather7(const Real* __restrict__ f, const Geom& g, int x, int y, int z, Real v[7][3],
@@ -126,10 +167,13 @@ __device__ __forceinline__ void stencil_diffs(const Real nn[7][3], const Real uu
 //   h_m/g1 = kg (S_m - 6 n_m) - kqg ce_m + w0g n_z delta_mz,
 //   -lambda n_a D_am + W_ma n_a = sum_a n_a [(1 - lambda)/4 v[a][m] - (1 + lambda)/4 v[m][a]],
 //   -u_a d_a n_m = -1/2 sum_a u_a e[a][m].
-// hx (optional) is an extra molecular field (three-constant correction).
+// hx (optional) is an extra molecular field (three-constant correction);
+// side is free_plate_side() of the point's layer; S2 (optional, lap_wide) the
+// distance-2 sum of wide_sum, which replaces the compact Laplacian.
 template <typename Real>
 __device__ __forceinline__ void director_rate(const Real nn[7][3], const Real uu[7][3], const FDPar<Real>& p,
-                                              Real rate[3], const Real* hx = nullptr)
+                                              Real rate[3], const Real* hx = nullptr, int side = 0,
+                                              const Real* S2 = nullptr)
 {
     Real e[3][3], v[3][3], S[3], ce[3];
     stencil_diffs(nn, uu, e, v, S, ce);
@@ -143,7 +187,7 @@ __device__ __forceinline__ void director_rate(const Real nn[7][3], const Real uu
     }
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-        Real r = p.kg * (S[m] - Real(6) * n[m]);
+        Real r = S2 != nullptr ? Real(0.25) * p.kg * (S2[m] - Real(6) * n[m]) : p.kg * (S[m] - Real(6) * n[m]);
         r = fma(-p.kqg, ce[m], r);
         if (m == 2) r = fma(p.w0g, n[2], r);
         if (hx != nullptr) r = fma(hx[m], p.inv_gamma1, r);
@@ -154,6 +198,11 @@ __device__ __forceinline__ void director_rate(const Real nn[7][3], const Real uu
             r = fma(hu[a], e[a][m], r);
         }
         rate[m] = r;
+    }
+    if (side != 0) {
+        const Real sk = Real(side) * p.kqg;
+        rate[0] = fma(-sk, n[1], rate[0]);
+        rate[1] = fma(sk, n[0], rate[1]);
     }
 }
 
@@ -252,17 +301,29 @@ __device__ __forceinline__ void fd_predict_site(const FDChan<Real>& c, int s)
     Real nn[7][3], uu[7][3], r[3];
     gather7(c.n, c.g, x, y, z, nn, true);
     gather7(c.u, c.g, x, y, z, uu, false, c.solid);
+    const int side = free_plate_side(c.g, z);
+    Real S2[3];
+    if (c.p.lap_wide) wide_sum(c.n, c.g, x, y, z, S2);
+    const Real* s2 = c.p.lap_wide ? S2 : nullptr;
     if (c.P3 != nullptr) {
         Real hx[3];
         frank3_field_site(c, nn, x, y, z, hx);
-        director_rate(nn, uu, c.p, r, hx);
+        director_rate(nn, uu, c.p, r, hx, side, s2);
     } else {
-        director_rate(nn, uu, c.p, r);
+        director_rate(nn, uu, c.p, r, (const Real*)nullptr, side, s2);
+    }
+    Real np[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) np[a] = nn[0][a] + c.p.dt * r[a];
+    if (c.p.renorm_p) {
+        const Real inv = Real(1) / sqrt(np[0] * np[0] + np[1] * np[1] + np[2] * np[2]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) np[a] *= inv;
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         c.ndot[a * N + s] = r[a];
-        c.nP[a * N + s] = nn[0][a] + c.p.dt * r[a];
+        c.nP[a * N + s] = np[a];
     }
 }
 
@@ -275,17 +336,28 @@ __device__ __forceinline__ void fd_correct_site(const FDChan<Real>& c, int s)
     Real nn[7][3], uu[7][3], r[3];
     gather7(c.nP, c.g, x, y, z, nn, true);
     gather7(c.u, c.g, x, y, z, uu, false, c.solid);
+    const int side = free_plate_side(c.g, z);
+    Real S2[3];
+    if (c.p.lap_wide) wide_sum(c.nP, c.g, x, y, z, S2);
+    const Real* s2 = c.p.lap_wide ? S2 : nullptr;
     if (c.P3 != nullptr) {
         Real hx[3];
         frank3_field_site(c, nn, x, y, z, hx);
-        director_rate(nn, uu, c.p, r, hx);
+        director_rate(nn, uu, c.p, r, hx, side, s2);
     } else {
-        director_rate(nn, uu, c.p, r);
+        director_rate(nn, uu, c.p, r, (const Real*)nullptr, side, s2);
     }
     const int N = c.g.N;
-    Real nw[3];
+    Real nw[3], avg[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) nw[a] = c.n[a * N + s] + c.p.dt * Real(0.5) * (c.ndot[a * N + s] + r[a]);
+    for (int a = 0; a < 3; ++a) {
+        avg[a] = Real(0.5) * (c.ndot[a * N + s] + r[a]);
+        nw[a] = c.n[a * N + s] + c.p.dt * avg[a];
+    }
+    if (c.p.n_rate) {  // the averaged rate stays in ndot for the stress (reading flag n_from_rate)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) c.ndot[a * N + s] = avg[a];
+    }
     const Real inv = Real(1) / sqrt(nw[0] * nw[0] + nw[1] * nw[1] + nw[2] * nw[2]);
 #pragma unroll
     for (int a = 0; a < 3; ++a) c.n[a * N + s] = nw[a] * inv;
@@ -293,9 +365,13 @@ __device__ __forceinline__ void fd_correct_site(const FDChan<Real>& c, int s)
 
 // LC stress (Eq. force-lc-eq, bracket) at one point from its 7-point
 // neighbourhood of n and u: sigma[3a+b].
+// S2 (optional, lap_wide): the distance-2 sum of wide_sum; rate (optional,
+// n_from_rate): the corrector's averaged dn/dt at the point, from which
+// N = P_perp(rate) + u.grad n - W n replaces the director-equation form.
 template <typename Real>
 __device__ __forceinline__ void stress_point(const Real nn[7][3], const Real uu[7][3], const FDPar<Real>& p,
-                                             Real sig[9], const Real* hx = nullptr, const Real* Pd = nullptr)
+                                             Real sig[9], const Real* hx = nullptr, const Real* Pd = nullptr,
+                                             int side = 0, const Real* S2 = nullptr, const Real* rate = nullptr)
 {
     // In the differences of stencil_diffs (Ds = v + v^T = 4 D, Dn_a = Ds_am n_m = 4 D_am n_m):
     //   N_m = [h_m - (h.n) n_m]/g1 - lambda/4 [Dn_m - (n.Dn) n_m]       (kinematic transport, normal to n)
@@ -310,10 +386,16 @@ __device__ __forceinline__ void stress_point(const Real nn[7][3], const Real uu[
     Real h[3];
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-        h[m] = fma(-p.kq, ce[m], p.K * (S[m] - Real(6) * n[m]));
+        const Real lap = S2 != nullptr ? Real(0.25) * (S2[m] - Real(6) * n[m]) : S[m] - Real(6) * n[m];
+        h[m] = fma(-p.kq, ce[m], p.K * lap);
         if (hx != nullptr) h[m] += hx[m];
     }
     h[2] = fma(p.W0, n[2], h[2]);
+    if (side != 0) {  // free plate layer (see free_plate_side)
+        const Real sk = Real(side) * p.kq;
+        h[0] = fma(-sk, n[1], h[0]);
+        h[1] = fma(sk, n[0], h[1]);
+    }
     Real Ds[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -328,9 +410,29 @@ __device__ __forceinline__ void stress_point(const Real nn[7][3], const Real uu[
     const Real nDn = fma(n[2], Dn[2], fma(n[1], Dn[1], n[0] * Dn[0]));
     const Real hn = fma(n[2], h[2], fma(n[1], h[1], n[0] * h[0]));
     Real P[3], Q[3];
+    Real Nr[3] = {0, 0, 0};
+    if (rate != nullptr) {
+        // t_m = rate_m + u_a d_a n_m - W_ma n_a, W_ma = (d_a u_m - d_m u_a)/2 (in the raw
+        // differences u_a e[a][m]/2 and (v[a][m] - v[m][a]) n_a / 4); N = t - (n.t) n
+        Real t[3];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            Real acc = rate[m];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                acc = fma(Real(0.5) * uu[0][a], e[a][m], acc);
+                acc = fma(Real(-0.25) * (v[a][m] - v[m][a]), n[a], acc);
+            }
+            t[m] = acc;
+        }
+        const Real nt = fma(n[2], t[2], fma(n[1], t[1], n[0] * t[0]));
+#pragma unroll
+        for (int m = 0; m < 3; ++m) Nr[m] = fma(-nt, n[m], t[m]);
+    }
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-        const Real Nm = p.inv_gamma1 * fma(-hn, n[m], h[m]) - p.g2q * fma(-nDn, n[m], Dn[m]);
+        const Real Nm = rate != nullptr ? Nr[m]
+                                        : p.inv_gamma1 * fma(-hn, n[m], h[m]) - p.g2q * fma(-nDn, n[m], Dn[m]);
         P[m] = fma(p.a5q, Dn[m], fma(p.a2, Nm, p.a1q * nDn * n[m]));
         Q[m] = fma(p.a6q, Dn[m], p.a3 * Nm);
     }
@@ -375,14 +477,22 @@ __device__ __forceinline__ void stress_site(const FDChan<Real>& c, int s)
     Real nn[7][3], uu[7][3], sig[9];
     gather7(c.n, c.g, x, y, z, nn, true);
     gather7(c.u, c.g, x, y, z, uu, false, c.solid);
+    Real S2[3], rate[3];
+    if (c.p.lap_wide) wide_sum(c.n, c.g, x, y, z, S2);
+    if (c.p.n_rate) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) rate[a] = c.ndot[a * c.g.N + s];
+    }
+    const Real* s2 = c.p.lap_wide ? S2 : nullptr;
+    const Real* rt = c.p.n_rate ? rate : nullptr;
     if (c.P3 != nullptr) {
         Real hx[3], Pd[9];
         frank3_field_site(c, nn, x, y, z, hx);
 #pragma unroll
         for (int k = 0; k < 9; ++k) Pd[k] = c.P3[k * c.g.N + s];
-        stress_point(nn, uu, c.p, sig, hx, Pd);
+        stress_point(nn, uu, c.p, sig, hx, Pd, free_plate_side(c.g, z), s2, rt);
     } else {
-        stress_point(nn, uu, c.p, sig);
+        stress_point(nn, uu, c.p, sig, (const Real*)nullptr, (const Real*)nullptr, free_plate_side(c.g, z), s2, rt);
     }
     const int N = c.g.N;
 #pragma unroll
@@ -415,12 +525,14 @@ __device__ __forceinline__ void force_site(const FDChan<Real>& c, int s)
     const int sxp = xp + g.nx * (y + g.ny * z), sxm = xm + g.nx * (y + g.ny * z);
     const int syp = x + g.nx * (yp + g.ny * z), sym = x + g.nx * (ym + g.ny * z);
     const int szp = x + g.nx * (y + g.ny * (zp_ok ? zp : 0)), szm = x + g.nx * (y + g.ny * (zm_ok ? zm : 0));
+    // ghost stress beyond a plate: zero, or the wall layer's own (mirror)
+    const Real gmir = c.p.mirror ? Real(1) : Real(0);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const Real* sx = c.sigma + (3 * a + 0) * N;
         const Real* sy = c.sigma + (3 * a + 1) * N;
         const Real* sz = c.sigma + (3 * a + 2) * N;
-        const Real dz = (zp_ok ? sz[szp] : Real(0)) - (zm_ok ? sz[szm] : Real(0));
+        const Real dz = (zp_ok ? sz[szp] : gmir * sz[s]) - (zm_ok ? sz[szm] : gmir * sz[s]);
         c.F[a * N + s] = Real(0.5) * ((sx[sxp] - sx[sxm]) + (sy[syp] - sy[sym]) + dz);
     }
 }
@@ -690,13 +802,18 @@ __device__ __forceinline__ HaloPoint halo_point()
 // hi): n^P into pslot[i1], the rate into r.
 template <typename Real>
 __device__ __forceinline__ void predict_point(const FDPar<Real>& par, const Real* lo, const Real* mid, const Real* hi,
-                                              int i1, int i2, Real* pslot, Real r[3])
+                                              int i1, int i2, Real* pslot, Real r[3], int side)
 {
     Real nn[7][3], uu[7][3], np[3];
     gather_slots(lo, mid, hi, i2, nn, uu);
-    director_rate(nn, uu, par, r);
+    director_rate(nn, uu, par, r, (const Real*)nullptr, side);
 #pragma unroll
     for (int a = 0; a < 3; ++a) np[a] = nn[0][a] + par.dt * r[a];
+    if (par.renorm_p) {
+        const Real inv = Real(1) / sqrt(np[0] * np[0] + np[1] * np[1] + np[2] * np[2]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) np[a] *= inv;
+    }
     st3(pslot, i1, np);
 }
 
@@ -705,12 +822,13 @@ __device__ __forceinline__ void predict_point(const FDPar<Real>& par, const Real
 // chunk need n^P only at the tile's own points (halo = false).
 template <typename Real>
 __device__ __forceinline__ void predict_plane(const FDPar<Real>& par, const Real* lo, const Real* mid, const Real* hi,
-                                              Real* pslot, int i1, int i2, const HaloPoint& hp, bool halo, Real rown[3])
+                                              Real* pslot, int i1, int i2, const HaloPoint& hp, bool halo, Real rown[3],
+                                              int side)
 {
-    predict_point(par, lo, mid, hi, i1, i2, pslot, rown);
+    predict_point(par, lo, mid, hi, i1, i2, pslot, rown, side);
     if (halo && hp.has) {
         Real r[3];
-        predict_point(par, lo, mid, hi, hp.i1, hp.i2, pslot, r);
+        predict_point(par, lo, mid, hi, hp.i1, hp.i2, pslot, r, side);
     }
 }
 
@@ -749,7 +867,8 @@ __device__ void fused_a_tile(const FDChan<Real>& c, const Real* __restrict__ nin
     prefetch_plane(nin, c.u, g, pm, zb + 1, v);  // in flight during the first predictor plane
     __syncthreads();
     Real rcur[3] = {0, 0, 0}, rnext[3] = {0, 0, 0};  // predictor rate at the own point, planes z and z + 1
-    if (!is_ghost_plane(g, zb - 1)) predict_plane(c.p, IN(s0), IN(s1), IN(s2), PR(s1), i1, i2, hp, false, rnext);
+    if (!is_ghost_plane(g, zb - 1))
+        predict_plane(c.p, IN(s0), IN(s1), IN(s2), PR(s1), i1, i2, hp, false, rnext, free_plate_side(g, zb - 1));
     // u one layer below the corrector's plane, at the thread's own point, carried in registers
     Real ulo[3], nc[3];
     split_pt(IN(s1), i2, nc, ulo);
@@ -757,14 +876,16 @@ __device__ void fused_a_tile(const FDChan<Real>& c, const Real* __restrict__ nin
     commit_plane(pm, v, IN(s0));  // plane zb + 1
     prefetch_plane(nin, c.u, g, pm, zb + 2, v);
     __syncthreads();
-    if (!is_ghost_plane(g, zb)) predict_plane(c.p, IN(s1), IN(s2), IN(s0), PR(s2), i1, i2, hp, true, rcur);
+    if (!is_ghost_plane(g, zb))
+        predict_plane(c.p, IN(s1), IN(s2), IN(s0), PR(s2), i1, i2, hp, true, rcur, free_plate_side(g, zb));
     int sa = s1, sb = s2, sc = s0;  // slots of planes z - 1, z, z + 1 (plane z + 2 takes sa)
     for (int z = zb; z < ze; ++z) {
         __syncthreads();  // plane z - 1 is no longer read; its slot takes plane z + 2
         commit_plane(pm, v, IN(sa));
         __syncthreads();
         if (z + 1 < ze) prefetch_plane(nin, c.u, g, pm, z + 3, v);  // overlaps the two evaluations below
-        if (!is_ghost_plane(g, z + 1)) predict_plane(c.p, IN(sb), IN(sc), IN(sa), PR(sc), i1, i2, hp, z + 1 < ze, rnext);
+        if (!is_ghost_plane(g, z + 1))
+            predict_plane(c.p, IN(sb), IN(sc), IN(sa), PR(sc), i1, i2, hp, z + 1 < ze, rnext, free_plate_side(g, z + 1));
         __syncthreads();
         if (active) {
             const Real* mid = PR(sb);
@@ -798,7 +919,7 @@ __device__ void fused_a_tile(const FDChan<Real>& c, const Real* __restrict__ nin
             split_pt(inh, i2, dummy, uu[5]);
 #pragma unroll
             for (int a = 0; a < 3; ++a) uu[6][a] = ulo[a];
-            director_rate(nn, uu, c.p, r);
+            director_rate(nn, uu, c.p, r, (const Real*)nullptr, free_plate_side(g, z));
             Real nw[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) nw[a] = n0[a] + c.p.dt * Real(0.5) * (rcur[a] + r[a]);
@@ -826,11 +947,11 @@ __device__ void fused_a_tile(const FDChan<Real>& c, const Real* __restrict__ nin
 // that owns the point (szown).
 template <typename Real>
 __device__ __forceinline__ void stress_point_plane(const FDPar<Real>& par, const Real* lo, const Real* mid,
-                                                   const Real* hi, int i1, int i2, Real* slot, Real sz[3])
+                                                   const Real* hi, int i1, int i2, Real* slot, Real sz[3], int side)
 {
     Real nn[7][3], uu[7][3], sig[9];
     gather_slots(lo, mid, hi, i2, nn, uu);
-    stress_point(nn, uu, par, sig);
+    stress_point(nn, uu, par, sig, (const Real*)nullptr, (const Real*)nullptr, side);
     const Real sx[3] = {sig[0], sig[3], sig[6]}, sy[3] = {sig[1], sig[4], sig[7]};
     st3(slot, i1, sx);
     st3(slot + 4 * kP1, i1, sy);
@@ -851,11 +972,12 @@ __device__ __forceinline__ void stress_plane(const FDChan<Real>& c, int p, const
         for (int a = 0; a < 3; ++a) szown[a] = Real(0);
         return;
     }
-    stress_point_plane(c.p, lo, mid, hi, i1, i2, slot, szown);
+    const int side = free_plate_side(c.g, p);
+    stress_point_plane(c.p, lo, mid, hi, i1, i2, slot, szown, side);
     const HaloPoint hp = halo_point();  // recomputed here: kernel B runs at the register limit
     if (halo && hp.has) {
         Real sz[3];
-        stress_point_plane(c.p, lo, mid, hi, hp.i1, hp.i2, slot, sz);
+        stress_point_plane(c.p, lo, mid, hi, hp.i1, hp.i2, slot, sz, side);
     }
 }
 
@@ -912,8 +1034,13 @@ __device__ void fused_b_tile(const FDChan<Real>& c, const Real* __restrict__ nin
             ld3(sy, i1 + kHX1, yp);
             ld3(sy, i1 - kHX1, ym);
             const int s = (x0 + tx) + g.nx * ((y0 + ty) + g.ny * z);
+            // ghost planes hold zero sigma_az; mirror: the wall layer's own
+            const bool mlo = c.p.mirror && is_ghost_plane(g, z - 1), mhi = c.p.mirror && is_ghost_plane(g, z + 1);
 #pragma unroll
-            for (int a = 0; a < 3; ++a) c.F[a * N + s] = Real(0.5) * ((xp[a] - xm[a]) + (yp[a] - ym[a]) + (szhi[a] - szlo[a]));
+            for (int a = 0; a < 3; ++a) {
+                const Real hi = mhi ? szmid[a] : szhi[a], lo = mlo ? szmid[a] : szlo[a];
+                c.F[a * N + s] = Real(0.5) * ((xp[a] - xm[a]) + (yp[a] - ym[a]) + (hi - lo));
+            }
             if (ncopy) {
                 Real n0[3], u0[3];
                 split_pt(IN(sb), i2, n0, u0);

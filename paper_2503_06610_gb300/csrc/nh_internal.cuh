@@ -114,6 +114,12 @@ struct FDPar {
     // of the strain-rate and vorticity tensors folded in (lambda = g2/g1):
     Real kg, kqg, w0g, c1, c2;            // K/g1, K q0/g1, W0/g1, (1 - lambda)/4, -(1 + lambda)/4
     Real kq, g2q, a1q, a4q, a5q, a6q, k4, kq2;  // K q0, lambda/4, a1/4, a4'/4, a5/4, a6/4, K/4, K q0/2
+    // Reading flags (nh_params): renormalise the predictor; central-of-central
+    // second derivatives in h (per-site kernels); N of the stress from the
+    // corrector's averaged rate, which the corrector then leaves in ndot
+    // (per-site kernels; set only for the force that follows an FD update);
+    // ghost stress = the adjacent layer's in the force divergence.
+    int renorm_p, lap_wide, n_rate, mirror;
 };
 
 // Three-constant correction of the Frank energy density at one site
@@ -272,6 +278,27 @@ cudaError_t launch_director_change(const Real* n, Real* snap, double* partial, d
 // C4 projection of the director about the axis through (nx/2, nx/2) (diag.cu)
 template <typename Real>
 cudaError_t launch_symmetrize_c4(const Real* n, Real* out, int nx, int nz, cudaStream_t s);
+
+// Row copies between slabs (slab.cu): item k copies `comps` components of
+// one row (nz runs of nx consecutive elements) from src to dst; component c,
+// layer z starts at c * cstride + z * zstride elements from the base.
+constexpr int kMaxRowCopies = 96;
+constexpr int kMaxSlabs = 64;
+struct RowCopyItem {
+    const void* src;
+    void* dst;
+    int nx, nz, comps;
+    int src_zstride, dst_zstride;
+    int src_cstride, dst_cstride;
+};
+struct RowCopyList {
+    int count;
+    RowCopyItem item[kMaxRowCopies];
+};
+cudaError_t launch_row_copies(const RowCopyList& list, int elem_bytes, cudaStream_t s);
+
+// The parameter checks of nh_create (api.cu): NH_OK, or NH_EINVAL with the reason in err.
+int validate_params(const nh_params* p, std::string& err);
 
 // Record the text returned by nh_last_error(NULL) on this thread (api.cu).
 void set_global_error(const char* msg);

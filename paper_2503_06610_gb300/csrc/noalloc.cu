@@ -67,16 +67,19 @@ extern "C" int nh_diagnostics_noalloc(const nh_params* p, const void* f, const v
                                       const void* rho, double* out, void* stream)
 {
     if (!p || !f || !n || !u || !rho || !out) return noalloc_fail(NH_EINVAL, "NULL argument");
-    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return noalloc_fail(NH_EINVAL, "nx, ny, nz must be >= 1");
-    if (19.0 * p->nx * p->ny * p->nz > 2147483647.0)
-        return noalloc_fail(NH_EINVAL, "domain too large: 19*nx*ny*nz must fit in a signed 32-bit index");
+    std::string err;
+    if (nh::validate_params(p, err) != NH_OK) return noalloc_fail(NH_EINVAL, err);  // the checks of nh_create
     const bool fp64 = p->precision == NH_FP64 && p->storage == NH_STORE_F64;
     const bool fp32 = p->precision == NH_FP32 && p->storage == NH_STORE_F32;
     if (!fp64 && !fp32)
         return noalloc_fail(NH_EINVAL, "nh_diagnostics_noalloc supports FP64/F64 and FP32/F32 populations only");
+    // A bound on the work of one call, not on the scratch: the reduction runs at
+    // most 1024 blocks (the scratch holds their partials) that stride over the
+    // domain, so larger domains would reduce correctly but are kept to at most
+    // 256 column chunks per block.
     const long long items = (long long)p->nx * p->ny * ((p->nz + 15) / 16);
     if (items > NH_NOALLOC_MAX_ITEMS)
-        return noalloc_fail(NH_EINVAL, "domain too large for the static scratch: nx*ny*ceil(nz/16) = " +
+        return noalloc_fail(NH_EINVAL, "domain larger than this entry point accepts: nx*ny*ceil(nz/16) = " +
                                            std::to_string(items) + " > " + std::to_string(NH_NOALLOC_MAX_ITEMS));
     double* partials = nullptr;
     int r = partials_address(&partials);

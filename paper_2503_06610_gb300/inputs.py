@@ -236,17 +236,27 @@ def warmstart_samples(count, seed=0, nx=64, ny=64, lz_choices=(32,), K=0.005, dt
 
 # ------------------------------------------------------------------ paper regime (Table I)
 
-def table1_regime(nx=64, ny=64, nz=16, dt_fd=250, split=0.15, lb_share=None, radius=7.0, shifted=True):
+def table1_regime(nx=64, ny=64, nz=16, dt_fd=250, split=0.5, lb_share=None, radius=7.0, shifted=True,
+                  paper_order=True):
     """The paper's test case in lattice units: Table I (MBBA, doubled alpha4),
     pitch P = 14, 64x64x16 (Sec. III.A), g = 2e-9, no anchoring at the plates
     with bulk W0 = 1.5e-8.  The one-constant K is the mean of K11, K22, K33;
     gamma1 = alpha3 - alpha2, gamma2 = alpha3 + alpha2.  The isotropic viscosity
     alpha4 is shared between the FD force (alpha4' = split * alpha4) and the
     lattice Boltzmann fluid (2 rho c_s^2 (tau - 1/2) = (1 - split) alpha4, which
-    fixes tau; lb_share overrides that share).  The explicit FD stress is held
-    over dt_FD LB steps, so its stiffest part, about alpha4' + alpha1 + alpha5 +
-    alpha6, must stay well below the LB viscous stress: split = 0.15 is stable
-    at dt_FD = 2, 10, 250 with the Table I viscosities, an even split is not.
+    fixes tau; lb_share overrides that share).  The default split = 0.5 is
+    Sec. II.B's choice of the same viscosity in both parts (tau = 1.199).
+
+    paper_order = True runs the loop of Sec. II.D in its printed order: the
+    FD update and the force come between the macroscopic fields and the
+    collision of the same step.  With the fused order (the collision keeps the
+    force of the previous interval) the force lags the velocity it is computed
+    from by one LB step, and at odd dt_FD that lag feeds a lattice mode of
+    wavevector (pi/2, pi/2, pi/2) that flips sign every step, through the
+    central differences of the viscous stress; with these viscosities it grows
+    until the run diverges.  Even dt_FD samples that mode in phase and does
+    not feed it.
+
     The tube is the radial pi-twist ansatz of radius P/2 (the cited ansatz is
     not available)."""
     K11, K22, K33 = 1.67e-7, 7.88e-8, 2.62e-7
@@ -255,6 +265,6 @@ def table1_regime(nx=64, ny=64, nz=16, dt_fd=250, split=0.15, lb_share=None, rad
     params = dict(nx=nx, ny=ny, nz=nz, walls_z=True, anchoring="none", shifted=shifted, tau=tau,
                   g=(2e-9, 0.0, 0.0), K=(K11 + K22 + K33) / 3.0, q0=2 * math.pi / 14.0, W0=1.5e-8,
                   dt_fd=dt_fd, gamma1=a3 - a2, gamma2=a3 + a2, alpha1=a1, alpha2=a2, alpha3=a3,
-                  alpha4p=split * a4, alpha5=a5, alpha6=a6)
+                  alpha4p=split * a4, alpha5=a5, alpha6=a6, paper_order=paper_order)
     n0 = skyrmion_tubes(nx, ny, nz, [(nx / 2, ny / 2)], radius)
     return params, n0

@@ -50,6 +50,8 @@ class nh_params(ctypes.Structure):
         ("precision", ctypes.c_int32), ("storage", ctypes.c_int32), ("shifted", ctypes.c_int32),
         ("dt_fd", ctypes.c_int32), ("check_stability", ctypes.c_int32),
         ("paper_order", ctypes.c_int32), ("frank3", ctypes.c_int32),
+        ("renorm_predictor", ctypes.c_int32), ("lap_wide", ctypes.c_int32),
+        ("n_from_rate", ctypes.c_int32), ("ghost_sigma", ctypes.c_int32),
         ("tau", ctypes.c_double), ("g", ctypes.c_double * 3),
         ("K", ctypes.c_double), ("q0", ctypes.c_double),
         ("gamma1", ctypes.c_double), ("gamma2", ctypes.c_double),
@@ -68,6 +70,14 @@ class nh_diag(ctypes.Structure):
         ("centroid", (ctypes.c_double * 2) * NH_MAX_TUBES),
         ("tube_weight", ctypes.c_double * NH_MAX_TUBES),
     ]
+
+
+class nh_row_copy(ctypes.Structure):
+    _fields_ = [("src_slab", ctypes.c_int32), ("src_row", ctypes.c_int32),
+                ("dst_slab", ctypes.c_int32), ("dst_row", ctypes.c_int32), ("comp_mask", ctypes.c_uint32)]
+
+
+NH_HALO_POPULATIONS, NH_HALO_VECTOR, NH_HALO_STRESS = 0, 1, 2
 
 
 class nh_timing(ctypes.Structure):
@@ -106,6 +116,7 @@ SIGNATURES = {
     "nh_get_timing": ([_VP, ctypes.POINTER(nh_timing)], ctypes.c_int),
     "nh_launch_count": ([_VP], ctypes.c_int64),
     "nh_set_graphs": ([_VP, ctypes.c_int], ctypes.c_int),
+    "nh_set_wait_limit": ([_VP, ctypes.c_double], ctypes.c_int),
     "nh_set_lb_variant": ([_VP, ctypes.c_int], ctypes.c_int),
     "nh_set_fd_variant": ([_VP, ctypes.c_int], ctypes.c_int),
     "nh_autotune": ([_VP, _VP, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
@@ -121,6 +132,10 @@ SIGNATURES = {
     "nh_unet_adam": ([_VP, _VP, _VP, _VP, ctypes.c_int64, ctypes.c_int, ctypes.c_float, _VP], ctypes.c_int),
     "nh_unet_destroy": ([_VP], None),
     "nh_diagnostics_noalloc": ([ctypes.POINTER(nh_params), _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "nh_slab_plan": ([ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_int, ctypes.POINTER(nh_row_copy),
+                      ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "nh_slab_init": ([ctypes.POINTER(_VP), ctypes.c_int, _VP], ctypes.c_int),
+    "nh_slab_step": ([ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int64, _VP], ctypes.c_int),
 }
 
 _lib = None
@@ -173,6 +188,11 @@ def make_params(d: dict) -> nh_params:
     p.dt_fd = int(d.get("dt_fd", 1))
     p.check_stability = 1 if d.get("check_stability", False) else 0
     p.paper_order = 1 if d.get("paper_order", False) else 0
+    for k in ("renorm_predictor", "lap_wide", "n_from_rate"):
+        v = d.get(k, False)
+        setattr(p, k, int(v) if not isinstance(v, bool) else (1 if v else 0))
+    gs = d.get("ghost_sigma", "zero")
+    p.ghost_sigma = {"zero": 0, "mirror": 1}[gs] if isinstance(gs, str) else int(gs)
     if d.get("K11") is not None and d.get("K22") is not None and d.get("K33") is not None:
         p.frank3 = 1
         p.K11, p.K22, p.K33 = float(d["K11"]), float(d["K22"]), float(d["K33"])
@@ -253,6 +273,29 @@ def nh_fd_update(ctx, stream=None):
 def nh_batch_step(ctxs, n_lb_steps: int, stream=None):
     arr = (_VP * len(ctxs))(*[c.value if isinstance(c, _VP) else c for c in ctxs])
     _check(load_library().nh_batch_step(arr, len(ctxs), int(n_lb_steps), _VP(stream or 0)))
+
+
+def nh_slab_plan(ny_local, kind):
+    """Halo plan of slabs with ny_local interior rows each: a list of
+    (src_slab, src_row, dst_slab, dst_row, [components])."""
+    lib = load_library()
+    arr = (ctypes.c_int32 * len(ny_local))(*[int(v) for v in ny_local])
+    n = ctypes.c_int(0)
+    _check(lib.nh_slab_plan(len(ny_local), arr, int(kind), None, 0, ctypes.byref(n)))
+    out = (nh_row_copy * max(1, n.value))()
+    _check(lib.nh_slab_plan(len(ny_local), arr, int(kind), out, n.value, ctypes.byref(n)))
+    return [(c.src_slab, c.src_row, c.dst_slab, c.dst_row, [b for b in range(32) if c.comp_mask >> b & 1])
+            for c in out[:n.value]]
+
+
+def nh_slab_init(ctxs, stream=None):
+    arr = (_VP * len(ctxs))(*[c.value if isinstance(c, _VP) else c for c in ctxs])
+    _check(load_library().nh_slab_init(arr, len(ctxs), _VP(stream or 0)))
+
+
+def nh_slab_step(ctxs, n_lb_steps: int, stream=None):
+    arr = (_VP * len(ctxs))(*[c.value if isinstance(c, _VP) else c for c in ctxs])
+    _check(load_library().nh_slab_step(arr, len(ctxs), int(n_lb_steps), _VP(stream or 0)))
 
 
 def nh_batch_autotune(ctxs, stream=None) -> int:
@@ -341,6 +384,10 @@ def nh_launch_count(ctx) -> int:
 
 def nh_set_graphs(ctx, on: bool):
     _check(load_library().nh_set_graphs(ctx, 1 if on else 0), ctx)
+
+
+def nh_set_wait_limit(ctx, seconds):
+    _check(load_library().nh_set_wait_limit(ctx, float(seconds)), ctx)
 
 
 def nh_set_lb_variant(ctx, variant: int):
@@ -467,6 +514,10 @@ class Channel:
     def set_graphs(self, on=True):
         nh_set_graphs(self.ctx, on)
 
+    def set_wait_limit(self, seconds):
+        """Bound the host-side waits (seconds > 0; NHError with code NH_ETIMEOUT when exceeded)."""
+        nh_set_wait_limit(self.ctx, seconds)
+
     def set_lb_variant(self, variant):
         nh_set_lb_variant(self.ctx, variant)
 
@@ -563,3 +614,61 @@ class UNet:
 def nh_unet_adam(params, grad, m, v, step, lr, stream=None):
     _check(load_library().nh_unet_adam(_dp(params), _dp(grad), _dp(m), _dp(v), params.numel(), int(step),
                                        float(lr), _VP(stream or 0)))
+
+
+class SlabGroup:
+    """One channel split along y into slabs (nh_slab_*): slab k is a Channel
+    over ny_local[k] interior rows plus a ghost row on each side.  Fields are
+    split into and gathered from the slabs by indexing only."""
+
+    def __init__(self, params: dict, ny_local, device: int = 0, stream=None):
+        self.params = dict(params)
+        self.ny_local = [int(v) for v in ny_local]
+        assert sum(self.ny_local) == int(params["ny"]), "the slabs must cover the channel"
+        self.y0 = np.concatenate([[0], np.cumsum(self.ny_local)[:-1]]).astype(int)
+        self.slabs = [Channel(dict(params, ny=n + 2), device=device, stream=stream) for n in self.ny_local]
+        self.stream = self.slabs[0].stream
+        for ch in self.slabs:
+            ch.set_fd_variant(0)
+
+    def _rows(self, k):
+        return (self.y0[k] - 1 + np.arange(self.ny_local[k] + 2)) % int(self.params["ny"])
+
+    def _split(self, a, k, comps):
+        if a is None:
+            return None
+        nx, ny, nz = int(self.params["nx"]), int(self.params["ny"]), int(self.params["nz"])
+        g = np.asarray(a, dtype=np.float64).reshape(comps, nz, ny, nx)
+        return np.ascontiguousarray(g[:, :, self._rows(k), :].reshape(comps, -1))
+
+    def set_fields(self, n, u=None, rho=None):
+        for k, ch in enumerate(self.slabs):
+            r = self._split(rho, k, 1)
+            ch.set_fields(self._split(n, k, 3), self._split(u, k, 3), None if r is None else r[0])
+        nh_slab_init([c.ctx for c in self.slabs], self.stream.cuda_stream)
+
+    def step(self, count: int):
+        nh_slab_step([c.ctx for c in self.slabs], count, self.stream.cuda_stream)
+
+    def _gather(self, parts, comps):
+        nx, ny, nz = int(self.params["nx"]), int(self.params["ny"]), int(self.params["nz"])
+        out = np.empty((comps, nz, ny, nx))
+        for k, a in enumerate(parts):
+            a = a.reshape(comps, nz, self.ny_local[k] + 2, nx)
+            out[:, :, self.y0[k]:self.y0[k] + self.ny_local[k], :] = a[:, :, 1:-1, :]
+        return out.reshape(comps, -1)
+
+    def get_fields(self):
+        got = [ch.get_fields() for ch in self.slabs]
+        return (self._gather([g[0] for g in got], 3), self._gather([g[1] for g in got], 3),
+                self._gather([g[2][None] for g in got], 1)[0])
+
+    def get_populations(self):
+        return self._gather([ch.get_populations() for ch in self.slabs], 19)
+
+    def get_force(self):
+        return self._gather([ch.get_force() for ch in self.slabs], 3)
+
+    def close(self):
+        for ch in self.slabs:
+            ch.close()

@@ -1,7 +1,8 @@
 """Precision x dt_FD sweep of the hybrid step (the experiment of Secs. III.A-III.B).
 
 For one workload (by default the 96x96x32 single skyrmion tube in Poiseuille
-flow, g_x in {1e-6, 1e-5}) every combination of arithmetic / population store
+flow, g_x in {1e-6, 1e-5}; also the Table I regime of Sec. III.A and the
+256x256x64 multi-tube channel) every combination of arithmetic / population store
 (FP64, FP32 plain, FP32 shifted, FP16 and BF16 shifted) and dt_FD is run on the
 GPU through the C ABI; each run reports
 
@@ -10,7 +11,7 @@ GPU through the C ABI; each run reports
   as in the paper, or the smallest dt_FD that is stable for the workload
   (``--ref-dt``) - as relative L2 and as the paper's epsilon (Sec. III.A) and
   its per-component form (Sec. III.B),
-* the tube centroid and its distance from the reference centroid.
+* the tube centroids and their largest distance from the reference centroids.
 
 Usage:  python -m paper_2503_06610_gb300.sweep [--steps 5000] [--gx 1e-5] [--out sweep.json]
 """
@@ -46,11 +47,11 @@ def eps_component(u, uref, a):
     return float(np.sum(np.abs(u[a] - uref[a])) / np.sum(np.abs(uref[a])))
 
 
-def run_one(params, n0, centre, precision, storage, shifted, steps):
+def run_one(params, n0, centres, precision, storage, shifted, steps):
     import torch
     ch = nh.Channel(dict(params, precision=precision, storage=storage, shifted=shifted))
     ch.set_fields(n0)
-    ch.set_tubes([centre])
+    ch.set_tubes(centres)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -62,39 +63,50 @@ def run_one(params, n0, centre, precision, storage, shifted, steps):
     n, u, rho = ch.get_fields()
     d = ch.diagnostics(allow_unstable=True)
     ch.close()
-    return {"mlups": ch.N * steps / (ms * 1e-3) / 1e6, "n": n, "u": u, "centroid": d["centroids"][0].tolist(),
+    return {"mlups": ch.N * steps / (ms * 1e-3) / 1e6, "n": n, "u": u, "centroid": d["centroids"].tolist(),
             "max_u": float(np.nanmax(np.abs(u))) if np.isfinite(u).any() else float("nan"),
             "nonfinite": d["nonfinite"], "energy": d["energy"]}
 
 
 def sweep(steps=5000, gx=1e-5, dts=(1, 2, 4, 8, 16), settings=SETTINGS, nx=96, ny=96, nz=32, radius=12.0,
-          regime="skyrmion", ref_dt=1, split=0.15):
+          regime="skyrmion", ref_dt=1, split=0.5, paper_order=None):
     if regime == "table1":
-        base, n0 = inputs.table1_regime(nx=nx, ny=ny, nz=nz, dt_fd=1, split=split)
+        base, n0 = inputs.table1_regime(nx=nx, ny=ny, nz=nz, dt_fd=1, split=split,
+                                        paper_order=True if paper_order is None else paper_order)
         radius = 7.0
+        centres = [(nx / 2, ny / 2)]
+    elif regime == "multitube":
+        base, n0, centres = inputs.multi_tube_channel(dt_fd=1, nx=nx, ny=ny, nz=nz)
+        radius = 20.0
+        if paper_order is not None:
+            base = dict(base, paper_order=paper_order)
     else:
         base, n0 = inputs.skyrmion_channel(gx=gx, dt_fd=1, nx=nx, ny=ny, nz=nz, radius=radius)
-    centre = (nx / 2, ny / 2)
-    ref = run_one(dict(base, dt_fd=ref_dt), n0, centre, "fp64", "f64", True, steps)
+        if paper_order is not None:
+            base = dict(base, paper_order=paper_order)
+        centres = [(nx / 2, ny / 2)]
+    ref = run_one(dict(base, dt_fd=ref_dt), n0, centres, "fp64", "f64", True, steps)
     rows = []
     for dt in dts:
         for precision, storage, shifted in settings:
             if (precision, storage, shifted, dt) == ("fp64", "f64", True, ref_dt):
                 r = ref
             else:
-                r = run_one(dict(base, dt_fd=dt), n0, centre, precision, storage, shifted, steps)
+                r = run_one(dict(base, dt_fd=dt), n0, centres, precision, storage, shifted, steps)
             dx = (np.array(r["centroid"]) - np.array(ref["centroid"]) + 0.5 * np.array([nx, ny])) % np.array(
                 [nx, ny]) - 0.5 * np.array([nx, ny])
+            shift = np.hypot(dx[:, 0], dx[:, 1])
             rows.append({
                 "dt_fd": dt, "precision": precision, "storage": storage, "shifted": shifted,
                 "mlups": r["mlups"], "rel_l2_u": rel_l2(r["u"], ref["u"]), "rel_l2_n": rel_l2(r["n"], ref["n"]),
                 "eps_u": eps(r["u"], ref["u"]), "eps_ux": eps_component(r["u"], ref["u"], 0),
                 "eps_uy": eps_component(r["u"], ref["u"], 1), "eps_uz": eps_component(r["u"], ref["u"], 2),
-                "centroid": r["centroid"], "centroid_shift": float(np.hypot(*dx)), "nonfinite": r["nonfinite"],
+                "centroid": r["centroid"], "centroid_shift": float(np.max(shift)), "nonfinite": r["nonfinite"],
                 "max_u": r["max_u"], "max_u_ref": ref["max_u"],
             })
-    name = ("Table I regime" if regime == "table1" else "skyrmion channel") + \
-        f" {nx}x{ny}x{nz}, R={radius}, q0={base['q0']:.4f}, gx={base['g'][0]}, K={base['K']:.3g}"
+    name = {"table1": "Table I regime", "multitube": "multi-tube channel"}.get(regime, "skyrmion channel") + \
+        f" {nx}x{ny}x{nz}, R={radius}, q0={base['q0']:.4f}, gx={base['g'][0]}, K={base['K']:.3g}" + \
+        (", loop order of Sec. II.D" if base.get("paper_order") else ", fused loop order")
     return {"workload": name,
             "steps": steps, "reference": f"fp64 shifted dt_FD={ref_dt}", "reference_centroid": ref["centroid"],
             "tau": base["tau"], "alpha4p": base["alpha4p"], "reference_nonfinite": ref["nonfinite"],
@@ -107,20 +119,27 @@ def main():
     ap.add_argument("--gx", type=float, nargs="+", default=[1e-6, 1e-5])
     ap.add_argument("--dts", type=int, nargs="+", default=[1, 2, 4, 8, 16])
     ap.add_argument("--out", default=None)
-    ap.add_argument("--regime", default="skyrmion", choices=["skyrmion", "table1"])
+    ap.add_argument("--regime", default="skyrmion", choices=["skyrmion", "table1", "multitube"])
+    ap.add_argument("--settings", nargs="+", default=None,
+                    help="precision/storage/s|p triples, e.g. fp32/f16s/s (default: all five)")
     ap.add_argument("--size", type=int, nargs=3, default=None, help="nx ny nz")
-    ap.add_argument("--ref-dt", type=int, default=None,
-                    help="dt_FD of the FP64 reference run (default 1; 2 for table1, where dt_FD = 1 is unstable)")
-    ap.add_argument("--split", type=float, default=0.15, help="table1: share of alpha4 carried by the FD force")
+    ap.add_argument("--ref-dt", type=int, default=1, help="dt_FD of the FP64 reference run")
+    ap.add_argument("--split", type=float, default=0.5, help="table1: share of alpha4 carried by the FD force")
+    ap.add_argument("--order", choices=["default", "paper", "fused"], default="default",
+                    help="loop order: paper = Sec. II.D as printed (the table1 default), fused = the collision keeps "
+                         "the force of the previous interval (the skyrmion default)")
     args = ap.parse_args()
     results = []
-    size = args.size or ((64, 64, 16) if args.regime == "table1" else (96, 96, 32))
-    gxs = [2e-9] if args.regime == "table1" else args.gx
+    size = args.size or {"table1": (64, 64, 16), "multitube": (256, 256, 64)}.get(args.regime, (96, 96, 32))
+    gxs = {"table1": [2e-9], "multitube": [1e-5]}.get(args.regime, args.gx)
+    settings = SETTINGS
+    if args.settings:
+        settings = [(a, b, c == "s") for a, b, c in (t.split("/") for t in args.settings)]
     for gx in gxs:
         t0 = time.time()
-        res = sweep(steps=args.steps, gx=gx, dts=tuple(args.dts), nx=size[0], ny=size[1], nz=size[2],
-                    regime=args.regime, split=args.split,
-                    ref_dt=args.ref_dt or (2 if args.regime == "table1" else 1))
+        res = sweep(steps=args.steps, gx=gx, dts=tuple(args.dts), nx=size[0], ny=size[1], nz=size[2], settings=settings,
+                    regime=args.regime, split=args.split, ref_dt=args.ref_dt,
+                    paper_order={"default": None, "paper": True, "fused": False}[args.order])
         res["wall_s"] = time.time() - t0
         results.append(res)
         for r in res["rows"]:

@@ -32,9 +32,11 @@ def test_library_exports_every_declared_symbol(nh):
 
 def test_params_struct_layout_matches_header(nh):
     import ctypes
-    # 12 int32 then 18 doubles, no padding
-    assert ctypes.sizeof(nh.nh_params) == 12 * 4 + 18 * 8
-    assert nh.nh_params.tau.offset == 48
+    # 16 int32 then 18 doubles, no padding; the reading flags follow frank3
+    assert ctypes.sizeof(nh.nh_params) == 16 * 4 + 18 * 8
+    assert nh.nh_params.tau.offset == 64
+    names = [f[0] for f in nh.nh_params._fields_]
+    assert names[11:16] == ["frank3", "renorm_predictor", "lap_wide", "n_from_rate", "ghost_sigma"]
 
 
 def _base(**kw):
@@ -51,6 +53,7 @@ def _base(**kw):
     dict(K=0.04, dt_fd=8, check_stability=True),
     dict(K11=0.0, K22=1.0, K33=1.0), dict(K11=1.0, K22=float("inf"), K33=1.0),
     dict(nx=113025456, ny=1, nz=1),
+    dict(renorm_predictor=2), dict(lap_wide=-1), dict(n_from_rate=3), dict(ghost_sigma=2),
 ])
 def test_invalid_params_rejected(nh, bad):
     p = nh.make_params(_base(**bad))

@@ -90,6 +90,7 @@ def test_stress_force_rows_fp64(nh, oracle_mod, anchoring, walls, grid, fused):
     ch.set_fields(n0, u0)
     F = ch.get_force()
     assert O.rel_l2(F, Fref) < 1e-12
+    assert np.max(np.abs(F - Fref)) <= 1e-12 * np.max(np.abs(Fref))  # every site, plate layers included
 
 
 @pytest.mark.parametrize("fused", [1, 0])
@@ -109,6 +110,7 @@ def test_fd_update_rows_fp64(nh, oracle_mod, anchoring, walls, grid, fused):
     ch.fd_update()
     n, u, _ = ch.get_fields()
     assert O.rel_l2(n, nref) < 1e-13
+    assert np.max(np.abs(n - nref)) < 1e-13  # every site, plate layers included
     assert np.max(np.abs(np.linalg.norm(n, axis=0) - 1)) < 1e-14
     assert O.rel_l2(ch.get_force(), Fref) < 1e-12
 
