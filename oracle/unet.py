@@ -99,13 +99,12 @@ def _bf16(t):
     return t.to(torch.bfloat16).to(t.dtype)
 
 
-class _RoundAct(torch.autograd.Function):
-    """Rounds a stored activation to BF16 and the gradient arriving at it to
-    BF16 (a layer output kept in BF16 whose gradient enters BF16 matrix products)."""
+class _RoundGrad(torch.autograd.Function):
+    """Identity in the forward pass; rounds the gradient to BF16 (the operand of a BF16 matrix product)."""
 
     @staticmethod
     def forward(ctx, t):
-        return _bf16(t)
+        return t.clone()
 
     @staticmethod
     def backward(ctx, g):
@@ -128,12 +127,17 @@ def forward(params, x, n_ansatz, bf16_storage=False, keep=None):
     """x [B][16][Z][Y][X], n_ansatz [B][3][Z][Y][X] -> (n_pred, delta).
 
     bf16_storage=True keeps every stored activation in BF16 and rounds the
-    gradient entering each convolution to BF16, as a BF16-activation
-    implementation does; the arithmetic itself stays float64."""
-    ra = _RoundAct.apply if bf16_storage else (lambda t: t)
+    gradient entering each convolution's weight and data products to BF16, as a
+    BF16-activation implementation does, while the bias gradient sums the
+    unrounded gradient of the pre-activation (an FP32 reduction); the
+    arithmetic itself stays float64."""
     rf = _RoundFwd.apply if bf16_storage else (lambda t: t)
+    rg = _RoundGrad.apply if bf16_storage else (lambda t: t)
+
     def r(name, t):
-        y = ra(F.relu(conv3(t, *params[name])))
+        w, b = params[name]
+        pre = rg(conv3(t, w, None)) + b.view(1, -1, 1, 1, 1)
+        y = rf(F.relu(pre))
         if keep is not None:
             keep[name] = y.detach()
         return y

@@ -78,7 +78,7 @@ class WarmStartNet:
 
 # ------------------------------------------------------------------ plain relaxation
 
-def relax(chans, tol=2e-10, check_every=100, max_steps=200000):
+def relax(chans, tol=5e-11, check_every=100, max_steps=200000):
     """Relax every channel (batched) until the director's largest rate of change,
     max |n(t) - n(t - T)| / T over the last check interval T = check_every
     FD steps, is below tol; returns the FD steps each one needed (capped at
@@ -250,7 +250,7 @@ def main():
     ap.add_argument("--samples", type=int, default=2000)
     ap.add_argument("--held-out", type=int, default=200)
     ap.add_argument("--epochs", type=int, default=20)
-    ap.add_argument("--tol", type=float, default=2e-10, help="stop when max |dn/dt| < tol")
+    ap.add_argument("--tol", type=float, default=5e-11, help="stop when max |dn/dt| < tol (per LB time unit)")
     ap.add_argument("--max-steps", type=int, default=200000)
     ap.add_argument("--out", default=None)
     args = ap.parse_args()

@@ -32,14 +32,20 @@ def _bf16(a):
     return torch.tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
 
 
-def _problem(B=2, nx=16, ny=16, nz=16, seed=0):
+def _problem(B=2, nx=16, ny=16, nz=16, seed=0, smooth_target=False):
+    """Network parameters, ansatz, target and scalars.  The random target makes
+    every gradient a small residual of many random-sign terms; the smooth
+    target (a tube of another radius, as in training) makes it a coherent sum."""
     rng = np.random.default_rng(seed)
     flat = I.unet_init_params(seed)
     hs = len(flat) - 51
     flat[hs:hs + 48] = rng.normal(0, 0.3, size=48)        # a head large enough to move n
     flat[:hs] += 0.02 * rng.normal(size=hs) * (rng.random(hs) < 0.01)
     n_ans = np.stack([I.skyrmion_tubes(nx, ny, nz, [(nx / 2 + k, ny / 2)], 5.0) for k in range(B)])
-    target = np.stack([I.random_director(nx, ny, nz, seed=10 + k) for k in range(B)])
+    if smooth_target:
+        target = np.stack([I.skyrmion_tubes(nx, ny, nz, [(nx / 2 + k, ny / 2)], 3.5 + k) for k in range(B)])
+    else:
+        target = np.stack([I.random_director(nx, ny, nz, seed=10 + k) for k in range(B)])
     scal = np.array([[2 * math.pi / (12 + 4 * k), float(nz), 1e-5 * (k + 1)] for k in range(B)])
     return flat, n_ans, target, scal
 
@@ -103,37 +109,67 @@ def test_forward_and_gradients_match_oracle(env):
     assert rel(g, grad_o) < 0.12
     assert all(r[2] < 0.25 and r[3] > 0.97 for r in report), report
     assert report[-1][2] < 2e-2
-    # against the oracle that keeps activations and the gradients entering
-    # each convolution in BF16 (float64 arithmetic otherwise) the weight
-    # gradients must agree to FP32-accumulation level.  (Bias gradients are
-    # summed from the unrounded FP32 output gradient on the GPU, so they are
-    # compared with the float64 oracle above.)
-    loss_e, grad_e, npred_e = _oracle(U, flat, n_ans, target, scal, dims, bf16_storage=True)
-    worst = 0.0
+
+
+def _gpu_loss_grad(torch, nh, flat, n_ans, scal, target, dims):
+    dev = torch.device("cuda")
+    B = n_ans.shape[0]
+    net = nh.UNet(B, *dims)
+    params = torch.tensor(flat, dtype=torch.float32, device=dev)
+    na = torch.tensor(n_ans, dtype=torch.float32, device=dev)
+    out = torch.empty_like(na)
+    grad = torch.zeros_like(params)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    net.set_params(params)
+    net.forward(params, na, torch.tensor(scal, dtype=torch.float32, device=dev), out)
+    net.backward(params, na, torch.tensor(target, dtype=torch.float32, device=dev), grad, loss)
+    torch.cuda.synchronize()
+    return float(loss), grad.cpu().numpy().astype(np.float64), out.cpu().numpy().astype(np.float64)
+
+
+def _per_layer(U, g, ref):
+    rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+    rows = []
     off = 0
     for name, ci, co in U.CONV_LAYERS:
         n_w = 27 * ci * co
-        e_w = rel(g[off:off + n_w], grad_e[off:off + n_w])
-        e_b = rel(g[off + n_w:off + n_w + co], grad_e[off + n_w:off + n_w + co])
-        print("vs BF16-storage oracle %-6s W %.3e b %.3e" % (name, e_w, e_b))
-        worst = max(worst, e_w)
+        rows.append((name, rel(g[off:off + n_w], ref[off:off + n_w]),
+                     rel(g[off + n_w:off + n_w + co], ref[off + n_w:off + n_w + co])))
         off += n_w + co
-    print("worst weight gradient vs BF16-storage oracle: %.3e" % worst)
-    # with a random target each weight gradient is a small residual of ~1e4
-    # random-sign terms, which magnifies the rare BF16 rounding flips of the
-    # activations; the exactly representable case below pins the kernels tightly
+    rows.append(("head", rel(g[off:], ref[off:]), 0.0))
+    return rows
+
+
+def test_gradients_match_bf16_storage_oracle(env):
+    """Against the oracle that stores every activation in BF16 and rounds the
+    gradient entering each convolution's products to BF16, with the bias
+    gradient summed from the unrounded gradient as the kernels do (float64
+    arithmetic otherwise), for a smooth target as in training: every layer's
+    weight and bias gradient agrees to within 3 %.  What remains are the rare
+    activations whose FP32 and float64 sums round to neighbouring BF16 values."""
+    torch, nh, ws, U = env
+    dims = (16, 16, 16)
+    flat, n_ans, target, scal = _problem(B=2, smooth_target=True)
+    loss_e, grad_e, npred_e = _oracle(U, flat, n_ans, target, scal, dims, bf16_storage=True)
+    loss, g, npred = _gpu_loss_grad(torch, nh, flat, n_ans, scal, target, dims)
+    rows = _per_layer(U, g, grad_e)
+    for r in rows:
+        print("vs BF16-storage oracle %-6s W %.3e b %.3e" % r)
+    assert abs(loss - loss_e) / loss_e < 1e-3
     assert np.linalg.norm(npred - npred_e) / np.linalg.norm(npred_e - n_ans) < 1e-2
-    assert worst < 0.15
+    assert all(w < 3e-2 and b < 3e-2 for _, w, b in rows), rows
 
 
 def test_gradients_exact_representable_case(env):
-    """Weights k/64, inputs m/16, biases k/64: FP32 sums of the early layers are
-    exact and both sides round identical values to BF16, so the GPU gradients
-    must equal the BF16-storage oracle's closely (no cancellation blow-up)."""
+    """Weights k/64, inputs m/16, biases k/64 and a smooth target: the FP32
+    sums of the early layers are exact, so both sides round identical values
+    to BF16 there and the GPU gradients follow the BF16-storage oracle's more
+    closely still; differences start only in the deeper layers, whose sums
+    round in FP32."""
     torch, nh, ws, U = env
     dims = (16, 16, 16)
     B = 2
-    flat, n_ans, target, scal = _problem(B=B)
+    flat, n_ans, target, scal = _problem(B=B, smooth_target=True)
     hs = len(flat) - 51
     q = np.round(flat[:hs] * 64.0) / 64.0
     rng = np.random.default_rng(9)
@@ -145,30 +181,13 @@ def test_gradients_exact_representable_case(env):
     n_ans = np.round(n_ans * 16.0) / 16.0
     scal = np.array([[2 * math.pi / 16, 16.0, 0.0]] * B)   # q0 Lz / 2 pi = 1, Lz / 32 = 0.5, W0 = 0
     loss_e, grad_e, npred_e = _oracle(U, flat, n_ans, target, scal, dims, bf16_storage=True)
-    dev = torch.device("cuda")
-    net = nh.UNet(B, *dims)
-    params = torch.tensor(flat, dtype=torch.float32, device=dev)
-    na = torch.tensor(n_ans, dtype=torch.float32, device=dev)
-    out = torch.empty_like(na)
-    grad = torch.zeros_like(params)
-    loss = torch.zeros(1, dtype=torch.float32, device=dev)
-    net.set_params(params)
-    net.forward(params, na, torch.tensor(scal, dtype=torch.float32, device=dev), out)
-    net.backward(params, na, torch.tensor(target, dtype=torch.float32, device=dev), grad, loss)
-    torch.cuda.synchronize()
-    g = grad.cpu().numpy().astype(np.float64)
-    rel = lambda a, b: np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
-    assert abs(float(loss) - loss_e) / loss_e < 1e-4
-    off = 0
-    errs = []
-    for name, ci, co in U.CONV_LAYERS:
-        n_w = 27 * ci * co
-        e_w = rel(g[off:off + n_w], grad_e[off:off + n_w])
-        errs.append(e_w)
-        print("exact case %-6s W %.3e" % (name, e_w))
-        off += n_w + co
-    assert max(errs) < 2e-2
-    assert np.median(errs) < 5e-3
+    loss, g, npred = _gpu_loss_grad(torch, nh, flat, n_ans, scal, target, dims)
+    rows = _per_layer(U, g, grad_e)
+    for r in rows:
+        print("exact case %-6s W %.3e b %.3e" % r)
+    assert abs(loss - loss_e) / loss_e < 1e-4
+    assert all(w < 1e-2 and b < 1e-2 for _, w, b in rows), rows
+    assert np.median([w for _, w, _ in rows]) < 2e-3
 
 
 def test_forward_activations_match_bf16_oracle(env):
@@ -258,10 +277,11 @@ def test_trained_network_saves_relaxation_steps(env):
     warm-start experiment (48x48x16 cells, wide enough that a tube does not feel
     its periodic images): the plain relaxation continued from the trained
     network's prediction ends on the field of the relaxation from the ansatz
-    (max |dn| <= 1e-4) from a start several times closer to it, in fewer FD steps."""
+    (max |dn| <= 1e-4) from a start several times closer to it, in fewer FD
+    steps."""
     torch, nh, ws, U = env
     samples = I.warmstart_samples(176, seed=3, nx=48, ny=48, lz_choices=(16,))
-    kw = dict(tol=2e-10, max_steps=80000)
+    kw = dict(tol=5e-11, max_steps=160000)
     targets, steps, _ = ws.generate(samples, **kw)
     valid = [i for i in range(len(samples)) if not ws.collapsed(targets[i], samples[i][0]["nz"])]
     train_idx = [i for i in valid if i < 160]
@@ -272,6 +292,8 @@ def test_trained_network_saves_relaxation_steps(env):
     assert hist[-1] < 0.5 * hist[0]
     res = ws.evaluate(net, samples, targets, steps, test_idx, **kw)
     print("warm start (48x48x16):", {k: v for k, v in res.items() if k != "per_sample"})
+    for ps in sorted(res["per_sample"], key=lambda q: -q["max_dn"])[:3]:
+        print("  worst held-out samples:", ps)
     assert res["max_dn_final"] <= 1e-4
     # the prediction starts several times closer (RMS over the cell) to the
     # relaxed field than the ansatz; relaxation to the stop tolerance is
