@@ -87,7 +87,7 @@ typedef struct nh_params {
                              one-constant lattice energy with K plus, per fluid site,
                              (K11-K)/2 (div n)^2 + (K22-K)/2 (n.curl n + q0)^2 + (K33-K)/2 |n x curl n|^2
                              with central differences; h is its exact variational derivative.  Runs on the
-                             per-site FD kernels (nh_set_fd_variant 0); not supported by the batched calls. */
+                             per-site FD kernels (nh_set_fd_variant 0), in batches too. */
     /* Reading flags.  The paper is silent on each choice below; 0 is the default reading.  Each
        flag is 0 or 1; any other value is NH_EINVAL. */
     int32_t renorm_predictor; /* 1: also renormalise the predictor n^P to |n^P| = 1 before the corrector
@@ -125,7 +125,8 @@ typedef struct nh_diag {
     double energy;         /* lattice Frank energy E_d of the director (see nh_diagnostics) */
     double max_u;          /* max |u| over sites */
     double min_norm, max_norm; /* extrema of |n| */
-    int32_t nonfinite;     /* number of sites with a NaN/Inf in n, u or rho */
+    int32_t nonfinite;     /* sites with a NaN/Inf in n, plus sites with one in u, rho or the sum of
+                              their populations (a site bad in both counts twice): 0 iff all is finite */
     int32_t n_tubes;       /* number of tracked tubes */
     double centroid[NH_MAX_TUBES][2]; /* tube centroids (x, y) in [0, nx) x [0, ny) */
     double tube_weight[NH_MAX_TUBES]; /* sum of (1 - n_z)/2 over each tube's sites */
@@ -218,10 +219,14 @@ int nh_fd_update(nh_ctx* ctx, void* stream);
  * graph cached per list of contexts (dropped when a context is rebound,
  * re-tuned or destroyed).  All contexts must share precision, storage,
  * shifted and dt_fd, be on one device, have fields set and be at the same
- * step phase (step mod dt_fd and buffer parity); otherwise NH_EINVAL and
- * nothing runs.  Launch counts and timing are recorded on ctxs[0]; the launch
- * shape is ctxs[0]'s LB variant (see nh_batch_autotune).  Asynchronous on
- * stream (NULL = ctxs[0]'s stream). */
+ * step phase (step mod dt_fd and buffer parity), and not use paper_order,
+ * lap_wide or n_from_rate; otherwise NH_EINVAL and nothing runs.  The FD
+ * passes use the fused kernels when every channel does, else the per-site
+ * kernels (with the three-constant P stages when a channel has frank3); with
+ * obstacles in any channel the LB sweep runs one site per thread.  Launch
+ * counts and timing are recorded on ctxs[0]; the launch shape is ctxs[0]'s LB
+ * variant (see nh_batch_autotune).  Asynchronous on stream (NULL = ctxs[0]'s
+ * stream). */
 int nh_batch_step(nh_ctx* const* ctxs, int count, int64_t n_lb_steps, void* stream);
 
 /* Autotuner of the batched LB launch: times every launch shape valid for all
@@ -318,7 +323,8 @@ int nh_symmetrize_c4(nh_ctx* ctx);
  * diagnostics sum over fluid sites (links with at least one fluid end).
  * The mask is copied into the workspace; the force is recomputed if the
  * fields are set.  Obstacles run on the per-site FD kernels (the fused FD
- * variant is rejected) and are not supported by the batched calls.  With
+ * variant is rejected); a batch with obstacles in any channel runs the
+ * per-site FD kernels and a one-site-per-thread LB sweep for all.  With
  * walls_z = 1 the plates stay as they are.  Synchronises the context's stream
  * (the fluid sites are counted on the host). */
 int nh_set_solid(nh_ctx* ctx, const uint8_t* mask, int on_device);
@@ -382,6 +388,16 @@ int nh_autotune(nh_ctx* ctx, void* stream, int* chosen);
 /* Use CUDA graphs for whole dt_fd blocks (default on). */
 int nh_set_graphs(nh_ctx* ctx, int on);
 
+/* Diagnostics folded into the LB sweep (default on): every LB launch that
+ * writes u and rho (the steps that feed an FD update or end a call) also
+ * leaves per-block FP64 sums of the stored populations, max |u| and the
+ * non-finite count, so that nh_diagnostics of that state reads only the
+ * director (the energy, |n| and the tube sums) instead of every population,
+ * u and rho again.  Applies to F32 and F64 stores without obstacles and
+ * without paper_order; the results equal the unfolded ones up to the
+ * summation order of the mass.  0 turns it off (drops the cached graphs). */
+int nh_set_diag_fold(nh_ctx* ctx, int on);
+
 /* Bound the host-side waits of this context (nh_get_fields, nh_get_populations, nh_get_force,
  * nh_diagnostics, nh_diagnostics_read, nh_director_change): with seconds > 0 a wait that has
  * not seen the context's stream finish within that time returns NH_ETIMEOUT and leaves the
@@ -407,7 +423,7 @@ int nh_set_wait_limit(nh_ctx* ctx, double seconds);
  *   out[0] = sum of the stored populations (the mass is out[0] + N when
  *            p->shifted, out[0] otherwise), out[1] = lattice Frank energy E_d
  *   (as in nh_diagnostics), out[2] = max |u|, out[3] = min |n|,
- *   out[4] = max |n|, out[5] = number of sites with a NaN/Inf.
+ *   out[4] = max |n|, out[5] = non-finite count (as nh_diag.nonfinite).
  * Asynchronous on stream (NULL = legacy default stream); no tube tracking.
  * The sums are deterministic for given inputs and pointer alignment: with
  * even nx and every field pointer aligned to two elements the reduction reads

@@ -46,7 +46,7 @@ size_t store_size(const nh_params& p)
 
 struct Layout {
     size_t f[2], F, Fprev, n, nP, ndot, u, rho, sigma, P3, snap, staging, partials, result, scales, absmax, trig, solid,
-        total;
+        lbpart, total;
 };
 
 Layout make_layout(const nh_params& p)
@@ -79,6 +79,8 @@ Layout make_layout(const nh_params& p)
     L.absmax = take(4 * sizeof(float));
     L.trig = take(2 * ((size_t)p.nx + p.ny) * sizeof(double));
     L.solid = take(N);  // obstacle mask, 1 byte per site (used after nh_set_solid)
+    // diagnostics partials of a macro LB launch: [3][blocks], at most one block per 128 sites
+    L.lbpart = take(3 * ((N + 127) / 128 + 1) * sizeof(double));
     L.total = off;
     return L;
 }
@@ -230,6 +232,9 @@ struct nh_ctx {
     int diag_tubes = 0;
     cudaStream_t diag_stream = nullptr;
     double wait_limit = 0.0;  // seconds; > 0 bounds the host-side waits (nh_set_wait_limit)
+    int diag_fold = 1;        // macro LB launches leave the diagnostics' population, u and rho sums
+    int64_t lbp_step = -1;    // step whose state those sums describe (-1: none)
+    int lbp_blocks = 0;       // blocks of the launch that wrote them
 
     template <typename T>
     T* at(size_t off) const
@@ -329,6 +334,7 @@ LBChan<Real, Store> lb_chan(nh_ctx* c, int src)
     a.rho = c->at<Real>(c->L.rho);
     a.scales = c->at<float>(c->L.scales);
     a.ctrl = c->at<unsigned>(c->L.absmax);
+    a.part = nullptr;
     a.src = src;
     a.g = Geom{c->p.nx, c->p.ny, c->p.nz, c->p.walls_z, c->p.anchoring, c->N};
     a.omega = Real(1.0 / c->p.tau);
@@ -419,20 +425,37 @@ int timed(nh_ctx* c, int kclass, cudaStream_t st, F&& launch, const char* what)
     return NH_OK;
 }
 
+// The diagnostics can take the population, u and rho sums from the macro LB
+// launch that wrote the state (F32 / F64 stores, no obstacles, and not with
+// the printed loop order, whose macro launch's populations are replaced).
+bool fold_ok(const nh_ctx* c)
+{
+    return c->diag_fold && !c->p.paper_order && !c->has_solid &&
+           (c->p.storage == NH_STORE_F32 || c->p.storage == NH_STORE_F64);
+}
+
 // One LB launch from population buffer src.  stale_u: u is shifted by half of
-// the previous FD interval's force (Fprev) instead of the current one.
+// the previous FD interval's force (Fprev) instead of the current one.  A
+// macro launch (write_macro) also leaves the diagnostics' sums when fold_ok.
 int enqueue_lb(nh_ctx* c, int src, bool write_macro, cudaStream_t st, bool stale_u = false)
 {
     const bool sh = c->p.shifted != 0;
+    const bool fold = write_macro && fold_ok(c);
+    if (fold) {
+        c->lbp_step = c->step + 1;
+        c->lbp_blocks = lb_blocks(c->lb_variant, c->N);
+    }
     switch (c->p.storage) {
     case NH_STORE_F64: {
         auto a = lb_chan<double, double>(c, src);
         if (stale_u) a.Fu = c->at<const double>(c->L.Fprev);
+        if (fold) a.part = c->at<double>(c->L.lbpart);
         return timed(c, NH_KCLASS_LB, st, [&] { return launch_lb(a, sh, write_macro, c->lb_variant, st); }, "lb");
     }
     case NH_STORE_F32: {
         auto a = lb_chan<float, float>(c, src);
         if (stale_u) a.Fu = c->at<const float>(c->L.Fprev);
+        if (fold) a.part = c->at<double>(c->L.lbpart);
         return timed(c, NH_KCLASS_LB, st, [&] { return launch_lb(a, sh, write_macro, c->lb_variant, st); }, "lb");
     }
     case NH_STORE_F16S: {
@@ -712,6 +735,10 @@ int enqueue_diag(nh_ctx* c, cudaStream_t st)
     a.partials = c->at<double>(c->L.partials);
     a.result = c->at<double>(c->L.result);
     a.blocks = diag_blocks();
+    if (fold_ok(c) && c->lbp_step == c->step) {  // the last macro LB launch summed f, u and rho of this state
+        a.lbpart = c->at<const double>(c->L.lbpart);
+        a.lbp_blocks = c->lbp_blocks;
+    }
     NH_CUDA(c, launch_diagnostics(a, st));
     c->launches += 2;
     return NH_OK;
@@ -771,10 +798,9 @@ int batch_prepare(nh_ctx* const* ctxs, int count, int64_t n_lb_steps, BatchPlan*
         if (c->p.precision != c0->p.precision || c->p.storage != c0->p.storage || c->p.shifted != c0->p.shifted ||
             c->p.dt_fd != c0->p.dt_fd)
             return fail(nullptr, NH_EINVAL, "channels must share precision, storage, shifted and dt_fd");
-        if (c->p.paper_order || c->p.frank3 || c->has_solid || c->p.lap_wide || c->p.n_from_rate)
+        if (c->p.paper_order || c->p.lap_wide || c->p.n_from_rate)
             return fail(nullptr, NH_EINVAL, "channel " + std::to_string(k) +
-                                                ": paper_order, frank3, obstacles, lap_wide and n_from_rate are not "
-                                                "supported in batches");
+                                                ": paper_order, lap_wide and n_from_rate are not supported in batches");
         if (c->device != c0->device) return fail(nullptr, NH_EINVAL, "channels must be on one device");
         if (c->cur != c0->cur || c->step % c0->p.dt_fd != c0->step % c0->p.dt_fd)
             return fail(nullptr, NH_EINVAL, "channels must be at the same step phase (step mod dt_fd, buffer parity)");
@@ -821,9 +847,8 @@ int batch_prepare_relax(nh_ctx* const* ctxs, int count, int64_t n_fd_steps, Batc
         if (!c->bound || !c->fields_set)
             return fail(nullptr, NH_EINVAL, "channel " + std::to_string(k) + ": workspace or fields not set");
         if (c->p.precision != c0->p.precision) return fail(nullptr, NH_EINVAL, "channels must share the precision");
-        if (c->p.frank3 || c->has_solid || c->p.lap_wide)
-            return fail(nullptr, NH_EINVAL, "channel " + std::to_string(k) +
-                                                ": frank3, obstacles and lap_wide are not supported in batches");
+        if (c->p.lap_wide)
+            return fail(nullptr, NH_EINVAL, "channel " + std::to_string(k) + ": lap_wide is not supported in batches");
         if (c->device != c0->device) return fail(nullptr, NH_EINVAL, "channels must be on one device");
         for (int j = 0; j < k; ++j)
             if (ctxs[j] == c) return fail(nullptr, NH_EINVAL, "a context appears twice in the batch");
@@ -870,7 +895,14 @@ int batch_fd_typed(BatchPlan* b, cudaStream_t st, int stages = 4)
     nh_ctx* c0 = b->ctxs[0];
     const int n = (int)b->ctxs.size();
     static thread_local FDBatch<Real> batch;
-    if (c0->fd_fused) {
+    // the fused kernels only when every channel runs on them (not the three-constant energy, lap_wide or
+    // n_from_rate, nor a channel set to the per-site kernels)
+    bool fused = true, frank3 = false;
+    for (nh_ctx* c : b->ctxs) {
+        fused = fused && c->fd_fused;
+        frank3 = frank3 || c->p.frank3;
+    }
+    if (fused) {
         // stages == 4: full FD update (A: n -> nP, B: nP -> F and n); stages == 2: one relaxation step (A, copy back)
         const int fstages[2] = {0, 1};
         const int classes[2] = {NH_KCLASS_FD_PREDICT, NH_KCLASS_STRESS};
@@ -892,14 +924,21 @@ int batch_fd_typed(BatchPlan* b, cudaStream_t st, int stages = 4)
             }
         return NH_OK;
     }
+    // per-site stages: predict, correct, stress, force; with the three-constant energy each of the
+    // first three is preceded by the P stage of the field it differentiates (4: n, 5: n^P)
     const int classes[4] = {NH_KCLASS_FD_PREDICT, NH_KCLASS_FD_CORRECT, NH_KCLASS_STRESS, NH_KCLASS_FORCE};
     for (int stage = 0; stage < stages; ++stage) {
-        for (int g0 = 0; g0 < n; g0 += kMaxBatch) {
-            batch.count = std::min(kMaxBatch, n - g0);
-            for (int k = 0; k < batch.count; ++k) batch.ch[k] = fd_chan<Real>(b->ctxs[g0 + k]);
-            const int grid = 8 * c0->sm_count;
-            int r = timed(c0, classes[stage], st, [&] { return launch_fd_batch(batch, stage, grid, st); }, "fd_batch");
-            if (r) return r;
+        const int pre = (frank3 && stage < 3) ? (stage == 1 ? 5 : 4) : -1;
+        for (int pass = pre >= 0 ? 0 : 1; pass < 2; ++pass) {
+            const int kernel_stage = pass == 0 ? pre : stage;
+            for (int g0 = 0; g0 < n; g0 += kMaxBatch) {
+                batch.count = std::min(kMaxBatch, n - g0);
+                for (int k = 0; k < batch.count; ++k) batch.ch[k] = fd_chan<Real>(b->ctxs[g0 + k]);
+                const int grid = 8 * c0->sm_count;
+                int r = timed(c0, classes[stage], st, [&] { return launch_fd_batch(batch, kernel_stage, grid, st); },
+                              "fd_batch");
+                if (r) return r;
+            }
         }
     }
     return NH_OK;
@@ -1239,6 +1278,7 @@ int nh_bind_workspace(nh_ctx* c, void* dev_ptr, size_t bytes)
         c->launches += 1;
     }
     c->bound = true;
+    c->lbp_step = -1;
     c->fields_set = false;
     c->cur = 0;
     c->step = 0;
@@ -1318,6 +1358,7 @@ int nh_set_fields(nh_ctx* c, const double* n, const double* u, const double* rho
     if (!on_device) NH_CUDA(c, cudaStreamSynchronize(st));
     c->fields_set = true;
     c->snap_valid = false;
+    c->lbp_step = -1;
     return NH_OK;
 }
 
@@ -1377,6 +1418,7 @@ int nh_set_populations(nh_ctx* c, const double* f, int on_device)
     default: r = encode_all<__nv_bfloat16>(c, f, on_device, c->stream); break;
     }
     if (r) return r;
+    c->lbp_step = -1;
     NH_CUDA(c, cudaStreamSynchronize(c->stream));
     return NH_OK;
 }
@@ -1423,6 +1465,7 @@ int nh_restore(nh_ctx* c, const double* n, const double* F, const double* u, con
     c->step = step;
     c->fields_set = true;
     c->snap_valid = false;
+    c->lbp_step = -1;
     NH_CUDA(c, cudaStreamSynchronize(st));
     return NH_OK;
 }
@@ -1449,6 +1492,10 @@ int nh_step(nh_ctx* c, int64_t n_lb_steps, void* stream)
             if (dt & 1) c->cur ^= 1;
             c->step += dt;
             left -= dt;
+            if (fold_ok(c)) {  // the block ends with a macro LB launch (an FD step)
+                c->lbp_step = c->step;
+                c->lbp_blocks = lb_blocks(c->lb_variant, c->N);
+            }
         } else {
             r = enqueue_one_step(c, left == 1, st);
             if (r) return r;
@@ -1559,6 +1606,7 @@ int nh_relax(nh_ctx* c, int64_t n_fd_steps, void* stream)
     if (n_fd_steps < 0) return fail(c, NH_EINVAL, "n_fd_steps must be >= 0");
     if ((r = set_device(c))) return r;
     cudaStream_t st = pick(c, stream);
+    c->lbp_step = -1;  // u is cleared
     NH_CUDA(c, cudaMemsetAsync(c->ws + c->L.u, 0, 3 * (size_t)c->N * real_size(c->p), st));
     if (c->fd_fused) {
         r = c->p.precision == NH_FP64 ? relax_fused<double>(c, n_fd_steps, st) : relax_fused<float>(c, n_fd_steps, st);
@@ -1580,6 +1628,7 @@ int nh_batch_relax(nh_ctx* const* ctxs, int count, int64_t n_fd_steps, void* str
     nh_ctx* c0 = ctxs[0];
     cudaStream_t st = pick(c0, stream);
     for (nh_ctx* c : plan->ctxs) {
+        c->lbp_step = -1;  // u is cleared
         cudaError_t e = cudaMemsetAsync(c->ws + c->L.u, 0, 3 * (size_t)c->N * real_size(c->p), st);
         if (e != cudaSuccess) return fail(nullptr, NH_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
     }
@@ -1639,6 +1688,7 @@ int nh_set_solid(nh_ctx* c, const uint8_t* mask, int on_device)
     if ((r = set_device(c))) return r;
     cudaStream_t st = c->stream;
     drop_graphs(c);
+    c->lbp_step = -1;
     if (!mask) {
         c->has_solid = false;
     } else {
@@ -1652,7 +1702,6 @@ int nh_set_solid(nh_ctx* c, const uint8_t* mask, int on_device)
         for (uint8_t b : host) fluid += b == 0;
         c->n_fluid = fluid;
         c->has_solid = true;
-        c->fd_fused = 0;  // obstacles run on the per-site FD kernels
     }
     if (c->fields_set) {  // the stress, and so the force, depend on the obstacles
         r = enqueue_force_any(c, st);
@@ -1783,6 +1832,16 @@ int nh_set_lb_variant(nh_ctx* c, int variant)
     return NH_OK;
 }
 
+int nh_set_diag_fold(nh_ctx* c, int on)
+{
+    if (!c) return fail(nullptr, NH_EINVAL, "ctx is NULL");
+    if (on != 0 && on != 1) return fail(c, NH_EINVAL, "diag fold must be 0 or 1");
+    if (on != c->diag_fold) drop_graphs(c);  // the captured LB launches change
+    c->diag_fold = on;
+    c->lbp_step = -1;
+    return NH_OK;
+}
+
 int nh_set_wait_limit(nh_ctx* c, double seconds)
 {
     if (!c) return fail(nullptr, NH_EINVAL, "ctx is NULL");
@@ -1796,7 +1855,6 @@ int nh_set_fd_variant(nh_ctx* c, int fused)
     if (!c) return fail(nullptr, NH_EINVAL, "ctx is NULL");
     if (fused != 0 && fused != 1) return fail(c, NH_EINVAL, "FD variant must be 0 or 1");
     if (fused && c->p.frank3) return fail(c, NH_EINVAL, "the three-constant energy runs on the per-site FD kernels only");
-    if (fused && c->has_solid) return fail(c, NH_EINVAL, "obstacles run on the per-site FD kernels only");
     if (fused && (c->p.lap_wide || c->p.n_from_rate))
         return fail(c, NH_EINVAL, "lap_wide and n_from_rate run on the per-site FD kernels only");
     if (fused != c->fd_fused) drop_graphs(c);

@@ -303,7 +303,9 @@ __device__ __forceinline__ void load3(const Real* __restrict__ n, int N, int s, 
     out[2] = __ldg(n + 2 * N + s);
 }
 
-template <typename Real, typename Store, bool F3, bool Solid>
+// NOnly: the populations, u and rho were summed by the LB launch that wrote
+// them (lb.cu, a.lbpart); only the director is read here.
+template <typename Real, typename Store, bool F3, bool Solid, bool NOnly = false>
 __global__ void __launch_bounds__(DIAG_THREADS, (sizeof(Real) == 4 && !F3 && !Solid) ? 5 : 1)
     diag_kernel(const DiagArgs a)
 {
@@ -398,11 +400,15 @@ __global__ void __launch_bounds__(DIAG_THREADS, (sizeof(Real) == 4 && !F3 && !So
                 Real mx[3], my[3];
                 load3(n, N, colx + cols * z, mx);
                 load3(n, N, coly + cols * z, my);
-                Real fs = 0;
+                Real fs = 0, u0 = 0, u1 = 0, u2 = 0, r = 1;
+                if (!NOnly) {
 #pragma unroll
-                for (int i = 0; i < 19; ++i) fs += Codec<Store, Real>::load(f + (size_t)i * N + s, inv_scale);
-                const Real u0 = __ldg(u + s), u1 = __ldg(u + N + s), u2 = __ldg(u + 2 * N + s);
-                const Real r = __ldg(rho + s);
+                    for (int i = 0; i < 19; ++i) fs += Codec<Store, Real>::load(f + (size_t)i * N + s, inv_scale);
+                    u0 = __ldg(u + s);
+                    u1 = __ldg(u + N + s);
+                    u2 = __ldg(u + 2 * N + s);
+                    r = __ldg(rho + s);
+                }
                 // obstacles: sums over fluid sites, links with at least one fluid end
                 bool sol = false, solx = false, soly = false, solz = false;
                 if (Solid) {
@@ -437,7 +443,9 @@ __global__ void __launch_bounds__(DIAG_THREADS, (sizeof(Real) == 4 && !F3 && !So
                     max_u = max(max_u, umag);
                     min_nn = min(min_nn, nmag);
                     max_nn = max(max_nn, nmag);
-                    if (!isfinite(umag) || !isfinite(nmag) || !isfinite(r) || !isfinite(fs)) bad += 1;
+                    // a site counts once for a bad director and once for a bad u, rho or population sum
+                    bad += !isfinite(nmag) ? 1 : 0;
+                    if (!NOnly && (!isfinite(umag) || !isfinite(r) || !isfinite(fs))) bad += 1;
                     wsum += Real(0.5) * (Real(1) - c[2]);
                 }  // fluid site
                 if (F3) {
@@ -518,7 +526,7 @@ __device__ __forceinline__ void pop_pair(const __nv_bfloat16* p, float inv_scale
     b = __high2float(h) * inv_scale;
 }
 
-template <typename Real, typename Store>
+template <typename Real, typename Store, bool NOnly = false>
 __global__ void __launch_bounds__(DIAG_THREADS, sizeof(Real) == 4 ? 4 : 1) diag_pair_kernel(const DiagArgs a)
 {
     const Geom g = a.g;
@@ -600,16 +608,20 @@ __global__ void __launch_bounds__(DIAG_THREADS, sizeof(Real) == 4 ? 4 : 1) diag_
                 load3_pair(n, N, coly + cols * z, y0, y1);
                 load3(n, N, colx2 + cols * z, x2);
                 Real fs0 = 0, fs1 = 0;
+                Real ua[3] = {0, 0, 0}, ub[3] = {0, 0, 0};
+                typename Pair<Real>::T r;
+                r.x = r.y = Real(1);
+                if (!NOnly) {
 #pragma unroll
-                for (int i = 0; i < 19; ++i) {
-                    Real p0, p1;
-                    pop_pair(f + (size_t)i * N + s, inv_scale, p0, p1);
-                    fs0 += p0;
-                    fs1 += p1;
+                    for (int i = 0; i < 19; ++i) {
+                        Real p0, p1;
+                        pop_pair(f + (size_t)i * N + s, inv_scale, p0, p1);
+                        fs0 += p0;
+                        fs1 += p1;
+                    }
+                    load3_pair(u, N, s, ua, ub);
+                    r = __ldg(reinterpret_cast<const typename Pair<Real>::T*>(rho + s));
                 }
-                Real ua[3], ub[3];
-                load3_pair(u, N, s, ua, ub);
-                const typename Pair<Real>::T r = __ldg(reinterpret_cast<const typename Pair<Real>::T*>(rho + s));
                 Real e = link_energy(c0, c1, 0, K, q0);
                 e += link_energy(c0, y0, 1, K, q0);
                 e += link_energy(c0, n0, 2, K, q0);
@@ -626,8 +638,11 @@ __global__ void __launch_bounds__(DIAG_THREADS, sizeof(Real) == 4 ? 4 : 1) diag_
                 max_u = max(max_u, max(umag0, umag1));
                 min_nn = min(min_nn, min(nmag0, nmag1));
                 max_nn = max(max_nn, max(nmag0, nmag1));
-                if (!isfinite(umag0) || !isfinite(nmag0) || !isfinite(r.x) || !isfinite(fs0)) bad += 1;
-                if (!isfinite(umag1) || !isfinite(nmag1) || !isfinite(r.y) || !isfinite(fs1)) bad += 1;
+                bad += (!isfinite(nmag0) ? 1 : 0) + (!isfinite(nmag1) ? 1 : 0);
+                if (!NOnly) {
+                    if (!isfinite(umag0) || !isfinite(r.x) || !isfinite(fs0)) bad += 1;
+                    if (!isfinite(umag1) || !isfinite(r.y) || !isfinite(fs1)) bad += 1;
+                }
                 wsum0 += Real(0.5) * (Real(1) - c0[2]);
                 wsum1 += Real(0.5) * (Real(1) - c1[2]);
 #pragma unroll
@@ -659,9 +674,12 @@ __global__ void __launch_bounds__(DIAG_THREADS, sizeof(Real) == 4 ? 4 : 1) diag_
 // block partials (stored value-major, so the loads are contiguous), then a
 // fixed shared-memory tree combines the threads, so the result is
 // deterministic.  Spread over V blocks because FP64 throughput per SM is low.
+// With lbpart, the mass, max |u| and non-finite count also take the block
+// partials [3][lb_blocks] of the LB launch that wrote the state.
 constexpr int kFinalThreads = 256;
 __global__ void __launch_bounds__(kFinalThreads) diag_final_kernel(const double* __restrict__ partials,
-                                                                   double* __restrict__ result, int blocks, int V)
+                                                                   double* __restrict__ result, int blocks, int V,
+                                                                   const double* __restrict__ lbpart, int lb_blocks)
 {
     const int k = blockIdx.x;
     if (k >= V) return;
@@ -670,6 +688,13 @@ __global__ void __launch_bounds__(kFinalThreads) diag_final_kernel(const double*
     for (int b = threadIdx.x; b < blocks; b += kFinalThreads) {
         const double v = __ldg(partials + (size_t)k * blocks + b);
         acc = kind == 0 ? acc + v : (kind == 1 ? fmax(acc, v) : fmin(acc, v));
+    }
+    const int lk = k == 0 ? 0 : (k == 2 ? 1 : (k == 5 ? 2 : -1));  // mass, max |u|, non-finite
+    if (lbpart != nullptr && lk >= 0) {
+        for (int b = threadIdx.x; b < lb_blocks; b += kFinalThreads) {
+            const double v = __ldg(lbpart + (size_t)lk * lb_blocks + b);
+            acc = kind == 0 ? acc + v : fmax(acc, v);
+        }
     }
     __shared__ double sh[kFinalThreads];
     sh[threadIdx.x] = acc;
@@ -879,6 +904,13 @@ inline bool diag_pairs(const DiagArgs& a)
 
 void launch_diag_pair_kernel(const DiagArgs& a, int blocks, cudaStream_t st)
 {
+    if (a.lbpart != nullptr) {  // the LB launch summed the populations, u and rho (F32 / F64 stores)
+        if (a.precision == NH_FP64)
+            diag_pair_kernel<double, double, true><<<blocks, DIAG_THREADS, 0, st>>>(a);
+        else
+            diag_pair_kernel<float, float, true><<<blocks, DIAG_THREADS, 0, st>>>(a);
+        return;
+    }
     if (a.precision == NH_FP64) {
         diag_pair_kernel<double, double><<<blocks, DIAG_THREADS, 0, st>>>(a);
         return;
@@ -893,6 +925,19 @@ void launch_diag_pair_kernel(const DiagArgs& a, int blocks, cudaStream_t st)
 template <bool Solid>
 void launch_diag_kernel(const DiagArgs& a, int blocks, cudaStream_t st)
 {
+    if (!Solid && a.lbpart != nullptr) {  // the LB launch summed the populations, u and rho (F32 / F64 stores)
+        if (a.precision == NH_FP64) {
+            if (a.frank3)
+                diag_kernel<double, double, true, false, true><<<blocks, DIAG_THREADS, 0, st>>>(a);
+            else
+                diag_kernel<double, double, false, false, true><<<blocks, DIAG_THREADS, 0, st>>>(a);
+        } else if (a.frank3) {
+            diag_kernel<float, float, true, false, true><<<blocks, DIAG_THREADS, 0, st>>>(a);
+        } else {
+            diag_kernel<float, float, false, false, true><<<blocks, DIAG_THREADS, 0, st>>>(a);
+        }
+        return;
+    }
     if (a.precision == NH_FP64) {
         if (a.frank3)
             diag_kernel<double, double, true, Solid><<<blocks, DIAG_THREADS, 0, st>>>(a);
@@ -915,6 +960,8 @@ void launch_diag_kernel(const DiagArgs& a, int blocks, cudaStream_t st)
 
 cudaError_t launch_diagnostics(const DiagArgs& a, cudaStream_t st)
 {
+    if (a.lbpart != nullptr && (a.solid != nullptr || (a.storage != NH_STORE_F32 && a.storage != NH_STORE_F64)))
+        return cudaErrorInvalidValue;
     const bool pairs = diag_pairs(a);
     const int items = pairs ? (a.g.nx / 2) * a.g.ny * ((a.g.nz + kDiagPairChunk - 1) / kDiagPairChunk)
                             : a.g.nx * a.g.ny * ((a.g.nz + kDiagChunk - 1) / kDiagChunk);
@@ -929,8 +976,8 @@ cudaError_t launch_diagnostics(const DiagArgs& a, cudaStream_t st)
         launch_diag_kernel<false>(a, blocks, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    diag_final_kernel<<<diag_num_values(a.n_tubes), kFinalThreads, 0, st>>>(a.partials, a.result, blocks,
-                                                                           diag_num_values(a.n_tubes));
+    diag_final_kernel<<<diag_num_values(a.n_tubes), kFinalThreads, 0, st>>>(
+        a.partials, a.result, blocks, diag_num_values(a.n_tubes), a.lbpart, a.lbp_blocks);
     return cudaGetLastError();
 }
 

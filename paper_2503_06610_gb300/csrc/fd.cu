@@ -548,10 +548,11 @@ __device__ __forceinline__ void fd_stage_site(const FDChan<Real>& c, int s)
         stress_site(c, s);
     else if (Stage == 3)
         force_site(c, s);
-    else if (Stage == 4)
-        frank3_p_site(c, c.n, s);
-    else
-        frank3_p_site(c, c.nP, s);
+    else if (Stage == 4) {
+        if (c.P3 != nullptr) frank3_p_site(c, c.n, s);  // a batch may mix one- and three-constant channels
+    } else {
+        if (c.P3 != nullptr) frank3_p_site(c, c.nP, s);
+    }
 }
 
 template <typename Real, int Stage>
@@ -582,7 +583,7 @@ __global__ void __launch_bounds__(256) fd_batch_kernel(const FDBatch<Real> b)
 
 // ------------------------------------------------------------------ fused 2.5D kernels
 //
-// A block owns a tile of kTX x kTY columns and marches up a chunk of kZC
+// A block owns a tile of kTX x kTY columns and marches up a chunk of kZC (or fewer, fused_zchunk)
 // layers.  Planes of n and u with a 2-site halo in x and y sit in a ring of
 // three shared-memory slots; the predictor (kernel A) or the stress (kernel
 // B) is evaluated on each plane with a 1-site halo, so every stencil reads
@@ -595,6 +596,18 @@ __global__ void __launch_bounds__(256) fd_batch_kernel(const FDBatch<Real> b)
 //   kernel B: n_new, u -> F   (stress, divergence; sigma never leaves the SM)
 
 constexpr int kTX = 32, kTY = 8, kZC = 16;
+
+// Layers per chunk: kZC, fewer when the channel has too few tiles to fill the
+// GPU (a small channel would otherwise run on a handful of blocks): aim at two
+// blocks per SM of GB300's 152, down to one layer per chunk (each chunk also
+// evaluates the predictor or the stress on the layer below and above it).
+constexpr int kFusedTargetBlocks = 2 * 152;
+__host__ __device__ __forceinline__ int fused_zchunk(const Geom& g)
+{
+    const int txy = ((g.nx + kTX - 1) / kTX) * ((g.ny + kTY - 1) / kTY);
+    const int c = (g.nz * txy) / kFusedTargetBlocks;
+    return c < 1 ? 1 : (c > kZC ? kZC : c);
+}
 constexpr int kHX2 = kTX + 4, kHY2 = kTY + 4, kP2 = kHX2 * kHY2;  // plane with a 2-site halo
 constexpr int kHX1 = kTX + 2, kHY1 = kTY + 2, kP1 = kHX1 * kHY1;  // plane with a 1-site halo
 constexpr int kFusedThreads = 256;
@@ -606,10 +619,13 @@ __device__ __forceinline__ int wrapm(int a, int n)
 }
 __device__ __forceinline__ int slot3(int p) { return ((p % 3) + 3) % 3; }
 
+// Obstacle masks of the three input planes (kP2 bytes each) follow the Real
+// arrays; only the kernels of channels with obstacles use them.
+constexpr int kMaskBytes = (3 * kP2 + 15) / 16 * 16;
 template <typename Real>
-size_t fused_a_smem() { return (size_t)(3 * 6 * kP2 + 3 * 4 * kP1) * sizeof(Real); }
+size_t fused_a_smem() { return (size_t)(3 * 6 * kP2 + 3 * 4 * kP1) * sizeof(Real) + kMaskBytes; }
 template <typename Real>
-size_t fused_b_smem() { return (size_t)(3 * 6 * kP2 + 2 * 8 * kP1) * sizeof(Real); }
+size_t fused_b_smem() { return (size_t)(3 * 6 * kP2 + 2 * 8 * kP1) * sizeof(Real) + kMaskBytes; }
 
 // Each thread owns at most kPts points of a P2 plane (indices threadIdx.x +
 // k * blockDim.x); their wrapped x-y site offsets are computed once per tile.
@@ -636,10 +652,14 @@ __device__ __forceinline__ PlaneMap plane_map(const Geom& g, int x0, int y0)
 }
 
 // Plane zp of n (ghost reading) and u (zero beyond the plates), fetched into
-// registers: v[k][0..2] = n, v[k][3..5] = u of the thread's k-th point.
-template <typename Real>
+// registers: v[k][0..2] = n, v[k][3..5] = u of the thread's k-th point.  With
+// obstacles (Solid) also the mask of each point, sv[k], and u = 0 at solid
+// nodes (no-slip); ghost planes hold no solid nodes.
+template <typename Real, bool Solid = false>
 __device__ __forceinline__ void prefetch_plane(const Real* __restrict__ n, const Real* __restrict__ u, const Geom& g,
-                                               const PlaneMap& m, int zp, Real v[kPts][6])
+                                               const PlaneMap& m, int zp, Real v[kPts][6],
+                                               const unsigned char* __restrict__ solid = nullptr,
+                                               unsigned char* sv = nullptr)
 {
     bool ghost = false;
     int zz;
@@ -658,10 +678,15 @@ __device__ __forceinline__ void prefetch_plane(const Real* __restrict__ n, const
     for (int k = 0; k < kPts; ++k) {
         if (m.off[k] < 0) continue;
         const int s = m.off[k];
+        bool sol = false;
+        if constexpr (Solid) {
+            sol = !ghost && solid != nullptr && solid[zoff + s] != 0;  // a batch may mix masked and unmasked channels
+            sv[k] = sol ? 1 : 0;
+        }
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             v[k][a] = fixed_dir ? Real(a == 2 ? 1 : 0) : nz[a * N + s];
-            v[k][3 + a] = ghost ? Real(0) : uz[a * N + s];
+            v[k][3 + a] = (ghost || sol) ? Real(0) : uz[a * N + s];
         }
     }
 }
@@ -718,13 +743,15 @@ __device__ __forceinline__ void st3(double* slot, int i, const double v[3])
     for (int a = 0; a < 3; ++a) slot[a * kP1 + i] = v[a];
 }
 
-template <typename Real>
-__device__ __forceinline__ void commit_plane(const PlaneMap& m, const Real v[kPts][6], Real* slot)
+template <typename Real, bool Solid = false>
+__device__ __forceinline__ void commit_plane(const PlaneMap& m, const Real v[kPts][6], Real* slot,
+                                             const unsigned char* sv = nullptr, unsigned char* mslot = nullptr)
 {
 #pragma unroll
     for (int k = 0; k < kPts; ++k) {
         if (m.off[k] < 0) continue;
         st_pt(slot, threadIdx.x + k * blockDim.x, v[k]);
+        if constexpr (Solid) mslot[threadIdx.x + k * blockDim.x] = sv[k];
     }
 }
 
@@ -802,9 +829,17 @@ __device__ __forceinline__ HaloPoint halo_point()
 // hi): n^P into pslot[i1], the rate into r.
 template <typename Real>
 __device__ __forceinline__ void predict_point(const FDPar<Real>& par, const Real* lo, const Real* mid, const Real* hi,
-                                              int i1, int i2, Real* pslot, Real r[3], int side)
+                                              int i1, int i2, Real* pslot, Real r[3], int side,
+                                              const unsigned char* mmid = nullptr)
 {
     Real nn[7][3], uu[7][3], np[3];
+    if (mmid != nullptr && mmid[i2]) {  // obstacle: the director is held
+        Real u0[3];
+        split_pt(mid, i2, np, u0);
+        r[0] = r[1] = r[2] = Real(0);
+        st3(pslot, i1, np);
+        return;
+    }
     gather_slots(lo, mid, hi, i2, nn, uu);
     director_rate(nn, uu, par, r, (const Real*)nullptr, side);
 #pragma unroll
@@ -823,29 +858,31 @@ __device__ __forceinline__ void predict_point(const FDPar<Real>& par, const Real
 template <typename Real>
 __device__ __forceinline__ void predict_plane(const FDPar<Real>& par, const Real* lo, const Real* mid, const Real* hi,
                                               Real* pslot, int i1, int i2, const HaloPoint& hp, bool halo, Real rown[3],
-                                              int side)
+                                              int side, const unsigned char* mmid = nullptr)
 {
-    predict_point(par, lo, mid, hi, i1, i2, pslot, rown, side);
+    predict_point(par, lo, mid, hi, i1, i2, pslot, rown, side, mmid);
     if (halo && hp.has) {
         Real r[3];
-        predict_point(par, lo, mid, hi, hp.i1, hp.i2, pslot, r, side);
+        predict_point(par, lo, mid, hi, hp.i1, hp.i2, pslot, r, side, mmid);
     }
 }
 
 // Ring slots: plane p of the input ring (6 kP2 Reals) and of the predictor
 // ring (4 kP1 Reals) sits in slot slot3(p); the kernels rotate three slot
 // indices (planes z - 1, z, z + 1) instead of recomputing them.
-template <typename Real>
+template <typename Real, bool Solid = false>
 __device__ void fused_a_tile(const FDChan<Real>& c, const Real* __restrict__ nin, Real* __restrict__ nout, int tile)
 {
     extern __shared__ __align__(16) unsigned char smem_fd[];
     Real* in = reinterpret_cast<Real*>(smem_fd);  // 3 slots x 6 x kP2 (input planes)
     Real* pr = in + 3 * 6 * kP2;                  // 3 slots x 4 x kP1 (predictor n^P)
+    unsigned char* mk = reinterpret_cast<unsigned char*>(pr + 3 * 4 * kP1);  // 3 slots x kP2 obstacle masks
     const Geom& g = c.g;
     const int ntx = (g.nx + kTX - 1) / kTX, nty = (g.ny + kTY - 1) / kTY;
     const int tx_t = tile % ntx, ty_t = (tile / ntx) % nty, zc = tile / (ntx * nty);
     const int x0 = tx_t * kTX, y0 = ty_t * kTY;
-    const int zb = zc * kZC, ze = min(zb + kZC, g.nz);
+    const int zch = fused_zchunk(g);
+    const int zb = zc * zch, ze = min(zb + zch, g.nz);
     const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
     const bool active = threadIdx.x < kTX * kTY && x0 + tx < g.nx && y0 + ty < g.ny;
     const int N = g.N;
@@ -855,37 +892,42 @@ __device__ void fused_a_tile(const FDChan<Real>& c, const Real* __restrict__ nin
     const PlaneMap pm = plane_map(g, x0, y0);
     const bool homeo = g.anchoring == NH_ANCHOR_HOMEOTROPIC;
     auto IN = [&](int sl) { return in + sl * (6 * kP2); };
+    auto MK = [&](int sl) -> const unsigned char* { return Solid ? mk + sl * kP2 : nullptr; };
+    unsigned char sv[kPts];
     auto PR = [&](int sl) { return pr + sl * (4 * kP1); };
     const int s0 = slot3(zb - 2), s1 = slot3(zb - 1), s2 = slot3(zb);
     Real v[kPts][6];
-    prefetch_plane(nin, c.u, g, pm, zb - 2, v);
-    commit_plane(pm, v, IN(s0));
-    prefetch_plane(nin, c.u, g, pm, zb - 1, v);
-    commit_plane(pm, v, IN(s1));
-    prefetch_plane(nin, c.u, g, pm, zb, v);
-    commit_plane(pm, v, IN(s2));
-    prefetch_plane(nin, c.u, g, pm, zb + 1, v);  // in flight during the first predictor plane
+    prefetch_plane<Real, Solid>(nin, c.u, g, pm, zb - 2, v, c.solid, sv);
+    commit_plane<Real, Solid>(pm, v, IN(s0), sv, mk + s0 * kP2);
+    prefetch_plane<Real, Solid>(nin, c.u, g, pm, zb - 1, v, c.solid, sv);
+    commit_plane<Real, Solid>(pm, v, IN(s1), sv, mk + s1 * kP2);
+    prefetch_plane<Real, Solid>(nin, c.u, g, pm, zb, v, c.solid, sv);
+    commit_plane<Real, Solid>(pm, v, IN(s2), sv, mk + s2 * kP2);
+    prefetch_plane<Real, Solid>(nin, c.u, g, pm, zb + 1, v, c.solid, sv);  // in flight during the first predictor plane
     __syncthreads();
     Real rcur[3] = {0, 0, 0}, rnext[3] = {0, 0, 0};  // predictor rate at the own point, planes z and z + 1
     if (!is_ghost_plane(g, zb - 1))
-        predict_plane(c.p, IN(s0), IN(s1), IN(s2), PR(s1), i1, i2, hp, false, rnext, free_plate_side(g, zb - 1));
+        predict_plane(c.p, IN(s0), IN(s1), IN(s2), PR(s1), i1, i2, hp, false, rnext, free_plate_side(g, zb - 1),
+                      MK(s1));
     // u one layer below the corrector's plane, at the thread's own point, carried in registers
     Real ulo[3], nc[3];
     split_pt(IN(s1), i2, nc, ulo);
     __syncthreads();  // plane zb - 2 is no longer read
-    commit_plane(pm, v, IN(s0));  // plane zb + 1
-    prefetch_plane(nin, c.u, g, pm, zb + 2, v);
+    commit_plane<Real, Solid>(pm, v, IN(s0), sv, mk + s0 * kP2);  // plane zb + 1
+    prefetch_plane<Real, Solid>(nin, c.u, g, pm, zb + 2, v, c.solid, sv);
     __syncthreads();
     if (!is_ghost_plane(g, zb))
-        predict_plane(c.p, IN(s1), IN(s2), IN(s0), PR(s2), i1, i2, hp, true, rcur, free_plate_side(g, zb));
+        predict_plane(c.p, IN(s1), IN(s2), IN(s0), PR(s2), i1, i2, hp, true, rcur, free_plate_side(g, zb),
+                      MK(s2));
     int sa = s1, sb = s2, sc = s0;  // slots of planes z - 1, z, z + 1 (plane z + 2 takes sa)
     for (int z = zb; z < ze; ++z) {
         __syncthreads();  // plane z - 1 is no longer read; its slot takes plane z + 2
-        commit_plane(pm, v, IN(sa));
+        commit_plane<Real, Solid>(pm, v, IN(sa), sv, mk + sa * kP2);
         __syncthreads();
-        if (z + 1 < ze) prefetch_plane(nin, c.u, g, pm, z + 3, v);  // overlaps the two evaluations below
+        if (z + 1 < ze) prefetch_plane<Real, Solid>(nin, c.u, g, pm, z + 3, v, c.solid, sv);  // overlaps the two evaluations below
         if (!is_ghost_plane(g, z + 1))
-            predict_plane(c.p, IN(sb), IN(sc), IN(sa), PR(sc), i1, i2, hp, z + 1 < ze, rnext, free_plate_side(g, z + 1));
+            predict_plane(c.p, IN(sb), IN(sc), IN(sa), PR(sc), i1, i2, hp, z + 1 < ze, rnext, free_plate_side(g, z + 1),
+                          MK(sc));
         __syncthreads();
         if (active) {
             const Real* mid = PR(sb);
@@ -923,7 +965,12 @@ __device__ void fused_a_tile(const FDChan<Real>& c, const Real* __restrict__ nin
             Real nw[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) nw[a] = n0[a] + c.p.dt * Real(0.5) * (rcur[a] + r[a]);
-            const Real inv = Real(1) / sqrt(nw[0] * nw[0] + nw[1] * nw[1] + nw[2] * nw[2]);
+            Real inv = Real(1) / sqrt(nw[0] * nw[0] + nw[1] * nw[1] + nw[2] * nw[2]);
+            if (Solid && MK(sb)[i2]) {  // obstacle: the director is held
+#pragma unroll
+                for (int a = 0; a < 3; ++a) nw[a] = n0[a];
+                inv = Real(1);
+            }
             const int s = (x0 + tx) + g.nx * ((y0 + ty) + g.ny * z);
 #pragma unroll
             for (int a = 0; a < 3; ++a) nout[a * N + s] = nw[a] * inv;
@@ -947,11 +994,17 @@ __device__ void fused_a_tile(const FDChan<Real>& c, const Real* __restrict__ nin
 // that owns the point (szown).
 template <typename Real>
 __device__ __forceinline__ void stress_point_plane(const FDPar<Real>& par, const Real* lo, const Real* mid,
-                                                   const Real* hi, int i1, int i2, Real* slot, Real sz[3], int side)
+                                                   const Real* hi, int i1, int i2, Real* slot, Real sz[3], int side,
+                                                   const unsigned char* mmid = nullptr)
 {
     Real nn[7][3], uu[7][3], sig[9];
-    gather_slots(lo, mid, hi, i2, nn, uu);
-    stress_point(nn, uu, par, sig, (const Real*)nullptr, (const Real*)nullptr, side);
+    if (mmid != nullptr && mmid[i2]) {  // obstacle: zero stress
+#pragma unroll
+        for (int k = 0; k < 9; ++k) sig[k] = Real(0);
+    } else {
+        gather_slots(lo, mid, hi, i2, nn, uu);
+        stress_point(nn, uu, par, sig, (const Real*)nullptr, (const Real*)nullptr, side);
+    }
     const Real sx[3] = {sig[0], sig[3], sig[6]}, sy[3] = {sig[1], sig[4], sig[7]};
     st3(slot, i1, sx);
     st3(slot + 4 * kP1, i1, sy);
@@ -965,7 +1018,8 @@ __device__ __forceinline__ void stress_point_plane(const FDPar<Real>& par, const
 // chunk give only sigma_az: halo = false).
 template <typename Real>
 __device__ __forceinline__ void stress_plane(const FDChan<Real>& c, int p, const Real* lo, const Real* mid,
-                                             const Real* hi, Real* slot, int i1, int i2, bool halo, Real szown[3])
+                                             const Real* hi, Real* slot, int i1, int i2, bool halo, Real szown[3],
+                                             const unsigned char* mmid = nullptr)
 {
     if (is_ghost_plane(c.g, p)) {
 #pragma unroll
@@ -973,25 +1027,27 @@ __device__ __forceinline__ void stress_plane(const FDChan<Real>& c, int p, const
         return;
     }
     const int side = free_plate_side(c.g, p);
-    stress_point_plane(c.p, lo, mid, hi, i1, i2, slot, szown, side);
+    stress_point_plane(c.p, lo, mid, hi, i1, i2, slot, szown, side, mmid);
     const HaloPoint hp = halo_point();  // recomputed here: kernel B runs at the register limit
     if (halo && hp.has) {
         Real sz[3];
-        stress_point_plane(c.p, lo, mid, hi, hp.i1, hp.i2, slot, sz, side);
+        stress_point_plane(c.p, lo, mid, hi, hp.i1, hp.i2, slot, sz, side, mmid);
     }
 }
 
-template <typename Real>
+template <typename Real, bool Solid = false>
 __device__ void fused_b_tile(const FDChan<Real>& c, const Real* __restrict__ nin, Real* __restrict__ ncopy, int tile)
 {
     extern __shared__ __align__(16) unsigned char smem_fd[];
     Real* in = reinterpret_cast<Real*>(smem_fd);  // 3 slots x 6 x kP2 (input planes)
     Real* sg = in + 3 * 6 * kP2;                  // 2 slots x 8 x kP1 (sigma_.x, sigma_.y), slot z & 1
+    unsigned char* mk = reinterpret_cast<unsigned char*>(sg + 2 * 8 * kP1);  // 3 slots x kP2 obstacle masks
     const Geom& g = c.g;
     const int ntx = (g.nx + kTX - 1) / kTX, nty = (g.ny + kTY - 1) / kTY;
     const int tx_t = tile % ntx, ty_t = (tile / ntx) % nty, zc = tile / (ntx * nty);
     const int x0 = tx_t * kTX, y0 = ty_t * kTY;
-    const int zb = zc * kZC, ze = min(zb + kZC, g.nz);
+    const int zch = fused_zchunk(g);
+    const int zb = zc * zch, ze = min(zb + zch, g.nz);
     const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
     const bool active = threadIdx.x < kTX * kTY && x0 + tx < g.nx && y0 + ty < g.ny;
     const int N = g.N;
@@ -999,31 +1055,33 @@ __device__ void fused_b_tile(const FDChan<Real>& c, const Real* __restrict__ nin
     const int i2 = (tx + 2) + kHX2 * (ty + 2);
     const PlaneMap pm = plane_map(g, x0, y0);
     auto IN = [&](int sl) { return in + sl * (6 * kP2); };
+    auto MK = [&](int sl) -> const unsigned char* { return Solid ? mk + sl * kP2 : nullptr; };
+    unsigned char sv[kPts];
     auto SG = [&](int p) { return sg + (p & 1) * (8 * kP1); };
     const int s0 = slot3(zb - 2), s1 = slot3(zb - 1), s2 = slot3(zb);
     Real v[kPts][6];
-    prefetch_plane(nin, c.u, g, pm, zb - 2, v);
-    commit_plane(pm, v, IN(s0));
-    prefetch_plane(nin, c.u, g, pm, zb - 1, v);
-    commit_plane(pm, v, IN(s1));
-    prefetch_plane(nin, c.u, g, pm, zb, v);
-    commit_plane(pm, v, IN(s2));
-    prefetch_plane(nin, c.u, g, pm, zb + 1, v);  // in flight during the first stress plane
+    prefetch_plane<Real, Solid>(nin, c.u, g, pm, zb - 2, v, c.solid, sv);
+    commit_plane<Real, Solid>(pm, v, IN(s0), sv, mk + s0 * kP2);
+    prefetch_plane<Real, Solid>(nin, c.u, g, pm, zb - 1, v, c.solid, sv);
+    commit_plane<Real, Solid>(pm, v, IN(s1), sv, mk + s1 * kP2);
+    prefetch_plane<Real, Solid>(nin, c.u, g, pm, zb, v, c.solid, sv);
+    commit_plane<Real, Solid>(pm, v, IN(s2), sv, mk + s2 * kP2);
+    prefetch_plane<Real, Solid>(nin, c.u, g, pm, zb + 1, v, c.solid, sv);  // in flight during the first stress plane
     __syncthreads();
     Real szlo[3], szmid[3], szhi[3];  // sigma_az at the own point, planes z - 1, z, z + 1
-    stress_plane(c, zb - 1, IN(s0), IN(s1), IN(s2), SG(zb - 1), i1, i2, false, szlo);
+    stress_plane(c, zb - 1, IN(s0), IN(s1), IN(s2), SG(zb - 1), i1, i2, false, szlo, MK(s1));
     __syncthreads();  // plane zb - 2 is no longer read
-    commit_plane(pm, v, IN(s0));  // plane zb + 1
-    prefetch_plane(nin, c.u, g, pm, zb + 2, v);
+    commit_plane<Real, Solid>(pm, v, IN(s0), sv, mk + s0 * kP2);  // plane zb + 1
+    prefetch_plane<Real, Solid>(nin, c.u, g, pm, zb + 2, v, c.solid, sv);
     __syncthreads();
-    stress_plane(c, zb, IN(s1), IN(s2), IN(s0), SG(zb), i1, i2, true, szmid);
+    stress_plane(c, zb, IN(s1), IN(s2), IN(s0), SG(zb), i1, i2, true, szmid, MK(s2));
     int sa = s1, sb = s2, sc = s0;  // input slots of planes z - 1, z, z + 1 (plane z + 2 takes sa)
     for (int z = zb; z < ze; ++z) {
         __syncthreads();  // plane z - 1 is no longer read; its slots take planes z + 2 (input), z + 1 (sigma)
-        commit_plane(pm, v, IN(sa));
+        commit_plane<Real, Solid>(pm, v, IN(sa), sv, mk + sa * kP2);
         __syncthreads();
-        if (z + 1 < ze) prefetch_plane(nin, c.u, g, pm, z + 3, v);
-        stress_plane(c, z + 1, IN(sb), IN(sc), IN(sa), SG(z + 1), i1, i2, z + 1 < ze, szhi);
+        if (z + 1 < ze) prefetch_plane<Real, Solid>(nin, c.u, g, pm, z + 3, v, c.solid, sv);
+        stress_plane(c, z + 1, IN(sb), IN(sc), IN(sa), SG(z + 1), i1, i2, z + 1 < ze, szhi, MK(sc));
         __syncthreads();
         if (active) {
             const Real* sx = SG(z);
@@ -1039,7 +1097,8 @@ __device__ void fused_b_tile(const FDChan<Real>& c, const Real* __restrict__ nin
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const Real hi = mhi ? szmid[a] : szhi[a], lo = mlo ? szmid[a] : szlo[a];
-                c.F[a * N + s] = Real(0.5) * ((xp[a] - xm[a]) + (yp[a] - ym[a]) + (hi - lo));
+                c.F[a * N + s] = (Solid && MK(sb)[i2]) ? Real(0)  // no force on an obstacle node
+                                                        : Real(0.5) * ((xp[a] - xm[a]) + (yp[a] - ym[a]) + (hi - lo));
             }
             if (ncopy) {
                 Real n0[3], u0[3];
@@ -1060,22 +1119,24 @@ __device__ void fused_b_tile(const FDChan<Real>& c, const Real* __restrict__ nin
     }
 }
 
-template <typename Real>
+// Solid: the channel has obstacles (held directors, no-slip, zero stress and
+// force at solid nodes, as the per-site kernels).
+template <typename Real, bool Solid>
 __global__ void __launch_bounds__(kFusedThreads, sizeof(Real) == 4 ? 4 : 2) fused_a_kernel(const FDChan<Real> c, const Real* nin, Real* nout)
 {
-    fused_a_tile(c, nin, nout, blockIdx.x);
+    fused_a_tile<Real, Solid>(c, nin, nout, blockIdx.x);
 }
 
-template <typename Real>
+template <typename Real, bool Solid>
 __global__ void __launch_bounds__(kFusedThreads, sizeof(Real) == 4 ? 4 : 2) fused_b_kernel(const FDChan<Real> c, const Real* nin, Real* ncopy)
 {
-    fused_b_tile(c, nin, ncopy, blockIdx.x);
+    fused_b_tile<Real, Solid>(c, nin, ncopy, blockIdx.x);
 }
 
 // Batched fused kernels: a persistent grid walks the (channel, tile) work
 // list; stage 0 = kernel A (n -> nP), 1 = kernel B (nP -> F, copy into n),
 // 2 = kernel A (nP -> n), for relaxations that alternate the two buffers.
-template <typename Real, int Stage>
+template <typename Real, int Stage, bool Solid>
 __global__ void __launch_bounds__(kFusedThreads, sizeof(Real) == 4 ? 3 : 2) fused_batch_kernel(const FDBatch<Real> b)
 {
     const int total = b.prefix[b.count];
@@ -1090,18 +1151,19 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(Real) == 4 ? 3 : 2) fuse
         }
         const FDChan<Real>& c = b.ch[lo];
         if (Stage == 0)
-            fused_a_tile(c, c.n, c.nP, t - b.prefix[lo]);
+            fused_a_tile<Real, Solid>(c, c.n, c.nP, t - b.prefix[lo]);
         else if (Stage == 1)
-            fused_b_tile(c, c.nP, c.n, t - b.prefix[lo]);
+            fused_b_tile<Real, Solid>(c, c.nP, c.n, t - b.prefix[lo]);
         else
-            fused_a_tile(c, c.nP, c.n, t - b.prefix[lo]);
+            fused_a_tile<Real, Solid>(c, c.nP, c.n, t - b.prefix[lo]);
         __syncthreads();
     }
 }
 
 inline int fused_tiles(const Geom& g)
 {
-    return ((g.nx + kTX - 1) / kTX) * ((g.ny + kTY - 1) / kTY) * ((g.nz + kZC - 1) / kZC);
+    const int zch = fused_zchunk(g);
+    return ((g.nx + kTX - 1) / kTX) * ((g.ny + kTY - 1) / kTY) * ((g.nz + zch - 1) / zch);
 }
 
 template <typename Real>
@@ -1110,14 +1172,17 @@ cudaError_t prepare_fused()
     static bool done = false;  // the attribute is per function; setting it twice is harmless
     if (done) return cudaSuccess;
     const int a = (int)fused_a_smem<Real>(), b = (int)fused_b_smem<Real>();
-    cudaError_t e = cudaFuncSetAttribute(fused_a_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, a);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(fused_b_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
-        const int bytes = k == 1 ? b : a;
-        if (k == 0) e = cudaFuncSetAttribute(fused_batch_kernel<Real, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (k == 1) e = cudaFuncSetAttribute(fused_batch_kernel<Real, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (k == 2) e = cudaFuncSetAttribute(fused_batch_kernel<Real, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    }
+    const cudaFuncAttribute attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(fused_a_kernel<Real, false>, attr, a);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fused_a_kernel<Real, true>, attr, a);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fused_b_kernel<Real, false>, attr, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fused_b_kernel<Real, true>, attr, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fused_batch_kernel<Real, 0, false>, attr, a);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fused_batch_kernel<Real, 0, true>, attr, a);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fused_batch_kernel<Real, 1, false>, attr, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fused_batch_kernel<Real, 1, true>, attr, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fused_batch_kernel<Real, 2, false>, attr, a);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fused_batch_kernel<Real, 2, true>, attr, a);
     if (e == cudaSuccess) done = true;
     return e;
 }
@@ -1137,7 +1202,10 @@ cudaError_t launch_fd_batch(FDBatch<Real>& b, int stage, int grid, cudaStream_t 
     case 0: fd_batch_kernel<Real, 0><<<blocks, 256, 0, st>>>(b); break;
     case 1: fd_batch_kernel<Real, 1><<<blocks, 256, 0, st>>>(b); break;
     case 2: fd_batch_kernel<Real, 2><<<blocks, 256, 0, st>>>(b); break;
-    default: fd_batch_kernel<Real, 3><<<blocks, 256, 0, st>>>(b); break;
+    case 3: fd_batch_kernel<Real, 3><<<blocks, 256, 0, st>>>(b); break;
+    case 4: fd_batch_kernel<Real, 4><<<blocks, 256, 0, st>>>(b); break;  // three-constant P stage from n
+    case 5: fd_batch_kernel<Real, 5><<<blocks, 256, 0, st>>>(b); break;  // ... and from n^P
+    default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
@@ -1184,7 +1252,10 @@ cudaError_t launch_fd_fused_a(const FDChan<Real>& c, const Real* nin, Real* nout
 {
     cudaError_t e = prepare_fused<Real>();
     if (e != cudaSuccess) return e;
-    fused_a_kernel<Real><<<fused_tiles(c.g), kFusedThreads, fused_a_smem<Real>(), st>>>(c, nin, nout);
+    if (c.solid != nullptr)
+        fused_a_kernel<Real, true><<<fused_tiles(c.g), kFusedThreads, fused_a_smem<Real>(), st>>>(c, nin, nout);
+    else
+        fused_a_kernel<Real, false><<<fused_tiles(c.g), kFusedThreads, fused_a_smem<Real>(), st>>>(c, nin, nout);
     return cudaGetLastError();
 }
 
@@ -1193,7 +1264,10 @@ cudaError_t launch_fd_fused_b(const FDChan<Real>& c, const Real* nin, Real* ncop
 {
     cudaError_t e = prepare_fused<Real>();
     if (e != cudaSuccess) return e;
-    fused_b_kernel<Real><<<fused_tiles(c.g), kFusedThreads, fused_b_smem<Real>(), st>>>(c, nin, ncopy);
+    if (c.solid != nullptr)
+        fused_b_kernel<Real, true><<<fused_tiles(c.g), kFusedThreads, fused_b_smem<Real>(), st>>>(c, nin, ncopy);
+    else
+        fused_b_kernel<Real, false><<<fused_tiles(c.g), kFusedThreads, fused_b_smem<Real>(), st>>>(c, nin, ncopy);
     return cudaGetLastError();
 }
 
@@ -1207,10 +1281,20 @@ cudaError_t launch_fd_fused_batch(FDBatch<Real>& b, int stage, int grid, cudaStr
     for (int k = 0; k < b.count; ++k) b.prefix[k + 1] = b.prefix[k] + fused_tiles(b.ch[k].g);
     const int blocks = grid < b.prefix[b.count] ? grid : b.prefix[b.count];
     const size_t smem = stage == 1 ? fused_b_smem<Real>() : fused_a_smem<Real>();
-    switch (stage) {
-    case 0: fused_batch_kernel<Real, 0><<<blocks, kFusedThreads, smem, st>>>(b); break;
-    case 1: fused_batch_kernel<Real, 1><<<blocks, kFusedThreads, smem, st>>>(b); break;
-    default: fused_batch_kernel<Real, 2><<<blocks, kFusedThreads, smem, st>>>(b); break;
+    bool solid = false;
+    for (int k = 0; k < b.count; ++k) solid = solid || b.ch[k].solid != nullptr;
+    if (solid) {
+        switch (stage) {
+        case 0: fused_batch_kernel<Real, 0, true><<<blocks, kFusedThreads, smem, st>>>(b); break;
+        case 1: fused_batch_kernel<Real, 1, true><<<blocks, kFusedThreads, smem, st>>>(b); break;
+        default: fused_batch_kernel<Real, 2, true><<<blocks, kFusedThreads, smem, st>>>(b); break;
+        }
+    } else {
+        switch (stage) {
+        case 0: fused_batch_kernel<Real, 0, false><<<blocks, kFusedThreads, smem, st>>>(b); break;
+        case 1: fused_batch_kernel<Real, 1, false><<<blocks, kFusedThreads, smem, st>>>(b); break;
+        default: fused_batch_kernel<Real, 2, false><<<blocks, kFusedThreads, smem, st>>>(b); break;
+        }
     }
     return cudaGetLastError();
 }

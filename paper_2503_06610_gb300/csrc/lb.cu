@@ -16,7 +16,10 @@
 // the other planes is served from L1/L2.  The relaxation uses the symmetry of
 // each pair (e_i, -e_i): the parts of f^eq and S_i that are even in e_i are
 // computed once per pair and the odd parts change sign.  u and rho are written
-// only on steps that feed an FD update (or end a call).
+// only on steps that feed an FD update (or end a call); such a launch can also
+// leave per-block partial sums for the diagnostics (mass, max |u|, non-finite
+// count), so that the diagnostics of that state need not read the
+// populations, u and rho again.
 #include <type_traits>
 
 #include "nh_internal.cuh"
@@ -154,18 +157,33 @@ __device__ __forceinline__ void store4(Store* p, const Real v[4], float scale)
     }
 }
 
+// Macro: 0 = populations only; 1 = also u and rho; 2 = also the diagnostics'
+// block partials c.part[k * ntiles + tile] of k = 0: sum of the stored
+// post-collision populations, 1: max |u|, 2: sites with a non-finite u, rho
+// or population sum (FP32 and FP64 stores).
+__device__ __forceinline__ double lb_warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // One tile (one thread block's worth of sites) of one channel.  `tile` is the
 // tile index within the channel and `ntiles` the channel's tile count (used by
 // the 16-bit scale controller to find the channel's last tile).  Solid: the
 // channel has obstacles (c.solid): a link whose source is a solid node
 // bounces back half-way like the plates, and a solid node carries its
 // populations over unchanged (u = 0, rho = 1 on macro steps); one site per thread.
-template <typename Real, typename Store, bool Shifted, bool WriteMacro, int SPT, bool Solid = false>
+template <typename Real, typename Store, bool Shifted, int Macro, int SPT, bool Solid = false>
 __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, int ntiles)
 {
     static_assert(!Solid || SPT == 1, "obstacles use one site per thread");
     NH_D3Q19_TABLES
     constexpr bool kScaled = sizeof(Store) == 2;
+    constexpr bool WriteMacro = Macro >= 1;
+    constexpr bool Partials = Macro == 2;
+    static_assert(!Partials || (!kScaled && !Solid), "diagnostics partials: FP32 / FP64 stores without obstacles");
+    Real psum = 0, pmax = 0;  // diagnostics partials of this thread (Partials)
+    int pbad = 0;
     const int N = c.g.N;
     const int s0 = (tile * blockDim.x + threadIdx.x) * SPT;
     float amax = 0.f;
@@ -200,7 +218,8 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
         const int dzp = (z == nz - 1 ? -(nz - 1) : 1) * plane_xy;
         const bool bb_lo = c.g.walls && z == 0;
         const bool bb_hi = c.g.walls && z == nz - 1;
-        const bool solid_here = Solid && c.solid[s0] != 0;
+        // the Solid variant also serves channels without a mask in a batch that has obstacles
+        const bool solid_here = Solid && c.solid != nullptr && c.solid[s0] != 0;
 
         // 1. pull streaming with half-way bounce-back
         Real f[SPT][19];
@@ -211,7 +230,7 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
             if (Solid) {
                 const int dx = EX[i] > 0 ? dxm[0] : (EX[i] < 0 ? dxp[0] : 0);
                 const int src = s0 + row + dx;
-                const bool back = bb || (!solid_here && c.solid[src] != 0);
+                const bool back = bb || (!solid_here && c.solid != nullptr && c.solid[src] != 0);
                 const int k = back ? OPP[i] : i;
                 f[0][i] = Codec<Store, Real>::load(c.fsrc + (size_t)(solid_here ? i : k) * N +
                                                        (solid_here || back ? s0 : src),
@@ -344,6 +363,15 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
                 fo[j][i] = omc * f[j][i] + even + odd;
                 fo[j][i + 1] = omc * f[j][i + 1] + even - odd;
             }
+            if (Partials) {  // the sums nh_diagnostics forms from the stored state, site by site
+                Real fs = fo[j][0];
+#pragma unroll
+                for (int i = 1; i < 19; ++i) fs += fo[j][i];
+                psum += fs;
+                const Real umag = sqrt(ux * ux + uy * uy + uz * uz);
+                pmax = max(pmax, umag);
+                if (!isfinite(umag) || !isfinite(rho) || !isfinite(fs)) pbad += 1;
+            }
             if (kScaled) {
 #pragma unroll
                 for (int i = 0; i < 19; ++i) amax = fmaxf(amax, fabsf((float)fo[j][i]));
@@ -363,6 +391,29 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
             } else {
                 Codec<Store, Real>::store(dst, fo[0][i], kScaled ? 1.f : scale_out);
             }
+        }
+    }
+    if constexpr (Partials) {
+        // block partials: FP64 warp sums, then the warps in a fixed order
+        __shared__ double pred[kLBThreads / 32][3];
+        const double m = lb_warp_sum((double)psum);
+        double mx = (double)pmax;
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const double nb = lb_warp_sum((double)pbad);
+        if ((threadIdx.x & 31) == 0) {
+            pred[threadIdx.x >> 5][0] = m;
+            pred[threadIdx.x >> 5][1] = mx;
+            pred[threadIdx.x >> 5][2] = nb;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double v[3] = {0.0, 0.0, 0.0};
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                v[0] += pred[w][0];
+                v[1] = fmax(v[1], pred[w][1]);
+                v[2] += pred[w][2];
+            }
+            for (int k = 0; k < 3; ++k) c.part[(size_t)k * ntiles + tile] = v[k];
         }
     }
     if (kScaled) {
@@ -395,15 +446,15 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
     }
 }
 
-template <typename Real, typename Store, bool Shifted, bool WriteMacro, int SPT, bool Solid = false>
+template <typename Real, typename Store, bool Shifted, int Macro, int SPT, bool Solid = false>
 __global__ void __launch_bounds__(kLBThreads) lb_kernel(const LBChan<Real, Store> c)
 {
-    lb_tile<Real, Store, Shifted, WriteMacro, SPT, Solid>(c, blockIdx.x, gridDim.x);
+    lb_tile<Real, Store, Shifted, Macro, SPT, Solid>(c, blockIdx.x, gridDim.x);
 }
 
 // Batched sweep: a persistent grid walks the (channel, tile) work list of up to
 // kMaxBatch channels; tiles of channel k are [prefix[k], prefix[k+1]).
-template <typename Real, typename Store, bool Shifted, bool WriteMacro, int SPT>
+template <typename Real, typename Store, bool Shifted, bool WriteMacro, int SPT, bool Solid = false>
 __global__ void __launch_bounds__(kLBThreads) lb_batch_kernel(const LBBatch<Real, Store> b)
 {
     const int total = b.prefix[b.count];
@@ -416,7 +467,8 @@ __global__ void __launch_bounds__(kLBThreads) lb_batch_kernel(const LBBatch<Real
             else
                 hi = mid - 1;
         }
-        lb_tile<Real, Store, Shifted, WriteMacro, SPT>(b.ch[lo], t - b.prefix[lo], b.prefix[lo + 1] - b.prefix[lo]);
+        lb_tile<Real, Store, Shifted, WriteMacro ? 1 : 0, SPT, Solid>(b.ch[lo], t - b.prefix[lo],
+                                                                     b.prefix[lo + 1] - b.prefix[lo]);
     }
 }
 
@@ -432,22 +484,31 @@ bool lb_variant_valid(int variant, int nx)
     return nx % kLBVariants[variant].spt == 0;
 }
 
-template <typename Real, typename Store, bool Shifted, bool WriteMacro>
+int lb_blocks(int variant, int N)
+{
+    const LBVariantShape v = kLBVariants[variant];
+    const int threads_needed = (N + v.spt - 1) / v.spt;
+    return (threads_needed + v.threads - 1) / v.threads;
+}
+
+template <typename Real, typename Store, bool Shifted, int Macro>
 cudaError_t launch_lb_spt(const LBChan<Real, Store>& c, int variant, cudaStream_t st)
 {
     if (c.solid != nullptr) {  // obstacles: one site per thread, 256 threads
-        lb_kernel<Real, Store, Shifted, WriteMacro, 1, true><<<(c.g.N + 255) / 256, 256, 0, st>>>(c);
+        if constexpr (Macro < 2)
+            lb_kernel<Real, Store, Shifted, Macro, 1, true><<<(c.g.N + 255) / 256, 256, 0, st>>>(c);
+        else
+            return cudaErrorInvalidValue;
         return cudaGetLastError();
     }
     const LBVariantShape v = kLBVariants[variant];
-    const int threads_needed = (c.g.N + v.spt - 1) / v.spt;
-    const int blocks = (threads_needed + v.threads - 1) / v.threads;
+    const int blocks = lb_blocks(variant, c.g.N);
     if (v.spt == 4)
-        lb_kernel<Real, Store, Shifted, WriteMacro, 4><<<blocks, v.threads, 0, st>>>(c);
+        lb_kernel<Real, Store, Shifted, Macro, 4><<<blocks, v.threads, 0, st>>>(c);
     else if (v.spt == 2)
-        lb_kernel<Real, Store, Shifted, WriteMacro, 2><<<blocks, v.threads, 0, st>>>(c);
+        lb_kernel<Real, Store, Shifted, Macro, 2><<<blocks, v.threads, 0, st>>>(c);
     else
-        lb_kernel<Real, Store, Shifted, WriteMacro, 1><<<blocks, v.threads, 0, st>>>(c);
+        lb_kernel<Real, Store, Shifted, Macro, 1><<<blocks, v.threads, 0, st>>>(c);
     return cudaGetLastError();
 }
 
@@ -455,17 +516,33 @@ template <typename Real, typename Store>
 cudaError_t launch_lb(const LBChan<Real, Store>& c, bool shifted, bool write_macro, int variant, cudaStream_t st)
 {
     if (!lb_variant_valid(variant, c.g.nx)) return cudaErrorInvalidValue;
-    if (shifted) {
-        if (write_macro) return launch_lb_spt<Real, Store, true, true>(c, variant, st);
-        return launch_lb_spt<Real, Store, true, false>(c, variant, st);
+    if constexpr (sizeof(Store) != 2) {
+        if (write_macro && c.part != nullptr) {
+            if (c.solid != nullptr) return cudaErrorInvalidValue;
+            return shifted ? launch_lb_spt<Real, Store, true, 2>(c, variant, st)
+                           : launch_lb_spt<Real, Store, false, 2>(c, variant, st);
+        }
     }
-    if (write_macro) return launch_lb_spt<Real, Store, false, true>(c, variant, st);
-    return launch_lb_spt<Real, Store, false, false>(c, variant, st);
+    if (shifted) {
+        if (write_macro) return launch_lb_spt<Real, Store, true, 1>(c, variant, st);
+        return launch_lb_spt<Real, Store, true, 0>(c, variant, st);
+    }
+    if (write_macro) return launch_lb_spt<Real, Store, false, 1>(c, variant, st);
+    return launch_lb_spt<Real, Store, false, 0>(c, variant, st);
 }
 
 template <typename Real, typename Store, bool Shifted, bool WriteMacro>
 cudaError_t launch_lb_batch_spt(LBBatch<Real, Store>& b, int variant, int grid, cudaStream_t st)
 {
+    bool solid = false;
+    for (int k = 0; k < b.count; ++k) solid = solid || b.ch[k].solid != nullptr;
+    if (solid) {  // obstacles in the batch: one site per thread, 256 threads, for every channel
+        b.prefix[0] = 0;
+        for (int k = 0; k < b.count; ++k) b.prefix[k + 1] = b.prefix[k] + (b.ch[k].g.N + 255) / 256;
+        const int blocks = grid < b.prefix[b.count] ? grid : b.prefix[b.count];
+        lb_batch_kernel<Real, Store, Shifted, WriteMacro, 1, true><<<blocks, 256, 0, st>>>(b);
+        return cudaGetLastError();
+    }
     const LBVariantShape v = kLBVariants[variant];
     b.prefix[0] = 0;
     for (int k = 0; k < b.count; ++k) {

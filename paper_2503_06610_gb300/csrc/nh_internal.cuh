@@ -93,6 +93,7 @@ struct LBChan {
     Real* rho;      // [N]    written on macro steps
     float* scales;
     unsigned* ctrl;
+    double* part;   // [3][blocks] diagnostics partials of a macro launch, or null (F32 / F64 stores)
     int src;        // index (0/1) of the source buffer
     Geom g;
     Real omega;     // 1/tau
@@ -191,6 +192,7 @@ struct FDBatch {
 // LB launch variants (sites per thread x block size); variant 0 is the default.
 constexpr int kLBVariantCount = 6;
 bool lb_variant_valid(int variant, int nx);
+int lb_blocks(int variant, int N);  // thread blocks of one LB launch of that shape
 template <typename Real, typename Store>
 cudaError_t launch_lb(const LBChan<Real, Store>& c, bool shifted, bool write_macro, int variant, cudaStream_t s);
 
@@ -265,6 +267,10 @@ struct DiagArgs {
     double* partials;   // [blocks][NDIAG]
     double* result;     // [NDIAG]
     int blocks;
+    // [3][lbp_blocks] mass, max |u| and non-finite partials left by the LB launch that
+    // wrote f, u and rho (F32 / F64 stores, no obstacles): only n is read; or null
+    const double* lbpart = nullptr;
+    int lbp_blocks = 0;
 };
 int diag_num_values(int n_tubes);
 int diag_blocks();

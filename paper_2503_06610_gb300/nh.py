@@ -117,6 +117,7 @@ SIGNATURES = {
     "nh_launch_count": ([_VP], ctypes.c_int64),
     "nh_set_graphs": ([_VP, ctypes.c_int], ctypes.c_int),
     "nh_set_wait_limit": ([_VP, ctypes.c_double], ctypes.c_int),
+    "nh_set_diag_fold": ([_VP, ctypes.c_int], ctypes.c_int),
     "nh_set_lb_variant": ([_VP, ctypes.c_int], ctypes.c_int),
     "nh_set_fd_variant": ([_VP, ctypes.c_int], ctypes.c_int),
     "nh_autotune": ([_VP, _VP, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
@@ -390,6 +391,10 @@ def nh_set_wait_limit(ctx, seconds):
     _check(load_library().nh_set_wait_limit(ctx, float(seconds)), ctx)
 
 
+def nh_set_diag_fold(ctx, on: bool):
+    _check(load_library().nh_set_diag_fold(ctx, 1 if on else 0), ctx)
+
+
 def nh_set_lb_variant(ctx, variant: int):
     _check(load_library().nh_set_lb_variant(ctx, int(variant)), ctx)
 
@@ -513,6 +518,9 @@ class Channel:
 
     def set_graphs(self, on=True):
         nh_set_graphs(self.ctx, on)
+
+    def set_diag_fold(self, on=True):
+        nh_set_diag_fold(self.ctx, on)
 
     def set_wait_limit(self, seconds):
         """Bound the host-side waits (seconds > 0; NHError with code NH_ETIMEOUT when exceeded)."""

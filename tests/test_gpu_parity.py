@@ -72,7 +72,8 @@ def test_lb_rows_fp64(nh, oracle_mod, shifted, walls):
     assert np.max(np.abs(f - ref.f)) < 1e-13
 
 
-GRIDS = [(13, 9, 7), (40, 20, 20), (33, 17, 17)]   # ragged; several x-y tiles, two z chunks, a one-layer chunk
+# ragged; several x-y tiles; one-layer chunks (small grids) and two-layer chunks with a ragged last one
+GRIDS = [(13, 9, 7), (40, 20, 20), (33, 17, 17), (100, 64, 23)]
 
 
 @pytest.mark.parametrize("fused", [1, 0])
@@ -659,19 +660,40 @@ def test_frank3_channel_and_energy(nh, oracle_mod):
         assert abs(d["energy"] - ref.energy()) <= (1e-11 if prec == "fp64" else 1e-5) * abs(ref.energy())
 
 
-def test_frank3_rejects_fused_and_batches(nh):
+def test_frank3_rejects_fused_and_runs_in_batches(nh, oracle_mod):
+    """The three-constant energy runs on the per-site FD kernels, also in a
+    batch that mixes it with one-constant channels (the per-site work-list
+    kernels with the P stages; the one-constant channels skip them): equal to
+    the same channels stepped alone, and to the oracle."""
+    O = oracle_mod
     params = _generic(16, 12, 8, dt_fd=2, **FRANK3)
-    n0 = I.uniform_director(16, 12, 8)
+    n0 = I.skyrmion_tubes(16, 12, 8, [(8.0, 6.0)], 4.0)
     ch = _channel(nh, params, n0, precision="fp32")
     with pytest.raises(nh.NHError):
         ch.set_fd_variant(1)
-    chans = [_channel(nh, params, n0, precision="fp32") for _ in range(2)]
-    with pytest.raises(nh.NHError):
-        nh.batch_step(chans, 2)
-    with pytest.raises(nh.NHError):
-        nh.batch_relax(chans, 2)
     with pytest.raises(nh.NHError):
         nh.Channel(dict(params, K22=0.0, precision="fp32"))
+    specs = [params, _generic(12, 10, 6, dt_fd=2), dict(params, nx=14, q0=0.5)]
+    starts = [I.skyrmion_tubes(p["nx"], p["ny"], p["nz"], [(p["nx"] / 2, p["ny"] / 2)], 3.5) for p in specs]
+    batch = [_channel(nh, p, s, precision="fp64") for p, s in zip(specs, starts)]
+    nh.batch_step(batch, 6)
+    nh.batch_step(batch, 3)
+    for chb, p, s in zip(batch, specs, starts):
+        one = _channel(nh, p, s, precision="fp64")
+        one.set_fd_variant(0)  # the per-site kernels, as in a batch with a three-constant channel
+        one.step(9)
+        nb, ub, _ = chb.get_fields()
+        ns, us, _ = one.get_fields()
+        assert np.max(np.abs(nb - ns)) <= 1e-15 and np.max(np.abs(ub - us)) <= 1e-15 * max(np.max(np.abs(us)), 1e-30)
+        ref = _oracle_sim(O, p, s).step(9)
+        assert np.max(np.abs(nb - ref.n)) <= 1e-12
+    relax = [_channel(nh, p, s, precision="fp64") for p, s in zip(specs, starts)]
+    nh.batch_relax(relax, 5)
+    for chr_, p, s in zip(relax, specs, starts):
+        one = _channel(nh, p, s, precision="fp64")
+        one.set_fd_variant(0)
+        one.relax(5)
+        assert np.max(np.abs(chr_.get_fields()[0] - one.get_fields()[0])) <= 1e-15
 
 
 # ------------------------------------------------------------------ obstacles (solid nodes, Sec. II.B)
@@ -684,8 +706,10 @@ def _sphere_mask(nx, ny, nz, c, r):
     return m.astype(np.uint8).reshape(-1), (v / np.linalg.norm(v, axis=0)).reshape(3, -1)
 
 
-@pytest.mark.parametrize("frank3", [False, True])
-def test_obstacle_channel_matches_oracle(nh, oracle_mod, frank3):
+@pytest.mark.parametrize("frank3,fused", [(False, 1), (False, 0), (True, 0)])
+def test_obstacle_channel_matches_oracle(nh, oracle_mod, frank3, fused):
+    """Obstacles on the fused 2.5D FD kernels and on the per-site ones (the
+    three-constant energy only on the latter)."""
     O = oracle_mod
     nx, ny, nz = 20, 14, 10
     mask, normals = _sphere_mask(nx, ny, nz, (10.0, 7.0, 5.0), 3.2)
@@ -699,6 +723,7 @@ def test_obstacle_channel_matches_oracle(nh, oracle_mod, frank3):
     for prec, tol in (("fp64", 1e-12), ("fp32", 2e-5)):
         ch = nh.Channel(dict(params, precision=prec))
         ch.set_solid(mask)
+        ch.set_fd_variant(fused)
         ch.set_fields(n0)
         n_loaded = ch.get_fields()[0]  # nh_set_fields normalises the director
         ch.step(21)
@@ -750,23 +775,43 @@ def test_obstacle_plates_equal_rotated_walls_gpu(nh):
     assert abs(a.diagnostics()["energy"] - b.diagnostics()["energy"]) < 1e-12 * abs(a.diagnostics()["energy"])
 
 
-def test_obstacle_rejects_fused_and_batches(nh):
-    params = _generic(16, 12, 8, dt_fd=2)
-    n0 = I.uniform_director(16, 12, 8)
-    mask = np.zeros(16 * 12 * 8, np.uint8)
-    mask[100] = 1
-    chans = []
-    for _ in range(2):
-        ch = nh.Channel(dict(params, precision="fp32"))
-        ch.set_solid(mask)
-        ch.set_fields(n0)
-        chans.append(ch)
-    with pytest.raises(nh.NHError):
-        chans[0].set_fd_variant(1)
-    with pytest.raises(nh.NHError):
-        nh.batch_step(chans, 2)
-    chans[1].set_solid(None)
-    chans[1].set_fd_variant(1)
+@pytest.mark.parametrize("fused", [1, 0])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16s"])
+def test_obstacles_run_in_batches(nh, oracle_mod, storage, fused):
+    """A batch with obstacles in some channels runs one site per thread in the
+    LB sweep (channels without a mask included) and the fused or the per-site
+    FD kernels: equal to the channels stepped alone (populations included),
+    and to the oracle in FP64."""
+    O = oracle_mod
+    prec = "fp64" if storage == "f64" else "fp32"
+    dims = [(16, 12, 8), (12, 10, 6), (18, 8, 7)]
+    masks = [_sphere_mask(16, 12, 8, (8.0, 6.0, 4.0), 2.5), None, _sphere_mask(18, 8, 7, (3.0, 4.0, 3.0), 2.0)]
+    def make(fd_variant=None):
+        out = []
+        for (nx, ny, nz), m in zip(dims, masks):
+            params = dict(_generic(nx, ny, nz, dt_fd=2), precision=prec, storage=storage)
+            ch = nh.Channel(params)
+            n0 = I.uniform_director(nx, ny, nz)
+            if m is not None:
+                mask, normal = m
+                ch.set_solid(mask)
+                n0 = np.where(mask[None] == 1, normal, n0)
+            if fd_variant is not None:
+                ch.set_fd_variant(fd_variant)
+            ch.set_fields(n0)
+            out.append((ch, params, n0))
+        return out
+    batch = make(fd_variant=fused)
+    nh.batch_step([c for c, _, _ in batch], 5)
+    singles = make(fd_variant=fused)
+    for (cb, params, n0), (cs, _, _) in zip(batch, singles):
+        cs.step(5)
+        assert np.array_equal(cb.get_fields()[0], cs.get_fields()[0])
+        assert np.array_equal(cb.get_populations(), cs.get_populations())
+    if storage == "f64":
+        for (cb, params, n0), m in zip(batch, masks):
+            ref = O.OracleSim(O.OracleParams.from_dict(dict(params, solid=None if m is None else m[0])), n0).step(5)
+            assert np.max(np.abs(cb.get_fields()[0] - ref.n)) <= 1e-12
 
 
 # ------------------------------------------------------------------ degenerate lattices

@@ -277,11 +277,12 @@ def test_trained_network_saves_relaxation_steps(env):
     warm-start experiment (48x48x16 cells, wide enough that a tube does not feel
     its periodic images): the plain relaxation continued from the trained
     network's prediction ends on the field of the relaxation from the ansatz
-    (max |dn| <= 1e-4) from a start several times closer to it, in fewer FD
-    steps."""
+    (max |dn| <= 1e-4 once both are continued to a four times smaller stop
+    rate) from a start several times closer to it, in fewer FD steps to the
+    ordinary stop rate."""
     torch, nh, ws, U = env
     samples = I.warmstart_samples(176, seed=3, nx=48, ny=48, lz_choices=(16,))
-    kw = dict(tol=5e-11, max_steps=160000)
+    kw = dict(tol=2e-10, max_steps=160000)
     targets, steps, _ = ws.generate(samples, **kw)
     valid = [i for i in range(len(samples)) if not ws.collapsed(targets[i], samples[i][0]["nz"])]
     train_idx = [i for i in valid if i < 160]
@@ -290,7 +291,7 @@ def test_trained_network_saves_relaxation_steps(env):
     net = ws.WarmStartNet(seed=0)
     hist = ws.train(net, samples, targets, train_idx, epochs=60)
     assert hist[-1] < 0.5 * hist[0]
-    res = ws.evaluate(net, samples, targets, steps, test_idx, **kw)
+    res = ws.evaluate(net, samples, targets, steps, test_idx, judge_tol=5e-11, **kw)
     print("warm start (48x48x16):", {k: v for k, v in res.items() if k != "per_sample"})
     for ps in sorted(res["per_sample"], key=lambda q: -q["max_dn"])[:3]:
         print("  worst held-out samples:", ps)
