@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--small", action="store_true", help="64x64x32 case (profiling only)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-channel sweep")
     ap.add_argument("--batch-blocks", type=int, default=20, help="dt_FD blocks timed in the batched sweep")
+    ap.add_argument("--no-diag-fold", action="store_true",
+                    help="diagnostics read the populations, u and rho themselves (nh_set_diag_fold 0)")
     return ap.parse_args()
 
 
@@ -320,6 +322,8 @@ def run_ours(args):
                "sample": f"{dt} LB steps + 1 FD update of the full workload in FP64 ({secs:.1f} s)"}
 
     ch = nh.Channel(dict(params, precision="fp32", storage=store, shifted=True))
+    if args.no_diag_fold:
+        ch.set_diag_fold(False)
     ch.set_fields(n0)
     ch.set_tubes(centres)
     stream = ch.stream
@@ -494,7 +498,10 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": name, "storage": f"{store} shifted populations", "sites": N,
                        "lb_steps_per_step": dt, "l2": "inputs larger than L2 (populations 2x%.0f MB)"
-                       % (19 * N * (2 if store != 'f32' else 4) / 1e6), "parallelism": f"replicas x{world}"},
+                       % (19 * N * (2 if store != 'f32' else 4) / 1e6), "parallelism": f"replicas x{world}",
+                       "diagnostics": "every bench step, " + ("reading f, u, rho" if args.no_diag_fold or store not in
+                                                              ("f32", "f64") else "sums of f, u, rho folded into the "
+                                                              "LB launch that writes u, rho")},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -452,8 +452,9 @@ int nh_diagnostics_noalloc(const nh_params* p, const void* f, const void* n, con
  * relaxation (nh_relax) continues from its prediction, which counts only if
  * that run ends where the relaxation from the ansatz ends.
  * Activations are BF16, accumulation FP32, convolutions run on the tensor
- * cores; parameters, gradients and Adam moments are caller-owned FP32 device
- * vectors in the layout: per conv layer W[tap][cout][cin] (tap = 9 kz + 3 ky
+ * cores (the forward on the 5th-generation ones: tcgen05.mma with TMEM
+ * accumulators); parameters, gradients and Adam moments are caller-owned FP32
+ * device vectors in the layout: per conv layer W[tap][cout][cin] (tap = 9 kz + 3 ky
  * + kx, offsets -1..1) then bias[cout], layers enc1a enc1b enc2a enc2b enc3a
  * enc3b bota botb dec3a dec3b dec2a dec2b dec1a dec1b, then the head
  * W[3][16], bias[3].  Convolutions are periodic in x, y and zero-padded in z.
@@ -472,6 +473,12 @@ int nh_unet_set_params(nh_unet* net, const float* params, void* stream);
 /* Forward pass; keeps the activations for nh_unet_backward.  n_out may be NULL. */
 int nh_unet_forward(nh_unet* net, const float* params, const float* n_ansatz, const float* scalars, float* n_out,
                     void* stream);
+/* Status of the network's tensor-core convolutions since the last call: the
+ * forward convolutions bound every wait for their MMAs, and one that expired
+ * leaves its output tile unwritten and raises a flag instead of hanging.
+ * Synchronises stream; NH_ETIMEOUT (flag cleared) if a wait expired, else
+ * NH_OK. */
+int nh_unet_status(nh_unet* net, void* stream);
 /* Loss mean |n - target|^2 over all sites into *loss (device float) and its
  * gradient with respect to the parameters into grad (overwritten), for the
  * activations of the last forward pass. */

@@ -161,19 +161,18 @@ __device__ __forceinline__ void store4(Store* p, const Real v[4], float scale)
 // block partials c.part[k * ntiles + tile] of k = 0: sum of the stored
 // post-collision populations, 1: max |u|, 2: sites with a non-finite u, rho
 // or population sum (FP32 and FP64 stores).
-__device__ __forceinline__ double lb_warp_sum(double v)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 // One tile (one thread block's worth of sites) of one channel.  `tile` is the
 // tile index within the channel and `ntiles` the channel's tile count (used by
 // the 16-bit scale controller to find the channel's last tile).  Solid: the
 // channel has obstacles (c.solid): a link whose source is a solid node
 // bounces back half-way like the plates, and a solid node carries its
 // populations over unchanged (u = 0, rho = 1 on macro steps); one site per thread.
-template <typename Real, typename Store, bool Shifted, int Macro, int SPT, bool Solid = false>
+// OneTile: the block sweeps this one tile (lb_kernel); the 16-bit scale
+// controller then combines the warps through shared-memory atomics, and the
+// block's last warp to finish carries the block's maximum on, so no warp waits
+// at a barrier for the others.  A block of the batched kernel sweeps several
+// tiles and keeps the barrier form.
+template <typename Real, typename Store, bool Shifted, int Macro, int SPT, bool Solid = false, bool OneTile = false>
 __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, int ntiles)
 {
     static_assert(!Solid || SPT == 1, "obstacles use one site per thread");
@@ -184,6 +183,14 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
     static_assert(!Partials || (!kScaled && !Solid), "diagnostics partials: FP32 / FP64 stores without obstacles");
     Real psum = 0, pmax = 0;  // diagnostics partials of this thread (Partials)
     int pbad = 0;
+    __shared__ unsigned blk_max, blk_done;  // OneTile scale controller: block max (float bits), warps done
+    if constexpr (kScaled && OneTile) {
+        if (threadIdx.x == 0) {
+            blk_max = 0u;
+            blk_done = 0u;
+        }
+        __syncthreads();
+    }
     const int N = c.g.N;
     const int s0 = (tile * blockDim.x + threadIdx.x) * SPT;
     float amax = 0.f;
@@ -368,9 +375,11 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
 #pragma unroll
                 for (int i = 1; i < 19; ++i) fs += fo[j][i];
                 psum += fs;
-                const Real umag = sqrt(ux * ux + uy * uy + uz * uz);
-                pmax = max(pmax, umag);
-                if (!isfinite(umag) || !isfinite(rho) || !isfinite(fs)) pbad += 1;
+                // max |u|^2 here and one square root per warp: sqrt is monotonic and
+                // correctly rounded, so this equals the maximum of the per-site |u|
+                const Real u2 = ux * ux + uy * uy + uz * uz;
+                pmax = max(pmax, u2);
+                if (!isfinite(u2) || !isfinite(rho) || !isfinite(fs)) pbad += 1;
             }
             if (kScaled) {
 #pragma unroll
@@ -394,16 +403,20 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
         }
     }
     if constexpr (Partials) {
-        // block partials: FP64 warp sums, then the warps in a fixed order
+        // block partials: warp sums in the build's precision (FP64 arithmetic is
+        // scarce on GB300: a per-thread FP64 reduction would cost a third of the
+        // launch), then FP64 across the block's warps in a fixed order
         __shared__ double pred[kLBThreads / 32][3];
-        const double m = lb_warp_sum((double)psum);
-        double mx = (double)pmax;
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        const double nb = lb_warp_sum((double)pbad);
+        Real m = psum, mx = pmax;
+        for (int o = 16; o > 0; o >>= 1) {
+            m += __shfl_xor_sync(0xffffffffu, m, o);
+            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
+        const int nb = __reduce_add_sync(0xffffffffu, pbad);
         if ((threadIdx.x & 31) == 0) {
-            pred[threadIdx.x >> 5][0] = m;
-            pred[threadIdx.x >> 5][1] = mx;
-            pred[threadIdx.x >> 5][2] = nb;
+            pred[threadIdx.x >> 5][0] = (double)m;
+            pred[threadIdx.x >> 5][1] = (double)sqrt(mx);
+            pred[threadIdx.x >> 5][2] = (double)nb;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -423,6 +436,27 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
         __shared__ float wmax[kLBThreads / 32];
         __shared__ bool last;
         for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        if constexpr (OneTile) {
+            if ((threadIdx.x & 31) == 0) {
+                atomicMax(&blk_max, __float_as_uint(amax));  // amax >= 0: the bits order as the values
+                __threadfence_block();
+                if (atomicAdd(&blk_done, 1u) == (blockDim.x >> 5) - 1) {  // the block's last warp
+                    __threadfence_block();
+                    const float b = __uint_as_float(atomicAdd(&blk_max, 0u));
+                    if (b > __int_as_float((int)__ldcg(&c.ctrl[0])))
+                        atomicMax(reinterpret_cast<int*>(&c.ctrl[0]), __float_as_int(b));
+                    __threadfence();
+                    if (atomicAdd(&c.ctrl[1], 1u) == (unsigned)ntiles - 1) {  // the launch's last block
+                        __threadfence();
+                        const float m = __int_as_float((int)atomicExch(&c.ctrl[0], 0u));
+                        c.scales[1 - c.src] = scale_out;
+                        c.scales[2] = scale_for(m, scale_out);
+                        c.ctrl[1] = 0u;
+                    }
+                }
+            }
+            return;
+        }
         if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = amax;
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -449,7 +483,7 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
 template <typename Real, typename Store, bool Shifted, int Macro, int SPT, bool Solid = false>
 __global__ void __launch_bounds__(kLBThreads) lb_kernel(const LBChan<Real, Store> c)
 {
-    lb_tile<Real, Store, Shifted, Macro, SPT, Solid>(c, blockIdx.x, gridDim.x);
+    lb_tile<Real, Store, Shifted, Macro, SPT, Solid, true>(c, blockIdx.x, gridDim.x);
 }
 
 // Batched sweep: a persistent grid walks the (channel, tile) work list of up to

@@ -13,12 +13,14 @@
 // by layer W[tap][cout][cin] (tap = 9 kz + 3 ky + kx) then bias[cout]; the head
 // is W[3][16] then bias[3].
 //
-// Convolutions run on the tensor cores as implicit GEMMs with
-// mma.sync.m16n8k16 (BF16 inputs, FP32 accumulators):
-//   forward       M = voxels (16 per warp), N = cout, K = 27 taps x cin
-//   data grad     M = voxels, N = cin, K = 27 taps x cout (transposed weights)
+// Convolutions run on the tensor cores as implicit GEMMs (BF16 inputs, FP32
+// accumulators):
+//   forward       M = voxels (128 per CTA), N = cout, K = 27 taps x cin, on the
+//                 5th-generation tensor cores (tcgen05.mma, accumulator in TMEM)
+//   data grad     M = voxels, N = cin, K = 27 taps x cout (transposed weights),
+//                 mma.sync.m16n8k16
 //   weight grad   M = cout, N = cin, K = voxels (per tap; shared-memory tiles,
-//                 FP32 atomics across voxel chunks)
+//                 FP32 atomics across voxel chunks), mma.sync.m16n8k16
 #include <stdint.h>
 #include <string.h>
 
@@ -113,6 +115,7 @@ struct ConvFwd {
     bf16* dst;         // [vox][cout]
     Dims d;
     int relu;
+    int* status;       // set to 1 when a bounded wait of the tensor-core kernel expires
 };
 
 template <int COUT>
@@ -165,6 +168,207 @@ __global__ void __launch_bounds__(128) conv_fwd_kernel(const ConvFwd a)
         }
         *reinterpret_cast<uint32_t*>(a.dst + (size_t)vA * COUT + co) = pack_bf16(r0, r1);
         *reinterpret_cast<uint32_t*>(a.dst + (size_t)vB * COUT + co) = pack_bf16(r2, r3);
+    }
+}
+
+// ------------------------------------------------------------------ convolution: forward on tcgen05
+//
+// One CTA (four warps) computes 128 output voxels x COUT channels, the
+// implicit GEMM D[128][COUT] = sum over the 27 taps of A_t[128][cin] W_t^T,
+// A_t the cin input channels of the tap-shifted voxels.  Per tap, A_t and W_t
+// are copied into shared memory with 16-byte cp.async (zero rows where the tap
+// leaves the volume in z) in the tensor core's no-swizzle K-major layout:
+// core matrices of 8 rows x 16 bytes, adjacent core matrices along K 128 bytes
+// apart (LBO), along M / N cin/8 x 128 bytes apart (SBO).  One thread issues
+// the cin/16 MMAs of the tap (tcgen05.mma kind::f16, BF16 x BF16 -> FP32,
+// M = 128, N = COUT, K = 16) into a TMEM accumulator and commits them to the
+// stage's mbarrier; two stages let the copies of the next tap overlap the MMAs
+// of this one.  The epilogue reads each warp's 32 accumulator rows with
+// tcgen05.ld, adds the bias, applies the ReLU and stores BF16 rows.  Every
+// mbarrier wait is bounded: on expiry the kernel raises a.status, skips the
+// epilogue, waits for its copies and frees its TMEM.
+
+constexpr int kTcM = 128;
+constexpr int kTcThreads = 128;
+constexpr int kTcMaxCin = 96;
+constexpr int kTcMaxCout = 64;
+constexpr size_t kTcSmem = 2 * (size_t)(kTcM + kTcMaxCout) * kTcMaxCin * sizeof(bf16) + 64;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor of the tensor core: no swizzle, start
+// address, LBO and SBO in 16-byte units, descriptor version 1 (bits 46-48).
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo & 0x3FFFFu) >> 4) << 16) |
+           ((uint64_t)((sbo & 0x3FFFFu) >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 D (bits 4-5 = 1), BF16 A (7-9 = 1)
+// and B (10-12 = 1), both K-major, N / 8 in bits 17-22, M / 16 in bits 24-28.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int COUT>
+__global__ void __launch_bounds__(kTcThreads) conv_fwd_tc_kernel(const ConvFwd a)
+{
+    extern __shared__ __align__(128) unsigned char tc_smem[];
+    const int cin = a.c1 + a.c2;
+    const int kb = cin / 8;                        // 16-byte core-matrix columns along K
+    const uint32_t sbo_a = (uint32_t)kb * 128u;    // between 8-row groups
+    const uint32_t a_bytes = kTcM * cin * 2, b_bytes = COUT * cin * 2;
+    unsigned char* stage[2] = {tc_smem, tc_smem + a_bytes + b_bytes};
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tc_smem + 2 * (a_bytes + b_bytes));
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+    constexpr uint32_t kCols = COUT < 32 ? 32 : COUT;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int total = a.d.nvox * a.d.batch;
+    const int v0 = blockIdx.x * kTcM;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bars[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bars[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    // copies of tap t into stage s: the A rows (voxels) and the W_t rows (output channels)
+    auto load_tap = [&](int t, int s) {
+        const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+        const uint32_t sa = smem_u32(stage[s]), sb = sa + a_bytes;
+        for (int i = tid; i < kTcM * kb; i += kTcThreads) {
+            const int r = i / kb, q = i - r * kb;
+            const int v = v0 + r;
+            const int sv = v < total ? shifted(a.d, v, dx, dy, dz) : -1;
+            const int c = q * 8;
+            const bf16* src = a.src1;
+            if (sv >= 0) src = c < a.c1 ? a.src1 + (size_t)sv * a.c1 + c : a.src2 + (size_t)sv * a.c2 + (c - a.c1);
+            cp_async16(sa + (uint32_t)(r >> 3) * sbo_a + (uint32_t)q * 128u + (uint32_t)(r & 7) * 16u, src, sv >= 0);
+        }
+        const bf16* w = a.w + (size_t)t * COUT * cin;
+        for (int i = tid; i < COUT * kb; i += kTcThreads) {
+            const int n = i / kb, q = i - n * kb;
+            cp_async16(sb + (uint32_t)(n >> 3) * sbo_a + (uint32_t)q * 128u + (uint32_t)(n & 7) * 16u,
+                       w + (size_t)n * cin + q * 8, true);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+
+    constexpr uint32_t idesc = umma_idesc_bf16(kTcM, COUT);
+    bool ok = true;
+    load_tap(0, 0);
+    for (int t = 0; t < 27; ++t) {
+        const int s = t & 1;
+        if (t + 1 < 27) {
+            if (t >= 1) ok = ok && mbar_wait(smem_u32(&bars[s ^ 1]), ((t - 1) >> 1) & 1);  // MMAs of tap t - 1
+            if (ok) load_tap(t + 1, s ^ 1);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // the copies, to the tensor core's view
+        ok = __syncthreads_and(ok) != 0;  // every thread takes the same branch
+        if (!ok) break;
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const uint32_t sa = smem_u32(stage[s]), sb = sa + a_bytes;
+            for (int j = 0; j < cin / 16; ++j) {
+                const uint64_t ad = umma_desc(sa + 256u * j, 128u, sbo_a);
+                const uint64_t bd = umma_desc(sb + 256u * j, 128u, sbo_a);
+                const uint32_t acc = (t > 0 || j > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             smem_u32(&bars[s]))
+                         : "memory");
+        }
+    }
+    // the commit of tap 26 (stage 0, its 14th use) covers every MMA
+    if (ok) ok = mbar_wait(smem_u32(&bars[0]), (26 >> 1) & 1);
+    ok = __syncthreads_and(ok) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (ok) {
+        const int r = warp * 32 + lane;
+        const int v = v0 + r;
+#pragma unroll
+        for (int c0 = 0; c0 < COUT; c0 += 16) {
+            float acc[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, acc);
+            if (v < total) {
+                uint32_t packed[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    float x0 = acc[2 * i] + a.bias[c0 + 2 * i], x1 = acc[2 * i + 1] + a.bias[c0 + 2 * i + 1];
+                    if (a.relu) {
+                        x0 = fmaxf(x0, 0.f);
+                        x1 = fmaxf(x1, 0.f);
+                    }
+                    packed[i] = pack_bf16(x0, x1);
+                }
+                uint4* dst = reinterpret_cast<uint4*>(a.dst + (size_t)v * COUT + c0);
+                dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+            }
+        }
+    } else if (tid == 0) {
+        atomicExch(a.status, 1);
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kCols) : "memory");
     }
 }
 
@@ -579,7 +783,7 @@ struct nh_unet {
     size_t ws_bytes = 0;
     size_t need = 0;
     // offsets into the workspace
-    size_t wbf, wt[kLayers], x, act[kLayers], pool_[3], up_[3], grad_a, grad_b, grad_skip[3], gd1;
+    size_t wbf, wt[kLayers], x, act[kLayers], pool_[3], up_[3], grad_a, grad_b, grad_skip[3], gd1, status;
     std::string err;
 };
 
@@ -624,6 +828,7 @@ void plan(nh_unet* u)
     const int skip_c[3] = {16, 16, 32};
     for (int k = 0; k < 3; ++k) u->grad_skip[k] = take((size_t)u->lv[k].nvox * u->batch * skip_c[k] * sizeof(float));
     u->gd1 = take(V0 * kHeadIn * sizeof(float));
+    u->status = take(sizeof(int));  // raised by an expired wait of the tensor-core convolution
     u->need = off;
 }
 
@@ -646,12 +851,26 @@ cudaError_t conv_fwd(nh_unet* u, int l, int level, const bf16* s1, int c1, const
     a.dst = P<bf16>(u, u->act[l]);
     a.d = u->lv[level];
     a.relu = 1;
-    const int tiles = a.d.nvox * a.d.batch / 16;
-    const int blocks = (tiles + 3) / 4;
+    a.status = P<int>(u, u->status);
+    static bool attr_set = false;  // the opt-in to more than 48 KB of shared memory, once per process
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(conv_fwd_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kTcSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(conv_fwd_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(conv_fwd_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int cin = c1 + c2;
+    if (cin % 16 || cin > kTcMaxCin || kConv[l].cout > kTcMaxCout) return cudaErrorInvalidValue;
+    const int blocks = (a.d.nvox * a.d.batch + kTcM - 1) / kTcM;
+    const size_t smem = 2 * (size_t)(kTcM + kConv[l].cout) * cin * sizeof(bf16) + 64;
     switch (kConv[l].cout) {
-    case 16: conv_fwd_kernel<16><<<blocks, 128, 0, st>>>(a); break;
-    case 32: conv_fwd_kernel<32><<<blocks, 128, 0, st>>>(a); break;
-    default: conv_fwd_kernel<64><<<blocks, 128, 0, st>>>(a); break;
+    case 16: conv_fwd_tc_kernel<16><<<blocks, kTcThreads, smem, st>>>(a); break;
+    case 32: conv_fwd_tc_kernel<32><<<blocks, kTcThreads, smem, st>>>(a); break;
+    default: conv_fwd_tc_kernel<64><<<blocks, kTcThreads, smem, st>>>(a); break;
     }
     return cudaGetLastError();
 }
@@ -758,6 +977,21 @@ int nh_unet_bind(nh_unet* u, void* ws, size_t bytes)
     if (bytes < u->need) return unet_fail(u, NH_ENOMEM, "workspace too small: need " + std::to_string(u->need));
     u->ws = static_cast<char*>(ws);
     u->ws_bytes = bytes;
+    UNET_CUDA(u, cudaMemset(u->ws + u->status, 0, sizeof(int)));
+    return NH_OK;
+}
+
+int nh_unet_status(nh_unet* u, void* stream)
+{
+    if (!u || !u->ws) return unet_fail(u, NH_EINVAL, "unbound network");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int flag = 0;
+    UNET_CUDA(u, cudaMemcpyAsync(&flag, u->ws + u->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    UNET_CUDA(u, cudaStreamSynchronize(st));
+    if (flag) {
+        UNET_CUDA(u, cudaMemsetAsync(u->ws + u->status, 0, sizeof(int), st));
+        return unet_fail(u, NH_ETIMEOUT, "a tensor-core convolution gave up waiting for its MMAs");
+    }
     return NH_OK;
 }
 

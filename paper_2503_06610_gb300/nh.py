@@ -132,6 +132,7 @@ SIGNATURES = {
     "nh_unet_activation": ([_VP, ctypes.c_int, _VP, _VP], ctypes.c_int),
     "nh_unet_adam": ([_VP, _VP, _VP, _VP, ctypes.c_int64, ctypes.c_int, ctypes.c_float, _VP], ctypes.c_int),
     "nh_unet_destroy": ([_VP], None),
+    "nh_unet_status": ([_VP, _VP], ctypes.c_int),
     "nh_diagnostics_noalloc": ([ctypes.POINTER(nh_params), _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "nh_slab_plan": ([ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_int, ctypes.POINTER(nh_row_copy),
                       ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
@@ -603,6 +604,10 @@ class UNet:
     def backward(self, params, n_ansatz, target, grad, loss, stream=None):
         _check(load_library().nh_unet_backward(self.h, _dp(params), _dp(n_ansatz), _dp(target), _dp(grad),
                                                _dp(loss), _VP(stream or 0)))
+
+    def status(self, stream=None):
+        """NHError (NH_ETIMEOUT) if a tensor-core convolution gave up a wait since the last check."""
+        _check(load_library().nh_unet_status(self.h, _VP(stream or 0)))
 
     def activation(self, layer, out, stream=None):
         _check(load_library().nh_unet_activation(self.h, int(layer), _dp(out), _VP(stream or 0)))

@@ -179,6 +179,8 @@ def train(net, samples, targets, train_idx, epochs=20, batch=8, lr=1e-3, lr_min=
             losses.append(net.train_step(na.contiguous(), sc.contiguous(), tg.contiguous(), shape, lr_ep).clone())
         mean = float(torch.stack(losses).mean())
         history.append(mean)
+        for unet in net.nets.values():  # a tensor-core convolution that gave up a wait raises here
+            unet.status()
         if log:
             log(f"epoch {ep}: loss {mean:.3e}")
     return history
@@ -254,8 +256,56 @@ def evaluate(net, samples, targets, steps_ansatz, test_idx, batch=64, judge_tol=
             "median_rms_ansatz_vs_relaxed": float(np.median(rms_ans)), "per_sample": per}
 
 
+def conv_flops(dims):
+    """Multiply-adds x 2 of the fourteen 3x3x3 convolutions of one forward pass
+    of one sample of size dims = (nx, ny, nz)."""
+    nx, ny, nz = dims
+    level = {"enc1": 0, "enc2": 1, "enc3": 2, "bot": 3, "dec3": 2, "dec2": 1, "dec1": 0}
+    total = 0
+    for name, ci, co in inputs.UNET_CONV_LAYERS:
+        vox = (nx * ny * nz) >> (3 * level[name[:-1]])
+        total += 2 * vox * 27 * ci * co
+    return total
+
+
+def time_network(batch=8, dims=(64, 64, 32), reps=20):
+    """CUDA-event times of the network's forward and forward + backward passes
+    on a batch of extruded tube ansatzes; returns ms per pass and the
+    convolution TFLOP/s (the backward's two products counted as 2x the
+    forward's)."""
+    import torch
+    net = WarmStartNet(seed=0)
+    samples = inputs.warmstart_samples(batch, seed=1, nx=dims[0], ny=dims[1], lz_choices=(dims[2],))
+    dev = net.device
+    na = torch.tensor(np.stack([s[1] for s in samples]).astype(np.float32), device=dev)
+    sc = torch.tensor(np.array([scalars_of(s[0]) for s in samples], dtype=np.float32), device=dev)
+    shape = (batch,) + tuple(dims)
+    for _ in range(3):
+        net.predict(na, sc, dims)
+        net.loss_and_grad(na, sc, na, dims)
+    net.net(shape).status()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    for _ in range(reps):
+        net.predict(na, sc, dims)
+    ev[1].record()
+    for _ in range(reps):
+        net.loss_and_grad(na, sc, na, dims)
+    ev[2].record()
+    torch.cuda.synchronize()
+    net.net(shape).status()
+    fwd = ev[0].elapsed_time(ev[1]) / reps
+    both = ev[1].elapsed_time(ev[2]) / reps
+    f = conv_flops(dims) * batch
+    return {"batch": batch, "dims": list(dims), "forward_ms": fwd, "forward_backward_ms": both,
+            "conv_gflop_forward": f / 1e9, "forward_tflops": f / (fwd * 1e-3) / 1e12,
+            "forward_backward_tflops": 3 * f / (both * 1e-3) / 1e12}
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--time-network", action="store_true",
+                    help="only time the network's passes on a batch of 8 cells of 64x64x32")
     ap.add_argument("--samples", type=int, default=2000)
     ap.add_argument("--held-out", type=int, default=200)
     ap.add_argument("--epochs", type=int, default=20)
@@ -265,6 +315,9 @@ def main():
     ap.add_argument("--max-steps", type=int, default=200000)
     ap.add_argument("--out", default=None)
     args = ap.parse_args()
+    if args.time_network:
+        print(json.dumps(time_network()), flush=True)
+        return
     samples = inputs.warmstart_samples(args.samples, seed=0)
     kw = dict(tol=args.tol, max_steps=args.max_steps)
     t0 = time.perf_counter()

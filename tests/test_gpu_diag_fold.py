@@ -56,7 +56,9 @@ def test_folded_diagnostics_equal_unfolded(nh, prec, case, steps):
     n0 = I.skyrmion_tubes(nx, 20, 10, tubes, 4.5)
     (cf, a), (cu, b) = _pair(nh, params, n0, tubes, steps)
     assert np.array_equal(cf.get_fields()[1], cu.get_fields()[1])  # the same state
-    assert abs(a["mass"] - b["mass"]) <= 1e-12 * cf.N
+    # per-site population sums in the build's precision, grouped differently
+    # (warps of the LB launch vs items of the reduction), FP64 across groups
+    assert abs(a["mass"] - b["mass"]) <= (1e-12 if prec == "fp64" else 1e-10) * cf.N
     assert abs(a["energy"] - b["energy"]) <= 1e-14 * abs(b["energy"])
     assert abs(a["max_u"] - b["max_u"]) <= 1e-15 * b["max_u"]
     assert a["min_norm"] == b["min_norm"] and a["max_norm"] == b["max_norm"]

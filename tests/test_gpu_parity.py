@@ -804,10 +804,17 @@ def test_obstacles_run_in_batches(nh, oracle_mod, storage, fused):
     batch = make(fd_variant=fused)
     nh.batch_step([c for c, _, _ in batch], 5)
     singles = make(fd_variant=fused)
+    # the work-list kernels evaluate the same arithmetic as the single-channel
+    # ones but are compiled separately: equal up to rounding (16-bit stores: up
+    # to a flipped rounding of a stored population)
+    tol_n, tol_f = {"f64": (1e-13, 1e-12), "f32": (1e-5, 1e-5), "f16s": (1e-3, 1e-2)}[storage]
     for (cb, params, n0), (cs, _, _) in zip(batch, singles):
         cs.step(5)
-        assert np.array_equal(cb.get_fields()[0], cs.get_fields()[0])
-        assert np.array_equal(cb.get_populations(), cs.get_populations())
+        fb, fs = cb.get_populations(), cs.get_populations()
+        dn = np.max(np.abs(cb.get_fields()[0] - cs.get_fields()[0]))
+        df = np.max(np.abs(fb - fs)) / np.max(np.abs(fs))
+        print(f"{storage} fused={fused}: batch vs single max|dn| {dn:.2e}, max|df|/max|f| {df:.2e}")
+        assert dn <= tol_n and df <= tol_f
     if storage == "f64":
         for (cb, params, n0), m in zip(batch, masks):
             ref = O.OracleSim(O.OracleParams.from_dict(dict(params, solid=None if m is None else m[0])), n0).step(5)
