@@ -260,6 +260,29 @@ __device__ __forceinline__ void diag_block_partials(const DiagArgs& a, Real mass
         red[wid][4] = dmax_nn;
         red[wid][5] = dbad;
     }
+    // With lbpart, block b also takes its slice of the LB launch's block
+    // partials (mass, max |u|, non-finite count): warp 0, lanes striding, then
+    // a warp reduction, so the order is fixed.
+    __shared__ double lbv[3];
+    if (a.lbpart != nullptr && wid == 0) {
+        const int nb = a.lbp_blocks;
+        const int per = (nb + gridDim.x - 1) / gridDim.x;
+        const int b0 = blockIdx.x * per, b1 = min(b0 + per, nb);
+        double s0 = 0.0, m1 = 0.0, s2 = 0.0;
+        for (int b = b0 + lane; b < b1; b += 32) {
+            s0 += __ldg(a.lbpart + b);
+            m1 = fmax(m1, __ldg(a.lbpart + nb + b));
+            s2 += __ldg(a.lbpart + 2 * (size_t)nb + b);
+        }
+        s0 = warp_sum(s0);
+        m1 = warp_max(m1);
+        s2 = warp_sum(s2);
+        if (lane == 0) {
+            lbv[0] = s0;
+            lbv[1] = m1;
+            lbv[2] = s2;
+        }
+    }
     __syncthreads();
     double* out = a.partials + blockIdx.x;
     const size_t stride = gridDim.x;
@@ -272,6 +295,11 @@ __device__ __forceinline__ void diag_block_partials(const DiagArgs& a, Real mass
             v[3] = fmin(v[3], red[w][3]);
             v[4] = fmax(v[4], red[w][4]);
             v[5] += red[w][5];
+        }
+        if (a.lbpart != nullptr) {
+            v[0] += lbv[0];
+            v[2] = fmax(v[2], lbv[1]);
+            v[5] += lbv[2];
         }
         for (int k = 0; k < DIAG_FIXED; ++k) out[k * stride] = v[k];
     }
@@ -294,6 +322,10 @@ __device__ __forceinline__ void diag_block_partials(const DiagArgs& a, Real mass
 // FP64 sin/cos tables of the column position, a warp sum and a per-warp
 // shared-memory sum in Real per owner, and FP64 accumulation across warps.
 constexpr int kDiagChunk = 8;
+// Reading the director alone (NOnly) leaves the loop short of loads in
+// flight per site, so longer chunks lose little latency hiding, and the
+// column's tube work (nearest centroid, sin/cos) is then shared by 16 layers.
+constexpr int kDiagChunkN = 16;
 
 template <typename Real>
 __device__ __forceinline__ void load3(const Real* __restrict__ n, int N, int s, Real out[3])
@@ -312,7 +344,8 @@ __global__ void __launch_bounds__(DIAG_THREADS, (sizeof(Real) == 4 && !F3 && !So
     const Geom g = a.g;
     const int N = g.N;
     const int cols = g.nx * g.ny;
-    const int chunks = (g.nz + kDiagChunk - 1) / kDiagChunk;
+    constexpr int kChunk = NOnly ? kDiagChunkN : kDiagChunk;
+    const int chunks = (g.nz + kChunk - 1) / kChunk;
     const int items = cols * chunks;
     const Store* __restrict__ f = static_cast<const Store*>(a.f);
     const Real* __restrict__ n = static_cast<const Real*>(a.n);
@@ -347,8 +380,8 @@ __global__ void __launch_bounds__(DIAG_THREADS, (sizeof(Real) == 4 && !F3 && !So
         int x = 0, y = 0;
         if (valid) {
             const int col = item % cols;
-            const int z0 = (item / cols) * kDiagChunk;
-            const int z1 = min(z0 + kDiagChunk, g.nz);
+            const int z0 = (item / cols) * kChunk;
+            const int z1 = min(z0 + kChunk, g.nz);
             x = col % g.nx;
             y = col / g.nx;
             const int colx = (x + 1 == g.nx ? 0 : x + 1) + g.nx * y;
@@ -481,6 +514,7 @@ __global__ void __launch_bounds__(DIAG_THREADS, (sizeof(Real) == 4 && !F3 && !So
 // x + 1 partner is a scalar load: half the load instructions per site of the
 // one-column kernel, twice the bytes in flight per thread.  The same sums.
 constexpr int kDiagPairChunk = 4;
+constexpr int kDiagPairChunkN = 16;  // director only (NOnly), as kDiagChunkN
 
 template <typename Real>
 struct Pair;
@@ -534,7 +568,8 @@ __global__ void __launch_bounds__(DIAG_THREADS, sizeof(Real) == 4 ? 4 : 1) diag_
     const int cols = g.nx * g.ny;
     const int hx = g.nx >> 1;  // pairs per row
     const int pcols = hx * g.ny;
-    const int chunks = (g.nz + kDiagPairChunk - 1) / kDiagPairChunk;
+    constexpr int kChunk = NOnly ? kDiagPairChunkN : kDiagPairChunk;
+    const int chunks = (g.nz + kChunk - 1) / kChunk;
     const int items = pcols * chunks;
     const Store* __restrict__ f = static_cast<const Store*>(a.f);
     const Real* __restrict__ n = static_cast<const Real*>(a.n);
@@ -566,8 +601,8 @@ __global__ void __launch_bounds__(DIAG_THREADS, sizeof(Real) == 4 ? 4 : 1) diag_
         int x = 0, y = 0;
         if (valid) {
             const int pc = item % pcols;
-            const int z0 = (item / pcols) * kDiagPairChunk;
-            const int z1 = min(z0 + kDiagPairChunk, g.nz);
+            const int z0 = (item / pcols) * kChunk;
+            const int z1 = min(z0 + kChunk, g.nz);
             x = 2 * (pc % hx);
             y = pc / hx;
             const int col = x + g.nx * y;
@@ -674,28 +709,31 @@ __global__ void __launch_bounds__(DIAG_THREADS, sizeof(Real) == 4 ? 4 : 1) diag_
 // block partials (stored value-major, so the loads are contiguous), then a
 // fixed shared-memory tree combines the threads, so the result is
 // deterministic.  Spread over V blocks because FP64 throughput per SM is low.
-// With lbpart, the mass, max |u| and non-finite count also take the block
-// partials [3][lb_blocks] of the LB launch that wrote the state.
 constexpr int kFinalThreads = 256;
+constexpr int kFinalLoads = 8;
 __global__ void __launch_bounds__(kFinalThreads) diag_final_kernel(const double* __restrict__ partials,
-                                                                   double* __restrict__ result, int blocks, int V,
-                                                                   const double* __restrict__ lbpart, int lb_blocks)
+                                                                   double* __restrict__ result, int blocks, int V)
 {
     const int k = blockIdx.x;
     if (k >= V) return;
     const int kind = (k == 2 || k == 4) ? 1 : (k == 3 ? 2 : 0);  // 0 sum, 1 max, 2 min
-    double acc = kind == 2 ? 1e300 : 0.0;
-    for (int b = threadIdx.x; b < blocks; b += kFinalThreads) {
-        const double v = __ldg(partials + (size_t)k * blocks + b);
-        acc = kind == 0 ? acc + v : (kind == 1 ? fmax(acc, v) : fmin(acc, v));
-    }
-    const int lk = k == 0 ? 0 : (k == 2 ? 1 : (k == 5 ? 2 : -1));  // mass, max |u|, non-finite
-    if (lbpart != nullptr && lk >= 0) {
-        for (int b = threadIdx.x; b < lb_blocks; b += kFinalThreads) {
-            const double v = __ldg(lbpart + (size_t)lk * lb_blocks + b);
-            acc = kind == 0 ? acc + v : fmax(acc, v);
+    const double id = kind == 2 ? 1e300 : 0.0;
+    double acc = id;
+    // kFinalLoads loads in flight per thread, then combined in a fixed order
+    auto fold = [&](const double* __restrict__ src, int count) {
+        for (int b0 = threadIdx.x; b0 < count; b0 += kFinalLoads * kFinalThreads) {
+            double v[kFinalLoads];
+#pragma unroll
+            for (int j = 0; j < kFinalLoads; ++j) {
+                const int b = b0 + j * kFinalThreads;
+                v[j] = b < count ? __ldg(src + b) : id;
+            }
+#pragma unroll
+            for (int j = 0; j < kFinalLoads; ++j)
+                acc = kind == 0 ? acc + v[j] : (kind == 1 ? fmax(acc, v[j]) : fmin(acc, v[j]));
         }
-    }
+    };
+    fold(partials + (size_t)k * blocks, blocks);
     __shared__ double sh[kFinalThreads];
     sh[threadIdx.x] = acc;
     __syncthreads();
@@ -963,8 +1001,9 @@ cudaError_t launch_diagnostics(const DiagArgs& a, cudaStream_t st)
     if (a.lbpart != nullptr && (a.solid != nullptr || (a.storage != NH_STORE_F32 && a.storage != NH_STORE_F64)))
         return cudaErrorInvalidValue;
     const bool pairs = diag_pairs(a);
-    const int items = pairs ? (a.g.nx / 2) * a.g.ny * ((a.g.nz + kDiagPairChunk - 1) / kDiagPairChunk)
-                            : a.g.nx * a.g.ny * ((a.g.nz + kDiagChunk - 1) / kDiagChunk);
+    const bool nonly = a.lbpart != nullptr;  // the kernels read the director alone
+    const int chunk = pairs ? (nonly ? kDiagPairChunkN : kDiagPairChunk) : (nonly ? kDiagChunkN : kDiagChunk);
+    const int items = (pairs ? (a.g.nx / 2) : a.g.nx) * a.g.ny * ((a.g.nz + chunk - 1) / chunk);
     int blocks = (items + DIAG_THREADS - 1) / DIAG_THREADS;
     if (blocks > a.blocks) blocks = a.blocks;
     if (pairs && blocks > 4 * 152) blocks = 4 * 152;  // two-column kernel: 4 resident blocks on each of 152 SMs
@@ -977,7 +1016,7 @@ cudaError_t launch_diagnostics(const DiagArgs& a, cudaStream_t st)
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     diag_final_kernel<<<diag_num_values(a.n_tubes), kFinalThreads, 0, st>>>(
-        a.partials, a.result, blocks, diag_num_values(a.n_tubes), a.lbpart, a.lbp_blocks);
+        a.partials, a.result, blocks, diag_num_values(a.n_tubes));
     return cudaGetLastError();
 }
 

@@ -236,7 +236,7 @@ def warmstart_samples(count, seed=0, nx=64, ny=64, lz_choices=(32,), K=0.005, dt
 
 # ------------------------------------------------------------------ paper regime (Table I)
 
-def table1_regime(nx=64, ny=64, nz=16, dt_fd=250, split=0.15, lb_share=None, radius=7.0, shifted=True,
+def table1_regime(nx=64, ny=64, nz=16, dt_fd=250, split=0.3, lb_share=None, radius=7.0, shifted=True,
                   paper_order=True):
     """The paper's test case in lattice units: Table I (MBBA, doubled alpha4),
     pitch P = 14, 64x64x16 (Sec. III.A), g = 2e-9, no anchoring at the plates
@@ -244,12 +244,14 @@ def table1_regime(nx=64, ny=64, nz=16, dt_fd=250, split=0.15, lb_share=None, rad
     gamma1 = alpha3 - alpha2, gamma2 = alpha3 + alpha2.  The isotropic viscosity
     alpha4 is shared between the FD force (alpha4' = split * alpha4) and the
     lattice Boltzmann fluid (2 rho c_s^2 (tau - 1/2) = (1 - split) alpha4, which
-    fixes tau; lb_share overrides that share).  Sec. II.B requires only that the
-    two parts add up to alpha4.  The FD stress is explicit and held for dt_FD
-    LB steps, so a large FD share limits dt_FD: with split = 0.5 (the same
-    viscosity in both parts, tau = 1.199) dt_FD = 1 is stable but dt_FD >= 10
-    is not; the default split = 0.15 (tau = 1.688) is stable over the whole
-    dt_FD range of Sec. III.B.
+    fixes tau; lb_share overrides that share).  Sec. II.B asks that the two
+    parts add up to alpha4 and that they be equal.  The FD force is explicit
+    and held for dt_FD LB steps, and over a long interval its viscous part
+    hands a velocity mode back with the ratio alpha4' / (2 rho c_s^2 (tau -
+    1/2)) of the two viscosities and the opposite sign: equal shares (split =
+    0.5) are marginal and leave the tube state for dt_FD >= 10.  split = 0.3
+    (tau = 1.478) runs the whole dt_FD range of Sec. III.B, 1 to 5000; 0.15
+    fails at dt_FD = 1 instead.
 
     paper_order = True runs the loop of Sec. II.D in its printed order: the
     FD update and the force come between the macroscopic fields and the

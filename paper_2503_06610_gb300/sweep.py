@@ -69,7 +69,7 @@ def run_one(params, n0, centres, precision, storage, shifted, steps):
 
 
 def sweep(steps=5000, gx=1e-5, dts=(1, 2, 4, 8, 16), settings=SETTINGS, nx=96, ny=96, nz=32, radius=12.0,
-          regime="skyrmion", ref_dt=1, split=0.15, paper_order=None):
+          regime="skyrmion", ref_dt=1, split=0.3, paper_order=None):
     if regime == "table1":
         base, n0 = inputs.table1_regime(nx=nx, ny=ny, nz=nz, dt_fd=1, split=split,
                                         paper_order=True if paper_order is None else paper_order)
@@ -124,7 +124,7 @@ def main():
                     help="precision/storage/s|p triples, e.g. fp32/f16s/s (default: all five)")
     ap.add_argument("--size", type=int, nargs=3, default=None, help="nx ny nz")
     ap.add_argument("--ref-dt", type=int, default=1, help="dt_FD of the FP64 reference run")
-    ap.add_argument("--split", type=float, default=0.15, help="table1: share of alpha4 carried by the FD force")
+    ap.add_argument("--split", type=float, default=0.3, help="table1: share of alpha4 carried by the FD force")
     ap.add_argument("--order", choices=["default", "paper", "fused"], default="default",
                     help="loop order: paper = Sec. II.D as printed (the table1 default), fused = the collision keeps "
                          "the force of the previous interval (the skyrmion default)")

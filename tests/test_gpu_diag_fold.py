@@ -59,11 +59,15 @@ def test_folded_diagnostics_equal_unfolded(nh, prec, case, steps):
     # per-site population sums in the build's precision, grouped differently
     # (warps of the LB launch vs items of the reduction), FP64 across groups
     assert abs(a["mass"] - b["mass"]) <= (1e-12 if prec == "fp64" else 1e-10) * cf.N
-    assert abs(a["energy"] - b["energy"]) <= 1e-14 * abs(b["energy"])
+    # the director-only reduction sums chunks of 16 layers (the full one 4 or
+    # 8): the same per-site terms, partial sums in the build's precision
+    # grouped differently -- FP32 rounding of a few tens of terms
+    fp64 = prec == "fp64"
+    assert abs(a["energy"] - b["energy"]) <= (1e-14 if fp64 else 2e-6) * abs(b["energy"])
     assert abs(a["max_u"] - b["max_u"]) <= 1e-15 * b["max_u"]
     assert a["min_norm"] == b["min_norm"] and a["max_norm"] == b["max_norm"]
     assert a["nonfinite"] == b["nonfinite"] == 0
-    assert np.max(np.abs(a["centroids"] - b["centroids"])) <= 1e-12
+    assert np.max(np.abs(a["centroids"] - b["centroids"])) <= (1e-12 if fp64 else 1e-4)
     cf.close()
     cu.close()
 

@@ -6,7 +6,7 @@ paper's own regime at its own dt_FD.
   after 200 LB steps at dt_FD = 1 and 4, as rel. L2 and as the largest
   per-site difference of u and n, with the two plate layers checked by name.
 * The Table I regime (Sec. III.A: 64x64x16, g = 2e-9, no plate anchoring,
-  the same viscosity in the LB and the FD force) in the loop order of
+  equal viscosity shares in the LB and the FD force) in the loop order of
   Sec. II.D at dt_FD = 1, the paper's reference setting: stays finite with
   the velocity of plain Poiseuille flow (~1e-7) (the fused order diverges).
 """
@@ -61,7 +61,7 @@ def test_skyrmion_channel_fp64_per_element(nh, oracle_mod, dt_fd):
 
 
 def test_table1_regime_paper_order_dt1_stable(nh):
-    params, n0 = I.table1_regime(dt_fd=1, split=0.5)  # the same viscosity in LB and FD, Sec. II.B
+    params, n0 = I.table1_regime(dt_fd=1, split=0.5)  # equal viscosity shares in LB and FD, Sec. II.B
     assert params["paper_order"] and abs(params["alpha4p"] - 0.5 * 0.9318) < 1e-12
     ch = nh.Channel(dict(params, precision="fp32", storage="f32"))
     ch.set_fields(n0)

@@ -52,7 +52,10 @@ def test_noalloc_matches_nh_diagnostics_twice(env, prec):
         v = out.cpu().numpy()
         mass = v[0] + ch.N                      # shifted populations
         assert abs(mass - ref["mass"]) <= 1e-12 * ch.N
-        assert abs(v[1] - ref["energy"]) <= 1e-11 * abs(ref["energy"])
+        # nh_diagnostics reads the director alone after a folded LB step and sums
+        # 16-layer chunks, this entry point 4-layer ones: in FP32 the per-site
+        # energies are grouped differently before the FP64 sum
+        assert abs(v[1] - ref["energy"]) <= (1e-11 if prec == "fp64" else 2e-6) * abs(ref["energy"])
         assert abs(v[2] - ref["max_u"]) <= 1e-12 * ref["max_u"]
         assert abs(v[3] - ref["min_norm"]) <= 1e-15 and abs(v[4] - ref["max_norm"]) <= 1e-15
         assert v[5] == 0.0
