@@ -601,12 +601,22 @@ constexpr int kTX = 32, kTY = 8, kZC = 16;
 // GPU (a small channel would otherwise run on a handful of blocks): aim at two
 // blocks per SM of GB300's 152, down to one layer per chunk (each chunk also
 // evaluates the predictor or the stress on the layer below and above it).
+// A batch fills the GPU with all its channels' tiles, so its chunk length is
+// chosen once from their total (FDChan::zch).
 constexpr int kFusedTargetBlocks = 2 * 152;
-__host__ __device__ __forceinline__ int fused_zchunk(const Geom& g)
+__host__ __device__ __forceinline__ int fused_xy_tiles(const Geom& g)
 {
-    const int txy = ((g.nx + kTX - 1) / kTX) * ((g.ny + kTY - 1) / kTY);
-    const int c = (g.nz * txy) / kFusedTargetBlocks;
-    return c < 1 ? 1 : (c > kZC ? kZC : c);
+    return ((g.nx + kTX - 1) / kTX) * ((g.ny + kTY - 1) / kTY);
+}
+__host__ __device__ __forceinline__ int zchunk_for(long long tile_layers)
+{
+    const long long c = tile_layers / kFusedTargetBlocks;
+    return c < 1 ? 1 : (c > kZC ? kZC : (int)c);
+}
+template <typename Real>
+__host__ __device__ __forceinline__ int fused_zchunk(const FDChan<Real>& c)
+{
+    return c.zch > 0 ? c.zch : zchunk_for((long long)c.g.nz * fused_xy_tiles(c.g));
 }
 constexpr int kHX2 = kTX + 4, kHY2 = kTY + 4, kP2 = kHX2 * kHY2;  // plane with a 2-site halo
 constexpr int kHX1 = kTX + 2, kHY1 = kTY + 2, kP1 = kHX1 * kHY1;  // plane with a 1-site halo
@@ -881,7 +891,7 @@ __device__ void fused_a_tile(const FDChan<Real>& c, const Real* __restrict__ nin
     const int ntx = (g.nx + kTX - 1) / kTX, nty = (g.ny + kTY - 1) / kTY;
     const int tx_t = tile % ntx, ty_t = (tile / ntx) % nty, zc = tile / (ntx * nty);
     const int x0 = tx_t * kTX, y0 = ty_t * kTY;
-    const int zch = fused_zchunk(g);
+    const int zch = fused_zchunk(c);
     const int zb = zc * zch, ze = min(zb + zch, g.nz);
     const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
     const bool active = threadIdx.x < kTX * kTY && x0 + tx < g.nx && y0 + ty < g.ny;
@@ -1046,7 +1056,7 @@ __device__ void fused_b_tile(const FDChan<Real>& c, const Real* __restrict__ nin
     const int ntx = (g.nx + kTX - 1) / kTX, nty = (g.ny + kTY - 1) / kTY;
     const int tx_t = tile % ntx, ty_t = (tile / ntx) % nty, zc = tile / (ntx * nty);
     const int x0 = tx_t * kTX, y0 = ty_t * kTY;
-    const int zch = fused_zchunk(g);
+    const int zch = fused_zchunk(c);
     const int zb = zc * zch, ze = min(zb + zch, g.nz);
     const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
     const bool active = threadIdx.x < kTX * kTY && x0 + tx < g.nx && y0 + ty < g.ny;
@@ -1160,10 +1170,11 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(Real) == 4 ? 3 : 2) fuse
     }
 }
 
-inline int fused_tiles(const Geom& g)
+template <typename Real>
+inline int fused_tiles(const FDChan<Real>& c)
 {
-    const int zch = fused_zchunk(g);
-    return ((g.nx + kTX - 1) / kTX) * ((g.ny + kTY - 1) / kTY) * ((g.nz + zch - 1) / zch);
+    const int zch = fused_zchunk(c);
+    return fused_xy_tiles(c.g) * ((c.g.nz + zch - 1) / zch);
 }
 
 template <typename Real>
@@ -1253,9 +1264,9 @@ cudaError_t launch_fd_fused_a(const FDChan<Real>& c, const Real* nin, Real* nout
     cudaError_t e = prepare_fused<Real>();
     if (e != cudaSuccess) return e;
     if (c.solid != nullptr)
-        fused_a_kernel<Real, true><<<fused_tiles(c.g), kFusedThreads, fused_a_smem<Real>(), st>>>(c, nin, nout);
+        fused_a_kernel<Real, true><<<fused_tiles(c), kFusedThreads, fused_a_smem<Real>(), st>>>(c, nin, nout);
     else
-        fused_a_kernel<Real, false><<<fused_tiles(c.g), kFusedThreads, fused_a_smem<Real>(), st>>>(c, nin, nout);
+        fused_a_kernel<Real, false><<<fused_tiles(c), kFusedThreads, fused_a_smem<Real>(), st>>>(c, nin, nout);
     return cudaGetLastError();
 }
 
@@ -1265,9 +1276,9 @@ cudaError_t launch_fd_fused_b(const FDChan<Real>& c, const Real* nin, Real* ncop
     cudaError_t e = prepare_fused<Real>();
     if (e != cudaSuccess) return e;
     if (c.solid != nullptr)
-        fused_b_kernel<Real, true><<<fused_tiles(c.g), kFusedThreads, fused_b_smem<Real>(), st>>>(c, nin, ncopy);
+        fused_b_kernel<Real, true><<<fused_tiles(c), kFusedThreads, fused_b_smem<Real>(), st>>>(c, nin, ncopy);
     else
-        fused_b_kernel<Real, false><<<fused_tiles(c.g), kFusedThreads, fused_b_smem<Real>(), st>>>(c, nin, ncopy);
+        fused_b_kernel<Real, false><<<fused_tiles(c), kFusedThreads, fused_b_smem<Real>(), st>>>(c, nin, ncopy);
     return cudaGetLastError();
 }
 
@@ -1277,8 +1288,14 @@ cudaError_t launch_fd_fused_batch(FDBatch<Real>& b, int stage, int grid, cudaStr
     if (b.count < 1 || b.count > kMaxBatch) return cudaErrorInvalidValue;
     cudaError_t e = prepare_fused<Real>();
     if (e != cudaSuccess) return e;
+    long long tile_layers = 0;
+    for (int k = 0; k < b.count; ++k) tile_layers += (long long)b.ch[k].g.nz * fused_xy_tiles(b.ch[k].g);
+    const int zch = zchunk_for(tile_layers);
     b.prefix[0] = 0;
-    for (int k = 0; k < b.count; ++k) b.prefix[k + 1] = b.prefix[k] + fused_tiles(b.ch[k].g);
+    for (int k = 0; k < b.count; ++k) {
+        b.ch[k].zch = zch;
+        b.prefix[k + 1] = b.prefix[k] + fused_tiles(b.ch[k]);
+    }
     const int blocks = grid < b.prefix[b.count] ? grid : b.prefix[b.count];
     const size_t smem = stage == 1 ? fused_b_smem<Real>() : fused_a_smem<Real>();
     bool solid = false;

@@ -170,6 +170,7 @@ struct FDChan {
     const unsigned char* solid;  // [N] 1 = solid node (obstacle), or null: none
     Geom g;
     FDPar<Real> p;
+    int zch = 0;  // layers per chunk of the fused kernels; 0: chosen from g alone
 };
 
 // ------------------------------------------------------------------ launchers (host)

@@ -86,21 +86,32 @@ struct Dims {
     int nx, ny, nz, nvox, batch;
 };
 
-// Voxel index of v shifted by (dx, dy, dz), periodic in x, y; -1 outside in z.
-__device__ __forceinline__ int shifted(const Dims& d, int v, int dx, int dy, int dz)
+// Voxel v split into (batch, x, y, z) once, and shifted by (dx, dy, dz):
+// periodic in x, y; -1 outside in z (a kernel shifts one voxel by up to 27
+// taps).
+struct VoxCoord {
+    int b, x, y, z;  // b < 0: no voxel
+};
+__device__ __forceinline__ VoxCoord vox_coord(const Dims& d, int v)
 {
-    const int b = v / d.nvox;
-    const int r = v - b * d.nvox;
-    const int x = r % d.nx;
+    VoxCoord c{-1, 0, 0, 0};
+    if (v < 0 || v >= d.nvox * d.batch) return c;
+    c.b = v / d.nvox;
+    const int r = v - c.b * d.nvox;
+    c.x = r % d.nx;
     const int t = r / d.nx;
-    const int y = t % d.ny;
-    const int z = t / d.ny;
-    const int zs = z + dz;
-    if (zs < 0 || zs >= d.nz) return -1;
-    int xs = x + dx, ys = y + dy;
+    c.y = t % d.ny;
+    c.z = t / d.ny;
+    return c;
+}
+__device__ __forceinline__ int shifted(const Dims& d, const VoxCoord& c, int dx, int dy, int dz)
+{
+    const int zs = c.z + dz;
+    if (c.b < 0 || zs < 0 || zs >= d.nz) return -1;
+    int xs = c.x + dx, ys = c.y + dy;
     xs = xs < 0 ? xs + d.nx : (xs >= d.nx ? xs - d.nx : xs);
     ys = ys < 0 ? ys + d.ny : (ys >= d.ny ? ys - d.ny : ys);
-    return b * d.nvox + xs + d.nx * (ys + d.ny * zs);
+    return c.b * d.nvox + xs + d.nx * (ys + d.ny * zs);
 }
 
 // ------------------------------------------------------------------ convolution: forward
@@ -117,59 +128,6 @@ struct ConvFwd {
     int relu;
     int* status;       // set to 1 when a bounded wait of the tensor-core kernel expires
 };
-
-template <int COUT>
-__global__ void __launch_bounds__(128) conv_fwd_kernel(const ConvFwd a)
-{
-    const int lane = threadIdx.x & 31;
-    const int g = lane >> 2, t = lane & 3;
-    const int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int total = a.d.nvox * a.d.batch;
-    const int v0 = tile * 16;
-    if (v0 >= total) return;
-    const int cin = a.c1 + a.c2;
-    const int vA = v0 + g, vB = v0 + g + 8;
-    float acc[COUT / 8][4];
-#pragma unroll
-    for (int j = 0; j < COUT / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-    for (int tap = 0; tap < 27; ++tap) {
-        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-        const int sA = shifted(a.d, vA, dx, dy, dz);
-        const int sB = shifted(a.d, vB, dx, dy, dz);
-        const bf16* wt = a.w + (size_t)tap * COUT * cin;
-        for (int c = 0; c < cin; c += 16) {
-            const bool first = c < a.c1;
-            const bf16* base = first ? a.src1 : a.src2;
-            const int cs = first ? a.c1 : a.c2;
-            const int co = first ? c : c - a.c1;
-            uint32_t fa[4];
-            fa[0] = sA >= 0 ? ld_pair(base + (size_t)sA * cs + co + 2 * t) : 0u;
-            fa[1] = sB >= 0 ? ld_pair(base + (size_t)sB * cs + co + 2 * t) : 0u;
-            fa[2] = sA >= 0 ? ld_pair(base + (size_t)sA * cs + co + 8 + 2 * t) : 0u;
-            fa[3] = sB >= 0 ? ld_pair(base + (size_t)sB * cs + co + 8 + 2 * t) : 0u;
-#pragma unroll
-            for (int j = 0; j < COUT / 8; ++j) {
-                const bf16* wr = wt + (size_t)(j * 8 + g) * cin + c;
-                const uint32_t fb[2] = {ld_pair(wr + 2 * t), ld_pair(wr + 8 + 2 * t)};
-                mma16816(acc[j], fa, fb);
-            }
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < COUT / 8; ++j) {
-        const int co = j * 8 + 2 * t;
-        const float b0 = a.bias[co], b1 = a.bias[co + 1];
-        float r0 = acc[j][0] + b0, r1 = acc[j][1] + b1, r2 = acc[j][2] + b0, r3 = acc[j][3] + b1;
-        if (a.relu) {
-            r0 = fmaxf(r0, 0.f);
-            r1 = fmaxf(r1, 0.f);
-            r2 = fmaxf(r2, 0.f);
-            r3 = fmaxf(r3, 0.f);
-        }
-        *reinterpret_cast<uint32_t*>(a.dst + (size_t)vA * COUT + co) = pack_bf16(r0, r1);
-        *reinterpret_cast<uint32_t*>(a.dst + (size_t)vB * COUT + co) = pack_bf16(r2, r3);
-    }
-}
 
 // ------------------------------------------------------------------ convolution: forward on tcgen05
 //
@@ -279,18 +237,24 @@ __global__ void __launch_bounds__(kTcThreads) conv_fwd_tc_kernel(const ConvFwd a
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
+    // Thread tid stages A row tid (voxel v0 + tid) for every tap: its
+    // coordinates are split once here, and a tap only shifts and wraps them.
+    static_assert(kTcM == kTcThreads, "one A row per thread");
+    const VoxCoord row = vox_coord(a.d, v0 + tid);
+    const uint32_t arow = (uint32_t)(tid >> 3) * sbo_a + (uint32_t)(tid & 7) * 16u;
+
     // copies of tap t into stage s: the A rows (voxels) and the W_t rows (output channels)
     auto load_tap = [&](int t, int s) {
         const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
         const uint32_t sa = smem_u32(stage[s]), sb = sa + a_bytes;
-        for (int i = tid; i < kTcM * kb; i += kTcThreads) {
-            const int r = i / kb, q = i - r * kb;
-            const int v = v0 + r;
-            const int sv = v < total ? shifted(a.d, v, dx, dy, dz) : -1;
-            const int c = q * 8;
-            const bf16* src = a.src1;
-            if (sv >= 0) src = c < a.c1 ? a.src1 + (size_t)sv * a.c1 + c : a.src2 + (size_t)sv * a.c2 + (c - a.c1);
-            cp_async16(sa + (uint32_t)(r >> 3) * sbo_a + (uint32_t)q * 128u + (uint32_t)(r & 7) * 16u, src, sv >= 0);
+        {
+            const int sv = shifted(a.d, row, dx, dy, dz);  // -1 beyond the plates (zero fill)
+            const bf16* s1 = sv >= 0 ? a.src1 + (size_t)sv * a.c1 : a.src1;
+            const bf16* s2 = sv >= 0 ? a.src2 + (size_t)sv * a.c2 : a.src1;
+            for (int q = 0; q < kb; ++q) {
+                const int c = q * 8;
+                cp_async16(sa + arow + (uint32_t)q * 128u, c < a.c1 ? s1 + c : s2 + (c - a.c1), sv >= 0);
+            }
         }
         const bf16* w = a.w + (size_t)t * COUT * cin;
         for (int i = tid; i < COUT * kb; i += kTcThreads) {
@@ -397,6 +361,7 @@ __global__ void __launch_bounds__(128) conv_bwd_data_kernel(const ConvBwdData a)
     const int v0 = tile * 16;
     if (v0 >= total) return;
     const int vA = v0 + g, vB = v0 + g + 8;
+    const VoxCoord cA = vox_coord(a.d, vA), cB = vox_coord(a.d, vB);
     const int cout = a.cout;
     float acc[CIN / 8][4];
 #pragma unroll
@@ -404,8 +369,8 @@ __global__ void __launch_bounds__(128) conv_bwd_data_kernel(const ConvBwdData a)
     for (int tap = 0; tap < 27; ++tap) {
         const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
         // the output voxel that reads v through this tap sits at v - offset
-        const int sA = shifted(a.d, vA, -dx, -dy, -dz);
-        const int sB = shifted(a.d, vB, -dx, -dy, -dz);
+        const int sA = shifted(a.d, cA, -dx, -dy, -dz);
+        const int sB = shifted(a.d, cB, -dx, -dy, -dz);
         const bf16* wt = a.wt + (size_t)tap * CIN * cout;
         for (int c = 0; c < cout; c += 16) {
             uint32_t fa[4];
@@ -480,6 +445,7 @@ __global__ void __launch_bounds__(256) conv_bwd_w_kernel(const ConvBwdW a)
     const int cout = a.cout;
     bf16* Gs = reinterpret_cast<bf16*>(smem_raw);  // [kWChunkSub][cout]
     bf16* Xs = Gs + kWChunkSub * cout;              // [kWChunkSub][cin]
+    __shared__ int srow[kWChunkSub];                // tap-shifted source voxel of each staged row
     const int tap = blockIdx.y;
     const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
     const int total = a.d.nvox * a.d.batch;
@@ -494,6 +460,10 @@ __global__ void __launch_bounds__(256) conv_bwd_w_kernel(const ConvBwdW a)
     for (int k = 0; k < kMaxTiles; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0.f;
     for (int s0 = vbeg; s0 < vend; s0 += kWChunkSub) {
         __syncthreads();
+        if (threadIdx.x < kWChunkSub) {
+            const int v = s0 + threadIdx.x;
+            srow[threadIdx.x] = v < vend ? shifted(a.d, vox_coord(a.d, v), dx, dy, dz) : -1;
+        }
         for (int e = threadIdx.x; e < kWChunkSub * cout; e += blockDim.x) {
             const int r = e / cout, col = e - r * cout;
             const int v = s0 + r;
@@ -504,15 +474,13 @@ __global__ void __launch_bounds__(256) conv_bwd_w_kernel(const ConvBwdW a)
             }
             Gs[e] = __float2bfloat16_rn(gv);
         }
+        __syncthreads();  // srow
         for (int e = threadIdx.x; e < kWChunkSub * cin; e += blockDim.x) {
             const int r = e / cin, col = e - r * cin;
-            const int v = s0 + r;
+            const int sv = srow[r];
             bf16 xv = __float2bfloat16_rn(0.f);
-            if (v < vend) {
-                const int sv = shifted(a.d, v, dx, dy, dz);
-                if (sv >= 0)
-                    xv = col < a.c1 ? a.src1[(size_t)sv * a.c1 + col] : a.src2[(size_t)sv * a.c2 + (col - a.c1)];
-            }
+            if (sv >= 0)
+                xv = col < a.c1 ? a.src1[(size_t)sv * a.c1 + col] : a.src2[(size_t)sv * a.c2 + (col - a.c1)];
             Xs[e] = xv;
         }
         __syncthreads();

@@ -310,7 +310,7 @@ def main():
     ap.add_argument("--held-out", type=int, default=200)
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--tol", type=float, default=2e-10, help="stop when max |dn/dt| < tol (per LB time unit)")
-    ap.add_argument("--judge-tol", type=float, default=5e-11,
+    ap.add_argument("--judge-tol", type=float, default=1e-11,
                     help="both relaxations continue to this rate before their final fields are compared")
     ap.add_argument("--max-steps", type=int, default=200000)
     ap.add_argument("--out", default=None)
