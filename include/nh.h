@@ -388,14 +388,21 @@ int nh_autotune(nh_ctx* ctx, void* stream, int* chosen);
 /* Use CUDA graphs for whole dt_fd blocks (default on). */
 int nh_set_graphs(nh_ctx* ctx, int on);
 
-/* Diagnostics folded into the LB sweep (default on): every LB launch that
+/* Diagnostics folded into the step (default on): every LB launch that
  * writes u and rho (the steps that feed an FD update or end a call) also
  * leaves per-block FP64 sums of the stored populations, max |u| and the
  * non-finite count, so that nh_diagnostics of that state reads only the
  * director (the energy, |n| and the tube sums) instead of every population,
- * u and rho again.  Applies to F32 and F64 stores without obstacles and
- * without paper_order; the results equal the unfolded ones up to the
- * summation order of the mass.  0 turns it off (drops the cached graphs). */
+ * u and rho again.  When that LB launch is followed by an FD update on the
+ * fused kernels (nh_set_fd_variant 1), the stress kernel of the update also
+ * leaves the director's partials (lattice Frank energy, |n| extrema and
+ * non-finite count, tube sums about the previous centroids), so that
+ * nh_diagnostics of the state right after the update runs only the final
+ * reduction; a change of the centroids in between (nh_set_tubes, or the
+ * tracking of an earlier nh_diagnostics) falls back to the director-only
+ * pass.  Applies to F32 and F64 stores without obstacles and without
+ * paper_order; the results equal the unfolded ones up to the summation
+ * order.  0 turns it off (drops the cached graphs). */
 int nh_set_diag_fold(nh_ctx* ctx, int on);
 
 /* Bound the host-side waits of this context (nh_get_fields, nh_get_populations, nh_get_force,

@@ -46,7 +46,7 @@ size_t store_size(const nh_params& p)
 
 struct Layout {
     size_t f[2], F, Fprev, n, nP, ndot, u, rho, sigma, P3, snap, staging, partials, result, scales, absmax, trig, solid,
-        lbpart, total;
+        lbpart, bpart, tubesd, total;
 };
 
 Layout make_layout(const nh_params& p)
@@ -81,6 +81,10 @@ Layout make_layout(const nh_params& p)
     L.solid = take(N);  // obstacle mask, 1 byte per site (used after nh_set_solid)
     // diagnostics partials of a macro LB launch: [3][blocks], at most one block per 128 sites
     L.lbpart = take(3 * ((N + 127) / 128 + 1) * sizeof(double));
+    // diagnostics partials of the fused stress kernel: [V][blocks], at most one block per 32 x 8 columns and layer
+    const size_t fd_tiles = (size_t)((p.nx + 31) / 32) * ((p.ny + 7) / 8) * p.nz;
+    L.bpart = take(fd_tiles * diag_num_values(NH_MAX_TUBES) * sizeof(double));
+    L.tubesd = take(2 * NH_MAX_TUBES * sizeof(double));  // previous tube centroids on the device
     L.total = off;
     return L;
 }
@@ -235,6 +239,11 @@ struct nh_ctx {
     int diag_fold = 1;        // macro LB launches leave the diagnostics' population, u and rho sums
     int64_t lbp_step = -1;    // step whose state those sums describe (-1: none)
     int lbp_blocks = 0;       // blocks of the launch that wrote them
+    int64_t bdp_step = -1;    // step of the director whose diagnostics partials the fused stress kernel left
+    int bdp_blocks = 0;
+    int64_t tubes_epoch = 0;  // counts changes of the previous tube centroids (tubes, device copy at L.tubesd)
+    int64_t bdp_tubes_epoch = -1;  // the centroids those partials were assigned with
+    bool tubes_dirty = true;       // the device copy lags the host centroids
 
     template <typename T>
     T* at(size_t off) const
@@ -509,13 +518,33 @@ template <typename Real>
 int enqueue_fd(nh_ctx* c, cudaStream_t st)
 {
     auto a = fd_chan<Real>(c);
+    c->bdp_step = -1;
     if (c->fd_fused) {
         // predictor + corrector: n -> nP; stress + force from nP, which is copied back into n
         int r = timed(c, NH_KCLASS_FD_PREDICT, st, [&] { return launch_fd_fused_a<Real>(a, a.n, a.nP, st); },
                       "fd_fused");
         if (r) return r;
-        return timed(c, NH_KCLASS_STRESS, st, [&] { return launch_fd_fused_b<Real>(a, a.nP, a.n, st); },
-                     "stress_force");
+        // after a macro LB launch of this step, the stress kernel also leaves the diagnostics' partials of
+        // the updated director (with the LB launch's population, |u| and non-finite partials folded in)
+        BDiag bd{};
+        const bool dfold = fold_ok(c) && c->lbp_step == c->step;
+        if (dfold) {
+            bd.tubes = c->at<const double>(c->L.tubesd);
+            bd.n_tubes = c->n_tubes;
+            bd.trig = c->at<const double>(c->L.trig);
+            bd.partials = c->at<double>(c->L.bpart);
+            bd.lbpart = c->at<const double>(c->L.lbpart);
+            bd.lbp_blocks = c->lbp_blocks;
+        }
+        r = timed(c, NH_KCLASS_STRESS, st,
+                  [&] { return launch_fd_fused_b<Real>(a, a.nP, a.n, st, dfold ? &bd : nullptr); }, "stress_force");
+        if (r) return r;
+        if (dfold) {
+            c->bdp_step = c->step;
+            c->bdp_blocks = fd_fused_tiles(a);
+            c->bdp_tubes_epoch = c->tubes_epoch;
+        }
+        return NH_OK;
     }
     a.p.n_rate = c->p.n_from_rate;  // the corrector keeps its averaged rate
     int r = enqueue_predict_correct_sites<Real>(c, a, st);
@@ -708,6 +737,17 @@ int encode_all(nh_ctx* c, const double* f, int on_device, cudaStream_t st)
     return NH_OK;
 }
 
+// The previous tube centroids on the device (read where the fused stress
+// kernel leaves the diagnostics partials), refreshed before the next FD update
+// after they changed; a pageable-memory copy, so never inside a graph capture.
+int sync_tubes(nh_ctx* c, cudaStream_t st)
+{
+    if (!c->tubes_dirty) return NH_OK;
+    NH_CUDA(c, cudaMemcpyAsync(c->ws + c->L.tubesd, c->tubes, sizeof(c->tubes), cudaMemcpyHostToDevice, st));
+    c->tubes_dirty = false;
+    return NH_OK;
+}
+
 int enqueue_diag(nh_ctx* c, cudaStream_t st)
 {
     close_segment(c);
@@ -735,6 +775,13 @@ int enqueue_diag(nh_ctx* c, cudaStream_t st)
     a.partials = c->at<double>(c->L.partials);
     a.result = c->at<double>(c->L.result);
     a.blocks = diag_blocks();
+    if (fold_ok(c) && c->lbp_step == c->step && c->bdp_step == c->step && c->bdp_tubes_epoch == c->tubes_epoch) {
+        // the fused stress kernel of this step left every partial: the final reduction alone
+        NH_CUDA(c, launch_diag_final(c->at<const double>(c->L.bpart), a.result, c->bdp_blocks,
+                                     diag_num_values(c->n_tubes), st));
+        c->launches += 1;
+        return NH_OK;
+    }
     if (fold_ok(c) && c->lbp_step == c->step) {  // the last macro LB launch summed f, u and rho of this state
         a.lbpart = c->at<const double>(c->L.lbpart);
         a.lbp_blocks = c->lbp_blocks;
@@ -1279,6 +1326,7 @@ int nh_bind_workspace(nh_ctx* c, void* dev_ptr, size_t bytes)
     }
     c->bound = true;
     c->lbp_step = -1;
+    c->bdp_step = -1;
     c->fields_set = false;
     c->cur = 0;
     c->step = 0;
@@ -1359,6 +1407,7 @@ int nh_set_fields(nh_ctx* c, const double* n, const double* u, const double* rho
     c->fields_set = true;
     c->snap_valid = false;
     c->lbp_step = -1;
+    c->bdp_step = -1;
     return NH_OK;
 }
 
@@ -1419,6 +1468,7 @@ int nh_set_populations(nh_ctx* c, const double* f, int on_device)
     }
     if (r) return r;
     c->lbp_step = -1;
+    c->bdp_step = -1;
     NH_CUDA(c, cudaStreamSynchronize(c->stream));
     return NH_OK;
 }
@@ -1466,6 +1516,7 @@ int nh_restore(nh_ctx* c, const double* n, const double* F, const double* u, con
     c->fields_set = true;
     c->snap_valid = false;
     c->lbp_step = -1;
+    c->bdp_step = -1;
     NH_CUDA(c, cudaStreamSynchronize(st));
     return NH_OK;
 }
@@ -1479,6 +1530,7 @@ int nh_step(nh_ctx* c, int64_t n_lb_steps, void* stream)
     if (n_lb_steps < 0) return fail(c, NH_EINVAL, "n_lb_steps must be >= 0");
     if ((r = set_device(c))) return r;
     cudaStream_t st = pick(c, stream);
+    if ((r = sync_tubes(c, st))) return r;
     const int dt = c->p.dt_fd;
     int64_t left = n_lb_steps;
     while (left > 0) {
@@ -1495,6 +1547,15 @@ int nh_step(nh_ctx* c, int64_t n_lb_steps, void* stream)
             if (fold_ok(c)) {  // the block ends with a macro LB launch (an FD step)
                 c->lbp_step = c->step;
                 c->lbp_blocks = lb_blocks(c->lb_variant, c->N);
+                c->bdp_step = -1;
+                if (c->fd_fused) {  // ... and its fused stress kernel left the director's partials
+                    c->bdp_step = c->step;
+                    c->bdp_blocks = c->p.precision == NH_FP64 ? fd_fused_tiles(fd_chan<double>(c))
+                                                             : fd_fused_tiles(fd_chan<float>(c));
+                    c->bdp_tubes_epoch = c->tubes_epoch;
+                }
+            } else {
+                c->bdp_step = -1;
             }
         } else {
             r = enqueue_one_step(c, left == 1, st);
@@ -1513,6 +1574,7 @@ int nh_fd_update(nh_ctx* c, void* stream)
     if (r) return r;
     if (!c->fields_set) return fail(c, NH_EINVAL, "nh_set_fields must be called before nh_fd_update");
     if ((r = set_device(c))) return r;
+    if ((r = sync_tubes(c, pick(c, stream)))) return r;
     r = enqueue_fd_any(c, pick(c, stream));
     close_segment(c);
     return r;
@@ -1607,6 +1669,7 @@ int nh_relax(nh_ctx* c, int64_t n_fd_steps, void* stream)
     if ((r = set_device(c))) return r;
     cudaStream_t st = pick(c, stream);
     c->lbp_step = -1;  // u is cleared
+    c->bdp_step = -1;
     NH_CUDA(c, cudaMemsetAsync(c->ws + c->L.u, 0, 3 * (size_t)c->N * real_size(c->p), st));
     if (c->fd_fused) {
         r = c->p.precision == NH_FP64 ? relax_fused<double>(c, n_fd_steps, st) : relax_fused<float>(c, n_fd_steps, st);
@@ -1629,6 +1692,7 @@ int nh_batch_relax(nh_ctx* const* ctxs, int count, int64_t n_fd_steps, void* str
     cudaStream_t st = pick(c0, stream);
     for (nh_ctx* c : plan->ctxs) {
         c->lbp_step = -1;  // u is cleared
+        c->bdp_step = -1;
         cudaError_t e = cudaMemsetAsync(c->ws + c->L.u, 0, 3 * (size_t)c->N * real_size(c->p), st);
         if (e != cudaSuccess) return fail(nullptr, NH_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
     }
@@ -1678,6 +1742,7 @@ int nh_symmetrize_c4(nh_ctx* c)
         NH_CUDA(c, launch_symmetrize_c4<float>(c->at<float>(c->L.n), c->at<float>(c->L.nP), c->p.nx, c->p.nz, st));
     c->launches += 1;
     NH_CUDA(c, cudaMemcpyAsync(c->ws + c->L.n, c->ws + c->L.nP, bytes, cudaMemcpyDeviceToDevice, st));
+    c->bdp_step = -1;  // the director changed
     return NH_OK;
 }
 
@@ -1689,6 +1754,7 @@ int nh_set_solid(nh_ctx* c, const uint8_t* mask, int on_device)
     cudaStream_t st = c->stream;
     drop_graphs(c);
     c->lbp_step = -1;
+    c->bdp_step = -1;
     if (!mask) {
         c->has_solid = false;
     } else {
@@ -1716,11 +1782,14 @@ int nh_set_tubes(nh_ctx* c, const double* centres, int count)
     if (!c) return fail(nullptr, NH_EINVAL, "ctx is NULL");
     if (count < 0 || count > NH_MAX_TUBES) return fail(c, NH_EINVAL, "tube count out of range");
     if (count > 0 && !centres) return fail(c, NH_EINVAL, "centres is NULL");
+    if (count != c->n_tubes) drop_graphs(c);  // a captured stress kernel carries the tube count
     c->n_tubes = count;
     for (int k = 0; k < count; ++k) {
         c->tubes[k][0] = centres[2 * k];
         c->tubes[k][1] = centres[2 * k + 1];
     }
+    c->tubes_dirty = true;
+    c->tubes_epoch += 1;
     return NH_OK;
 }
 
@@ -1774,6 +1843,8 @@ int nh_diagnostics_read(nh_ctx* c, nh_diag* out)
         if (t[0] > 0 && k < c->n_tubes) {
             c->tubes[k][0] = cx;
             c->tubes[k][1] = cy;
+            c->tubes_dirty = true;
+            c->tubes_epoch += 1;
         }
     }
     if (out->nonfinite > 0) return fail(c, NH_EUNSTABLE, "non-finite values in n, u, rho or f");
@@ -1839,6 +1910,7 @@ int nh_set_diag_fold(nh_ctx* c, int on)
     if (on != c->diag_fold) drop_graphs(c);  // the captured LB launches change
     c->diag_fold = on;
     c->lbp_step = -1;
+    c->bdp_step = -1;
     return NH_OK;
 }
 

@@ -17,7 +17,7 @@
 // on the two plate layers the chiral term lacks the link to the ghost layer,
 // which the central curl over the copied ghost would contribute; the kernels
 // take that link out again (free_plate_side).
-#include "nh_internal.cuh"
+#include "diag_sum.cuh"
 
 namespace nh {
 
@@ -731,6 +731,23 @@ __device__ __forceinline__ void st_pt(double* slot, int i, const double v[6])
     for (int k = 0; k < 3; ++k) reinterpret_cast<double2*>(slot + 2 * k * kP2)[i] = make_double2(v[2 * k], v[2 * k + 1]);
 }
 
+// The director alone of point i of an input plane slot: one vector load in
+// FP32 (the float4 holds n0 n1 n2 u0), two in FP64.
+__device__ __forceinline__ void ld_n(const float* slot, int i, float n[3])
+{
+    const float4 a = reinterpret_cast<const float4*>(slot)[i];
+    n[0] = a.x;
+    n[1] = a.y;
+    n[2] = a.z;
+}
+__device__ __forceinline__ void ld_n(const double* slot, int i, double n[3])
+{
+    const double2 a = reinterpret_cast<const double2*>(slot)[i];
+    n[0] = a.x;
+    n[1] = a.y;
+    n[2] = reinterpret_cast<const double2*>(slot + 2 * kP2)[i].x;
+}
+
 // Predictor ring slot (4 kP1 Reals): n^P of a point as one float4 (n0 n1 n2 -)
 // in FP32, as three planes of kP1 doubles in FP64.
 __device__ __forceinline__ void ld3(const float* slot, int i, float v[3])
@@ -1045,8 +1062,14 @@ __device__ __forceinline__ void stress_plane(const FDChan<Real>& c, int p, const
     }
 }
 
-template <typename Real, bool Solid = false>
-__device__ void fused_b_tile(const FDChan<Real>& c, const Real* __restrict__ nin, Real* __restrict__ ncopy, int tile)
+// Diag: the kernel also leaves the diagnostics' block partials of the updated
+// director it holds (BDiag): per own site the lattice link energy to its x+1,
+// y+1 and z+1 neighbours (and from the lower ghost layer at a homeotropic
+// plate), the site terms, |n| and the tube weight (1 - n_z)/2, as the
+// director-only diagnostics kernels sum them.
+template <typename Real, bool Solid = false, bool Diag = false>
+__device__ void fused_b_tile(const FDChan<Real>& c, const Real* __restrict__ nin, Real* __restrict__ ncopy, int tile,
+                             const BDiag* bd = nullptr)
 {
     extern __shared__ __align__(16) unsigned char smem_fd[];
     Real* in = reinterpret_cast<Real*>(smem_fd);  // 3 slots x 6 x kP2 (input planes)
@@ -1086,6 +1109,8 @@ __device__ void fused_b_tile(const FDChan<Real>& c, const Real* __restrict__ nin
     __syncthreads();
     stress_plane(c, zb, IN(s1), IN(s2), IN(s0), SG(zb), i1, i2, true, szmid, MK(s2));
     int sa = s1, sb = s2, sc = s0;  // input slots of planes z - 1, z, z + 1 (plane z + 2 takes sa)
+    Real d_e = 0, d_w = 0, d_mn = Real(1e30), d_mx = 0;  // Diag: energy, tube weight, |n| extrema of the column
+    int d_bad = 0;
     for (int z = zb; z < ze; ++z) {
         __syncthreads();  // plane z - 1 is no longer read; its slots take planes z + 2 (input), z + 1 (sigma)
         commit_plane<Real, Solid>(pm, v, IN(sa), sv, mk + sa * kP2);
@@ -1110,11 +1135,33 @@ __device__ void fused_b_tile(const FDChan<Real>& c, const Real* __restrict__ nin
                 c.F[a * N + s] = (Solid && MK(sb)[i2]) ? Real(0)  // no force on an obstacle node
                                                         : Real(0.5) * ((xp[a] - xm[a]) + (yp[a] - ym[a]) + (hi - lo));
             }
-            if (ncopy) {
+            if (ncopy || Diag) {
                 Real n0[3], u0[3];
                 split_pt(IN(sb), i2, n0, u0);
+                if (ncopy) {
 #pragma unroll
-                for (int a = 0; a < 3; ++a) ncopy[a * N + s] = n0[a];
+                    for (int a = 0; a < 3; ++a) ncopy[a * N + s] = n0[a];
+                }
+                if constexpr (Diag) {
+                    const Real K = c.p.K, q0 = c.p.q0;
+                    Real nx[3], ny[3], nz[3];
+                    ld_n(IN(sb), i2 + 1, nx);
+                    ld_n(IN(sb), i2 + kHX2, ny);
+                    ld_n(IN(sc), i2, nz);  // plane z + 1 (the ghost layer above the top plate)
+                    Real e = dsum::link_energy(n0, nx, 0, K, q0);
+                    e += dsum::link_energy(n0, ny, 1, K, q0);
+                    e += dsum::link_energy(n0, nz, 2, K, q0);
+                    if (g.walls && z == 0 && g.anchoring == NH_ANCHOR_HOMEOTROPIC) {
+                        const Real zh[3] = {Real(0), Real(0), Real(1)};  // the ghost layer below
+                        e += dsum::link_energy(zh, n0, 2, K, q0);
+                    }
+                    d_e += e + (Real(0.5) * K * q0 * q0 - Real(0.5) * c.p.W0 * (n0[2] * n0[2]));
+                    const Real nm = dsum::norm3(n0);
+                    d_mn = min(d_mn, nm);
+                    d_mx = max(d_mx, nm);
+                    d_bad += !isfinite(nm) ? 1 : 0;
+                    d_w += Real(0.5) * (Real(1) - n0[2]);
+                }
             }
         }
 #pragma unroll
@@ -1126,6 +1173,31 @@ __device__ void fused_b_tile(const FDChan<Real>& c, const Real* __restrict__ nin
         sa = sb;
         sb = sc;
         sc = t;
+    }
+    if constexpr (Diag) {
+        // the planes are no longer read: the per-warp tube sums and the
+        // previous centroids take the start of the dynamic shared memory
+        const int T = bd->n_tubes;
+        __syncthreads();
+        Real(*tube_acc)[NH_MAX_TUBES * 5] = reinterpret_cast<Real(*)[NH_MAX_TUBES * 5]>(smem_fd);
+        float(*txy)[2] = reinterpret_cast<float(*)[2]>(smem_fd + sizeof(Real) * (kFusedThreads / 32) * NH_MAX_TUBES * 5);
+        for (int k = threadIdx.x; k < (kFusedThreads / 32) * NH_MAX_TUBES * 5; k += blockDim.x) (&tube_acc[0][0])[k] = Real(0);
+        for (int k = threadIdx.x; k < T; k += blockDim.x) {
+            txy[k][0] = (float)bd->tubes[2 * k];
+            txy[k][1] = (float)bd->tubes[2 * k + 1];
+        }
+        __syncthreads();
+        if (T > 0) {
+            int owner = -1;
+            Real v[5] = {0, 0, 0, 0, 0};
+            if (active) {
+                owner = dsum::nearest_tube(g, bd->tubes, txy, T, x0 + tx, y0 + ty);
+                dsum::tube_values(g, bd->trig, x0 + tx, y0 + ty, d_w, v);
+            }
+            dsum::warp_tube_accumulate(owner, v, threadIdx.x & 31, tube_acc[threadIdx.x >> 5]);
+        }
+        dsum::block_partials<kFusedThreads>(bd->partials, bd->lbpart, bd->lbp_blocks, Real(0), d_e, Real(0), d_mn,
+                                            d_mx, d_bad, tube_acc, T);
     }
 }
 
@@ -1141,6 +1213,13 @@ template <typename Real, bool Solid>
 __global__ void __launch_bounds__(kFusedThreads, sizeof(Real) == 4 ? 4 : 2) fused_b_kernel(const FDChan<Real> c, const Real* nin, Real* ncopy)
 {
     fused_b_tile<Real, Solid>(c, nin, ncopy, blockIdx.x);
+}
+// The same with the diagnostics partials of the updated director (no obstacles).
+template <typename Real>
+__global__ void __launch_bounds__(kFusedThreads, sizeof(Real) == 4 ? 4 : 2)
+    fused_b_diag_kernel(const FDChan<Real> c, const Real* nin, Real* ncopy, const BDiag bd)
+{
+    fused_b_tile<Real, false, true>(c, nin, ncopy, blockIdx.x, &bd);
 }
 
 // Batched fused kernels: a persistent grid walks the (channel, tile) work
@@ -1188,6 +1267,7 @@ cudaError_t prepare_fused()
     if (e == cudaSuccess) e = cudaFuncSetAttribute(fused_a_kernel<Real, true>, attr, a);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(fused_b_kernel<Real, false>, attr, b);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(fused_b_kernel<Real, true>, attr, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fused_b_diag_kernel<Real>, attr, b);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(fused_batch_kernel<Real, 0, false>, attr, a);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(fused_batch_kernel<Real, 0, true>, attr, a);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(fused_batch_kernel<Real, 1, false>, attr, b);
@@ -1271,15 +1351,25 @@ cudaError_t launch_fd_fused_a(const FDChan<Real>& c, const Real* nin, Real* nout
 }
 
 template <typename Real>
-cudaError_t launch_fd_fused_b(const FDChan<Real>& c, const Real* nin, Real* ncopy, cudaStream_t st)
+cudaError_t launch_fd_fused_b(const FDChan<Real>& c, const Real* nin, Real* ncopy, cudaStream_t st, const BDiag* diag)
 {
     cudaError_t e = prepare_fused<Real>();
     if (e != cudaSuccess) return e;
-    if (c.solid != nullptr)
+    if (diag != nullptr) {
+        if (c.solid != nullptr || diag->n_tubes < 0 || diag->n_tubes > NH_MAX_TUBES) return cudaErrorInvalidValue;
+        fused_b_diag_kernel<Real><<<fused_tiles(c), kFusedThreads, fused_b_smem<Real>(), st>>>(c, nin, ncopy, *diag);
+    } else if (c.solid != nullptr) {
         fused_b_kernel<Real, true><<<fused_tiles(c), kFusedThreads, fused_b_smem<Real>(), st>>>(c, nin, ncopy);
-    else
+    } else {
         fused_b_kernel<Real, false><<<fused_tiles(c), kFusedThreads, fused_b_smem<Real>(), st>>>(c, nin, ncopy);
+    }
     return cudaGetLastError();
+}
+
+template <typename Real>
+int fd_fused_tiles(const FDChan<Real>& c)
+{
+    return fused_tiles(c);
 }
 
 template <typename Real>
@@ -1318,8 +1408,11 @@ cudaError_t launch_fd_fused_batch(FDBatch<Real>& b, int stage, int grid, cudaStr
 
 template cudaError_t launch_fd_fused_a<double>(const FDChan<double>&, const double*, double*, cudaStream_t);
 template cudaError_t launch_fd_fused_a<float>(const FDChan<float>&, const float*, float*, cudaStream_t);
-template cudaError_t launch_fd_fused_b<double>(const FDChan<double>&, const double*, double*, cudaStream_t);
-template cudaError_t launch_fd_fused_b<float>(const FDChan<float>&, const float*, float*, cudaStream_t);
+template cudaError_t launch_fd_fused_b<double>(const FDChan<double>&, const double*, double*, cudaStream_t,
+                                                const BDiag*);
+template int fd_fused_tiles<double>(const FDChan<double>&);
+template cudaError_t launch_fd_fused_b<float>(const FDChan<float>&, const float*, float*, cudaStream_t, const BDiag*);
+template int fd_fused_tiles<float>(const FDChan<float>&);
 template cudaError_t launch_fd_fused_batch<double>(FDBatch<double>&, int, int, cudaStream_t);
 template cudaError_t launch_fd_fused_batch<float>(FDBatch<float>&, int, int, cudaStream_t);
 

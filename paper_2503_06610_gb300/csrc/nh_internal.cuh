@@ -173,6 +173,21 @@ struct FDChan {
     int zch = 0;  // layers per chunk of the fused kernels; 0: chosen from g alone
 };
 
+// Diagnostics folded into the stress kernel (fused B) of an FD update that
+// follows a macro LB launch: per-block partials of the lattice Frank energy,
+// the |n| extrema, the non-finite director count and the tube sums of the
+// updated director, laid out as the diagnostics kernels' partials
+// ([V][blocks]), each block also taking its slice of the LB launch's
+// population, max |u| and non-finite partials.
+struct BDiag {
+    const double* tubes;   // [n_tubes][2] previous centroids (device)
+    int n_tubes;
+    const double* trig;    // FP64 sin/cos tables of the column positions
+    double* partials;
+    const double* lbpart;  // [3][lbp_blocks]
+    int lbp_blocks;
+};
+
 // ------------------------------------------------------------------ launchers (host)
 // Batched launches: up to kMaxBatch channel descriptors travel as kernel
 // parameters (no device allocation); prefix[k] is the first tile of channel k.
@@ -214,7 +229,10 @@ cudaError_t launch_fd_batch(FDBatch<Real>& b, int stage, int grid, cudaStream_t 
 template <typename Real>
 cudaError_t launch_fd_fused_a(const FDChan<Real>& c, const Real* nin, Real* nout, cudaStream_t s);
 template <typename Real>
-cudaError_t launch_fd_fused_b(const FDChan<Real>& c, const Real* nin, Real* ncopy, cudaStream_t s);
+cudaError_t launch_fd_fused_b(const FDChan<Real>& c, const Real* nin, Real* ncopy, cudaStream_t s,
+                              const BDiag* diag = nullptr);
+template <typename Real>
+int fd_fused_tiles(const FDChan<Real>& c);  // blocks of a single-channel fused launch
 template <typename Real>
 cudaError_t launch_fd_fused_batch(FDBatch<Real>& b, int stage, int grid, cudaStream_t s);
 
@@ -276,6 +294,8 @@ struct DiagArgs {
 int diag_num_values(int n_tubes);
 int diag_blocks();
 cudaError_t launch_diagnostics(const DiagArgs& a, cudaStream_t s);
+// The final reduction alone, over partials [V][blocks] that another kernel left.
+cudaError_t launch_diag_final(const double* partials, double* result, int blocks, int V, cudaStream_t s);
 cudaError_t launch_trig_table(double* t, int nx, int ny, cudaStream_t s);
 
 // max |n - snap| over sites into *out (device), then snap <- n (diag.cu)

@@ -339,8 +339,7 @@ __global__ void __launch_bounds__(kTcThreads) conv_fwd_tc_kernel(const ConvFwd a
 // ------------------------------------------------------------------ convolution: data gradient
 
 struct ConvBwdData {
-    const float* gout;  // [vox][cout] gradient of the layer output (post-ReLU)
-    const bf16* out;    // [vox][cout] layer output, for the ReLU mask
+    const bf16* gp;     // [vox][cout] gradient of the pre-activation (ReLU mask applied), BF16
     const bf16* wt;     // [27][cin][cout] transposed weights
     float* dst1;        // [vox][c1] gradient of source 1 (overwritten)
     int c1;
@@ -348,7 +347,6 @@ struct ConvBwdData {
     int c2;
     int cout;
     Dims d;
-    int relu;
 };
 
 template <int CIN>
@@ -377,21 +375,7 @@ __global__ void __launch_bounds__(128) conv_bwd_data_kernel(const ConvBwdData a)
             const int cols[4] = {c + 2 * t, c + 2 * t, c + 8 + 2 * t, c + 8 + 2 * t};
             const int src[4] = {sA, sB, sA, sB};
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                float g0 = 0.f, g1 = 0.f;
-                if (src[q] >= 0) {
-                    const size_t o = (size_t)src[q] * cout + cols[q];
-                    const float2 gv = *reinterpret_cast<const float2*>(a.gout + o);
-                    g0 = gv.x;
-                    g1 = gv.y;
-                    if (a.relu) {
-                        const __nv_bfloat162 y = *reinterpret_cast<const __nv_bfloat162*>(a.out + o);
-                        g0 = __bfloat162float(y.x) > 0.f ? g0 : 0.f;
-                        g1 = __bfloat162float(y.y) > 0.f ? g1 : 0.f;
-                    }
-                }
-                fa[q] = pack_bf16(g0, g1);
-            }
+            for (int q = 0; q < 4; ++q) fa[q] = src[q] >= 0 ? ld_pair(a.gp + (size_t)src[q] * cout + cols[q]) : 0u;
 #pragma unroll
             for (int j = 0; j < CIN / 8; ++j) {
                 const bf16* wr = wt + (size_t)(j * 8 + g) * cout + c;
@@ -422,8 +406,7 @@ __global__ void __launch_bounds__(128) conv_bwd_data_kernel(const ConvBwdData a)
 // ------------------------------------------------------------------ convolution: weight gradient
 
 struct ConvBwdW {
-    const float* gout;  // [vox][cout]
-    const bf16* out;    // [vox][cout] for the ReLU mask
+    const bf16* gp;     // [vox][cout] gradient of the pre-activation (ReLU mask applied), BF16
     const bf16* src1;   // [vox][c1]
     int c1;
     const bf16* src2;   // [vox][c2]
@@ -431,7 +414,6 @@ struct ConvBwdW {
     int cout;
     float* gw;          // [27][cout][cin] (accumulated)
     Dims d;
-    int relu;
     int chunk;          // voxels per block
 };
 
@@ -464,24 +446,25 @@ __global__ void __launch_bounds__(256) conv_bwd_w_kernel(const ConvBwdW a)
             const int v = s0 + threadIdx.x;
             srow[threadIdx.x] = v < vend ? shifted(a.d, vox_coord(a.d, v), dx, dy, dz) : -1;
         }
-        for (int e = threadIdx.x; e < kWChunkSub * cout; e += blockDim.x) {
-            const int r = e / cout, col = e - r * cout;
+        // 16-byte groups of 8 channels (cout, c1 and c2 are multiples of 8)
+        const int cg = cout >> 3;
+        for (int e = threadIdx.x; e < kWChunkSub * cg; e += blockDim.x) {
+            const int r = e / cg, q = e - r * cg;
             const int v = s0 + r;
-            float gv = 0.f;
-            if (v < vend) {
-                gv = a.gout[(size_t)v * cout + col];
-                if (a.relu && !(__bfloat162float(a.out[(size_t)v * cout + col]) > 0.f)) gv = 0.f;
-            }
-            Gs[e] = __float2bfloat16_rn(gv);
+            uint4 gv = make_uint4(0u, 0u, 0u, 0u);
+            if (v < vend) gv = __ldg(reinterpret_cast<const uint4*>(a.gp + (size_t)v * cout) + q);
+            reinterpret_cast<uint4*>(Gs)[e] = gv;
         }
         __syncthreads();  // srow
-        for (int e = threadIdx.x; e < kWChunkSub * cin; e += blockDim.x) {
-            const int r = e / cin, col = e - r * cin;
+        const int ig = cin >> 3, ig1 = a.c1 >> 3;
+        for (int e = threadIdx.x; e < kWChunkSub * ig; e += blockDim.x) {
+            const int r = e / ig, q = e - r * ig;
             const int sv = srow[r];
-            bf16 xv = __float2bfloat16_rn(0.f);
+            uint4 xv = make_uint4(0u, 0u, 0u, 0u);
             if (sv >= 0)
-                xv = col < a.c1 ? a.src1[(size_t)sv * a.c1 + col] : a.src2[(size_t)sv * a.c2 + (col - a.c1)];
-            Xs[e] = xv;
+                xv = q < ig1 ? __ldg(reinterpret_cast<const uint4*>(a.src1 + (size_t)sv * a.c1) + q)
+                             : __ldg(reinterpret_cast<const uint4*>(a.src2 + (size_t)sv * a.c2) + (q - ig1));
+            reinterpret_cast<uint4*>(Xs)[e] = xv;
         }
         __syncthreads();
         for (int kk = 0; kk < kWChunkSub; kk += 16) {
@@ -515,19 +498,49 @@ __global__ void __launch_bounds__(256) conv_bwd_w_kernel(const ConvBwdW a)
     }
 }
 
-// bias gradient: gb[co] += sum_v G'[v][co]
-__global__ void bias_grad_kernel(const float* __restrict__ gout, const bf16* __restrict__ out, float* gb, int cout,
-                                 int total, int relu)
+// Gradient of the pre-activation, once per layer: gp = BF16(gout masked by
+// the ReLU, out > 0), the operand of both convolution gradients; and the
+// bias gradient gb[co] += sum_v of the masked gout (FP32).  A thread takes
+// 8-channel groups of voxels (32-byte gout loads, 16-byte stores); the grid
+// stride is a multiple of cout/8, so a thread's group -- and its 8 bias
+// partials -- stay fixed; the block sums them in shared memory and adds
+// them to gb with one atomic per channel.
+__global__ void __launch_bounds__(256) grad_prep_kernel(const float* __restrict__ gout, const bf16* __restrict__ out,
+                                                        bf16* __restrict__ gp, float* gb, int cout, int total)
 {
-    const int co = threadIdx.x % cout;
-    const int lanes = blockDim.x / cout;
-    float s = 0.f;
-    for (int v = blockIdx.x * lanes + threadIdx.x / cout; v < total; v += gridDim.x * lanes) {
-        float gv = gout[(size_t)v * cout + co];
-        if (relu && !(__bfloat162float(out[(size_t)v * cout + co]) > 0.f)) gv = 0.f;
-        s += gv;
+    __shared__ float bsum[64];
+    const int cg = cout >> 3;
+    for (int k = threadIdx.x; k < cout; k += blockDim.x) bsum[k] = 0.f;
+    __syncthreads();
+    const int64_t items = (int64_t)total * cg;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = (int)(i0 % cg);  // fixed: stride % cg == 0
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int64_t i = i0; i < items; i += stride) {
+        const float4 g0 = __ldg(reinterpret_cast<const float4*>(gout) + 2 * i);
+        const float4 g1 = __ldg(reinterpret_cast<const float4*>(gout) + 2 * i + 1);
+        const uint4 y = __ldg(reinterpret_cast<const uint4*>(out) + i);
+        const __nv_bfloat162* yh = reinterpret_cast<const __nv_bfloat162*>(&y);
+        float g[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (!(__low2float(yh[k]) > 0.f)) g[2 * k] = 0.f;
+            if (!(__high2float(yh[k]) > 0.f)) g[2 * k + 1] = 0.f;
+        }
+        uint4 o;
+        o.x = pack_bf16(g[0], g[1]);
+        o.y = pack_bf16(g[2], g[3]);
+        o.z = pack_bf16(g[4], g[5]);
+        o.w = pack_bf16(g[6], g[7]);
+        reinterpret_cast<uint4*>(gp)[i] = o;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] += g[k];
     }
-    if (threadIdx.x < lanes * cout) atomicAdd(&gb[co], s);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) atomicAdd(&bsum[q * 8 + k], acc[k]);
+    __syncthreads();
+    for (int k = threadIdx.x; k < cout; k += blockDim.x) atomicAdd(&gb[k], bsum[k]);
 }
 
 // ------------------------------------------------------------------ pooling / upsampling
@@ -751,7 +764,7 @@ struct nh_unet {
     size_t ws_bytes = 0;
     size_t need = 0;
     // offsets into the workspace
-    size_t wbf, wt[kLayers], x, act[kLayers], pool_[3], up_[3], grad_a, grad_b, grad_skip[3], gd1, status;
+    size_t wbf, wt[kLayers], x, act[kLayers], pool_[3], up_[3], grad_a, grad_b, grad_skip[3], gd1, gprep, status;
     std::string err;
 };
 
@@ -796,6 +809,10 @@ void plan(nh_unet* u)
     const int skip_c[3] = {16, 16, 32};
     for (int k = 0; k < 3; ++k) u->grad_skip[k] = take((size_t)u->lv[k].nvox * u->batch * skip_c[k] * sizeof(float));
     u->gd1 = take(V0 * kHeadIn * sizeof(float));
+    size_t gp_max = 0;  // BF16 pre-activation gradient of the largest layer output
+    for (int l = 0; l < kLayers; ++l)
+        gp_max = std::max(gp_max, (size_t)u->lv[level_of[l]].nvox * u->batch * kConv[l].cout);
+    u->gprep = take(gp_max * sizeof(bf16));
     u->status = take(sizeof(int));  // raised by an expired wait of the tensor-core convolution
     u->need = off;
 }
@@ -853,9 +870,13 @@ cudaError_t conv_bwd(nh_unet* u, int l, int level, const float* gout, const bf16
     const int total = d.nvox * d.batch;
     const int cout = kConv[l].cout, cin = kConv[l].cin;
     const bf16* out = P<bf16>(u, u->act[l]);
+    bf16* gp = P<bf16>(u, u->gprep);
+    grad_prep_kernel<<<std::min(4 * 152, grid_for(total * (cout / 8), 256)), 256, 0, st>>>(
+        gout, out, gp, grad + layer_offset(l) + 27LL * cin * cout, cout, total);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     ConvBwdW w;
-    w.gout = gout;
-    w.out = out;
+    w.gp = gp;
     w.src1 = s1;
     w.c1 = c1;
     w.src2 = s2;
@@ -863,20 +884,14 @@ cudaError_t conv_bwd(nh_unet* u, int l, int level, const float* gout, const bf16
     w.cout = cout;
     w.gw = grad + layer_offset(l);
     w.d = d;
-    w.relu = 1;
     w.chunk = 1024;
     dim3 grid((total + w.chunk - 1) / w.chunk, 27);
     const size_t smem = (size_t)kWChunkSub * (cin + cout) * sizeof(bf16);
     conv_bwd_w_kernel<<<grid, 256, smem, st>>>(w);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    bias_grad_kernel<<<std::min(64, grid_for(total / 8, 256)), 256, 0, st>>>(
-        gout, out, grad + layer_offset(l) + 27LL * cin * cout, cout, total, 1);
     e = cudaGetLastError();
     if (e != cudaSuccess || !need_data) return e;
     ConvBwdData b;
-    b.gout = gout;
-    b.out = out;
+    b.gp = gp;
     b.wt = P<bf16>(u, u->wt[l]);
     b.dst1 = dst1;
     b.c1 = c1;
@@ -884,7 +899,6 @@ cudaError_t conv_bwd(nh_unet* u, int l, int level, const float* gout, const bf16
     b.c2 = c2;
     b.cout = cout;
     b.d = d;
-    b.relu = 1;
     const int blocks = (total / 16 + 3) / 4;
     switch (cin) {
     case 16: conv_bwd_data_kernel<16><<<blocks, 128, 0, st>>>(b); break;
