@@ -146,13 +146,18 @@ __device__ __forceinline__ void block_partials(double* partials, const double* l
 {
     __shared__ double red[Threads / 32][DIAG_FIXED];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    double dmax_u = (double)max_u, dmin_nn = (double)min_nn, dmax_nn = (double)max_nn, dbad = (double)bad;
-    double mass = warp_sum((double)mass_t);
-    double energy = warp_sum((double)energy_t);
-    dbad = warp_sum(dbad);
-    dmax_u = warp_max(dmax_u);
-    dmin_nn = warp_min(dmin_nn);
-    dmax_nn = warp_max(dmax_nn);
+    // within a warp: sums in the build's precision, extrema exactly, the count
+    // in integers (GB300's FP64 pipe is narrow); FP64 across the warps below
+    const double mass = (double)warp_sum(mass_t);
+    const double energy = (double)warp_sum(energy_t);
+    const double dbad = (double)__reduce_add_sync(0xffffffffu, (unsigned)bad);
+    Real mu = max_u, mn = min_nn, mx = max_nn;
+    for (int o = 16; o > 0; o >>= 1) {
+        mu = max(mu, __shfl_xor_sync(0xffffffffu, mu, o));
+        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    const double dmax_u = (double)mu, dmin_nn = (double)mn, dmax_nn = (double)mx;
     if (lane == 0) {
         red[wid][0] = mass;
         red[wid][1] = energy;
