@@ -127,6 +127,7 @@ struct ConvFwd {
     Dims d;
     int relu;
     int* status;       // set to 1 when a bounded wait of the tensor-core kernel expires
+    int tps;           // taps per shared-memory stage of the tensor-core kernel (1..9)
 };
 
 // ------------------------------------------------------------------ convolution: forward on tcgen05
@@ -137,11 +138,12 @@ struct ConvFwd {
 // are copied into shared memory with 16-byte cp.async (zero rows where the tap
 // leaves the volume in z) in the tensor core's no-swizzle K-major layout:
 // core matrices of 8 rows x 16 bytes, adjacent core matrices along K 128 bytes
-// apart (LBO), along M / N cin/8 x 128 bytes apart (SBO).  One thread issues
-// the cin/16 MMAs of the tap (tcgen05.mma kind::f16, BF16 x BF16 -> FP32,
-// M = 128, N = COUT, K = 16) into a TMEM accumulator and commits them to the
-// stage's mbarrier; two stages let the copies of the next tap overlap the MMAs
-// of this one.  The epilogue reads each warp's 32 accumulator rows with
+// apart (LBO), along M / N cin/8 x 128 bytes apart (SBO).  A stage holds tps
+// consecutive taps (tc_taps_per_stage: as many as fit in 14 KB, 1 to 9);
+// one thread issues their cin/16 MMAs each (tcgen05.mma kind::f16, BF16 x
+// BF16 -> FP32, M = 128, N = COUT, K = 16) into a TMEM accumulator and commits
+// them to the stage's mbarrier; two stages let the copies of the next taps
+// overlap the MMAs of these.  The epilogue reads each warp's 32 accumulator rows with
 // tcgen05.ld, adds the bias, applies the ReLU and stores BF16 rows.  Every
 // mbarrier wait is bounded: on expiry the kernel raises a.status, skips the
 // epilogue, waits for its copies and frees its TMEM.
@@ -150,7 +152,18 @@ constexpr int kTcM = 128;
 constexpr int kTcThreads = 128;
 constexpr int kTcMaxCin = 96;
 constexpr int kTcMaxCout = 64;
-constexpr size_t kTcSmem = 2 * (size_t)(kTcM + kTcMaxCout) * kTcMaxCin * sizeof(bf16) + 64;
+// A stage holds as many taps as fit in kTcStageBytes (at least one, at most 9:
+// one dz plane of the stencil), so that thin layers commit a K of several
+// taps per barrier round trip while several CTAs still fit on an SM.
+constexpr size_t kTcStageBytes = 14 * 1024;
+constexpr size_t kTcWidestTap = (size_t)(kTcM + kTcMaxCout) * kTcMaxCin * sizeof(bf16);
+constexpr size_t kTcSmem = 2 * (kTcWidestTap > kTcStageBytes ? kTcWidestTap : kTcStageBytes) + 64;
+inline int tc_taps_per_stage(int cin, int cout)
+{
+    const size_t tap = (size_t)(kTcM + cout) * cin * sizeof(bf16);
+    const int t = (int)(kTcStageBytes / tap);
+    return t < 1 ? 1 : (t > 9 ? 9 : t);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
@@ -213,8 +226,11 @@ __global__ void __launch_bounds__(kTcThreads) conv_fwd_tc_kernel(const ConvFwd a
     const int kb = cin / 8;                        // 16-byte core-matrix columns along K
     const uint32_t sbo_a = (uint32_t)kb * 128u;    // between 8-row groups
     const uint32_t a_bytes = kTcM * cin * 2, b_bytes = COUT * cin * 2;
-    unsigned char* stage[2] = {tc_smem, tc_smem + a_bytes + b_bytes};
-    uint64_t* bars = reinterpret_cast<uint64_t*>(tc_smem + 2 * (a_bytes + b_bytes));
+    const int tps = a.tps;                              // taps per stage
+    const uint32_t tap_bytes = a_bytes + b_bytes, stage_bytes = (uint32_t)tps * tap_bytes;
+    const int stages = (27 + tps - 1) / tps;
+    const uint32_t smem0 = smem_u32(tc_smem);  // stage s starts at smem0 + s stage_bytes
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tc_smem + 2 * stage_bytes);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
     constexpr uint32_t kCols = COUT < 32 ? 32 : COUT;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -243,10 +259,10 @@ __global__ void __launch_bounds__(kTcThreads) conv_fwd_tc_kernel(const ConvFwd a
     const VoxCoord row = vox_coord(a.d, v0 + tid);
     const uint32_t arow = (uint32_t)(tid >> 3) * sbo_a + (uint32_t)(tid & 7) * 16u;
 
-    // copies of tap t into stage s: the A rows (voxels) and the W_t rows (output channels)
-    auto load_tap = [&](int t, int s) {
+    // copies of tap t into slot tt of stage s: the A rows (voxels) and the W_t rows (output channels)
+    auto load_tap = [&](int t, int s, int tt) {
         const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-        const uint32_t sa = smem_u32(stage[s]), sb = sa + a_bytes;
+        const uint32_t sa = (smem0 + (uint32_t)s * stage_bytes) + (uint32_t)tt * tap_bytes, sb = sa + a_bytes;
         {
             const int sv = shifted(a.d, row, dx, dy, dz);  // -1 beyond the plates (zero fill)
             const bf16* s1 = sv >= 0 ? a.src1 + (size_t)sv * a.c1 : a.src1;
@@ -262,17 +278,24 @@ __global__ void __launch_bounds__(kTcThreads) conv_fwd_tc_kernel(const ConvFwd a
             cp_async16(sb + (uint32_t)(n >> 3) * sbo_a + (uint32_t)q * 128u + (uint32_t)(n & 7) * 16u,
                        w + (size_t)n * cin + q * 8, true);
         }
+    };
+    // stage g: taps g tps .. g tps + tps - 1, one commit group
+    auto load_stage = [&](int g, int s) {
+        for (int tt = 0; tt < tps; ++tt) {
+            const int t = g * tps + tt;
+            if (t < 27) load_tap(t, s, tt);
+        }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
 
     constexpr uint32_t idesc = umma_idesc_bf16(kTcM, COUT);
     bool ok = true;
-    load_tap(0, 0);
-    for (int t = 0; t < 27; ++t) {
-        const int s = t & 1;
-        if (t + 1 < 27) {
-            if (t >= 1) ok = ok && mbar_wait(smem_u32(&bars[s ^ 1]), ((t - 1) >> 1) & 1);  // MMAs of tap t - 1
-            if (ok) load_tap(t + 1, s ^ 1);
+    load_stage(0, 0);
+    for (int g = 0; g < stages; ++g) {
+        const int s = g & 1;
+        if (g + 1 < stages) {
+            if (g >= 1) ok = ok && mbar_wait(smem_u32(&bars[s ^ 1]), ((g - 1) >> 1) & 1);  // MMAs of stage g - 1
+            if (ok) load_stage(g + 1, s ^ 1);
             asm volatile("cp.async.wait_group 1;\n" ::: "memory");
         } else {
             asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -282,24 +305,26 @@ __global__ void __launch_bounds__(kTcThreads) conv_fwd_tc_kernel(const ConvFwd a
         if (!ok) break;
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const uint32_t sa = smem_u32(stage[s]), sb = sa + a_bytes;
-            for (int j = 0; j < cin / 16; ++j) {
-                const uint64_t ad = umma_desc(sa + 256u * j, 128u, sbo_a);
-                const uint64_t bd = umma_desc(sb + 256u * j, 128u, sbo_a);
-                const uint32_t acc = (t > 0 || j > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                    : "memory");
+            for (int tt = 0; tt < tps && g * tps + tt < 27; ++tt) {
+                const uint32_t sa = (smem0 + (uint32_t)s * stage_bytes) + (uint32_t)tt * tap_bytes, sb = sa + a_bytes;
+                for (int j = 0; j < cin / 16; ++j) {
+                    const uint64_t ad = umma_desc(sa + 256u * j, 128u, sbo_a);
+                    const uint64_t bd = umma_desc(sb + 256u * j, 128u, sbo_a);
+                    const uint32_t acc = (g > 0 || tt > 0 || j > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                        : "memory");
+                }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                              smem_u32(&bars[s]))
                          : "memory");
         }
     }
-    // the commit of tap 26 (stage 0, its 14th use) covers every MMA
-    if (ok) ok = mbar_wait(smem_u32(&bars[0]), (26 >> 1) & 1);
+    // the commit of the last stage covers every MMA
+    if (ok) ok = mbar_wait(smem_u32(&bars[(stages - 1) & 1]), ((stages - 1) >> 1) & 1);
     ok = __syncthreads_and(ok) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (ok) {
@@ -851,7 +876,8 @@ cudaError_t conv_fwd(nh_unet* u, int l, int level, const bf16* s1, int c1, const
     const int cin = c1 + c2;
     if (cin % 16 || cin > kTcMaxCin || kConv[l].cout > kTcMaxCout) return cudaErrorInvalidValue;
     const int blocks = (a.d.nvox * a.d.batch + kTcM - 1) / kTcM;
-    const size_t smem = 2 * (size_t)(kTcM + kConv[l].cout) * cin * sizeof(bf16) + 64;
+    a.tps = tc_taps_per_stage(cin, kConv[l].cout);
+    const size_t smem = 2 * (size_t)a.tps * (kTcM + kConv[l].cout) * cin * sizeof(bf16) + 64;
     switch (kConv[l].cout) {
     case 16: conv_fwd_tc_kernel<16><<<blocks, kTcThreads, smem, st>>>(a); break;
     case 32: conv_fwd_tc_kernel<32><<<blocks, kTcThreads, smem, st>>>(a); break;
