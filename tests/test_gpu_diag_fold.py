@@ -64,7 +64,8 @@ def test_folded_diagnostics_equal_unfolded(nh, prec, case, steps):
     # grouped differently -- FP32 rounding of a few tens of terms
     fp64 = prec == "fp64"
     assert abs(a["energy"] - b["energy"]) <= (1e-14 if fp64 else 2e-6) * abs(b["energy"])
-    assert abs(a["max_u"] - b["max_u"]) <= 1e-15 * b["max_u"]
+    # max |u| from the LB launch's own components against the stored u: one FP32 ulp
+    assert abs(a["max_u"] - b["max_u"]) <= (1e-15 if fp64 else 2.5e-7) * b["max_u"]
     assert a["min_norm"] == b["min_norm"] and a["max_norm"] == b["max_norm"]
     assert a["nonfinite"] == b["nonfinite"] == 0
     assert np.max(np.abs(a["centroids"] - b["centroids"])) <= (1e-12 if fp64 else 1e-4)

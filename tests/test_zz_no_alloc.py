@@ -56,7 +56,9 @@ def test_noalloc_matches_nh_diagnostics_twice(env, prec):
         # 16-layer chunks, this entry point 4-layer ones: in FP32 the per-site
         # energies are grouped differently before the FP64 sum
         assert abs(v[1] - ref["energy"]) <= (1e-11 if prec == "fp64" else 2e-6) * abs(ref["energy"])
-        assert abs(v[2] - ref["max_u"]) <= 1e-12 * ref["max_u"]
+        # nh_diagnostics takes max |u| from the LB launch's own components, this
+        # entry point from the stored u: in FP32 the two norms may round one ulp apart
+        assert abs(v[2] - ref["max_u"]) <= (1e-12 if prec == "fp64" else 2.5e-7) * ref["max_u"]
         assert abs(v[3] - ref["min_norm"]) <= 1e-15 and abs(v[4] - ref["max_norm"]) <= 1e-15
         assert v[5] == 0.0
 
