@@ -1209,15 +1209,16 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(Real) == 4 ? 4 : 2) fuse
     fused_a_tile<Real, Solid>(c, nin, nout, blockIdx.x);
 }
 
+// Fused B at three blocks per SM (up to 85 registers): 101 us against 116 us
+// at four blocks of 64 registers on the 256x256x64 channel, FP32.
 template <typename Real, bool Solid>
-__global__ void __launch_bounds__(kFusedThreads, sizeof(Real) == 4 ? 4 : 2) fused_b_kernel(const FDChan<Real> c, const Real* nin, Real* ncopy)
+__global__ void __launch_bounds__(kFusedThreads, sizeof(Real) == 4 ? 3 : 2) fused_b_kernel(const FDChan<Real> c, const Real* nin, Real* ncopy)
 {
     fused_b_tile<Real, Solid>(c, nin, ncopy, blockIdx.x);
 }
 // The same with the diagnostics partials of the updated director (no obstacles).
-// Three blocks per SM: the diagnostics sums need the registers (measured:
-// 122 us against 137 us at four blocks of 64 registers on the 256x256x64
-// channel).
+// Three blocks per SM, as fused B (measured on the 256x256x64 channel: 122 us
+// against 137 us at four blocks of 64 registers).
 template <typename Real>
 __global__ void __launch_bounds__(kFusedThreads, sizeof(Real) == 4 ? 3 : 2)
     fused_b_diag_kernel(const FDChan<Real> c, const Real* nin, Real* ncopy, const BDiag bd)
