@@ -14,9 +14,12 @@ one site at a time, compiled without FMA contraction).  This module holds:
   error metrics (relative L2 and the paper's epsilon of Sec. III.A).
 
 Parity pins (see ``tests/test_oracle_*.py``) fix each routine against what the
-paper and the mathematics determine.  The absolute magnitude of the fully
-coupled backflow in a skyrmion channel has no closed form: that part is
-"parity unpinned" and is only checked for self-consistency (FP64 GPU vs oracle).
+paper and the mathematics determine; the coupled loop is held to the energy
+dissipation and momentum balance of the Ericksen-Leslie equations, which fix
+the sign and index placement of every coupling term.  The absolute magnitude
+of the fully coupled backflow in a skyrmion channel has no closed form: that
+part is "parity unpinned" and is only checked for self-consistency (FP64 GPU
+vs oracle).
 """
 from __future__ import annotations
 

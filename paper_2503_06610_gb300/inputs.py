@@ -30,6 +30,14 @@ LESLIE_ALIGN_09 = dict(gamma1=1.0, gamma2=-0.9, alpha1=0.0, alpha2=-0.95, alpha3
                        alpha4p=0.0, alpha5=0.45, alpha6=-0.45)
 
 
+# gamma2/gamma1 = -0.5 with gamma1 = 1 and alpha5 = -alpha6 = 1/4 (Parodi holds):
+# with the LB viscosity of tau = 1 (alpha4 = 2 (tau - 1/2)/3 = 1/3) these satisfy
+# Leslie's inequalities, so the Ericksen-Leslie dissipation is positive
+# definite (gamma1 (2 alpha4 + alpha5 + alpha6) = 2/3 > gamma2^2 = 1/4).
+LESLIE_DISSIPATIVE = dict(gamma1=1.0, gamma2=-0.5, alpha1=0.0, alpha2=-0.75, alpha3=0.25,
+                          alpha4p=0.0, alpha5=0.25, alpha6=-0.25)
+
+
 def _grid(nx, ny, nz):
     z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
     return x.astype(np.float64), y.astype(np.float64), z.astype(np.float64)
@@ -53,6 +61,15 @@ def tilted_director(nx, ny, nz, amplitude=0.05, seed=0):
     xi = rng.uniform(-1.0, 1.0, size=(2, N))
     n = np.stack([amplitude * xi[0], amplitude * xi[1], np.ones(N)])
     return n / np.linalg.norm(n, axis=0, keepdims=True)
+
+
+def distorted_director(nx, ny, nz, tilt=0.6, swing=0.4, twist=0.5):
+    """Smooth splay-bend-twist field: polar angle tilt sin(2 pi x/nx) + swing cos(2 pi y/ny),
+    azimuth twist sin(2 pi z/nz + 0.3); one period per axis, so periodic in x, y and z."""
+    x, y, z = _grid(nx, ny, nz)
+    a = tilt * np.sin(2 * math.pi * x / nx) + swing * np.cos(2 * math.pi * y / ny)
+    b = twist * np.sin(2 * math.pi * z / nz + 0.3)
+    return _pack(np.sin(a) * np.cos(b), np.sin(a) * np.sin(b), np.cos(a))
 
 
 def skyrmion_tubes(nx, ny, nz, centres, radius, handedness=1.0):
