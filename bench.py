@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--small", action="store_true", help="64x64x32 case (profiling only)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-channel sweep")
     ap.add_argument("--batch-blocks", type=int, default=20, help="dt_FD blocks timed in the batched sweep")
+    ap.add_argument("--lb-sweep", action="store_true",
+                    help="also time every LB launch shape the workload admits (lb_sweep_us in the JSON line)")
     ap.add_argument("--no-diag-fold", action="store_true",
                     help="diagnostics read the populations, u and rho themselves (nh_set_diag_fold 0)")
     return ap.parse_args()
@@ -486,6 +488,29 @@ def run_ours(args):
                "api": "nh_set_fields(host) + bench steps of nh_step + nh_diagnostics(host) + nh_get_fields(host)"}
         ce.close()
 
+    # every LB launch shape on the same workload (nh_set_lb_variant), CUDA events around the LB launches
+    lb_sweep = None
+    if rank == 0 and args.lb_sweep:
+        lb_sweep = {}
+        cs = nh.Channel(dict(params, precision="fp32", storage=store, shifted=True))
+        cs.set_fields(n0)
+        cs.step(4 * dt)
+        for v in range(7):
+            try:
+                cs.set_lb_variant(v)
+            except nh.NHError:
+                continue  # this shape does not fit the workload
+            cs.step(2 * dt)
+            torch.cuda.synchronize()
+            cs.set_timing(2)
+            cs.timing()
+            cs.step(20 * dt)
+            n_l, ms_l = cs.timing()["lb"]
+            cs.set_timing(0)
+            cs.timing()
+            lb_sweep[str(v)] = 1000.0 * ms_l / max(n_l, 1)
+        cs.close()
+
     # batched sweep: 64 independent channels of uneven size in one launch per pass
     batched = None
     if rank == 0 and not args.no_batch:
@@ -513,6 +538,7 @@ def run_ours(args):
                                     **{k: {"launches": v[0], "ms": v[1]} for k, v in kt_all.items()}},
             "fp64_compare": compare,
             "batched_sweep": batched,
+            "lb_sweep_us": lb_sweep,
             "diagnostics": {"mass_minus_N": diag["mass"] - N, "energy": diag["energy"], "max_u": diag["max_u"],
                             "centroids": diag["centroids"].tolist()[:8], "nonfinite": diag["nonfinite"]},
         }

@@ -368,9 +368,16 @@ int64_t nh_launch_count(const nh_ctx* ctx);
 /* Select the launch shape of the fused LB kernel: 0 = two sites per thread,
  * 256 threads (default; needs even nx), 1 = one site per thread, 256 threads,
  * 2 = two sites, 128 threads, 3 = one site, 128 threads, 4 = four sites,
- * 128 threads, 5 = four sites, 64 threads (4 and 5 need nx % 4 == 0).  All
- * variants compute the same arithmetic.  NH_EINVAL if the variant does not fit
- * the domain. */
+ * 128 threads, 5 = four sites, 64 threads (4 and 5 need nx % 4 == 0),
+ * 6 = 16-bit stores only (F16S, BF16S): whole x-rows of the 19 source planes
+ * staged in shared memory by bulk asynchronous copies, the next row in flight
+ * while a block collides the current one, four sites per thread (needs
+ * nx % 128 == 0 and nx <= 256; with obstacles it runs as variant 0).  All variants compute the same arithmetic
+ * and give bit-identical results.  Batches use variants 0 .. 5 (a batch of
+ * channels set to 6 runs variant 0).  NH_EINVAL if the variant does not fit
+ * the domain.  Variant 6 bounds its waits on the copies: an expired wait is
+ * reported by the next nh_diagnostics / nh_diagnostics_read as NH_ETIMEOUT
+ * (that launch's populations are incomplete). */
 int nh_set_lb_variant(nh_ctx* ctx, int variant);
 
 /* Select the FD kernels: 1 = fused (default): one 2.5D shared-memory kernel

@@ -874,7 +874,11 @@ int batch_prepare(nh_ctx* const* ctxs, int count, int64_t n_lb_steps, BatchPlan*
         int v = c0->lb_variant;
         bool ok = true;
         for (nh_ctx* c : key) ok = ok && lb_variant_valid(v, c->p.nx);
-        if (!ok) v = 1;  // one site per thread fits every domain
+        if (!ok) {  // the row-staged variant (single channels only), or a shape some channel cannot take
+            v = 0;
+            for (nh_ctx* c : key)
+                if (!lb_variant_valid(0, c->p.nx)) v = 1;  // one site per thread fits every domain
+        }
         plan->variant = v;
     }
     *out = plan;
@@ -1323,6 +1327,7 @@ int nh_bind_workspace(nh_ctx* c, void* dev_ptr, size_t bytes)
         if (r) return r;
         NH_CUDA(c, launch_trig_table(c->at<double>(c->L.trig), c->p.nx, c->p.ny, c->stream));
         c->launches += 1;
+        NH_CUDA(c, lb_rows_prepare(c->p.nx, c->p.storage));  // the row-staged LB kernel of 16-bit stores
     }
     c->bound = true;
     c->lbp_step = -1;
@@ -1818,6 +1823,11 @@ int nh_diagnostics_read(nh_ctx* c, nh_diag* out)
     if ((r = bounded_wait(c, st))) return r;  // the result stays pending: a later call reads it
     const int V = diag_num_values(c->diag_tubes);
     NH_CUDA(c, cudaMemcpyAsync(c->host_result, c->ws + c->L.result, V * sizeof(double), cudaMemcpyDeviceToHost, st));
+    // 16-bit stores: the row-staged LB kernel records an expired bulk-copy wait in the controller's third word
+    unsigned lb_timeout = 0;
+    char* lb_flag = c->ws + c->L.absmax + 2 * sizeof(unsigned);
+    if (store_size(c->p) == 2)
+        NH_CUDA(c, cudaMemcpyAsync(&lb_timeout, lb_flag, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     NH_CUDA(c, cudaStreamSynchronize(st));
     c->diag_pending = false;
     memset(out, 0, sizeof(*out));
@@ -1846,6 +1856,10 @@ int nh_diagnostics_read(nh_ctx* c, nh_diag* out)
             c->tubes_dirty = true;
             c->tubes_epoch += 1;
         }
+    }
+    if (lb_timeout) {
+        NH_CUDA(c, cudaMemsetAsync(lb_flag, 0, sizeof(unsigned), st));
+        return fail(c, NH_ETIMEOUT, "a bulk-copy wait of the row-staged LB kernel expired: populations incomplete");
     }
     if (out->nonfinite > 0) return fail(c, NH_EUNSTABLE, "non-finite values in n, u, rho or f");
     return NH_OK;
@@ -1897,7 +1911,8 @@ int64_t nh_launch_count(const nh_ctx* c) { return c ? c->launches : 0; }
 int nh_set_lb_variant(nh_ctx* c, int variant)
 {
     if (!c) return fail(nullptr, NH_EINVAL, "ctx is NULL");
-    if (!lb_variant_valid(variant, c->p.nx)) return fail(c, NH_EINVAL, "LB variant not valid for this domain");
+    if (!lb_variant_valid_for(variant, c->p.nx, (int)store_size(c->p)))
+        return fail(c, NH_EINVAL, "LB variant not valid for this domain");
     if (variant != c->lb_variant) drop_graphs(c);
     c->lb_variant = variant;
     return NH_OK;
@@ -1952,7 +1967,7 @@ int nh_autotune(nh_ctx* c, void* stream, int* chosen)
     // Each trial streams the current buffer into the other one without
     // advancing the state (no macro write, no buffer swap).
     for (int v = 0; v < kLBVariantCount && r == NH_OK; ++v) {
-        if (!lb_variant_valid(v, c->p.nx)) continue;
+        if (!lb_variant_valid_for(v, c->p.nx, (int)store_size(c->p))) continue;
         c->lb_variant = v;
         r = enqueue_lb(c, c->cur, false, st);
         if (r) break;

@@ -157,6 +157,142 @@ __device__ __forceinline__ void store4(Store* p, const Real v[4], float scale)
     }
 }
 
+// Scale controller, barrier form: the block's warps combine their maxima
+// (amax already reduced over each warp, in population units) in wmax, one
+// thread folds the block maximum into the launch's running maximum c.ctrl[0]
+// and takes a ticket c.ctrl[1]; the launch's last block records the scale of
+// the buffer just written and sets the target of the next step.
+template <typename Real, typename Store>
+__device__ __forceinline__ void scale_controller_block(const LBChan<Real, Store>& c, float amax, float scale_out,
+                                                       int ntiles, float* wmax, bool& last)
+{
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = amax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float b = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = fmaxf(b, wmax[w]);
+        if (b > __int_as_float((int)__ldcg(&c.ctrl[0])))
+            atomicMax(reinterpret_cast<int*>(&c.ctrl[0]), __float_as_int(b));
+        __threadfence();
+        const unsigned ticket = atomicAdd(&c.ctrl[1], 1u);
+        last = ticket == (unsigned)ntiles - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const float m = __int_as_float((int)atomicExch(&c.ctrl[0], 0u));
+        c.scales[1 - c.src] = scale_out;
+        c.scales[2] = scale_for(m, scale_out);
+        c.ctrl[1] = 0u;
+    }
+    __syncthreads();  // the shared controller state is reused by the next tile
+}
+
+// Moments, equilibrium, Guo source and relaxation of one site s from its
+// streamed populations f (decoded values; raw 2^k-scaled ones for the 16-bit
+// stores, whose power-of-two factors inv_in and scale_out are folded in), into
+// fo; u and rho written when Macro >= 1, the diagnostics partials accumulated
+// when Macro == 2, the largest |fo| (encoded units) into amax for the 16-bit
+// scale controller.  Every launch shape calls this for every site, so all
+// shapes give bit-identical results.
+template <typename Real, typename Store, bool Shifted, int Macro>
+__device__ __forceinline__ void lb_collide_site(const LBChan<Real, Store>& c, int s, const Real (&f)[19],
+                                                Real (&fo)[19], float inv_in, float scale_out, Real& psum, Real& pmax,
+                                                int& pbad, float& amax)
+{
+    NH_D3Q19_TABLES
+    constexpr bool kScaled = sizeof(Store) == 2;
+    constexpr bool WriteMacro = Macro >= 1;
+    constexpr bool Partials = Macro == 2;
+    const int N = c.g.N;
+    // 2. moments: pair sums and differences of (e_i, -e_i)
+    Real sum = f[0], mx = 0, my = 0, mz = 0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int i = 2 * k + 1;
+        sum += f[i] + f[i + 1];
+        const Real d = f[i] - f[i + 1];
+        if (EX[i] != 0) mx += EX[i] > 0 ? d : -d;
+        if (EY[i] != 0) my += EY[i] > 0 ? d : -d;
+        if (EZ[i] != 0) mz += EZ[i] > 0 ? d : -d;
+    }
+    if (kScaled) {  // raw populations: scale the sums once
+        sum *= Real(inv_in);
+        mx *= Real(inv_in);
+        my *= Real(inv_in);
+        mz *= Real(inv_in);
+    }
+    const Real rho = Shifted ? Real(1) + sum : sum;
+    const Real drho = Shifted ? sum : sum - Real(1);
+    const Real Fx = c.F[s] + rho * c.gx;
+    const Real Fy = c.F[N + s] + rho * c.gy;
+    const Real Fz = c.F[2 * N + s] + rho * c.gz;
+    const Real inv_rho = Real(1) / rho;
+    Real Hx = Fx, Hy = Fy, Hz = Fz;  // force whose half shifts u
+    if (c.Fu != nullptr) {
+        Hx = c.Fu[s] + rho * c.gx;
+        Hy = c.Fu[N + s] + rho * c.gy;
+        Hz = c.Fu[2 * N + s] + rho * c.gz;
+    }
+    const Real ux = (mx + Real(0.5) * Hx) * inv_rho;
+    const Real uy = (my + Real(0.5) * Hy) * inv_rho;
+    const Real uz = (mz + Real(0.5) * Hz) * inv_rho;
+    if (WriteMacro) {
+        c.u[s] = ux;
+        c.u[N + s] = uy;
+        c.u[2 * N + s] = uz;
+        c.rho[s] = rho;
+    }
+
+    // 3-4. equilibrium, Guo source and relaxation, per (e_i, -e_i) pair:
+    //   f^eq = w rho [3 eu + 4.5 eu^2 - 1.5 u.u] + w (rho - 1 | rho)
+    //   S    = w [3 eF + 9 eu eF - 3 u.F]
+    //   f*   = (1 - omega) f + omega f^eq + (1 - omega/2) S
+    // with a 16-bit store the constants carry scale_out (and omc the raw
+    // input's inv_in), so fo[] leaves here already in encoded units
+    const Real so = kScaled ? Real(scale_out) : Real(1);
+    const Real omega = c.omega * so;
+    const Real omc = (Real(1) - c.omega) * (kScaled ? Real(inv_in) * so : Real(1));
+    const Real cS = (Real(1) - Real(0.5) * c.omega) * so;
+    const Real uu15 = Real(1.5) * (ux * ux + uy * uy + uz * uz);
+    const Real uF3 = Real(3) * (ux * Fx + uy * Fy + uz * Fz);
+    const Real base = Shifted ? drho : rho;
+    // rest population (w = 1/3)
+    {
+        const Real w = Real(1) / Real(3);
+        fo[0] = omc * f[0] + omega * w * (base - rho * uu15) - cS * w * uF3;
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int i = 2 * k + 1;
+        const Real w = i < 7 ? Real(1) / Real(18) : Real(1) / Real(36);
+        const Real A = omega * w * rho;
+        const Real B = omega * w * base;
+        const Real C = cS * w;
+        const Real eu = Real(EX[i]) * ux + Real(EY[i]) * uy + Real(EZ[i]) * uz;
+        const Real eF = Real(EX[i]) * Fx + Real(EY[i]) * Fy + Real(EZ[i]) * Fz;
+        const Real even = A * (Real(4.5) * eu * eu - uu15) + B + C * (Real(9) * eu * eF - uF3);
+        const Real odd = Real(3) * (A * eu + C * eF);
+        fo[i] = omc * f[i] + even + odd;
+        fo[i + 1] = omc * f[i + 1] + even - odd;
+    }
+    if (Partials) {  // the sums nh_diagnostics forms from the stored state, site by site
+        Real fs = fo[0];
+#pragma unroll
+        for (int i = 1; i < 19; ++i) fs += fo[i];
+        psum += fs;
+        // max |u|^2 here and one square root per warp: sqrt is monotonic and
+        // correctly rounded, so this equals the maximum of the per-site |u|
+        const Real u2 = ux * ux + uy * uy + uz * uz;
+        pmax = max(pmax, u2);
+        if (!isfinite(u2) || !isfinite(rho) || !isfinite(fs)) pbad += 1;
+    }
+    if (kScaled) {
+#pragma unroll
+        for (int i = 0; i < 19; ++i) amax = fmaxf(amax, fabsf((float)fo[i]));
+    }
+}
+
 // Macro: 0 = populations only; 1 = also u and rho; 2 = also the diagnostics'
 // block partials c.part[k * ntiles + tile] of k = 0: sum of the stored
 // post-collision populations, 1: max |u|, 2: sites with a non-finite u, rho
@@ -298,93 +434,8 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
 #pragma unroll
         for (int j = 0; j < SPT; ++j) {
             if (solid_here) break;
-            const int s = s0 + j;
-            // 2. moments: pair sums and differences of (e_i, -e_i)
-            Real sum = f[j][0], mx = 0, my = 0, mz = 0;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                const int i = 2 * k + 1;
-                sum += f[j][i] + f[j][i + 1];
-                const Real d = f[j][i] - f[j][i + 1];
-                if (EX[i] != 0) mx += EX[i] > 0 ? d : -d;
-                if (EY[i] != 0) my += EY[i] > 0 ? d : -d;
-                if (EZ[i] != 0) mz += EZ[i] > 0 ? d : -d;
-            }
-            if (kScaled) {  // raw populations: scale the sums once
-                sum *= Real(inv_in);
-                mx *= Real(inv_in);
-                my *= Real(inv_in);
-                mz *= Real(inv_in);
-            }
-            const Real rho = Shifted ? Real(1) + sum : sum;
-            const Real drho = Shifted ? sum : sum - Real(1);
-            const Real Fx = c.F[s] + rho * c.gx;
-            const Real Fy = c.F[N + s] + rho * c.gy;
-            const Real Fz = c.F[2 * N + s] + rho * c.gz;
-            const Real inv_rho = Real(1) / rho;
-            Real Hx = Fx, Hy = Fy, Hz = Fz;  // force whose half shifts u
-            if (c.Fu != nullptr) {
-                Hx = c.Fu[s] + rho * c.gx;
-                Hy = c.Fu[N + s] + rho * c.gy;
-                Hz = c.Fu[2 * N + s] + rho * c.gz;
-            }
-            const Real ux = (mx + Real(0.5) * Hx) * inv_rho;
-            const Real uy = (my + Real(0.5) * Hy) * inv_rho;
-            const Real uz = (mz + Real(0.5) * Hz) * inv_rho;
-            if (WriteMacro) {
-                c.u[s] = ux;
-                c.u[N + s] = uy;
-                c.u[2 * N + s] = uz;
-                c.rho[s] = rho;
-            }
-
-            // 3-4. equilibrium, Guo source and relaxation, per (e_i, -e_i) pair:
-            //   f^eq = w rho [3 eu + 4.5 eu^2 - 1.5 u.u] + w (rho - 1 | rho)
-            //   S    = w [3 eF + 9 eu eF - 3 u.F]
-            //   f*   = (1 - omega) f + omega f^eq + (1 - omega/2) S
-            // with a 16-bit store the constants carry scale_out (and omc the raw
-            // input's inv_in), so fo[] leaves here already in encoded units
-            const Real so = kScaled ? Real(scale_out) : Real(1);
-            const Real omega = c.omega * so;
-            const Real omc = (Real(1) - c.omega) * (kScaled ? Real(inv_in) * so : Real(1));
-            const Real cS = (Real(1) - Real(0.5) * c.omega) * so;
-            const Real uu15 = Real(1.5) * (ux * ux + uy * uy + uz * uz);
-            const Real uF3 = Real(3) * (ux * Fx + uy * Fy + uz * Fz);
-            const Real base = Shifted ? drho : rho;
-            // rest population (w = 1/3)
-            {
-                const Real w = Real(1) / Real(3);
-                fo[j][0] = omc * f[j][0] + omega * w * (base - rho * uu15) - cS * w * uF3;
-            }
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                const int i = 2 * k + 1;
-                const Real w = i < 7 ? Real(1) / Real(18) : Real(1) / Real(36);
-                const Real A = omega * w * rho;
-                const Real B = omega * w * base;
-                const Real C = cS * w;
-                const Real eu = Real(EX[i]) * ux + Real(EY[i]) * uy + Real(EZ[i]) * uz;
-                const Real eF = Real(EX[i]) * Fx + Real(EY[i]) * Fy + Real(EZ[i]) * Fz;
-                const Real even = A * (Real(4.5) * eu * eu - uu15) + B + C * (Real(9) * eu * eF - uF3);
-                const Real odd = Real(3) * (A * eu + C * eF);
-                fo[j][i] = omc * f[j][i] + even + odd;
-                fo[j][i + 1] = omc * f[j][i + 1] + even - odd;
-            }
-            if (Partials) {  // the sums nh_diagnostics forms from the stored state, site by site
-                Real fs = fo[j][0];
-#pragma unroll
-                for (int i = 1; i < 19; ++i) fs += fo[j][i];
-                psum += fs;
-                // max |u|^2 here and one square root per warp: sqrt is monotonic and
-                // correctly rounded, so this equals the maximum of the per-site |u|
-                const Real u2 = ux * ux + uy * uy + uz * uz;
-                pmax = max(pmax, u2);
-                if (!isfinite(u2) || !isfinite(rho) || !isfinite(fs)) pbad += 1;
-            }
-            if (kScaled) {
-#pragma unroll
-                for (int i = 0; i < 19; ++i) amax = fmaxf(amax, fabsf((float)fo[j][i]));
-            }
+            lb_collide_site<Real, Store, Shifted, Macro>(c, s0 + j, f[j], fo[j], inv_in, scale_out, psum, pmax, pbad,
+                                                        amax);
         }
         if (kScaled) amax /= scale_out;  // back to population units for the controller
 
@@ -457,26 +508,7 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
             }
             return;
         }
-        if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = amax;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            float b = 0.f;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = fmaxf(b, wmax[w]);
-            if (b > __int_as_float((int)__ldcg(&c.ctrl[0])))
-                atomicMax(reinterpret_cast<int*>(&c.ctrl[0]), __float_as_int(b));
-            __threadfence();
-            const unsigned ticket = atomicAdd(&c.ctrl[1], 1u);
-            last = ticket == (unsigned)ntiles - 1;
-        }
-        __syncthreads();
-        if (last && threadIdx.x == 0) {
-            __threadfence();
-            const float m = __int_as_float((int)atomicExch(&c.ctrl[0], 0u));
-            c.scales[1 - c.src] = scale_out;
-            c.scales[2] = scale_for(m, scale_out);
-            c.ctrl[1] = 0u;
-        }
-        __syncthreads();  // the shared controller state is reused by the next tile
+        scale_controller_block(c, amax, scale_out, ntiles, wmax, last);
     }
 }
 
@@ -484,6 +516,265 @@ template <typename Real, typename Store, bool Shifted, int Macro, int SPT, bool 
 __global__ void __launch_bounds__(kLBThreads) lb_kernel(const LBChan<Real, Store> c)
 {
     lb_tile<Real, Store, Shifted, Macro, SPT, Solid, true>(c, blockIdx.x, gridDim.x);
+}
+
+// ------------------------------------------------------------------ 16-bit stores: rows staged by bulk copies
+//
+// The 16-bit kernels above are bound by latency and issue, not by HBM: each
+// thread must hold its sites' 19 populations in registers while the loads are
+// in flight, so the bytes in flight per SM are capped by the register file.
+// lb_rows_kernel moves the streaming step to the copy engine.  A persistent
+// block walks the x-rows (y, z) of the lattice; the row needs, per direction
+// i, source row (y - e_y, z - e_z) of plane i, or its own row of plane opp(i)
+// where e_i crosses a plate (half-way bounce-back): nx contiguous 16-bit
+// values that one cp.async.bulk copies whole into shared memory, completing on
+// the stage's mbarrier.  kRowStages stages keep the copies of the next row in
+// flight while the block collides the current one; the e_x = +-1 shift and the
+// periodic x wrap are resolved by indexing the staged row.  Thread t owns the
+// kRowSPT sites x = 4t .. 4t + 3 of the row (blockDim.x = nx / 4), read as
+// aligned 4-site chunks as in the four-site register shape, and collides them
+// with lb_collide_site, the code of every other shape, so the results are
+// bit-identical to theirs.  Requirements (checked by lb_rows_valid): 16-bit
+// stores, nx a multiple of 128 (whole warps; 16-byte aligned rows and planes)
+// and at most kRowMaxNx, no obstacles.  Every mbarrier wait is bounded: on
+// expiry the block records the timeout in c.ctrl[2], stops sweeping, waits
+// (bounded) for the copies it issued and still takes its controller ticket.
+constexpr int kRowSPT = 4;        // sites per thread: four consecutive sites of the row
+constexpr int kRowStages = 2;      // rows in shared memory per block: the one collided, the next in flight
+constexpr int kRowMaxNx = 256;
+constexpr int kRowMinBlocks = 8;   // per SM: at most 128 registers a thread (64 threads at nx = 256)
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool row_bar_wait(uint32_t bar, uint32_t parity)
+{
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Direction of lane i < 19 of the issuing warp, packed in one register:
+// (e_y + 1) | (e_z + 1) << 2 | opp(i) << 4.
+__device__ __forceinline__ int row_lane(int lane)
+{
+    NH_D3Q19_TABLES
+    int d = 0;
+#pragma unroll
+    for (int i = 0; i < 19; ++i)
+        if (lane == i) d = (EY[i] + 1) | ((EZ[i] + 1) << 2) | (OPP[i] << 4);
+    return d;
+}
+
+// Warp 0: the 19 source rows of row r into stage buffer dst, completing on
+// bar.  Lane 0 arms the barrier with the row's bytes, then lane i < 19 copies
+// direction i: row (y - e_y, z - e_z) of plane i, or its own row of plane
+// opp(i) where e_i crosses a plate.
+template <typename Store>
+__device__ __forceinline__ void issue_row(const Store* fsrc, const Geom& g, int r, Store* dst, uint32_t bar)
+{
+    const uint32_t row_bytes = (uint32_t)g.nx * sizeof(Store);
+    const int lane = (int)threadIdx.x & 31;
+    if (lane == 0)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(19u * row_bytes)
+                     : "memory");
+    __syncwarp();
+    if (lane < 19) {
+        const int y = r % g.ny, z = r / g.ny;
+        const int d = row_lane(lane);
+        const int ey = (d & 3) - 1, ez = ((d >> 2) & 3) - 1, opp = d >> 4;
+        const bool bb = g.walls && ((ez > 0 && z == 0) || (ez < 0 && z == g.nz - 1));
+        const Store* src;
+        if (bb) {
+            src = fsrc + (size_t)opp * g.N + (size_t)r * g.nx;
+        } else {
+            int ys = y - ey, zs = z - ez;
+            ys = ys < 0 ? ys + g.ny : (ys >= g.ny ? ys - g.ny : ys);
+            zs = zs < 0 ? zs + g.nz : (zs >= g.nz ? zs - g.nz : zs);
+            src = fsrc + (size_t)lane * g.N + (size_t)(ys + g.ny * zs) * g.nx;
+        }
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                smem_addr(dst + (size_t)lane * g.nx)),
+            "l"(src), "r"(row_bytes), "r"(bar)
+            : "memory");
+    }
+}
+
+}  // namespace
+
+template <typename Real, typename Store, bool Shifted, int Macro>
+__global__ void __launch_bounds__(kRowMaxNx / kRowSPT, kRowMinBlocks) lb_rows_kernel(const LBChan<Real, Store> c)
+{
+    static_assert(sizeof(Store) == 2 && Macro < 2, "row staging: 16-bit stores, no diagnostics partials");
+    static_assert(kRowSPT == 4, "the staged rows are read as aligned 4-site chunks");
+    NH_D3Q19_TABLES
+    extern __shared__ __align__(128) unsigned char rows_smem[];
+    __shared__ __align__(8) uint64_t full[kRowStages];
+    __shared__ float wmax[kRowMaxNx / kRowSPT / 32];
+    __shared__ bool last;
+    const Geom& g = c.g;
+    const int nx = g.nx, N = g.N;
+    Store* stages = reinterpret_cast<Store*>(rows_smem);
+    const int rows = g.ny * g.nz;
+    const int my_rows = (int)blockIdx.x < rows ? (rows - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const float inv_in = 1.f / c.scales[c.src];
+    const float scale_out = c.scales[2];
+    const int x0 = kRowSPT * (int)threadIdx.x;
+    Real psum = 0, pmax = 0;  // unused: no partials with 16-bit stores
+    int pbad = 0;
+    float amax = 0.f;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < kRowStages; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&full[k])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    const bool issuer = threadIdx.x < 32;  // warp 0 issues the copies, one direction per lane
+    if (issuer)
+        for (int k = 0; k < kRowStages && k < my_rows; ++k)
+            issue_row(c.fsrc, g, (int)blockIdx.x + k * (int)gridDim.x, stages + (size_t)k * 19 * nx,
+                      smem_addr(&full[k]));
+    int k = 0;
+    bool timed_out = false;
+    for (; k < my_rows; ++k) {
+        const int stage = k % kRowStages;
+        const bool ok = row_bar_wait(smem_addr(&full[stage]), (uint32_t)(k / kRowStages) & 1u);
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            break;
+        }
+        const int r = (int)blockIdx.x + k * (int)gridDim.x;
+        const Store* st = stages + (size_t)stage * 19 * nx;
+        const int z = r / g.ny;
+        Real f[kRowSPT][19];
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            const bool bb = g.walls && ((EZ[i] > 0 && z == 0) || (EZ[i] < 0 && z == g.nz - 1));
+            const Store* row = st + (size_t)i * nx;
+            // aligned 4-site chunks of the staged row; e_x = +-1 takes one value of the neighbouring chunk
+            Real a[4];
+            load4(row + x0, 1.f, a);
+            if (EX[i] == 0 || bb) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) f[j][i] = a[j];
+            } else if (EX[i] > 0) {  // sources x0 - 1 .. x0 + 2
+                Real b[4];
+                load4(row + (x0 == 0 ? nx - 4 : x0 - 4), 1.f, b);
+                f[0][i] = b[3];
+                f[1][i] = a[0];
+                f[2][i] = a[1];
+                f[3][i] = a[2];
+            } else {  // sources x0 + 1 .. x0 + 4
+                Real b[4];
+                load4(row + (x0 + 4 == nx ? 0 : x0 + 4), 1.f, b);
+                f[0][i] = a[1];
+                f[1][i] = a[2];
+                f[2][i] = a[3];
+                f[3][i] = b[0];
+            }
+        }
+        __syncthreads();  // the stage is read: refill it with the row kRowStages ahead
+        if (issuer && k + kRowStages < my_rows)
+            issue_row(c.fsrc, g, (int)blockIdx.x + (k + kRowStages) * (int)gridDim.x,
+                      stages + (size_t)stage * 19 * nx, smem_addr(&full[stage]));
+        const int s0 = r * nx + x0;
+        Real fo[kRowSPT][19];
+#pragma unroll
+        for (int j = 0; j < kRowSPT; ++j)
+            lb_collide_site<Real, Store, Shifted, Macro>(c, s0 + j, f[j], fo[j], inv_in, scale_out, psum, pmax, pbad,
+                                                        amax);
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            const Real v[4] = {fo[0][i], fo[1][i], fo[2][i], fo[3][i]};
+            store4(c.fdst + (size_t)i * N + s0, v, 1.f);
+        }
+    }
+    if (timed_out && threadIdx.x == 0) {
+        atomicOr(&c.ctrl[2], 1u);
+        // rows k .. k + kRowStages - 1 (those that exist) were issued and not consumed
+        for (int q = k; q < k + kRowStages && q < my_rows; ++q)
+            row_bar_wait(smem_addr(&full[q % kRowStages]), (uint32_t)(q / kRowStages) & 1u);
+    }
+    amax /= scale_out;  // back to population units for the controller
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    scale_controller_block(c, amax, scale_out, (int)gridDim.x, wmax, last);
+}
+
+size_t lb_rows_smem(int nx, int store_bytes) { return (size_t)kRowStages * 19 * nx * store_bytes; }
+
+bool lb_rows_valid(int nx, int store_bytes)
+{
+    return store_bytes == 2 && nx % (32 * kRowSPT) == 0 && nx <= kRowMaxNx;
+}
+
+// Resident blocks of one instantiation for rows of nx sites (the persistent
+// grid), computed once per row length by lb_rows_prepare, outside any graph
+// capture.
+template <typename Real, typename Store, bool Shifted, int Macro>
+int& rows_resident(int nx)
+{
+    static int resident[kRowMaxNx / (32 * kRowSPT) + 1] = {};
+    return resident[nx / (32 * kRowSPT)];
+}
+
+template <typename Real, typename Store, bool Shifted, int Macro>
+cudaError_t prepare_rows_one(int nx)
+{
+    int& resident = rows_resident<Real, Store, Shifted, Macro>(nx);
+    if (resident > 0) return cudaSuccess;
+    auto kern = lb_rows_kernel<Real, Store, Shifted, Macro>;
+    const size_t smem = lb_rows_smem(nx, (int)sizeof(Store));
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)lb_rows_smem(kRowMaxNx, 2));
+    int dev = 0, sms = 0, per_sm = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nx / kRowSPT, smem);
+    if (e == cudaSuccess) resident = (per_sm > 0 ? per_sm : 1) * sms;
+    return e;
+}
+
+template <typename Store>
+cudaError_t prepare_rows_store(int nx)
+{
+    cudaError_t e = prepare_rows_one<float, Store, true, 0>(nx);
+    if (e == cudaSuccess) e = prepare_rows_one<float, Store, true, 1>(nx);
+    if (e == cudaSuccess) e = prepare_rows_one<float, Store, false, 0>(nx);
+    if (e == cudaSuccess) e = prepare_rows_one<float, Store, false, 1>(nx);
+    return e;
+}
+
+cudaError_t lb_rows_prepare(int nx, int storage)
+{
+    if (!lb_rows_valid(nx, 2)) return cudaSuccess;
+    if (storage == NH_STORE_F16S) return prepare_rows_store<__half>(nx);
+    if (storage == NH_STORE_BF16S) return prepare_rows_store<__nv_bfloat16>(nx);
+    return cudaSuccess;
+}
+
+template <typename Real, typename Store, bool Shifted, int Macro>
+cudaError_t launch_lb_rows(const LBChan<Real, Store>& c, cudaStream_t st)
+{
+    const int resident = rows_resident<Real, Store, Shifted, Macro>(c.g.nx);
+    if (resident <= 0) return cudaErrorNotReady;  // lb_rows_prepare was not run for this row length
+    const int rows = c.g.ny * c.g.nz;
+    const int blocks = rows < resident ? rows : resident;
+    lb_rows_kernel<Real, Store, Shifted, Macro>
+        <<<blocks, c.g.nx / kRowSPT, lb_rows_smem(c.g.nx, (int)sizeof(Store)), st>>>(c);
+    return cudaGetLastError();
 }
 
 // Batched sweep: a persistent grid walks the (channel, tile) work list of up to
@@ -510,12 +801,21 @@ __global__ void __launch_bounds__(kLBThreads) lb_batch_kernel(const LBBatch<Real
 struct LBVariantShape {
     int spt, threads;
 };
-constexpr LBVariantShape kLBVariants[kLBVariantCount] = {{2, 256}, {1, 256}, {2, 128}, {1, 128}, {4, 128}, {4, 64}};
+// The last variant, kLBRowsVariant, is lb_rows_kernel (16-bit stores only);
+// its entry here is the two-site shape it falls back to where it does not apply.
+constexpr LBVariantShape kLBVariants[kLBVariantCount] = {{2, 256}, {1, 256}, {2, 128}, {1, 128},
+                                                         {4, 128}, {4, 64},  {2, 256}};
 
 bool lb_variant_valid(int variant, int nx)
 {
-    if (variant < 0 || variant >= kLBVariantCount) return false;
+    if (variant < 0 || variant >= kLBVariantCount || variant == kLBRowsVariant) return false;
     return nx % kLBVariants[variant].spt == 0;
+}
+
+bool lb_variant_valid_for(int variant, int nx, int store_bytes)
+{
+    if (variant == kLBRowsVariant) return lb_rows_valid(nx, store_bytes);
+    return lb_variant_valid(variant, nx);
 }
 
 int lb_blocks(int variant, int N)
@@ -528,6 +828,10 @@ int lb_blocks(int variant, int N)
 template <typename Real, typename Store, bool Shifted, int Macro>
 cudaError_t launch_lb_spt(const LBChan<Real, Store>& c, int variant, cudaStream_t st)
 {
+    if constexpr (sizeof(Store) == 2 && Macro < 2) {
+        if (variant == kLBRowsVariant && c.solid == nullptr && lb_rows_valid(c.g.nx, 2))
+            return launch_lb_rows<Real, Store, Shifted, Macro>(c, st);
+    }
     if (c.solid != nullptr) {  // obstacles: one site per thread, 256 threads
         if constexpr (Macro < 2)
             lb_kernel<Real, Store, Shifted, Macro, 1, true><<<(c.g.N + 255) / 256, 256, 0, st>>>(c);
@@ -549,7 +853,7 @@ cudaError_t launch_lb_spt(const LBChan<Real, Store>& c, int variant, cudaStream_
 template <typename Real, typename Store>
 cudaError_t launch_lb(const LBChan<Real, Store>& c, bool shifted, bool write_macro, int variant, cudaStream_t st)
 {
-    if (!lb_variant_valid(variant, c.g.nx)) return cudaErrorInvalidValue;
+    if (!lb_variant_valid_for(variant, c.g.nx, (int)sizeof(Store))) return cudaErrorInvalidValue;
     if constexpr (sizeof(Store) != 2) {
         if (write_macro && c.part != nullptr) {
             if (c.solid != nullptr) return cudaErrorInvalidValue;

@@ -206,8 +206,12 @@ struct FDBatch {
 };
 
 // LB launch variants (sites per thread x block size); variant 0 is the default.
-constexpr int kLBVariantCount = 6;
-bool lb_variant_valid(int variant, int nx);
+constexpr int kLBVariantCount = 7;
+constexpr int kLBRowsVariant = 6;  // rows staged in shared memory by bulk copies (16-bit stores)
+bool lb_variant_valid(int variant, int nx);  // the register shapes 0 .. 5 (also in batches)
+bool lb_rows_valid(int nx, int store_bytes);
+bool lb_variant_valid_for(int variant, int nx, int store_bytes);  // any variant, one channel
+cudaError_t lb_rows_prepare(int nx, int storage);  // once per context, outside graph capture
 int lb_blocks(int variant, int N);  // thread blocks of one LB launch of that shape
 template <typename Real, typename Store>
 cudaError_t launch_lb(const LBChan<Real, Store>& c, bool shifted, bool write_macro, int variant, cudaStream_t s);
