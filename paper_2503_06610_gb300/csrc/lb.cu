@@ -188,13 +188,34 @@ __device__ __forceinline__ void scale_controller_block(const LBChan<Real, Store>
     __syncthreads();  // the shared controller state is reused by the next tile
 }
 
+// Rounded products and fused multiply-adds written out: the compiler may not
+// contract a*b + c on its own here, so every launch shape and kernel that
+// collides a site (single channels, batches, the row-staged kernel) rounds
+// in the same order and gives the same bits.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return fma(a, b, c); }
+
+// e . v for a lattice vector with components in {-1, 0, 1} (constants once the
+// direction loop is unrolled): sums and differences only.
+template <typename Real>
+__device__ __forceinline__ Real edot(int X, int Y, int Z, Real vx, Real vy, Real vz)
+{
+    Real r = Real(0);
+    if (X != 0) r = X > 0 ? vx : -vx;
+    if (Y != 0) r = (X != 0) ? (Y > 0 ? r + vy : r - vy) : (Y > 0 ? vy : -vy);
+    if (Z != 0) r = (X != 0 || Y != 0) ? (Z > 0 ? r + vz : r - vz) : (Z > 0 ? vz : -vz);
+    return r;
+}
+
 // Moments, equilibrium, Guo source and relaxation of one site s from its
 // streamed populations f (decoded values; raw 2^k-scaled ones for the 16-bit
 // stores, whose power-of-two factors inv_in and scale_out are folded in), into
 // fo; u and rho written when Macro >= 1, the diagnostics partials accumulated
 // when Macro == 2, the largest |fo| (encoded units) into amax for the 16-bit
-// scale controller.  Every launch shape calls this for every site, so all
-// shapes give bit-identical results.
+// scale controller.  Every launch shape calls this for every site, and its
+// rounding order is explicit, so all shapes give bit-identical results.
 template <typename Real, typename Store, bool Shifted, int Macro>
 __device__ __forceinline__ void lb_collide_site(const LBChan<Real, Store>& c, int s, const Real (&f)[19],
                                                 Real (&fo)[19], float inv_in, float scale_out, Real& psum, Real& pmax,
@@ -217,26 +238,26 @@ __device__ __forceinline__ void lb_collide_site(const LBChan<Real, Store>& c, in
         if (EZ[i] != 0) mz += EZ[i] > 0 ? d : -d;
     }
     if (kScaled) {  // raw populations: scale the sums once
-        sum *= Real(inv_in);
-        mx *= Real(inv_in);
-        my *= Real(inv_in);
-        mz *= Real(inv_in);
+        sum = mul_rn(sum, Real(inv_in));
+        mx = mul_rn(mx, Real(inv_in));
+        my = mul_rn(my, Real(inv_in));
+        mz = mul_rn(mz, Real(inv_in));
     }
     const Real rho = Shifted ? Real(1) + sum : sum;
     const Real drho = Shifted ? sum : sum - Real(1);
-    const Real Fx = c.F[s] + rho * c.gx;
-    const Real Fy = c.F[N + s] + rho * c.gy;
-    const Real Fz = c.F[2 * N + s] + rho * c.gz;
+    const Real Fx = fma_rn(rho, c.gx, c.F[s]);
+    const Real Fy = fma_rn(rho, c.gy, c.F[N + s]);
+    const Real Fz = fma_rn(rho, c.gz, c.F[2 * N + s]);
     const Real inv_rho = Real(1) / rho;
     Real Hx = Fx, Hy = Fy, Hz = Fz;  // force whose half shifts u
     if (c.Fu != nullptr) {
-        Hx = c.Fu[s] + rho * c.gx;
-        Hy = c.Fu[N + s] + rho * c.gy;
-        Hz = c.Fu[2 * N + s] + rho * c.gz;
+        Hx = fma_rn(rho, c.gx, c.Fu[s]);
+        Hy = fma_rn(rho, c.gy, c.Fu[N + s]);
+        Hz = fma_rn(rho, c.gz, c.Fu[2 * N + s]);
     }
-    const Real ux = (mx + Real(0.5) * Hx) * inv_rho;
-    const Real uy = (my + Real(0.5) * Hy) * inv_rho;
-    const Real uz = (mz + Real(0.5) * Hz) * inv_rho;
+    const Real ux = mul_rn(fma_rn(Real(0.5), Hx, mx), inv_rho);
+    const Real uy = mul_rn(fma_rn(Real(0.5), Hy, my), inv_rho);
+    const Real uz = mul_rn(fma_rn(Real(0.5), Hz, mz), inv_rho);
     if (WriteMacro) {
         c.u[s] = ux;
         c.u[N + s] = uy;
@@ -251,30 +272,35 @@ __device__ __forceinline__ void lb_collide_site(const LBChan<Real, Store>& c, in
     // with a 16-bit store the constants carry scale_out (and omc the raw
     // input's inv_in), so fo[] leaves here already in encoded units
     const Real so = kScaled ? Real(scale_out) : Real(1);
-    const Real omega = c.omega * so;
-    const Real omc = (Real(1) - c.omega) * (kScaled ? Real(inv_in) * so : Real(1));
-    const Real cS = (Real(1) - Real(0.5) * c.omega) * so;
-    const Real uu15 = Real(1.5) * (ux * ux + uy * uy + uz * uz);
-    const Real uF3 = Real(3) * (ux * Fx + uy * Fy + uz * Fz);
+    const Real omega = mul_rn(c.omega, so);
+    const Real omc = mul_rn(Real(1) - c.omega, kScaled ? mul_rn(Real(inv_in), so) : Real(1));
+    const Real cS = mul_rn(fma_rn(Real(-0.5), c.omega, Real(1)), so);
+    const Real u2 = fma_rn(uz, uz, fma_rn(uy, uy, mul_rn(ux, ux)));
+    const Real uu15 = mul_rn(Real(1.5), u2);
+    const Real uF3 = mul_rn(Real(3), fma_rn(uz, Fz, fma_rn(uy, Fy, mul_rn(ux, Fx))));
     const Real base = Shifted ? drho : rho;
     // rest population (w = 1/3)
     {
         const Real w = Real(1) / Real(3);
-        fo[0] = omc * f[0] + omega * w * (base - rho * uu15) - cS * w * uF3;
+        const Real t = fma_rn(-rho, uu15, base);
+        fo[0] = fma_rn(omc, f[0], fma_rn(mul_rn(omega, w), t, -mul_rn(mul_rn(cS, w), uF3)));
     }
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         const int i = 2 * k + 1;
         const Real w = i < 7 ? Real(1) / Real(18) : Real(1) / Real(36);
-        const Real A = omega * w * rho;
-        const Real B = omega * w * base;
-        const Real C = cS * w;
-        const Real eu = Real(EX[i]) * ux + Real(EY[i]) * uy + Real(EZ[i]) * uz;
-        const Real eF = Real(EX[i]) * Fx + Real(EY[i]) * Fy + Real(EZ[i]) * Fz;
-        const Real even = A * (Real(4.5) * eu * eu - uu15) + B + C * (Real(9) * eu * eF - uF3);
-        const Real odd = Real(3) * (A * eu + C * eF);
-        fo[i] = omc * f[i] + even + odd;
-        fo[i + 1] = omc * f[i + 1] + even - odd;
+        const Real ow = mul_rn(omega, w);
+        const Real A = mul_rn(ow, rho);
+        const Real B = mul_rn(ow, base);
+        const Real C = mul_rn(cS, w);
+        const Real eu = edot(EX[i], EY[i], EZ[i], ux, uy, uz);
+        const Real eF = edot(EX[i], EY[i], EZ[i], Fx, Fy, Fz);
+        const Real X = fma_rn(mul_rn(Real(4.5), eu), eu, -uu15);
+        const Real Y = fma_rn(mul_rn(Real(9), eu), eF, -uF3);
+        const Real even = fma_rn(C, Y, fma_rn(A, X, B));
+        const Real odd = mul_rn(Real(3), fma_rn(A, eu, mul_rn(C, eF)));
+        fo[i] = fma_rn(omc, f[i], even) + odd;
+        fo[i + 1] = fma_rn(omc, f[i + 1], even) - odd;
     }
     if (Partials) {  // the sums nh_diagnostics forms from the stored state, site by site
         Real fs = fo[0];
@@ -283,7 +309,6 @@ __device__ __forceinline__ void lb_collide_site(const LBChan<Real, Store>& c, in
         psum += fs;
         // max |u|^2 here and one square root per warp: sqrt is monotonic and
         // correctly rounded, so this equals the maximum of the per-site |u|
-        const Real u2 = ux * ux + uy * uy + uz * uz;
         pmax = max(pmax, u2);
         if (!isfinite(u2) || !isfinite(rho) || !isfinite(fs)) pbad += 1;
     }
