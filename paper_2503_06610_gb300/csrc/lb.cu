@@ -211,15 +211,16 @@ __device__ __forceinline__ Real edot(int X, int Y, int Z, Real vx, Real vy, Real
 
 // Moments, equilibrium, Guo source and relaxation of one site s from its
 // streamed populations f (decoded values; raw 2^k-scaled ones for the 16-bit
-// stores, whose power-of-two factors inv_in and scale_out are folded in), into
+// stores, whose power-of-two factors inv_in and scale_out are folded in) and
+// its liquid-crystal force F_lc = (flx, fly, flz) (the body force rho g is added here), into
 // fo; u and rho written when Macro >= 1, the diagnostics partials accumulated
 // when Macro == 2, the largest |fo| (encoded units) into amax for the 16-bit
 // scale controller.  Every launch shape calls this for every site, and its
 // rounding order is explicit, so all shapes give bit-identical results.
 template <typename Real, typename Store, bool Shifted, int Macro>
 __device__ __forceinline__ void lb_collide_site(const LBChan<Real, Store>& c, int s, const Real (&f)[19],
-                                                Real (&fo)[19], float inv_in, float scale_out, Real& psum, Real& pmax,
-                                                int& pbad, float& amax)
+                                                Real (&fo)[19], Real flx, Real fly, Real flz, float inv_in,
+                                                float scale_out, Real& psum, Real& pmax, int& pbad, float& amax)
 {
     NH_D3Q19_TABLES
     constexpr bool kScaled = sizeof(Store) == 2;
@@ -245,9 +246,9 @@ __device__ __forceinline__ void lb_collide_site(const LBChan<Real, Store>& c, in
     }
     const Real rho = Shifted ? Real(1) + sum : sum;
     const Real drho = Shifted ? sum : sum - Real(1);
-    const Real Fx = fma_rn(rho, c.gx, c.F[s]);
-    const Real Fy = fma_rn(rho, c.gy, c.F[N + s]);
-    const Real Fz = fma_rn(rho, c.gz, c.F[2 * N + s]);
+    const Real Fx = fma_rn(rho, c.gx, flx);
+    const Real Fy = fma_rn(rho, c.gy, fly);
+    const Real Fz = fma_rn(rho, c.gz, flz);
     const Real inv_rho = Real(1) / rho;
     Real Hx = Fx, Hy = Fy, Hz = Fz;  // force whose half shifts u
     if (c.Fu != nullptr) {
@@ -459,8 +460,9 @@ __device__ __forceinline__ void lb_tile(const LBChan<Real, Store>& c, int tile, 
 #pragma unroll
         for (int j = 0; j < SPT; ++j) {
             if (solid_here) break;
-            lb_collide_site<Real, Store, Shifted, Macro>(c, s0 + j, f[j], fo[j], inv_in, scale_out, psum, pmax, pbad,
-                                                        amax);
+            const int s = s0 + j;
+            lb_collide_site<Real, Store, Shifted, Macro>(c, s, f[j], fo[j], c.F[s], c.F[N + s], c.F[2 * N + s], inv_in,
+                                                        scale_out, psum, pmax, pbad, amax);
         }
         if (kScaled) amax /= scale_out;  // back to population units for the controller
 
@@ -553,7 +555,8 @@ __global__ void __launch_bounds__(kLBThreads) lb_kernel(const LBChan<Real, Store
 // i, source row (y - e_y, z - e_z) of plane i, or its own row of plane opp(i)
 // where e_i crosses a plate (half-way bounce-back): nx contiguous 16-bit
 // values that one cp.async.bulk copies whole into shared memory, completing on
-// the stage's mbarrier.  kRowStages stages keep the copies of the next row in
+// the stage's mbarrier, together with the row's three force rows F_lc (the
+// other load of the collision, which would otherwise wait on HBM latency).  kRowStages stages keep the copies of the next row in
 // flight while the block collides the current one; the e_x = +-1 shift and the
 // periodic x wrap are resolved by indexing the staged row.  Thread t owns the
 // kRowSPT sites x = 4t .. 4t + 3 of the row (blockDim.x = nx / 4), read as
@@ -602,17 +605,21 @@ __device__ __forceinline__ int row_lane(int lane)
     return d;
 }
 
-// Warp 0: the 19 source rows of row r into stage buffer dst, completing on
-// bar.  Lane 0 arms the barrier with the row's bytes, then lane i < 19 copies
-// direction i: row (y - e_y, z - e_z) of plane i, or its own row of plane
-// opp(i) where e_i crosses a plate.
-template <typename Store>
-__device__ __forceinline__ void issue_row(const Store* fsrc, const Geom& g, int r, Store* dst, uint32_t bar)
+// Warp 0: the source rows of row r into one stage, completing on bar.  Lane
+// 0 arms the barrier with the stage's bytes, then lane i < 19 copies
+// direction i -- row (y - e_y, z - e_z) of plane i, or its own row of plane
+// opp(i) where e_i crosses a plate -- to dst, and lanes 19 .. 21 copy row r of
+// the three components of the force F_lc to fdst.
+template <typename Store, typename Real>
+__device__ __forceinline__ void issue_row(const Store* fsrc, const Real* F, const Geom& g, int r, Store* dst,
+                                          Real* fdst, uint32_t bar)
 {
     const uint32_t row_bytes = (uint32_t)g.nx * sizeof(Store);
+    const uint32_t force_bytes = (uint32_t)g.nx * sizeof(Real);
     const int lane = (int)threadIdx.x & 31;
     if (lane == 0)
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(19u * row_bytes)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar),
+                     "r"(19u * row_bytes + 3u * force_bytes)
                      : "memory");
     __syncwarp();
     if (lane < 19) {
@@ -634,6 +641,13 @@ __device__ __forceinline__ void issue_row(const Store* fsrc, const Geom& g, int 
                 smem_addr(dst + (size_t)lane * g.nx)),
             "l"(src), "r"(row_bytes), "r"(bar)
             : "memory");
+    } else if (lane < 22) {
+        const int a = lane - 19;
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                smem_addr(fdst + (size_t)a * g.nx)),
+            "l"(F + (size_t)a * g.N + (size_t)r * g.nx), "r"(force_bytes), "r"(bar)
+            : "memory");
     }
 }
 
@@ -644,6 +658,7 @@ __global__ void __launch_bounds__(kRowMaxNx / kRowSPT, kRowMinBlocks) lb_rows_ke
 {
     static_assert(sizeof(Store) == 2 && Macro < 2, "row staging: 16-bit stores, no diagnostics partials");
     static_assert(kRowSPT == 4, "the staged rows are read as aligned 4-site chunks");
+    static_assert(std::is_same<Real, float>::value, "16-bit stores compute in FP32");
     NH_D3Q19_TABLES
     extern __shared__ __align__(128) unsigned char rows_smem[];
     __shared__ __align__(8) uint64_t full[kRowStages];
@@ -651,7 +666,11 @@ __global__ void __launch_bounds__(kRowMaxNx / kRowSPT, kRowMinBlocks) lb_rows_ke
     __shared__ bool last;
     const Geom& g = c.g;
     const int nx = g.nx, N = g.N;
-    Store* stages = reinterpret_cast<Store*>(rows_smem);
+    // stage q: 19 population rows (Store) then the 3 force rows (Real) of one x-row
+    const size_t pop_bytes = (size_t)19 * nx * sizeof(Store);
+    const size_t stage_bytes = pop_bytes + (size_t)3 * nx * sizeof(Real);
+    auto pop_stage = [&](int q) { return reinterpret_cast<Store*>(rows_smem + (size_t)q * stage_bytes); };
+    auto force_stage = [&](int q) { return reinterpret_cast<Real*>(rows_smem + (size_t)q * stage_bytes + pop_bytes); };
     const int rows = g.ny * g.nz;
     const int my_rows = (int)blockIdx.x < rows ? (rows - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const float inv_in = 1.f / c.scales[c.src];
@@ -670,7 +689,7 @@ __global__ void __launch_bounds__(kRowMaxNx / kRowSPT, kRowMinBlocks) lb_rows_ke
     const bool issuer = threadIdx.x < 32;  // warp 0 issues the copies, one direction per lane
     if (issuer)
         for (int k = 0; k < kRowStages && k < my_rows; ++k)
-            issue_row(c.fsrc, g, (int)blockIdx.x + k * (int)gridDim.x, stages + (size_t)k * 19 * nx,
+            issue_row(c.fsrc, c.F, g, (int)blockIdx.x + k * (int)gridDim.x, pop_stage(k), force_stage(k),
                       smem_addr(&full[k]));
     int k = 0;
     bool timed_out = false;
@@ -682,7 +701,7 @@ __global__ void __launch_bounds__(kRowMaxNx / kRowSPT, kRowMinBlocks) lb_rows_ke
             break;
         }
         const int r = (int)blockIdx.x + k * (int)gridDim.x;
-        const Store* st = stages + (size_t)stage * 19 * nx;
+        const Store* st = pop_stage(stage);
         const int z = r / g.ny;
         Real f[kRowSPT][19];
 #pragma unroll
@@ -711,16 +730,23 @@ __global__ void __launch_bounds__(kRowMaxNx / kRowSPT, kRowMinBlocks) lb_rows_ke
                 f[3][i] = b[0];
             }
         }
+        float4 fl[3];  // F_lc of the thread's four sites, per component
+#pragma unroll
+        for (int a = 0; a < 3; ++a) fl[a] = *reinterpret_cast<const float4*>(force_stage(stage) + a * nx + x0);
         __syncthreads();  // the stage is read: refill it with the row kRowStages ahead
         if (issuer && k + kRowStages < my_rows)
-            issue_row(c.fsrc, g, (int)blockIdx.x + (k + kRowStages) * (int)gridDim.x,
-                      stages + (size_t)stage * 19 * nx, smem_addr(&full[stage]));
+            issue_row(c.fsrc, c.F, g, (int)blockIdx.x + (k + kRowStages) * (int)gridDim.x, pop_stage(stage),
+                      force_stage(stage), smem_addr(&full[stage]));
         const int s0 = r * nx + x0;
         Real fo[kRowSPT][19];
 #pragma unroll
-        for (int j = 0; j < kRowSPT; ++j)
-            lb_collide_site<Real, Store, Shifted, Macro>(c, s0 + j, f[j], fo[j], inv_in, scale_out, psum, pmax, pbad,
-                                                        amax);
+        for (int j = 0; j < kRowSPT; ++j) {
+            const float fx = j == 0 ? fl[0].x : (j == 1 ? fl[0].y : (j == 2 ? fl[0].z : fl[0].w));
+            const float fy = j == 0 ? fl[1].x : (j == 1 ? fl[1].y : (j == 2 ? fl[1].z : fl[1].w));
+            const float fz = j == 0 ? fl[2].x : (j == 1 ? fl[2].y : (j == 2 ? fl[2].z : fl[2].w));
+            lb_collide_site<Real, Store, Shifted, Macro>(c, s0 + j, f[j], fo[j], fx, fy, fz, inv_in, scale_out, psum,
+                                                        pmax, pbad, amax);
+        }
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
             const Real v[4] = {fo[0][i], fo[1][i], fo[2][i], fo[3][i]};
@@ -738,7 +764,10 @@ __global__ void __launch_bounds__(kRowMaxNx / kRowSPT, kRowMinBlocks) lb_rows_ke
     scale_controller_block(c, amax, scale_out, (int)gridDim.x, wmax, last);
 }
 
-size_t lb_rows_smem(int nx, int store_bytes) { return (size_t)kRowStages * 19 * nx * store_bytes; }
+size_t lb_rows_smem(int nx, int store_bytes)
+{
+    return (size_t)kRowStages * ((size_t)19 * nx * store_bytes + (size_t)3 * nx * sizeof(float));
+}
 
 bool lb_rows_valid(int nx, int store_bytes)
 {
