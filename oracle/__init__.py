@@ -16,10 +16,9 @@ one site at a time, compiled without FMA contraction).  This module holds:
 Parity pins (see ``tests/test_oracle_*.py``) fix each routine against what the
 paper and the mathematics determine; the coupled loop is held to the energy
 dissipation and momentum balance of the Ericksen-Leslie equations, which fix
-the sign and index placement of every coupling term.  The absolute magnitude
-of the fully coupled backflow in a skyrmion channel has no closed form: that
-part is "parity unpinned" and is only checked for self-consistency (FP64 GPU
-vs oracle).
+the sign and index placement of every coupling term, and to the linear theory
+of a director wave coupled to shear flow, which fixes the size of the
+backflow.
 """
 from __future__ import annotations
 
